@@ -1,0 +1,273 @@
+"""CPU oracle of BLB's RNS-CKKS linear path (arXiv 2508.19525).
+
+TEST INFRASTRUCTURE ONLY: imported by the test suite, the smoke check and the
+benchmark's CPU-baseline leg, never by the product library.  This wrapper only
+marshals numpy arrays into the C oracle (oracle.c); every operation is computed
+there.
+"""
+import ctypes
+import numpy as np
+
+from .build import build
+
+_u64p = ctypes.POINTER(ctypes.c_uint64)
+_i64p = ctypes.POINTER(ctypes.c_int64)
+_f64p = ctypes.POINTER(ctypes.c_double)
+_u32p = ctypes.POINTER(ctypes.c_uint32)
+
+MAX_PRIMES = 32
+SECRET, KEY_A, KEY_E, ENC_A, ENC_E, MASK = 1, 2, 3, 4, 5, 6
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [("logN", ctypes.c_uint32), ("N", ctypes.c_uint32), ("nQ", ctypes.c_uint32),
+                ("nP", ctypes.c_uint32), ("dnum", ctypes.c_uint32), ("alpha", ctypes.c_uint32),
+                ("prime", ctypes.c_uint64 * MAX_PRIMES), ("psi", ctypes.c_uint64 * MAX_PRIMES)]
+
+
+class _GaloisSet(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_uint32), ("gal", _u64p), ("ksk", ctypes.POINTER(_u64p))]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = ctypes.CDLL(build())
+        L = _lib
+        L.orc_galois_elt.restype = ctypes.c_uint64
+        L.orc_ksk_words.restype = ctypes.c_uint64
+        L.orc_cp_num_rotations.restype = ctypes.c_uint32
+        L.orc_is_prime.argtypes = [ctypes.c_uint64]
+        L.orc_galois_elt.argtypes = [ctypes.c_void_p, ctypes.c_int32]
+    return _lib
+
+
+def _p(a, t):
+    return a.ctypes.data_as(t)
+
+
+def philox(ctr, key):
+    c = (ctypes.c_uint32 * 4)(*ctr)
+    k = (ctypes.c_uint32 * 2)(*key)
+    o = (ctypes.c_uint32 * 4)()
+    lib().orc_philox(c, k, o)
+    return list(o)
+
+
+def is_prime(n):
+    return bool(lib().orc_is_prime(ctypes.c_uint64(n)))
+
+
+def cdt_table():
+    t = np.zeros(19, np.uint64)
+    lib().orc_cdt_table(_p(t, _u64p))
+    return t
+
+
+def sample_ternary(N, seed, obj, purpose, j=0):
+    out = np.zeros(N, np.int64)
+    lib().orc_sample_ternary(ctypes.c_uint32(N), ctypes.c_uint64(seed), ctypes.c_uint32(obj),
+                             ctypes.c_uint32(purpose), ctypes.c_uint32(j), _p(out, _i64p))
+    return out
+
+
+def sample_gauss(N, seed, obj, purpose, j=0):
+    out = np.zeros(N, np.int64)
+    lib().orc_sample_gauss(ctypes.c_uint32(N), ctypes.c_uint64(seed), ctypes.c_uint32(obj),
+                           ctypes.c_uint32(purpose), ctypes.c_uint32(j), _p(out, _i64p))
+    return out
+
+
+def sample_uniform(N, q, seed, obj, purpose, j=0):
+    out = np.zeros(N, np.uint64)
+    lib().orc_sample_uniform(ctypes.c_uint32(N), ctypes.c_uint64(q), ctypes.c_uint64(seed),
+                             ctypes.c_uint32(obj), ctypes.c_uint32(purpose), ctypes.c_uint32(j),
+                             _p(out, _u64p))
+    return out
+
+
+class Oracle:
+    """One parameter set.  Polynomials are numpy uint64 arrays in coefficient
+    form, shape (..., limbs, N); ciphertexts have shape (polys, level+1, N)."""
+
+    def __init__(self, logN, q_bits, p_bits, dnum):
+        self.P = _Params()
+        qb = (ctypes.c_uint32 * len(q_bits))(*q_bits)
+        pb = (ctypes.c_uint32 * len(p_bits))(*p_bits)
+        rc = lib().orc_params_init(ctypes.byref(self.P), logN, len(q_bits), len(p_bits), qb, pb, dnum)
+        if rc:
+            raise ValueError(f"orc_params_init failed: {rc}")
+        self.logN, self.N = logN, 1 << logN
+        self.nQ, self.nP, self.dnum, self.alpha = len(q_bits), len(p_bits), dnum, self.P.alpha
+        self.primes = [int(self.P.prime[i]) for i in range(self.nQ + self.nP)]
+        self.psi = [int(self.P.psi[i]) for i in range(self.nQ + self.nP)]
+        self._pp = ctypes.byref(self.P)
+
+    # -- ring --------------------------------------------------------------
+    def galois_elt(self, r):
+        return int(lib().orc_galois_elt(self._pp, r))
+
+    def ntt(self, a, prime_idx):
+        a = np.ascontiguousarray(a, np.uint64).copy()
+        lib().orc_ntt(self._pp, prime_idx, _p(a, _u64p))
+        return a
+
+    def intt(self, a, prime_idx):
+        a = np.ascontiguousarray(a, np.uint64).copy()
+        lib().orc_intt(self._pp, prime_idx, _p(a, _u64p))
+        return a
+
+    def negacyclic_mul(self, a, b, prime_idx):
+        a = np.ascontiguousarray(a, np.uint64)
+        b = np.ascontiguousarray(b, np.uint64)
+        out = np.zeros(self.N, np.uint64)
+        lib().orc_negacyclic_mul(self._pp, prime_idx, _p(a, _u64p), _p(b, _u64p), _p(out, _u64p))
+        return out
+
+    # -- encoding ----------------------------------------------------------
+    def encode_int(self, z, scale):
+        z = np.ascontiguousarray(z, np.float64)
+        out = np.zeros(self.N, np.int64)
+        rc = lib().orc_encode_int(self._pp, _p(z, _f64p), len(z), ctypes.c_double(scale), _p(out, _i64p))
+        if rc:
+            raise ValueError(f"encode failed {rc}")
+        return out
+
+    def encode(self, z, level, scale):
+        z = np.ascontiguousarray(z, np.float64)
+        out = np.zeros((level + 1, self.N), np.uint64)
+        rc = lib().orc_encode(self._pp, _p(z, _f64p), len(z), level, ctypes.c_double(scale), _p(out, _u64p))
+        if rc:
+            raise ValueError(f"encode failed {rc}")
+        return out
+
+    def decode(self, coef, scale):
+        coef = np.ascontiguousarray(coef, np.int64)
+        z = np.zeros(self.N // 2, np.float64)
+        lib().orc_decode(self._pp, _p(coef, _i64p), ctypes.c_double(scale), _p(z, _f64p))
+        return z
+
+    def centered(self, limb, prime_idx=0):
+        q = self.primes[prime_idx]
+        v = np.asarray(limb, np.uint64)
+        return np.where(v > q // 2, -(np.uint64(q) - v).astype(np.int64), v.astype(np.int64))
+
+    # -- keys --------------------------------------------------------------
+    def ksk_shape(self):
+        return (self.dnum, 2, self.nQ + self.nP, self.N)
+
+    def keygen_secret(self, seed):
+        s = np.zeros(self.N, np.int64)
+        lib().orc_keygen_secret(self._pp, ctypes.c_uint64(seed), _p(s, _i64p))
+        return s
+
+    def keygen_relin(self, seed, s):
+        k = np.zeros(self.ksk_shape(), np.uint64)
+        lib().orc_keygen_relin(self._pp, ctypes.c_uint64(seed), _p(s, _i64p), _p(k, _u64p))
+        return k
+
+    def keygen_galois(self, seed, s, g):
+        k = np.zeros(self.ksk_shape(), np.uint64)
+        lib().orc_keygen_galois(self._pp, ctypes.c_uint64(seed), _p(s, _i64p), ctypes.c_uint64(g), _p(k, _u64p))
+        return k
+
+    def keygen_ksk(self, seed, s, s_prime, obj):
+        k = np.zeros(self.ksk_shape(), np.uint64)
+        s_prime = np.ascontiguousarray(s_prime, np.int64)
+        lib().orc_keygen_ksk(self._pp, ctypes.c_uint64(seed), _p(s, _i64p), _p(s_prime, _i64p), obj, _p(k, _u64p))
+        return k
+
+    # -- ciphertexts -------------------------------------------------------
+    def encrypt(self, s, pt, seed, nonce):
+        pt = np.ascontiguousarray(pt, np.uint64)
+        level = pt.shape[0] - 1
+        ct = np.zeros((2, level + 1, self.N), np.uint64)
+        lib().orc_encrypt(self._pp, _p(s, _i64p), _p(pt, _u64p), level, ctypes.c_uint64(seed), nonce, _p(ct, _u64p))
+        return ct
+
+    def decrypt(self, s, ct):
+        ct = np.ascontiguousarray(ct, np.uint64)
+        npolys, n = ct.shape[0], ct.shape[1]
+        m = np.zeros((n, self.N), np.uint64)
+        lib().orc_decrypt(self._pp, _p(s, _i64p), _p(ct, _u64p), n - 1, npolys, _p(m, _u64p))
+        return m
+
+    def automorphism(self, poly, g):
+        poly = np.ascontiguousarray(poly, np.uint64)
+        out = np.zeros_like(poly)
+        lib().orc_automorphism(self._pp, _p(poly, _u64p), poly.shape[0], ctypes.c_uint64(g), _p(out, _u64p))
+        return out
+
+    def keyswitch(self, d, ksk):
+        d = np.ascontiguousarray(d, np.uint64)
+        n = d.shape[0]
+        out = np.zeros((2, n, self.N), np.uint64)
+        lib().orc_keyswitch(self._pp, _p(d, _u64p), n - 1, _p(np.ascontiguousarray(ksk), _u64p), _p(out, _u64p))
+        return out
+
+    def rotate(self, ct, r, gksk):
+        ct = np.ascontiguousarray(ct, np.uint64)
+        out = np.zeros_like(ct)
+        lib().orc_rotate(self._pp, _p(ct, _u64p), ct.shape[1] - 1, r, _p(np.ascontiguousarray(gksk), _u64p), _p(out, _u64p))
+        return out
+
+    def rescale(self, ct):
+        ct = np.ascontiguousarray(ct, np.uint64)
+        npolys, n = ct.shape[0], ct.shape[1]
+        out = np.zeros((npolys, n - 1, self.N), np.uint64)
+        lib().orc_rescale(self._pp, _p(ct, _u64p), n - 1, npolys, _p(out, _u64p))
+        return out
+
+    def mul_plain(self, ct, pt):
+        ct = np.ascontiguousarray(ct, np.uint64)
+        out = np.zeros_like(ct)
+        lib().orc_mul_plain(self._pp, _p(ct, _u64p), _p(np.ascontiguousarray(pt, np.uint64), _u64p), ct.shape[1] - 1, _p(out, _u64p))
+        return out
+
+    def tensor(self, a, b):
+        a = np.ascontiguousarray(a, np.uint64)
+        b = np.ascontiguousarray(b, np.uint64)
+        out = np.zeros((3,) + a.shape[1:], np.uint64)
+        lib().orc_tensor(self._pp, _p(a, _u64p), _p(b, _u64p), a.shape[1] - 1, _p(out, _u64p))
+        return out
+
+    def relinearize(self, ct3, rksk):
+        ct3 = np.ascontiguousarray(ct3, np.uint64)
+        out = np.zeros((2,) + ct3.shape[1:], np.uint64)
+        lib().orc_relinearize(self._pp, _p(ct3, _u64p), ct3.shape[1] - 1, _p(np.ascontiguousarray(rksk), _u64p), _p(out, _u64p))
+        return out
+
+    # -- protocols ---------------------------------------------------------
+    def matmul_cp(self, X_cts, m, d, W, d_out, b1, galois, out_idx=None):
+        """X_cts: (nX, 2, level+1, N); galois: dict g -> ksk array."""
+        X_cts = np.ascontiguousarray(X_cts, np.uint64)
+        nX, level = X_cts.shape[0], X_cts.shape[2] - 1
+        k = (self.N // 2) // m
+        nY = (d_out + k - 1) // k
+        out_idx = list(range(nY)) if out_idx is None else list(out_idx)
+        W = np.ascontiguousarray(W, np.float64)
+        gals = np.array(list(galois.keys()), np.uint64)
+        keys = [np.ascontiguousarray(galois[int(g)], np.uint64) for g in gals]
+        ptrs = (_u64p * len(keys))(*[_p(kk, _u64p) for kk in keys])
+        gs = _GaloisSet(len(keys), _p(gals, _u64p), ptrs)
+        oi = np.array(out_idx, np.uint32)
+        Y = np.zeros((len(out_idx), 2, level, self.N), np.uint64)
+        rc = lib().orc_matmul_cp(self._pp, ctypes.byref(gs), _p(X_cts, _u64p), nX, level, m, d,
+                                 _p(W, _f64p), d_out, b1, _p(oi, _u32p), len(out_idx), _p(Y, _u64p))
+        if rc:
+            raise ValueError(f"orc_matmul_cp failed: {rc}")
+        return Y
+
+    def cp_num_rotations(self, nX, nY, b1, G):
+        return int(lib().orc_cp_num_rotations(nX, nY, b1, G))
+
+    def he2mpc(self, ct, seed, nonce):
+        ct = np.ascontiguousarray(ct, np.uint64)
+        masked = np.zeros((2, 1, self.N), np.uint64)
+        share = np.zeros(self.N, np.uint64)
+        lib().orc_he2mpc(self._pp, _p(ct, _u64p), ct.shape[1] - 1, ctypes.c_uint64(seed), nonce,
+                         _p(masked, _u64p), _p(share, _u64p))
+        return masked, share

@@ -1,0 +1,896 @@
+/*
+ * oracle.c -- plain CPU oracle of BLB's RNS-CKKS linear path.
+ *
+ * TEST INFRASTRUCTURE ONLY (see oracle.h).  Written for a reader checking it
+ * against the paper by eye: one function per operation, steps in the order
+ * the operation is defined, modular products as (__int128)a*b % q.
+ *
+ * Paper passages followed (arXiv 2508.19525):
+ *   Sec. 2.1  notation: A_{N,q} = Z_q[X]/(X^N+1), centered Z_q
+ *   Sec. 2.4  CKKS plaintext/ciphertext, rescale, HomAdd/HomMul, Rot_l / Rot_r
+ *   Sec. 6.1  Eq. 2: Encode(m) = round(Delta * pi^-1(m)), Decode = pi(Delta^-1 m)
+ *   Sec. 4.2.1 spatial-first packing; Sec. 5 matmul protocols (BOLT's ct-pt
+ *             product is cited there, not restated; the reading implemented
+ *             here is the standard diagonal method with baby-step giant-step,
+ *             App. C.1)
+ *   Sec. 6.3 / Alg. 1  secure CKKS-to-MPC masking with a uniform mask
+ * Where the paper is silent (key switching, sampling, prime choice, rounding
+ * modes) the readings are the ones listed in the design notes; each function
+ * below states the one it implements.
+ */
+#include "oracle.h"
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef unsigned __int128 u128;
+
+/* ------------------------------------------------------------------------- */
+/* modular arithmetic                                                          */
+/* ------------------------------------------------------------------------- */
+static uint64_t mulmod(uint64_t a, uint64_t b, uint64_t q) { return (uint64_t)(((u128)a * b) % q); }
+static uint64_t addmod(uint64_t a, uint64_t b, uint64_t q) { uint64_t s = a + b; return s >= q ? s - q : s; }
+static uint64_t submod(uint64_t a, uint64_t b, uint64_t q) { return a >= b ? a - b : a + q - b; }
+static uint64_t negmod(uint64_t a, uint64_t q) { return a ? q - a : 0; }
+static uint64_t powmod(uint64_t b, uint64_t e, uint64_t q)
+{
+    uint64_t r = 1 % q;
+    b %= q;
+    while (e) {
+        if (e & 1) r = mulmod(r, b, q);
+        b = mulmod(b, b, q);
+        e >>= 1;
+    }
+    return r;
+}
+/* q prime: a^(q-2) is the inverse (Fermat). */
+static uint64_t invmod(uint64_t a, uint64_t q) { return powmod(a % q, q - 2, q); }
+/* signed integer -> residue in [0, q) */
+static uint64_t from_signed(int64_t v, uint64_t q)
+{
+    if (v >= 0) return (uint64_t)v % q;
+    uint64_t r = (uint64_t)(-(v + 1)) % q; /* -(v+1) avoids overflow at INT64_MIN */
+    return q - 1 - r;
+}
+
+/* Deterministic Miller-Rabin: the first twelve primes as bases decide every
+ * n < 3.3e24, which covers all 64-bit n. */
+int orc_is_prime(uint64_t n)
+{
+    static const uint64_t bases[12] = {2, 3, 5, 7, 11, 13, 17, 19, 23, 29, 31, 37};
+    if (n < 2) return 0;
+    for (int i = 0; i < 12; i++) {
+        if (n == bases[i]) return 1;
+        if (n % bases[i] == 0) return 0;
+    }
+    uint64_t d = n - 1;
+    int r = 0;
+    while ((d & 1) == 0) { d >>= 1; r++; }
+    for (int i = 0; i < 12; i++) {
+        uint64_t x = powmod(bases[i], d, n);
+        if (x == 1 || x == n - 1) continue;
+        int composite = 1;
+        for (int k = 1; k < r; k++) {
+            x = mulmod(x, x, n);
+            if (x == n - 1) { composite = 0; break; }
+        }
+        if (composite) return 0;
+    }
+    return 1;
+}
+
+static uint32_t bitrev(uint32_t x, uint32_t bits)
+{
+    uint32_t r = 0;
+    for (uint32_t i = 0; i < bits; i++) r |= ((x >> i) & 1u) << (bits - 1 - i);
+    return r;
+}
+
+/* ------------------------------------------------------------------------- */
+/* parameters                                                                  */
+/* ------------------------------------------------------------------------- */
+/* Prime rule (the paper fixes only bit widths, Table 4 / Sec. 7.1): for each
+ * requested bit size b, in the order q_0, q_1, ..., p_0, p_1, ..., take the
+ * largest prime below 2^b that is 1 mod 2N and not already taken.
+ * psi rule: the first x = 2, 3, ... whose power x^((q-1)/2N) has order exactly
+ * 2N (i.e. its N-th power is -1); that power is psi. */
+int orc_params_init(orc_params* p, uint32_t logN, uint32_t nQ, uint32_t nP,
+                    const uint32_t* q_bits, const uint32_t* p_bits, uint32_t dnum)
+{
+    memset(p, 0, sizeof(*p));
+    if (logN < 2 || logN > 17 || nQ < 1 || nP < 1 || nQ + nP > ORC_MAX_PRIMES || dnum < 1) return -1;
+    p->logN = logN;
+    p->N = 1u << logN;
+    p->nQ = nQ;
+    p->nP = nP;
+    p->dnum = dnum;
+    p->alpha = (nQ + dnum - 1) / dnum;
+    const uint64_t twoN = 2ull * p->N;
+    for (uint32_t i = 0; i < nQ + nP; i++) {
+        uint32_t b = i < nQ ? q_bits[i] : p_bits[i - nQ];
+        if (b < logN + 2 || b > 62) return -2;
+        uint64_t top = (1ull << b) - 1;
+        uint64_t c = top - (top - 1) % twoN; /* largest value <= 2^b - 1 that is 1 mod 2N */
+        for (;;) {
+            if (c <= twoN) return -3;
+            int used = 0;
+            for (uint32_t k = 0; k < i; k++) used |= (p->prime[k] == c);
+            if (!used && orc_is_prime(c)) break;
+            c -= twoN;
+        }
+        p->prime[i] = c;
+        for (uint64_t x = 2;; x++) {
+            uint64_t w = powmod(x, (c - 1) / twoN, c);
+            if (powmod(w, p->N, c) == c - 1) { p->psi[i] = w; break; }
+        }
+    }
+    return 0;
+}
+
+/* Rot_l^r is the automorphism X -> X^g with g = 5^r mod 2N; a right rotation
+ * by r is a left rotation by -r, and 5 has order N/2 (Sec. 2.4). */
+uint64_t orc_galois_elt(const orc_params* p, int32_t r)
+{
+    int64_t s = p->N / 2;
+    int64_t e = ((int64_t)r % s + s) % s;
+    return powmod(5, (uint64_t)e, 2ull * p->N);
+}
+
+/* ------------------------------------------------------------------------- */
+/* NTT                                                                         */
+/* ------------------------------------------------------------------------- */
+/* Forward negacyclic NTT, Cooley-Tukey butterflies with the psi powers in
+ * bit-reversed order, natural-order input, output A[k] = a(psi^(2 brv(k)+1)).
+ * (The tests check this statement against the O(N^2) definition.) */
+void orc_ntt(const orc_params* p, uint32_t pi, uint64_t* a)
+{
+    const uint32_t N = p->N, logN = p->logN;
+    const uint64_t q = p->prime[pi], psi = p->psi[pi];
+    for (uint32_t m = 1, t = N / 2; m < N; m <<= 1, t >>= 1) {
+        for (uint32_t i = 0; i < m; i++) {
+            uint64_t S = powmod(psi, bitrev(m + i, logN), q);
+            for (uint32_t j = 2 * i * t; j < 2 * i * t + t; j++) {
+                uint64_t U = a[j], V = mulmod(a[j + t], S, q);
+                a[j] = addmod(U, V, q);
+                a[j + t] = submod(U, V, q);
+            }
+        }
+    }
+}
+
+/* Inverse of orc_ntt: Gentleman-Sande butterflies with psi^-1 powers, then
+ * multiplication by N^-1. */
+void orc_intt(const orc_params* p, uint32_t pi, uint64_t* a)
+{
+    const uint32_t N = p->N, logN = p->logN;
+    const uint64_t q = p->prime[pi], psi_inv = invmod(p->psi[pi], q);
+    for (uint32_t m = N, t = 1; m > 1; m >>= 1, t <<= 1) {
+        uint32_t h = m / 2;
+        for (uint32_t i = 0; i < h; i++) {
+            uint64_t S = powmod(psi_inv, bitrev(h + i, logN), q);
+            for (uint32_t j = 2 * i * t; j < 2 * i * t + t; j++) {
+                uint64_t U = a[j], V = a[j + t];
+                a[j] = addmod(U, V, q);
+                a[j + t] = mulmod(submod(U, V, q), S, q);
+            }
+        }
+    }
+    uint64_t n_inv = invmod(N, q);
+    for (uint32_t j = 0; j < N; j++) a[j] = mulmod(a[j], n_inv, q);
+}
+
+/* a*b in Z_q[X]/(X^N+1) via forward NTT, pointwise product, inverse NTT. */
+void orc_negacyclic_mul(const orc_params* p, uint32_t pi, const uint64_t* a, const uint64_t* b,
+                        uint64_t* out)
+{
+    const uint32_t N = p->N;
+    const uint64_t q = p->prime[pi];
+    uint64_t* A = malloc(sizeof(uint64_t) * N);
+    uint64_t* B = malloc(sizeof(uint64_t) * N);
+    memcpy(A, a, sizeof(uint64_t) * N);
+    memcpy(B, b, sizeof(uint64_t) * N);
+    orc_ntt(p, pi, A);
+    orc_ntt(p, pi, B);
+    for (uint32_t j = 0; j < N; j++) A[j] = mulmod(A[j], B[j], q);
+    orc_intt(p, pi, A);
+    memcpy(out, A, sizeof(uint64_t) * N);
+    free(A);
+    free(B);
+}
+
+/* ------------------------------------------------------------------------- */
+/* sampling                                                                    */
+/* ------------------------------------------------------------------------- */
+/* Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy
+ * as 1, 2, 3", SC'11): ten rounds of two 32x32->64 multiplies with the
+ * published multipliers and Weyl key increments. */
+void orc_philox(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; round++) {
+        uint64_t p0 = (uint64_t)0xD2511F53u * c0;
+        uint64_t p1 = (uint64_t)0xCD9E8D57u * c2;
+        uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ k0;
+        uint32_t n1 = (uint32_t)p1;
+        uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ k1;
+        uint32_t n3 = (uint32_t)p0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* One 128-bit draw for coefficient i: counter (i, j, obj, purpose), key = seed. */
+static void draw(uint64_t seed, uint32_t i, uint32_t j, uint32_t obj, uint32_t purpose, uint32_t out[4])
+{
+    uint32_t ctr[4] = {i, j, obj, purpose};
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    orc_philox(ctr, key, out);
+}
+
+/* Cumulative table of |e| for the discrete Gaussian rho(x) = exp(-x^2/(2 sigma^2)),
+ * sigma = 3.2 (the usual CKKS error width), support cut at |x| <= 19:
+ * table[k] = floor(2^64 * P(|e| <= k)) for k = 0..18. */
+void orc_cdt_table(uint64_t table[19])
+{
+    const double sigma = 3.2;
+    double partial[20];
+    double acc = 1.0; /* rho(0) */
+    partial[0] = acc;
+    for (int x = 1; x <= 19; x++) {
+        acc += 2.0 * exp(-(double)(x * x) / (2.0 * sigma * sigma));
+        partial[x] = acc;
+    }
+    for (int k = 0; k < 19; k++) {
+        double cdf = partial[k] / acc;
+        table[k] = cdf < 1.0 ? (uint64_t)ldexp(cdf, 64) : UINT64_MAX;
+    }
+}
+
+/* Ternary secret: (u32 mod 3) - 1. */
+void orc_sample_ternary(uint32_t N, uint64_t seed, uint32_t obj, uint32_t purpose, uint32_t j,
+                        int64_t* out)
+{
+    for (uint32_t i = 0; i < N; i++) {
+        uint32_t r[4];
+        draw(seed, i, j, obj, purpose, r);
+        out[i] = (int64_t)(r[0] % 3u) - 1;
+    }
+}
+
+/* Discrete Gaussian by cumulative-table inversion: magnitude = number of table
+ * entries <= the 64-bit draw (words 0,1), sign from bit 0 of word 2. */
+void orc_sample_gauss(uint32_t N, uint64_t seed, uint32_t obj, uint32_t purpose, uint32_t j,
+                      int64_t* out)
+{
+    uint64_t T[19];
+    orc_cdt_table(T);
+    for (uint32_t i = 0; i < N; i++) {
+        uint32_t r[4];
+        draw(seed, i, j, obj, purpose, r);
+        uint64_t u = (uint64_t)r[0] | ((uint64_t)r[1] << 32);
+        int64_t k = 0;
+        for (int t = 0; t < 19; t++) k += (u >= T[t]);
+        out[i] = (r[2] & 1u) ? -k : k;
+    }
+}
+
+/* Uniform residue: the full 128-bit draw (word 3 most significant) mod q. */
+void orc_sample_uniform(uint32_t N, uint64_t q, uint64_t seed, uint32_t obj, uint32_t purpose,
+                        uint32_t j, uint64_t* out)
+{
+    for (uint32_t i = 0; i < N; i++) {
+        uint32_t r[4];
+        draw(seed, i, j, obj, purpose, r);
+        u128 v = ((u128)r[3] << 96) | ((u128)r[2] << 64) | ((u128)r[1] << 32) | (u128)r[0];
+        out[i] = (uint64_t)(v % q);
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* encode / decode (Sec. 6.1, Eq. 2)                                           */
+/* ------------------------------------------------------------------------- */
+/* Slot j of a real polynomial m is m(zeta^(5^j)), zeta = exp(i pi / N), j < N/2
+ * (real slots only, as in the footnote to Eq. 2).  With s = N/2 and
+ * v_t = m_t + i m_{t+s}, slot j equals sum_t v_t zeta^(t 5^j), an s-point DFT
+ * (root omega = zeta^4) of v_t zeta^t read at index k_j = (5^j - 1)/4.
+ * Encode inverts it: V[k_j] = z_j, a = inverse DFT (no 1/s), c_t = a_t zeta^-t,
+ * m_t = round(Re c_t * Delta/s), m_{t+s} = round(Im c_t * Delta/s), round half
+ * to even.  The DFT is the iterative radix-2 decimation-in-time FFT on
+ * bit-reversed input with the complex product (ac - bd, ad + bc) and
+ * zeta^k = (cos(pi k/N), sin(pi k/N)) from the C library; no fused multiply-add
+ * (this file is built with -ffp-contract=off). */
+typedef struct { double re, im; } cplx;
+
+static cplx cmul(cplx x, cplx w)
+{
+    double t1 = x.re * w.re, t2 = x.im * w.im, t3 = x.re * w.im, t4 = x.im * w.re;
+    cplx r = {t1 - t2, t3 + t4};
+    return r;
+}
+
+static cplx zeta_pow(uint32_t N, uint32_t k)
+{
+    double ang = M_PI * (double)k / (double)N;
+    cplx r = {cos(ang), sin(ang)};
+    return r;
+}
+
+/* In-place radix-2 DIT DFT of length s on A (already bit-reversed):
+ * sign = -1 computes sum_k A[k] omega^(-k t), sign = +1 uses omega^(+k t). */
+static void fft_dit(cplx* A, uint32_t s, uint32_t N, int sign)
+{
+    for (uint32_t len = 2; len <= s; len <<= 1) {
+        uint32_t half = len / 2, step = s / len;
+        for (uint32_t i = 0; i < s; i += len) {
+            for (uint32_t j = 0; j < half; j++) {
+                cplx w = zeta_pow(N, 4 * j * step);
+                if (sign < 0) w.im = -w.im;
+                cplx u = A[i + j];
+                cplx v = cmul(A[i + j + half], w);
+                A[i + j].re = u.re + v.re;
+                A[i + j].im = u.im + v.im;
+                A[i + j + half].re = u.re - v.re;
+                A[i + j + half].im = u.im - v.im;
+            }
+        }
+    }
+}
+
+int orc_encode_int(const orc_params* p, const double* z, uint32_t n, double scale, int64_t* out)
+{
+    const uint32_t N = p->N, s = N / 2, logs = p->logN - 1;
+    if (n > s) return -1;
+    cplx* V = calloc(s, sizeof(cplx));
+    cplx* A = calloc(s, sizeof(cplx));
+    uint64_t g = 1;
+    for (uint32_t j = 0; j < s; j++) {
+        uint32_t k = (uint32_t)((g - 1) / 4);
+        V[k].re = j < n ? z[j] : 0.0;
+        V[k].im = 0.0;
+        g = (g * 5) % (2ull * N);
+    }
+    for (uint32_t k = 0; k < s; k++) A[bitrev(k, logs)] = V[k];
+    fft_dit(A, s, N, -1);
+    const double f = scale / (double)s;
+    int rc = 0;
+    for (uint32_t t = 0; t < s; t++) {
+        cplx w = zeta_pow(N, t);
+        w.im = -w.im;
+        cplx c = cmul(A[t], w);
+        double re = rint(c.re * f), im = rint(c.im * f);
+        if (fabs(re) >= 9.2e18 || fabs(im) >= 9.2e18) rc = -2;
+        out[t] = (int64_t)re;
+        out[t + s] = (int64_t)im;
+    }
+    free(V);
+    free(A);
+    return rc;
+}
+
+int orc_encode(const orc_params* p, const double* z, uint32_t n, uint32_t level, double scale,
+               uint64_t* out)
+{
+    const uint32_t N = p->N;
+    int64_t* m = malloc(sizeof(int64_t) * N);
+    int rc = orc_encode_int(p, z, n, scale, m);
+    for (uint32_t i = 0; i <= level; i++)
+        for (uint32_t t = 0; t < N; t++) out[(size_t)i * N + t] = from_signed(m[t], p->prime[i]);
+    free(m);
+    return rc;
+}
+
+/* Decode: z_j = (1/Delta) sum_t m_t zeta^(t 5^j) for signed coefficients m. */
+void orc_decode(const orc_params* p, const int64_t* coef, double scale, double* z)
+{
+    const uint32_t N = p->N, s = N / 2, logs = p->logN - 1;
+    cplx* A = calloc(s, sizeof(cplx));
+    for (uint32_t t = 0; t < s; t++) {
+        cplx v = {(double)coef[t], (double)coef[t + s]};
+        A[bitrev(t, logs)] = cmul(v, zeta_pow(N, t));
+    }
+    fft_dit(A, s, N, +1);
+    uint64_t g = 1;
+    for (uint32_t j = 0; j < s; j++) {
+        z[j] = A[(g - 1) / 4].re / scale;
+        g = (g * 5) % (2ull * N);
+    }
+    free(A);
+}
+
+/* ------------------------------------------------------------------------- */
+/* keys                                                                        */
+/* ------------------------------------------------------------------------- */
+uint64_t orc_ksk_words(const orc_params* p)
+{
+    return (uint64_t)p->dnum * 2 * (p->nQ + p->nP) * p->N;
+}
+
+void orc_keygen_secret(const orc_params* p, uint64_t seed, int64_t* s)
+{
+    orc_sample_ternary(p->N, seed, 0, ORC_SECRET, 0, s);
+}
+
+/* Hybrid key-switching key from s' to s (standard hybrid key switching; the
+ * paper uses rotations and relinearization, Sec. 2.4, without restating them).
+ * Digit j covers ciphertext primes D_j = {j*alpha, ..., min((j+1)*alpha, nQ)-1}.
+ * For every prime t of Q u P:
+ *   a_j[t] uniform (purpose KEY_A, sub-index 64*j + t),
+ *   e_j    Gaussian, shared by all primes of the digit (purpose KEY_E, sub-index j),
+ *   b_j[t] = -a_j[t]*s + e_j + [t in D_j] * (P mod q_t) * s'   (mod prime t).
+ * The gadget factor P*(Q/Q_j)*[(Q/Q_j)^-1 mod Q_j] is P mod q_t on the digit's
+ * own primes and 0 on every other prime, which is what the last term writes. */
+void orc_keygen_ksk(const orc_params* p, uint64_t seed, const int64_t* s, const int64_t* s_prime,
+                    uint32_t obj, uint64_t* ksk)
+{
+    const uint32_t N = p->N, L = p->nQ + p->nP;
+    int64_t* e = malloc(sizeof(int64_t) * N);
+    uint64_t* a = malloc(sizeof(uint64_t) * N);
+    uint64_t* sq = malloc(sizeof(uint64_t) * N);
+    uint64_t* as = malloc(sizeof(uint64_t) * N);
+    for (uint32_t j = 0; j < p->dnum; j++) {
+        orc_sample_gauss(N, seed, obj, ORC_KEY_E, j, e);
+        for (uint32_t t = 0; t < L; t++) {
+            const uint64_t q = p->prime[t];
+            uint64_t* B = ksk + ((size_t)(j * 2 + 0) * L + t) * N;
+            uint64_t* A = ksk + ((size_t)(j * 2 + 1) * L + t) * N;
+            orc_sample_uniform(N, q, seed, obj, ORC_KEY_A, 64 * j + t, a);
+            for (uint32_t i = 0; i < N; i++) sq[i] = from_signed(s[i], q);
+            orc_negacyclic_mul(p, t, a, sq, as);
+            int in_digit = t < p->nQ && t >= j * p->alpha && t < (j + 1) * p->alpha;
+            uint64_t Pmod = 1 % q;
+            for (uint32_t k = 0; k < p->nP; k++) Pmod = mulmod(Pmod, p->prime[p->nQ + k] % q, q);
+            for (uint32_t i = 0; i < N; i++) {
+                uint64_t v = addmod(negmod(as[i], q), from_signed(e[i], q), q);
+                if (in_digit) v = addmod(v, mulmod(Pmod, from_signed(s_prime[i], q), q), q);
+                B[i] = v;
+                A[i] = a[i];
+            }
+        }
+    }
+    free(e); free(a); free(sq); free(as);
+}
+
+/* s^2 as a signed integer polynomial (coefficients are tiny for ternary s). */
+static void square_secret(uint32_t N, const int64_t* s, int64_t* s2)
+{
+    for (uint32_t k = 0; k < N; k++) s2[k] = 0;
+    for (uint32_t i = 0; i < N; i++) {
+        if (!s[i]) continue;
+        for (uint32_t j = 0; j < N; j++) {
+            if (!s[j]) continue;
+            uint32_t k = i + j;
+            int64_t v = s[i] * s[j];
+            if (k >= N) { k -= N; v = -v; }
+            s2[k] += v;
+        }
+    }
+}
+
+void orc_keygen_relin(const orc_params* p, uint64_t seed, const int64_t* s, uint64_t* ksk)
+{
+    int64_t* s2 = malloc(sizeof(int64_t) * p->N);
+    square_secret(p->N, s, s2);
+    orc_keygen_ksk(p, seed, s, s2, 0, ksk);
+    free(s2);
+}
+
+/* sigma_g on signed coefficients: X^i -> X^(i g mod 2N), negated past N. */
+static void automorph_signed(uint32_t N, const int64_t* in, uint64_t g, int64_t* out)
+{
+    for (uint32_t i = 0; i < N; i++) {
+        uint64_t k = ((uint64_t)i * g) % (2ull * N);
+        if (k < N) out[k] = in[i];
+        else out[k - N] = -in[i];
+    }
+}
+
+void orc_keygen_galois(const orc_params* p, uint64_t seed, const int64_t* s, uint64_t g, uint64_t* ksk)
+{
+    int64_t* sg = malloc(sizeof(int64_t) * p->N);
+    automorph_signed(p->N, s, g, sg);
+    orc_keygen_ksk(p, seed, s, sg, (uint32_t)g, ksk);
+    free(sg);
+}
+
+/* ------------------------------------------------------------------------- */
+/* ciphertext operations                                                       */
+/* ------------------------------------------------------------------------- */
+/* Secret-key encryption c = (-a*s + m + e, a): a uniform per prime (ENC_A,
+ * sub-index = prime index), e Gaussian shared by all primes (ENC_E), both keyed
+ * by the caller's nonce. */
+void orc_encrypt(const orc_params* p, const int64_t* s, const uint64_t* pt, uint32_t level,
+                 uint64_t seed, uint32_t nonce, uint64_t* ct)
+{
+    const uint32_t N = p->N, n = level + 1;
+    int64_t* e = malloc(sizeof(int64_t) * N);
+    orc_sample_gauss(N, seed, nonce, ORC_ENC_E, 0, e);
+    #pragma omp parallel for
+    for (uint32_t i = 0; i < n; i++) {
+        const uint64_t q = p->prime[i];
+        uint64_t* a = malloc(sizeof(uint64_t) * N);
+        uint64_t* sq = malloc(sizeof(uint64_t) * N);
+        uint64_t* as = malloc(sizeof(uint64_t) * N);
+        orc_sample_uniform(N, q, seed, nonce, ORC_ENC_A, i, a);
+        for (uint32_t k = 0; k < N; k++) sq[k] = from_signed(s[k], q);
+        orc_negacyclic_mul(p, i, a, sq, as);
+        uint64_t* c0 = ct + (size_t)i * N;
+        uint64_t* c1 = ct + ((size_t)n + i) * N;
+        for (uint32_t k = 0; k < N; k++) {
+            c0[k] = addmod(addmod(negmod(as[k], q), pt[(size_t)i * N + k], q), from_signed(e[k], q), q);
+            c1[k] = a[k];
+        }
+        free(a); free(sq); free(as);
+    }
+    free(e);
+}
+
+/* m = sum_k c_k * s^k over the ciphertext's polynomials (2, or 3 before
+ * relinearization). */
+void orc_decrypt(const orc_params* p, const int64_t* s, const uint64_t* ct, uint32_t level,
+                 uint32_t npolys, uint64_t* m)
+{
+    const uint32_t N = p->N, n = level + 1;
+    #pragma omp parallel for
+    for (uint32_t i = 0; i < n; i++) {
+        const uint64_t q = p->prime[i];
+        uint64_t* sp = malloc(sizeof(uint64_t) * N);
+        uint64_t* tmp = malloc(sizeof(uint64_t) * N);
+        for (uint32_t k = 0; k < N; k++) sp[k] = from_signed(s[k], q);
+        /* Horner: ((c_{np-1}) s + c_{np-2}) s + ... + c_0 */
+        uint64_t* h = malloc(sizeof(uint64_t) * N);
+        memcpy(h, ct + ((size_t)(npolys - 1) * n + i) * N, sizeof(uint64_t) * N);
+        for (int k = (int)npolys - 2; k >= 0; k--) {
+            orc_negacyclic_mul(p, i, h, sp, tmp);
+            const uint64_t* ck = ct + ((size_t)k * n + i) * N;
+            for (uint32_t t = 0; t < N; t++) h[t] = addmod(tmp[t], ck[t], q);
+        }
+        memcpy(m + (size_t)i * N, h, sizeof(uint64_t) * N);
+        free(sp); free(tmp); free(h);
+    }
+}
+
+void orc_automorphism(const orc_params* p, const uint64_t* in, uint32_t nlimbs, uint64_t g, uint64_t* out)
+{
+    const uint32_t N = p->N;
+    for (uint32_t l = 0; l < nlimbs; l++) {
+        const uint64_t* a = in + (size_t)l * N;
+        uint64_t* b = out + (size_t)l * N;
+        for (uint32_t i = 0; i < N; i++) {
+            uint64_t k = ((uint64_t)i * g) % (2ull * N);
+            if (k < N) b[k] = a[i];
+            else b[k - N] = negmod(a[i], p->prime[l]);
+        }
+    }
+}
+
+/* Fast base conversion (approximate, no overflow correction) from the primes
+ * src[0..ns) to prime t, for every coefficient c:
+ *   Conv(x)_t = sum_i [x_i * (S/s_i)^-1]_{s_i} * (S/s_i mod t)   mod t,
+ * S = prod_i s_i.  x holds ns limbs of N residues, limb i mod src[i]. */
+static void base_convert(uint32_t N, const uint64_t* const* x, const uint64_t* src, uint32_t ns,
+                         uint64_t t, uint64_t* out)
+{
+    uint64_t hat_inv[ORC_MAX_PRIMES], hat_t[ORC_MAX_PRIMES];
+    for (uint32_t i = 0; i < ns; i++) {
+        uint64_t hat_mod_si = 1 % src[i], h_t = 1 % t;
+        for (uint32_t k = 0; k < ns; k++) {
+            if (k == i) continue;
+            hat_mod_si = mulmod(hat_mod_si, src[k] % src[i], src[i]);
+            h_t = mulmod(h_t, src[k] % t, t);
+        }
+        hat_inv[i] = invmod(hat_mod_si, src[i]);
+        hat_t[i] = h_t;
+    }
+    for (uint32_t c = 0; c < N; c++) {
+        uint64_t acc = 0;
+        for (uint32_t i = 0; i < ns; i++) {
+            uint64_t y = mulmod(x[i][c], hat_inv[i], src[i]);
+            acc = addmod(acc, mulmod(y % t, hat_t[i], t), t);
+        }
+        out[c] = acc;
+    }
+}
+
+/* Hybrid key switching of one polynomial d (coefficient form, level l) with a
+ * key from s' to s; returns (k0, k1) with k0 + k1 s ~ d s' (mod Q_l):
+ *   1. decompose d into beta = ceil((l+1)/alpha) digits over the primes D_j;
+ *   2. ModUp: extend each digit to every prime of Q_l u P by fast base
+ *      conversion (the digit's own primes keep d's residues);
+ *   3. inner product with the key's digits over Q_l u P;
+ *   4. ModDown: k_i = (acc_i - Conv_{P->q_i}(acc_P)) * P^-1 mod q_i. */
+void orc_keyswitch(const orc_params* p, const uint64_t* d, uint32_t level, const uint64_t* ksk,
+                   uint64_t* out)
+{
+    const uint32_t N = p->N, n = level + 1, nP = p->nP, L = p->nQ + p->nP;
+    const uint32_t ext = n + nP; /* limbs of Q_l u P; index e < n is q_e, else p_{e-n} */
+    const uint32_t beta = (n + p->alpha - 1) / p->alpha;
+    uint64_t* acc = calloc((size_t)2 * ext * N, sizeof(uint64_t));
+
+    #pragma omp parallel for
+    for (uint32_t e = 0; e < ext; e++) {
+        const uint32_t pi = e < n ? e : p->nQ + (e - n);
+        const uint64_t t = p->prime[pi];
+        uint64_t* x = malloc(sizeof(uint64_t) * N);
+        uint64_t* kb = malloc(sizeof(uint64_t) * N);
+        uint64_t* ka = malloc(sizeof(uint64_t) * N);
+        uint64_t* xb = malloc(sizeof(uint64_t) * N);
+        uint64_t* xa = malloc(sizeof(uint64_t) * N);
+        uint64_t src[ORC_MAX_PRIMES];
+        const uint64_t* xs[ORC_MAX_PRIMES];
+        for (uint32_t j = 0; j < beta; j++) {
+            uint32_t lo = j * p->alpha, hi = (j + 1) * p->alpha;
+            if (hi > n) hi = n;
+            if (e >= lo && e < hi) {
+                memcpy(x, d + (size_t)e * N, sizeof(uint64_t) * N);
+            } else {
+                for (uint32_t i = lo; i < hi; i++) {
+                    src[i - lo] = p->prime[i];
+                    xs[i - lo] = d + (size_t)i * N;
+                }
+                base_convert(N, xs, src, hi - lo, t, x);
+            }
+            memcpy(kb, ksk + ((size_t)(j * 2 + 0) * L + pi) * N, sizeof(uint64_t) * N);
+            memcpy(ka, ksk + ((size_t)(j * 2 + 1) * L + pi) * N, sizeof(uint64_t) * N);
+            orc_negacyclic_mul(p, pi, x, kb, xb);
+            orc_negacyclic_mul(p, pi, x, ka, xa);
+            uint64_t* a0 = acc + (size_t)e * N;
+            uint64_t* a1 = acc + ((size_t)ext + e) * N;
+            for (uint32_t c = 0; c < N; c++) {
+                a0[c] = addmod(a0[c], xb[c], t);
+                a1[c] = addmod(a1[c], xa[c], t);
+            }
+        }
+        free(x); free(kb); free(ka); free(xb); free(xa);
+    }
+
+    /* ModDown */
+    uint64_t srcP[ORC_MAX_PRIMES];
+    for (uint32_t k = 0; k < nP; k++) srcP[k] = p->prime[p->nQ + k];
+    #pragma omp parallel for
+    for (uint32_t i = 0; i < n; i++) {
+        const uint64_t q = p->prime[i];
+        uint64_t Pinv = 1 % q;
+        for (uint32_t k = 0; k < nP; k++) Pinv = mulmod(Pinv, srcP[k] % q, q);
+        Pinv = invmod(Pinv, q);
+        const uint64_t* xs[ORC_MAX_PRIMES];
+        uint64_t* conv = malloc(sizeof(uint64_t) * N);
+        for (uint32_t poly = 0; poly < 2; poly++) {
+            const uint64_t* A = acc + (size_t)poly * ext * N;
+            uint64_t* o = out + ((size_t)poly * n + i) * N;
+            for (uint32_t k = 0; k < nP; k++) xs[k] = A + (size_t)(n + k) * N;
+            base_convert(N, xs, srcP, nP, q, conv);
+            for (uint32_t c = 0; c < N; c++) o[c] = mulmod(submod(A[(size_t)i * N + c], conv[c], q), Pinv, q);
+        }
+        free(conv);
+    }
+    free(acc);
+}
+
+/* Rot_l^r: apply X -> X^g (g = 5^r) to both polynomials, then switch the
+ * second from sigma_g(s) back to s and add. */
+void orc_rotate(const orc_params* p, const uint64_t* ct, uint32_t level, int32_t r,
+                const uint64_t* galois_ksk, uint64_t* out)
+{
+    const uint32_t N = p->N, n = level + 1;
+    const uint64_t g = orc_galois_elt(p, r);
+    uint64_t* rc = malloc(sizeof(uint64_t) * 2 * n * N);
+    uint64_t* ks = malloc(sizeof(uint64_t) * 2 * n * N);
+    orc_automorphism(p, ct, n, g, rc);
+    orc_automorphism(p, ct + (size_t)n * N, n, g, rc + (size_t)n * N);
+    orc_keyswitch(p, rc + (size_t)n * N, level, galois_ksk, ks);
+    for (uint32_t l = 0; l < n; l++) {
+        const uint64_t q = p->prime[l];
+        for (uint32_t i = 0; i < N; i++) {
+            out[(size_t)l * N + i] = addmod(rc[(size_t)l * N + i], ks[(size_t)l * N + i], q);
+            out[((size_t)n + l) * N + i] = ks[((size_t)n + l) * N + i];
+        }
+    }
+    free(rc);
+    free(ks);
+}
+
+/* Rescale (Sec. 2.4): divide by the last prime q_l with rounding,
+ * c_i <- (c_i - [c]_{q_l}) * q_l^-1 mod q_i, where [c]_{q_l} is the residue
+ * mod q_l lifted to the centered range (-q_l/2, q_l/2]. */
+void orc_rescale(const orc_params* p, const uint64_t* ct, uint32_t level, uint32_t npolys, uint64_t* out)
+{
+    const uint32_t N = p->N, n = level + 1;
+    const uint64_t ql = p->prime[level];
+    for (uint32_t poly = 0; poly < npolys; poly++) {
+        const uint64_t* last = ct + ((size_t)poly * n + level) * N;
+        for (uint32_t i = 0; i < level; i++) {
+            const uint64_t q = p->prime[i];
+            const uint64_t inv = invmod(ql % q, q);
+            const uint64_t* ci = ct + ((size_t)poly * n + i) * N;
+            uint64_t* o = out + ((size_t)poly * level + i) * N;
+            for (uint32_t c = 0; c < N; c++) {
+                uint64_t v = last[c];
+                int64_t centered = v > ql / 2 ? -(int64_t)(ql - v) : (int64_t)v;
+                o[c] = mulmod(submod(ci[c], from_signed(centered, q), q), inv, q);
+            }
+        }
+    }
+}
+
+/* Limb-wise sum of two polynomials with limbs over primes q_0..q_{nlimbs-1}. */
+void orc_add(const orc_params* p, const uint64_t* a, const uint64_t* b, uint32_t nlimbs, uint64_t* out)
+{
+    const uint32_t N = p->N;
+    for (uint32_t l = 0; l < nlimbs; l++)
+        for (uint32_t i = 0; i < N; i++)
+            out[(size_t)l * N + i] = addmod(a[(size_t)l * N + i], b[(size_t)l * N + i], p->prime[l]);
+}
+
+static void ct_add_inplace(const orc_params* p, uint64_t* acc, const uint64_t* b, uint32_t level, uint32_t npolys)
+{
+    const uint32_t N = p->N, n = level + 1;
+    for (uint32_t poly = 0; poly < npolys; poly++)
+        for (uint32_t l = 0; l < n; l++) {
+            uint64_t* a = acc + ((size_t)poly * n + l) * N;
+            const uint64_t* c = b + ((size_t)poly * n + l) * N;
+            for (uint32_t i = 0; i < N; i++) a[i] = addmod(a[i], c[i], p->prime[l]);
+        }
+}
+
+/* ct (x) pt: both polynomials times the plaintext (HomMul with a plaintext). */
+void orc_mul_plain(const orc_params* p, const uint64_t* ct, const uint64_t* pt, uint32_t level, uint64_t* out)
+{
+    const uint32_t N = p->N, n = level + 1;
+    #pragma omp parallel for
+    for (uint32_t l = 0; l < n; l++)
+        for (uint32_t poly = 0; poly < 2; poly++)
+            orc_negacyclic_mul(p, l, ct + ((size_t)poly * n + l) * N, pt + (size_t)l * N,
+                               out + ((size_t)poly * n + l) * N);
+}
+
+/* ct (x) ct before relinearization: (a0 b0, a0 b1 + a1 b0, a1 b1). */
+void orc_tensor(const orc_params* p, const uint64_t* a, const uint64_t* b, uint32_t level, uint64_t* out)
+{
+    const uint32_t N = p->N, n = level + 1;
+    #pragma omp parallel for
+    for (uint32_t l = 0; l < n; l++) {
+        const uint64_t q = p->prime[l];
+        uint64_t* t1 = malloc(sizeof(uint64_t) * N);
+        uint64_t* t2 = malloc(sizeof(uint64_t) * N);
+        const uint64_t *a0 = a + (size_t)l * N, *a1 = a + ((size_t)n + l) * N;
+        const uint64_t *b0 = b + (size_t)l * N, *b1 = b + ((size_t)n + l) * N;
+        orc_negacyclic_mul(p, l, a0, b0, out + (size_t)l * N);
+        orc_negacyclic_mul(p, l, a0, b1, t1);
+        orc_negacyclic_mul(p, l, a1, b0, t2);
+        for (uint32_t i = 0; i < N; i++) out[((size_t)n + l) * N + i] = addmod(t1[i], t2[i], q);
+        orc_negacyclic_mul(p, l, a1, b1, out + ((size_t)2 * n + l) * N);
+        free(t1); free(t2);
+    }
+}
+
+/* (d0, d1, d2) -> (d0 + k0, d1 + k1) with (k0, k1) = KeySwitch_{s^2 -> s}(d2). */
+void orc_relinearize(const orc_params* p, const uint64_t* ct3, uint32_t level, const uint64_t* relin_ksk, uint64_t* out)
+{
+    const uint32_t N = p->N, n = level + 1;
+    uint64_t* ks = malloc(sizeof(uint64_t) * 2 * n * N);
+    orc_keyswitch(p, ct3 + (size_t)2 * n * N, level, relin_ksk, ks);
+    for (uint32_t poly = 0; poly < 2; poly++)
+        for (uint32_t l = 0; l < n; l++)
+            for (uint32_t i = 0; i < N; i++) {
+                size_t o = ((size_t)poly * n + l) * N + i;
+                out[o] = addmod(ct3[o], ks[o], p->prime[l]);
+            }
+    free(ks);
+}
+
+/* ------------------------------------------------------------------------- */
+/* matmul_cp: ciphertext X (m x d) times plaintext W (d x d_out)               */
+/* ------------------------------------------------------------------------- */
+/* Packing (spatial-first, Sec. 4.2.1): with s = N/2 slots and k = s/m columns
+ * per ciphertext, ciphertext c holds X[i][c*k + b] at slot i + m*b.  Output
+ * ciphertext e holds Y[i][e*k + b] the same way.
+ * Diagonal method (the ct-pt product of BOLT that Sec. 4.2.1 and 5.2 build on):
+ *   Y_e = sum_c sum_{tau<k} Rot_l^{tau m}(X_c) (.) D_{c,e,tau},
+ *   D_{c,e,tau}[i + m b] = W[c k + (b + tau) mod k][e k + b].
+ * Baby-step giant-step (App. C.1) with tau = g*b1 + b, G = k/b1:
+ *   Y_e = sum_g Rot_l^{g b1 m}( sum_c sum_b Rot_l^{b m}(X_c) (.) D'_{c,e,g,b} ),
+ *   D'_{c,e,g,b}[i + m beta] = W[c k + (beta + b) mod k][e k + (beta - g b1) mod k],
+ * zero outside W.  Plaintexts are encoded at the level of X with scale q_l (the
+ * prime the final rescale drops), so Y_e returns to the scale of X. */
+uint32_t orc_cp_num_rotations(uint32_t nX, uint32_t nY, uint32_t b1, uint32_t G)
+{
+    return nX * (b1 - 1) + nY * (G - 1);
+}
+
+static const uint64_t* find_galois(const orc_params* p, const orc_galois_set* gk, int32_t r)
+{
+    uint64_t g = orc_galois_elt(p, r);
+    for (uint32_t i = 0; i < gk->n; i++)
+        if (gk->gal[i] == g) return gk->ksk[i];
+    return NULL;
+}
+
+int orc_matmul_cp(const orc_params* p, const orc_galois_set* gk, const uint64_t* X, uint32_t nX,
+                  uint32_t level, uint32_t m, uint32_t d, const double* W, uint32_t d_out,
+                  uint32_t b1, const uint32_t* out_idx, uint32_t n_out, uint64_t* Y)
+{
+    const uint32_t N = p->N, s = N / 2, n = level + 1;
+    if (level < 1 || m == 0 || s % m) return -1;
+    const uint32_t k = s / m;
+    if (b1 == 0 || k % b1 || nX != (d + k - 1) / k) return -1;
+    const uint32_t G = k / b1;
+    const size_t ctw = (size_t)2 * n * N;
+
+    /* baby steps: Rot^{b m}(X_c), b < b1 */
+    uint64_t* baby = malloc(sizeof(uint64_t) * ctw * nX * b1);
+    for (uint32_t c = 0; c < nX; c++) {
+        memcpy(baby + ((size_t)c * b1) * ctw, X + (size_t)c * ctw, sizeof(uint64_t) * ctw);
+        for (uint32_t b = 1; b < b1; b++) {
+            const uint64_t* key = find_galois(p, gk, (int32_t)(b * m));
+            if (!key) { free(baby); return -2; }
+            orc_rotate(p, X + (size_t)c * ctw, level, (int32_t)(b * m), key, baby + ((size_t)c * b1 + b) * ctw);
+        }
+    }
+
+    double* z = malloc(sizeof(double) * s);
+    uint64_t* pt = malloc(sizeof(uint64_t) * n * N);
+    uint64_t* prod = malloc(sizeof(uint64_t) * ctw);
+    uint64_t* T = malloc(sizeof(uint64_t) * ctw);
+    uint64_t* R = malloc(sizeof(uint64_t) * ctw);
+    uint64_t* acc = malloc(sizeof(uint64_t) * ctw);
+    const double pt_scale = (double)p->prime[level];
+    int rc = 0;
+    for (uint32_t oi = 0; oi < n_out && !rc; oi++) {
+        const uint32_t e = out_idx[oi];
+        memset(acc, 0, sizeof(uint64_t) * ctw);
+        for (uint32_t g = 0; g < G && !rc; g++) {
+            memset(T, 0, sizeof(uint64_t) * ctw);
+            for (uint32_t c = 0; c < nX; c++) {
+                for (uint32_t b = 0; b < b1; b++) {
+                    for (uint32_t beta = 0; beta < k; beta++) {
+                        uint32_t row = c * k + (beta + b) % k;
+                        uint32_t col = e * k + (beta + k - (g * b1) % k) % k;
+                        double w = (row < d && col < d_out) ? W[(size_t)row * d_out + col] : 0.0;
+                        for (uint32_t i = 0; i < m; i++) z[i + m * beta] = w;
+                    }
+                    if (orc_encode(p, z, s, level, pt_scale, pt)) rc = -3;
+                    orc_mul_plain(p, baby + ((size_t)c * b1 + b) * ctw, pt, level, prod);
+                    ct_add_inplace(p, T, prod, level, 2);
+                }
+            }
+            if (g == 0) {
+                ct_add_inplace(p, acc, T, level, 2);
+            } else {
+                const uint64_t* key = find_galois(p, gk, (int32_t)(g * b1 * m));
+                if (!key) { rc = -2; break; }
+                orc_rotate(p, T, level, (int32_t)(g * b1 * m), key, R);
+                ct_add_inplace(p, acc, R, level, 2);
+            }
+        }
+        orc_rescale(p, acc, level, 2, Y + (size_t)oi * 2 * level * N);
+    }
+    free(baby); free(z); free(pt); free(prod); free(T); free(R); free(acc);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------- */
+/* CKKS -> MPC masking (Alg. 1, first two steps; Sec. 6.3)                      */
+/* ------------------------------------------------------------------------- */
+/* The paper's conversion works modulo a single prime q.  The ciphertext is
+ * first reduced to level 0 (drop every limb but q_0), then P1 adds a mask
+ * r drawn uniformly from Z_{q_0}[X]/(X^N+1) (purpose MASK, keyed by the nonce)
+ * to the first polynomial and keeps -r as its share.  P0's share is the
+ * decryption of the masked ciphertext; the two shares sum to the message plus
+ * noise mod q_0. */
+void orc_he2mpc(const orc_params* p, const uint64_t* ct, uint32_t level, uint64_t seed,
+                uint32_t nonce, uint64_t* masked, uint64_t* p1_share)
+{
+    const uint32_t N = p->N, n = level + 1;
+    const uint64_t q0 = p->prime[0];
+    uint64_t* r = malloc(sizeof(uint64_t) * N);
+    orc_sample_uniform(N, q0, seed, nonce, ORC_MASK, 0, r);
+    for (uint32_t i = 0; i < N; i++) {
+        masked[i] = addmod(ct[i], r[i], q0);
+        masked[N + i] = ct[(size_t)n * N + i];
+        p1_share[i] = negmod(r[i], q0);
+    }
+    free(r);
+}
