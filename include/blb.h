@@ -1,0 +1,208 @@
+/*
+ * blb.h -- C ABI of the B300 RNS-CKKS linear path of BLB ("Breaking the Layer
+ * Barrier", arXiv 2508.19525): ciphertext x plaintext matrix products
+ * (matmul_cp, Sec. 4.2.1 / 5.2 with the baby-step giant-step split of App. C.1),
+ * the CKKS primitives they are built on (Sec. 2.4, Eq. 2) and the secure
+ * CKKS-to-MPC masking step (Alg. 1, Sec. 6.3).  Both parties of the protocol
+ * run in one process: "sending" a ciphertext is handing over a handle.
+ *
+ * Conventions
+ *  - Every entry point returns 0 (BLB_OK) or a negative BLB_ERR_* code and never
+ *    throws; blb_last_error() gives a message for the calling thread.
+ *  - Objects (context, keys, plaintexts, ciphertexts, cp plans) are opaque,
+ *    library-owned and device-resident; free them with the matching *_free.
+ *    Their device memory comes from the allocator installed with
+ *    blb_set_allocator (default: cudaMalloc / cudaFree).
+ *  - All device work of a context runs in order on the CUDA stream given to
+ *    blb_ctx_create (NULL = the legacy default stream).  Calls that return data
+ *    into host memory synchronize that stream before returning.
+ *  - Pointers marked "host or device" are classified with
+ *    cudaPointerGetAttributes; unregistered pointers are treated as host memory.
+ *  - Polynomials are stored limb-major: limb i holds N residues mod q_i in the
+ *    evaluation (NTT) domain.  Exports in coefficient form give the canonical
+ *    representation: residues in [0, q_i), limb-major, (level+1) x N words per
+ *    polynomial, polynomial-major for ciphertexts.
+ *  - Levels: a ciphertext at level l has the l+1 primes q_0..q_l.  Rescaling
+ *    drops q_l.
+ */
+#ifndef BLB_H
+#define BLB_H
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    BLB_OK = 0,
+    BLB_ERR_ARG = -1,     /* invalid argument: null pointer, size, shape, range */
+    BLB_ERR_LEVEL = -2,   /* no level left (rescale at level 0, product needs one) */
+    BLB_ERR_SCALE = -3,   /* operands carry different scales */
+    BLB_ERR_NO_KEY = -4,  /* the rotation / relinearization key is missing */
+    BLB_ERR_OOM = -5,     /* allocation failed */
+    BLB_ERR_CUDA = -6,    /* a CUDA runtime call failed (message has the details) */
+    BLB_ERR_TIMEOUT = -7, /* a bounded device wait expired */
+    BLB_ERR_PARAM = -8    /* parameter set rejected (no prime of a requested size) */
+};
+
+typedef struct blb_ctx blb_ctx;
+typedef struct blb_keys blb_keys;
+typedef struct blb_pt blb_pt;
+typedef struct blb_ct blb_ct;
+typedef struct blb_cp_plan blb_cp_plan;
+
+/* Parameter set.  q_bits[0..nQ) are the bit sizes of the ciphertext primes,
+ * p_bits[0..nP) those of the special primes of hybrid key switching; dnum is
+ * the number of key-switching digits (alpha = ceil(nQ/dnum) primes each; nP must
+ * be >= alpha).  Prime rule: for each size b, in the order q_0, q_1, ..., p_0,
+ * ..., the largest prime below 2^b that is 1 mod 2N and not already taken.
+ * scale is the default encoding scale Delta (informational). */
+typedef struct {
+    uint32_t logN;
+    uint32_t nQ, nP;
+    const uint32_t* q_bits;
+    const uint32_t* p_bits;
+    uint32_t dnum;
+    double scale;
+} blb_params;
+
+/* Baby-step giant-step split for matmul_cp: b1 baby steps, G = k/b1 giant
+ * steps (k = N/2/m columns per ciphertext); b1 must divide k.  b1 = 0 picks
+ * the power of two nearest sqrt(k) (rounded up). */
+typedef struct {
+    uint32_t b1;
+} blb_sched;
+
+/* ---- library ---------------------------------------------------------------
+ * Allocator used for all device memory of objects created afterwards.
+ * alloc(bytes, stream, user) returns a device pointer or NULL; free(ptr, bytes,
+ * stream, user).  Pass NULLs to restore cudaMalloc / cudaFree. */
+typedef void* (*blb_alloc_fn)(size_t bytes, void* stream, void* user);
+typedef void (*blb_free_fn)(void* ptr, size_t bytes, void* stream, void* user);
+int blb_set_allocator(blb_alloc_fn alloc, blb_free_fn free_fn, void* user);
+const char* blb_last_error(void);
+const char* blb_version(void);
+
+/* Host-only: the primes a parameter set selects (no GPU needed).
+ * out receives nQ + nP words (q_0..q_{nQ-1}, p_0..p_{nP-1}). */
+int blb_params_primes(const blb_params* params, uint64_t* out);
+
+/* ---- context ----------------------------------------------------------------
+ * Builds primes, NTT / base-conversion / encoding tables on the device.
+ * stream: a cudaStream_t (NULL = default stream). */
+int blb_ctx_create(const blb_params* params, void* stream, blb_ctx** out);
+void blb_ctx_free(blb_ctx* ctx);
+int blb_ctx_info(const blb_ctx* ctx, uint32_t* logN, uint32_t* nQ, uint32_t* nP, uint32_t* dnum);
+int blb_ctx_primes(const blb_ctx* ctx, uint64_t* out /* host, nQ + nP words */);
+int blb_ctx_sync(blb_ctx* ctx);
+/* Device memory currently held by this context and its objects (bytes). */
+uint64_t blb_ctx_bytes_in_use(const blb_ctx* ctx);
+
+/* ---- keys (Sec. 2.4: rotations and products need switching keys) -----------
+ * Secret key s (ternary) and switching keys drawn from Philox4x32-10 with key
+ * `seed`: relinearization key (s^2 -> s) if relin != 0, and one Galois key per
+ * left-rotation amount rot_steps[i] (negative = right rotation).  Each key has
+ * dnum digits over all nQ + nP primes. */
+int blb_keygen(blb_ctx* ctx, uint64_t seed, const int32_t* rot_steps, uint32_t n_rot, int relin,
+               blb_keys** out);
+void blb_keys_free(blb_keys* keys);
+/* Export in coefficient form to host memory.  which = 0: secret key, N signed
+ * words (int64).  which = 1: relinearization key; which = 2: Galois key for
+ * left rotation `rot`; both as dnum x 2 x (nQ+nP) x N words (b then a). */
+int blb_keys_export(blb_ctx* ctx, const blb_keys* keys, int which, int32_t rot, void* host_out);
+
+/* ---- encode / decode (Sec. 6.1, Eq. 2) -------------------------------------
+ * Encode n <= N/2 real slot values (host or device doubles; missing slots are
+ * 0) at `level` with `scale`: round(scale * pi^-1(z)) (round half to even),
+ * reduced mod q_0..q_level, stored in the NTT domain. */
+int blb_encode(blb_ctx* ctx, const double* vals, uint64_t n, uint32_t level, double scale,
+               blb_pt** out);
+void blb_pt_free(blb_pt* pt);
+/* Plaintext in coefficient form to host: (level+1) x N words. */
+int blb_pt_export(blb_ctx* ctx, const blb_pt* pt, uint64_t* host_out);
+
+/* ---- ciphertexts -------------------------------------------------------------
+ * Secret-key encryption (-a s + m + e, a); `nonce` selects the Philox stream of
+ * a and e (key = the keygen seed).  Only the low 32 bits of nonce are used. */
+int blb_encrypt(blb_ctx* ctx, const blb_keys* keys, const blb_pt* pt, uint64_t nonce, blb_ct** out);
+void blb_ct_free(blb_ct* ct);
+int blb_ct_info(const blb_ct* ct, uint32_t* level, uint32_t* npolys, double* scale);
+/* Export in coefficient form: npolys x (level+1) x N words into host or device
+ * memory. */
+int blb_ct_export(blb_ctx* ctx, const blb_ct* ct, uint64_t* out);
+/* Import a ciphertext given in coefficient form (host or device words,
+ * npolys x (level+1) x N, residues in [0, q_i)). */
+int blb_ct_import(blb_ctx* ctx, const uint64_t* coeffs, uint32_t level, uint32_t npolys,
+                  double scale, blb_ct** out);
+/* Decrypt (m = c0 + c1 s [+ c2 s^2]).  coeff_limbs (nullable, host or device):
+ * (level+1) x N words, coefficient form.  slots (nullable, host or device):
+ * N/2 doubles, the decoding of the q_0 limb lifted to (-q_0/2, q_0/2] and divided
+ * by the ciphertext's scale (exact while |message| < q_0/2). */
+int blb_decrypt(blb_ctx* ctx, const blb_keys* keys, const blb_ct* ct, uint64_t* coeff_limbs,
+                double* slots);
+
+/* ---- homomorphic operations (Sec. 2.4) ------------------------------------- */
+/* Rot_l^steps (left by steps slots; negative = right) with hybrid key switching. */
+int blb_rotate(blb_ctx* ctx, const blb_keys* keys, const blb_ct* in, int32_t steps, blb_ct** out);
+/* Divide by the last prime with rounding; drops one level, scale /= q_l. */
+int blb_rescale(blb_ctx* ctx, blb_ct* inout);
+int blb_add(blb_ctx* ctx, const blb_ct* a, const blb_ct* b, blb_ct** out);
+int blb_mul_plain(blb_ctx* ctx, const blb_ct* a, const blb_pt* b, blb_ct** out);
+/* ct x ct: tensor product (3 polynomials) followed by relinearization when
+ * relin != 0 (needs the relinearization key). */
+int blb_mul(blb_ctx* ctx, const blb_keys* keys, const blb_ct* a, const blb_ct* b, int relin,
+            blb_ct** out);
+int blb_relinearize(blb_ctx* ctx, const blb_keys* keys, const blb_ct* in, blb_ct** out);
+/* Key switching of one polynomial d (coefficient form, host or device, (level+1)
+ * x N words) with the Galois key of rotation `rot`: writes (k0, k1) in
+ * coefficient form, 2 x (level+1) x N words, to out (host or device).
+ * Exposed for parity testing of the key-switch pipeline. */
+int blb_keyswitch_coeffs(blb_ctx* ctx, const blb_keys* keys, int32_t rot, const uint64_t* d,
+                         uint32_t level, uint64_t* out);
+
+/* ---- matmul_cp: encrypted X (m x d) times plaintext W (d x d_out) ------------
+ * Spatial-first packing (Sec. 4.2.1): with k = N/2/m, input ciphertext c holds
+ * X[i][c k + b] at slot i + m b (nX = ceil(d/k) ciphertexts); output e holds
+ * Y[i][e k + b] likewise (nY = ceil(d_out/k)).  Diagonal method with
+ * baby-step giant-step (App. C.1): nX(b1-1) + nY(G-1) rotations,
+ * nX nY k plaintext products, one rescale per output.  The output is at
+ * level-1 with the input's scale (plaintexts are encoded with scale q_level).
+ * Needs Galois keys for left rotations b m (0 < b < b1) and g b1 m (0 < g < G).
+ *
+ * blb_cp_plan_create encodes all plaintext diagonals of W (host or device,
+ * row-major d x d_out doubles) once, for inputs at `level`; plans are reused
+ * across calls (model weights).  blb_matmul_cp_plan runs the product for nX
+ * input ciphertexts and writes nY new handles into Y.  blb_matmul_cp is the
+ * one-shot form (plan, run, free). */
+int blb_cp_plan_create(blb_ctx* ctx, uint32_t m, uint32_t d, const double* W, uint32_t d_out,
+                       uint32_t level, const blb_sched* sched, blb_cp_plan** out);
+void blb_cp_plan_free(blb_cp_plan* plan);
+int blb_cp_plan_info(const blb_cp_plan* plan, uint32_t* nX, uint32_t* nY, uint32_t* b1,
+                     uint32_t* G, uint64_t* plaintext_bytes);
+int blb_matmul_cp_plan(blb_ctx* ctx, const blb_keys* keys, const blb_cp_plan* plan,
+                       blb_ct* const* X, uint32_t nX, blb_ct** Y);
+int blb_matmul_cp(blb_ctx* ctx, const blb_keys* keys, blb_ct* const* X, uint32_t nX, uint32_t m,
+                  uint32_t d, const double* W, uint32_t d_out, const blb_sched* sched, blb_ct** Y);
+
+/* ---- CKKS -> MPC (Alg. 1 steps 1-2, Sec. 6.3) --------------------------------
+ * P1 reduces the ciphertext to level 0, adds a mask r drawn uniformly from
+ * Z_{q_0}[X]/(X^N+1) (Philox stream `nonce`, key = the keygen seed) and keeps
+ * -r mod q_0 as its share: p1_share (host or device) receives N words in
+ * coefficient form.  masked_for_p0 receives a new level-0 ciphertext; P0's share
+ * is its decryption (blb_decrypt, coeff_limbs).  The two shares sum to the
+ * message plus noise mod q_0. */
+int blb_he2mpc(blb_ctx* ctx, const blb_keys* keys, const blb_ct* ct, uint64_t nonce,
+               blb_ct** masked_for_p0, uint64_t* p1_share);
+
+/* ---- low-level transforms (parity testing) ------------------------------------
+ * Forward / inverse negacyclic NTT of `rows` limbs of N words in place (host or
+ * device).  Limb r uses prime q_{prime_idx[r]} (host array).  Forward output
+ * order: A[k] = a(psi^(2 bitrev(k) + 1)) with psi the context's root for that
+ * prime (first x = 2, 3, ... whose power x^((q-1)/2N) has order 2N). */
+int blb_ntt(blb_ctx* ctx, uint64_t* data, uint32_t rows, const uint32_t* prime_idx, int inverse);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,365 @@
+"""ctypes binding of libblb.so (include/blb.h).
+
+Argument marshalling only: every step of the path runs in the library's CUDA
+kernels.  Device memory comes from PyTorch's caching allocator, installed with
+blb_set_allocator; streams are PyTorch streams.  There is no CPU fallback: if
+the library is missing or no GPU is present, the calls raise.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libblb.so")
+
+OK, ERR_ARG, ERR_LEVEL, ERR_SCALE, ERR_NO_KEY, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_PARAM = 0, -1, -2, -3, -4, -5, -6, -7, -8
+
+_vp = ctypes.c_void_p
+_u32 = ctypes.c_uint32
+_u64 = ctypes.c_uint64
+_i32 = ctypes.c_int32
+_dbl = ctypes.c_double
+_pp = ctypes.POINTER(ctypes.c_void_p)
+
+
+class BlbError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"blb error {code}: {msg}")
+        self.code = code
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [("logN", _u32), ("nQ", _u32), ("nP", _u32), ("q_bits", ctypes.POINTER(_u32)),
+                ("p_bits", ctypes.POINTER(_u32)), ("dnum", _u32), ("scale", _dbl)]
+
+
+class _Sched(ctypes.Structure):
+    _fields_ = [("b1", _u32)]
+
+
+ALLOC_FN = ctypes.CFUNCTYPE(_vp, ctypes.c_size_t, _vp, _vp)
+FREE_FN = ctypes.CFUNCTYPE(None, _vp, ctypes.c_size_t, _vp, _vp)
+
+# every function of include/blb.h with its ctypes signature
+SIGNATURES = {
+    "blb_set_allocator": (ctypes.c_int, [ALLOC_FN, FREE_FN, _vp]),
+    "blb_last_error": (ctypes.c_char_p, []),
+    "blb_version": (ctypes.c_char_p, []),
+    "blb_params_primes": (ctypes.c_int, [ctypes.POINTER(_Params), _vp]),
+    "blb_ctx_create": (ctypes.c_int, [ctypes.POINTER(_Params), _vp, _pp]),
+    "blb_ctx_free": (None, [_vp]),
+    "blb_ctx_info": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
+    "blb_ctx_primes": (ctypes.c_int, [_vp, _vp]),
+    "blb_ctx_sync": (ctypes.c_int, [_vp]),
+    "blb_ctx_bytes_in_use": (_u64, [_vp]),
+    "blb_keygen": (ctypes.c_int, [_vp, _u64, _vp, _u32, ctypes.c_int, _pp]),
+    "blb_keys_free": (None, [_vp]),
+    "blb_keys_export": (ctypes.c_int, [_vp, _vp, ctypes.c_int, _i32, _vp]),
+    "blb_encode": (ctypes.c_int, [_vp, _vp, _u64, _u32, _dbl, _pp]),
+    "blb_pt_free": (None, [_vp]),
+    "blb_pt_export": (ctypes.c_int, [_vp, _vp, _vp]),
+    "blb_encrypt": (ctypes.c_int, [_vp, _vp, _vp, _u64, _pp]),
+    "blb_ct_free": (None, [_vp]),
+    "blb_ct_info": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "blb_ct_export": (ctypes.c_int, [_vp, _vp, _vp]),
+    "blb_ct_import": (ctypes.c_int, [_vp, _vp, _u32, _u32, _dbl, _pp]),
+    "blb_decrypt": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
+    "blb_rotate": (ctypes.c_int, [_vp, _vp, _vp, _i32, _pp]),
+    "blb_rescale": (ctypes.c_int, [_vp, _vp]),
+    "blb_add": (ctypes.c_int, [_vp, _vp, _vp, _pp]),
+    "blb_mul_plain": (ctypes.c_int, [_vp, _vp, _vp, _pp]),
+    "blb_mul": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.c_int, _pp]),
+    "blb_relinearize": (ctypes.c_int, [_vp, _vp, _vp, _pp]),
+    "blb_keyswitch_coeffs": (ctypes.c_int, [_vp, _vp, _i32, _vp, _u32, _vp]),
+    "blb_cp_plan_create": (ctypes.c_int, [_vp, _u32, _u32, _vp, _u32, _u32, ctypes.POINTER(_Sched), _pp]),
+    "blb_cp_plan_free": (None, [_vp]),
+    "blb_cp_plan_info": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
+    "blb_matmul_cp_plan": (ctypes.c_int, [_vp, _vp, _vp, _pp, _u32, _pp]),
+    "blb_matmul_cp": (ctypes.c_int, [_vp, _vp, _pp, _u32, _u32, _u32, _vp, _u32, ctypes.POINTER(_Sched), _pp]),
+    "blb_he2mpc": (ctypes.c_int, [_vp, _vp, _vp, _u64, _pp, _vp]),
+    "blb_ntt": (ctypes.c_int, [_vp, _vp, _u32, _vp, ctypes.c_int]),
+}
+
+_lib = None
+_alloc_refs = None
+
+
+def lib():
+    """Load libblb.so (raises if it was not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} missing: run paper_2508_19525_b300/build.py (no CPU fallback exists)")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(rc):
+    if rc != OK:
+        raise BlbError(rc, lib().blb_last_error().decode())
+
+
+def last_error():
+    return lib().blb_last_error().decode()
+
+
+def use_torch_allocator():
+    """Route the library's device allocations through PyTorch's caching allocator."""
+    global _alloc_refs
+    import torch
+
+    def _alloc(nbytes, stream, user):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), stream=int(stream or 0))
+        except Exception:
+            return None
+
+    def _free(ptr, nbytes, stream, user):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    a, f = ALLOC_FN(_alloc), FREE_FN(_free)
+    _check(lib().blb_set_allocator(a, f, None))
+    _alloc_refs = (a, f)
+
+
+def _ptr(a):
+    """Data pointer of a numpy array or torch tensor (host or device)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        assert a.flags["C_CONTIGUOUS"]
+        return a.ctypes.data
+    assert a.is_contiguous()
+    return a.data_ptr()
+
+
+def _params(logN, q_bits, p_bits, dnum, scale):
+    qb = (_u32 * len(q_bits))(*q_bits)
+    pb = (_u32 * len(p_bits))(*p_bits)
+    p = _Params(logN, len(q_bits), len(p_bits), qb, pb, dnum, scale)
+    return p, (qb, pb)
+
+
+def params_primes(logN, q_bits, p_bits, dnum):
+    """Host-only prime selection of the library (no GPU needed)."""
+    p, keep = _params(logN, q_bits, p_bits, dnum, 2.0 ** 40)
+    out = np.zeros(len(q_bits) + len(p_bits), np.uint64)
+    _check(lib().blb_params_primes(ctypes.byref(p), out.ctypes.data))
+    return [int(x) for x in out]
+
+
+class _Handle:
+    _free = None
+
+    def __init__(self, ctx, h):
+        self.ctx, self.h = ctx, h
+
+    def free(self):
+        if self.h:
+            getattr(lib(), self._free)(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class Keys(_Handle):
+    _free = "blb_keys_free"
+
+
+class Plaintext(_Handle):
+    _free = "blb_pt_free"
+
+
+class Ciphertext(_Handle):
+    _free = "blb_ct_free"
+
+    def info(self):
+        lv, npl, sc = _u32(), _u32(), _dbl()
+        _check(lib().blb_ct_info(self.h, ctypes.byref(lv), ctypes.byref(npl), ctypes.byref(sc)))
+        return lv.value, npl.value, sc.value
+
+    @property
+    def level(self):
+        return self.info()[0]
+
+    @property
+    def scale(self):
+        return self.info()[2]
+
+
+class CpPlan(_Handle):
+    _free = "blb_cp_plan_free"
+
+    def info(self):
+        v = [_u32() for _ in range(4)] + [_u64()]
+        _check(lib().blb_cp_plan_info(self.h, *[ctypes.byref(x) for x in v]))
+        return dict(nX=v[0].value, nY=v[1].value, b1=v[2].value, G=v[3].value, plaintext_bytes=v[4].value)
+
+
+class Context:
+    """blb_ctx: one parameter set on one CUDA stream (a torch stream; default:
+    torch's current stream)."""
+
+    def __init__(self, logN, q_bits, p_bits, dnum, scale=2.0 ** 40, stream=None, torch_allocator=True):
+        import torch
+        if torch_allocator:
+            use_torch_allocator()
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        p, keep = _params(logN, q_bits, p_bits, dnum, scale)
+        h = ctypes.c_void_p()
+        _check(lib().blb_ctx_create(ctypes.byref(p), ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h)))
+        self.h = h.value
+        self.logN, self.N, self.nQ, self.nP, self.dnum = logN, 1 << logN, len(q_bits), len(p_bits), dnum
+        self.scale = scale
+        out = np.zeros(self.nQ + self.nP, np.uint64)
+        _check(lib().blb_ctx_primes(self.h, out.ctypes.data))
+        self.primes = [int(x) for x in out]
+
+    def free(self):
+        if getattr(self, "h", None):
+            lib().blb_ctx_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    def _new(self, cls, fn, *args):
+        h = ctypes.c_void_p()
+        _check(fn(self.h, *args, ctypes.byref(h)))
+        return cls(self, h.value)
+
+    def sync(self):
+        _check(lib().blb_ctx_sync(self.h))
+
+    def bytes_in_use(self):
+        return int(lib().blb_ctx_bytes_in_use(self.h))
+
+    # keys
+    def keygen(self, seed, rot_steps=(), relin=False):
+        r = (_i32 * max(1, len(rot_steps)))(*rot_steps)
+        return self._new(Keys, lib().blb_keygen, _u64(seed), r, len(rot_steps), int(relin))
+
+    def keys_export(self, keys, which, rot=0):
+        if which == 0:
+            out = np.zeros(self.N, np.int64)
+        else:
+            out = np.zeros((self.dnum, 2, self.nQ + self.nP, self.N), np.uint64)
+        _check(lib().blb_keys_export(self.h, keys.h, which, rot, out.ctypes.data))
+        return out
+
+    # encoding
+    def encode(self, vals, level, scale=None):
+        scale = self.scale if scale is None else scale
+        if isinstance(vals, np.ndarray):
+            vals = np.ascontiguousarray(vals, np.float64)
+        n = int(vals.numel() if hasattr(vals, "numel") else vals.size)
+        return self._new(Plaintext, lib().blb_encode, _ptr(vals), _u64(n), level, _dbl(scale))
+
+    def pt_export(self, pt, level):
+        out = np.zeros((level + 1, self.N), np.uint64)
+        _check(lib().blb_pt_export(self.h, pt.h, out.ctypes.data))
+        return out
+
+    # ciphertexts
+    def encrypt(self, keys, pt, nonce):
+        return self._new(Ciphertext, lib().blb_encrypt, keys.h, pt.h, _u64(nonce))
+
+    def ct_export(self, ct, out=None):
+        lv, npl, _ = ct.info()
+        if out is None:
+            out = np.zeros((npl, lv + 1, self.N), np.uint64)
+        _check(lib().blb_ct_export(self.h, ct.h, _ptr(out)))
+        return out
+
+    def ct_import(self, coeffs, scale):
+        coeffs = np.ascontiguousarray(coeffs, np.uint64) if isinstance(coeffs, np.ndarray) else coeffs
+        npl, n = coeffs.shape[0], coeffs.shape[1]
+        return self._new(Ciphertext, lib().blb_ct_import, _ptr(coeffs), n - 1, npl, _dbl(scale))
+
+    def decrypt(self, keys, ct, coeffs=True, slots=True, coeff_out=None, slot_out=None):
+        lv = ct.level
+        if coeffs and coeff_out is None:
+            coeff_out = np.zeros((lv + 1, self.N), np.uint64)
+        if slots and slot_out is None:
+            slot_out = np.zeros(self.N // 2, np.float64)
+        _check(lib().blb_decrypt(self.h, keys.h, ct.h, _ptr(coeff_out) if coeffs else None,
+                                 _ptr(slot_out) if slots else None))
+        return coeff_out, slot_out
+
+    # operations
+    def rotate(self, keys, ct, steps):
+        return self._new(Ciphertext, lib().blb_rotate, keys.h, ct.h, _i32(steps))
+
+    def rescale(self, ct):
+        _check(lib().blb_rescale(self.h, ct.h))
+        return ct
+
+    def add(self, a, b):
+        return self._new(Ciphertext, lib().blb_add, a.h, b.h)
+
+    def mul_plain(self, a, pt):
+        return self._new(Ciphertext, lib().blb_mul_plain, a.h, pt.h)
+
+    def mul(self, keys, a, b, relin=True):
+        return self._new(Ciphertext, lib().blb_mul, keys.h if keys else None, a.h, b.h, int(relin))
+
+    def relinearize(self, keys, ct):
+        return self._new(Ciphertext, lib().blb_relinearize, keys.h, ct.h)
+
+    def keyswitch_coeffs(self, keys, rot, d):
+        d = np.ascontiguousarray(d, np.uint64)
+        n = d.shape[0]
+        out = np.zeros((2, n, self.N), np.uint64)
+        _check(lib().blb_keyswitch_coeffs(self.h, keys.h, _i32(rot), d.ctypes.data, n - 1, out.ctypes.data))
+        return out
+
+    # matmul_cp
+    def cp_plan(self, m, d, W, d_out, level, b1=0):
+        if isinstance(W, np.ndarray):
+            W = np.ascontiguousarray(W, np.float64)
+        s = _Sched(b1)
+        return self._new(CpPlan, lib().blb_cp_plan_create, m, d, _ptr(W), d_out, level, ctypes.byref(s))
+
+    def matmul_cp_plan(self, keys, plan, X):
+        info = plan.info()
+        xs = (ctypes.c_void_p * len(X))(*[x.h for x in X])
+        ys = (ctypes.c_void_p * info["nY"])()
+        _check(lib().blb_matmul_cp_plan(self.h, keys.h, plan.h, xs, len(X), ys))
+        return [Ciphertext(self, y) for y in ys]
+
+    def matmul_cp(self, keys, X, m, d, W, d_out, b1=0):
+        W = np.ascontiguousarray(W, np.float64) if isinstance(W, np.ndarray) else W
+        k = (self.N // 2) // m
+        nY = (d_out + k - 1) // k
+        xs = (ctypes.c_void_p * len(X))(*[x.h for x in X])
+        ys = (ctypes.c_void_p * nY)()
+        s = _Sched(b1)
+        _check(lib().blb_matmul_cp(self.h, keys.h, xs, len(X), m, d, _ptr(W), d_out, ctypes.byref(s), ys))
+        return [Ciphertext(self, y) for y in ys]
+
+    # CKKS -> MPC
+    def he2mpc(self, keys, ct, nonce, share_out=None):
+        if share_out is None:
+            share_out = np.zeros(self.N, np.uint64)
+        h = ctypes.c_void_p()
+        _check(lib().blb_he2mpc(self.h, keys.h, ct.h, _u64(nonce), ctypes.byref(h), _ptr(share_out)))
+        return Ciphertext(self, h.value), share_out
+
+    def ntt(self, data, prime_idx, inverse=False):
+        data = np.ascontiguousarray(data, np.uint64).copy()
+        pi = np.ascontiguousarray(prime_idx, np.uint32)
+        _check(lib().blb_ntt(self.h, data.ctypes.data, data.shape[0], pi.ctypes.data, int(inverse)))
+        return data

@@ -1,0 +1,271 @@
+// common.cuh -- shared definitions of the B300 RNS-CKKS library (device
+// arithmetic, context / object layouts, launcher declarations).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/blb.h"
+
+#define BLB_MAXP 32
+
+// ---------------------------------------------------------------------------
+// error plumbing: every entry point returns a code; the message is kept per
+// thread.
+// ---------------------------------------------------------------------------
+void blb_set_error(const std::string& msg);
+int blb_fail(int code, const std::string& msg);
+#define BLB_CUDA(call)                                                                        \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess)                                                                \
+            return blb_fail(BLB_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+#define BLB_TRY(expr)                  \
+    do {                               \
+        int rc_ = (expr);              \
+        if (rc_ != BLB_OK) return rc_; \
+    } while (0)
+// launch check: catches configuration errors without synchronizing
+#define BLB_LAUNCHED() BLB_CUDA(cudaGetLastError())
+
+// ---------------------------------------------------------------------------
+// device modular arithmetic (all primes < 2^62)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t add_mod(uint64_t a, uint64_t b, uint64_t q)
+{
+    uint64_t s = a + b;
+    return s >= q ? s - q : s;
+}
+__device__ __forceinline__ uint64_t sub_mod(uint64_t a, uint64_t b, uint64_t q)
+{
+    return a >= b ? a - b : a + q - b;
+}
+__device__ __forceinline__ uint64_t neg_mod(uint64_t a, uint64_t q) { return a ? q - a : 0; }
+
+// x * w mod q for a constant w with companion wp = floor(w 2^64 / q) (Shoup).
+// Valid for any 64-bit x; result in [0, q).
+__device__ __forceinline__ uint64_t mul_shoup(uint64_t x, uint64_t w, uint64_t wp, uint64_t q)
+{
+    uint64_t qt = __umul64hi(x, wp);
+    uint64_t r = x * w - qt * q;
+    return r >= q ? r - q : r;
+}
+
+// Barrett reduction of a 128-bit x = x1 2^64 + x0 with R = floor(2^128 / q)
+// = r1 2^64 + r0: qhat = floor(x R / 2^128) computed exactly, which is at least
+// floor(x / q) - 1, so one conditional subtraction lands in [0, q).
+__device__ __forceinline__ uint64_t barrett128(uint64_t x0, uint64_t x1, uint64_t q, uint64_t r0,
+                                               uint64_t r1)
+{
+    uint64_t c0 = __umul64hi(x0, r0);
+    uint64_t a_lo = x1 * r0, a_hi = __umul64hi(x1, r0);
+    uint64_t b_lo = x0 * r1, b_hi = __umul64hi(x0, r1);
+    uint64_t s = a_lo + b_lo;
+    uint64_t k1 = s < a_lo;
+    uint64_t s2 = s + c0;
+    uint64_t k2 = s2 < s;
+    uint64_t qhat = x1 * r1 + a_hi + b_hi + k1 + k2;
+    uint64_t r = x0 - qhat * q;
+    return r >= q ? r - q : r;
+}
+
+__device__ __forceinline__ uint64_t mul_mod(uint64_t a, uint64_t b, uint64_t q, uint64_t r0, uint64_t r1)
+{
+    return barrett128(a * b, __umul64hi(a, b), q, r0, r1);
+}
+
+// 128-bit accumulator for lazy sums of products
+struct acc128 {
+    uint64_t lo, hi;
+};
+__device__ __forceinline__ void mad128(acc128& acc, uint64_t a, uint64_t b)
+{
+    uint64_t p_lo = a * b, p_hi = __umul64hi(a, b);
+    uint64_t lo = acc.lo + p_lo;
+    acc.hi += p_hi + (lo < p_lo);
+    acc.lo = lo;
+}
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon et al., SC'11); key = (seed lo, seed hi)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k)
+{
+#pragma unroll
+    for (int r = 0; r < 10; r++) {
+        uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+        k.x += 0x9E3779B9u;
+        k.y += 0xBB67AE85u;
+    }
+    return c;
+}
+
+enum { PURPOSE_SECRET = 1, PURPOSE_KEY_A = 2, PURPOSE_KEY_E = 3, PURPOSE_ENC_A = 4, PURPOSE_ENC_E = 5,
+       PURPOSE_MASK = 6 };
+
+// ---------------------------------------------------------------------------
+// limb -> prime maps passed by value to kernels: row r of a polynomial stack uses
+// prime p[r % n].
+// ---------------------------------------------------------------------------
+struct LimbMap {
+    uint8_t p[BLB_MAXP];
+    uint32_t n;
+};
+
+// Base-conversion constants for one (source set -> target set) conversion:
+//   out_t = sum_i [x_i * hat_inv_i]_{s_i} * hat[i][t] mod t
+struct ConvTable {
+    uint32_t ns, nt;
+    uint8_t src[BLB_MAXP];             // prime indices of the sources
+    uint8_t dst[BLB_MAXP];             // prime indices of the targets
+    uint8_t dst_row[BLB_MAXP];         // output row of each target
+    uint64_t hat_inv[BLB_MAXP];        // (S/s_i)^-1 mod s_i
+    uint64_t hat_inv_sh[BLB_MAXP];     // Shoup companions
+    uint64_t hat[BLB_MAXP][BLB_MAXP];  // [i][t] = S/s_i mod t
+};
+
+// ---------------------------------------------------------------------------
+// objects
+// ---------------------------------------------------------------------------
+struct blb_ctx {
+    uint32_t logN, N, nQ, nP, dnum, alpha, np;
+    double scale;
+    cudaStream_t stream;
+    std::vector<uint64_t> q, psi;     // np primes, roots
+    // device tables
+    uint64_t* d_q = nullptr;          // [np]
+    uint64_t* d_bar = nullptr;        // [np][2]: floor(2^128/q) lo, hi
+    uint64_t* d_tw = nullptr;         // [np][4][N]: psi_rev, shoup, psi_inv_rev, shoup
+    uint64_t* d_ninv = nullptr;       // [np][2]: N^-1, shoup
+    double2* d_zeta = nullptr;        // [N]: (cos, sin)(pi k / N)
+    uint64_t* d_cdt = nullptr;        // [19]
+    uint32_t* d_kperm = nullptr;      // [N/2]: k_j = (5^j mod 2N - 1)/4
+    int* d_flag = nullptr;            // device status word (encoding overflow)
+    // host-side constants
+    std::vector<uint64_t> P_mod_q;              // [nQ]  P mod q_i
+    std::vector<uint64_t> P_inv_mod_q;          // [nQ]  P^-1 mod q_i
+    std::vector<std::vector<uint64_t>> ql_inv;  // [l][i] q_l^-1 mod q_i
+    // conversion tables: ModUp per (level, digit), ModDown P -> Q
+    std::vector<ConvTable> h_modup;             // index level * dnum + j
+    std::vector<ConvTable*> d_modup;
+    ConvTable h_moddown;
+    ConvTable* d_moddown = nullptr;
+    // scratch arena (stream-ordered reuse)
+    uint64_t* scratch = nullptr;
+    size_t scratch_words = 0;
+    size_t bytes_in_use = 0;
+
+    LimbMap qmap(uint32_t nlimbs, uint32_t first = 0) const;  // limbs -> q_first..
+    LimbMap extmap(uint32_t level) const;                     // q_0..q_l, p_0..p_{nP-1}
+    LimbMap pmap() const;                                     // p_0..p_{nP-1}
+    // scratch regions (words): key switching uses [0, ks_words), operations
+    // above it
+    size_t ks_words() const;
+    uint64_t* op_scratch() const { return scratch + ks_words(); }
+};
+
+struct blb_ct {
+    blb_ctx* ctx;
+    uint32_t level, npolys;
+    double scale;
+    uint64_t* d;   // npolys x (level+1) x N, NTT domain
+    size_t bytes;
+};
+
+struct blb_pt {
+    blb_ctx* ctx;
+    uint32_t level;
+    double scale;
+    uint64_t* d;   // (level+1) x N, NTT domain
+    size_t bytes;
+};
+
+struct KeyEntry {
+    uint64_t galois;   // Galois element (0 = relinearization)
+    uint64_t* d;       // dnum x 2 x np x N, NTT domain (b then a)
+};
+
+struct blb_keys {
+    blb_ctx* ctx;
+    uint64_t seed;
+    uint64_t* d_s;     // np x N, NTT domain
+    int64_t* d_s_coef; // N signed coefficients
+    std::vector<KeyEntry> keys;
+    size_t bytes;
+    const KeyEntry* find(uint64_t g) const
+    {
+        for (auto& k : keys)
+            if (k.galois == g) return &k;
+        return nullptr;
+    }
+};
+
+struct blb_cp_plan {
+    blb_ctx* ctx;
+    uint32_t m, d, d_out, level, k, nX, nY, b1, G;
+    uint64_t* d_pts;   // [nY][G][nX][b1] plaintexts, each (level+1) x N, NTT domain
+    size_t bytes;
+};
+
+// ---------------------------------------------------------------------------
+// memory / host helpers
+// ---------------------------------------------------------------------------
+void* dev_alloc(blb_ctx* ctx, size_t bytes);
+void dev_free(blb_ctx* ctx, void* p, size_t bytes);
+bool is_device_ptr(const void* p);
+
+uint64_t host_mulmod(uint64_t a, uint64_t b, uint64_t q);
+uint64_t host_powmod(uint64_t b, uint64_t e, uint64_t q);
+uint64_t host_invmod(uint64_t a, uint64_t q);
+uint64_t shoup_companion(uint64_t w, uint64_t q);
+uint64_t galois_element(uint32_t N, int32_t rot);
+
+// ---------------------------------------------------------------------------
+// launchers (all on ctx->stream)
+// ---------------------------------------------------------------------------
+// NTT of `rows` rows of N words; row r uses prime map.p[r % map.n]
+int ntt_forward(blb_ctx* ctx, uint64_t* data, uint32_t rows, const LimbMap& map);
+int ntt_inverse(blb_ctx* ctx, uint64_t* data, uint32_t rows, const LimbMap& map);
+
+// element-wise (row r uses prime map.p[r % map.n]; operand b repeats every
+// b_rows rows)
+int launch_mul_rows(blb_ctx* ctx, uint64_t* out, const uint64_t* a, const uint64_t* b, uint32_t rows,
+                    const LimbMap& map, uint32_t b_rows);
+int launch_mac_rows(blb_ctx* ctx, uint64_t* acc, const uint64_t* a, const uint64_t* b, uint32_t rows,
+                    const LimbMap& map, uint32_t b_rows);
+int launch_add_rows(blb_ctx* ctx, uint64_t* out, const uint64_t* a, const uint64_t* b, uint32_t rows,
+                    const LimbMap& map);
+int launch_sub_rows(blb_ctx* ctx, uint64_t* out, const uint64_t* a, const uint64_t* b, uint32_t rows,
+                    const LimbMap& map);
+int launch_neg_rows(blb_ctx* ctx, uint64_t* out, const uint64_t* a, uint32_t rows, const LimbMap& map);
+int launch_mul_const_rows(blb_ctx* ctx, uint64_t* out, const uint64_t* a, uint32_t rows, const LimbMap& map,
+                          const uint64_t* consts_per_row_host);
+int launch_automorph_ntt(blb_ctx* ctx, uint64_t* out, const uint64_t* in, uint32_t rows, uint64_t g);
+int launch_signed_to_rows(blb_ctx* ctx, uint64_t* out, const int64_t* in, uint32_t rows, const LimbMap& map);
+int launch_rescale(blb_ctx* ctx, uint64_t* out, const uint64_t* in, uint32_t level, uint32_t npolys);
+int launch_tensor(blb_ctx* ctx, uint64_t* out, const uint64_t* a, const uint64_t* b, uint32_t level);
+
+// sampling: counter (coefficient, j, obj, purpose), key = seed
+int launch_sample_ternary(blb_ctx* ctx, int64_t* out, uint64_t seed, uint32_t obj, uint32_t purpose, uint32_t j);
+int launch_sample_gauss(blb_ctx* ctx, int64_t* out, uint64_t seed, uint32_t obj, uint32_t purpose, uint32_t j);
+// rows of uniform residues: row r mod prime map.p[r % map.n], sub-index j_of_row[r]
+int launch_sample_uniform(blb_ctx* ctx, uint64_t* out, uint32_t rows, const LimbMap& map, uint64_t seed,
+                          uint32_t obj, uint32_t purpose, const uint32_t* j_of_row);
+
+// key switching of d (NTT domain, level+1 rows) with key (dnum x 2 x np x N)
+int keyswitch(blb_ctx* ctx, const uint64_t* d_ntt, uint32_t level, const uint64_t* key, uint64_t* out0,
+              uint64_t* out1);
+
+// encoding (Eq. 2)
+int encode_slots(blb_ctx* ctx, const double* d_z, uint32_t npts, uint32_t n, uint32_t level, double scale,
+                 uint64_t* d_out /* npts x (level+1) x N, NTT domain */);
+int decode_limb0(blb_ctx* ctx, const uint64_t* d_coef0, double scale, double* d_slots);
+// matmul_cp plaintext diagonals for pts [first, first+count) of a plan (slot vectors)
+int cp_build_diagonals(blb_ctx* ctx, const blb_cp_plan* plan, const double* d_W, uint32_t first, uint32_t count,
+                       double* d_z);
+int launch_cp_mac(blb_ctx* ctx, const blb_cp_plan* plan, const uint64_t* baby, uint64_t* T);

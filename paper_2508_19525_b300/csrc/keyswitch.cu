@@ -1,0 +1,134 @@
+// keyswitch.cu -- hybrid key switching (decompose into dnum digits, ModUp by
+// fast base conversion, inner product with the key, ModDown by P).
+//
+// The paper's rotations and ct-ct products (Sec. 2.4) need key switching but do
+// not restate it; this is the standard hybrid method.  For a polynomial d at
+// level l (n = l+1 primes) and a key {(b_j, a_j)} from s' to s:
+//   digits D_j = {j alpha, ..., min((j+1) alpha, n) - 1}, j < beta = ceil(n/alpha)
+//   d~_j = Conv_{D_j -> Q_l u P}([d]_{D_j})   (the digit's own primes keep d)
+//   acc  = sum_j d~_j (b_j, a_j)              (over Q_l u P)
+//   out_i = (acc_i - Conv_{P -> q_i}([acc]_P)) * P^-1 mod q_i
+// Conv(x)_t = sum_i [x_i (S/s_i)^-1]_{s_i} (S/s_i mod t) mod t, without
+// overflow correction.  Every step is an exact integer function of d's
+// coefficients, so any correct schedule of it yields the same limbs.
+#include "common.cuh"
+
+namespace {
+constexpr int kT = 256;
+
+// Base conversion of `npolys` polynomials: sources are tab.ns consecutive rows
+// at src (poly stride src_ps words), targets 0..nt-1 of the table written to
+// dst rows tab.dst_row[k] (poly stride dst_ps words).  Coefficient form.
+__global__ void k_conv(const uint64_t* __restrict__ src, size_t src_ps, const ConvTable* __restrict__ tab,
+                       uint32_t nt, uint64_t* __restrict__ dst, size_t dst_ps, const uint64_t* __restrict__ qs,
+                       const uint64_t* __restrict__ bar, uint32_t N)
+{
+    const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x, poly = blockIdx.y;
+    if (c >= N) return;
+    const uint32_t ns = tab->ns;
+    uint64_t y[BLB_MAXP];
+    for (uint32_t i = 0; i < ns; i++) {
+        uint64_t si = qs[tab->src[i]];
+        y[i] = mul_shoup(src[poly * src_ps + (size_t)i * N + c], tab->hat_inv[i], tab->hat_inv_sh[i], si);
+    }
+    for (uint32_t k = 0; k < nt; k++) {
+        const uint32_t pt = tab->dst[k];
+        acc128 a{0, 0};
+        for (uint32_t i = 0; i < ns; i++) mad128(a, y[i], tab->hat[i][k]);
+        dst[poly * dst_ps + (size_t)tab->dst_row[k] * N + c] = barrett128(a.lo, a.hi, qs[pt], bar[2 * pt], bar[2 * pt + 1]);
+    }
+}
+
+// acc_p[t] = sum_{j < beta} ext[j][t] * key[j][p][kt],  p in {0, 1}
+__global__ void k_ks_inner(uint64_t* __restrict__ acc, const uint64_t* __restrict__ ext,
+                           const uint64_t* __restrict__ key, LimbMap emap, uint32_t n, uint32_t E, uint32_t beta,
+                           uint32_t nQ, uint32_t np, const uint64_t* __restrict__ qs,
+                           const uint64_t* __restrict__ bar, uint32_t N)
+{
+    const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x, t = blockIdx.y;
+    if (c >= N) return;
+    const uint32_t pi = emap.p[t];
+    const uint32_t kt = t < n ? t : nQ + (t - n);
+    acc128 a0{0, 0}, a1{0, 0};
+    for (uint32_t j = 0; j < beta; j++) {
+        uint64_t x = ext[((size_t)j * E + t) * N + c];
+        mad128(a0, x, key[(((size_t)j * 2 + 0) * np + kt) * N + c]);
+        mad128(a1, x, key[(((size_t)j * 2 + 1) * np + kt) * N + c]);
+    }
+    const uint64_t q = qs[pi], r0 = bar[2 * pi], r1 = bar[2 * pi + 1];
+    acc[(size_t)t * N + c] = barrett128(a0.lo, a0.hi, q, r0, r1);
+    acc[((size_t)E + t) * N + c] = barrett128(a1.lo, a1.hi, q, r0, r1);
+}
+
+struct PInv {
+    uint64_t w[BLB_MAXP], wp[BLB_MAXP];
+};
+// out_p[i] = (acc_p[i] - cv_p[i]) * P^-1 mod q_i
+__global__ void k_moddown_finish(uint64_t* __restrict__ out0, uint64_t* __restrict__ out1,
+                                 const uint64_t* __restrict__ acc, const uint64_t* __restrict__ cv, uint32_t n,
+                                 uint32_t E, PInv pinv, const uint64_t* __restrict__ qs, uint32_t N)
+{
+    const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x, row = blockIdx.y;  // row = p * n + i
+    if (c >= N) return;
+    const uint32_t p = row / n, i = row % n;
+    const uint64_t q = qs[i];
+    uint64_t x = acc[((size_t)p * E + i) * N + c];
+    uint64_t v = cv[(size_t)row * N + c];
+    uint64_t r = mul_shoup(sub_mod(x, v, q), pinv.w[i], pinv.wp[i], q);
+    (p ? out1 : out0)[(size_t)i * N + c] = r;
+}
+
+}  // namespace
+
+int keyswitch(blb_ctx* ctx, const uint64_t* d_ntt, uint32_t level, const uint64_t* key, uint64_t* out0,
+              uint64_t* out1)
+{
+    const uint32_t N = ctx->N, n = level + 1, nP = ctx->nP, E = n + nP;
+    const uint32_t alpha = ctx->alpha, beta = (n + alpha - 1) / alpha;
+    uint64_t* coef = ctx->scratch;
+    uint64_t* ext = coef + (size_t)n * N;
+    uint64_t* acc = ext + (size_t)beta * E * N;
+    uint64_t* cv = acc + (size_t)2 * E * N;
+    const LimbMap emap = ctx->extmap(level);
+    const dim3 g1((N + kT - 1) / kT, 1);
+
+    // 1. coefficient form of d
+    BLB_CUDA(cudaMemcpyAsync(coef, d_ntt, (size_t)n * N * 8, cudaMemcpyDeviceToDevice, ctx->stream));
+    BLB_TRY(ntt_inverse(ctx, coef, n, ctx->qmap(n)));
+    // 2. ModUp of every digit, then back to the evaluation domain
+    for (uint32_t j = 0; j < beta; j++) {
+        const uint32_t lo = j * alpha, hi = std::min((j + 1) * alpha, n);
+        const ConvTable& h = ctx->h_modup[(size_t)level * ctx->dnum + j];
+        uint64_t* ej = ext + (size_t)j * E * N;
+        k_conv<<<g1, kT, 0, ctx->stream>>>(coef + (size_t)lo * N, 0, ctx->d_modup[(size_t)level * ctx->dnum + j], h.nt,
+                                           ej, 0, ctx->d_q, ctx->d_bar, N);
+        BLB_LAUNCHED();
+        if (lo > 0) BLB_TRY(ntt_forward(ctx, ej, lo, ctx->qmap(lo)));
+        LimbMap tail{};
+        for (uint32_t r = hi; r < E; r++) tail.p[r - hi] = emap.p[r];
+        tail.n = E - hi;
+        BLB_TRY(ntt_forward(ctx, ej + (size_t)hi * N, E - hi, tail));
+        BLB_CUDA(cudaMemcpyAsync(ej + (size_t)lo * N, d_ntt + (size_t)lo * N, (size_t)(hi - lo) * N * 8,
+                                 cudaMemcpyDeviceToDevice, ctx->stream));
+    }
+    // 3. inner product with the key
+    k_ks_inner<<<dim3((N + kT - 1) / kT, E), kT, 0, ctx->stream>>>(acc, ext, key, emap, n, E, beta, ctx->nQ, ctx->np,
+                                                                   ctx->d_q, ctx->d_bar, N);
+    BLB_LAUNCHED();
+    // 4. ModDown: P limbs to coefficient form, convert to Q_l, back to evaluation
+    BLB_TRY(ntt_inverse(ctx, acc + (size_t)n * N, nP, ctx->pmap()));
+    BLB_TRY(ntt_inverse(ctx, acc + ((size_t)E + n) * N, nP, ctx->pmap()));
+    k_conv<<<dim3((N + kT - 1) / kT, 2), kT, 0, ctx->stream>>>(acc + (size_t)n * N, (size_t)E * N, ctx->d_moddown, n,
+                                                               cv, (size_t)n * N, ctx->d_q, ctx->d_bar, N);
+    BLB_LAUNCHED();
+    BLB_TRY(ntt_forward(ctx, cv, 2 * n, ctx->qmap(n)));
+    PInv pinv{};
+    for (uint32_t i = 0; i < n; i++) {
+        pinv.w[i] = ctx->P_inv_mod_q[i];
+        pinv.wp[i] = shoup_companion(pinv.w[i], ctx->q[i]);
+    }
+    k_moddown_finish<<<dim3((N + kT - 1) / kT, 2 * n), kT, 0, ctx->stream>>>(out0, out1, acc, cv, n, E, pinv,
+                                                                             ctx->d_q, N);
+    BLB_LAUNCHED();
+    return BLB_OK;
+}
