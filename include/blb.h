@@ -202,6 +202,16 @@ int blb_he2mpc(blb_ctx* ctx, const blb_keys* keys, const blb_ct* ct, uint64_t no
  * prime (first x = 2, 3, ... whose power x^((q-1)/2N) has order 2N). */
 int blb_ntt(blb_ctx* ctx, uint64_t* data, uint32_t rows, const uint32_t* prime_idx, int inverse);
 
+/* ---- measurement ------------------------------------------------------------
+ * Total kernel launches issued by this library in this process. */
+uint64_t blb_kernel_launches(void);
+/* When enabled, CUDA events on the context's stream bracket each launch site
+ * ("ntt", "intt", "keyswitch", "cp_mac"); blb_profile_read synchronizes the
+ * stream and returns the summed milliseconds and the number of bracketed
+ * calls of a site since profiling was enabled.  Enabling resets the sums. */
+int blb_profile_enable(blb_ctx* ctx, int on);
+int blb_profile_read(blb_ctx* ctx, const char* site, double* ms, uint64_t* count);
+
 #ifdef __cplusplus
 }
 #endif

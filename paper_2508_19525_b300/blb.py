@@ -79,6 +79,9 @@ SIGNATURES = {
     "blb_matmul_cp": (ctypes.c_int, [_vp, _vp, _pp, _u32, _u32, _u32, _vp, _u32, ctypes.POINTER(_Sched), _pp]),
     "blb_he2mpc": (ctypes.c_int, [_vp, _vp, _vp, _u64, _pp, _vp]),
     "blb_ntt": (ctypes.c_int, [_vp, _vp, _u32, _vp, ctypes.c_int]),
+    "blb_kernel_launches": (_u64, []),
+    "blb_profile_enable": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "blb_profile_read": (ctypes.c_int, [_vp, ctypes.c_char_p, _vp, _vp]),
 }
 
 _lib = None
@@ -103,6 +106,10 @@ def lib():
 def _check(rc):
     if rc != OK:
         raise BlbError(rc, lib().blb_last_error().decode())
+
+
+def kernel_launches():
+    return int(lib().blb_kernel_launches())
 
 
 def last_error():
@@ -357,6 +364,14 @@ class Context:
         h = ctypes.c_void_p()
         _check(lib().blb_he2mpc(self.h, keys.h, ct.h, _u64(nonce), ctypes.byref(h), _ptr(share_out)))
         return Ciphertext(self, h.value), share_out
+
+    def profile(self, on=True):
+        _check(lib().blb_profile_enable(self.h, int(on)))
+
+    def profile_read(self, site):
+        ms, cnt = _dbl(), _u64()
+        _check(lib().blb_profile_read(self.h, site.encode(), ctypes.byref(ms), ctypes.byref(cnt)))
+        return ms.value, cnt.value
 
     def ntt(self, data, prime_idx, inverse=False):
         data = np.ascontiguousarray(data, np.uint64).copy()

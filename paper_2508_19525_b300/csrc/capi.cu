@@ -122,6 +122,7 @@ __global__ void k_cp_mac(uint64_t* __restrict__ T, const uint64_t* __restrict__ 
 
 int launch_cp_mac(blb_ctx* c, const blb_cp_plan* plan, const uint64_t* baby, uint64_t* T)
 {
+    ProfScope prof(c, "cp_mac");
     const uint32_t n = plan->level + 1;
     dim3 grid((c->N + kT - 1) / kT, n, plan->nY * plan->G);
     k_cp_mac<<<grid, kT, 0, c->stream>>>(T, baby, plan->d_pts, n, c->N, plan->nX, plan->b1, c->d_q, c->d_bar);

@@ -28,8 +28,14 @@ int blb_fail(int code, const std::string& msg);
         int rc_ = (expr);              \
         if (rc_ != BLB_OK) return rc_; \
     } while (0)
-// launch check: catches configuration errors without synchronizing
-#define BLB_LAUNCHED() BLB_CUDA(cudaGetLastError())
+// launch check: catches configuration errors without synchronizing; counts
+// the library's kernel launches
+void blb_count_launch();
+#define BLB_LAUNCHED()            \
+    do {                          \
+        blb_count_launch();       \
+        BLB_CUDA(cudaGetLastError()); \
+    } while (0)
 
 // ---------------------------------------------------------------------------
 // device modular arithmetic (all primes < 2^62)
@@ -155,6 +161,15 @@ struct blb_ctx {
     std::vector<ConvTable*> d_modup;
     ConvTable h_moddown;
     ConvTable* d_moddown = nullptr;
+    // optional CUDA-event timing of named launch sites (bench / profiling)
+    bool profiling = false;
+    struct ProfSite {
+        std::string name;
+        std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
+        double ms = 0;
+        uint64_t count = 0;
+    };
+    std::vector<ProfSite> prof;
     // scratch arena (stream-ordered reuse)
     uint64_t* scratch = nullptr;
     size_t scratch_words = 0;
@@ -210,6 +225,15 @@ struct blb_cp_plan {
     uint32_t m, d, d_out, level, k, nX, nY, b1, G;
     uint64_t* d_pts;   // [nY][G][nX][b1] plaintexts, each (level+1) x N, NTT domain
     size_t bytes;
+};
+
+// RAII timer around a launch site (no-op unless the context is profiling)
+struct ProfScope {
+    blb_ctx* c;
+    int site;
+    cudaEvent_t b = nullptr, e = nullptr;
+    ProfScope(blb_ctx* ctx, const char* name);
+    ~ProfScope();
 };
 
 // ---------------------------------------------------------------------------

@@ -1,6 +1,7 @@
 // ctx.cu -- context creation: primes, NTT twiddles, base-conversion and encoding
 // tables, allocator hooks, error strings.  Host code only.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -21,6 +22,72 @@ int blb_fail(int code, const std::string& msg)
 }
 extern "C" const char* blb_last_error(void) { return g_err.c_str(); }
 extern "C" const char* blb_version(void) { return "blb-b300 0.1 (sm_103a)"; }
+
+// ---------------------------------------------------------------------------
+// launch counting and event timing of launch sites
+// ---------------------------------------------------------------------------
+static std::atomic<uint64_t> g_launches{0};
+void blb_count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+extern "C" uint64_t blb_kernel_launches(void) { return g_launches.load(); }
+
+ProfScope::ProfScope(blb_ctx* ctx, const char* name) : c(ctx), site(-1)
+{
+    if (!c->profiling) return;
+    for (size_t i = 0; i < c->prof.size(); i++)
+        if (c->prof[i].name == name) site = (int)i;
+    if (site < 0) {
+        c->prof.push_back(blb_ctx::ProfSite{name, {}, 0, 0});
+        site = (int)c->prof.size() - 1;
+    }
+    cudaEventCreate(&b);
+    cudaEventCreate(&e);
+    cudaEventRecord(b, c->stream);
+}
+ProfScope::~ProfScope()
+{
+    if (site < 0) return;
+    cudaEventRecord(e, c->stream);
+    c->prof[site].ev.push_back({b, e});
+}
+
+static void prof_collect(blb_ctx* c)
+{
+    cudaStreamSynchronize(c->stream);
+    for (auto& s : c->prof) {
+        for (auto& p : s.ev) {
+            float ms = 0;
+            cudaEventElapsedTime(&ms, p.first, p.second);
+            s.ms += ms;
+            s.count++;
+            cudaEventDestroy(p.first);
+            cudaEventDestroy(p.second);
+        }
+        s.ev.clear();
+    }
+}
+
+extern "C" int blb_profile_enable(blb_ctx* c, int on)
+{
+    if (!c) return blb_fail(BLB_ERR_ARG, "null context");
+    prof_collect(c);
+    c->prof.clear();
+    c->profiling = on != 0;
+    return BLB_OK;
+}
+
+extern "C" int blb_profile_read(blb_ctx* c, const char* site, double* ms, uint64_t* count)
+{
+    if (!c || !site) return blb_fail(BLB_ERR_ARG, "null argument");
+    prof_collect(c);
+    if (ms) *ms = 0;
+    if (count) *count = 0;
+    for (auto& s : c->prof)
+        if (s.name == site) {
+            if (ms) *ms = s.ms;
+            if (count) *count = s.count;
+        }
+    return BLB_OK;
+}
 
 // ---------------------------------------------------------------------------
 // allocator
@@ -430,6 +497,7 @@ extern "C" int blb_ctx_create(const blb_params* params, void* stream, blb_ctx** 
 extern "C" void blb_ctx_free(blb_ctx* c)
 {
     if (!c) return;
+    prof_collect(c);
     cudaStreamSynchronize(c->stream);
     dev_free(c, c->d_q, c->np * 8);
     dev_free(c, c->d_bar, c->np * 16);

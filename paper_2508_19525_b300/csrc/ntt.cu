@@ -191,6 +191,7 @@ __global__ void __launch_bounds__(kThreads) k_ntt_inv_cols(uint64_t* __restrict_
 int ntt_forward(blb_ctx* ctx, uint64_t* data, uint32_t rows, const LimbMap& map)
 {
     if (rows == 0) return BLB_OK;
+    ProfScope prof(ctx, "ntt");
     NttGeom g = geom(ctx->logN);
     if (g.N1 > 1) {
         dim3 grid(g.N2 / kCols, rows);
@@ -208,6 +209,7 @@ int ntt_forward(blb_ctx* ctx, uint64_t* data, uint32_t rows, const LimbMap& map)
 int ntt_inverse(blb_ctx* ctx, uint64_t* data, uint32_t rows, const LimbMap& map)
 {
     if (rows == 0) return BLB_OK;
+    ProfScope prof(ctx, "intt");
     NttGeom g = geom(ctx->logN);
     uint32_t bpc = g.N2 >= (uint32_t)kSmemWords ? 1 : kSmemWords / g.N2;
     if (bpc > g.N1) bpc = g.N1;
