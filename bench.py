@@ -1,0 +1,405 @@
+#!/usr/bin/env python
+"""Benchmark of the B300 RNS-CKKS linear path (BLB, arXiv 2508.19525).
+
+Workload (one GPU): the BERT-base fused linear block of the paper's ct-pt
+matrix products -- an encrypted activation X (128 x 768, U[-1,1]) times the
+fused QKV weight (768 x 2304), then the first 768 output columns times the
+output projection W_O (768 x 768); N = 2^15, 8 RNS primes (60 + 7 x 40 bits),
+3 special primes, dnum = 3, scale 2^40.  One step is the whole hot path for
+one sequence of 128 tokens:
+  client: encode + encrypt X (6 ciphertexts),
+  server: matmul_cp QKV (6 -> 18 ciphertexts), matmul_cp W_O (6 -> 6),
+          CKKS->MPC masking of the 18 outputs that leave the block,
+  client: decryption of the 18 masked ciphertexts (its additive shares).
+The plaintext diagonals of both weight matrices are encoded once, when the
+weights are loaded (36.6 GB resident in HBM), like any model weights.
+
+Output: one JSON line (rank 0).  `value` is tokens/s with X already in HBM;
+`e2e` is the same step through the C ABI from pinned host buffers (X copied
+in, both parties' shares copied out).  `--impl reference` times the CPU
+oracle on a bounded sample of the same step instead.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "CKKS fused-matmul tokens/s"
+UNIT = "tokens/s"
+WORKLOAD = ("bert-base fused linear ct-pt: X 128x768 @ W_QKV 768x2304 then @ W_O 768x768, "
+            "N=2^15, 8 primes (60+7x40 bits), 3 special primes, dnum=3, scale 2^40, "
+            "he2mpc + client decryption of 18 outputs")
+M, D, D_QKV, D_O, B1 = 128, 768, 2304, 768, 16
+LEVEL = 7
+TOKENS_PER_STEP = 128
+
+
+def config(world):
+    return {"workload": WORKLOAD, "global_batch": world, "seq_len": M,
+            "parallelism": "replicas" if world > 1 else "single",
+            "l2": "working set larger than L2 (36.6 GB of plaintext diagonals read per step)",
+            "bsgs_b1": B1}
+
+
+# --------------------------------------------------------------------------- clocks
+class Clocks:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        self.p.wait()
+        self.f.flush()
+        rows = [l.split(",") for l in open(self.f.name).read().strip().splitlines() if l.strip()]
+        os.unlink(self.f.name)
+        sm = [float(r[1]) for r in rows if len(r) >= 9 and r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if len(r) >= 9 and r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in rows:
+            if len(r) >= 9:
+                for n, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------- distributed
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def dist_init(world, backend):
+    if world > 1:
+        import torch.distributed as dist
+        if not dist.is_initialized():
+            dist.init_process_group(backend)
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    """Largest value of x over all ranks (elapsed seconds: the job is as slow as
+    its slowest replica)."""
+    if world == 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate(elapsed_s, units_per_rank, world):
+    """Whole-job throughput: units processed by all ranks / max elapsed."""
+    t = max_over_ranks(elapsed_s, world)
+    return units_per_rank * world / t, t
+
+
+# --------------------------------------------------------------------------- workload
+def pack_columns(X, m, k):
+    """Spatial-first packing (Sec. 4.2.1): ciphertext c holds X[i, c k + b] at slot i + m b."""
+    n_cts = -(-X.shape[1] // k)
+    Z = np.zeros((n_cts, m * k))
+    for c in range(n_cts):
+        blk = X[:, c * k:(c + 1) * k]
+        Z[c, :blk.shape[1] * m] = blk.T.reshape(-1)
+    return Z
+
+
+def unpack_columns(Z, m, k, d_out):
+    cols = [Z[e, b * m:(b + 1) * m] for e in range(Z.shape[0]) for b in range(k)]
+    return np.stack(cols[:d_out], axis=1)
+
+
+class Workload:
+    def __init__(self, device):
+        import torch
+        from paper_2508_19525_b300 import blb
+        from paper_2508_19525_b300 import workloads as wl
+        self.torch, self.blb = torch, blb
+        prm = wl.BERT_CP
+        self.stream = torch.cuda.Stream(device=device)
+        self.ctx = blb.Context(prm.logN, prm.q_bits, prm.p_bits, prm.dnum, prm.scale, stream=self.stream)
+        self.N = self.ctx.N
+        self.k = self.N // 2 // M
+        G = self.k // B1
+        rots = [b * M for b in range(1, B1)] + [g * B1 * M for g in range(1, G)]
+        self.keys = self.ctx.keygen(0, rots)
+        self.X, Wqkv, Wo = wl.bert_base_cp(seed=0)
+        self.ref_qkv = self.X @ Wqkv
+        self.ref_o = self.ref_qkv[:, :D_O] @ Wo
+        t = time.time()
+        self.plan_qkv = self.ctx.cp_plan(M, D, Wqkv, D_QKV, LEVEL, B1)
+        self.plan_o = self.ctx.cp_plan(M, D, Wo, D_O, LEVEL - 1, B1)
+        self.ctx.sync()
+        self.plan_s = time.time() - t
+        self.plan_bytes = self.plan_qkv.info()["plaintext_bytes"] + self.plan_o.info()["plaintext_bytes"]
+        Z = pack_columns(self.X, M, self.k)
+        self.n_in = Z.shape[0]
+        self.n_out = 18
+        self.Zdev = torch.tensor(Z, dtype=torch.float64, device=device)
+        self.Zhost = torch.tensor(Z, dtype=torch.float64).pin_memory()
+        self.p0_dev = torch.zeros((self.n_out, self.N), dtype=torch.uint64, device=device)
+        self.p1_dev = torch.zeros((self.n_out, self.N), dtype=torch.uint64, device=device)
+        self.p0_host = torch.zeros((self.n_out, self.N), dtype=torch.uint64).pin_memory()
+        self.p1_host = torch.zeros((self.n_out, self.N), dtype=torch.uint64).pin_memory()
+        self.nonce = 1000
+
+    def step(self, host=False, keep=False):
+        ctx, keys = self.ctx, self.keys
+        Z = self.Zhost if host else self.Zdev
+        p0 = self.p0_host if host else self.p0_dev
+        p1 = self.p1_host if host else self.p1_dev
+        cts = []
+        for c in range(self.n_in):
+            self.nonce += 1
+            cts.append(ctx.encrypt(keys, ctx.encode(Z[c], LEVEL), self.nonce))
+        Y = ctx.matmul_cp_plan(keys, self.plan_qkv, cts)
+        O = ctx.matmul_cp_plan(keys, self.plan_o, Y[:self.n_in])
+        outs = Y[self.n_in:] + O
+        for i, y in enumerate(outs):
+            self.nonce += 1
+            masked, _ = ctx.he2mpc(keys, y, self.nonce, share_out=p1[i])
+            ctx.decrypt(keys, masked, coeffs=True, slots=False, coeff_out=p0[i:i + 1])
+        return (Y, O) if keep else None
+
+    def accuracy(self):
+        Y, O = self.step(keep=True)
+        got_qkv = unpack_columns(np.stack([self.ctx.decrypt(self.keys, y, coeffs=False)[1] for y in Y]), M, self.k, D_QKV)
+        got_o = unpack_columns(np.stack([self.ctx.decrypt(self.keys, y, coeffs=False)[1] for y in O]), M, self.k, D_O)
+        err = np.concatenate([(got_qkv - self.ref_qkv).ravel(), (got_o - self.ref_o).ravel()])
+        return float(np.max(np.abs(err))), float(np.mean(err ** 2))
+
+    def counts(self):
+        qkv, o = self.plan_qkv.info(), self.plan_o.info()
+        rot = lambda i: i["nX"] * (i["b1"] - 1) + i["nY"] * (i["G"] - 1)
+        return {"rotations": rot(qkv) + rot(o),
+                "plaintext_products": qkv["nX"] * qkv["nY"] * self.k + o["nX"] * o["nY"] * self.k,
+                "rescales": qkv["nY"] + o["nY"], "he2mpc": self.n_out}
+
+
+def timed(w, steps, host, world):
+    torch = w.torch
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier(world)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ev0.record(w.stream)
+    for _ in range(steps):
+        w.step(host=host)
+    ev1.record(w.stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    barrier(world)
+    return ev0.elapsed_time(ev1) / 1e3, wall
+
+
+def run_blb(args):
+    world, rank, local = dist_env()
+    import torch
+    dist_init(world, "nccl")
+    torch.cuda.set_device(local)
+    from paper_2508_19525_b300 import blb
+    w = Workload(torch.device("cuda", local))
+    for _ in range(args.warmup):
+        w.step()
+    # device-resident timed region, with per-site CUDA events and clock samples
+    clocks = Clocks(local)
+    w.ctx.profile(True)
+    launches0 = blb.kernel_launches()
+    clocks.start()
+    dev_s, _ = timed(w, args.steps, False, world)
+    clk = clocks.stop()
+    launches = blb.kernel_launches() - launches0
+    sites = {s: w.ctx.profile_read(s) for s in ("cp_mac", "keyswitch", "ntt", "intt")}
+    w.ctx.profile(False)
+    value, dev_max = aggregate(dev_s, TOKENS_PER_STEP * args.steps, world)
+    # end to end from pinned host buffers
+    for _ in range(max(1, args.warmup // 2)):
+        w.step(host=True)
+    _, e2e_wall = timed(w, args.steps, True, world)
+    e2e_value, _ = aggregate(e2e_wall, TOKENS_PER_STEP * args.steps, world)
+    max_err, mse = w.accuracy()
+    if rank != 0:
+        return
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    hbm = peaks.get("hbm_gbs", 6400.0)
+    peak_note = "measured" if "hbm_gbs" in peaks else "fallback"
+    roof = {}
+    for s, (ms, cnt, nbytes) in sites.items():
+        if cnt and ms > 0:
+            gbs = nbytes / (ms / 1e3) / 1e9
+            roof[s] = {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm, "unit": "GB/s",
+                       "frac": round(gbs / hbm, 4), "ms_total": round(ms, 3), "launch_sites": cnt,
+                       "share_of_step": round(ms / (dev_s * 1e3), 4),
+                       "algorithmic_bytes_per_call": nbytes // cnt, "peak_kind": peak_note}
+    dominant = max(roof, key=lambda s: roof[s]["ms_total"]) if roof else None
+    traffic = None
+    tfile = os.path.join(ROOT, "profiles", "traffic.json")
+    if dominant and os.path.exists(tfile):
+        traffic = json.load(open(tfile)).get(dominant)
+    line = {
+        "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(dev_max * 1e3 / args.steps, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u64 (RNS residues; FP64 encode/decode)",
+        "data": "synthetic (seeded U[-1,1] BERT-base-shaped operands)", "config": config(world),
+        "clocks": clk,
+        "e2e": {"value": round(e2e_value, 3), "unit": UNIT,
+                "h2d_bytes_per_step": int(w.Zhost.numel() * 8),
+                "d2h_bytes_per_step": int(w.p0_host.numel() * 8 + w.p1_host.numel() * 8)},
+        "gpu_launches": int(launches),
+        "roofline": dict(roof[dominant], kernel=dominant, traffic=traffic) if dominant else None,
+        "roofline_sites": roof,
+        "accuracy": {"max_abs_err_vs_fp64": max_err, "mse": mse, "bound": 1e-4},
+        "counts_per_step": w.counts(),
+        "weights": {"plaintext_bytes": w.plan_bytes, "encode_s": round(w.plan_s, 2), "timed": False},
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.cpu_sample)
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------- CPU oracle
+def oracle_step_estimate(sample):
+    """Time the CPU oracle on a bounded sample of one step and extrapolate by
+    operation counts: returns (seconds per step, sample description)."""
+    import oracle
+    from paper_2508_19525_b300 import workloads as wl
+    prm = wl.BERT_CP
+    o = oracle.Oracle(prm.logN, prm.q_bits, prm.p_bits, prm.dnum)
+    sk = o.keygen_secret(0)
+    gk = {}
+    for r in (M, 2 * M):
+        gk[r] = o.keygen_galois(0, sk, o.galois_elt(r))
+    Z = pack_columns(wl.bert_base_cp(0)[0], M, (o.N // 2) // M)
+    t = {}
+    n_rot, n_pt = sample
+    for lv in (LEVEL, LEVEL - 1):
+        t0 = time.perf_counter()
+        ct = o.encrypt(sk, o.encode(Z[0], lv, prm.scale), 0, lv)
+        t[("enc", lv)] = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        for i in range(n_rot):
+            r = M if i % 2 == 0 else 2 * M
+            o.rotate(ct, r, gk[r])
+        t[("rot", lv)] = (time.perf_counter() - t0) / n_rot
+        t0 = time.perf_counter()
+        acc = np.zeros_like(ct)
+        for i in range(n_pt):
+            pt = o.encode(Z[i % len(Z)], lv, float(o.primes[lv]))
+            prod = o.mul_plain(ct, pt)
+            acc = prod  # accumulation is a limb-wise add, negligible next to the product
+        t[("pt", lv)] = (time.perf_counter() - t0) / n_pt
+        t0 = time.perf_counter()
+        o.rescale(acc)
+        t[("rs", lv)] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    m, sh = o.he2mpc(ct, 0, 1)
+    o.decrypt(sk, m)
+    t_mask = time.perf_counter() - t0
+    # BERT-base step: 6 encryptions; QKV at level 7: 90 + 126 rotations, 13824
+    # plaintext products, 18 rescales; W_O at level 6: 90 + 42 rotations, 4608
+    # products, 6 rescales; 18 maskings + decryptions
+    est = (6 * t[("enc", LEVEL)] + 216 * t[("rot", LEVEL)] + 13824 * t[("pt", LEVEL)] + 18 * t[("rs", LEVEL)]
+           + 132 * t[("rot", LEVEL - 1)] + 4608 * t[("pt", LEVEL - 1)] + 6 * t[("rs", LEVEL - 1)] + 18 * t_mask)
+    desc = (f"{n_rot} rotations + {n_pt} plaintext encode-and-multiply + 1 rescale + 1 encryption at each of "
+            f"levels {LEVEL} and {LEVEL - 1}, 1 he2mpc + decryption (N=2^15); extrapolated to the step's "
+            f"348 rotations, 18432 plaintext products, 24 rescales, 6 encryptions, 18 maskings")
+    return est, desc
+
+
+def oracle_threads():
+    n = os.environ.get("OMP_NUM_THREADS")
+    return int(n) if n and n.isdigit() else (os.cpu_count() or 1)
+
+
+def cpu_baseline(sample):
+    est, desc = oracle_step_estimate(sample)
+    return {"value": round(TOKENS_PER_STEP / est, 6), "unit": UNIT, "cores": oracle_threads(), "kind": "oracle",
+            "sample": desc, "est_s_per_step": round(est, 1)}
+
+
+def run_reference(args):
+    world, rank, local = dist_env()
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        oracle_step_estimate((1, 2))
+    ests = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        e, desc = oracle_step_estimate(args.cpu_sample)
+        ests.append(e)
+    wall = time.perf_counter() - t0
+    est = sum(ests) / len(ests)
+    value = TOKENS_PER_STEP / est
+    line = {"metric": METRIC, "value": round(value, 6), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(est * 1e3, 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64 (RNS residues; FP64 encode/decode)",
+            "data": "synthetic (seeded U[-1,1] BERT-base-shaped operands)", "config": config(1),
+            "impl": "reference",
+            "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": oracle_threads(), "kind": "oracle",
+                             "sample": desc},
+            "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "sample_wall_s": round(wall, 1)}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["blb", "reference"], default="blb")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-rotations", type=int, default=6)
+    ap.add_argument("--cpu-products", type=int, default=48)
+    args = ap.parse_args()
+    args.cpu_sample = (args.cpu_rotations, args.cpu_products)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_blb(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -207,10 +207,13 @@ int blb_ntt(blb_ctx* ctx, uint64_t* data, uint32_t rows, const uint32_t* prime_i
 uint64_t blb_kernel_launches(void);
 /* When enabled, CUDA events on the context's stream bracket each launch site
  * ("ntt", "intt", "keyswitch", "cp_mac"); blb_profile_read synchronizes the
- * stream and returns the summed milliseconds and the number of bracketed
- * calls of a site since profiling was enabled.  Enabling resets the sums. */
+ * stream and returns, since profiling was enabled, the summed milliseconds, the
+ * number of bracketed calls and their algorithmic bytes (the minimum HBM
+ * traffic of the operation: NTT one read and one write per word; key switch
+ * its input, the used key digits and its output; cp_mac every plaintext, every
+ * baby-step ciphertext and every partial sum once).  Enabling resets the sums. */
 int blb_profile_enable(blb_ctx* ctx, int on);
-int blb_profile_read(blb_ctx* ctx, const char* site, double* ms, uint64_t* count);
+int blb_profile_read(blb_ctx* ctx, const char* site, double* ms, uint64_t* count, uint64_t* bytes);
 
 #ifdef __cplusplus
 }

@@ -81,7 +81,7 @@ SIGNATURES = {
     "blb_ntt": (ctypes.c_int, [_vp, _vp, _u32, _vp, ctypes.c_int]),
     "blb_kernel_launches": (_u64, []),
     "blb_profile_enable": (ctypes.c_int, [_vp, ctypes.c_int]),
-    "blb_profile_read": (ctypes.c_int, [_vp, ctypes.c_char_p, _vp, _vp]),
+    "blb_profile_read": (ctypes.c_int, [_vp, ctypes.c_char_p, _vp, _vp, _vp]),
 }
 
 _lib = None
@@ -369,9 +369,9 @@ class Context:
         _check(lib().blb_profile_enable(self.h, int(on)))
 
     def profile_read(self, site):
-        ms, cnt = _dbl(), _u64()
-        _check(lib().blb_profile_read(self.h, site.encode(), ctypes.byref(ms), ctypes.byref(cnt)))
-        return ms.value, cnt.value
+        ms, cnt, nb = _dbl(), _u64(), _u64()
+        _check(lib().blb_profile_read(self.h, site.encode(), ctypes.byref(ms), ctypes.byref(cnt), ctypes.byref(nb)))
+        return ms.value, cnt.value, nb.value
 
     def ntt(self, data, prime_idx, inverse=False):
         data = np.ascontiguousarray(data, np.uint64).copy()

@@ -122,8 +122,11 @@ __global__ void k_cp_mac(uint64_t* __restrict__ T, const uint64_t* __restrict__ 
 
 int launch_cp_mac(blb_ctx* c, const blb_cp_plan* plan, const uint64_t* baby, uint64_t* T)
 {
-    ProfScope prof(c, "cp_mac");
     const uint32_t n = plan->level + 1;
+    // algorithmic bytes: every plaintext once, the baby-step ciphertexts once,
+    // the (e, g) partial sums written once
+    const uint64_t terms = (uint64_t)plan->nX * plan->b1, outs = (uint64_t)plan->nY * plan->G;
+    ProfScope prof(c, "cp_mac", (outs * terms * n + terms * 2 * n + outs * 2 * n) * c->N * 8);
     dim3 grid((c->N + kT - 1) / kT, n, plan->nY * plan->G);
     k_cp_mac<<<grid, kT, 0, c->stream>>>(T, baby, plan->d_pts, n, c->N, plan->nX, plan->b1, c->d_q, c->d_bar);
     BLB_LAUNCHED();
@@ -229,7 +232,6 @@ extern "C" void blb_keys_free(blb_keys* K)
 {
     if (!K) return;
     blb_ctx* c = K->ctx;
-    cudaStreamSynchronize(c->stream);
     const size_t poly_bytes = (size_t)c->np * c->N * 8;
     dev_free(c, K->d_s, poly_bytes);
     dev_free(c, K->d_s_coef, (size_t)c->N * 8);
@@ -287,7 +289,6 @@ extern "C" int blb_encode(blb_ctx* c, const double* vals, uint64_t n, uint32_t l
 extern "C" void blb_pt_free(blb_pt* pt)
 {
     if (!pt) return;
-    cudaStreamSynchronize(pt->ctx->stream);
     dev_free(pt->ctx, pt->d, pt->bytes);
     delete pt;
 }
@@ -341,7 +342,6 @@ extern "C" int blb_encrypt(blb_ctx* c, const blb_keys* K, const blb_pt* pt, uint
 extern "C" void blb_ct_free(blb_ct* ct)
 {
     if (!ct) return;
-    cudaStreamSynchronize(ct->ctx->stream);
     dev_free(ct->ctx, ct->d, ct->bytes);
     delete ct;
 }
@@ -435,7 +435,6 @@ extern "C" int blb_rescale(blb_ctx* c, blb_ct* ct)
         dev_free(c, o, bytes);
         return rc;
     }
-    cudaStreamSynchronize(c->stream);
     dev_free(c, ct->d, ct->bytes);
     ct->d = o;
     ct->bytes = bytes;
@@ -617,7 +616,6 @@ extern "C" int blb_cp_plan_create(blb_ctx* c, uint32_t m, uint32_t d, const doub
 extern "C" void blb_cp_plan_free(blb_cp_plan* P)
 {
     if (!P) return;
-    cudaStreamSynchronize(P->ctx->stream);
     dev_free(P->ctx, P->d_pts, P->bytes);
     delete P;
 }
@@ -668,7 +666,6 @@ extern "C" int blb_matmul_cp_plan(blb_ctx* c, const blb_keys* K, const blb_cp_pl
         if (!rc) rc = launch_rescale(c, y->d, acc, P->level, 2);
         Y[e] = y;
     }
-    cudaStreamSynchronize(c->stream);
     dev_free(c, baby, baby_bytes);
     dev_free(c, T, T_bytes);
     if (rc) {

@@ -168,8 +168,10 @@ struct blb_ctx {
         std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
         double ms = 0;
         uint64_t count = 0;
+        uint64_t bytes = 0;  // algorithmic bytes of the bracketed calls
     };
     std::vector<ProfSite> prof;
+    std::vector<cudaEvent_t> event_pool;
     // scratch arena (stream-ordered reuse)
     uint64_t* scratch = nullptr;
     size_t scratch_words = 0;
@@ -232,7 +234,7 @@ struct ProfScope {
     blb_ctx* c;
     int site;
     cudaEvent_t b = nullptr, e = nullptr;
-    ProfScope(blb_ctx* ctx, const char* name);
+    ProfScope(blb_ctx* ctx, const char* name, uint64_t algorithmic_bytes);
     ~ProfScope();
 };
 

@@ -30,17 +30,30 @@ static std::atomic<uint64_t> g_launches{0};
 void blb_count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 extern "C" uint64_t blb_kernel_launches(void) { return g_launches.load(); }
 
-ProfScope::ProfScope(blb_ctx* ctx, const char* name) : c(ctx), site(-1)
+static cudaEvent_t pool_event(blb_ctx* c)
+{
+    if (!c->event_pool.empty()) {
+        cudaEvent_t e = c->event_pool.back();
+        c->event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+ProfScope::ProfScope(blb_ctx* ctx, const char* name, uint64_t algorithmic_bytes) : c(ctx), site(-1)
 {
     if (!c->profiling) return;
     for (size_t i = 0; i < c->prof.size(); i++)
         if (c->prof[i].name == name) site = (int)i;
     if (site < 0) {
-        c->prof.push_back(blb_ctx::ProfSite{name, {}, 0, 0});
+        c->prof.push_back(blb_ctx::ProfSite{name, {}, 0, 0, 0});
         site = (int)c->prof.size() - 1;
     }
-    cudaEventCreate(&b);
-    cudaEventCreate(&e);
+    c->prof[site].bytes += algorithmic_bytes;
+    b = pool_event(c);
+    e = pool_event(c);
     cudaEventRecord(b, c->stream);
 }
 ProfScope::~ProfScope()
@@ -59,8 +72,8 @@ static void prof_collect(blb_ctx* c)
             cudaEventElapsedTime(&ms, p.first, p.second);
             s.ms += ms;
             s.count++;
-            cudaEventDestroy(p.first);
-            cudaEventDestroy(p.second);
+            c->event_pool.push_back(p.first);
+            c->event_pool.push_back(p.second);
         }
         s.ev.clear();
     }
@@ -75,16 +88,18 @@ extern "C" int blb_profile_enable(blb_ctx* c, int on)
     return BLB_OK;
 }
 
-extern "C" int blb_profile_read(blb_ctx* c, const char* site, double* ms, uint64_t* count)
+extern "C" int blb_profile_read(blb_ctx* c, const char* site, double* ms, uint64_t* count, uint64_t* bytes)
 {
     if (!c || !site) return blb_fail(BLB_ERR_ARG, "null argument");
     prof_collect(c);
     if (ms) *ms = 0;
     if (count) *count = 0;
+    if (bytes) *bytes = 0;
     for (auto& s : c->prof)
         if (s.name == site) {
             if (ms) *ms = s.ms;
             if (count) *count = s.count;
+            if (bytes) *bytes = s.bytes;
         }
     return BLB_OK;
 }
@@ -498,6 +513,7 @@ extern "C" void blb_ctx_free(blb_ctx* c)
 {
     if (!c) return;
     prof_collect(c);
+    for (auto e : c->event_pool) cudaEventDestroy(e);
     cudaStreamSynchronize(c->stream);
     dev_free(c, c->d_q, c->np * 8);
     dev_free(c, c->d_bar, c->np * 16);

@@ -214,7 +214,6 @@ int encode_slots(blb_ctx* ctx, const double* d_z, uint32_t npts, uint32_t n, uin
         if (flag) rc = blb_fail(BLB_ERR_ARG, "encoded coefficient exceeds 2^63: value * scale too large");
     } while (0);
     if (own) {
-        cudaStreamSynchronize(ctx->stream);
         dev_free(ctx, A, words * 8);
     }
     return rc;

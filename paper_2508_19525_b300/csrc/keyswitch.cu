@@ -83,9 +83,10 @@ __global__ void k_moddown_finish(uint64_t* __restrict__ out0, uint64_t* __restri
 int keyswitch(blb_ctx* ctx, const uint64_t* d_ntt, uint32_t level, const uint64_t* key, uint64_t* out0,
               uint64_t* out1)
 {
-    ProfScope prof(ctx, "keyswitch");
     const uint32_t N = ctx->N, n = level + 1, nP = ctx->nP, E = n + nP;
     const uint32_t alpha = ctx->alpha, beta = (n + alpha - 1) / alpha;
+    // algorithmic bytes: read d and the used key digits, write (k0, k1)
+    ProfScope prof(ctx, "keyswitch", ((uint64_t)n + 2ull * beta * E + 2ull * n) * N * 8);
     uint64_t* coef = ctx->scratch;
     uint64_t* ext = coef + (size_t)n * N;
     uint64_t* acc = ext + (size_t)beta * E * N;

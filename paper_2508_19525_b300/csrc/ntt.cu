@@ -191,7 +191,7 @@ __global__ void __launch_bounds__(kThreads) k_ntt_inv_cols(uint64_t* __restrict_
 int ntt_forward(blb_ctx* ctx, uint64_t* data, uint32_t rows, const LimbMap& map)
 {
     if (rows == 0) return BLB_OK;
-    ProfScope prof(ctx, "ntt");
+    ProfScope prof(ctx, "ntt", (uint64_t)rows * ctx->N * 16);  // one read + one write per word
     NttGeom g = geom(ctx->logN);
     if (g.N1 > 1) {
         dim3 grid(g.N2 / kCols, rows);
@@ -209,7 +209,7 @@ int ntt_forward(blb_ctx* ctx, uint64_t* data, uint32_t rows, const LimbMap& map)
 int ntt_inverse(blb_ctx* ctx, uint64_t* data, uint32_t rows, const LimbMap& map)
 {
     if (rows == 0) return BLB_OK;
-    ProfScope prof(ctx, "intt");
+    ProfScope prof(ctx, "intt", (uint64_t)rows * ctx->N * 16);
     NttGeom g = geom(ctx->logN);
     uint32_t bpc = g.N2 >= (uint32_t)kSmemWords ? 1 : kSmemWords / g.N2;
     if (bpc > g.N1) bpc = g.N1;
