@@ -28,10 +28,15 @@ def _stale():
     return max(os.path.getmtime(f) for f in deps) > os.path.getmtime(LIB)
 
 
-def build(force=False, verbose=False, extra=()):
+def build(force=False, verbose=False, extra=(), asan=False):
+    """Compile every csrc/*.cu for sm_103a and link libblb.so.  asan=True adds
+    AddressSanitizer to the host code (debug builds; run python with the
+    sanitizer runtime preloaded and ASAN_OPTIONS=protect_shadow_gap=0)."""
     if not force and not _stale():
         return LIB
     nvcc = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
+    san = ["-Xcompiler", "-fsanitize=address", "-Xcompiler", "-fno-omit-frame-pointer", "-g"] if asan else []
+    extra = list(extra) + san
     objdir = os.path.join(HERE, "_build")
     os.makedirs(objdir, exist_ok=True)
     objs = []
@@ -52,7 +57,7 @@ def build(force=False, verbose=False, extra=()):
             print(out.decode(errors="replace"), file=sys.stderr)
     if failed:
         raise RuntimeError("nvcc failed:\n" + "\n".join(failed))
-    cmd = [nvcc, *ARCH, "-shared", "-o", LIB + ".tmp", *objs, "-lcudart"]
+    cmd = [nvcc, *ARCH, "-shared", "-o", LIB + ".tmp", *objs, "-lcudart"] + (["-Xcompiler", "-fsanitize=address"] if asan else [])
     subprocess.run(cmd, check=True)
     os.replace(LIB + ".tmp", LIB)
     return LIB
@@ -60,4 +65,4 @@ def build(force=False, verbose=False, extra=()):
 
 if __name__ == "__main__":
     print(build(force="--force" in sys.argv, verbose="-v" in sys.argv,
-                extra=["-Xptxas", "-v"] if "--ptxas" in sys.argv else []))
+                extra=["-Xptxas", "-v"] if "--ptxas" in sys.argv else [], asan="--asan" in sys.argv))

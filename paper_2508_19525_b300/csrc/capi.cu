@@ -46,6 +46,7 @@ int new_ct(blb_ctx* c, uint32_t level, uint32_t npolys, double scale, blb_ct** o
         delete ct;
         return blb_fail(BLB_ERR_OOM, "ciphertext allocation failed");
     }
+    ctx_retain(c);
     *out = ct;
     return BLB_OK;
 }
@@ -144,6 +145,7 @@ extern "C" int blb_keygen(blb_ctx* c, uint64_t seed, const int32_t* rot_steps, u
     const uint32_t N = c->N, np = c->np;
     blb_keys* K = new blb_keys();
     K->ctx = c;
+    ctx_retain(c);
     K->seed = seed;
     K->bytes = 0;
     const size_t poly_bytes = (size_t)np * N * 8;
@@ -237,6 +239,7 @@ extern "C" void blb_keys_free(blb_keys* K)
     dev_free(c, K->d_s_coef, (size_t)c->N * 8);
     for (auto& k : K->keys) dev_free(c, k.d, (size_t)c->dnum * 2 * poly_bytes);
     delete K;
+    ctx_release(c);
 }
 
 extern "C" int blb_keys_export(blb_ctx* c, const blb_keys* K, int which, int32_t rot, void* host_out)
@@ -270,6 +273,7 @@ extern "C" int blb_encode(blb_ctx* c, const double* vals, uint64_t n, uint32_t l
     if (!(scale > 0)) return blb_fail(BLB_ERR_ARG, "scale must be positive");
     blb_pt* pt = new blb_pt();
     pt->ctx = c;
+    ctx_retain(c);
     pt->level = level;
     pt->scale = scale;
     pt->bytes = (size_t)(level + 1) * c->N * 8;
@@ -289,8 +293,10 @@ extern "C" int blb_encode(blb_ctx* c, const double* vals, uint64_t n, uint32_t l
 extern "C" void blb_pt_free(blb_pt* pt)
 {
     if (!pt) return;
-    dev_free(pt->ctx, pt->d, pt->bytes);
+    blb_ctx* c = pt->ctx;
+    dev_free(c, pt->d, pt->bytes);
     delete pt;
+    ctx_release(c);
 }
 
 extern "C" int blb_pt_export(blb_ctx* c, const blb_pt* pt, uint64_t* out)
@@ -342,8 +348,10 @@ extern "C" int blb_encrypt(blb_ctx* c, const blb_keys* K, const blb_pt* pt, uint
 extern "C" void blb_ct_free(blb_ct* ct)
 {
     if (!ct) return;
-    dev_free(ct->ctx, ct->d, ct->bytes);
+    blb_ctx* c = ct->ctx;
+    dev_free(c, ct->d, ct->bytes);
     delete ct;
+    ctx_release(c);
 }
 
 extern "C" int blb_ct_info(const blb_ct* ct, uint32_t* level, uint32_t* npolys, double* scale)
@@ -566,6 +574,7 @@ extern "C" int blb_cp_plan_create(blb_ctx* c, uint32_t m, uint32_t d, const doub
     if (b1 > k || k % b1) return blb_fail(BLB_ERR_ARG, "b1 must divide k = N/2/m");
     blb_cp_plan* P = new blb_cp_plan();
     P->ctx = c;
+    ctx_retain(c);
     P->m = m;
     P->d = d;
     P->d_out = d_out;
@@ -580,7 +589,7 @@ extern "C" int blb_cp_plan_create(blb_ctx* c, uint32_t m, uint32_t d, const doub
     P->bytes = npts * n * c->N * 8;
     P->d_pts = (uint64_t*)dev_alloc(c, P->bytes);
     if (!P->d_pts) {
-        delete P;
+        blb_cp_plan_free(P);
         return blb_fail(BLB_ERR_OOM, "plaintext diagonals do not fit");
     }
     const size_t wbytes = (size_t)d * d_out * 8;
@@ -616,8 +625,10 @@ extern "C" int blb_cp_plan_create(blb_ctx* c, uint32_t m, uint32_t d, const doub
 extern "C" void blb_cp_plan_free(blb_cp_plan* P)
 {
     if (!P) return;
-    dev_free(P->ctx, P->d_pts, P->bytes);
+    blb_ctx* c = P->ctx;
+    dev_free(c, P->d_pts, P->bytes);
     delete P;
+    ctx_release(c);
 }
 
 extern "C" int blb_cp_plan_info(const blb_cp_plan* P, uint32_t* nX, uint32_t* nY, uint32_t* b1, uint32_t* G,

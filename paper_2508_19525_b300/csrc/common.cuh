@@ -176,6 +176,10 @@ struct blb_ctx {
     uint64_t* scratch = nullptr;
     size_t scratch_words = 0;
     size_t bytes_in_use = 0;
+    // lifetime: objects (keys, plaintexts, ciphertexts, plans) hold the
+    // context; blb_ctx_free releases it once the last of them is freed
+    uint64_t live_objects = 0;
+    bool closing = false;
 
     LimbMap qmap(uint32_t nlimbs, uint32_t first = 0) const;  // limbs -> q_first..
     LimbMap extmap(uint32_t level) const;                     // q_0..q_l, p_0..p_{nP-1}
@@ -242,6 +246,8 @@ struct ProfScope {
 // memory / host helpers
 // ---------------------------------------------------------------------------
 void* dev_alloc(blb_ctx* ctx, size_t bytes);
+void ctx_retain(blb_ctx* ctx);
+void ctx_release(blb_ctx* ctx);
 void dev_free(blb_ctx* ctx, void* p, size_t bytes);
 bool is_device_ptr(const void* p);
 

@@ -44,7 +44,7 @@ static cudaEvent_t pool_event(blb_ctx* c)
 
 ProfScope::ProfScope(blb_ctx* ctx, const char* name, uint64_t algorithmic_bytes) : c(ctx), site(-1)
 {
-    if (!c->profiling) return;
+    if (!c || !c->profiling) return;
     for (size_t i = 0; i < c->prof.size(); i++)
         if (c->prof[i].name == name) site = (int)i;
     if (site < 0) {
@@ -509,9 +509,27 @@ extern "C" int blb_ctx_create(const blb_params* params, void* stream, blb_ctx** 
     return BLB_OK;
 }
 
+static void ctx_destroy(blb_ctx* c);
+
+void ctx_retain(blb_ctx* c) { c->live_objects++; }
+
+void ctx_release(blb_ctx* c)
+{
+    if (--c->live_objects == 0 && c->closing) ctx_destroy(c);
+}
+
+// A context freed while objects created from it are alive (the order in which
+// a garbage collector finalizes handles is arbitrary) is destroyed when the
+// last of those objects is freed.
 extern "C" void blb_ctx_free(blb_ctx* c)
 {
-    if (!c) return;
+    if (!c || c->closing) return;
+    c->closing = true;
+    if (c->live_objects == 0) ctx_destroy(c);
+}
+
+static void ctx_destroy(blb_ctx* c)
+{
     prof_collect(c);
     for (auto e : c->event_pool) cudaEventDestroy(e);
     cudaStreamSynchronize(c->stream);
