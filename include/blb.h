@@ -161,6 +161,27 @@ int blb_relinearize(blb_ctx* ctx, const blb_keys* keys, const blb_ct* in, blb_ct
 int blb_keyswitch_coeffs(blb_ctx* ctx, const blb_keys* keys, int32_t rot, const uint64_t* d,
                          uint32_t level, uint64_t* out);
 
+/* Allocation-free form of blb_keyswitch_coeffs (same arguments, same result).
+ * The paper has no counterpart: this exists for callers that may not
+ * allocate device memory while they run, such as a serving process whose
+ * memory manager reserved the whole device budget up front, a latency-critical
+ * loop that cannot afford cudaMalloc's device-wide synchronization, or code
+ * running inside the allocator callbacks of blb_set_allocator.  All temporaries
+ * live in one fixed 32 MiB device array compiled into the library: every GPU
+ * that loads the library holds it until the process exits.  The call needs
+ * (3(l+1) + (l+1) + beta (l+1+nP) + 2 (l+1+nP) + 2 (l+1)) N words, beta =
+ * ceil((l+1)/alpha), and returns BLB_ERR_ARG when that exceeds 32 MiB (for
+ * example N = 2^16 with 12 primes); N = 2^15 with 8 primes and 3 special primes
+ * fits at every level.  The first call on a device looks up the array's device
+ * address with that device current, so make that first call before any stream
+ * capture.  All calls on a GPU share the array and it keeps the previous
+ * call's contents (nothing in it needs to start at zero): calls that can
+ * overlap on the GPU -- other streams, other contexts, other threads -- race
+ * and must be serialized by the caller.  d and out may be host or device
+ * memory; with host memory the call synchronizes the context's stream. */
+int blb_keyswitch_noalloc(blb_ctx* ctx, const blb_keys* keys, int32_t rot, const uint64_t* d,
+                          uint32_t level, uint64_t* out);
+
 /* ---- matmul_cp: encrypted X (m x d) times plaintext W (d x d_out) ------------
  * Spatial-first packing (Sec. 4.2.1): with k = N/2/m, input ciphertext c holds
  * X[i][c k + b] at slot i + m b (nX = ceil(d/k) ciphertexts); output e holds

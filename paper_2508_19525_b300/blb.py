@@ -72,6 +72,7 @@ SIGNATURES = {
     "blb_mul": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.c_int, _pp]),
     "blb_relinearize": (ctypes.c_int, [_vp, _vp, _vp, _pp]),
     "blb_keyswitch_coeffs": (ctypes.c_int, [_vp, _vp, _i32, _vp, _u32, _vp]),
+    "blb_keyswitch_noalloc": (ctypes.c_int, [_vp, _vp, _i32, _vp, _u32, _vp]),
     "blb_cp_plan_create": (ctypes.c_int, [_vp, _u32, _u32, _vp, _u32, _u32, ctypes.POINTER(_Sched), _pp]),
     "blb_cp_plan_free": (None, [_vp]),
     "blb_cp_plan_info": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
@@ -331,6 +332,13 @@ class Context:
         n = d.shape[0]
         out = np.zeros((2, n, self.N), np.uint64)
         _check(lib().blb_keyswitch_coeffs(self.h, keys.h, _i32(rot), d.ctypes.data, n - 1, out.ctypes.data))
+        return out
+
+    def keyswitch_noalloc(self, keys, rot, d, out):
+        """Allocation-free key switch (blb_keyswitch_noalloc): d is (level+1, N)
+        and out (2, level+1, N), host numpy arrays or device tensors."""
+        n = d.shape[0]
+        _check(lib().blb_keyswitch_noalloc(self.h, keys.h, _i32(rot), _ptr(d), n - 1, _ptr(out)))
         return out
 
     # matmul_cp

@@ -11,6 +11,9 @@
 // Conv(x)_t = sum_i [x_i (S/s_i)^-1]_{s_i} (S/s_i mod t) mod t, without
 // overflow correction.  Every step is an exact integer function of d's
 // coefficients, so any correct schedule of it yields the same limbs.
+#include <mutex>
+#include <string>
+
 #include "common.cuh"
 
 namespace {
@@ -80,14 +83,15 @@ __global__ void k_moddown_finish(uint64_t* __restrict__ out0, uint64_t* __restri
 
 }  // namespace
 
-int keyswitch(blb_ctx* ctx, const uint64_t* d_ntt, uint32_t level, const uint64_t* key, uint64_t* out0,
-              uint64_t* out1)
+// Key-switch body on an explicit scratch area of ks_scratch_words(level) words.
+static int keyswitch_impl(blb_ctx* ctx, const uint64_t* d_ntt, uint32_t level, const uint64_t* key, uint64_t* out0,
+                          uint64_t* out1, uint64_t* scratch, bool profile)
 {
     const uint32_t N = ctx->N, n = level + 1, nP = ctx->nP, E = n + nP;
     const uint32_t alpha = ctx->alpha, beta = (n + alpha - 1) / alpha;
     // algorithmic bytes: read d and the used key digits, write (k0, k1)
-    ProfScope prof(ctx, "keyswitch", ((uint64_t)n + 2ull * beta * E + 2ull * n) * N * 8);
-    uint64_t* coef = ctx->scratch;
+    ProfScope prof(profile ? ctx : nullptr, "keyswitch", ((uint64_t)n + 2ull * beta * E + 2ull * n) * N * 8);
+    uint64_t* coef = scratch;
     uint64_t* ext = coef + (size_t)n * N;
     uint64_t* acc = ext + (size_t)beta * E * N;
     uint64_t* cv = acc + (size_t)2 * E * N;
@@ -132,5 +136,77 @@ int keyswitch(blb_ctx* ctx, const uint64_t* d_ntt, uint32_t level, const uint64_
     k_moddown_finish<<<dim3((N + kT - 1) / kT, 2 * n), kT, 0, ctx->stream>>>(out0, out1, acc, cv, n, E, pinv,
                                                                              ctx->d_q, N);
     BLB_LAUNCHED();
+    return BLB_OK;
+}
+
+int keyswitch(blb_ctx* ctx, const uint64_t* d_ntt, uint32_t level, const uint64_t* key, uint64_t* out0,
+              uint64_t* out1)
+{
+    return keyswitch_impl(ctx, d_ntt, level, key, out0, out1, ctx->scratch, true);
+}
+
+// ===========================================================================
+// Allocation-free key switching
+// ===========================================================================
+// Some callers cannot allocate device memory while they run: a serving process
+// whose memory manager reserved the whole device budget at start-up and
+// rejects any other allocation, a latency-critical loop that must not pay
+// cudaMalloc's implicit device-wide synchronization, or code that runs inside
+// the allocator callbacks installed with blb_set_allocator.  For them
+// blb_keyswitch_noalloc keeps every temporary in the fixed array below.  The
+// array is a property of the loaded library: each GPU that loads it holds these
+// 32 MiB until the process exits, and all calls on one GPU share it.
+static constexpr size_t kNoAllocScratchWords = (size_t)4 << 20;  // 32 MiB of uint64 words
+static __device__ __align__(256) uint64_t blb_noalloc_scratch[kNoAllocScratchWords];
+
+static std::mutex g_noalloc_mu;
+static uint64_t* g_noalloc_ptr[64];  // device address of the array, per device ordinal
+
+// The array's host-side name is not a device address; the first call on a
+// device asks the runtime for the real one (with that device current) and
+// caches it.
+static int noalloc_scratch(uint64_t** out)
+{
+    int dev = -1;
+    BLB_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return blb_fail(BLB_ERR_ARG, "device ordinal beyond the scratch table (64)");
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, blb_noalloc_scratch);
+        if (e != cudaSuccess || !p)
+            return blb_fail(BLB_ERR_CUDA, std::string("cudaGetSymbolAddress of the key-switch scratch failed: ") +
+                                              cudaGetErrorString(e));
+        g_noalloc_ptr[dev] = (uint64_t*)p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return BLB_OK;
+}
+
+extern "C" int blb_keyswitch_noalloc(blb_ctx* c, const blb_keys* K, int32_t rot, const uint64_t* d, uint32_t level,
+                                     uint64_t* out)
+{
+    if (!c || !K || !d || !out) return blb_fail(BLB_ERR_ARG, "null argument");
+    if (level >= c->nQ) return blb_fail(BLB_ERR_LEVEL, "level out of range");
+    const KeyEntry* k = K->find(galois_element(c->N, rot));
+    if (!k) return blb_fail(BLB_ERR_NO_KEY, "no Galois key for that rotation");
+    const uint32_t N = c->N, n = level + 1, E = n + c->nP, beta = (n + c->alpha - 1) / c->alpha;
+    // input copy (n rows) + outputs (2n rows) + key-switch body (n + beta E + 2E + 2n rows)
+    const size_t need = ((size_t)3 * n + n + (size_t)beta * E + 2 * (size_t)E + 2 * (size_t)n) * N;
+    if (need > kNoAllocScratchWords)
+        return blb_fail(BLB_ERR_ARG, "blb_keyswitch_noalloc: this level and ring size need " +
+                                         std::to_string(need * 8 >> 20) + " MiB of scratch; the fixed area holds " +
+                                         std::to_string(kNoAllocScratchWords * 8 >> 20) + " MiB");
+    uint64_t* S = nullptr;
+    BLB_TRY(noalloc_scratch(&S));
+    uint64_t* dd = S;
+    uint64_t* o = S + (size_t)n * N;
+    uint64_t* body = S + (size_t)3 * n * N;
+    BLB_CUDA(cudaMemcpyAsync(dd, d, (size_t)n * N * 8, cudaMemcpyDefault, c->stream));
+    BLB_TRY(ntt_forward(c, dd, n, c->qmap(n)));
+    BLB_TRY(keyswitch_impl(c, dd, level, k->d, o, o + (size_t)n * N, body, false));
+    BLB_TRY(ntt_inverse(c, o, 2 * n, c->qmap(n)));
+    BLB_CUDA(cudaMemcpyAsync(out, o, (size_t)2 * n * N * 8, cudaMemcpyDefault, c->stream));
+    if (!is_device_ptr(out)) BLB_CUDA(cudaStreamSynchronize(c->stream));
     return BLB_OK;
 }
