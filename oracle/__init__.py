@@ -208,6 +208,13 @@ class Oracle:
         lib().orc_keyswitch(self._pp, _p(d, _u64p), n - 1, _p(np.ascontiguousarray(ksk), _u64p), _p(out, _u64p))
         return out
 
+    def moddown(self, acc, level):
+        """acc: (2, level+1+nP, N) over Q_l then P -> (2, level+1, N)."""
+        acc = np.ascontiguousarray(acc, np.uint64)
+        out = np.zeros((2, level + 1, self.N), np.uint64)
+        lib().orc_moddown(self._pp, _p(acc, _u64p), level, _p(out, _u64p))
+        return out
+
     def rotate(self, ct, r, gksk):
         ct = np.ascontiguousarray(ct, np.uint64)
         out = np.zeros_like(ct)

@@ -594,13 +594,66 @@ static void base_convert(uint32_t N, const uint64_t* const* x, const uint64_t* s
     }
 }
 
+/* ModDown: divide a polynomial pair given over Q_l u P (coefficient form,
+ * 2 x (n + nP) rows, Q rows first) by P with rounding:
+ *   out_i = (x_i - X mod q_i) * P^-1 mod q_i,
+ * where X is the representative of x mod P in (-P/2, P/2], obtained by the
+ * base conversion of Halevi, Polyakov and Shoup (2019): with
+ * y_k = [x_k (P/p_k)^-1]_{p_k}, sum_k y_k (P/p_k) = [x]_P + v P and
+ * v = round(sum_k y_k / p_k), so X = sum_k y_k (P/p_k) - v P.  The sum is
+ * taken in double precision in the order k = 0, 1, ... (IEEE division and
+ * addition, round half to even).  The result is round(x / P) mod q_i (up to
+ * a misrounding of v when the fraction is within ~2^-50 of 1/2). */
+void orc_moddown(const orc_params* p, const uint64_t* acc, uint32_t level, uint64_t* out)
+{
+    const uint32_t N = p->N, n = level + 1, nP = p->nP, ext = n + nP;
+    const uint64_t* pp = p->prime + p->nQ;
+    uint64_t hat_inv[ORC_MAX_PRIMES];
+    for (uint32_t k = 0; k < nP; k++) {
+        uint64_t h = 1 % pp[k];
+        for (uint32_t l = 0; l < nP; l++)
+            if (l != k) h = mulmod(h, pp[l] % pp[k], pp[k]);
+        hat_inv[k] = invmod(h, pp[k]);
+    }
+    #pragma omp parallel for
+    for (uint32_t i = 0; i < n; i++) {
+        const uint64_t q = p->prime[i];
+        uint64_t hat_q[ORC_MAX_PRIMES], P_q = 1 % q;
+        for (uint32_t k = 0; k < nP; k++) {
+            uint64_t h = 1 % q;
+            for (uint32_t l = 0; l < nP; l++)
+                if (l != k) h = mulmod(h, pp[l] % q, q);
+            hat_q[k] = h;
+            P_q = mulmod(P_q, pp[k] % q, q);
+        }
+        const uint64_t Pinv = invmod(P_q, q);
+        for (uint32_t poly = 0; poly < 2; poly++) {
+            const uint64_t* A = acc + (size_t)poly * ext * N;
+            uint64_t* o = out + ((size_t)poly * n + i) * N;
+            for (uint32_t c = 0; c < N; c++) {
+                uint64_t y[ORC_MAX_PRIMES];
+                double frac = 0.0;
+                for (uint32_t k = 0; k < nP; k++) {
+                    y[k] = mulmod(A[(size_t)(n + k) * N + c], hat_inv[k], pp[k]);
+                    frac += (double)y[k] / (double)pp[k];
+                }
+                uint64_t v = (uint64_t)rint(frac);
+                uint64_t X = 0;
+                for (uint32_t k = 0; k < nP; k++) X = addmod(X, mulmod(y[k] % q, hat_q[k], q), q);
+                X = submod(X, mulmod(v % q, P_q, q), q);
+                o[c] = mulmod(submod(A[(size_t)i * N + c], X, q), Pinv, q);
+            }
+        }
+    }
+}
+
 /* Hybrid key switching of one polynomial d (coefficient form, level l) with a
  * key from s' to s; returns (k0, k1) with k0 + k1 s ~ d s' (mod Q_l):
  *   1. decompose d into beta = ceil((l+1)/alpha) digits over the primes D_j;
  *   2. ModUp: extend each digit to every prime of Q_l u P by fast base
  *      conversion (the digit's own primes keep d's residues);
  *   3. inner product with the key's digits over Q_l u P;
- *   4. ModDown: k_i = (acc_i - Conv_{P->q_i}(acc_P)) * P^-1 mod q_i. */
+ *   4. ModDown: k_i = round(acc / P) mod q_i (orc_moddown). */
 void orc_keyswitch(const orc_params* p, const uint64_t* d, uint32_t level, const uint64_t* ksk,
                    uint64_t* out)
 {
@@ -647,25 +700,7 @@ void orc_keyswitch(const orc_params* p, const uint64_t* d, uint32_t level, const
     }
 
     /* ModDown */
-    uint64_t srcP[ORC_MAX_PRIMES];
-    for (uint32_t k = 0; k < nP; k++) srcP[k] = p->prime[p->nQ + k];
-    #pragma omp parallel for
-    for (uint32_t i = 0; i < n; i++) {
-        const uint64_t q = p->prime[i];
-        uint64_t Pinv = 1 % q;
-        for (uint32_t k = 0; k < nP; k++) Pinv = mulmod(Pinv, srcP[k] % q, q);
-        Pinv = invmod(Pinv, q);
-        const uint64_t* xs[ORC_MAX_PRIMES];
-        uint64_t* conv = malloc(sizeof(uint64_t) * N);
-        for (uint32_t poly = 0; poly < 2; poly++) {
-            const uint64_t* A = acc + (size_t)poly * ext * N;
-            uint64_t* o = out + ((size_t)poly * n + i) * N;
-            for (uint32_t k = 0; k < nP; k++) xs[k] = A + (size_t)(n + k) * N;
-            base_convert(N, xs, srcP, nP, q, conv);
-            for (uint32_t c = 0; c < N; c++) o[c] = mulmod(submod(A[(size_t)i * N + c], conv[c], q), Pinv, q);
-        }
-        free(conv);
-    }
+    orc_moddown(p, acc, level, out);
     free(acc);
 }
 

@@ -80,6 +80,8 @@ void orc_decrypt(const orc_params* p, const int64_t* s, const uint64_t* ct, uint
                  uint32_t npolys, uint64_t* m /* (level+1) x N */);
 void orc_automorphism(const orc_params* p, const uint64_t* in, uint32_t nlimbs, uint64_t g,
                       uint64_t* out);
+void orc_moddown(const orc_params* p, const uint64_t* acc /* 2 x (level+1+nP) x N */, uint32_t level,
+                 uint64_t* out /* 2 x (level+1) x N */);
 void orc_keyswitch(const orc_params* p, const uint64_t* d, uint32_t level, const uint64_t* ksk,
                    uint64_t* out /* 2 x (level+1) x N */);
 void orc_rotate(const orc_params* p, const uint64_t* ct, uint32_t level, int32_t r,

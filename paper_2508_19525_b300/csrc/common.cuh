@@ -133,6 +133,7 @@ struct ConvTable {
     uint64_t hat_inv[BLB_MAXP];        // (S/s_i)^-1 mod s_i
     uint64_t hat_inv_sh[BLB_MAXP];     // Shoup companions
     uint64_t hat[BLB_MAXP][BLB_MAXP];  // [i][t] = S/s_i mod t
+    uint64_t prod_mod_t[BLB_MAXP];     // S mod t
 };
 
 // ---------------------------------------------------------------------------

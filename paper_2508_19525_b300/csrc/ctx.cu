@@ -337,6 +337,11 @@ static void build_conv(const blb_ctx* c, const std::vector<uint32_t>& src, const
             t.hat[i][k] = v;
         }
     }
+    for (uint32_t k = 0; k < t.nt; k++) {
+        uint64_t tq = c->q[dst[k]], v = 1 % tq;
+        for (uint32_t l = 0; l < t.ns; l++) v = host_mulmod(v, c->q[src[l]] % tq, tq);
+        t.prod_mod_t[k] = v;
+    }
 }
 
 extern "C" int blb_ctx_create(const blb_params* params, void* stream, blb_ctx** out)

@@ -7,9 +7,11 @@
 //   digits D_j = {j alpha, ..., min((j+1) alpha, n) - 1}, j < beta = ceil(n/alpha)
 //   d~_j = Conv_{D_j -> Q_l u P}([d]_{D_j})   (the digit's own primes keep d)
 //   acc  = sum_j d~_j (b_j, a_j)              (over Q_l u P)
-//   out_i = (acc_i - Conv_{P -> q_i}([acc]_P)) * P^-1 mod q_i
-// Conv(x)_t = sum_i [x_i (S/s_i)^-1]_{s_i} (S/s_i mod t) mod t, without
-// overflow correction.  Every step is an exact integer function of d's
+//   out_i = (acc_i - X_i) * P^-1 mod q_i = round(acc / P) mod q_i, X the centered
+//           representative of acc mod P (k_moddown_conv)
+// Conv(x)_t = sum_i [x_i (S/s_i)^-1]_{s_i} (S/s_i mod t) mod t, the ModUp
+// conversion, without overflow correction (the overflow is a multiple of the
+// digit modulus, which the key's gadget factor cancels).  Every step is an exact integer function of d's
 // coefficients, so any correct schedule of it yields the same limbs.
 #include <mutex>
 #include <string>
@@ -39,6 +41,37 @@ __global__ void k_conv(const uint64_t* __restrict__ src, size_t src_ps, const Co
         acc128 a{0, 0};
         for (uint32_t i = 0; i < ns; i++) mad128(a, y[i], tab->hat[i][k]);
         dst[poly * dst_ps + (size_t)tab->dst_row[k] * N + c] = barrett128(a.lo, a.hi, qs[pt], bar[2 * pt], bar[2 * pt + 1]);
+    }
+}
+
+// ModDown conversion with rounding (Halevi, Polyakov, Shoup 2019): for the P
+// limbs x_k, y_k = [x_k (P/p_k)^-1]_{p_k}, v = round(sum_k y_k / p_k) in double
+// precision (IEEE division and addition, in the order k = 0, 1, ...), and
+// X = sum_k y_k (P/p_k) - v P is the representative of x mod P in (-P/2, P/2];
+// dst row t gets X mod q_t.
+__global__ void k_moddown_conv(const uint64_t* __restrict__ src, size_t src_ps, const ConvTable* __restrict__ tab,
+                               uint32_t nt, uint64_t* __restrict__ dst, size_t dst_ps,
+                               const uint64_t* __restrict__ qs, const uint64_t* __restrict__ bar, uint32_t N)
+{
+    const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x, poly = blockIdx.y;
+    if (c >= N) return;
+    const uint32_t ns = tab->ns;
+    uint64_t y[BLB_MAXP];
+    double frac = 0.0;
+    for (uint32_t k = 0; k < ns; k++) {
+        const uint64_t pk = qs[tab->src[k]];
+        y[k] = mul_shoup(src[poly * src_ps + (size_t)k * N + c], tab->hat_inv[k], tab->hat_inv_sh[k], pk);
+        frac = __dadd_rn(frac, __ddiv_rn(__ull2double_rn(y[k]), __ull2double_rn(pk)));
+    }
+    const uint64_t v = (uint64_t)__double2ll_rn(frac);
+    for (uint32_t t = 0; t < nt; t++) {
+        const uint32_t pt = tab->dst[t];
+        const uint64_t q = qs[pt], r0 = bar[2 * pt], r1 = bar[2 * pt + 1];
+        acc128 a{0, 0};
+        for (uint32_t k = 0; k < ns; k++) mad128(a, y[k], tab->hat[k][t]);
+        const uint64_t x = barrett128(a.lo, a.hi, q, r0, r1);
+        const uint64_t vp = mul_mod(v, tab->prod_mod_t[t], q, r0, r1);
+        dst[poly * dst_ps + (size_t)tab->dst_row[t] * N + c] = sub_mod(x, vp, q);
     }
 }
 
@@ -124,8 +157,9 @@ static int keyswitch_impl(blb_ctx* ctx, const uint64_t* d_ntt, uint32_t level, c
     // 4. ModDown: P limbs to coefficient form, convert to Q_l, back to evaluation
     BLB_TRY(ntt_inverse(ctx, acc + (size_t)n * N, nP, ctx->pmap()));
     BLB_TRY(ntt_inverse(ctx, acc + ((size_t)E + n) * N, nP, ctx->pmap()));
-    k_conv<<<dim3((N + kT - 1) / kT, 2), kT, 0, ctx->stream>>>(acc + (size_t)n * N, (size_t)E * N, ctx->d_moddown, n,
-                                                               cv, (size_t)n * N, ctx->d_q, ctx->d_bar, N);
+    k_moddown_conv<<<dim3((N + kT - 1) / kT, 2), kT, 0, ctx->stream>>>(acc + (size_t)n * N, (size_t)E * N,
+                                                                       ctx->d_moddown, n, cv, (size_t)n * N, ctx->d_q,
+                                                                       ctx->d_bar, N);
     BLB_LAUNCHED();
     BLB_TRY(ntt_forward(ctx, cv, 2 * n, ctx->qmap(n)));
     PInv pinv{};

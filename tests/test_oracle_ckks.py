@@ -279,3 +279,31 @@ def test_tensor_and_relinearize_decrypt_to_product():
         scale = 2.0 ** 80 / o.primes[2]
         got = o.decode(o.centered(o.decrypt(s, res)[0]), scale)
         assert np.max(np.abs(got - z1 * z2)) < 1e-6
+
+
+@pytest.mark.parametrize("level", [4, 2, 0])
+def test_moddown_is_rounded_division_by_P(level):
+    """ModDown returns round(x / P) mod q_i for x given by its residues over
+    Q_l u P (big-integer CRT and rounding in Python)."""
+    prm = wl.HEParams(6, wl.SMALL.q_bits, wl.SMALL.p_bits, wl.SMALL.dnum)
+    o = make(prm)
+    n = level + 1
+    basis = o.primes[:n] + o.primes[o.nQ:]
+    acc = wl.random_residues(basis, o.N, seed=300 + level, polys=2)
+    out = o.moddown(acc, level)
+    QP = 1
+    for q in basis:
+        QP *= q
+    P = 1
+    for p in o.primes[o.nQ:]:
+        P *= p
+    for poly in range(2):
+        for c in range(o.N):
+            x = 0
+            for i, q in enumerate(basis):
+                Qi = QP // q
+                x += int(acc[poly, i, c]) * Qi * pow(Qi, -1, q)
+            x %= QP
+            r = (2 * x + P) // (2 * P)  # round(x / P), x in [0, QP)
+            for i in range(n):
+                assert int(out[poly, i, c]) == r % o.primes[i], (poly, c, i)
