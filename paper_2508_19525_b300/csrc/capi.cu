@@ -93,30 +93,53 @@ int rotate_add(blb_ctx* c, const blb_keys* keys, const uint64_t* in, uint32_t le
     return BLB_OK;
 }
 
-// matmul_cp inner products: T[e][g] = sum_{c, b} baby[c][b] (.) pt[e][g][c][b]
-__global__ void k_cp_mac(uint64_t* __restrict__ T, const uint64_t* __restrict__ baby, const uint64_t* __restrict__ pts,
-                         uint32_t n, uint32_t N, uint32_t nX, uint32_t b1, const uint64_t* __restrict__ qs,
-                         const uint64_t* __restrict__ bar)
+// matmul_cp inner products: T[e][g] = sum_{c, b} baby[c][b] (.) pt[e][g][c][b].
+// A CTA owns C coefficients of one limb: it stages the baby-step values of
+// every term for those coefficients in shared memory once, then streams the
+// plaintexts of every (e, g) through them.  Each plaintext word and each
+// baby-step word is read from HBM exactly once.  Lazy 128-bit sums, folded
+// every 8 terms; the 8 plaintext loads of a group are issued together.
+__global__ void __launch_bounds__(256) k_cp_mac_tile(uint64_t* __restrict__ T, const uint64_t* __restrict__ baby,
+                                                      const uint64_t* __restrict__ pts, uint32_t n, uint32_t N,
+                                                      uint32_t terms, uint32_t neg, uint32_t logC,
+                                                      const uint64_t* __restrict__ qs, const uint64_t* __restrict__ bar)
 {
-    const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x, i = blockIdx.y, eg = blockIdx.z;
-    if (c >= N) return;
+    extern __shared__ uint64_t sb[];  // [terms][2][C]
+    const uint32_t C = 1u << logC;
+    const uint32_t i = blockIdx.y, c0 = blockIdx.x << logC;
+    const size_t nN = (size_t)n * N;
+    for (uint32_t idx = threadIdx.x; idx < terms * 2 * C; idx += blockDim.x) {
+        const uint32_t cc = idx & (C - 1), tp = idx >> logC;  // tp = t * 2 + poly
+        sb[idx] = baby[(size_t)(tp >> 1) * 2 * nN + (size_t)(tp & 1) * nN + (size_t)i * N + c0 + cc];
+    }
+    __syncthreads();
     const uint64_t q = qs[i], r0 = bar[2 * i], r1 = bar[2 * i + 1];
-    acc128 a0{0, 0}, a1{0, 0};
-    const uint32_t terms = nX * b1;
-    const uint64_t* P = pts + (size_t)eg * terms * n * N + (size_t)i * N + c;
-    for (uint32_t t = 0; t < terms; t++) {
-        const uint64_t w = P[(size_t)t * n * N];
-        const uint64_t* B = baby + (size_t)t * 2 * n * N + (size_t)i * N + c;
-        mad128(a0, B[0], w);
-        mad128(a1, B[(size_t)n * N], w);
-        if ((t & 15) == 15) {  // keep the 128-bit sums far from overflow
-            a0 = acc128{barrett128(a0.lo, a0.hi, q, r0, r1), 0};
+    const uint32_t lanes = blockDim.x >> logC, lane = threadIdx.x >> logC, cc = threadIdx.x & (C - 1);
+    for (uint32_t eg = lane; eg < neg; eg += lanes) {
+        const uint64_t* P = pts + (size_t)eg * terms * nN + (size_t)i * N + c0 + cc;
+        acc128 a0{0, 0}, a1{0, 0};
+        uint32_t t = 0;
+        for (; t + 8 <= terms; t += 8) {
+            uint64_t w[8];
+#pragma unroll
+            for (int u = 0; u < 8; u++) w[u] = __ldcs(P + (size_t)(t + u) * nN);  // streamed once
+#pragma unroll
+            for (int u = 0; u < 8; u++) {
+                mad128(a0, sb[(2 * (t + u)) * C + cc], w[u]);
+                mad128(a1, sb[(2 * (t + u) + 1) * C + cc], w[u]);
+            }
+            a0 = acc128{barrett128(a0.lo, a0.hi, q, r0, r1), 0};  // keep the 128-bit sums far from overflow
             a1 = acc128{barrett128(a1.lo, a1.hi, q, r0, r1), 0};
         }
+        for (; t < terms; t++) {
+            const uint64_t w = __ldcs(P + (size_t)t * nN);
+            mad128(a0, sb[(2 * t) * C + cc], w);
+            mad128(a1, sb[(2 * t + 1) * C + cc], w);
+        }
+        uint64_t* o = T + (size_t)eg * 2 * nN + (size_t)i * N + c0 + cc;
+        o[0] = barrett128(a0.lo, a0.hi, q, r0, r1);
+        o[nN] = barrett128(a1.lo, a1.hi, q, r0, r1);
     }
-    uint64_t* o = T + (size_t)eg * 2 * n * N + (size_t)i * N + c;
-    o[0] = barrett128(a0.lo, a0.hi, q, r0, r1);
-    o[(size_t)n * N] = barrett128(a1.lo, a1.hi, q, r0, r1);
 }
 
 }  // namespace
@@ -128,8 +151,19 @@ int launch_cp_mac(blb_ctx* c, const blb_cp_plan* plan, const uint64_t* baby, uin
     // the (e, g) partial sums written once
     const uint64_t terms = (uint64_t)plan->nX * plan->b1, outs = (uint64_t)plan->nY * plan->G;
     ProfScope prof(c, "cp_mac", (outs * terms * n + terms * 2 * n + outs * 2 * n) * c->N * 8);
-    dim3 grid((c->N + kT - 1) / kT, n, plan->nY * plan->G);
-    k_cp_mac<<<grid, kT, 0, c->stream>>>(T, baby, plan->d_pts, n, c->N, plan->nX, plan->b1, c->d_q, c->d_bar);
+    // coefficients per CTA: largest power of two <= 64 whose baby tile fits 64 KB
+    uint32_t logC = 6;
+    while (logC > 3 && terms * 2 * (8ull << logC) > (64u << 10)) logC--;
+    const size_t smem = terms * 2 * (8ull << logC);
+    if (smem > (160u << 10)) return blb_fail(BLB_ERR_ARG, "too many plaintext terms per output for one CTA");
+    static bool attr_set = false;
+    if (!attr_set) {
+        BLB_CUDA(cudaFuncSetAttribute(k_cp_mac_tile, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 << 10));
+        attr_set = true;
+    }
+    dim3 grid(c->N >> logC, n);
+    k_cp_mac_tile<<<grid, 256, smem, c->stream>>>(T, baby, plan->d_pts, n, c->N, (uint32_t)terms, (uint32_t)outs, logC,
+                                                  c->d_q, c->d_bar);
     BLB_LAUNCHED();
     return BLB_OK;
 }
@@ -661,20 +695,47 @@ extern "C" int blb_matmul_cp_plan(blb_ctx* c, const blb_keys* K, const blb_cp_pl
     uint64_t* T = (uint64_t*)dev_alloc(c, T_bytes);
     for (uint32_t e = 0; e < P->nY; e++) Y[e] = nullptr;
     int rc = (baby && T) ? BLB_OK : blb_fail(BLB_ERR_OOM, "matmul_cp workspace");
-    // baby steps
-    for (uint32_t ci = 0; !rc && ci < nX; ci++)
-        for (uint32_t b = 0; !rc && b < P->b1; b++)
-            rc = rotate_into(c, K, X[ci]->d, P->level, (int32_t)(b * P->m), baby + ((size_t)ci * P->b1 + b) * ctw);
+    // baby steps: Rot^{b m}(X_c), all in one batched key-switch pass
+    std::vector<KsItem> items;
+    for (uint32_t ci = 0; !rc && ci < nX; ci++) {
+        uint64_t* dst0 = baby + (size_t)ci * P->b1 * ctw;
+        if (cudaMemcpyAsync(dst0, X[ci]->d, ctw * 8, cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess)
+            rc = blb_fail(BLB_ERR_CUDA, "copy failed");
+        for (uint32_t b = 1; !rc && b < P->b1; b++) {
+            const uint64_t g = galois_element(N, (int32_t)(b * P->m));
+            const KeyEntry* k = K->find(g);
+            if (!k) {
+                rc = blb_fail(BLB_ERR_NO_KEY, "no Galois key for rotation " + std::to_string(b * P->m));
+                break;
+            }
+            uint64_t* o = baby + ((size_t)ci * P->b1 + b) * ctw;
+            items.push_back(KsItem{X[ci]->d, X[ci]->d + (size_t)n * N, nullptr, k->d, o, o + (size_t)n * N, g});
+        }
+    }
+    if (!rc) rc = keyswitch_batch(c, P->level, items.data(), (uint32_t)items.size(), 0);
     // plaintext products for every (e, g)
     if (!rc) rc = launch_cp_mac(c, P, baby, T);
-    // giant steps and rescale
+    // giant steps: acc_e += Rot^{g b1 m}(T[e][g]); one batched pass per g (distinct outputs)
+    for (uint32_t g = 1; !rc && g < P->G; g++) {
+        const uint64_t ge = galois_element(N, (int32_t)(g * P->b1 * P->m));
+        const KeyEntry* k = K->find(ge);
+        if (!k) {
+            rc = blb_fail(BLB_ERR_NO_KEY, "no Galois key for rotation " + std::to_string(g * P->b1 * P->m));
+            break;
+        }
+        items.clear();
+        for (uint32_t e = 0; e < P->nY; e++) {
+            uint64_t* acc = T + (size_t)e * P->G * ctw;
+            const uint64_t* src = acc + (size_t)g * ctw;
+            items.push_back(KsItem{src, src + (size_t)n * N, nullptr, k->d, acc, acc + (size_t)n * N, ge});
+        }
+        rc = keyswitch_batch(c, P->level, items.data(), (uint32_t)items.size(), 1);
+    }
+    // rescale
     for (uint32_t e = 0; !rc && e < P->nY; e++) {
-        uint64_t* acc = T + (size_t)e * P->G * ctw;
-        for (uint32_t g = 1; !rc && g < P->G; g++)
-            rc = rotate_add(c, K, acc + (size_t)g * ctw, P->level, (int32_t)(g * P->b1 * P->m), acc);
         blb_ct* y = nullptr;
-        if (!rc) rc = new_ct(c, P->level - 1, 2, X[0]->scale, &y);
-        if (!rc) rc = launch_rescale(c, y->d, acc, P->level, 2);
+        rc = new_ct(c, P->level - 1, 2, X[0]->scale, &y);
+        if (!rc) rc = launch_rescale(c, y->d, T + (size_t)e * P->G * ctw, P->level, 2);
         Y[e] = y;
     }
     dev_free(c, baby, baby_bytes);

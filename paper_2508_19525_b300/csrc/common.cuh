@@ -159,7 +159,8 @@ struct blb_ctx {
     std::vector<std::vector<uint64_t>> ql_inv;  // [l][i] q_l^-1 mod q_i
     // conversion tables: ModUp per (level, digit), ModDown P -> Q
     std::vector<ConvTable> h_modup;             // index level * dnum + j
-    std::vector<ConvTable*> d_modup;
+    std::vector<ConvTable*> d_modup;            // pointers into d_modup_all
+    ConvTable* d_modup_all = nullptr;
     ConvTable h_moddown;
     ConvTable* d_moddown = nullptr;
     // optional CUDA-event timing of named launch sites (bench / profiling)
@@ -173,6 +174,9 @@ struct blb_ctx {
     };
     std::vector<ProfSite> prof;
     std::vector<cudaEvent_t> event_pool;
+    // grow-only arena for batched key switching (stream-ordered reuse)
+    uint64_t* batch = nullptr;
+    size_t batch_words = 0;
     // scratch arena (stream-ordered reuse)
     uint64_t* scratch = nullptr;
     size_t scratch_words = 0;
@@ -264,6 +268,9 @@ uint64_t galois_element(uint32_t N, int32_t rot);
 // NTT of `rows` rows of N words; row r uses prime map.p[r % map.n]
 int ntt_forward(blb_ctx* ctx, uint64_t* data, uint32_t rows, const LimbMap& map);
 int ntt_inverse(blb_ctx* ctx, uint64_t* data, uint32_t rows, const LimbMap& map);
+// same on an explicit device row list: entry = row index | prime index << 24
+int ntt_forward_list(blb_ctx* ctx, uint64_t* data, uint32_t rows, const uint32_t* d_rowlist);
+int ntt_inverse_list(blb_ctx* ctx, uint64_t* data, uint32_t rows, const uint32_t* d_rowlist);
 
 // element-wise (row r uses prime map.p[r % map.n]; operand b repeats every
 // b_rows rows)
@@ -293,6 +300,24 @@ int launch_sample_uniform(blb_ctx* ctx, uint64_t* out, uint32_t rows, const Limb
 // key switching of d (NTT domain, level+1 rows) with key (dnum x 2 x np x N)
 int keyswitch(blb_ctx* ctx, const uint64_t* d_ntt, uint32_t level, const uint64_t* key, uint64_t* out0,
               uint64_t* out1);
+
+// Batched key switching with fused automorphism: for each item,
+//   (k0, k1) = KeySwitch(sigma_g(c1), key)
+//   out0 = [out0 +] sigma_g(c0) + k0          (c0 may be null)
+//   out1 = [out1 +] sigma_g(add1) + k1        (add1 may be null)
+// g = 1 means no automorphism.  All items are at `level`; accumulate != 0 adds
+// into the outputs instead of overwriting them (items of one call must then
+// have distinct outputs).
+struct KsItem {
+    const uint64_t* c0;
+    const uint64_t* c1;
+    const uint64_t* add1;
+    const uint64_t* key;
+    uint64_t* out0;
+    uint64_t* out1;
+    uint64_t g;
+};
+int keyswitch_batch(blb_ctx* ctx, uint32_t level, const KsItem* items, uint32_t count, int accumulate);
 
 // encoding (Eq. 2)
 int encode_slots(blb_ctx* ctx, const double* d_z, uint32_t npts, uint32_t n, uint32_t level, double scale,

@@ -479,11 +479,12 @@ extern "C" int blb_ctx_create(const blb_params* params, void* stream, blb_ctx** 
                 dst.push_back(c->nQ + k);
                 row.push_back(n + k);
             }
-            ConvTable& tab = c->h_modup[(size_t)l * c->dnum + j];
-            build_conv(c, src, dst, row, tab);
-            if ((rc = upload(c, &c->d_modup[(size_t)l * c->dnum + j], &tab, 1))) return fail(rc);
+            build_conv(c, src, dst, row, c->h_modup[(size_t)l * c->dnum + j]);
         }
     }
+    // one contiguous device array [level][digit]
+    if ((rc = upload(c, &c->d_modup_all, c->h_modup.data(), c->h_modup.size()))) return fail(rc);
+    for (size_t i = 0; i < c->h_modup.size(); i++) c->d_modup[i] = c->d_modup_all + i;
     {
         std::vector<uint32_t> src, dst, row;
         for (uint32_t k = 0; k < c->nP; k++) src.push_back(c->nQ + k);
@@ -546,9 +547,10 @@ static void ctx_destroy(blb_ctx* c)
     dev_free(c, c->d_cdt, 19 * 8);
     dev_free(c, c->d_kperm, (size_t)c->N / 2 * 4);
     dev_free(c, c->d_flag, sizeof(int));
-    for (auto* p : c->d_modup) dev_free(c, p, sizeof(ConvTable));
+    dev_free(c, c->d_modup_all, c->h_modup.size() * sizeof(ConvTable));
     dev_free(c, c->d_moddown, sizeof(ConvTable));
     dev_free(c, c->scratch, c->scratch_words * 8);
+    dev_free(c, c->batch, c->batch_words * 8);
     delete c;
 }
 

@@ -244,3 +244,206 @@ extern "C" int blb_keyswitch_noalloc(blb_ctx* c, const blb_keys* K, int32_t rot,
     if (!is_device_ptr(out)) BLB_CUDA(cudaStreamSynchronize(c->stream));
     return BLB_OK;
 }
+
+// ===========================================================================
+// Batched key switching (many polynomials, each with its own key and Galois
+// element, in one pass of launches)
+// ===========================================================================
+namespace {
+
+struct DevItem {
+    const uint64_t* c0;
+    const uint64_t* c1;
+    const uint64_t* add1;
+    const uint64_t* key;
+    uint64_t* out0;
+    uint64_t* out1;
+    uint64_t g;
+};
+
+__device__ __forceinline__ uint32_t perm_index(uint32_t k, uint32_t logN, uint64_t g)
+{
+    if (g == 1) return k;
+    const uint32_t N = 1u << logN;
+    const uint64_t e = 2 * (uint64_t)(__brev(k) >> (32 - logN)) + 1;
+    const uint32_t ge = (uint32_t)((g * e) & (2ull * N - 1));
+    return __brev((ge - 1) >> 1) >> (32 - logN);
+}
+
+// din[item][i][k] = c1[i][perm(k)] and coef = din (the latter transformed in place)
+__global__ void k_ksb_gather(uint64_t* __restrict__ din, uint64_t* __restrict__ coef, const DevItem* __restrict__ it,
+                             uint32_t n, uint32_t logN)
+{
+    const uint32_t N = 1u << logN;
+    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x, i = blockIdx.y, item = blockIdx.z;
+    if (k >= N) return;
+    const DevItem d = it[item];
+    const uint64_t v = d.c1[(size_t)i * N + perm_index(k, logN, d.g)];
+    const size_t o = ((size_t)item * n + i) * N + k;
+    din[o] = v;
+    coef[o] = v;
+}
+
+// ModUp of every digit of every item: grid.y = item * beta + j
+__global__ void k_ksb_modup(const uint64_t* __restrict__ coef, uint64_t* __restrict__ ext,
+                            const ConvTable* __restrict__ tabs, uint32_t n, uint32_t E, uint32_t beta,
+                            uint32_t alpha, const uint64_t* __restrict__ qs, const uint64_t* __restrict__ bar,
+                            uint32_t N)
+{
+    const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= N) return;
+    const uint32_t item = blockIdx.y / beta, j = blockIdx.y % beta;
+    const ConvTable* tab = tabs + j;
+    const uint32_t ns = tab->ns, nt = tab->nt;
+    const uint64_t* src = coef + ((size_t)item * n + j * alpha) * N + c;
+    uint64_t* dst = ext + ((size_t)item * beta + j) * E * N + c;
+    uint64_t y[BLB_MAXP];
+    for (uint32_t i = 0; i < ns; i++)
+        y[i] = mul_shoup(src[(size_t)i * N], tab->hat_inv[i], tab->hat_inv_sh[i], qs[tab->src[i]]);
+    for (uint32_t t = 0; t < nt; t++) {
+        const uint32_t pt = tab->dst[t];
+        acc128 a{0, 0};
+        for (uint32_t i = 0; i < ns; i++) mad128(a, y[i], tab->hat[i][t]);
+        dst[(size_t)tab->dst_row[t] * N] = barrett128(a.lo, a.hi, qs[pt], bar[2 * pt], bar[2 * pt + 1]);
+    }
+}
+
+// the digit's own rows of the extended digit are the input's evaluation rows
+__global__ void k_ksb_digit_rows(uint64_t* __restrict__ ext, const uint64_t* __restrict__ din, uint32_t n, uint32_t E,
+                                 uint32_t beta, uint32_t alpha, uint32_t N)
+{
+    const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x, t = blockIdx.y, item = blockIdx.z;
+    if (c >= N) return;
+    const uint32_t j = t / alpha;
+    ext[(((size_t)item * beta + j) * E + t) * N + c] = din[((size_t)item * n + t) * N + c];
+}
+
+// acc[item][p][t] = sum_j ext[item][j][t] * key_item[j][p][kt]
+__global__ void k_ksb_inner(uint64_t* __restrict__ acc, const uint64_t* __restrict__ ext,
+                            const DevItem* __restrict__ it, LimbMap emap, uint32_t n, uint32_t E, uint32_t beta,
+                            uint32_t nQ, uint32_t np, const uint64_t* __restrict__ qs,
+                            const uint64_t* __restrict__ bar, uint32_t N)
+{
+    const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x, t = blockIdx.y, item = blockIdx.z;
+    if (c >= N) return;
+    const uint32_t pi = emap.p[t];
+    const uint32_t kt = t < n ? t : nQ + (t - n);
+    const uint64_t* key = it[item].key;
+    const uint64_t* x = ext + (size_t)item * beta * E * N + (size_t)t * N + c;
+    acc128 a0{0, 0}, a1{0, 0};
+    for (uint32_t j = 0; j < beta; j++) {
+        uint64_t v = x[(size_t)j * E * N];
+        mad128(a0, v, key[(((size_t)j * 2 + 0) * np + kt) * N + c]);
+        mad128(a1, v, key[(((size_t)j * 2 + 1) * np + kt) * N + c]);
+    }
+    const uint64_t q = qs[pi], r0 = bar[2 * pi], r1 = bar[2 * pi + 1];
+    uint64_t* o = acc + (size_t)item * 2 * E * N + (size_t)t * N + c;
+    o[0] = barrett128(a0.lo, a0.hi, q, r0, r1);
+    o[(size_t)E * N] = barrett128(a1.lo, a1.hi, q, r0, r1);
+}
+
+// outputs: p = 0: [out0 +] sigma(c0) + (acc0 - cv0) P^-1;  p = 1: [out1 +] sigma(add1) + (acc1 - cv1) P^-1
+__global__ void k_ksb_finish(const DevItem* __restrict__ it, const uint64_t* __restrict__ acc,
+                             const uint64_t* __restrict__ cv, uint32_t n, uint32_t E, PInv pinv,
+                             const uint64_t* __restrict__ qs, uint32_t logN, int accumulate)
+{
+    const uint32_t N = 1u << logN;
+    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x, row = blockIdx.y, item = blockIdx.z;
+    if (k >= N) return;
+    const uint32_t p = row / n, i = row % n;
+    const DevItem d = it[item];
+    const uint64_t q = qs[i];
+    const uint64_t a = acc[(((size_t)item * 2 + p) * E + i) * N + k];
+    const uint64_t v = cv[(((size_t)item * 2 + p) * n + i) * N + k];
+    uint64_t r = mul_shoup(sub_mod(a, v, q), pinv.w[i], pinv.wp[i], q);
+    const uint64_t* addp = p ? d.add1 : d.c0;
+    if (addp) r = add_mod(r, addp[(size_t)i * N + perm_index(k, logN, d.g)], q);
+    uint64_t* o = (p ? d.out1 : d.out0) + (size_t)i * N + k;
+    *o = accumulate ? add_mod(*o, r, q) : r;
+}
+
+}  // namespace
+
+int keyswitch_batch(blb_ctx* ctx, uint32_t level, const KsItem* items, uint32_t count, int accumulate)
+{
+    if (count == 0) return BLB_OK;
+    const uint32_t N = ctx->N, n = level + 1, nP = ctx->nP, E = n + nP;
+    const uint32_t alpha = ctx->alpha, beta = (n + alpha - 1) / alpha;
+    // words per item: din n + coef n + ext beta E + acc 2E + cv 2n
+    const size_t per_item = ((size_t)2 * n + (size_t)beta * E + 2 * (size_t)E + 2 * (size_t)n) * N;
+    const size_t budget = (size_t)1 << 27;  // 1 GiB of words per chunk
+    const uint32_t chunk = (uint32_t)std::max<size_t>(1, std::min<size_t>(count, budget / per_item));
+    // rows to transform for one chunk of `chunk` items
+    std::vector<uint32_t> ext_rows, p_rows;
+    for (uint32_t item = 0; item < chunk; item++) {
+        for (uint32_t j = 0; j < beta; j++) {
+            const uint32_t lo = j * alpha, hi = std::min((j + 1) * alpha, n);
+            for (uint32_t t = 0; t < E; t++) {
+                if (t >= lo && t < hi) continue;
+                const uint32_t prime = t < n ? t : ctx->nQ + (t - n);
+                ext_rows.push_back((uint32_t)(((size_t)item * beta + j) * E + t) | (prime << 24));
+            }
+        }
+        for (uint32_t pp = 0; pp < 2; pp++)
+            for (uint32_t k = 0; k < nP; k++)
+                p_rows.push_back((uint32_t)(((size_t)item * 2 + pp) * E + n + k) | ((ctx->nQ + k) << 24));
+    }
+    if ((size_t)chunk * beta * E >= (1u << 24)) return blb_fail(BLB_ERR_ARG, "key-switch batch too large");
+    const size_t table_words = (ext_rows.size() + p_rows.size() + 1) / 2 + (size_t)chunk * sizeof(DevItem) / 8 + 8;
+    const size_t need = per_item * chunk + table_words;
+    if (need > ctx->batch_words) {
+        dev_free(ctx, ctx->batch, ctx->batch_words * 8);
+        ctx->batch = (uint64_t*)dev_alloc(ctx, need * 8);
+        ctx->batch_words = ctx->batch ? need : 0;
+        if (!ctx->batch) return blb_fail(BLB_ERR_OOM, "key-switch batch arena");
+    }
+    uint64_t* din = ctx->batch;
+    uint64_t* coef = din + (size_t)chunk * n * N;
+    uint64_t* ext = coef + (size_t)chunk * n * N;
+    uint64_t* acc = ext + (size_t)chunk * beta * E * N;
+    uint64_t* cv = acc + (size_t)chunk * 2 * E * N;
+    DevItem* d_items = (DevItem*)(cv + (size_t)chunk * 2 * n * N);
+    uint32_t* d_ext_rows = (uint32_t*)(d_items + chunk);
+    uint32_t* d_p_rows = d_ext_rows + ext_rows.size();
+    BLB_CUDA(cudaMemcpyAsync(d_ext_rows, ext_rows.data(), ext_rows.size() * 4, cudaMemcpyHostToDevice, ctx->stream));
+    BLB_CUDA(cudaMemcpyAsync(d_p_rows, p_rows.data(), p_rows.size() * 4, cudaMemcpyHostToDevice, ctx->stream));
+    PInv pinv{};
+    for (uint32_t i = 0; i < n; i++) {
+        pinv.w[i] = ctx->P_inv_mod_q[i];
+        pinv.wp[i] = shoup_companion(pinv.w[i], ctx->q[i]);
+    }
+    const LimbMap emap = ctx->extmap(level);
+    const uint32_t gx = (N + kT - 1) / kT;
+    for (uint32_t first = 0; first < count; first += chunk) {
+        const uint32_t cnt = std::min(chunk, count - first);
+        ProfScope prof(ctx, "keyswitch", ((uint64_t)n + 2ull * beta * E + 2ull * n) * N * 8 * cnt);
+        std::vector<DevItem> h(cnt);
+        for (uint32_t i = 0; i < cnt; i++) {
+            const KsItem& s = items[first + i];
+            h[i] = DevItem{s.c0, s.c1, s.add1, s.key, s.out0, s.out1, s.g};
+        }
+        BLB_CUDA(cudaMemcpyAsync(d_items, h.data(), cnt * sizeof(DevItem), cudaMemcpyHostToDevice, ctx->stream));
+        k_ksb_gather<<<dim3(gx, n, cnt), kT, 0, ctx->stream>>>(din, coef, d_items, n, ctx->logN);
+        BLB_LAUNCHED();
+        BLB_TRY(ntt_inverse(ctx, coef, cnt * n, ctx->qmap(n)));
+        k_ksb_modup<<<dim3(gx, cnt * beta), kT, 0, ctx->stream>>>(coef, ext, ctx->d_modup[(size_t)level * ctx->dnum],
+                                                                  n, E, beta, alpha, ctx->d_q, ctx->d_bar, N);
+        BLB_LAUNCHED();
+        const uint32_t ext_per_item = (uint32_t)(ext_rows.size() / chunk);
+        BLB_TRY(ntt_forward_list(ctx, ext, cnt * ext_per_item, d_ext_rows));
+        k_ksb_digit_rows<<<dim3(gx, n, cnt), kT, 0, ctx->stream>>>(ext, din, n, E, beta, alpha, N);
+        BLB_LAUNCHED();
+        k_ksb_inner<<<dim3(gx, E, cnt), kT, 0, ctx->stream>>>(acc, ext, d_items, emap, n, E, beta, ctx->nQ, ctx->np,
+                                                              ctx->d_q, ctx->d_bar, N);
+        BLB_LAUNCHED();
+        BLB_TRY(ntt_inverse_list(ctx, acc, cnt * 2 * nP, d_p_rows));
+        k_moddown_conv<<<dim3(gx, 2 * cnt), kT, 0, ctx->stream>>>(acc + (size_t)n * N, (size_t)E * N, ctx->d_moddown,
+                                                                  n, cv, (size_t)n * N, ctx->d_q, ctx->d_bar, N);
+        BLB_LAUNCHED();
+        BLB_TRY(ntt_forward(ctx, cv, cnt * 2 * n, ctx->qmap(n)));
+        k_ksb_finish<<<dim3(gx, 2 * n, cnt), kT, 0, ctx->stream>>>(d_items, acc, cv, n, E, pinv, ctx->d_q, ctx->logN,
+                                                                   accumulate);
+        BLB_LAUNCHED();
+    }
+    return BLB_OK;
+}
