@@ -40,6 +40,7 @@ def lib():
         L.orc_galois_elt.restype = ctypes.c_uint64
         L.orc_ksk_words.restype = ctypes.c_uint64
         L.orc_cp_num_rotations.restype = ctypes.c_uint32
+        L.orc_cc_num_rotations.restype = ctypes.c_uint32
         L.orc_is_prime.argtypes = [ctypes.c_uint64]
         L.orc_galois_elt.argtypes = [ctypes.c_void_p, ctypes.c_int32]
     return _lib
@@ -267,6 +268,26 @@ class Oracle:
         if rc:
             raise ValueError(f"orc_matmul_cp failed: {rc}")
         return Y
+
+    def matmul_cc(self, A_cts, B_cts, L, Hg, b1s1, b1s2, galois, relin):
+        """A_cts, B_cts: (n_c, 2, level+1, N) -> C: (L/Kc, 2, level-3, N)."""
+        A_cts = np.ascontiguousarray(A_cts, np.uint64)
+        B_cts = np.ascontiguousarray(B_cts, np.uint64)
+        n_c, level = A_cts.shape[0], A_cts.shape[2] - 1
+        Kc = (self.N // 2) // (L * Hg)
+        gals = np.array(list(galois.keys()), np.uint64)
+        keys = [np.ascontiguousarray(galois[int(g)], np.uint64) for g in gals]
+        ptrs = (_u64p * max(1, len(keys)))(*[_p(kk, _u64p) for kk in keys])
+        gs = _GaloisSet(len(keys), _p(gals, _u64p), ptrs)
+        C = np.zeros((L // Kc, 2, level - 3, self.N), np.uint64)
+        rc = lib().orc_matmul_cc(self._pp, ctypes.byref(gs), _p(np.ascontiguousarray(relin, np.uint64), _u64p),
+                                 _p(A_cts, _u64p), _p(B_cts, _u64p), n_c, level, L, Hg, b1s1, b1s2, _p(C, _u64p))
+        if rc:
+            raise ValueError(f"orc_matmul_cc failed: {rc}")
+        return C
+
+    def cc_num_rotations(self, n_c, L, Kc, b1s1, b1s2):
+        return int(lib().orc_cc_num_rotations(n_c, L, Kc, b1s1, b1s2))
 
     def cp_num_rotations(self, nX, nY, b1, G):
         return int(lib().orc_cp_num_rotations(nX, nY, b1, G))

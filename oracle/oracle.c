@@ -907,6 +907,245 @@ int orc_matmul_cp(const orc_params* p, const orc_galois_set* gk, const uint64_t*
 }
 
 /* ------------------------------------------------------------------------- */
+/* matmul_cc: ciphertext A (L x R per head) times ciphertext B (R x L per head) */
+/* ------------------------------------------------------------------------- */
+/* Multi-head packing (Sec. 5.1): s = N/2 slots in blocks of L; block
+ * beta = h + Hg * kappa of input ciphertext c holds column k = c Kc + kappa of
+ * A_h (spatial-first) or row k of B_h (reduce-first), Kc = s / (L Hg).
+ * Output ciphertext j (of L/Kc) holds diagonal delta = j Kc + kappa' of
+ * C_h = A_h B_h at block h + Hg kappa', element i = C_h[i][(i + delta) mod L].
+ * Schedule (Sec. 5.1 steps 1-3, baby-step giant-step of App. C.1), with
+ * b1s1 | Kc and b1s2 | L, G1 = Kc/b1s1, G2 = L/b1s2:
+ *   1. B'_c = Rescale( sum_{g1} Rot^{g1 b1s1}( sum_{b0} m1lo(g1,b0) Rot^{b0}(B_c)
+ *                                                + m1hi(g1,b0) Rot^{b0-L}(B_c) ) )
+ *      -- block kappa = g1 b1s1 + b0 of B'_c holds B[k][(i + kappa) mod L];
+ *   2. for t = g b1s2 + b:
+ *      V_c = Rescale( m2lo(g,b) Rot^{b}(B'_c) + m2hi(g,b) Rot^{b-L}(B'_c) ),
+ *      W_t = Rescale( Relin( sum_c Rot^{-g b1s2}(A_c) (x) V_c ) )
+ *      -- Rot^{g b1s2}(W_t) would hold diagonal (t + kappa) mod L at block kappa;
+ *   3. C_j = Rescale( sum_t m3(t, j) Rot^{g b1s2 - (t mod Kc) Hg L}(W_t) ).
+ * Masks (0/1 slot vectors, encoded at scale q_level of the level they are
+ * applied at): m1lo(g1,b0) = Rot^{-g1 b1s1}([kappa(slot) = g1 b1s1 + b0 and
+ * i < L - kappa]), m1hi likewise with i >= L - kappa; m2lo(g,b) =
+ * Rot^{-g b1s2}([i < L - t]), m2hi with i >= L - t; m3(t, j) = [the block that
+ * lands at kappa' comes from kappa = (kappa' - t) mod Kc and carries diagonal
+ * (t + kappa) mod L in output j].  Depth 4 (two mask levels, the tensor, the
+ * routing masks). */
+static int slot_kappa(uint32_t slot, uint32_t L, uint32_t Hg) { return (int)((slot / L) / Hg); }
+
+static void drop_limbs(const orc_params* p, const uint64_t* ct, uint32_t from_level, uint32_t to_level,
+                       uint32_t npolys, uint64_t* out)
+{
+    const uint32_t N = p->N;
+    for (uint32_t poly = 0; poly < npolys; poly++)
+        memcpy(out + (size_t)poly * (to_level + 1) * N, ct + (size_t)poly * (from_level + 1) * N,
+               sizeof(uint64_t) * (to_level + 1) * N);
+}
+
+/* z[slot] = mask value of slot (slot - shift) mod s, i.e. Rot^{-shift} of the
+ * unrotated mask; returns whether the mask has any nonzero entry */
+static int build_mask(double* z, uint32_t s, int64_t shift, int (*pred)(uint32_t, const int64_t*), const int64_t* args)
+{
+    int any = 0;
+    for (uint32_t slot = 0; slot < s; slot++) {
+        uint32_t src = (uint32_t)((((int64_t)slot - shift) % (int64_t)s + s) % s);
+        z[slot] = pred(src, args) ? 1.0 : 0.0;
+        any |= z[slot] != 0.0;
+    }
+    return any;
+}
+
+/* args: {L, Hg, kappa, hi} */
+static int pred_m1(uint32_t slot, const int64_t* a)
+{
+    uint32_t L = (uint32_t)a[0], Hg = (uint32_t)a[1];
+    int64_t kappa = a[2];
+    int64_t i = slot % L;
+    if (slot_kappa(slot, L, Hg) != kappa) return 0;
+    return a[3] ? (i >= (int64_t)L - kappa) : (i < (int64_t)L - kappa);
+}
+/* args: {L, t, hi} */
+static int pred_m2(uint32_t slot, const int64_t* a)
+{
+    int64_t L = a[0], t = a[1], i = slot % L;
+    return a[2] ? (i >= L - t) : (i < L - t);
+}
+/* args: {L, Hg, Kc, t, j} */
+static int pred_m3(uint32_t slot, const int64_t* a)
+{
+    int64_t L = a[0], Hg = a[1], Kc = a[2], t = a[3], j = a[4];
+    int64_t kp = (slot / L) / Hg;
+    int64_t kappa = ((kp - t) % Kc + Kc) % Kc;
+    int64_t delta = (t + kappa) % L;
+    return delta / Kc == j;
+}
+
+uint32_t orc_cc_num_rotations(uint32_t n_c, uint32_t L, uint32_t Kc, uint32_t b1s1, uint32_t b1s2)
+{
+    uint32_t G1 = Kc / b1s1, G2 = L / b1s2;
+    uint32_t s1 = (b1s1 - 1) + (G1 > 1 ? b1s1 : b1s1 - 1) + (G1 - 1);
+    uint32_t s2 = (b1s2 - 1) + b1s2 + (G2 - 1);
+    return n_c * (s1 + s2) + (L - 1);
+}
+
+/* acc += ct (x) encode(mask); skipped when the mask is zero */
+static int mac_mask(const orc_params* p, uint64_t* acc, const uint64_t* ct, uint32_t level, double* z,
+                    uint64_t* pt, uint64_t* prod)
+{
+    const uint32_t s = p->N / 2;
+    if (orc_encode(p, z, s, level, (double)p->prime[level], pt)) return -3;
+    orc_mul_plain(p, ct, pt, level, prod);
+    ct_add_inplace(p, acc, prod, level, 2);
+    return 0;
+}
+
+int orc_matmul_cc(const orc_params* p, const orc_galois_set* gk, const uint64_t* relin_ksk, const uint64_t* A,
+                  const uint64_t* B, uint32_t n_c, uint32_t level, uint32_t L, uint32_t Hg, uint32_t b1s1,
+                  uint32_t b1s2, uint64_t* C)
+{
+    const uint32_t N = p->N, s = N / 2;
+    if (level < 4 || L == 0 || Hg == 0 || s % (L * Hg)) return -1;
+    const uint32_t Kc = s / (L * Hg);
+    if (Kc == 0 || L % Kc || b1s1 == 0 || Kc % b1s1 || b1s2 == 0 || L % b1s2) return -1;
+    const uint32_t G1 = Kc / b1s1, G2 = L / b1s2, nout = L / Kc;
+    const uint32_t l0 = level, l1 = level - 1, l2 = level - 2, l3 = level - 3;
+    const size_t w0 = (size_t)2 * (l0 + 1) * N, w1 = (size_t)2 * (l1 + 1) * N, w2 = (size_t)2 * (l2 + 1) * N;
+    const size_t w3 = (size_t)2 * (l3 + 1) * N;
+    double* z = malloc(sizeof(double) * s);
+    uint64_t* pt = malloc(sizeof(uint64_t) * (l0 + 1) * N);
+    uint64_t* prod = malloc(sizeof(uint64_t) * w0);
+    uint64_t* tmp = malloc(sizeof(uint64_t) * w0);
+    uint64_t* Bp = calloc((size_t)n_c * w1, sizeof(uint64_t));
+    uint64_t* W = calloc((size_t)L * w3, sizeof(uint64_t));
+    int rc = 0;
+#define ROT(dst, src, lv, r)                                                  \
+    do {                                                                      \
+        const uint64_t* key_ = find_galois(p, gk, (int32_t)(r));              \
+        if (!key_) { rc = -2; goto done; }                                    \
+        orc_rotate(p, (src), (lv), (int32_t)(r), key_, (dst));                \
+    } while (0)
+
+    /* step 1 */
+    {
+        uint64_t* lo = malloc(sizeof(uint64_t) * w0 * b1s1);
+        uint64_t* hi = malloc(sizeof(uint64_t) * w0 * b1s1);
+        uint64_t* acc = malloc(sizeof(uint64_t) * w0);
+        uint64_t* inner = malloc(sizeof(uint64_t) * w0);
+        for (uint32_t c = 0; c < n_c && !rc; c++) {
+            const uint64_t* Bc = B + (size_t)c * w0;
+            for (uint32_t b0 = 0; b0 < b1s1; b0++) {
+                if (b0 == 0) memcpy(lo, Bc, sizeof(uint64_t) * w0);
+                else ROT(lo + (size_t)b0 * w0, Bc, l0, b0);
+                if (b0 > 0 || G1 > 1) ROT(hi + (size_t)b0 * w0, Bc, l0, (int32_t)b0 - (int32_t)L);
+            }
+            memset(acc, 0, sizeof(uint64_t) * w0);
+            for (uint32_t g1 = 0; g1 < G1 && !rc; g1++) {
+                memset(inner, 0, sizeof(uint64_t) * w0);
+                for (uint32_t b0 = 0; b0 < b1s1 && !rc; b0++) {
+                    int64_t args[4] = {L, Hg, (int64_t)(g1 * b1s1 + b0), 0};
+                    if (build_mask(z, s, (int64_t)g1 * b1s1, pred_m1, args))
+                        rc = mac_mask(p, inner, lo + (size_t)b0 * w0, l0, z, pt, prod);
+                    args[3] = 1;
+                    if (!rc && build_mask(z, s, (int64_t)g1 * b1s1, pred_m1, args))
+                        rc = mac_mask(p, inner, hi + (size_t)b0 * w0, l0, z, pt, prod);
+                }
+                if (rc) break;
+                if (g1 == 0) ct_add_inplace(p, acc, inner, l0, 2);
+                else {
+                    ROT(tmp, inner, l0, g1 * b1s1);
+                    ct_add_inplace(p, acc, tmp, l0, 2);
+                }
+            }
+            if (!rc) orc_rescale(p, acc, l0, 2, Bp + (size_t)c * w1);
+        }
+        free(lo); free(hi); free(acc); free(inner);
+    }
+    if (rc) goto done;
+
+    /* step 2 */
+    {
+        const size_t w2_3 = (size_t)3 * (l2 + 1) * N;
+        uint64_t* U = calloc((size_t)L * w2_3, sizeof(uint64_t));
+        uint64_t* blo = malloc(sizeof(uint64_t) * w1 * b1s2);
+        uint64_t* bhi = malloc(sizeof(uint64_t) * w1 * b1s2);
+        uint64_t* Ag = malloc(sizeof(uint64_t) * w2 * G2);
+        uint64_t* A2 = malloc(sizeof(uint64_t) * w2);
+        uint64_t* vacc = malloc(sizeof(uint64_t) * w1);
+        uint64_t* V = malloc(sizeof(uint64_t) * w2);
+        uint64_t* T3 = malloc(sizeof(uint64_t) * w2_3);
+        for (uint32_t c = 0; c < n_c && !rc; c++) {
+            const uint64_t* Bc = Bp + (size_t)c * w1;
+            for (uint32_t b = 0; b < b1s2; b++) {
+                if (b == 0) memcpy(blo, Bc, sizeof(uint64_t) * w1);
+                else ROT(blo + (size_t)b * w1, Bc, l1, b);
+                if (b > 0 || G2 > 1) ROT(bhi + (size_t)b * w1, Bc, l1, (int32_t)b - (int32_t)L);
+            }
+            drop_limbs(p, A + (size_t)c * w0, l0, l2, 2, A2);
+            for (uint32_t g = 0; g < G2; g++) {
+                if (g == 0) memcpy(Ag, A2, sizeof(uint64_t) * w2);
+                else ROT(Ag + (size_t)g * w2, A2, l2, -(int32_t)(g * b1s2));
+            }
+            for (uint32_t g = 0; g < G2 && !rc; g++) {
+                for (uint32_t b = 0; b < b1s2 && !rc; b++) {
+                    const uint32_t t = g * b1s2 + b;
+                    memset(vacc, 0, sizeof(uint64_t) * w1);
+                    int64_t args[3] = {L, t, 0};
+                    int used = 0;
+                    if (build_mask(z, s, (int64_t)g * b1s2, pred_m2, args)) {
+                        rc = mac_mask(p, vacc, blo + (size_t)b * w1, l1, z, pt, prod);
+                        used = 1;
+                    }
+                    args[2] = 1;
+                    if (!rc && build_mask(z, s, (int64_t)g * b1s2, pred_m2, args)) {
+                        rc = mac_mask(p, vacc, bhi + (size_t)b * w1, l1, z, pt, prod);
+                        used = 1;
+                    }
+                    if (rc || !used) continue;
+                    orc_rescale(p, vacc, l1, 2, V);
+                    orc_tensor(p, Ag + (size_t)g * w2, V, l2, T3);
+                    uint64_t* Ut = U + (size_t)t * w2_3;
+                    for (uint32_t poly = 0; poly < 3; poly++)
+                        orc_add(p, Ut + (size_t)poly * (l2 + 1) * N, T3 + (size_t)poly * (l2 + 1) * N, l2 + 1,
+                                Ut + (size_t)poly * (l2 + 1) * N);
+                }
+            }
+        }
+        for (uint32_t t = 0; t < L && !rc; t++) {
+            uint64_t* R2 = malloc(sizeof(uint64_t) * w2);
+            orc_relinearize(p, U + (size_t)t * w2_3, l2, relin_ksk, R2);
+            orc_rescale(p, R2, l2, 2, W + (size_t)t * w3);
+            free(R2);
+        }
+        free(U); free(blo); free(bhi); free(Ag); free(A2); free(vacc); free(V); free(T3);
+    }
+    if (rc) goto done;
+
+    /* step 3 */
+    {
+        uint64_t* Cacc = calloc((size_t)nout * w3, sizeof(uint64_t));
+        uint64_t* Rt = malloc(sizeof(uint64_t) * w3);
+        for (uint32_t t = 0; t < L && !rc; t++) {
+            const uint32_t g = t / b1s2;
+            const int64_t r = (((int64_t)g * b1s2 - (int64_t)(t % Kc) * Hg * L) % (int64_t)s + s) % s;
+            if (r == 0) memcpy(Rt, W + (size_t)t * w3, sizeof(uint64_t) * w3);
+            else ROT(Rt, W + (size_t)t * w3, l3, (int32_t)r);
+            for (uint32_t j = 0; j < nout && !rc; j++) {
+                int64_t args[5] = {L, Hg, Kc, t, j};
+                if (build_mask(z, s, 0, pred_m3, args))
+                    rc = mac_mask(p, Cacc + (size_t)j * w3, Rt, l3, z, pt, prod);
+            }
+        }
+        for (uint32_t j = 0; j < nout && !rc; j++)
+            orc_rescale(p, Cacc + (size_t)j * w3, l3, 2, C + (size_t)j * 2 * l3 * N);
+        free(Cacc); free(Rt);
+    }
+done:
+#undef ROT
+    free(z); free(pt); free(prod); free(tmp); free(Bp); free(W);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------- */
 /* CKKS -> MPC masking (Alg. 1, first two steps; Sec. 6.3)                      */
 /* ------------------------------------------------------------------------- */
 /* The paper's conversion works modulo a single prime q.  The ciphertext is

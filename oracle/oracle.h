@@ -110,6 +110,10 @@ uint32_t orc_cp_num_rotations(uint32_t nX, uint32_t nY, uint32_t b1, uint32_t G)
 int orc_matmul_cp(const orc_params* p, const orc_galois_set* gk, const uint64_t* X, uint32_t nX,
                   uint32_t level, uint32_t m, uint32_t d, const double* W, uint32_t d_out,
                   uint32_t b1, const uint32_t* out_idx, uint32_t n_out, uint64_t* Y);
+uint32_t orc_cc_num_rotations(uint32_t n_c, uint32_t L, uint32_t Kc, uint32_t b1s1, uint32_t b1s2);
+int orc_matmul_cc(const orc_params* p, const orc_galois_set* gk, const uint64_t* relin_ksk, const uint64_t* A,
+                  const uint64_t* B, uint32_t n_c, uint32_t level, uint32_t L, uint32_t Hg, uint32_t b1s1,
+                  uint32_t b1s2, uint64_t* C /* (L/Kc) x 2 x (level-3) x N */);
 void orc_he2mpc(const orc_params* p, const uint64_t* ct, uint32_t level, uint64_t seed,
                 uint32_t nonce, uint64_t* masked /* 2 x N */, uint64_t* p1_share /* N */);
 
