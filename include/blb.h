@@ -51,6 +51,7 @@ typedef struct blb_keys blb_keys;
 typedef struct blb_pt blb_pt;
 typedef struct blb_ct blb_ct;
 typedef struct blb_cp_plan blb_cp_plan;
+typedef struct blb_cc_plan blb_cc_plan;
 
 /* Parameter set.  q_bits[0..nQ) are the bit sizes of the ciphertext primes,
  * p_bits[0..nP) those of the special primes of hybrid key switching; dnum is
@@ -205,6 +206,37 @@ int blb_matmul_cp_plan(blb_ctx* ctx, const blb_keys* keys, const blb_cp_plan* pl
                        blb_ct* const* X, uint32_t nX, blb_ct** Y);
 int blb_matmul_cp(blb_ctx* ctx, const blb_keys* keys, blb_ct* const* X, uint32_t nX, uint32_t m,
                   uint32_t d, const double* W, uint32_t d_out, const blb_sched* sched, blb_ct** Y);
+
+/* ---- matmul_cc: encrypted A_h (L x R) times encrypted B_h (R x L), Hg heads ----
+ * Sec. 5.1 (three steps, multi-head packing) with the baby-step giant-step split
+ * of App. C.1.  Packing: N/2 slots in blocks of L; block h + Hg kappa of input
+ * ciphertext c holds column k = c Kc + kappa of A_h (spatial-first) or row k of
+ * B_h (reduce-first), element i at slot (h + Hg kappa) L + i, Kc = N/2/(L Hg)
+ * (Kc <= L, n_c = ceil(R/Kc) ciphertexts per operand).  Output ciphertext j of
+ * L/Kc holds diagonal delta = j Kc + kappa of C_h at block h + Hg kappa:
+ * element i = C_h[i][(i + delta) mod L] (diagonal packing).
+ * Schedule (both sides of the parity tests implement the same):
+ *   1. pre-rotate row k of block kappa of B by kappa (masks, BSGS split b1s1 | Kc);
+ *   2. for t = g b1s2 + b: V = masks x {Rot^b, Rot^{b-L}}(B'), tensor with
+ *      Rot^{-g b1s2}(A), sum over input ciphertexts, relinearize, rescale;
+ *   3. one rotation Rot^{g b1s2 - (t mod Kc) Hg L} per t, two routing masks.
+ * Depth 4: inputs at `level` (>= 4), outputs at level-4 with scale
+ * scale(A) scale(B) / q_{level-2}.  Needs the relinearization key and the Galois
+ * keys of blb_cc_plan_rotations.  Masks are encoded once per plan. */
+typedef struct {
+    uint32_t b1s1, b1s2; /* 0 = about sqrt(Kc/2), sqrt(L/2) */
+} blb_cc_sched;
+int blb_cc_plan_create(blb_ctx* ctx, uint32_t L, uint32_t Hg, uint32_t R, uint32_t level,
+                       const blb_cc_sched* sched, blb_cc_plan** out);
+void blb_cc_plan_free(blb_cc_plan* plan);
+int blb_cc_plan_info(const blb_cc_plan* plan, uint32_t* n_c, uint32_t* Kc, uint32_t* nout, uint32_t* b1s1,
+                     uint32_t* b1s2, uint64_t* mask_bytes);
+/* Left-rotation amounts the plan needs keys for; out may be NULL to query count. */
+int blb_cc_plan_rotations(const blb_cc_plan* plan, int32_t* out, uint32_t cap, uint32_t* count);
+int blb_matmul_cc_plan(blb_ctx* ctx, const blb_keys* keys, const blb_cc_plan* plan, blb_ct* const* A,
+                       blb_ct* const* B, uint32_t n_in, blb_ct** C /* L/Kc handles */);
+int blb_matmul_cc(blb_ctx* ctx, const blb_keys* keys, blb_ct* const* A, blb_ct* const* B, uint32_t n_in,
+                  uint32_t L, uint32_t R, uint32_t Hg, const blb_cc_sched* sched, blb_ct** C);
 
 /* ---- CKKS -> MPC (Alg. 1 steps 1-2, Sec. 6.3) --------------------------------
  * P1 reduces the ciphertext to level 0, adds a mask r drawn uniformly from

@@ -38,6 +38,10 @@ class _Sched(ctypes.Structure):
     _fields_ = [("b1", _u32)]
 
 
+class _CcSched(ctypes.Structure):
+    _fields_ = [("b1s1", _u32), ("b1s2", _u32)]
+
+
 ALLOC_FN = ctypes.CFUNCTYPE(_vp, ctypes.c_size_t, _vp, _vp)
 FREE_FN = ctypes.CFUNCTYPE(None, _vp, ctypes.c_size_t, _vp, _vp)
 
@@ -78,6 +82,12 @@ SIGNATURES = {
     "blb_cp_plan_info": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "blb_matmul_cp_plan": (ctypes.c_int, [_vp, _vp, _vp, _pp, _u32, _pp]),
     "blb_matmul_cp": (ctypes.c_int, [_vp, _vp, _pp, _u32, _u32, _u32, _vp, _u32, ctypes.POINTER(_Sched), _pp]),
+    "blb_cc_plan_create": (ctypes.c_int, [_vp, _u32, _u32, _u32, _u32, ctypes.POINTER(_CcSched), _pp]),
+    "blb_cc_plan_free": (None, [_vp]),
+    "blb_cc_plan_info": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "blb_cc_plan_rotations": (ctypes.c_int, [_vp, _vp, _u32, _vp]),
+    "blb_matmul_cc_plan": (ctypes.c_int, [_vp, _vp, _vp, _pp, _pp, _u32, _pp]),
+    "blb_matmul_cc": (ctypes.c_int, [_vp, _vp, _pp, _pp, _u32, _u32, _u32, _u32, ctypes.POINTER(_CcSched), _pp]),
     "blb_he2mpc": (ctypes.c_int, [_vp, _vp, _vp, _u64, _pp, _vp]),
     "blb_ntt": (ctypes.c_int, [_vp, _vp, _u32, _vp, ctypes.c_int]),
     "blb_kernel_launches": (_u64, []),
@@ -212,6 +222,23 @@ class CpPlan(_Handle):
         v = [_u32() for _ in range(4)] + [_u64()]
         _check(lib().blb_cp_plan_info(self.h, *[ctypes.byref(x) for x in v]))
         return dict(nX=v[0].value, nY=v[1].value, b1=v[2].value, G=v[3].value, plaintext_bytes=v[4].value)
+
+
+class CcPlan(_Handle):
+    _free = "blb_cc_plan_free"
+
+    def info(self):
+        v = [_u32() for _ in range(5)] + [_u64()]
+        _check(lib().blb_cc_plan_info(self.h, *[ctypes.byref(x) for x in v]))
+        return dict(n_c=v[0].value, Kc=v[1].value, nout=v[2].value, b1s1=v[3].value, b1s2=v[4].value,
+                    mask_bytes=v[5].value)
+
+    def rotations(self):
+        n = _u32()
+        _check(lib().blb_cc_plan_rotations(self.h, None, 0, ctypes.byref(n)))
+        out = (_i32 * max(1, n.value))()
+        _check(lib().blb_cc_plan_rotations(self.h, out, n.value, ctypes.byref(n)))
+        return list(out)[:n.value]
 
 
 class Context:
@@ -364,6 +391,19 @@ class Context:
         s = _Sched(b1)
         _check(lib().blb_matmul_cp(self.h, keys.h, xs, len(X), m, d, _ptr(W), d_out, ctypes.byref(s), ys))
         return [Ciphertext(self, y) for y in ys]
+
+    # matmul_cc
+    def cc_plan(self, L, Hg, R, level, b1s1=0, b1s2=0):
+        s = _CcSched(b1s1, b1s2)
+        return self._new(CcPlan, lib().blb_cc_plan_create, L, Hg, R, level, ctypes.byref(s))
+
+    def matmul_cc_plan(self, keys, plan, A, B):
+        info = plan.info()
+        a = (ctypes.c_void_p * len(A))(*[x.h for x in A])
+        b = (ctypes.c_void_p * len(B))(*[x.h for x in B])
+        out = (ctypes.c_void_p * info["nout"])()
+        _check(lib().blb_matmul_cc_plan(self.h, keys.h, plan.h, a, b, len(A), out))
+        return [Ciphertext(self, y) for y in out]
 
     # CKKS -> MPC
     def he2mpc(self, keys, ct, nonce, share_out=None):

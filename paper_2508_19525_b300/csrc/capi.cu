@@ -144,6 +144,11 @@ __global__ void __launch_bounds__(256) k_cp_mac_tile(uint64_t* __restrict__ T, c
 
 }  // namespace
 
+int new_ciphertext(blb_ctx* c, uint32_t level, uint32_t npolys, double scale, blb_ct** out)
+{
+    return new_ct(c, level, npolys, scale, out);
+}
+
 int launch_cp_mac(blb_ctx* c, const blb_cp_plan* plan, const uint64_t* baby, uint64_t* T)
 {
     const uint32_t n = plan->level + 1;

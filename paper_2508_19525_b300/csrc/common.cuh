@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cmath>
 #include <string>
 #include <vector>
 
@@ -288,6 +289,9 @@ int launch_mul_const_rows(blb_ctx* ctx, uint64_t* out, const uint64_t* a, uint32
 int launch_automorph_ntt(blb_ctx* ctx, uint64_t* out, const uint64_t* in, uint32_t rows, uint64_t g);
 int launch_signed_to_rows(blb_ctx* ctx, uint64_t* out, const int64_t* in, uint32_t rows, const LimbMap& map);
 int launch_rescale(blb_ctx* ctx, uint64_t* out, const uint64_t* in, uint32_t level, uint32_t npolys);
+int launch_rescale_stack(blb_ctx* ctx, uint64_t* out, const uint64_t* in, uint32_t level, uint32_t npolys);
+// new ciphertext object (retains the context)
+int new_ciphertext(blb_ctx* ctx, uint32_t level, uint32_t npolys, double scale, blb_ct** out);
 int launch_tensor(blb_ctx* ctx, uint64_t* out, const uint64_t* a, const uint64_t* b, uint32_t level);
 
 // sampling: counter (coefficient, j, obj, purpose), key = seed

@@ -287,28 +287,49 @@ int launch_sample_uniform(blb_ctx* ctx, uint64_t* out, uint32_t rows, const Limb
 }
 
 // in: npolys x (level+1) rows; out: npolys x level rows (may not alias in).
-// Uses the operation scratch region: npolys rows (last limb) + npolys*level rows.
-int launch_rescale(blb_ctx* ctx, uint64_t* out, const uint64_t* in, uint32_t level, uint32_t npolys)
+// Temporaries: npolys rows (last limb) + npolys*level rows, in the operation
+// scratch when they fit, else in a temporary allocation.
+int launch_rescale_stack(blb_ctx* ctx, uint64_t* out, const uint64_t* in, uint32_t level, uint32_t npolys)
 {
     if (level == 0) return blb_fail(BLB_ERR_LEVEL, "rescale at level 0");
     const uint32_t N = ctx->N;
+    const size_t need = (size_t)npolys * (level + 1) * N;
+    const size_t have = ctx->scratch_words - ctx->ks_words();
+    uint64_t* tmp = nullptr;
     uint64_t* last = ctx->op_scratch();
-    uint64_t* T = last + (size_t)npolys * N;
-    k_copy_last<<<grid_rows(N, npolys), kT, 0, ctx->stream>>>(last, in, N, level);
-    BLB_LAUNCHED();
-    BLB_TRY(ntt_inverse(ctx, last, npolys, ctx->qmap(1, level)));
-    const uint32_t rows = npolys * level;
-    k_lift_last<<<grid_rows(N, rows), kT, 0, ctx->stream>>>(T, last, ctx->d_q, N, level);
-    BLB_LAUNCHED();
-    BLB_TRY(ntt_forward(ctx, T, rows, ctx->qmap(level)));
-    RescaleConsts rc{};
-    for (uint32_t i = 0; i < level; i++) {
-        rc.inv[i] = ctx->ql_inv[level][i];
-        rc.inv_sh[i] = shoup_companion(rc.inv[i], ctx->q[i]);
+    if (need > have) {
+        tmp = (uint64_t*)dev_alloc(ctx, need * 8);
+        if (!tmp) return blb_fail(BLB_ERR_OOM, "rescale temporary");
+        last = tmp;
     }
-    k_rescale_finish<<<grid_rows(N, rows), kT, 0, ctx->stream>>>(out, in, T, ctx->d_q, N, level, rc);
-    BLB_LAUNCHED();
-    return BLB_OK;
+    uint64_t* T = last + (size_t)npolys * N;
+    int rc = BLB_OK;
+    do {
+        k_copy_last<<<grid_rows(N, npolys), kT, 0, ctx->stream>>>(last, in, N, level);
+        if (cudaGetLastError() != cudaSuccess) { rc = blb_fail(BLB_ERR_CUDA, "rescale launch failed"); break; }
+        blb_count_launch();
+        if ((rc = ntt_inverse(ctx, last, npolys, ctx->qmap(1, level)))) break;
+        const uint32_t rows = npolys * level;
+        k_lift_last<<<grid_rows(N, rows), kT, 0, ctx->stream>>>(T, last, ctx->d_q, N, level);
+        if (cudaGetLastError() != cudaSuccess) { rc = blb_fail(BLB_ERR_CUDA, "rescale launch failed"); break; }
+        blb_count_launch();
+        if ((rc = ntt_forward(ctx, T, rows, ctx->qmap(level)))) break;
+        RescaleConsts rcst{};
+        for (uint32_t i = 0; i < level; i++) {
+            rcst.inv[i] = ctx->ql_inv[level][i];
+            rcst.inv_sh[i] = shoup_companion(rcst.inv[i], ctx->q[i]);
+        }
+        k_rescale_finish<<<grid_rows(N, rows), kT, 0, ctx->stream>>>(out, in, T, ctx->d_q, N, level, rcst);
+        if (cudaGetLastError() != cudaSuccess) { rc = blb_fail(BLB_ERR_CUDA, "rescale launch failed"); break; }
+        blb_count_launch();
+    } while (0);
+    if (tmp) dev_free(ctx, tmp, need * 8);
+    return rc;
+}
+
+int launch_rescale(blb_ctx* ctx, uint64_t* out, const uint64_t* in, uint32_t level, uint32_t npolys)
+{
+    return launch_rescale_stack(ctx, out, in, level, npolys);
 }
 
 int launch_tensor(blb_ctx* ctx, uint64_t* out, const uint64_t* a, const uint64_t* b, uint32_t level)

@@ -1,0 +1,614 @@
+// matmul_cc.cu -- ciphertext x ciphertext matrix product of Sec. 5.1 (three
+// steps, multi-head packing, baby-step giant-step of App. C.1).
+//
+// Packing: s = N/2 slots in blocks of L; block beta = h + Hg kappa of input
+// ciphertext c holds column k = c Kc + kappa of A_h (spatial-first) or row k
+// of B_h (reduce-first), element i at slot beta L + i, Kc = s / (L Hg).  Output
+// ciphertext j (of L/Kc) holds diagonal delta = j Kc + kappa' of C_h = A_h B_h at
+// block h + Hg kappa', element i = C_h[i][(i + delta) mod L].
+//
+// Schedule (b1s1 | Kc, b1s2 | L, G1 = Kc/b1s1, G2 = L/b1s2):
+//   1. B'_c = Rescale( sum_{g1} Rot^{g1 b1s1}( sum_{b0} m1lo(g1,b0) Rot^{b0}(B_c)
+//                                               + m1hi(g1,b0) Rot^{b0-L}(B_c) ) )
+//      (block kappa of B'_c holds B[k][(i + kappa) mod L]);
+//   2. for t = g b1s2 + b: V_{c,t} = Rescale( m2lo(g,b) Rot^{b}(B'_c) + m2hi(g,b) Rot^{b-L}(B'_c) ),
+//      W_t = Rescale( Relin( sum_c Rot^{-g b1s2}(A_c) (x) V_{c,t} ) );
+//   3. C_j = Rescale( sum_t m3(t,j) Rot^{g b1s2 - (t mod Kc) Hg L}(W_t) ).
+// Masks are 0/1 slot vectors encoded at scale q_l of the level they are applied
+// at (so masking and its rescale leave the scale unchanged):
+//   m1lo(g1,b0) = Rot^{-g1 b1s1}[kappa(slot) = g1 b1s1 + b0, i < L - kappa]   (hi: i >= L - kappa)
+//   m2lo(g,b)   = Rot^{-g b1s2}[i < L - t]                                    (hi: i >= L - t)
+//   m3(t,j)     = [the block landing at kappa' comes from kappa = (kappa' - t) mod Kc and
+//                  carries diagonal (t + kappa) mod L of output j]
+// Depth 4: step-1 masks, step-2 masks, the tensor product, step-3 masks.
+#include <algorithm>
+#include <cstring>
+
+#include "common.cuh"
+
+struct blb_cc_plan {
+    blb_ctx* ctx;
+    uint32_t L, Hg, R, level, Kc, n_c, nout, b1s1, b1s2, G1, G2;
+    uint64_t* d_m1;  // [G1][b1s1][2] at level, (level+1) x N each
+    uint64_t* d_m2;  // [G2][b1s2][2] at level-1
+    uint64_t* d_m3;  // [L][nout] at level-3
+    std::vector<uint8_t> nz1, nz2, nz3;
+    size_t bytes;
+};
+
+namespace {
+constexpr int kT = 256;
+
+struct MaskSpec {
+    uint32_t L, Hg, Kc, s, b1s1, b1s2, nout;
+};
+
+// mask value at slot (before the giant-step rotation) for mask id of `type`
+__host__ __device__ inline bool mask_pred(const MaskSpec& m, int type, uint32_t id, uint32_t slot)
+{
+    const uint32_t i = slot % m.L, kap = (slot / m.L) / m.Hg;
+    if (type == 1) {  // id = (g1 b1s1 + b0) * 2 + hi
+        const uint32_t kappa = id >> 1, hi = id & 1;
+        if (kap != kappa) return false;
+        return hi ? i >= m.L - kappa : i < m.L - kappa;
+    }
+    if (type == 2) {  // id = t * 2 + hi
+        const uint32_t t = id >> 1, hi = id & 1;
+        return hi ? i >= m.L - t : i < m.L - t;
+    }
+    // type 3: id = t * nout + j
+    const uint32_t t = id / m.nout, j = id % m.nout;
+    const uint32_t kappa = (uint32_t)(((int64_t)kap - (int64_t)t) % (int64_t)m.Kc + m.Kc) % m.Kc;
+    const uint32_t delta = (t + kappa) % m.L;
+    return delta / m.Kc == j;
+}
+
+__host__ __device__ inline uint32_t mask_shift(const MaskSpec& m, int type, uint32_t id)
+{
+    if (type == 1) return ((id >> 1) / m.b1s1) * m.b1s1;  // g1 b1s1
+    if (type == 2) return ((id >> 1) / m.b1s2) * m.b1s2;  // g b1s2
+    return 0;
+}
+
+// z[m][slot] = mask(type, first + m) at slot (slot - shift) mod s
+__global__ void k_cc_masks(double* __restrict__ z, MaskSpec spec, int type, uint32_t first)
+{
+    const uint32_t slot = blockIdx.x * blockDim.x + threadIdx.x, m = blockIdx.y;
+    if (slot >= spec.s) return;
+    const uint32_t id = first + m;
+    const uint32_t src = (slot + spec.s - mask_shift(spec, type, id) % spec.s) % spec.s;
+    z[(size_t)m * spec.s + slot] = mask_pred(spec, type, id, src) ? 1.0 : 0.0;
+}
+
+// out[o] = sum_{t in [start[o], start[o+1])} ct[t] (.) pt[t]  (2 polynomials, n limbs)
+struct LcTerm {
+    const uint64_t* ct;
+    const uint64_t* pt;
+};
+__global__ void k_lincomb(uint64_t* __restrict__ out, const uint32_t* __restrict__ start,
+                          const LcTerm* __restrict__ terms, uint32_t n, uint32_t N, const uint64_t* __restrict__ qs,
+                          const uint64_t* __restrict__ bar)
+{
+    const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x, i = blockIdx.y, o = blockIdx.z;
+    if (c >= N) return;
+    const uint64_t q = qs[i], r0 = bar[2 * i], r1 = bar[2 * i + 1];
+    const size_t nN = (size_t)n * N, off = (size_t)i * N + c;
+    acc128 a0{0, 0}, a1{0, 0};
+    const uint32_t t0 = start[o], t1 = start[o + 1];
+    for (uint32_t t = t0; t < t1; t++) {
+        const uint64_t w = terms[t].pt[off];
+        mad128(a0, terms[t].ct[off], w);
+        mad128(a1, terms[t].ct[nN + off], w);
+        if (((t - t0) & 7) == 7) {
+            a0 = acc128{barrett128(a0.lo, a0.hi, q, r0, r1), 0};
+            a1 = acc128{barrett128(a1.lo, a1.hi, q, r0, r1), 0};
+        }
+    }
+    uint64_t* dst = out + (size_t)o * 2 * nN + off;
+    dst[0] = barrett128(a0.lo, a0.hi, q, r0, r1);
+    dst[nN] = barrett128(a1.lo, a1.hi, q, r0, r1);
+}
+
+// U[t] = sum_c a[t][c] (x) b[t][c]: (a0 b0, a0 b1 + a1 b0, a1 b1), n limbs
+struct TensorPair {
+    const uint64_t* a;
+    const uint64_t* b;
+};
+__global__ void k_tensor_acc(uint64_t* __restrict__ U, const TensorPair* __restrict__ pairs, uint32_t n_c,
+                             uint32_t n, uint32_t N, const uint64_t* __restrict__ qs,
+                             const uint64_t* __restrict__ bar)
+{
+    const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x, i = blockIdx.y, t = blockIdx.z;
+    if (c >= N) return;
+    const uint64_t q = qs[i], r0 = bar[2 * i], r1 = bar[2 * i + 1];
+    const size_t nN = (size_t)n * N, off = (size_t)i * N + c;
+    acc128 x0{0, 0}, x1{0, 0}, x2{0, 0};
+    for (uint32_t k = 0; k < n_c; k++) {
+        const TensorPair p = pairs[(size_t)t * n_c + k];
+        const uint64_t a0 = p.a[off], a1 = p.a[nN + off], b0 = p.b[off], b1 = p.b[nN + off];
+        mad128(x0, a0, b0);
+        mad128(x1, a0, b1);
+        mad128(x1, a1, b0);
+        mad128(x2, a1, b1);
+        if ((k & 7) == 7) {
+            x0 = acc128{barrett128(x0.lo, x0.hi, q, r0, r1), 0};
+            x1 = acc128{barrett128(x1.lo, x1.hi, q, r0, r1), 0};
+            x2 = acc128{barrett128(x2.lo, x2.hi, q, r0, r1), 0};
+        }
+    }
+    uint64_t* dst = U + (size_t)t * 3 * nN + off;
+    dst[0] = barrett128(x0.lo, x0.hi, q, r0, r1);
+    dst[nN] = barrett128(x1.lo, x1.hi, q, r0, r1);
+    dst[2 * nN] = barrett128(x2.lo, x2.hi, q, r0, r1);
+}
+
+// copy polynomials from `from` limbs per polynomial to `to` limbs (drop the top limbs)
+__global__ void k_drop(uint64_t* __restrict__ out, const uint64_t* __restrict__ in, uint32_t from, uint32_t to,
+                       uint32_t N)
+{
+    const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x, i = blockIdx.y, poly = blockIdx.z;
+    if (c >= N) return;
+    out[((size_t)poly * to + i) * N + c] = in[((size_t)poly * from + i) * N + c];
+}
+
+template <class T>
+int upload_table(blb_ctx* c, const std::vector<T>& v, T** d, size_t* bytes)
+{
+    *bytes = std::max<size_t>(v.size() * sizeof(T), 16);
+    *d = (T*)dev_alloc(c, *bytes);
+    if (!*d) return blb_fail(BLB_ERR_OOM, "table allocation failed");
+    BLB_CUDA(cudaMemcpyAsync(*d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, c->stream));
+    return BLB_OK;
+}
+
+// Device buffer holding `count` ciphertexts of 2 polynomials at `level`
+struct Stack {
+    blb_ctx* c = nullptr;
+    uint64_t* d = nullptr;
+    size_t bytes = 0, words_per = 0;
+    int alloc(blb_ctx* ctx, uint32_t count, uint32_t level, uint32_t npolys = 2)
+    {
+        c = ctx;
+        words_per = (size_t)npolys * (level + 1) * ctx->N;
+        bytes = std::max<size_t>((size_t)count * words_per * 8, 16);
+        d = (uint64_t*)dev_alloc(ctx, bytes);
+        return d ? BLB_OK : blb_fail(BLB_ERR_OOM, "matmul_cc workspace");
+    }
+    uint64_t* at(size_t k) const { return d + k * words_per; }
+    ~Stack()
+    {
+        if (d) dev_free(c, d, bytes);
+    }
+};
+
+}  // namespace
+
+// Rescale `count` ciphertexts of npolys polynomials stored back to back (in:
+// level l, out: level l-1).
+static int rescale_many(blb_ctx* c, uint64_t* out, const uint64_t* in, uint32_t level, uint32_t count,
+                        uint32_t npolys)
+{
+    // the rescale kernels treat count * npolys polynomials as one stack
+    return launch_rescale_stack(c, out, in, level, count * npolys);
+}
+
+// ---------------------------------------------------------------------------
+// plan
+// ---------------------------------------------------------------------------
+static MaskSpec spec_of(const blb_cc_plan* P)
+{
+    return MaskSpec{P->L, P->Hg, P->Kc, P->ctx->N / 2, P->b1s1, P->b1s2, P->nout};
+}
+
+static int encode_masks(blb_ctx* c, const MaskSpec& spec, int type, uint32_t count, uint32_t level, uint64_t* out)
+{
+    const uint32_t s = spec.s, n = level + 1;
+    const uint32_t chunk = std::max<uint32_t>(1, std::min<uint32_t>(count, (uint32_t)((32ull << 20) / ((uint64_t)s * 8))));
+    double* z = (double*)dev_alloc(c, (size_t)chunk * s * 8);
+    if (!z) return blb_fail(BLB_ERR_OOM, "mask buffer");
+    int rc = BLB_OK;
+    for (uint32_t first = 0; !rc && first < count; first += chunk) {
+        const uint32_t cnt = std::min(chunk, count - first);
+        k_cc_masks<<<dim3((s + kT - 1) / kT, cnt), kT, 0, c->stream>>>(z, spec, type, first);
+        if (cudaGetLastError() != cudaSuccess) rc = blb_fail(BLB_ERR_CUDA, "mask kernel launch failed");
+        else {
+            blb_count_launch();
+            rc = encode_slots(c, z, cnt, s, level, (double)c->q[level], out + (size_t)first * n * c->N);
+        }
+    }
+    dev_free(c, z, (size_t)chunk * s * 8);
+    return rc;
+}
+
+extern "C" int blb_cc_plan_create(blb_ctx* c, uint32_t L, uint32_t Hg, uint32_t R, uint32_t level,
+                                  const blb_cc_sched* sched, blb_cc_plan** out)
+{
+    if (!c || !out) return blb_fail(BLB_ERR_ARG, "null argument");
+    *out = nullptr;
+    const uint32_t s = c->N / 2;
+    if (L == 0 || Hg == 0 || (L & (L - 1)) || (Hg & (Hg - 1)) || s % (L * Hg))
+        return blb_fail(BLB_ERR_ARG, "L and Hg must be powers of two with L Hg dividing N/2");
+    const uint32_t Kc = s / (L * Hg);
+    if (Kc == 0 || Kc > L) return blb_fail(BLB_ERR_ARG, "need Kc = N/2/(L Hg) <= L");
+    if (R == 0 || R > L) return blb_fail(BLB_ERR_ARG, "R must be in [1, L]");
+    if (level < 4 || level >= c->nQ) return blb_fail(BLB_ERR_LEVEL, "matmul_cc needs 4 levels");
+    uint32_t b1s1 = sched ? sched->b1s1 : 0, b1s2 = sched ? sched->b1s2 : 0;
+    if (b1s1 == 0) {
+        b1s1 = 1;
+        while (2 * b1s1 * b1s1 * 2 <= Kc) b1s1 <<= 1;  // about sqrt(Kc/2)
+    }
+    if (b1s2 == 0) {
+        b1s2 = 1;
+        while (2 * b1s2 * b1s2 * 2 <= L) b1s2 <<= 1;
+    }
+    if (Kc % b1s1 || L % b1s2) return blb_fail(BLB_ERR_ARG, "b1s1 must divide Kc and b1s2 must divide L");
+    blb_cc_plan* P = new blb_cc_plan();
+    P->ctx = c;
+    ctx_retain(c);
+    P->L = L;
+    P->Hg = Hg;
+    P->R = R;
+    P->level = level;
+    P->Kc = Kc;
+    P->n_c = (R + Kc - 1) / Kc;
+    P->nout = L / Kc;
+    P->b1s1 = b1s1;
+    P->b1s2 = b1s2;
+    P->G1 = Kc / b1s1;
+    P->G2 = L / b1s2;
+    P->d_m1 = P->d_m2 = P->d_m3 = nullptr;
+    const uint32_t N = c->N;
+    const size_t n1 = 2ull * Kc, n2 = 2ull * L, n3 = (size_t)L * P->nout;
+    const size_t b1 = n1 * (level + 1) * N * 8, b2 = n2 * level * N * 8, b3 = n3 * (level - 2) * N * 8;
+    P->bytes = b1 + b2 + b3;
+    P->d_m1 = (uint64_t*)dev_alloc(c, b1);
+    P->d_m2 = (uint64_t*)dev_alloc(c, b2);
+    P->d_m3 = (uint64_t*)dev_alloc(c, b3);
+    int rc = (P->d_m1 && P->d_m2 && P->d_m3) ? BLB_OK : blb_fail(BLB_ERR_OOM, "mask plaintexts do not fit");
+    const MaskSpec spec = spec_of(P);
+    // which masks are non-zero (host evaluation of the same predicates)
+    auto nonzero = [&](int type, uint32_t id) {
+        for (uint32_t slot = 0; slot < s; slot++)
+            if (mask_pred(spec, type, id, slot)) return (uint8_t)1;
+        return (uint8_t)0;
+    };
+    P->nz1.resize(n1);
+    P->nz2.resize(n2);
+    P->nz3.resize(n3);
+    for (size_t k = 0; k < n1; k++) P->nz1[k] = nonzero(1, (uint32_t)k);
+    for (size_t k = 0; k < n2; k++) P->nz2[k] = nonzero(2, (uint32_t)k);
+    for (size_t k = 0; k < n3; k++) P->nz3[k] = nonzero(3, (uint32_t)k);
+    if (!rc) rc = encode_masks(c, spec, 1, (uint32_t)n1, level, P->d_m1);
+    if (!rc) rc = encode_masks(c, spec, 2, (uint32_t)n2, level - 1, P->d_m2);
+    if (!rc) rc = encode_masks(c, spec, 3, (uint32_t)n3, level - 3, P->d_m3);
+    if (rc) {
+        blb_cc_plan_free(P);
+        return rc;
+    }
+    *out = P;
+    return BLB_OK;
+}
+
+extern "C" void blb_cc_plan_free(blb_cc_plan* P)
+{
+    if (!P) return;
+    blb_ctx* c = P->ctx;
+    const uint32_t N = c->N;
+    dev_free(c, P->d_m1, 2ull * P->Kc * (P->level + 1) * N * 8);
+    dev_free(c, P->d_m2, 2ull * P->L * P->level * N * 8);
+    dev_free(c, P->d_m3, (size_t)P->L * P->nout * (P->level - 2) * N * 8);
+    delete P;
+    ctx_release(c);
+}
+
+static int32_t step3_rot(const blb_cc_plan* P, uint32_t t)
+{
+    const int64_t s = P->ctx->N / 2;
+    const int64_t g = t / P->b1s2;
+    return (int32_t)((((int64_t)g * P->b1s2 - (int64_t)(t % P->Kc) * P->Hg * P->L) % s + s) % s);
+}
+
+static std::vector<int32_t> plan_rotations(const blb_cc_plan* P)
+{
+    std::vector<int32_t> r;
+    auto add = [&](int64_t x) {
+        const int64_t s = P->ctx->N / 2;
+        int32_t v = (int32_t)x;
+        if (((x % s) + s) % s == 0) return;
+        if (std::find(r.begin(), r.end(), v) == r.end()) r.push_back(v);
+    };
+    for (uint32_t b0 = 1; b0 < P->b1s1; b0++) add(b0);
+    for (uint32_t b0 = 0; b0 < P->b1s1; b0++) add((int64_t)b0 - P->L);
+    for (uint32_t g1 = 1; g1 < P->G1; g1++) add((int64_t)g1 * P->b1s1);
+    for (uint32_t b = 1; b < P->b1s2; b++) add(b);
+    for (uint32_t b = 0; b < P->b1s2; b++) add((int64_t)b - P->L);
+    for (uint32_t g = 1; g < P->G2; g++) add(-(int64_t)g * P->b1s2);
+    for (uint32_t t = 1; t < P->L; t++) add(step3_rot(P, t));
+    return r;
+}
+
+extern "C" int blb_cc_plan_info(const blb_cc_plan* P, uint32_t* n_c, uint32_t* Kc, uint32_t* nout, uint32_t* b1s1,
+                                uint32_t* b1s2, uint64_t* mask_bytes)
+{
+    if (!P) return blb_fail(BLB_ERR_ARG, "null plan");
+    if (n_c) *n_c = P->n_c;
+    if (Kc) *Kc = P->Kc;
+    if (nout) *nout = P->nout;
+    if (b1s1) *b1s1 = P->b1s1;
+    if (b1s2) *b1s2 = P->b1s2;
+    if (mask_bytes) *mask_bytes = P->bytes;
+    return BLB_OK;
+}
+
+extern "C" int blb_cc_plan_rotations(const blb_cc_plan* P, int32_t* out, uint32_t cap, uint32_t* count)
+{
+    if (!P || !count) return blb_fail(BLB_ERR_ARG, "null argument");
+    std::vector<int32_t> r = plan_rotations(P);
+    *count = (uint32_t)r.size();
+    if (out) {
+        if (cap < r.size()) return blb_fail(BLB_ERR_ARG, "rotation buffer too small");
+        memcpy(out, r.data(), r.size() * 4);
+    }
+    return BLB_OK;
+}
+
+// ---------------------------------------------------------------------------
+// run
+// ---------------------------------------------------------------------------
+static int lincomb(blb_ctx* c, uint64_t* out, uint32_t nout, const std::vector<uint32_t>& start,
+                   const std::vector<LcTerm>& terms, uint32_t level)
+{
+    uint32_t* d_start = nullptr;
+    LcTerm* d_terms = nullptr;
+    size_t bs = 0, bt = 0;
+    int rc = upload_table(c, start, &d_start, &bs);
+    if (!rc) rc = upload_table(c, terms, &d_terms, &bt);
+    if (!rc) {
+        k_lincomb<<<dim3((c->N + kT - 1) / kT, level + 1, nout), kT, 0, c->stream>>>(out, d_start, d_terms, level + 1,
+                                                                                   c->N, c->d_q, c->d_bar);
+        if (cudaGetLastError() != cudaSuccess) rc = blb_fail(BLB_ERR_CUDA, "lincomb launch failed");
+        else blb_count_launch();
+    }
+    dev_free(c, d_start, bs);
+    dev_free(c, d_terms, bt);
+    return rc;
+}
+
+static const uint64_t* key_for(const blb_keys* K, uint32_t N, int32_t rot, int* rc)
+{
+    const KeyEntry* k = K->find(galois_element(N, rot));
+    if (!k) *rc = blb_fail(BLB_ERR_NO_KEY, "no Galois key for rotation " + std::to_string(rot));
+    return k ? k->d : nullptr;
+}
+
+extern "C" int blb_matmul_cc_plan(blb_ctx* c, const blb_keys* K, const blb_cc_plan* P, blb_ct* const* A,
+                                  blb_ct* const* B, uint32_t n_in, blb_ct** C)
+{
+    if (!c || !K || !P || !A || !B || !C) return blb_fail(BLB_ERR_ARG, "null argument");
+    if (n_in != P->n_c) return blb_fail(BLB_ERR_ARG, "number of input ciphertexts does not match the plan");
+    for (uint32_t i = 0; i < n_in; i++) {
+        if (!A[i] || !B[i] || A[i]->level != P->level || B[i]->level != P->level || A[i]->npolys != 2 ||
+            B[i]->npolys != 2)
+            return blb_fail(BLB_ERR_LEVEL, "input ciphertexts must be 2-polynomial ciphertexts at the plan's level");
+        if (std::fabs(A[i]->scale - A[0]->scale) > 1e-9 * A[0]->scale ||
+            std::fabs(B[i]->scale - B[0]->scale) > 1e-9 * B[0]->scale)
+            return blb_fail(BLB_ERR_SCALE, "inputs have different scales");
+    }
+    if (!K->find(0)) return blb_fail(BLB_ERR_NO_KEY, "matmul_cc needs the relinearization key");
+    for (uint32_t j = 0; j < P->nout; j++) C[j] = nullptr;
+    const uint32_t N = c->N, n_c = P->n_c, L = P->L, l0 = P->level;
+    const uint32_t l1 = l0 - 1, l2 = l0 - 2, l3 = l0 - 3;
+    const size_t pw0 = (size_t)(l0 + 1) * N, pw1 = (size_t)(l1 + 1) * N, pw2 = (size_t)(l2 + 1) * N,
+                 pw3 = (size_t)(l3 + 1) * N;
+    int rc = BLB_OK;
+    std::vector<KsItem> items;
+
+    // ---- step 1 ----
+    Stack LO, HI, INNER, ACC, BP;
+    rc = LO.alloc(c, n_c * P->b1s1, l0);
+    if (!rc) rc = HI.alloc(c, n_c * P->b1s1, l0);
+    if (!rc) rc = INNER.alloc(c, n_c * P->G1, l0);
+    if (!rc) rc = ACC.alloc(c, n_c, l0);
+    if (!rc) rc = BP.alloc(c, n_c, l1);
+    for (uint32_t ci = 0; !rc && ci < n_c; ci++) {
+        const uint64_t* Bc = B[ci]->d;
+        for (uint32_t b0 = 0; !rc && b0 < P->b1s1; b0++) {
+            uint64_t* lo = LO.at((size_t)ci * P->b1s1 + b0);
+            uint64_t* hi = HI.at((size_t)ci * P->b1s1 + b0);
+            if (b0 == 0) {
+                if (cudaMemcpyAsync(lo, Bc, 2 * pw0 * 8, cudaMemcpyDeviceToDevice, c->stream))
+                    rc = blb_fail(BLB_ERR_CUDA, "copy failed");
+            } else {
+                const uint64_t* k = key_for(K, N, (int32_t)b0, &rc);
+                if (k) items.push_back(KsItem{Bc, Bc + pw0, nullptr, k, lo, lo + pw0, galois_element(N, (int32_t)b0)});
+            }
+            if (!rc && (b0 > 0 || P->G1 > 1)) {
+                const int32_t r = (int32_t)b0 - (int32_t)L;
+                const uint64_t* k = key_for(K, N, r, &rc);
+                if (k) items.push_back(KsItem{Bc, Bc + pw0, nullptr, k, hi, hi + pw0, galois_element(N, r)});
+            }
+        }
+    }
+    if (!rc) rc = keyswitch_batch(c, l0, items.data(), (uint32_t)items.size(), 0);
+    if (!rc) {  // inner[c][g1] = sum_b0 m1lo LO + m1hi HI
+        std::vector<uint32_t> start{0};
+        std::vector<LcTerm> terms;
+        for (uint32_t ci = 0; ci < n_c; ci++)
+            for (uint32_t g1 = 0; g1 < P->G1; g1++) {
+                for (uint32_t b0 = 0; b0 < P->b1s1; b0++) {
+                    const uint32_t kappa = g1 * P->b1s1 + b0;
+                    for (uint32_t hi = 0; hi < 2; hi++) {
+                        const uint32_t id = kappa * 2 + hi;
+                        if (!P->nz1[id]) continue;
+                        const uint64_t* ct = (hi ? HI : LO).at((size_t)ci * P->b1s1 + b0);
+                        terms.push_back(LcTerm{ct, P->d_m1 + (size_t)id * pw0});
+                    }
+                }
+                start.push_back((uint32_t)terms.size());
+            }
+        rc = lincomb(c, INNER.d, n_c * P->G1, start, terms, l0);
+    }
+    for (uint32_t ci = 0; !rc && ci < n_c; ci++)
+        if (cudaMemcpyAsync(ACC.at(ci), INNER.at((size_t)ci * P->G1), 2 * pw0 * 8, cudaMemcpyDeviceToDevice,
+                            c->stream))
+            rc = blb_fail(BLB_ERR_CUDA, "copy failed");
+    for (uint32_t g1 = 1; !rc && g1 < P->G1; g1++) {
+        items.clear();
+        const int32_t r = (int32_t)(g1 * P->b1s1);
+        const uint64_t* k = key_for(K, N, r, &rc);
+        for (uint32_t ci = 0; k && ci < n_c; ci++) {
+            const uint64_t* src = INNER.at((size_t)ci * P->G1 + g1);
+            items.push_back(KsItem{src, src + pw0, nullptr, k, ACC.at(ci), ACC.at(ci) + pw0, galois_element(N, r)});
+        }
+        if (!rc) rc = keyswitch_batch(c, l0, items.data(), (uint32_t)items.size(), 1);
+    }
+    if (!rc) rc = rescale_many(c, BP.d, ACC.d, l0, n_c, 2);
+
+    // ---- step 2 ----
+    Stack BLO, BHI, A2, AG, VPRE, V, U, WP, W;
+    if (!rc) rc = BLO.alloc(c, n_c * P->b1s2, l1);
+    if (!rc) rc = BHI.alloc(c, n_c * P->b1s2, l1);
+    if (!rc) rc = A2.alloc(c, n_c, l2);
+    if (!rc) rc = AG.alloc(c, n_c * P->G2, l2);
+    if (!rc) rc = VPRE.alloc(c, n_c * L, l1);
+    if (!rc) rc = V.alloc(c, n_c * L, l2);
+    if (!rc) rc = U.alloc(c, L, l2, 3);
+    if (!rc) rc = WP.alloc(c, L, l2);
+    if (!rc) rc = W.alloc(c, L, l3);
+    items.clear();
+    for (uint32_t ci = 0; !rc && ci < n_c; ci++) {
+        const uint64_t* Bc = BP.at(ci);
+        for (uint32_t b = 0; !rc && b < P->b1s2; b++) {
+            uint64_t* lo = BLO.at((size_t)ci * P->b1s2 + b);
+            uint64_t* hi = BHI.at((size_t)ci * P->b1s2 + b);
+            if (b == 0) {
+                if (cudaMemcpyAsync(lo, Bc, 2 * pw1 * 8, cudaMemcpyDeviceToDevice, c->stream))
+                    rc = blb_fail(BLB_ERR_CUDA, "copy failed");
+            } else {
+                const uint64_t* k = key_for(K, N, (int32_t)b, &rc);
+                if (k) items.push_back(KsItem{Bc, Bc + pw1, nullptr, k, lo, lo + pw1, galois_element(N, (int32_t)b)});
+            }
+            if (!rc && (b > 0 || P->G2 > 1)) {
+                const int32_t r = (int32_t)b - (int32_t)L;
+                const uint64_t* k = key_for(K, N, r, &rc);
+                if (k) items.push_back(KsItem{Bc, Bc + pw1, nullptr, k, hi, hi + pw1, galois_element(N, r)});
+            }
+        }
+    }
+    if (!rc) rc = keyswitch_batch(c, l1, items.data(), (uint32_t)items.size(), 0);
+    for (uint32_t ci = 0; !rc && ci < n_c; ci++) {  // A at level l2, then its giant-step rotations
+        k_drop<<<dim3((N + kT - 1) / kT, l2 + 1, 2), kT, 0, c->stream>>>(A2.at(ci), A[ci]->d, l0 + 1, l2 + 1, N);
+        if (cudaGetLastError() != cudaSuccess) rc = blb_fail(BLB_ERR_CUDA, "drop launch failed");
+        else blb_count_launch();
+        if (!rc && cudaMemcpyAsync(AG.at((size_t)ci * P->G2), A2.at(ci), 2 * pw2 * 8, cudaMemcpyDeviceToDevice,
+                                   c->stream))
+            rc = blb_fail(BLB_ERR_CUDA, "copy failed");
+    }
+    items.clear();
+    for (uint32_t ci = 0; !rc && ci < n_c; ci++)
+        for (uint32_t g = 1; !rc && g < P->G2; g++) {
+            const int32_t r = -(int32_t)(g * P->b1s2);
+            const uint64_t* k = key_for(K, N, r, &rc);
+            uint64_t* o = AG.at((size_t)ci * P->G2 + g);
+            if (k) items.push_back(KsItem{A2.at(ci), A2.at(ci) + pw2, nullptr, k, o, o + pw2, galois_element(N, r)});
+        }
+    if (!rc) rc = keyswitch_batch(c, l2, items.data(), (uint32_t)items.size(), 0);
+    if (!rc) {  // VPRE[c][t] = m2lo BLO + m2hi BHI
+        std::vector<uint32_t> start{0};
+        std::vector<LcTerm> terms;
+        for (uint32_t ci = 0; ci < n_c; ci++)
+            for (uint32_t t = 0; t < L; t++) {
+                const uint32_t b = t % P->b1s2;
+                for (uint32_t hi = 0; hi < 2; hi++) {
+                    const uint32_t id = t * 2 + hi;
+                    if (!P->nz2[id]) continue;
+                    const uint64_t* ct = (hi ? BHI : BLO).at((size_t)ci * P->b1s2 + b);
+                    terms.push_back(LcTerm{ct, P->d_m2 + (size_t)id * pw1});
+                }
+                start.push_back((uint32_t)terms.size());
+            }
+        rc = lincomb(c, VPRE.d, n_c * L, start, terms, l1);
+    }
+    if (!rc) rc = rescale_many(c, V.d, VPRE.d, l1, n_c * L, 2);
+    if (!rc) {  // U[t] = sum_c AG[c][g] (x) V[c][t]
+        std::vector<TensorPair> pairs;
+        for (uint32_t t = 0; t < L; t++)
+            for (uint32_t ci = 0; ci < n_c; ci++)
+                pairs.push_back(TensorPair{AG.at((size_t)ci * P->G2 + t / P->b1s2), V.at((size_t)ci * L + t)});
+        TensorPair* d_pairs = nullptr;
+        size_t bp = 0;
+        rc = upload_table(c, pairs, &d_pairs, &bp);
+        if (!rc) {
+            k_tensor_acc<<<dim3((N + kT - 1) / kT, l2 + 1, L), kT, 0, c->stream>>>(U.d, d_pairs, n_c, l2 + 1, N,
+                                                                                c->d_q, c->d_bar);
+            if (cudaGetLastError() != cudaSuccess) rc = blb_fail(BLB_ERR_CUDA, "tensor launch failed");
+            else blb_count_launch();
+        }
+        dev_free(c, d_pairs, bp);
+    }
+    if (!rc) {  // relinearize: (d0, d1, d2) -> (d0 + k0, d1 + k1)
+        items.clear();
+        const uint64_t* rk = K->find(0)->d;
+        for (uint32_t t = 0; t < L; t++) {
+            const uint64_t* u = U.at(t);
+            uint64_t* o = WP.at(t);
+            items.push_back(KsItem{u, u + 2 * pw2, u + pw2, rk, o, o + pw2, 1});
+        }
+        rc = keyswitch_batch(c, l2, items.data(), (uint32_t)items.size(), 0);
+    }
+    if (!rc) rc = rescale_many(c, W.d, WP.d, l2, L, 2);
+
+    // ---- step 3 ----
+    Stack RT, CP;
+    if (!rc) rc = RT.alloc(c, L, l3);
+    if (!rc) rc = CP.alloc(c, P->nout, l3);
+    items.clear();
+    for (uint32_t t = 0; !rc && t < L; t++) {
+        const int32_t r = step3_rot(P, t);
+        if (r == 0) {
+            if (cudaMemcpyAsync(RT.at(t), W.at(t), 2 * pw3 * 8, cudaMemcpyDeviceToDevice, c->stream))
+                rc = blb_fail(BLB_ERR_CUDA, "copy failed");
+            continue;
+        }
+        const uint64_t* k = key_for(K, N, r, &rc);
+        if (k) items.push_back(KsItem{W.at(t), W.at(t) + pw3, nullptr, k, RT.at(t), RT.at(t) + pw3, galois_element(N, r)});
+    }
+    if (!rc) rc = keyswitch_batch(c, l3, items.data(), (uint32_t)items.size(), 0);
+    if (!rc) {
+        std::vector<uint32_t> start{0};
+        std::vector<LcTerm> terms;
+        for (uint32_t j = 0; j < P->nout; j++) {
+            for (uint32_t t = 0; t < L; t++) {
+                const uint32_t id = t * P->nout + j;
+                if (P->nz3[id]) terms.push_back(LcTerm{RT.at(t), P->d_m3 + (size_t)id * pw3});
+            }
+            start.push_back((uint32_t)terms.size());
+        }
+        rc = lincomb(c, CP.d, P->nout, start, terms, l3);
+    }
+    const double out_scale = A[0]->scale * B[0]->scale / (double)c->q[l2];
+    for (uint32_t j = 0; !rc && j < P->nout; j++) {
+        blb_ct* y = nullptr;
+        rc = new_ciphertext(c, l3 - 1, 2, out_scale, &y);
+        if (!rc) rc = launch_rescale(c, y->d, CP.at(j), l3, 2);
+        C[j] = y;
+    }
+    if (rc) {
+        for (uint32_t j = 0; j < P->nout; j++) {
+            blb_ct_free(C[j]);
+            C[j] = nullptr;
+        }
+    }
+    return rc;
+}
+
+extern "C" int blb_matmul_cc(blb_ctx* c, const blb_keys* K, blb_ct* const* A, blb_ct* const* B, uint32_t n_in,
+                             uint32_t L, uint32_t R, uint32_t Hg, const blb_cc_sched* sched, blb_ct** C)
+{
+    if (!c || !A || n_in == 0 || !A[0]) return blb_fail(BLB_ERR_ARG, "null argument");
+    blb_cc_plan* P = nullptr;
+    BLB_TRY(blb_cc_plan_create(c, L, Hg, R, A[0]->level, sched, &P));
+    int rc = blb_matmul_cc_plan(c, K, P, A, B, n_in, C);
+    blb_cc_plan_free(P);
+    return rc;
+}
