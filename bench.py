@@ -146,6 +146,36 @@ def unpack_columns(Z, m, k, d_out):
     return np.stack(cols[:d_out], axis=1)
 
 
+def pack_heads(mats, L, Hg, Kc, n_c, rows):
+    """Multi-head packing (Sec. 5.1): block beta = h + Hg kappa of ciphertext c holds
+    column (rows=False, mats (Hg, L, R)) or row (rows=True, mats (Hg, R, L)) k = c Kc + kappa
+    of head h, element i at slot beta L + i."""
+    Z = np.zeros((n_c, L * Hg * Kc))
+    R = mats.shape[1] if rows else mats.shape[2]
+    for c in range(n_c):
+        for kappa in range(Kc):
+            k = c * Kc + kappa
+            if k < R:
+                for h in range(Hg):
+                    b = h + Hg * kappa
+                    Z[c, b * L:(b + 1) * L] = mats[h, k, :] if rows else mats[h, :, k]
+    return Z
+
+
+def unpack_head_diagonals(Z, L, Hg, Kc):
+    """Output ciphertext j holds diagonal delta = j Kc + kappa of head h at block
+    h + Hg kappa: element i is C_h[i, (i + delta) mod L]."""
+    out = np.zeros((Hg, L, L))
+    i = np.arange(L)
+    for j in range(Z.shape[0]):
+        for kappa in range(Kc):
+            delta = j * Kc + kappa
+            for h in range(Hg):
+                b = h + Hg * kappa
+                out[h, i, (i + delta) % L] = Z[j, b * L:(b + 1) * L]
+    return out
+
+
 class Workload:
     def __init__(self, device):
         import torch
@@ -198,6 +228,28 @@ class Workload:
             ctx.decrypt(keys, masked, coeffs=True, slots=False, coeff_out=p0[i:i + 1])
         return (Y, O) if keep else None
 
+    def step_batched(self, S):
+        """S sequences through the same plans in one batched pass per product."""
+        ctx, keys = self.ctx, self.keys
+        seqs = []
+        for _ in range(S):
+            cts = []
+            for c in range(self.n_in):
+                self.nonce += 1
+                cts.append(ctx.encrypt(keys, ctx.encode(self.Zdev[c], LEVEL), self.nonce))
+            seqs.append(cts)
+        Ys = ctx.matmul_cp_batch(keys, self.plan_qkv, seqs)
+        Os = ctx.matmul_cp_batch(keys, self.plan_o, [Y[:self.n_in] for Y in Ys])
+        if getattr(self, "bp0", None) is None or self.bp0.shape[0] != S * self.n_out:
+            self.bp0 = self.torch.zeros((S * self.n_out, self.N), dtype=self.torch.uint64, device=self.p0_dev.device)
+            self.bp1 = self.torch.zeros_like(self.bp0)
+        for s, (Y, O) in enumerate(zip(Ys, Os)):
+            for i, y in enumerate(Y[self.n_in:] + O):
+                self.nonce += 1
+                r = s * self.n_out + i
+                masked, _ = ctx.he2mpc(keys, y, self.nonce, share_out=self.bp1[r])
+                ctx.decrypt(keys, masked, coeffs=True, slots=False, coeff_out=self.bp0[r:r + 1])
+
     def accuracy(self):
         Y, O = self.step(keep=True)
         got_qkv = unpack_columns(np.stack([self.ctx.decrypt(self.keys, y, coeffs=False)[1] for y in Y]), M, self.k, D_QKV)
@@ -211,6 +263,77 @@ class Workload:
         return {"rotations": rot(qkv) + rot(o),
                 "plaintext_products": qkv["nX"] * qkv["nY"] * self.k + o["nX"] * o["nY"] * self.k,
                 "rescales": qkv["nY"] + o["nY"], "he2mpc": self.n_out}
+
+
+def timed_fn(w, fn, steps, world):
+    torch = w.torch
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier(world)
+    torch.cuda.synchronize()
+    ev0.record(w.stream)
+    for _ in range(steps):
+        fn()
+    ev1.record(w.stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    return ev0.elapsed_time(ev1) / 1e3
+
+
+def attention_cc(steps):
+    """BERT-base attention products on ciphertexts (12 heads in groups of 8 and
+    4, 128 tokens, head dim 64, N = 2^16, 12 primes, dnum 4): Q_h K_h^T and
+    Softmax x V_h with matmul_cc, one sequence per step.  Returns tokens/s, ms."""
+    import torch
+    from paper_2508_19525_b300 import blb
+    from paper_2508_19525_b300 import workloads as wl
+    prm = wl.BERT_CC
+    stream = torch.cuda.Stream()
+    ctx = blb.Context(prm.logN, prm.q_bits, prm.p_bits, prm.dnum, prm.scale, stream=stream)
+    L, Dh, level = 128, 64, ctx.nQ - 1
+    plans = {Hg: (ctx.cc_plan(L, Hg, Dh, level), ctx.cc_plan(L, Hg, L, level)) for Hg in (8, 4)}
+    rots = sorted({r for pq, pv in plans.values() for r in pq.rotations() + pv.rotations()})
+    keys = ctx.keygen(1, rots, relin=True)
+    Q, K, V, P = wl.attention_operands(L, 12, Dh, seed=3)
+    inputs = []
+    for Hg, h0 in ((8, 0), (4, 8)):
+        pq, pv = plans[Hg]
+        for kind, plan in (("qk", pq), ("pv", pv)):
+            info = plan.info()
+            if kind == "qk":
+                A, B = Q[h0:h0 + Hg], np.transpose(K[h0:h0 + Hg], (0, 2, 1))
+            else:
+                A = P[h0:h0 + Hg]
+                B = np.concatenate([V[h0:h0 + Hg], np.zeros((Hg, L, L - Dh))], axis=2)
+            Az = pack_heads(A, L, Hg, info["Kc"], info["n_c"], rows=False)
+            Bz = pack_heads(B, L, Hg, info["Kc"], info["n_c"], rows=True)
+            Ac = [ctx.encrypt(keys, ctx.encode(z, level), 7 * c) for c, z in enumerate(Az)]
+            Bc = [ctx.encrypt(keys, ctx.encode(z, level), 7 * c + 1) for c, z in enumerate(Bz)]
+            inputs.append((plan, Ac, Bc, A, B, Hg, info))
+
+    def one():
+        for plan, Ac, Bc, *_ in inputs:
+            ctx.matmul_cc_plan(keys, plan, Ac, Bc)
+    one()
+    ctx.sync()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(steps):
+        one()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    sec = ev0.elapsed_time(ev1) / 1e3 / steps
+    # accuracy of the last products against FP64
+    err = 0.0
+    for plan, Ac, Bc, A, B, Hg, info in inputs:
+        C = ctx.matmul_cc_plan(keys, plan, Ac, Bc)
+        zs = np.stack([ctx.decrypt(keys, c, coeffs=False)[1] for c in C])
+        got = unpack_head_diagonals(zs, L, Hg, info["Kc"])
+        err = max(err, float(np.max(np.abs(got - np.einsum("hik,hkj->hij", A, B)))))
+    rot = sum(len(p.rotations()) for pq, pv in plans.values() for p in (pq, pv))
+    return {"value": round(L / sec, 3), "unit": UNIT, "ms_per_step": round(sec * 1e3, 3),
+            "workload": "BERT-base attention: Q_h K_h^T and Softmax x V_h for 12 heads (groups 8+4), "
+                        "L=128, head dim 64, N=2^16, 12 primes, dnum 4, one sequence per step",
+            "max_abs_err_vs_fp64": err, "rotation_keys": rot}
 
 
 def timed(w, steps, host, world):
@@ -255,6 +378,16 @@ def run_blb(args):
     _, e2e_wall = timed(w, args.steps, True, world)
     e2e_value, _ = aggregate(e2e_wall, TOKENS_PER_STEP * args.steps, world)
     max_err, mse = w.accuracy()
+    # batched: several sequences share each plaintext stream
+    batched = None
+    if args.batch > 1:
+        w.step_batched(args.batch)
+        bsec = timed_fn(w, lambda: w.step_batched(args.batch), max(1, args.steps // 2), world)
+        bsteps = max(1, args.steps // 2)
+        bval, _ = aggregate(bsec, TOKENS_PER_STEP * args.batch * bsteps, world)
+        batched = {"sequences_per_step": args.batch, "value": round(bval, 3), "unit": UNIT,
+                   "ms_per_step": round(bsec * 1e3 / bsteps, 3), "speedup_vs_plain": round(bval / value, 3)}
+    attn = attention_cc(max(1, args.steps // 2)) if args.attention and world == 1 else None
     if rank != 0:
         return
     peaks = {}
@@ -292,6 +425,8 @@ def run_blb(args):
         "roofline": dict(roof[dominant], kernel=dominant, traffic=traffic) if dominant else None,
         "roofline_sites": roof,
         "accuracy": {"max_abs_err_vs_fp64": max_err, "mse": mse, "bound": 1e-4},
+        "batched": batched,
+        "attention_cc": attn,
         "counts_per_step": w.counts(),
         "weights": {"plaintext_bytes": w.plan_bytes, "encode_s": round(w.plan_s, 2), "timed": False},
     }
@@ -421,6 +556,9 @@ def main():
     ap.add_argument("--cpu-rotations", type=int, default=6)
     ap.add_argument("--cpu-products", type=int, default=48)
     ap.add_argument("--ncu-case", action="store_true", help="run the small profiling case and exit")
+    ap.add_argument("--batch", type=int, default=8, help="sequences per batched step (1 = skip)")
+    ap.add_argument("--no-attention", dest="attention", action="store_false",
+                    help="skip the matmul_cc attention measurement")
     args = ap.parse_args()
     if args.ncu_case:
         return ncu_case()

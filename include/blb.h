@@ -204,6 +204,12 @@ int blb_cp_plan_info(const blb_cp_plan* plan, uint32_t* nX, uint32_t* nY, uint32
                      uint32_t* G, uint64_t* plaintext_bytes);
 int blb_matmul_cp_plan(blb_ctx* ctx, const blb_keys* keys, const blb_cp_plan* plan,
                        blb_ct* const* X, uint32_t nX, blb_ct** Y);
+/* Batched form: n_seq sequences (same m and d, e.g. the sequences of one
+ * client's batch) through one plan.  X: n_seq x nX handles, sequence-major;
+ * Y: n_seq x nY.  Every plaintext word is read from HBM once per batch and
+ * applied to all sequences; results equal n_seq calls of blb_matmul_cp_plan. */
+int blb_matmul_cp_batch(blb_ctx* ctx, const blb_keys* keys, const blb_cp_plan* plan,
+                        blb_ct* const* X, uint32_t n_seq, blb_ct** Y);
 int blb_matmul_cp(blb_ctx* ctx, const blb_keys* keys, blb_ct* const* X, uint32_t nX, uint32_t m,
                   uint32_t d, const double* W, uint32_t d_out, const blb_sched* sched, blb_ct** Y);
 

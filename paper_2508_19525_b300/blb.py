@@ -81,6 +81,7 @@ SIGNATURES = {
     "blb_cp_plan_free": (None, [_vp]),
     "blb_cp_plan_info": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "blb_matmul_cp_plan": (ctypes.c_int, [_vp, _vp, _vp, _pp, _u32, _pp]),
+    "blb_matmul_cp_batch": (ctypes.c_int, [_vp, _vp, _vp, _pp, _u32, _pp]),
     "blb_matmul_cp": (ctypes.c_int, [_vp, _vp, _pp, _u32, _u32, _u32, _vp, _u32, ctypes.POINTER(_Sched), _pp]),
     "blb_cc_plan_create": (ctypes.c_int, [_vp, _u32, _u32, _u32, _u32, ctypes.POINTER(_CcSched), _pp]),
     "blb_cc_plan_free": (None, [_vp]),
@@ -381,6 +382,16 @@ class Context:
         ys = (ctypes.c_void_p * info["nY"])()
         _check(lib().blb_matmul_cp_plan(self.h, keys.h, plan.h, xs, len(X), ys))
         return [Ciphertext(self, y) for y in ys]
+
+    def matmul_cp_batch(self, keys, plan, X_seqs):
+        """X_seqs: list of per-sequence lists of nX ciphertexts -> list of lists of nY."""
+        info = plan.info()
+        flat = [x for seq in X_seqs for x in seq]
+        xs = (ctypes.c_void_p * len(flat))(*[x.h for x in flat])
+        ys = (ctypes.c_void_p * (len(X_seqs) * info["nY"]))()
+        _check(lib().blb_matmul_cp_batch(self.h, keys.h, plan.h, xs, len(X_seqs), ys))
+        out = [Ciphertext(self, y) for y in ys]
+        return [out[s * info["nY"]:(s + 1) * info["nY"]] for s in range(len(X_seqs))]
 
     def matmul_cp(self, keys, X, m, d, W, d_out, b1=0):
         W = np.ascontiguousarray(W, np.float64) if isinstance(W, np.ndarray) else W

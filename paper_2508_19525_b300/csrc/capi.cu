@@ -93,84 +93,18 @@ int rotate_add(blb_ctx* c, const blb_keys* keys, const uint64_t* in, uint32_t le
     return BLB_OK;
 }
 
-// matmul_cp inner products: T[e][g] = sum_{c, b} baby[c][b] (.) pt[e][g][c][b].
-// A CTA owns C coefficients of one limb: it stages the baby-step values of
-// every term for those coefficients in shared memory once, then streams the
-// plaintexts of every (e, g) through them.  Each plaintext word and each
-// baby-step word is read from HBM exactly once.  Lazy 128-bit sums, folded
-// every 8 terms; the 8 plaintext loads of a group are issued together.
-__global__ void __launch_bounds__(256) k_cp_mac_tile(uint64_t* __restrict__ T, const uint64_t* __restrict__ baby,
-                                                      const uint64_t* __restrict__ pts, uint32_t n, uint32_t N,
-                                                      uint32_t terms, uint32_t neg, uint32_t logC,
-                                                      const uint64_t* __restrict__ qs, const uint64_t* __restrict__ bar)
-{
-    extern __shared__ uint64_t sb[];  // [terms][2][C]
-    const uint32_t C = 1u << logC;
-    const uint32_t i = blockIdx.y, c0 = blockIdx.x << logC;
-    const size_t nN = (size_t)n * N;
-    for (uint32_t idx = threadIdx.x; idx < terms * 2 * C; idx += blockDim.x) {
-        const uint32_t cc = idx & (C - 1), tp = idx >> logC;  // tp = t * 2 + poly
-        sb[idx] = baby[(size_t)(tp >> 1) * 2 * nN + (size_t)(tp & 1) * nN + (size_t)i * N + c0 + cc];
-    }
-    __syncthreads();
-    const uint64_t q = qs[i], r0 = bar[2 * i], r1 = bar[2 * i + 1];
-    const uint32_t lanes = blockDim.x >> logC, lane = threadIdx.x >> logC, cc = threadIdx.x & (C - 1);
-    for (uint32_t eg = lane; eg < neg; eg += lanes) {
-        const uint64_t* P = pts + (size_t)eg * terms * nN + (size_t)i * N + c0 + cc;
-        acc128 a0{0, 0}, a1{0, 0};
-        uint32_t t = 0;
-        for (; t + 8 <= terms; t += 8) {
-            uint64_t w[8];
-#pragma unroll
-            for (int u = 0; u < 8; u++) w[u] = __ldcs(P + (size_t)(t + u) * nN);  // streamed once
-#pragma unroll
-            for (int u = 0; u < 8; u++) {
-                mad128(a0, sb[(2 * (t + u)) * C + cc], w[u]);
-                mad128(a1, sb[(2 * (t + u) + 1) * C + cc], w[u]);
-            }
-            a0 = acc128{barrett128(a0.lo, a0.hi, q, r0, r1), 0};  // keep the 128-bit sums far from overflow
-            a1 = acc128{barrett128(a1.lo, a1.hi, q, r0, r1), 0};
-        }
-        for (; t < terms; t++) {
-            const uint64_t w = __ldcs(P + (size_t)t * nN);
-            mad128(a0, sb[(2 * t) * C + cc], w);
-            mad128(a1, sb[(2 * t + 1) * C + cc], w);
-        }
-        uint64_t* o = T + (size_t)eg * 2 * nN + (size_t)i * N + c0 + cc;
-        o[0] = barrett128(a0.lo, a0.hi, q, r0, r1);
-        o[nN] = barrett128(a1.lo, a1.hi, q, r0, r1);
-    }
-}
-
+// matmul_cp inner products for a batch of S sequences sharing one plan:
+//   T[s][e][g] = sum_{c, b} baby[s][c][b] (.) pt[e][g][c][b].
+// A CTA owns C coefficients of one limb: it stages the baby-step values of every
+// sequence and term for those coefficients in shared memory once, then streams
+// the plaintexts of every (e, g) through them; each plaintext word is read from
+// HBM once and applied to all S sequences.  Lazy 128-bit sums folded every 8
+// terms; the 8 plaintext loads of a group are issued together.
 }  // namespace
 
 int new_ciphertext(blb_ctx* c, uint32_t level, uint32_t npolys, double scale, blb_ct** out)
 {
     return new_ct(c, level, npolys, scale, out);
-}
-
-int launch_cp_mac(blb_ctx* c, const blb_cp_plan* plan, const uint64_t* baby, uint64_t* T)
-{
-    const uint32_t n = plan->level + 1;
-    // algorithmic bytes: every plaintext once, the baby-step ciphertexts once,
-    // the (e, g) partial sums written once
-    const uint64_t terms = (uint64_t)plan->nX * plan->b1, outs = (uint64_t)plan->nY * plan->G;
-    ProfScope prof(c, "cp_mac", (outs * terms * n + terms * 2 * n + outs * 2 * n) * c->N * 8);
-    // coefficients per CTA: largest power of two <= 64 whose baby tile fits 64 KB
-    uint32_t logC = 6;
-    while (logC > 3 && terms * 2 * (8ull << logC) > (64u << 10)) logC--;
-    const size_t smem = terms * 2 * (8ull << logC);
-    if (smem > (160u << 10)) return blb_fail(BLB_ERR_ARG, "too many plaintext terms per output for one CTA");
-    static bool attr_set = false;
-    if (!attr_set) {
-        BLB_CUDA(cudaFuncSetAttribute(k_cp_mac_tile, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 << 10));
-        attr_set = true;
-    }
-    dim3 grid(c->N >> logC, n);
-    k_cp_mac_tile<<<grid, 256, smem, c->stream>>>(T, baby, plan->d_pts, n, c->N, (uint32_t)terms, (uint32_t)outs, logC,
-                                                  c->d_q, c->d_bar);
-    BLB_LAUNCHED();
-    return BLB_OK;
 }
 
 // ===========================================================================
@@ -624,10 +558,15 @@ extern "C" int blb_cp_plan_create(blb_ctx* c, uint32_t m, uint32_t d, const doub
     P->b1 = b1;
     P->G = k / b1;
     const uint32_t n = level + 1;
-    const uint64_t npts = (uint64_t)P->nY * P->G * P->nX * P->b1;
-    P->bytes = npts * n * c->N * 8;
-    P->d_pts = (uint64_t*)dev_alloc(c, P->bytes);
-    if (!P->d_pts) {
+    const uint32_t terms = P->nX * P->b1, neg = P->nY * P->G;
+    P->d_ptb = nullptr;
+    int lrc = cp_plan_layout(c, P);
+    if (lrc) {
+        blb_cp_plan_free(P);
+        return lrc;
+    }
+    P->d_ptb = (uint8_t*)dev_alloc(c, P->bytes);
+    if (!P->d_ptb) {
         blb_cp_plan_free(P);
         return blb_fail(BLB_ERR_OOM, "plaintext diagonals do not fit");
     }
@@ -642,16 +581,26 @@ extern "C" int blb_cp_plan_create(blb_ctx* c, uint32_t m, uint32_t d, const doub
             rc = blb_fail(BLB_ERR_CUDA, "weight upload failed");
         dW = Wcopy;
     }
-    const uint32_t chunk = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(npts, (64ull << 20) / ((uint64_t)s * 8)));
+    // one block of 16 outputs (e, g) at a time: encode its plaintexts, then
+    // slice them into the byte layout of the tensor-core product
+    const uint64_t blk_pts = (uint64_t)16 * terms;
+    const size_t blk_bytes = blk_pts * n * c->N * 8;
+    const uint32_t chunk = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(blk_pts, (64ull << 20) / ((uint64_t)s * 8)));
     double* z = rc ? nullptr : (double*)dev_alloc(c, (size_t)chunk * s * 8);
-    if (!rc && !z) rc = blb_fail(BLB_ERR_OOM, "diagonal buffer");
-    for (uint64_t first = 0; !rc && first < npts; first += chunk) {
-        uint32_t cnt = (uint32_t)std::min<uint64_t>(chunk, npts - first);
-        rc = cp_build_diagonals(c, P, dW, (uint32_t)first, cnt, z);
-        if (!rc) rc = encode_slots(c, z, cnt, s, level, (double)c->q[level], P->d_pts + first * n * c->N);
+    uint64_t* blk = rc ? nullptr : (uint64_t*)dev_alloc(c, blk_bytes);
+    if (!rc && (!z || !blk)) rc = blb_fail(BLB_ERR_OOM, "diagonal buffer");
+    for (uint32_t eb = 0; !rc && eb < P->NEB; eb++) {
+        const uint64_t first = (uint64_t)eb * blk_pts, npts = (uint64_t)std::min<uint32_t>(16, neg - eb * 16) * terms;
+        for (uint64_t f = 0; !rc && f < npts; f += chunk) {
+            uint32_t cnt = (uint32_t)std::min<uint64_t>(chunk, npts - f);
+            rc = cp_build_diagonals(c, P, dW, (uint32_t)(first + f), cnt, z);
+            if (!rc) rc = encode_slots(c, z, cnt, s, level, (double)c->q[level], blk + f * n * c->N);
+        }
+        if (!rc) rc = cp_plan_store_block(c, P, blk, eb);
     }
     cudaStreamSynchronize(c->stream);
     dev_free(c, z, (size_t)chunk * s * 8);
+    dev_free(c, blk, blk_bytes);
     dev_free(c, Wcopy, wbytes);
     if (rc) {
         blb_cp_plan_free(P);
@@ -665,7 +614,7 @@ extern "C" void blb_cp_plan_free(blb_cp_plan* P)
 {
     if (!P) return;
     blb_ctx* c = P->ctx;
-    dev_free(c, P->d_pts, P->bytes);
+    dev_free(c, P->d_ptb, P->bytes);
     delete P;
     ctx_release(c);
 }
@@ -682,27 +631,25 @@ extern "C" int blb_cp_plan_info(const blb_cp_plan* P, uint32_t* nX, uint32_t* nY
     return BLB_OK;
 }
 
-// Y_e = Rescale( sum_g Rot^{g b1 m}( sum_{c,b} Rot^{b m}(X_c) (.) D'_{c,e,g,b} ) )
-extern "C" int blb_matmul_cp_plan(blb_ctx* c, const blb_keys* K, const blb_cp_plan* P, blb_ct* const* X,
-                                  uint32_t nX, blb_ct** Y)
+// Y_e = Rescale( sum_g Rot^{g b1 m}( sum_{c,b} Rot^{b m}(X_c) (.) D'_{c,e,g,b} ) ), for S
+// sequences at once (X: S x nX handles, sequence-major; Y: S x nY)
+static int cp_run(blb_ctx* c, const blb_keys* K, const blb_cp_plan* P, blb_ct* const* X, uint32_t S, blb_ct** Y)
 {
-    if (!c || !K || !P || !X || !Y) return blb_fail(BLB_ERR_ARG, "null argument");
-    if (nX != P->nX) return blb_fail(BLB_ERR_ARG, "number of input ciphertexts does not match the plan");
-    for (uint32_t i = 0; i < nX; i++) {
+    const uint32_t nX = P->nX, n = P->level + 1, N = c->N;
+    for (uint32_t i = 0; i < S * nX; i++) {
         if (!X[i] || X[i]->level != P->level || X[i]->npolys != 2)
             return blb_fail(BLB_ERR_LEVEL, "input ciphertext level does not match the plan");
         if (!same_scale(X[i]->scale, X[0]->scale)) return blb_fail(BLB_ERR_SCALE, "inputs have different scales");
     }
-    const uint32_t n = P->level + 1, N = c->N;
     const size_t ctw = (size_t)2 * n * N;
-    const size_t baby_bytes = (size_t)nX * P->b1 * ctw * 8, T_bytes = (size_t)P->nY * P->G * ctw * 8;
+    const size_t baby_bytes = (size_t)S * nX * P->b1 * ctw * 8, T_bytes = (size_t)S * P->nY * P->G * ctw * 8;
     uint64_t* baby = (uint64_t*)dev_alloc(c, baby_bytes);
     uint64_t* T = (uint64_t*)dev_alloc(c, T_bytes);
-    for (uint32_t e = 0; e < P->nY; e++) Y[e] = nullptr;
+    for (uint32_t e = 0; e < S * P->nY; e++) Y[e] = nullptr;
     int rc = (baby && T) ? BLB_OK : blb_fail(BLB_ERR_OOM, "matmul_cp workspace");
-    // baby steps: Rot^{b m}(X_c), all in one batched key-switch pass
+    // baby steps: Rot^{b m}(X_c) of every sequence, in one batched key-switch pass
     std::vector<KsItem> items;
-    for (uint32_t ci = 0; !rc && ci < nX; ci++) {
+    for (uint32_t ci = 0; !rc && ci < S * nX; ci++) {
         uint64_t* dst0 = baby + (size_t)ci * P->b1 * ctw;
         if (cudaMemcpyAsync(dst0, X[ci]->d, ctw * 8, cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess)
             rc = blb_fail(BLB_ERR_CUDA, "copy failed");
@@ -718,9 +665,13 @@ extern "C" int blb_matmul_cp_plan(blb_ctx* c, const blb_keys* K, const blb_cp_pl
         }
     }
     if (!rc) rc = keyswitch_batch(c, P->level, items.data(), (uint32_t)items.size(), 0);
-    // plaintext products for every (e, g)
-    if (!rc) rc = launch_cp_mac(c, P, baby, T);
-    // giant steps: acc_e += Rot^{g b1 m}(T[e][g]); one batched pass per g (distinct outputs)
+    // plaintext products for every (sequence, e, g), at most 8 sequences per launch
+    for (uint32_t s0 = 0; !rc && s0 < S;) {
+        uint32_t chunk = S - s0 >= 8 ? 8 : S - s0 >= 4 ? 4 : S - s0 >= 2 ? 2 : 1;
+        rc = launch_cp_mac(c, P, baby + (size_t)s0 * nX * P->b1 * ctw, T + (size_t)s0 * P->nY * P->G * ctw, chunk);
+        s0 += chunk;
+    }
+    // giant steps: acc += Rot^{g b1 m}(T[s][e][g]); one batched pass per g (distinct outputs)
     for (uint32_t g = 1; !rc && g < P->G; g++) {
         const uint64_t ge = galois_element(N, (int32_t)(g * P->b1 * P->m));
         const KeyEntry* k = K->find(ge);
@@ -729,7 +680,7 @@ extern "C" int blb_matmul_cp_plan(blb_ctx* c, const blb_keys* K, const blb_cp_pl
             break;
         }
         items.clear();
-        for (uint32_t e = 0; e < P->nY; e++) {
+        for (uint32_t e = 0; e < S * P->nY; e++) {
             uint64_t* acc = T + (size_t)e * P->G * ctw;
             const uint64_t* src = acc + (size_t)g * ctw;
             items.push_back(KsItem{src, src + (size_t)n * N, nullptr, k->d, acc, acc + (size_t)n * N, ge});
@@ -737,7 +688,7 @@ extern "C" int blb_matmul_cp_plan(blb_ctx* c, const blb_keys* K, const blb_cp_pl
         rc = keyswitch_batch(c, P->level, items.data(), (uint32_t)items.size(), 1);
     }
     // rescale
-    for (uint32_t e = 0; !rc && e < P->nY; e++) {
+    for (uint32_t e = 0; !rc && e < S * P->nY; e++) {
         blb_ct* y = nullptr;
         rc = new_ct(c, P->level - 1, 2, X[0]->scale, &y);
         if (!rc) rc = launch_rescale(c, y->d, T + (size_t)e * P->G * ctw, P->level, 2);
@@ -746,13 +697,28 @@ extern "C" int blb_matmul_cp_plan(blb_ctx* c, const blb_keys* K, const blb_cp_pl
     dev_free(c, baby, baby_bytes);
     dev_free(c, T, T_bytes);
     if (rc) {
-        for (uint32_t e = 0; e < P->nY; e++) {
+        for (uint32_t e = 0; e < S * P->nY; e++) {
             blb_ct_free(Y[e]);
             Y[e] = nullptr;
         }
         return rc;
     }
     return BLB_OK;
+}
+
+extern "C" int blb_matmul_cp_plan(blb_ctx* c, const blb_keys* K, const blb_cp_plan* P, blb_ct* const* X,
+                                  uint32_t nX, blb_ct** Y)
+{
+    if (!c || !K || !P || !X || !Y) return blb_fail(BLB_ERR_ARG, "null argument");
+    if (nX != P->nX) return blb_fail(BLB_ERR_ARG, "number of input ciphertexts does not match the plan");
+    return cp_run(c, K, P, X, 1, Y);
+}
+
+extern "C" int blb_matmul_cp_batch(blb_ctx* c, const blb_keys* K, const blb_cp_plan* P, blb_ct* const* X,
+                                   uint32_t n_seq, blb_ct** Y)
+{
+    if (!c || !K || !P || !X || !Y || n_seq == 0) return blb_fail(BLB_ERR_ARG, "null argument or empty batch");
+    return cp_run(c, K, P, X, n_seq, Y);
 }
 
 extern "C" int blb_matmul_cp(blb_ctx* c, const blb_keys* K, blb_ct* const* X, uint32_t nX, uint32_t m, uint32_t d,

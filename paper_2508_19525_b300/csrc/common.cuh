@@ -154,6 +154,7 @@ struct blb_ctx {
     uint64_t* d_cdt = nullptr;        // [19]
     uint32_t* d_kperm = nullptr;      // [N/2]: k_j = (5^j mod 2N - 1)/4
     int* d_flag = nullptr;            // device status word (encoding overflow)
+    uint32_t* d_status = nullptr;     // set by a kernel whose bounded wait expired
     // host-side constants
     std::vector<uint64_t> P_mod_q;              // [nQ]  P mod q_i
     std::vector<uint64_t> P_inv_mod_q;          // [nQ]  P^-1 mod q_i
@@ -235,7 +236,10 @@ struct blb_keys {
 struct blb_cp_plan {
     blb_ctx* ctx;
     uint32_t m, d, d_out, level, k, nX, nY, b1, G;
-    uint64_t* d_pts;   // [nY][G][nX][b1] plaintexts, each (level+1) x N, NTT domain
+    uint32_t KT, NEB;           // 16-term tiles, 16-output blocks of the (e, g) x (c, b) contraction
+    uint8_t* d_ptb;             // byte-sliced plaintext diagonals, NTT domain (layout in mac_tc.cu)
+    std::vector<uint8_t> nb;    // bytes per word of each limb
+    std::vector<uint64_t> off;  // byte offset of each limb's region in d_ptb
     size_t bytes;
 };
 
@@ -330,4 +334,6 @@ int decode_limb0(blb_ctx* ctx, const uint64_t* d_coef0, double scale, double* d_
 // matmul_cp plaintext diagonals for pts [first, first+count) of a plan (slot vectors)
 int cp_build_diagonals(blb_ctx* ctx, const blb_cp_plan* plan, const double* d_W, uint32_t first, uint32_t count,
                        double* d_z);
-int launch_cp_mac(blb_ctx* ctx, const blb_cp_plan* plan, const uint64_t* baby, uint64_t* T);
+int launch_cp_mac(blb_ctx* ctx, const blb_cp_plan* plan, const uint64_t* baby, uint64_t* T, uint32_t S);
+int cp_plan_layout(blb_ctx* ctx, blb_cp_plan* plan);
+int cp_plan_store_block(blb_ctx* ctx, blb_cp_plan* plan, const uint64_t* src, uint32_t eblk);

@@ -427,6 +427,8 @@ extern "C" int blb_ctx_create(const blb_params* params, void* stream, blb_ctx** 
         if ((rc = upload(c, &c->d_kperm, kp.data(), s))) return fail(rc);
         int zero = 0;
         if ((rc = upload(c, &c->d_flag, &zero, 1))) return fail(rc);
+        uint32_t uzero = 0;
+        if ((rc = upload(c, &c->d_status, &uzero, 1))) return fail(rc);
     }
 
     // discrete Gaussian table: floor(2^64 P(|e| <= k)), sigma 3.2, |e| <= 19
@@ -547,6 +549,7 @@ static void ctx_destroy(blb_ctx* c)
     dev_free(c, c->d_cdt, 19 * 8);
     dev_free(c, c->d_kperm, (size_t)c->N / 2 * 4);
     dev_free(c, c->d_flag, sizeof(int));
+    dev_free(c, c->d_status, sizeof(uint32_t));
     dev_free(c, c->d_modup_all, c->h_modup.size() * sizeof(ConvTable));
     dev_free(c, c->d_moddown, sizeof(ConvTable));
     dev_free(c, c->scratch, c->scratch_words * 8);
@@ -575,6 +578,12 @@ extern "C" int blb_ctx_sync(blb_ctx* c)
 {
     if (!c) return blb_fail(BLB_ERR_ARG, "null context");
     BLB_CUDA(cudaStreamSynchronize(c->stream));
+    uint32_t st = 0;
+    BLB_CUDA(cudaMemcpy(&st, c->d_status, sizeof(st), cudaMemcpyDeviceToHost));
+    if (st) {
+        BLB_CUDA(cudaMemset(c->d_status, 0, sizeof(st)));
+        return blb_fail(BLB_ERR_TIMEOUT, "a bounded device wait expired (plaintext product pipeline)");
+    }
     return BLB_OK;
 }
 

@@ -1,0 +1,520 @@
+// Plaintext-ciphertext multiply-accumulate of matmul_cp (the inner sums of the
+// BSGS diagonal method, Sec. 4.2 / Eq. 2) on the tensor cores.
+//
+// For one RNS limb i and one coefficient j (NTT domain, so every coefficient is
+// independent) the step computes, for S sequences,
+//
+//     T[s][eg][p][i][j] = sum_t  D[eg][t][i][j] * X[s][t][p][i][j]   (mod q_i)
+//
+// with eg = (e, g) the output/giant-step pair, t = (c, b) the input/baby-step
+// pair and p the ciphertext polynomial.  Per coefficient this is a dense
+// (outputs x terms) . (terms x 2S) contraction.  Both operands are split into
+// bytes, D = sum_a 2^{8a} D_a and X = sum_b 2^{8b} X_b, so that every byte
+// product is exact in fp16 and every 16-term block sum of byte products stays
+// below 2^24, exact in the fp32 accumulators of mma.sync.m16n8k16:
+//
+//     sum_t D X = sum_{a,b} 2^{8(a+b)} (sum_t D_a X_b).
+//
+// The byte planes of D are the GEMM's M dimension (rows (a, eg)), those of X
+// are part of N (columns (b, s, p)).  The epilogue converts the exact fp32
+// sums to integers, shifts them into 128-bit accumulators and reduces mod q_i
+// (Barrett); segments of at most 16 term tiles (4 for primes above 2^60) keep
+// both the fp32 sums and the 128-bit sums exact.
+//
+// Plan layout (bytes): for limb i a region at off[i]; inside it, for each
+// coefficient j, each 16-output block, each 16-term tile kt and each byte
+// plane a (nb_i = ceil(bits(q_i)/8) planes), one 256-byte mma A fragment: lane
+// l = 4 g + h holds 8 bytes for (row, col) = (g + 8 ((e >> 1) & 1),
+// 2 h + (e & 1) + 8 (e >> 2)), e = 0..7.  The items (coefficient, output
+// block) of one CTA are therefore one contiguous byte range, streamed into a
+// shared-memory ring by cp.async.bulk copies that a producer warp issues on
+// mbarriers; consumer warps read their fragments from the ring.
+#include "common.cuh"
+
+#include <cuda_fp16.h>
+
+namespace {
+
+constexpr int MAC_CONSUMERS = 4;  // consumer warps per CTA (plus one producer warp)
+constexpr int MAC_THREADS = 32 * (MAC_CONSUMERS + 1);
+constexpr int MAC_MAX_GROUP = 64;  // limbs per launch
+constexpr uint64_t MAC_WAIT_NS = 2000000000ull;  // bounded waits: 2 s
+
+struct MacArgs {
+    uint64_t* T;
+    const uint64_t* baby;
+    const uint8_t* ptb;
+    const uint64_t* q;
+    const uint64_t* bar;
+    uint32_t* status;
+    uint64_t nN, seq_words;
+    uint32_t N, terms, KT, neg, NEB, CT, kseg, R, jstride;
+    uint32_t limb[MAC_MAX_GROUP];
+    uint64_t off[MAC_MAX_GROUP];
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ uint64_t globaltimer()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// Wait for the phase of the given parity to complete; false after MAC_WAIT_NS.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
+{
+    uint64_t t0 = 0;
+    for (uint32_t it = 0;; it++) {
+        uint32_t ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+            : "=r"(ok)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if (it == 0) t0 = globaltimer();
+        else if ((it & 63) == 0 && globaltimer() - t0 > MAC_WAIT_NS) return false;
+    }
+}
+
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void consumer_sync()
+{
+    asm volatile("bar.sync 1, %0;" ::"n"(32 * MAC_CONSUMERS) : "memory");
+}
+
+// 8 bytes -> 4 registers of fp16 pairs (low half = lower byte): 0x64XX is the
+// fp16 number 1024 + XX, so one byte permute and one subtraction per pair.
+__device__ __forceinline__ void bytes_to_f16x2(uint2 v, uint32_t (&f)[4])
+{
+    const uint32_t k = 0x64646464u;
+    uint32_t h[4] = {__byte_perm(v.x, k, 0x5140), __byte_perm(v.x, k, 0x5342), __byte_perm(v.y, k, 0x5140),
+                     __byte_perm(v.y, k, 0x5342)};
+    const __half2 off = __halves2half2(__ushort_as_half(0x6400), __ushort_as_half(0x6400));
+#pragma unroll
+    for (int r = 0; r < 4; r++) {
+        __half2 x = *reinterpret_cast<__half2*>(&h[r]);
+        x = __hsub2(x, off);
+        f[r] = *reinterpret_cast<uint32_t*>(&x);
+    }
+}
+
+__device__ __forceinline__ void mma16816(float (&c)[4], const uint32_t (&a)[4], uint2 b)
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b.x), "r"(b.y));
+}
+
+// (hi:lo) += v 2^sh for v < 2^32, sh < 128 (the caller guarantees no overflow)
+__device__ __forceinline__ void add_shl(uint64_t& lo, uint64_t& hi, uint64_t v, uint32_t sh)
+{
+    uint64_t l, h;
+    if (sh < 64) {
+        l = v << sh;
+        h = sh ? v >> (64 - sh) : 0;
+    } else {
+        l = 0;
+        h = v << (sh - 64);
+    }
+    lo += l;
+    hi += h + (lo < l);
+}
+
+__device__ __forceinline__ uint64_t reduce128(uint64_t lo, uint64_t hi, uint64_t q, uint64_t r0, uint64_t r1)
+{
+    const uint64_t h = barrett128(hi, 0, q, r0, r1);  // hi mod q, so (h:lo) < q 2^64
+    return barrett128(lo, h, q, r0, r1);
+}
+
+__device__ __forceinline__ uint64_t add_mod(uint64_t a, uint64_t b, uint64_t q)
+{
+    const uint64_t s = a + b;
+    return s >= q ? s - q : s;
+}
+
+// byte planes of D accumulated together: all of them when the accumulators fit
+// 64 registers, else the largest divisor of NB that does
+template <int NB, int NT>
+constexpr int plane_group()
+{
+    for (int g = NB; g >= 1; g--)
+        if (NB % g == 0 && g * NT * 4 <= 64) return g;
+    return 1;
+}
+
+template <int S, int NB>
+__global__ void __launch_bounds__(MAC_THREADS) k_cp_mac_tc(const __grid_constant__ MacArgs A)
+{
+    constexpr int SP = 2 * S;                 // (sequence, polynomial) columns per byte plane of X
+    constexpr int NT = (NB * SP + 7) / 8;     // n8 tiles
+    constexpr int SLOTS = SP >= 8 ? SP / 4 : 2;
+    constexpr int AG = plane_group<NB, NT>();
+    extern __shared__ __align__(128) uint8_t smem[];
+    const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t gi = blockIdx.y, i = A.limb[gi];
+    const uint32_t j0 = blockIdx.x * A.CT;
+    const uint32_t item_bytes = A.KT * NB * 256;
+    const uint32_t items = A.CT * A.NEB;
+    const uint32_t R = A.R;
+    uint8_t* Bs = smem;
+    uint8_t* ring = smem + (((size_t)A.CT * A.jstride + 127) & ~(size_t)127);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(ring + (size_t)R * item_bytes);
+    const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + R), ring0 = smem_u32(ring);
+
+    if (threadIdx.x == 0) {
+        for (uint32_t r = 0; r < R; r++) {
+            mbar_init(full0 + 8 * r, 1);
+            mbar_init(empty0 + 8 * r, 1);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+
+    if (warp == MAC_CONSUMERS) {  // producer: stream the CTA's contiguous byte range
+        if (lane == 0) {
+            const uint8_t* src = A.ptb + A.off[gi] + (size_t)j0 * A.NEB * item_bytes;
+            uint32_t issued = 0;
+            for (uint32_t k = 0; k < items; k++) {
+                const uint32_t st = k % R;
+                if (k >= R && !mbar_wait(empty0 + 8 * st, ((k / R) - 1) & 1)) {
+                    atomicExch(A.status, 1u);
+                    break;
+                }
+                mbar_expect_tx(full0 + 8 * st, item_bytes);
+                bulk_g2s(ring0 + st * item_bytes, src + (size_t)k * item_bytes, item_bytes, full0 + 8 * st);
+                issued = k + 1;
+            }
+            // shared memory must outlive every copy started here
+            for (uint32_t k = issued > R ? issued - R : 0; k < issued; k++)
+                if (!mbar_wait(full0 + 8 * (k % R), (k / R) & 1)) atomicExch(A.status, 1u);
+        }
+        return;
+    }
+
+    // ---- consumers: X's byte planes for the CTA's coefficients, as mma B fragments
+    {
+        const uint32_t zero_words = (A.CT * A.jstride) / 16;
+        for (uint32_t x = threadIdx.x; x < zero_words; x += 32 * MAC_CONSUMERS)
+            reinterpret_cast<uint4*>(Bs)[x] = make_uint4(0, 0, 0, 0);
+        consumer_sync();
+        const uint32_t nwords = A.CT * S * A.terms * 2;
+        for (uint32_t x = threadIdx.x; x < nwords; x += 32 * MAC_CONSUMERS) {
+            const uint32_t jj = x % A.CT;
+            uint32_t r = x / A.CT;
+            const uint32_t p = r & 1;
+            r >>= 1;
+            const uint32_t t = r % A.terms, s = r / A.terms;
+            const uint64_t w = A.baby[s * A.seq_words + (size_t)t * 2 * A.nN + p * A.nN + (size_t)i * A.N + j0 + jj];
+            const uint32_t sp = 2 * s + p, kt = t >> 4, kr = t & 15;
+            // element (k = kr, n) of a B fragment: lane 4 (n % 8) + (kr % 8) / 2, register kr / 8, half kr % 2
+            uint8_t* base = Bs + (size_t)jj * A.jstride + (size_t)kt * NT * 256 + ((kr & 7) >> 1) * 8 + (kr >> 3) * 4 +
+                            (kr & 1) * 2;
+#pragma unroll
+            for (int b = 0; b < NB; b++) {
+                const uint32_t col = b * SP + sp;
+                *reinterpret_cast<unsigned short*>(base + (col >> 3) * 256 + (col & 7) * 32) =
+                    __half_as_ushort(__uint2half_rn((uint32_t)(w >> (8 * b)) & 0xFFu));
+            }
+        }
+        consumer_sync();
+    }
+
+    const uint32_t g8 = lane >> 2, h4 = lane & 3;
+    const uint64_t q = A.q[i], r0 = A.bar[2 * i], r1 = A.bar[2 * i + 1];
+    bool ok = true;
+    for (uint32_t k = warp; k < items; k += MAC_CONSUMERS) {
+        const uint32_t st = k % R;
+        if (!mbar_wait(full0 + 8 * st, (k / R) & 1)) {
+            atomicExch(A.status, 1u);
+            ok = false;
+            break;
+        }
+        const uint32_t jj = k / A.NEB, eblk = k % A.NEB;
+        const uint8_t* As = ring + (size_t)st * item_bytes + lane * 8;
+        const uint8_t* Bj = Bs + (size_t)jj * A.jstride + lane * 8;
+        uint64_t fin[2][SLOTS];
+#pragma unroll
+        for (int r = 0; r < 2; r++)
+#pragma unroll
+            for (int u = 0; u < SLOTS; u++) fin[r][u] = 0;
+        for (uint32_t ks = 0; ks < A.KT; ks += A.kseg) {
+            const uint32_t ke = min(A.KT, ks + A.kseg);
+            uint64_t lo[2][SLOTS], hi[2][SLOTS];
+#pragma unroll
+            for (int r = 0; r < 2; r++)
+#pragma unroll
+                for (int u = 0; u < SLOTS; u++) lo[r][u] = hi[r][u] = 0;
+#pragma unroll
+            for (int a0 = 0; a0 < NB; a0 += AG) {
+                float acc[AG][NT][4];
+#pragma unroll
+                for (int a = 0; a < AG; a++)
+#pragma unroll
+                    for (int nt = 0; nt < NT; nt++)
+#pragma unroll
+                        for (int e = 0; e < 4; e++) acc[a][nt][e] = 0.f;
+                for (uint32_t kt = ks; kt < ke; kt++) {
+                    const uint8_t* Bk = Bj + (size_t)kt * NT * 256;
+                    if (AG > 1) {  // B fragments reused by every plane of the group
+                        uint2 bf[NT];
+#pragma unroll
+                        for (int nt = 0; nt < NT; nt++) bf[nt] = *reinterpret_cast<const uint2*>(Bk + nt * 256);
+#pragma unroll
+                        for (int a = 0; a < AG; a++) {
+                            uint32_t af[4];
+                            bytes_to_f16x2(*reinterpret_cast<const uint2*>(As + (size_t)(kt * NB + a0 + a) * 256), af);
+#pragma unroll
+                            for (int nt = 0; nt < NT; nt++) mma16816(acc[a][nt], af, bf[nt]);
+                        }
+                    } else {
+                        uint32_t af[4];
+                        bytes_to_f16x2(*reinterpret_cast<const uint2*>(As + (size_t)(kt * NB + a0) * 256), af);
+#pragma unroll
+                        for (int nt = 0; nt < NT; nt++)
+                            mma16816(acc[0][nt], af, *reinterpret_cast<const uint2*>(Bk + nt * 256));
+                    }
+                }
+                // fold: column c = 8 nt + 2 h4 + (e & 1) holds byte plane b = c / SP of
+                // (sequence, polynomial) c % SP; rows g8 (e < 2) and g8 + 8
+#pragma unroll
+                for (int a = 0; a < AG; a++)
+#pragma unroll
+                    for (int nt = 0; nt < NT; nt++)
+#pragma unroll
+                        for (int e = 0; e < 4; e++) {
+                            const int r = e >> 1, h = e & 1;
+                            const uint64_t v = __float2uint_rz(acc[a][nt][e]);
+                            if (SP >= 8) {
+                                const int u = (nt % (SP / 8)) * 2 + h, b = nt / (SP / 8);
+                                add_shl(lo[r][u], hi[r][u], v, 8 * (a0 + a + b));
+                            } else {
+                                const uint32_t b = (nt * 8 + 2 * h4 + h) / SP;
+                                if (b < NB) add_shl(lo[r][h], hi[r][h], v, 8 * (a0 + a + b));
+                            }
+                        }
+            }
+#pragma unroll
+            for (int r = 0; r < 2; r++)
+#pragma unroll
+                for (int u = 0; u < SLOTS; u++) fin[r][u] = add_mod(fin[r][u], reduce128(lo[r][u], hi[r][u], q, r0, r1), q);
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(empty0 + 8 * st);
+
+        // partial sums of the byte planes that other lanes of the quad hold
+        if (SP < 8) {
+#pragma unroll
+            for (int r = 0; r < 2; r++)
+#pragma unroll
+                for (int u = 0; u < SLOTS; u++) {
+                    if (SP == 2) fin[r][u] = add_mod(fin[r][u], __shfl_xor_sync(0xffffffffu, fin[r][u], 1), q);
+                    fin[r][u] = add_mod(fin[r][u], __shfl_xor_sync(0xffffffffu, fin[r][u], 2), q);
+                }
+        }
+        const size_t jcol = (size_t)i * A.N + j0 + jj;
+        auto store = [&](uint32_t row, uint32_t sp, uint64_t v) {
+            const uint32_t eg = eblk * 16 + row;
+            if (eg < A.neg) A.T[((size_t)((sp >> 1) * A.neg + eg) * 2 + (sp & 1)) * A.nN + jcol] = v;
+        };
+        if (SP == 2) {
+            const uint32_t r = h4 >> 1, h = h4 & 1;
+            store(g8 + 8 * r, h, r ? (h ? fin[1][1] : fin[1][0]) : (h ? fin[0][1] : fin[0][0]));
+        } else if (SP == 4) {
+            const uint32_t r = h4 >> 1;
+#pragma unroll
+            for (int h = 0; h < 2; h++) store(g8 + 8 * r, 2 * (h4 & 1) + h, r ? fin[1][h] : fin[0][h]);
+        } else {
+#pragma unroll
+            for (int r = 0; r < 2; r++)
+#pragma unroll
+                for (int u = 0; u < SLOTS; u++) store(g8 + 8 * r, 8 * (u >> 1) + 2 * h4 + (u & 1), fin[r][u]);
+        }
+    }
+    (void)ok;
+}
+
+// one thread per 8-byte fragment word of one output block: ((j KT + kt) nb + a) 32 + lane
+__global__ void k_cp_bytes(uint8_t* __restrict__ dst, const uint64_t* __restrict__ src, uint32_t i, uint32_t N,
+                           uint64_t nN, uint32_t terms, uint32_t rows, uint32_t KT, uint32_t NEB, uint32_t nb,
+                           uint32_t eblk)
+{
+    const uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (uint64_t)N * KT * nb * 32) return;
+    const uint32_t lane = idx & 31;
+    uint64_t r = idx >> 5;
+    const uint32_t a = r % nb;
+    r /= nb;
+    const uint32_t kt = r % KT, j = (uint32_t)(r / KT);
+    const uint32_t g = lane >> 2, h = lane & 3;
+    uint64_t out = 0;
+#pragma unroll
+    for (int e = 0; e < 8; e++) {
+        const uint32_t row = g + 8 * ((e >> 1) & 1), t = kt * 16 + 2 * h + (e & 1) + 8 * (e >> 2);
+        if (row < rows && t < terms)
+            out |= ((src[((size_t)row * terms + t) * nN + (size_t)i * N + j] >> (8 * a)) & 0xFFull) << (8 * e);
+    }
+    *reinterpret_cast<uint64_t*>(dst + ((((size_t)j * NEB + eblk) * KT + kt) * nb + a) * 256 + lane * 8) = out;
+}
+
+template <int S, int NB>
+int launch_group(blb_ctx* c, MacArgs& a, uint32_t nlimbs)
+{
+    constexpr int SP = 2 * S, NT = (NB * SP + 7) / 8;
+    const uint32_t item_bytes = a.KT * NB * 256;
+    a.jstride = a.KT * NT * 256 + 16;
+    a.CT = 16;
+    while (a.CT > 1 && (size_t)a.CT * a.jstride > (48u << 10)) a.CT >>= 1;
+    const uint32_t items = a.CT * a.NEB;
+    // ring depth: either every item has its own stage or the depth is a multiple
+    // of the consumer count, so that successive fills of a stage go to the same
+    // warp and a parity wait never sees the phase before the one it wants
+    a.R = std::min<uint32_t>(2 * MAC_CONSUMERS, items);
+    size_t smem = (((size_t)a.CT * a.jstride + 127) & ~(size_t)127) + (size_t)a.R * item_bytes + 16 * a.R;
+    if (smem > (200u << 10)) {
+        a.R = MAC_CONSUMERS < items ? MAC_CONSUMERS : items;
+        smem = (((size_t)a.CT * a.jstride + 127) & ~(size_t)127) + (size_t)a.R * item_bytes + 16 * a.R;
+    }
+    if (smem > (227u << 10)) return blb_fail(BLB_ERR_ARG, "plaintext tile too large for shared memory");
+    static bool attr = false;
+    if (!attr) {
+        BLB_CUDA(cudaFuncSetAttribute(k_cp_mac_tc<S, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 << 10));
+        attr = true;
+    }
+    dim3 grid(c->N / a.CT, nlimbs);
+    k_cp_mac_tc<S, NB><<<grid, MAC_THREADS, smem, c->stream>>>(a);
+    BLB_LAUNCHED();
+    return BLB_OK;
+}
+
+template <int S>
+int launch_nb(blb_ctx* c, MacArgs& a, uint32_t nb, uint32_t nlimbs)
+{
+    switch (nb) {
+    case 3: return launch_group<S, 3>(c, a, nlimbs);
+    case 4: return launch_group<S, 4>(c, a, nlimbs);
+    case 5: return launch_group<S, 5>(c, a, nlimbs);
+    case 6: return launch_group<S, 6>(c, a, nlimbs);
+    case 7: return launch_group<S, 7>(c, a, nlimbs);
+    case 8: return launch_group<S, 8>(c, a, nlimbs);
+    default: return blb_fail(BLB_ERR_PARAM, "prime size outside 17..64 bits for the tensor-core product");
+    }
+}
+
+}  // namespace
+
+uint32_t cp_word_bytes(uint64_t q)
+{
+    uint32_t bits = 64 - __builtin_clzll(q);
+    return (bits + 7) / 8;
+}
+
+int cp_plan_layout(blb_ctx* c, blb_cp_plan* P)
+{
+    const uint32_t n = P->level + 1;
+    P->KT = (P->nX * P->b1 + 15) / 16;
+    P->NEB = (P->nY * P->G + 15) / 16;
+    P->nb.assign(n, 0);
+    P->off.assign(n, 0);
+    uint64_t off = 0;
+    for (uint32_t i = 0; i < n; i++) {
+        P->nb[i] = (uint8_t)cp_word_bytes(c->q[i]);
+        if (P->nb[i] < 3) return blb_fail(BLB_ERR_PARAM, "primes below 2^17 are not supported by matmul_cp");
+        P->off[i] = off;
+        off += (uint64_t)c->N * P->NEB * P->KT * P->nb[i] * 256;
+    }
+    P->bytes = off;
+    return BLB_OK;
+}
+
+int cp_plan_store_block(blb_ctx* c, blb_cp_plan* P, const uint64_t* src, uint32_t eblk)
+{
+    const uint32_t n = P->level + 1, terms = P->nX * P->b1, neg = P->nY * P->G;
+    const uint32_t rows = std::min<uint32_t>(16, neg - eblk * 16);
+    for (uint32_t i = 0; i < n; i++) {
+        const uint64_t total = (uint64_t)c->N * P->KT * P->nb[i] * 32;
+        k_cp_bytes<<<(unsigned)((total + 255) / 256), 256, 0, c->stream>>>(P->d_ptb + P->off[i], src, i, c->N,
+                                                                         (uint64_t)n * c->N, terms, rows, P->KT,
+                                                                         P->NEB, P->nb[i], eblk);
+        BLB_LAUNCHED();
+    }
+    return BLB_OK;
+}
+
+// baby: [S][nX][b1] ciphertexts; T: [S][nY][G] ciphertexts (level of the plan)
+int launch_cp_mac(blb_ctx* c, const blb_cp_plan* P, const uint64_t* baby, uint64_t* T, uint32_t S)
+{
+    const uint32_t n = P->level + 1, N = c->N;
+    const uint64_t terms = (uint64_t)P->nX * P->b1, neg = (uint64_t)P->nY * P->G;
+    // algorithmic bytes: the byte-sliced plaintexts once, the baby-step
+    // ciphertexts once, the (e, g) partial sums written once
+    ProfScope prof(c, "cp_mac", P->bytes + (S * terms * 2 * n + S * neg * 2 * n) * N * 8);
+    MacArgs a{};
+    a.T = T;
+    a.baby = baby;
+    a.ptb = P->d_ptb;
+    a.q = c->d_q;
+    a.bar = c->d_bar;
+    a.status = c->d_status;
+    a.nN = (uint64_t)n * N;
+    a.seq_words = terms * 2 * a.nN;
+    a.N = N;
+    a.terms = (uint32_t)terms;
+    a.KT = P->KT;
+    a.neg = (uint32_t)neg;
+    a.NEB = P->NEB;
+    // limbs grouped by bytes per word, one launch per group
+    for (uint32_t nb = 3; nb <= 8; nb++) {
+        uint32_t cnt = 0;
+        bool big = false;
+        for (uint32_t i = 0; i < n; i++)
+            if (P->nb[i] == nb) {
+                if (cnt == MAC_MAX_GROUP) return blb_fail(BLB_ERR_PARAM, "too many limbs");
+                a.limb[cnt] = i;
+                a.off[cnt] = P->off[i];
+                big |= c->q[i] >= (1ull << 60);
+                cnt++;
+            }
+        if (!cnt) continue;
+        // 16 tiles keep 16 x 16 x 255^2 < 2^24; primes above 2^60 need 64 terms x q^2 < 2^128
+        a.kseg = big ? 4 : 16;
+        int rc;
+        switch (S) {
+        case 1: rc = launch_nb<1>(c, a, nb, cnt); break;
+        case 2: rc = launch_nb<2>(c, a, nb, cnt); break;
+        case 4: rc = launch_nb<4>(c, a, nb, cnt); break;
+        case 8: rc = launch_nb<8>(c, a, nb, cnt); break;
+        default: return blb_fail(BLB_ERR_ARG, "batch of sequences must be 1, 2, 4 or 8 per MAC launch");
+        }
+        if (rc) return rc;
+    }
+    return BLB_OK;
+}

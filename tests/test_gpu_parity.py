@@ -247,3 +247,24 @@ def test_error_paths():
     with pytest.raises(blb.BlbError) as e:
         ctx.matmul_cp(keys, [ct], 32, 64, np.zeros((64, 64)), 64, 8)
     assert e.value.code == blb.ERR_NO_KEY
+
+
+def test_matmul_cp_batch_equals_per_sequence():
+    """The batched form (one plaintext stream for several sequences) gives the
+    same limbs as one call per sequence; 5 sequences exercise the 4 + 1 split."""
+    prm, m, d, d_out, b1 = wl.SMALL, 64, 80, 40, 4
+    ctx = make_ctx(prm)
+    k = ctx.N // 2 // m
+    level = ctx.nQ - 1
+    keys = ctx.keygen(SEED, cp_rotations(m, b1, k // b1))
+    plan = ctx.cp_plan(m, d, wl.cp_operands(m, d, d_out, seed=1)[1], d_out, level, b1)
+    seqs = []
+    for s in range(5):
+        X = wl.cp_operands(m, d, d_out, seed=10 + s)[0]
+        seqs.append([ctx.encrypt(keys, ctx.encode(z, level), 10 * s + c)
+                     for c, z in enumerate(pack_cols(X, m, k, (d + k - 1) // k))])
+    batched = ctx.matmul_cp_batch(keys, plan, seqs)
+    for s, X in enumerate(seqs):
+        single = ctx.matmul_cp_plan(keys, plan, X)
+        for a, b in zip(batched[s], single):
+            assert np.array_equal(ctx.ct_export(a), ctx.ct_export(b)), s
