@@ -521,11 +521,12 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def ncu_case():
+def ncu_case(seqs=1):
     """Small profiling case of the same kernels for `ncu --profile-from-start off`:
-    N = 2^15, 8 primes, matmul_cp 128x256 @ 256x256 (1 GiB of plaintext diagonals,
-    larger than L2); one matmul_cp bracketed by cudaProfilerStart/Stop after a
-    warm-up run."""
+    N = 2^15, 8 primes, matmul_cp 128x768 @ 768x256 (96 plaintext terms per
+    output as in the BERT-base products, 2.2 GB of byte-sliced diagonals, larger
+    than L2) for `seqs` sequences; one call bracketed by cudaProfilerStart/Stop
+    after a warm-up call."""
     import torch
     from paper_2508_19525_b300 import blb
     from paper_2508_19525_b300 import workloads as wl
@@ -534,16 +535,20 @@ def ncu_case():
     k = ctx.N // 2 // M
     rots = [b * M for b in range(1, B1)] + [g * B1 * M for g in range(1, k // B1)]
     keys = ctx.keygen(0, rots)
-    X, W = wl.cp_operands(M, 256, 256, seed=1)
-    plan = ctx.cp_plan(M, 256, W, 256, LEVEL, B1)
-    cts = [ctx.encrypt(keys, ctx.encode(z, LEVEL), i) for i, z in enumerate(pack_columns(X, M, k))]
-    ctx.matmul_cp_plan(keys, plan, cts)
+    X, W = wl.cp_operands(M, D, 256, seed=1)
+    plan = ctx.cp_plan(M, D, W, 256, LEVEL, B1)
+    seq = [[ctx.encrypt(keys, ctx.encode(z, LEVEL), 100 * s + i) for i, z in enumerate(pack_columns(X, M, k))]
+           for s in range(seqs)]
+    run = (lambda: ctx.matmul_cp_plan(keys, plan, seq[0])) if seqs == 1 else \
+        (lambda: ctx.matmul_cp_batch(keys, plan, seq))
+    run()
     ctx.sync()
     torch.cuda.profiler.start()
-    ctx.matmul_cp_plan(keys, plan, cts)
+    run()
     ctx.sync()
     torch.cuda.profiler.stop()
-    print(json.dumps({"ncu_case": "matmul_cp 128x256 @ 256x256, N=2^15, level 7", "plan": plan.info()}))
+    print(json.dumps({"ncu_case": f"matmul_cp 128x768 @ 768x256, N=2^15, level 7, {seqs} sequence(s)",
+                      "plan": plan.info()}))
 
 
 def main():
@@ -556,12 +561,13 @@ def main():
     ap.add_argument("--cpu-rotations", type=int, default=6)
     ap.add_argument("--cpu-products", type=int, default=48)
     ap.add_argument("--ncu-case", action="store_true", help="run the small profiling case and exit")
+    ap.add_argument("--ncu-seqs", type=int, default=1, help="sequences in the profiling case")
     ap.add_argument("--batch", type=int, default=8, help="sequences per batched step (1 = skip)")
     ap.add_argument("--no-attention", dest="attention", action="store_false",
                     help="skip the matmul_cc attention measurement")
     args = ap.parse_args()
     if args.ncu_case:
-        return ncu_case()
+        return ncu_case(args.ncu_seqs)
     args.cpu_sample = (args.cpu_rotations, args.cpu_products)
     if args.impl == "reference":
         run_reference(args)

@@ -16,27 +16,36 @@
 //     sum_t D X = sum_{a,b} 2^{8(a+b)} (sum_t D_a X_b).
 //
 // The byte planes of D are the GEMM's M dimension (rows (a, eg)), those of X
-// are part of N (columns (b, s, p)).  The epilogue converts the exact fp32
-// sums to integers, shifts them into 128-bit accumulators and reduces mod q_i
-// (Barrett); segments of at most 16 term tiles (4 for primes above 2^60) keep
-// both the fp32 sums and the 128-bit sums exact.
+// are part of N (columns (b, s, p)).  The epilogue reads the exact fp32 sums
+// back as integers, adds them with their shifts 2^{8(a+b)} into four 64-bit
+// columns of weight 2^{32c} (no carries on the way), assembles the 128-bit sum
+// and reduces it mod q_i (Barrett).  Segments of at most 8 term tiles (4 for
+// primes above 2^60) keep the fp32 sums below 2^23 and the 128-bit sums exact.
 //
 // Plan layout (bytes): for limb i a region at off[i]; inside it, for each
 // coefficient j, each 16-output block, each 16-term tile kt and each byte
 // plane a (nb_i = ceil(bits(q_i)/8) planes), one 256-byte mma A fragment: lane
 // l = 4 g + h holds 8 bytes for (row, col) = (g + 8 ((e >> 1) & 1),
 // 2 h + (e & 1) + 8 (e >> 2)), e = 0..7.  The items (coefficient, output
-// block) of one CTA are therefore one contiguous byte range, streamed into a
-// shared-memory ring by cp.async.bulk copies that a producer warp issues on
-// mbarriers; consumer warps read their fragments from the ring.
+// block) of a tile of CT coefficients are therefore one contiguous byte range.
+//
+// Persistent CTAs (as many as fit on the SMs) walk the tiles.  A builder warp
+// turns each tile's baby-step ciphertexts into mma B fragments, one tile ahead,
+// in one of two shared buffers; a streamer warp copies the tiles' plaintext
+// ranges into a ring of shared-memory stages with cp.async.bulk copies
+// completed on mbarriers, without pausing between tiles; the consumer warps
+// take the items in turn, hand each stage back right after its last mma, and
+// run the epilogue while the next copies land.  Every wait is
+// bounded: an expired wait sets a CTA abort word that ends the other waits,
+// and the status word the host reads in blb_ctx_sync.
 #include "common.cuh"
 
 #include <cuda_fp16.h>
 
 namespace {
 
-constexpr int MAC_CONSUMERS = 4;  // consumer warps per CTA (plus one producer warp)
-constexpr int MAC_THREADS = 32 * (MAC_CONSUMERS + 1);
+constexpr int MAC_CONSUMERS = 4;  // consumer warps per CTA, plus a plaintext streamer and a B builder
+constexpr int MAC_THREADS = 32 * (MAC_CONSUMERS + 2);
 constexpr int MAC_MAX_GROUP = 64;  // limbs per launch
 constexpr uint64_t MAC_WAIT_NS = 2000000000ull;  // bounded waits: 2 s
 
@@ -49,6 +58,7 @@ struct MacArgs {
     uint32_t* status;
     uint64_t nN, seq_words;
     uint32_t N, terms, KT, neg, NEB, CT, kseg, R, jstride;
+    uint32_t tiles_per_limb, tiles;  // coefficient tiles of CT per limb, over all limbs of the launch
     uint32_t limb[MAC_MAX_GROUP];
     uint64_t off[MAC_MAX_GROUP];
 };
@@ -80,8 +90,10 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar)
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
-// Wait for the phase of the given parity to complete; false after MAC_WAIT_NS.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
+// Wait for the phase of the given parity to complete.  Returns false after
+// MAC_WAIT_NS, or as soon as another thread of the CTA has given up (abort
+// word in shared memory), so that one expired wait ends the whole CTA quickly.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile uint32_t* abort)
 {
     uint64_t t0 = 0;
     for (uint32_t it = 0;; it++) {
@@ -92,8 +104,14 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
             : "r"(bar), "r"(parity)
             : "memory");
         if (ok) return true;
-        if (it == 0) t0 = globaltimer();
-        else if ((it & 63) == 0 && globaltimer() - t0 > MAC_WAIT_NS) return false;
+        if (it == 0) {
+            t0 = globaltimer();
+        } else if ((it & 63) == 0) {
+            if (*abort || globaltimer() - t0 > MAC_WAIT_NS) {
+                *abort = 1;
+                return false;
+            }
+        }
     }
 }
 
@@ -102,11 +120,6 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
                  "l"(src), "r"(bytes), "r"(bar)
                  : "memory");
-}
-
-__device__ __forceinline__ void consumer_sync()
-{
-    asm volatile("bar.sync 1, %0;" ::"n"(32 * MAC_CONSUMERS) : "memory");
 }
 
 // 8 bytes -> 4 registers of fp16 pairs (low half = lower byte): 0x64XX is the
@@ -134,21 +147,6 @@ __device__ __forceinline__ void mma16816(float (&c)[4], const uint32_t (&a)[4], 
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b.x), "r"(b.y));
 }
 
-// (hi:lo) += v 2^sh for v < 2^32, sh < 128 (the caller guarantees no overflow)
-__device__ __forceinline__ void add_shl(uint64_t& lo, uint64_t& hi, uint64_t v, uint32_t sh)
-{
-    uint64_t l, h;
-    if (sh < 64) {
-        l = v << sh;
-        h = sh ? v >> (64 - sh) : 0;
-    } else {
-        l = 0;
-        h = v << (sh - 64);
-    }
-    lo += l;
-    hi += h + (lo < l);
-}
-
 __device__ __forceinline__ uint64_t reduce128(uint64_t lo, uint64_t hi, uint64_t q, uint64_t r0, uint64_t r1)
 {
     const uint64_t h = barrett128(hi, 0, q, r0, r1);  // hi mod q, so (h:lo) < q 2^64
@@ -171,6 +169,13 @@ constexpr int plane_group()
     return 1;
 }
 
+// exact fp32 integer x < 2^23 -> uint32: x + 2^23 has exponent 23, so its
+// mantissa field is x (one add and one mask instead of a conversion)
+__device__ __forceinline__ uint32_t f32_int(float x)
+{
+    return __float_as_uint(x + 8388608.0f) & 0x7FFFFFu;
+}
+
 template <int S, int NB>
 __global__ void __launch_bounds__(MAC_THREADS) k_cp_mac_tc(const __grid_constant__ MacArgs A)
 {
@@ -180,186 +185,248 @@ __global__ void __launch_bounds__(MAC_THREADS) k_cp_mac_tc(const __grid_constant
     constexpr int AG = plane_group<NB, NT>();
     extern __shared__ __align__(128) uint8_t smem[];
     const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const uint32_t gi = blockIdx.y, i = A.limb[gi];
-    const uint32_t j0 = blockIdx.x * A.CT;
     const uint32_t item_bytes = A.KT * NB * 256;
-    const uint32_t items = A.CT * A.NEB;
+    const uint32_t IPT = A.CT * A.NEB;  // items (coefficient, output block) per tile
     const uint32_t R = A.R;
-    uint8_t* Bs = smem;
-    uint8_t* ring = smem + (((size_t)A.CT * A.jstride + 127) & ~(size_t)127);
+    const size_t bbuf = ((size_t)A.CT * A.jstride + 127) & ~(size_t)127;
+    uint8_t* Bs = smem;  // two buffers of B fragments
+    uint8_t* ring = smem + 2 * bbuf;
     uint64_t* bars = reinterpret_cast<uint64_t*>(ring + (size_t)R * item_bytes);
-    const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + R), ring0 = smem_u32(ring);
+    volatile uint32_t* abort = reinterpret_cast<volatile uint32_t*>(bars + 2 * R + 4);
+    const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + R), bfull0 = smem_u32(bars + 2 * R),
+                   bempty0 = smem_u32(bars + 2 * R + 2), ring0 = smem_u32(ring);
 
+    // B padding (terms beyond the last term, columns beyond NB SP) stays zero
+    for (uint32_t x = threadIdx.x; x < 2 * bbuf / 16; x += MAC_THREADS)
+        reinterpret_cast<uint4*>(Bs)[x] = make_uint4(0, 0, 0, 0);
     if (threadIdx.x == 0) {
         for (uint32_t r = 0; r < R; r++) {
             mbar_init(full0 + 8 * r, 1);
             mbar_init(empty0 + 8 * r, 1);
         }
+        for (uint32_t r = 0; r < 2; r++) {
+            mbar_init(bfull0 + 8 * r, 1);
+            mbar_init(bempty0 + 8 * r, MAC_CONSUMERS);
+        }
+        *abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
 
-    if (warp == MAC_CONSUMERS) {  // producer: stream the CTA's contiguous byte range
-        if (lane == 0) {
-            const uint8_t* src = A.ptb + A.off[gi] + (size_t)j0 * A.NEB * item_bytes;
-            uint32_t issued = 0;
-            for (uint32_t k = 0; k < items; k++) {
-                const uint32_t st = k % R;
-                if (k >= R && !mbar_wait(empty0 + 8 * st, ((k / R) - 1) & 1)) {
-                    atomicExch(A.status, 1u);
-                    break;
+    if (warp == MAC_CONSUMERS + 1) {
+        // ---- B builder: per tile, X's byte planes as mma B fragments, one tile
+        // ahead of the consumers (two buffers)
+        for (uint32_t lt = 0, tau = blockIdx.x; tau < A.tiles; lt++, tau += gridDim.x) {
+            const uint32_t buf = lt & 1, gi = tau / A.tiles_per_limb, i = A.limb[gi];
+            const uint32_t j0 = (tau % A.tiles_per_limb) * A.CT;
+            if (lt >= 2 && !mbar_wait(bempty0 + 8 * buf, ((lt >> 1) - 1) & 1, abort)) break;
+            uint8_t* Bt = Bs + buf * bbuf;
+            // lane -> coefficient jj = lane % CT and a stride of 32 / CT over the
+            // rows (s, term pair, p); baby-step row r = (s terms + t) 2 + p lives
+            // at r nN, and terms 2 tp, 2 tp + 1 share one fp16 pair per byte plane
+            const uint32_t jj = lane % A.CT, rstep = 32 / A.CT, TP2 = ((A.terms + 1) >> 1) * 2;
+            const uint64_t* col0 = A.baby + (size_t)i * A.N + j0 + jj;
+            uint8_t* Bjj = Bt + (size_t)jj * A.jstride;
+#pragma unroll
+            for (int s = 0; s < S; s++) {
+                constexpr int U = 8;
+                for (uint32_t v0 = lane / A.CT; v0 < TP2; v0 += U * rstep) {
+                    uint2 w0[U], w1[U];
+#pragma unroll
+                    for (int u = 0; u < U; u++) {
+                        const uint32_t v = v0 + u * rstep, p = v & 1, t = (v >> 1) * 2;
+                        const size_t r = ((size_t)s * A.terms + t) * 2 + p;
+                        w0[u] = w1[u] = make_uint2(0, 0);
+                        if (v < TP2) {
+                            w0[u] = *reinterpret_cast<const uint2*>(col0 + r * A.nN);
+                            if (t + 1 < A.terms) w1[u] = *reinterpret_cast<const uint2*>(col0 + (r + 2) * A.nN);
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < U; u++) {
+                        const uint32_t v = v0 + u * rstep;
+                        if (v >= TP2) break;
+                        const uint32_t p = v & 1, t = (v >> 1) * 2, sp = 2 * s + p, kr = t & 15;
+                        uint8_t* base = Bjj + (size_t)(t >> 4) * NT * 256 + ((kr & 7) >> 1) * 8 + (kr >> 3) * 4;
+#pragma unroll
+                        for (int b = 0; b < NB; b++) {
+                            const uint32_t x0 = b < 4 ? w0[u].x : w0[u].y, x1 = b < 4 ? w1[u].x : w1[u].y;
+                            const uint32_t two = __byte_perm(x0, x1, (b & 3) | ((4 + (b & 3)) << 4));
+                            uint32_t hv = __byte_perm(two, 0x64646464u, 0x5140);
+                            __half2 hx = *reinterpret_cast<__half2*>(&hv);
+                            hx = __hsub2(hx, __halves2half2(__ushort_as_half(0x6400), __ushort_as_half(0x6400)));
+                            const uint32_t col = b * SP + sp;
+                            *reinterpret_cast<uint32_t*>(base + (col >> 3) * 256 + (col & 7) * 32) =
+                                *reinterpret_cast<uint32_t*>(&hx);
+                        }
+                    }
                 }
-                mbar_expect_tx(full0 + 8 * st, item_bytes);
-                bulk_g2s(ring0 + st * item_bytes, src + (size_t)k * item_bytes, item_bytes, full0 + 8 * st);
-                issued = k + 1;
             }
-            // shared memory must outlive every copy started here
-            for (uint32_t k = issued > R ? issued - R : 0; k < issued; k++)
-                if (!mbar_wait(full0 + 8 * (k % R), (k / R) & 1)) atomicExch(A.status, 1u);
+            __syncwarp();
+            if (lane == 0) mbar_arrive(bfull0 + 8 * buf);
+        }
+        return;
+    }
+    if (warp == MAC_CONSUMERS) {
+        // ---- streamer (lane 0): each tile's contiguous plaintext range into the ring
+        if (lane == 0) {
+            uint32_t issued = 0;
+            for (uint32_t lt = 0, tau = blockIdx.x; tau < A.tiles && !*abort; lt++, tau += gridDim.x) {
+                const uint32_t gi = tau / A.tiles_per_limb, j0 = (tau % A.tiles_per_limb) * A.CT;
+                const uint8_t* src = A.ptb + A.off[gi] + (size_t)j0 * A.NEB * item_bytes;
+                for (uint32_t it = 0; it < IPT; it++) {
+                    const uint32_t kg = lt * IPT + it, st = kg % R;
+                    if (kg >= R && !mbar_wait(empty0 + 8 * st, ((kg / R) - 1) & 1, abort)) break;
+                    mbar_expect_tx(full0 + 8 * st, item_bytes);
+                    bulk_g2s(ring0 + st * item_bytes, src + (size_t)it * item_bytes, item_bytes, full0 + 8 * st);
+                    issued = kg + 1;
+                }
+            }
+            // shared memory must outlive every copy started here: wait for them
+            // even after an abort (the copies land whatever the consumers do)
+            for (uint32_t kg = issued > R ? issued - R : 0; kg < issued; kg++) {
+                uint32_t dummy = 0;
+                mbar_wait(full0 + 8 * (kg % R), (kg / R) & 1, &dummy);
+            }
+            if (*abort) atomicExch(A.status, 1u);
         }
         return;
     }
 
-    // ---- consumers: X's byte planes for the CTA's coefficients, as mma B fragments
-    {
-        const uint32_t zero_words = (A.CT * A.jstride) / 16;
-        for (uint32_t x = threadIdx.x; x < zero_words; x += 32 * MAC_CONSUMERS)
-            reinterpret_cast<uint4*>(Bs)[x] = make_uint4(0, 0, 0, 0);
-        consumer_sync();
-        const uint32_t nwords = A.CT * S * A.terms * 2;
-        for (uint32_t x = threadIdx.x; x < nwords; x += 32 * MAC_CONSUMERS) {
-            const uint32_t jj = x % A.CT;
-            uint32_t r = x / A.CT;
-            const uint32_t p = r & 1;
-            r >>= 1;
-            const uint32_t t = r % A.terms, s = r / A.terms;
-            const uint64_t w = A.baby[s * A.seq_words + (size_t)t * 2 * A.nN + p * A.nN + (size_t)i * A.N + j0 + jj];
-            const uint32_t sp = 2 * s + p, kt = t >> 4, kr = t & 15;
-            // element (k = kr, n) of a B fragment: lane 4 (n % 8) + (kr % 8) / 2, register kr / 8, half kr % 2
-            uint8_t* base = Bs + (size_t)jj * A.jstride + (size_t)kt * NT * 256 + ((kr & 7) >> 1) * 8 + (kr >> 3) * 4 +
-                            (kr & 1) * 2;
-#pragma unroll
-            for (int b = 0; b < NB; b++) {
-                const uint32_t col = b * SP + sp;
-                *reinterpret_cast<unsigned short*>(base + (col >> 3) * 256 + (col & 7) * 32) =
-                    __half_as_ushort(__uint2half_rn((uint32_t)(w >> (8 * b)) & 0xFFu));
-            }
-        }
-        consumer_sync();
-    }
-
+    // ---- consumer warps: item kg (global within the CTA) goes to warp kg % W
     const uint32_t g8 = lane >> 2, h4 = lane & 3;
-    const uint64_t q = A.q[i], r0 = A.bar[2 * i], r1 = A.bar[2 * i + 1];
-    bool ok = true;
-    for (uint32_t k = warp; k < items; k += MAC_CONSUMERS) {
-        const uint32_t st = k % R;
-        if (!mbar_wait(full0 + 8 * st, (k / R) & 1)) {
-            atomicExch(A.status, 1u);
-            ok = false;
-            break;
-        }
-        const uint32_t jj = k / A.NEB, eblk = k % A.NEB;
-        const uint8_t* As = ring + (size_t)st * item_bytes + lane * 8;
-        const uint8_t* Bj = Bs + (size_t)jj * A.jstride + lane * 8;
-        uint64_t fin[2][SLOTS];
-#pragma unroll
-        for (int r = 0; r < 2; r++)
-#pragma unroll
-            for (int u = 0; u < SLOTS; u++) fin[r][u] = 0;
-        for (uint32_t ks = 0; ks < A.KT; ks += A.kseg) {
-            const uint32_t ke = min(A.KT, ks + A.kseg);
-            uint64_t lo[2][SLOTS], hi[2][SLOTS];
+    const uint32_t lane_b = SP >= 8 ? 0 : (2 * h4) / SP;  // byte plane offset of this lane's columns
+    for (uint32_t lt = 0, tau = blockIdx.x; tau < A.tiles; lt++, tau += gridDim.x) {
+        const uint32_t buf = lt & 1, gi = tau / A.tiles_per_limb, i = A.limb[gi];
+        const uint32_t j0 = (tau % A.tiles_per_limb) * A.CT;
+        const uint64_t q = A.q[i], r0 = A.bar[2 * i], r1 = A.bar[2 * i + 1];
+        if (!mbar_wait(bfull0 + 8 * buf, (lt >> 1) & 1, abort)) break;
+        const uint8_t* Bt = Bs + buf * bbuf + lane * 8;
+        uint32_t it = (warp + MAC_CONSUMERS - (lt * IPT) % MAC_CONSUMERS) % MAC_CONSUMERS;
+        bool ok = true;
+        for (; it < IPT; it += MAC_CONSUMERS) {
+            const uint32_t kg = lt * IPT + it, st = kg % R;
+            if (!mbar_wait(full0 + 8 * st, (kg / R) & 1, abort)) {
+                ok = false;
+                break;
+            }
+            const uint32_t jj = it / A.NEB, eblk = it % A.NEB;
+            const uint8_t* As = ring + (size_t)st * item_bytes + lane * 8;
+            const uint8_t* Bj = Bt + (size_t)jj * A.jstride;
+            uint64_t fin[2][SLOTS];
 #pragma unroll
             for (int r = 0; r < 2; r++)
 #pragma unroll
-                for (int u = 0; u < SLOTS; u++) lo[r][u] = hi[r][u] = 0;
+                for (int u = 0; u < SLOTS; u++) fin[r][u] = 0;
+            for (uint32_t ks = 0; ks < A.KT; ks += A.kseg) {
+                const uint32_t ke = min(A.KT, ks + A.kseg);
+                const bool last_seg = ke == A.KT;
+                // 32-bit columns of the 128-bit sums: col c holds weight 2^{32 c}
+                uint64_t col[2][SLOTS][4];
 #pragma unroll
-            for (int a0 = 0; a0 < NB; a0 += AG) {
-                float acc[AG][NT][4];
+                for (int r = 0; r < 2; r++)
 #pragma unroll
-                for (int a = 0; a < AG; a++)
+                    for (int u = 0; u < SLOTS; u++)
 #pragma unroll
-                    for (int nt = 0; nt < NT; nt++)
+                        for (int c = 0; c < 4; c++) col[r][u][c] = 0;
 #pragma unroll
-                        for (int e = 0; e < 4; e++) acc[a][nt][e] = 0.f;
-                for (uint32_t kt = ks; kt < ke; kt++) {
-                    const uint8_t* Bk = Bj + (size_t)kt * NT * 256;
-                    if (AG > 1) {  // B fragments reused by every plane of the group
-                        uint2 bf[NT];
+                for (int a0 = 0; a0 < NB; a0 += AG) {
+                    float acc[AG][NT][4];
 #pragma unroll
-                        for (int nt = 0; nt < NT; nt++) bf[nt] = *reinterpret_cast<const uint2*>(Bk + nt * 256);
-#pragma unroll
-                        for (int a = 0; a < AG; a++) {
-                            uint32_t af[4];
-                            bytes_to_f16x2(*reinterpret_cast<const uint2*>(As + (size_t)(kt * NB + a0 + a) * 256), af);
-#pragma unroll
-                            for (int nt = 0; nt < NT; nt++) mma16816(acc[a][nt], af, bf[nt]);
-                        }
-                    } else {
-                        uint32_t af[4];
-                        bytes_to_f16x2(*reinterpret_cast<const uint2*>(As + (size_t)(kt * NB + a0) * 256), af);
+                    for (int a = 0; a < AG; a++)
 #pragma unroll
                         for (int nt = 0; nt < NT; nt++)
-                            mma16816(acc[0][nt], af, *reinterpret_cast<const uint2*>(Bk + nt * 256));
-                    }
-                }
-                // fold: column c = 8 nt + 2 h4 + (e & 1) holds byte plane b = c / SP of
-                // (sequence, polynomial) c % SP; rows g8 (e < 2) and g8 + 8
 #pragma unroll
-                for (int a = 0; a < AG; a++)
+                            for (int e = 0; e < 4; e++) acc[a][nt][e] = 0.f;
+                    for (uint32_t kt = ks; kt < ke; kt++) {
+                        const uint8_t* Bk = Bj + (size_t)kt * NT * 256;
+                        if (AG > 1) {  // B fragments reused by every plane of the group
+                            uint2 bf[NT];
 #pragma unroll
-                    for (int nt = 0; nt < NT; nt++)
+                            for (int nt = 0; nt < NT; nt++) bf[nt] = *reinterpret_cast<const uint2*>(Bk + nt * 256);
 #pragma unroll
-                        for (int e = 0; e < 4; e++) {
-                            const int r = e >> 1, h = e & 1;
-                            const uint64_t v = __float2uint_rz(acc[a][nt][e]);
-                            if (SP >= 8) {
-                                const int u = (nt % (SP / 8)) * 2 + h, b = nt / (SP / 8);
-                                add_shl(lo[r][u], hi[r][u], v, 8 * (a0 + a + b));
-                            } else {
-                                const uint32_t b = (nt * 8 + 2 * h4 + h) / SP;
-                                if (b < NB) add_shl(lo[r][h], hi[r][h], v, 8 * (a0 + a + b));
+                            for (int a = 0; a < AG; a++) {
+                                uint32_t af[4];
+                                bytes_to_f16x2(*reinterpret_cast<const uint2*>(As + (size_t)(kt * NB + a0 + a) * 256),
+                                               af);
+#pragma unroll
+                                for (int nt = 0; nt < NT; nt++) mma16816(acc[a][nt], af, bf[nt]);
                             }
+                        } else {
+                            uint32_t af[4];
+                            bytes_to_f16x2(*reinterpret_cast<const uint2*>(As + (size_t)(kt * NB + a0) * 256), af);
+#pragma unroll
+                            for (int nt = 0; nt < NT; nt++)
+                                mma16816(acc[0][nt], af, *reinterpret_cast<const uint2*>(Bk + nt * 256));
                         }
-            }
+                    }
+                    if (a0 + AG >= NB && last_seg) {  // last read of the stage: hand it back
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(empty0 + 8 * st);
+                    }
+                    // fold: column 8 nt + 2 h4 + (e & 1) of the n8 tile is byte plane
+                    // b = b_ct(nt) + lane_b of (sequence, polynomial) slot; rows g8, g8 + 8
 #pragma unroll
-            for (int r = 0; r < 2; r++)
+                    for (int a = 0; a < AG; a++)
 #pragma unroll
-                for (int u = 0; u < SLOTS; u++) fin[r][u] = add_mod(fin[r][u], reduce128(lo[r][u], hi[r][u], q, r0, r1), q);
-        }
-        __syncwarp();
-        if (lane == 0) mbar_arrive(empty0 + 8 * st);
-
-        // partial sums of the byte planes that other lanes of the quad hold
-        if (SP < 8) {
+                        for (int nt = 0; nt < NT; nt++)
 #pragma unroll
-            for (int r = 0; r < 2; r++)
-#pragma unroll
-                for (int u = 0; u < SLOTS; u++) {
-                    if (SP == 2) fin[r][u] = add_mod(fin[r][u], __shfl_xor_sync(0xffffffffu, fin[r][u], 1), q);
-                    fin[r][u] = add_mod(fin[r][u], __shfl_xor_sync(0xffffffffu, fin[r][u], 2), q);
+                            for (int e = 0; e < 4; e++) {
+                                const int r = e >> 1, h = e & 1;
+                                const int u = SP >= 8 ? (nt % (SP / 8)) * 2 + h : h;
+                                const int b = SP >= 8 ? nt / (SP / 8) : nt * 8 / SP;
+                                const int sh = 8 * (a0 + a + b);
+                                col[r][u][sh >> 5] += (uint64_t)f32_int(acc[a][nt][e]) << (sh & 31);
+                            }
                 }
+#pragma unroll
+                for (int r = 0; r < 2; r++)
+#pragma unroll
+                    for (int u = 0; u < SLOTS; u++) {
+                        uint64_t lo = col[r][u][0] + (col[r][u][1] << 32);
+                        uint64_t hi = (col[r][u][1] >> 32) + col[r][u][2] + (col[r][u][3] << 32) + (lo < col[r][u][0]);
+                        if (SP < 8 && lane_b) {  // this lane's planes start at b = lane_b
+                            const uint32_t sh = 8 * lane_b;
+                            hi = (hi << sh) | (lo >> (64 - sh));
+                            lo <<= sh;
+                        }
+                        const uint64_t v = NB <= 6 ? barrett128(lo, hi, q, r0, r1) : reduce128(lo, hi, q, r0, r1);
+                        fin[r][u] = add_mod(fin[r][u], v, q);
+                    }
+            }
+            // partial sums of the byte planes that other lanes of the quad hold
+            if (SP < 8) {
+#pragma unroll
+                for (int r = 0; r < 2; r++)
+#pragma unroll
+                    for (int u = 0; u < SLOTS; u++) {
+                        if (SP == 2) fin[r][u] = add_mod(fin[r][u], __shfl_xor_sync(0xffffffffu, fin[r][u], 1), q);
+                        fin[r][u] = add_mod(fin[r][u], __shfl_xor_sync(0xffffffffu, fin[r][u], 2), q);
+                    }
+            }
+            const size_t jcol = (size_t)i * A.N + j0 + jj;
+            auto store = [&](uint32_t row, uint32_t sp, uint64_t v) {
+                const uint32_t eg = eblk * 16 + row;
+                if (eg < A.neg) A.T[((size_t)((sp >> 1) * A.neg + eg) * 2 + (sp & 1)) * A.nN + jcol] = v;
+            };
+            if (SP == 2) {
+                const uint32_t r = h4 >> 1, h = h4 & 1;
+                store(g8 + 8 * r, h, r ? (h ? fin[1][1] : fin[1][0]) : (h ? fin[0][1] : fin[0][0]));
+            } else if (SP == 4) {
+                const uint32_t r = h4 >> 1;
+#pragma unroll
+                for (int h = 0; h < 2; h++) store(g8 + 8 * r, 2 * (h4 & 1) + h, r ? fin[1][h] : fin[0][h]);
+            } else {
+#pragma unroll
+                for (int r = 0; r < 2; r++)
+#pragma unroll
+                    for (int u = 0; u < SLOTS; u++) store(g8 + 8 * r, 8 * (u >> 1) + 2 * h4 + (u & 1), fin[r][u]);
+            }
         }
-        const size_t jcol = (size_t)i * A.N + j0 + jj;
-        auto store = [&](uint32_t row, uint32_t sp, uint64_t v) {
-            const uint32_t eg = eblk * 16 + row;
-            if (eg < A.neg) A.T[((size_t)((sp >> 1) * A.neg + eg) * 2 + (sp & 1)) * A.nN + jcol] = v;
-        };
-        if (SP == 2) {
-            const uint32_t r = h4 >> 1, h = h4 & 1;
-            store(g8 + 8 * r, h, r ? (h ? fin[1][1] : fin[1][0]) : (h ? fin[0][1] : fin[0][0]));
-        } else if (SP == 4) {
-            const uint32_t r = h4 >> 1;
-#pragma unroll
-            for (int h = 0; h < 2; h++) store(g8 + 8 * r, 2 * (h4 & 1) + h, r ? fin[1][h] : fin[0][h]);
-        } else {
-#pragma unroll
-            for (int r = 0; r < 2; r++)
-#pragma unroll
-                for (int u = 0; u < SLOTS; u++) store(g8 + 8 * r, 8 * (u >> 1) + 2 * h4 + (u & 1), fin[r][u]);
-        }
+        if (!ok) break;
+        __syncwarp();
+        if (lane == 0) mbar_arrive(bempty0 + 8 * buf);
     }
-    (void)ok;
 }
 
 // one thread per 8-byte fragment word of one output block: ((j KT + kt) nb + a) 32 + lane
@@ -392,24 +459,30 @@ int launch_group(blb_ctx* c, MacArgs& a, uint32_t nlimbs)
     const uint32_t item_bytes = a.KT * NB * 256;
     a.jstride = a.KT * NT * 256 + 16;
     a.CT = 16;
-    while (a.CT > 1 && (size_t)a.CT * a.jstride > (48u << 10)) a.CT >>= 1;
-    const uint32_t items = a.CT * a.NEB;
-    // ring depth: either every item has its own stage or the depth is a multiple
-    // of the consumer count, so that successive fills of a stage go to the same
-    // warp and a parity wait never sees the phase before the one it wants
-    a.R = std::min<uint32_t>(2 * MAC_CONSUMERS, items);
-    size_t smem = (((size_t)a.CT * a.jstride + 127) & ~(size_t)127) + (size_t)a.R * item_bytes + 16 * a.R;
-    if (smem > (200u << 10)) {
-        a.R = MAC_CONSUMERS < items ? MAC_CONSUMERS : items;
-        smem = (((size_t)a.CT * a.jstride + 127) & ~(size_t)127) + (size_t)a.R * item_bytes + 16 * a.R;
-    }
+    while (a.CT > 1 && (size_t)a.CT * a.jstride > (32u << 10)) a.CT >>= 1;
+    a.tiles_per_limb = c->N / a.CT;
+    a.tiles = a.tiles_per_limb * nlimbs;
+    // ring depth a multiple of the consumer count: successive fills of a stage
+    // go to the same warp, so a parity wait never sees the phase before the one
+    // it wants
+    const size_t bbuf = ((size_t)a.CT * a.jstride + 127) & ~(size_t)127;
+    a.R = 2 * MAC_CONSUMERS;
+    auto smem_of = [&](uint32_t R) { return 2 * bbuf + (size_t)R * item_bytes + 16 * R + 64; };
+    if (smem_of(a.R) > (200u << 10)) a.R = MAC_CONSUMERS;
+    const size_t smem = smem_of(a.R);
     if (smem > (227u << 10)) return blb_fail(BLB_ERR_ARG, "plaintext tile too large for shared memory");
+    if (item_bytes >= (1u << 20)) return blb_fail(BLB_ERR_ARG, "too many plaintext terms per output");
     static bool attr = false;
+    static int per_sm = 0;
     if (!attr) {
         BLB_CUDA(cudaFuncSetAttribute(k_cp_mac_tc<S, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 << 10));
         attr = true;
     }
-    dim3 grid(c->N / a.CT, nlimbs);
+    BLB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cp_mac_tc<S, NB>, MAC_THREADS, smem));
+    int dev = 0, sms = 0;
+    BLB_CUDA(cudaGetDevice(&dev));
+    BLB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const uint32_t grid = std::min<uint32_t>(a.tiles, (uint32_t)std::max(1, per_sm) * sms);
     k_cp_mac_tc<S, NB><<<grid, MAC_THREADS, smem, c->stream>>>(a);
     BLB_LAUNCHED();
     return BLB_OK;
@@ -504,8 +577,9 @@ int launch_cp_mac(blb_ctx* c, const blb_cp_plan* P, const uint64_t* baby, uint64
                 cnt++;
             }
         if (!cnt) continue;
-        // 16 tiles keep 16 x 16 x 255^2 < 2^24; primes above 2^60 need 64 terms x q^2 < 2^128
-        a.kseg = big ? 4 : 16;
+        // 8 tiles keep 8 x 16 x 255^2 < 2^23 (exact fp32 sums, read back by one
+        // add); primes above 2^60 need 64 terms x q^2 < 2^128
+        a.kseg = big ? 4 : 8;
         int rc;
         switch (S) {
         case 1: rc = launch_nb<1>(c, a, nb, cnt); break;
