@@ -222,6 +222,31 @@ class Oracle:
         lib().orc_rotate(self._pp, _p(ct, _u64p), ct.shape[1] - 1, r, _p(np.ascontiguousarray(gksk), _u64p), _p(out, _u64p))
         return out
 
+    def rotate_hoisted(self, ct, rots, gksks):
+        """Rotations of one ciphertext sharing one ModUp: list of (2, n, N)."""
+        ct = np.ascontiguousarray(ct, np.uint64)
+        k = len(rots)
+        out = np.zeros((k,) + ct.shape, np.uint64)
+        keys = [np.ascontiguousarray(x, np.uint64) for x in gksks]
+        kp = (ctypes.POINTER(ctypes.c_uint64) * max(k, 1))(*[_p(x, _u64p) for x in keys])
+        r = (ctypes.c_int32 * max(k, 1))(*rots)
+        lib().orc_rotate_hoisted(self._pp, _p(ct, _u64p), ct.shape[1] - 1, k, r, kp, _p(out, _u64p))
+        return list(out)
+
+    def rotate_sum(self, base, Ts, rots, gksks):
+        """base + sum_x Rot^{rots[x]}(Ts[x]) with one ModDown; base may be None."""
+        k = len(Ts)
+        shape = np.shape(base) if k == 0 else np.shape(Ts[0])
+        Ts = np.ascontiguousarray(np.stack(Ts) if k else np.zeros((1,) + tuple(shape)), np.uint64)
+        out = np.zeros(shape, np.uint64)
+        keys = [np.ascontiguousarray(x, np.uint64) for x in gksks]
+        kp = (ctypes.POINTER(ctypes.c_uint64) * max(k, 1))(*[_p(x, _u64p) for x in keys])
+        r = (ctypes.c_int32 * max(k, 1))(*rots)
+        bp = None if base is None else np.ascontiguousarray(base, np.uint64)
+        lib().orc_rotate_sum(self._pp, None if bp is None else _p(bp, _u64p), _p(Ts, _u64p), shape[1] - 1, k, r, kp,
+                             _p(out, _u64p))
+        return out
+
     def rescale(self, ct):
         ct = np.ascontiguousarray(ct, np.uint64)
         npolys, n = ct.shape[0], ct.shape[1]

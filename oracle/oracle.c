@@ -647,60 +647,99 @@ void orc_moddown(const orc_params* p, const uint64_t* acc, uint32_t level, uint6
     }
 }
 
-/* Hybrid key switching of one polynomial d (coefficient form, level l) with a
- * key from s' to s; returns (k0, k1) with k0 + k1 s ~ d s' (mod Q_l):
- *   1. decompose d into beta = ceil((l+1)/alpha) digits over the primes D_j;
- *   2. ModUp: extend each digit to every prime of Q_l u P by fast base
- *      conversion (the digit's own primes keep d's residues);
- *   3. inner product with the key's digits over Q_l u P;
- *   4. ModDown: k_i = round(acc / P) mod q_i (orc_moddown). */
-void orc_keyswitch(const orc_params* p, const uint64_t* d, uint32_t level, const uint64_t* ksk,
-                   uint64_t* out)
+/* sigma_g on one limb mod q: X^i -> X^(i g mod 2N), negated past N. */
+static void automorph_limb(uint32_t N, const uint64_t* in, uint64_t g, uint64_t q, uint64_t* out)
 {
-    const uint32_t N = p->N, n = level + 1, nP = p->nP, L = p->nQ + p->nP;
-    const uint32_t ext = n + nP; /* limbs of Q_l u P; index e < n is q_e, else p_{e-n} */
-    const uint32_t beta = (n + p->alpha - 1) / p->alpha;
-    uint64_t* acc = calloc((size_t)2 * ext * N, sizeof(uint64_t));
+    for (uint32_t i = 0; i < N; i++) {
+        uint64_t k = ((uint64_t)i * g) % (2ull * N);
+        if (k < N) out[k] = in[i];
+        else out[k - N] = negmod(in[i], q);
+    }
+}
 
-    #pragma omp parallel for
-    for (uint32_t e = 0; e < ext; e++) {
-        const uint32_t pi = e < n ? e : p->nQ + (e - n);
-        const uint64_t t = p->prime[pi];
-        uint64_t* x = malloc(sizeof(uint64_t) * N);
-        uint64_t* kb = malloc(sizeof(uint64_t) * N);
-        uint64_t* ka = malloc(sizeof(uint64_t) * N);
-        uint64_t* xb = malloc(sizeof(uint64_t) * N);
-        uint64_t* xa = malloc(sizeof(uint64_t) * N);
-        uint64_t src[ORC_MAX_PRIMES];
-        const uint64_t* xs[ORC_MAX_PRIMES];
-        for (uint32_t j = 0; j < beta; j++) {
+/* Prime index of limb e of the extended basis Q_l u P (e < n: q_e, else p_{e-n}). */
+static uint32_t ext_prime(const orc_params* p, uint32_t n, uint32_t e) { return e < n ? e : p->nQ + (e - n); }
+
+/* Steps 1-2 of hybrid key switching for a polynomial d (coefficient form, level
+ * l): decompose d into beta = ceil((l+1)/alpha) digits over the primes
+ * D_j = {j alpha, ..., min((j+1) alpha, l+1) - 1} and extend each digit to
+ * every prime of Q_l u P by fast base conversion; the digit's own primes keep
+ * d's residues.  ext: [beta][l+1+nP][N]. */
+void orc_modup(const orc_params* p, const uint64_t* d, uint32_t level, uint64_t* ext)
+{
+    const uint32_t N = p->N, n = level + 1, E = n + p->nP;
+    const uint32_t beta = (n + p->alpha - 1) / p->alpha;
+    #pragma omp parallel for collapse(2)
+    for (uint32_t j = 0; j < beta; j++) {
+        for (uint32_t e = 0; e < E; e++) {
             uint32_t lo = j * p->alpha, hi = (j + 1) * p->alpha;
             if (hi > n) hi = n;
+            uint64_t* x = ext + ((size_t)j * E + e) * N;
             if (e >= lo && e < hi) {
                 memcpy(x, d + (size_t)e * N, sizeof(uint64_t) * N);
             } else {
+                uint64_t src[ORC_MAX_PRIMES];
+                const uint64_t* xs[ORC_MAX_PRIMES];
                 for (uint32_t i = lo; i < hi; i++) {
                     src[i - lo] = p->prime[i];
                     xs[i - lo] = d + (size_t)i * N;
                 }
-                base_convert(N, xs, src, hi - lo, t, x);
+                base_convert(N, xs, src, hi - lo, p->prime[ext_prime(p, n, e)], x);
             }
-            memcpy(kb, ksk + ((size_t)(j * 2 + 0) * L + pi) * N, sizeof(uint64_t) * N);
-            memcpy(ka, ksk + ((size_t)(j * 2 + 1) * L + pi) * N, sizeof(uint64_t) * N);
-            orc_negacyclic_mul(p, pi, x, kb, xb);
-            orc_negacyclic_mul(p, pi, x, ka, xa);
+        }
+    }
+}
+
+/* Step 3 of hybrid key switching, accumulated: for every limb e of Q_l u P,
+ *   acc[0][e] += sum_j sigma_g(x_j[e]) * b_j[e],  acc[1][e] += sum_j sigma_g(x_j[e]) * a_j[e]
+ * with the key's digits (b_j, a_j); g = 1 applies no automorphism.  Applying
+ * sigma_g to the extended digits of d instead of extending the digits of
+ * sigma_g(d) is the hoisted form of a rotation: the decomposition and ModUp of
+ * one ciphertext then serve all its rotations. */
+void orc_ks_accumulate(const orc_params* p, const uint64_t* ext, uint32_t level, uint64_t g, const uint64_t* ksk,
+                       uint64_t* acc)
+{
+    const uint32_t N = p->N, n = level + 1, E = n + p->nP, L = p->nQ + p->nP;
+    const uint32_t beta = (n + p->alpha - 1) / p->alpha;
+    #pragma omp parallel for
+    for (uint32_t e = 0; e < E; e++) {
+        const uint32_t pi = ext_prime(p, n, e);
+        const uint64_t t = p->prime[pi];
+        uint64_t* x = malloc(sizeof(uint64_t) * N);
+        uint64_t* xb = malloc(sizeof(uint64_t) * N);
+        uint64_t* xa = malloc(sizeof(uint64_t) * N);
+        for (uint32_t j = 0; j < beta; j++) {
+            const uint64_t* xj = ext + ((size_t)j * E + e) * N;
+            if (g == 1) memcpy(x, xj, sizeof(uint64_t) * N);
+            else automorph_limb(N, xj, g, t, x);
+            orc_negacyclic_mul(p, pi, x, ksk + ((size_t)(j * 2 + 0) * L + pi) * N, xb);
+            orc_negacyclic_mul(p, pi, x, ksk + ((size_t)(j * 2 + 1) * L + pi) * N, xa);
             uint64_t* a0 = acc + (size_t)e * N;
-            uint64_t* a1 = acc + ((size_t)ext + e) * N;
+            uint64_t* a1 = acc + ((size_t)E + e) * N;
             for (uint32_t c = 0; c < N; c++) {
                 a0[c] = addmod(a0[c], xb[c], t);
                 a1[c] = addmod(a1[c], xa[c], t);
             }
         }
-        free(x); free(kb); free(ka); free(xb); free(xa);
+        free(x); free(xb); free(xa);
     }
+}
 
-    /* ModDown */
+/* Hybrid key switching of one polynomial d (coefficient form, level l) with a
+ * key from s' to s; returns (k0, k1) with k0 + k1 s ~ d s' (mod Q_l):
+ * ModUp (orc_modup), the inner product with the key over Q_l u P
+ * (orc_ks_accumulate), and ModDown k_i = round(acc / P) mod q_i (orc_moddown). */
+void orc_keyswitch(const orc_params* p, const uint64_t* d, uint32_t level, const uint64_t* ksk,
+                   uint64_t* out)
+{
+    const uint32_t N = p->N, n = level + 1, E = n + p->nP;
+    const uint32_t beta = (n + p->alpha - 1) / p->alpha;
+    uint64_t* ext = malloc(sizeof(uint64_t) * (size_t)beta * E * N);
+    uint64_t* acc = calloc((size_t)2 * E * N, sizeof(uint64_t));
+    orc_modup(p, d, level, ext);
+    orc_ks_accumulate(p, ext, level, 1, ksk, acc);
     orc_moddown(p, acc, level, out);
+    free(ext);
     free(acc);
 }
 
@@ -725,6 +764,72 @@ void orc_rotate(const orc_params* p, const uint64_t* ct, uint32_t level, int32_t
     }
     free(rc);
     free(ks);
+}
+
+/* Hoisted rotations of one ciphertext (c0, c1) by r_0..r_{k-1} (Halevi and
+ * Shoup 2018): c1 is decomposed and extended once; rotation r is
+ *   (sigma_g(c0) + k0, k1),  (k0, k1) = ModDown( sum_j sigma_g(x_j) (b_j, a_j) ),
+ * g = 5^r, x_j the extended digits of c1 and (b_j, a_j) the key for r.
+ * out: k ciphertexts of 2 x (l+1) x N words. */
+void orc_rotate_hoisted(const orc_params* p, const uint64_t* ct, uint32_t level, uint32_t k, const int32_t* r,
+                        const uint64_t* const* galois_ksk, uint64_t* out)
+{
+    const uint32_t N = p->N, n = level + 1, E = n + p->nP;
+    const uint32_t beta = (n + p->alpha - 1) / p->alpha;
+    uint64_t* ext = malloc(sizeof(uint64_t) * (size_t)beta * E * N);
+    uint64_t* acc = malloc(sizeof(uint64_t) * (size_t)2 * E * N);
+    uint64_t* ks = malloc(sizeof(uint64_t) * (size_t)2 * n * N);
+    uint64_t* r0 = malloc(sizeof(uint64_t) * (size_t)n * N);
+    orc_modup(p, ct + (size_t)n * N, level, ext);
+    for (uint32_t x = 0; x < k; x++) {
+        const uint64_t g = orc_galois_elt(p, r[x]);
+        memset(acc, 0, sizeof(uint64_t) * (size_t)2 * E * N);
+        orc_ks_accumulate(p, ext, level, g, galois_ksk[x], acc);
+        orc_moddown(p, acc, level, ks);
+        orc_automorphism(p, ct, n, g, r0);
+        uint64_t* o = out + (size_t)x * 2 * n * N;
+        for (uint32_t l = 0; l < n; l++) {
+            const uint64_t q = p->prime[l];
+            for (uint32_t i = 0; i < N; i++) {
+                o[(size_t)l * N + i] = addmod(r0[(size_t)l * N + i], ks[(size_t)l * N + i], q);
+                o[((size_t)n + l) * N + i] = ks[((size_t)n + l) * N + i];
+            }
+        }
+    }
+    free(ext); free(acc); free(ks); free(r0);
+}
+
+/* Sum of rotations with one ModDown (the giant-step sum of a BSGS product):
+ *   base + sum_x Rot^{r_x}(T_x)
+ * = base + sum_x (sigma_{g_x}(T_x.c0), 0) + ModDown( sum_x sum_j y_{x,j} (b_{x,j}, a_{x,j}) ),
+ * y_{x,j} the extended digits of sigma_{g_x}(T_x.c1).  The inner products are
+ * summed over Q_l u P before a single division by P.  base may be NULL. */
+void orc_rotate_sum(const orc_params* p, const uint64_t* base, const uint64_t* T, uint32_t level, uint32_t k,
+                    const int32_t* r, const uint64_t* const* galois_ksk, uint64_t* out)
+{
+    const uint32_t N = p->N, n = level + 1, E = n + p->nP;
+    const uint32_t beta = (n + p->alpha - 1) / p->alpha;
+    const size_t ctw = (size_t)2 * n * N;
+    uint64_t* ext = malloc(sizeof(uint64_t) * (size_t)beta * E * N);
+    uint64_t* acc = calloc((size_t)2 * E * N, sizeof(uint64_t));
+    uint64_t* ks = malloc(sizeof(uint64_t) * ctw);
+    uint64_t* rc = malloc(sizeof(uint64_t) * ctw);
+    if (base) memcpy(out, base, sizeof(uint64_t) * ctw);
+    else memset(out, 0, sizeof(uint64_t) * ctw);
+    for (uint32_t x = 0; x < k; x++) {
+        const uint64_t g = orc_galois_elt(p, r[x]);
+        orc_automorphism(p, T + (size_t)x * ctw, n, g, rc);
+        orc_automorphism(p, T + (size_t)x * ctw + (size_t)n * N, n, g, rc + (size_t)n * N);
+        orc_modup(p, rc + (size_t)n * N, level, ext);
+        orc_ks_accumulate(p, ext, level, 1, galois_ksk[x], acc);
+        orc_add(p, out, rc, n, out);
+    }
+    if (k) {
+        orc_moddown(p, acc, level, ks);
+        orc_add(p, out, ks, n, out);
+        orc_add(p, out + (size_t)n * N, ks + (size_t)n * N, n, out + (size_t)n * N);
+    }
+    free(ext); free(acc); free(ks); free(rc);
 }
 
 /* Rescale (Sec. 2.4): divide by the last prime q_l with rounding,
@@ -854,30 +959,39 @@ int orc_matmul_cp(const orc_params* p, const orc_galois_set* gk, const uint64_t*
     const uint32_t G = k / b1;
     const size_t ctw = (size_t)2 * n * N;
 
-    /* baby steps: Rot^{b m}(X_c), b < b1 */
+    /* baby steps: Rot^{b m}(X_c), b < b1, hoisted (one ModUp of X_c serves all b) */
     uint64_t* baby = malloc(sizeof(uint64_t) * ctw * nX * b1);
-    for (uint32_t c = 0; c < nX; c++) {
+    int32_t* rots = malloc(sizeof(int32_t) * (b1 > G ? b1 : G));
+    const uint64_t** keys = malloc(sizeof(uint64_t*) * (b1 > G ? b1 : G));
+    int rc = 0;
+    for (uint32_t b = 1; b < b1; b++) {
+        rots[b - 1] = (int32_t)(b * m);
+        keys[b - 1] = find_galois(p, gk, rots[b - 1]);
+        if (!keys[b - 1]) rc = -2;
+    }
+    for (uint32_t c = 0; c < nX && !rc; c++) {
         memcpy(baby + ((size_t)c * b1) * ctw, X + (size_t)c * ctw, sizeof(uint64_t) * ctw);
-        for (uint32_t b = 1; b < b1; b++) {
-            const uint64_t* key = find_galois(p, gk, (int32_t)(b * m));
-            if (!key) { free(baby); return -2; }
-            orc_rotate(p, X + (size_t)c * ctw, level, (int32_t)(b * m), key, baby + ((size_t)c * b1 + b) * ctw);
-        }
+        orc_rotate_hoisted(p, X + (size_t)c * ctw, level, b1 - 1, rots, keys, baby + ((size_t)c * b1 + 1) * ctw);
+    }
+    /* giant steps: Rot^{g b1 m}, g >= 1, summed with one ModDown per output */
+    for (uint32_t g = 1; g < G && !rc; g++) {
+        rots[g - 1] = (int32_t)(g * b1 * m);
+        keys[g - 1] = find_galois(p, gk, rots[g - 1]);
+        if (!keys[g - 1]) rc = -2;
     }
 
     double* z = malloc(sizeof(double) * s);
     uint64_t* pt = malloc(sizeof(uint64_t) * n * N);
     uint64_t* prod = malloc(sizeof(uint64_t) * ctw);
-    uint64_t* T = malloc(sizeof(uint64_t) * ctw);
-    uint64_t* R = malloc(sizeof(uint64_t) * ctw);
+    uint64_t* T = malloc(sizeof(uint64_t) * ctw * G);
     uint64_t* acc = malloc(sizeof(uint64_t) * ctw);
     const double pt_scale = (double)p->prime[level];
-    int rc = 0;
     for (uint32_t oi = 0; oi < n_out && !rc; oi++) {
         const uint32_t e = out_idx[oi];
-        memset(acc, 0, sizeof(uint64_t) * ctw);
+        /* T_g = sum_{c,b} Rot^{b m}(X_c) (.) D'_{c,e,g,b} */
         for (uint32_t g = 0; g < G && !rc; g++) {
-            memset(T, 0, sizeof(uint64_t) * ctw);
+            uint64_t* Tg = T + (size_t)g * ctw;
+            memset(Tg, 0, sizeof(uint64_t) * ctw);
             for (uint32_t c = 0; c < nX; c++) {
                 for (uint32_t b = 0; b < b1; b++) {
                     for (uint32_t beta = 0; beta < k; beta++) {
@@ -888,21 +1002,15 @@ int orc_matmul_cp(const orc_params* p, const orc_galois_set* gk, const uint64_t*
                     }
                     if (orc_encode(p, z, s, level, pt_scale, pt)) rc = -3;
                     orc_mul_plain(p, baby + ((size_t)c * b1 + b) * ctw, pt, level, prod);
-                    ct_add_inplace(p, T, prod, level, 2);
+                    ct_add_inplace(p, Tg, prod, level, 2);
                 }
             }
-            if (g == 0) {
-                ct_add_inplace(p, acc, T, level, 2);
-            } else {
-                const uint64_t* key = find_galois(p, gk, (int32_t)(g * b1 * m));
-                if (!key) { rc = -2; break; }
-                orc_rotate(p, T, level, (int32_t)(g * b1 * m), key, R);
-                ct_add_inplace(p, acc, R, level, 2);
-            }
         }
+        /* Y_e = Rescale( T_0 + sum_{g >= 1} Rot^{g b1 m}(T_g) ) */
+        orc_rotate_sum(p, T, T + ctw, level, G - 1, rots, keys, acc);
         orc_rescale(p, acc, level, 2, Y + (size_t)oi * 2 * level * N);
     }
-    free(baby); free(z); free(pt); free(prod); free(T); free(R); free(acc);
+    free(baby); free(rots); free(keys); free(z); free(pt); free(prod); free(T); free(acc);
     return rc;
 }
 

@@ -82,10 +82,20 @@ void orc_automorphism(const orc_params* p, const uint64_t* in, uint32_t nlimbs, 
                       uint64_t* out);
 void orc_moddown(const orc_params* p, const uint64_t* acc /* 2 x (level+1+nP) x N */, uint32_t level,
                  uint64_t* out /* 2 x (level+1) x N */);
+void orc_modup(const orc_params* p, const uint64_t* d, uint32_t level,
+               uint64_t* ext /* beta x (level+1+nP) x N */);
+void orc_ks_accumulate(const orc_params* p, const uint64_t* ext, uint32_t level, uint64_t g,
+                       const uint64_t* ksk, uint64_t* acc /* 2 x (level+1+nP) x N */);
 void orc_keyswitch(const orc_params* p, const uint64_t* d, uint32_t level, const uint64_t* ksk,
                    uint64_t* out /* 2 x (level+1) x N */);
 void orc_rotate(const orc_params* p, const uint64_t* ct, uint32_t level, int32_t r,
                 const uint64_t* galois_ksk, uint64_t* out);
+void orc_rotate_hoisted(const orc_params* p, const uint64_t* ct, uint32_t level, uint32_t k,
+                        const int32_t* r, const uint64_t* const* galois_ksk,
+                        uint64_t* out /* k x 2 x (level+1) x N */);
+void orc_rotate_sum(const orc_params* p, const uint64_t* base /* nullable */, const uint64_t* T,
+                    uint32_t level, uint32_t k, const int32_t* r, const uint64_t* const* galois_ksk,
+                    uint64_t* out /* 2 x (level+1) x N */);
 void orc_rescale(const orc_params* p, const uint64_t* ct, uint32_t level, uint32_t npolys,
                  uint64_t* out /* npolys x level x N */);
 void orc_add(const orc_params* p, const uint64_t* a, const uint64_t* b, uint32_t nlimbs,
