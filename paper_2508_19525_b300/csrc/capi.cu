@@ -647,45 +647,78 @@ static int cp_run(blb_ctx* c, const blb_keys* K, const blb_cp_plan* P, blb_ct* c
     uint64_t* T = (uint64_t*)dev_alloc(c, T_bytes);
     for (uint32_t e = 0; e < S * P->nY; e++) Y[e] = nullptr;
     int rc = (baby && T) ? BLB_OK : blb_fail(BLB_ERR_OOM, "matmul_cp workspace");
-    // baby steps: Rot^{b m}(X_c) of every sequence, in one batched key-switch pass
-    std::vector<KsItem> items;
-    for (uint32_t ci = 0; !rc && ci < S * nX; ci++) {
-        uint64_t* dst0 = baby + (size_t)ci * P->b1 * ctw;
-        if (cudaMemcpyAsync(dst0, X[ci]->d, ctw * 8, cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess)
-            rc = blb_fail(BLB_ERR_CUDA, "copy failed");
-        for (uint32_t b = 1; !rc && b < P->b1; b++) {
-            const uint64_t g = galois_element(N, (int32_t)(b * P->m));
-            const KeyEntry* k = K->find(g);
-            if (!k) {
-                rc = blb_fail(BLB_ERR_NO_KEY, "no Galois key for rotation " + std::to_string(b * P->m));
-                break;
-            }
-            uint64_t* o = baby + ((size_t)ci * P->b1 + b) * ctw;
-            items.push_back(KsItem{X[ci]->d, X[ci]->d + (size_t)n * N, nullptr, k->d, o, o + (size_t)n * N, g});
-        }
+    // baby steps: Rot^{b m}(X_c) of every sequence in one pass, hoisted: the
+    // decomposition and ModUp of X_c serve all its b1 - 1 rotations
+    const uint32_t nb = P->b1 - 1;
+    std::vector<uint64_t> gb(nb);
+    std::vector<const uint64_t*> kb(nb);
+    for (uint32_t b = 1; !rc && b <= nb; b++) {
+        gb[b - 1] = galois_element(N, (int32_t)(b * P->m));
+        const KeyEntry* k = K->find(gb[b - 1]);
+        if (!k) rc = blb_fail(BLB_ERR_NO_KEY, "no Galois key for rotation " + std::to_string(b * P->m));
+        else kb[b - 1] = k->d;
     }
-    if (!rc) rc = keyswitch_batch(c, P->level, items.data(), (uint32_t)items.size(), 0);
+    {
+        std::vector<KsSource> src;
+        std::vector<KsProduct> prod;
+        std::vector<KsGroup> grp;
+        std::vector<KsAdd> adds;
+        for (uint32_t ci = 0; !rc && ci < S * nX; ci++) {
+            uint64_t* dst0 = baby + (size_t)ci * P->b1 * ctw;
+            if (cudaMemcpyAsync(dst0, X[ci]->d, ctw * 8, cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess)
+                rc = blb_fail(BLB_ERR_CUDA, "copy failed");
+            src.push_back(KsSource{X[ci]->d + (size_t)n * N, 1});
+            for (uint32_t b = 1; b <= nb; b++) {
+                uint64_t* o = dst0 + (size_t)b * ctw;
+                grp.push_back(KsGroup{o, o + (size_t)n * N, (uint32_t)prod.size(), (uint32_t)prod.size() + 1,
+                                      (uint32_t)adds.size(), (uint32_t)adds.size() + 1});
+                prod.push_back(KsProduct{ci, gb[b - 1], kb[b - 1]});
+                adds.push_back(KsAdd{X[ci]->d, gb[b - 1], 0});
+            }
+        }
+        if (!rc && nb)
+            rc = ks_run(c, P->level, src.data(), (uint32_t)src.size(), prod.data(), grp.data(), (uint32_t)grp.size(),
+                        adds.data(), 0);
+    }
     // plaintext products for every (sequence, e, g), at most 8 sequences per launch
     for (uint32_t s0 = 0; !rc && s0 < S;) {
         uint32_t chunk = S - s0 >= 8 ? 8 : S - s0 >= 4 ? 4 : S - s0 >= 2 ? 2 : 1;
         rc = launch_cp_mac(c, P, baby + (size_t)s0 * nX * P->b1 * ctw, T + (size_t)s0 * P->nY * P->G * ctw, chunk);
         s0 += chunk;
     }
-    // giant steps: acc += Rot^{g b1 m}(T[s][e][g]); one batched pass per g (distinct outputs)
-    for (uint32_t g = 1; !rc && g < P->G; g++) {
-        const uint64_t ge = galois_element(N, (int32_t)(g * P->b1 * P->m));
-        const KeyEntry* k = K->find(ge);
-        if (!k) {
-            rc = blb_fail(BLB_ERR_NO_KEY, "no Galois key for rotation " + std::to_string(g * P->b1 * P->m));
-            break;
+    // giant steps: T[e][0] + sum_{g >= 1} Rot^{g b1 m}(T[e][g]), the inner
+    // products of all g summed over Q_l u P before one ModDown per output
+    if (!rc && P->G > 1) {
+        std::vector<KsSource> src;
+        std::vector<KsProduct> prod;
+        std::vector<KsGroup> grp;
+        std::vector<KsAdd> adds;
+        std::vector<uint64_t> gg(P->G);
+        std::vector<const uint64_t*> kg(P->G);
+        for (uint32_t g = 1; !rc && g < P->G; g++) {
+            gg[g] = galois_element(N, (int32_t)(g * P->b1 * P->m));
+            const KeyEntry* k = K->find(gg[g]);
+            if (!k) rc = blb_fail(BLB_ERR_NO_KEY, "no Galois key for rotation " + std::to_string(g * P->b1 * P->m));
+            else kg[g] = k->d;
         }
-        items.clear();
-        for (uint32_t e = 0; e < S * P->nY; e++) {
-            uint64_t* acc = T + (size_t)e * P->G * ctw;
-            const uint64_t* src = acc + (size_t)g * ctw;
-            items.push_back(KsItem{src, src + (size_t)n * N, nullptr, k->d, acc, acc + (size_t)n * N, ge});
+        for (uint32_t e = 0; !rc && e < S * P->nY; e++) {
+            uint64_t* T0 = T + (size_t)e * P->G * ctw;
+            KsGroup G{T0, T0 + (size_t)n * N, (uint32_t)prod.size(), 0, (uint32_t)adds.size(), 0};
+            adds.push_back(KsAdd{T0, 1, 0});
+            adds.push_back(KsAdd{T0 + (size_t)n * N, 1, 1});
+            for (uint32_t g = 1; g < P->G; g++) {
+                const uint64_t* Tg = T0 + (size_t)g * ctw;
+                prod.push_back(KsProduct{(uint32_t)src.size(), 1, kg[g]});
+                src.push_back(KsSource{Tg + (size_t)n * N, gg[g]});
+                adds.push_back(KsAdd{Tg, gg[g], 0});
+            }
+            G.prod1 = (uint32_t)prod.size();
+            G.add1 = (uint32_t)adds.size();
+            grp.push_back(G);
         }
-        rc = keyswitch_batch(c, P->level, items.data(), (uint32_t)items.size(), 1);
+        if (!rc)
+            rc = ks_run(c, P->level, src.data(), (uint32_t)src.size(), prod.data(), grp.data(), (uint32_t)grp.size(),
+                        adds.data(), 0);
     }
     // rescale
     for (uint32_t e = 0; !rc && e < S * P->nY; e++) {

@@ -327,6 +327,32 @@ struct KsItem {
 };
 int keyswitch_batch(blb_ctx* ctx, uint32_t level, const KsItem* items, uint32_t count, int accumulate);
 
+// General key-switching pass (keyswitch.cu): sources are ModUp'd once (after
+// the automorphism g), products apply g to the extended digits and multiply by
+// a key, groups sum their products, divide by P once and add their addends.
+struct KsSource {
+    const uint64_t* c1;
+    uint64_t g;
+};
+struct KsProduct {
+    uint32_t src;
+    uint64_t g;
+    const uint64_t* key;
+};
+struct KsAdd {
+    const uint64_t* ptr;  // (level+1) x N, NTT domain, read through sigma_g
+    uint64_t g;
+    uint32_t poly;        // added to out0 (0) or out1 (1)
+};
+struct KsGroup {
+    uint64_t* out0;
+    uint64_t* out1;
+    uint32_t prod0, prod1;  // products [prod0, prod1)
+    uint32_t add0, add1;    // addends [add0, add1)
+};
+int ks_run(blb_ctx* ctx, uint32_t level, const KsSource* sources, uint32_t n_src, const KsProduct* prods,
+           const KsGroup* groups, uint32_t n_groups, const KsAdd* adds, int accumulate);
+
 // encoding (Eq. 2)
 int encode_slots(blb_ctx* ctx, const double* d_z, uint32_t npts, uint32_t n, uint32_t level, double scale,
                  uint64_t* d_out /* npts x (level+1) x N, NTT domain */);

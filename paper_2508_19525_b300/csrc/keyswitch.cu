@@ -246,19 +246,36 @@ extern "C" int blb_keyswitch_noalloc(blb_ctx* c, const blb_keys* K, int32_t rot,
 }
 
 // ===========================================================================
-// Batched key switching (many polynomials, each with its own key and Galois
-// element, in one pass of launches)
+// Key-switching passes over many polynomials (one set of launches per chunk).
+//
+// A pass has sources, products and groups:
+//   source s : a polynomial c1_s (NTT domain) and an automorphism g applied
+//              before the decomposition; its extended digits are built once;
+//   product x: source s, an automorphism g' applied to the extended digits
+//              (hoisting: x~_j -> sigma_g'(x~_j), an index permutation in the
+//              NTT domain) and a key; it contributes sum_j sigma_g'(x~_j) key_j;
+//   group  G : the sum of its products over Q_l u P, one ModDown, then
+//              out_p = [out_p +] sum of its addends of polynomial p (each read
+//              through its own automorphism) + ModDown_p.
+// One rotation is a source, a product and a group; hoisted rotations of one
+// ciphertext share the source; a giant-step sum puts several products (each
+// its own source) into one group.
 // ===========================================================================
 namespace {
 
-struct DevItem {
-    const uint64_t* c0;
+struct DevSource {
     const uint64_t* c1;
-    const uint64_t* add1;
+    uint64_t g;
+};
+struct DevProduct {
+    uint32_t src;
+    uint64_t g;
     const uint64_t* key;
+};
+struct DevGroup {
     uint64_t* out0;
     uint64_t* out1;
-    uint64_t g;
+    uint32_t prod0, prod1, add0, add1;
 };
 
 __device__ __forceinline__ uint32_t perm_index(uint32_t k, uint32_t logN, uint64_t g)
@@ -270,21 +287,21 @@ __device__ __forceinline__ uint32_t perm_index(uint32_t k, uint32_t logN, uint64
     return __brev((ge - 1) >> 1) >> (32 - logN);
 }
 
-// din[item][i][k] = c1[i][perm(k)] and coef = din (the latter transformed in place)
-__global__ void k_ksb_gather(uint64_t* __restrict__ din, uint64_t* __restrict__ coef, const DevItem* __restrict__ it,
-                             uint32_t n, uint32_t logN)
+// din[src][i][k] = c1[i][perm(k)] and coef = din (the latter transformed in place)
+__global__ void k_ksb_gather(uint64_t* __restrict__ din, uint64_t* __restrict__ coef,
+                             const DevSource* __restrict__ srcs, uint32_t n, uint32_t logN)
 {
     const uint32_t N = 1u << logN;
-    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x, i = blockIdx.y, item = blockIdx.z;
+    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x, i = blockIdx.y, s = blockIdx.z;
     if (k >= N) return;
-    const DevItem d = it[item];
+    const DevSource d = srcs[s];
     const uint64_t v = d.c1[(size_t)i * N + perm_index(k, logN, d.g)];
-    const size_t o = ((size_t)item * n + i) * N + k;
+    const size_t o = ((size_t)s * n + i) * N + k;
     din[o] = v;
     coef[o] = v;
 }
 
-// ModUp of every digit of every item: grid.y = item * beta + j
+// ModUp of every digit of every source: grid.y = source * beta + j
 __global__ void k_ksb_modup(const uint64_t* __restrict__ coef, uint64_t* __restrict__ ext,
                             const ConvTable* __restrict__ tabs, uint32_t n, uint32_t E, uint32_t beta,
                             uint32_t alpha, const uint64_t* __restrict__ qs, const uint64_t* __restrict__ bar,
@@ -292,14 +309,14 @@ __global__ void k_ksb_modup(const uint64_t* __restrict__ coef, uint64_t* __restr
 {
     const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= N) return;
-    const uint32_t item = blockIdx.y / beta, j = blockIdx.y % beta;
+    const uint32_t src = blockIdx.y / beta, j = blockIdx.y % beta;
     const ConvTable* tab = tabs + j;
     const uint32_t ns = tab->ns, nt = tab->nt;
-    const uint64_t* src = coef + ((size_t)item * n + j * alpha) * N + c;
-    uint64_t* dst = ext + ((size_t)item * beta + j) * E * N + c;
+    const uint64_t* in = coef + ((size_t)src * n + j * alpha) * N + c;
+    uint64_t* dst = ext + ((size_t)src * beta + j) * E * N + c;
     uint64_t y[BLB_MAXP];
     for (uint32_t i = 0; i < ns; i++)
-        y[i] = mul_shoup(src[(size_t)i * N], tab->hat_inv[i], tab->hat_inv_sh[i], qs[tab->src[i]]);
+        y[i] = mul_shoup(in[(size_t)i * N], tab->hat_inv[i], tab->hat_inv_sh[i], qs[tab->src[i]]);
     for (uint32_t t = 0; t < nt; t++) {
         const uint32_t pt = tab->dst[t];
         acc128 a{0, 0};
@@ -312,101 +329,86 @@ __global__ void k_ksb_modup(const uint64_t* __restrict__ coef, uint64_t* __restr
 __global__ void k_ksb_digit_rows(uint64_t* __restrict__ ext, const uint64_t* __restrict__ din, uint32_t n, uint32_t E,
                                  uint32_t beta, uint32_t alpha, uint32_t N)
 {
-    const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x, t = blockIdx.y, item = blockIdx.z;
+    const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x, t = blockIdx.y, src = blockIdx.z;
     if (c >= N) return;
     const uint32_t j = t / alpha;
-    ext[(((size_t)item * beta + j) * E + t) * N + c] = din[((size_t)item * n + t) * N + c];
+    ext[(((size_t)src * beta + j) * E + t) * N + c] = din[((size_t)src * n + t) * N + c];
 }
 
-// acc[item][p][t] = sum_j ext[item][j][t] * key_item[j][p][kt]
+// acc[group][p][t] = sum over the group's products x of sum_j sigma_x(ext[src_x][j][t]) key_x[j][p][kt]
 __global__ void k_ksb_inner(uint64_t* __restrict__ acc, const uint64_t* __restrict__ ext,
-                            const DevItem* __restrict__ it, LimbMap emap, uint32_t n, uint32_t E, uint32_t beta,
-                            uint32_t nQ, uint32_t np, const uint64_t* __restrict__ qs,
-                            const uint64_t* __restrict__ bar, uint32_t N)
+                            const DevGroup* __restrict__ groups, const DevProduct* __restrict__ prods, LimbMap emap,
+                            uint32_t n, uint32_t E, uint32_t beta, uint32_t nQ, uint32_t np,
+                            const uint64_t* __restrict__ qs, const uint64_t* __restrict__ bar, uint32_t logN)
 {
-    const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x, t = blockIdx.y, item = blockIdx.z;
+    const uint32_t N = 1u << logN;
+    const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x, t = blockIdx.y, gr = blockIdx.z;
     if (c >= N) return;
     const uint32_t pi = emap.p[t];
     const uint32_t kt = t < n ? t : nQ + (t - n);
-    const uint64_t* key = it[item].key;
-    const uint64_t* x = ext + (size_t)item * beta * E * N + (size_t)t * N + c;
-    acc128 a0{0, 0}, a1{0, 0};
-    for (uint32_t j = 0; j < beta; j++) {
-        uint64_t v = x[(size_t)j * E * N];
-        mad128(a0, v, key[(((size_t)j * 2 + 0) * np + kt) * N + c]);
-        mad128(a1, v, key[(((size_t)j * 2 + 1) * np + kt) * N + c]);
-    }
     const uint64_t q = qs[pi], r0 = bar[2 * pi], r1 = bar[2 * pi + 1];
-    uint64_t* o = acc + (size_t)item * 2 * E * N + (size_t)t * N + c;
-    o[0] = barrett128(a0.lo, a0.hi, q, r0, r1);
-    o[(size_t)E * N] = barrett128(a1.lo, a1.hi, q, r0, r1);
+    const DevGroup G = groups[gr];
+    uint64_t s0 = 0, s1 = 0;
+    for (uint32_t x = G.prod0; x < G.prod1; x++) {
+        const DevProduct P = prods[x];
+        const uint64_t* xs = ext + (size_t)P.src * beta * E * N + (size_t)t * N + perm_index(c, logN, P.g);
+        acc128 a0{0, 0}, a1{0, 0};
+        for (uint32_t j = 0; j < beta; j++) {
+            const uint64_t v = xs[(size_t)j * E * N];
+            mad128(a0, v, P.key[(((size_t)j * 2 + 0) * np + kt) * N + c]);
+            mad128(a1, v, P.key[(((size_t)j * 2 + 1) * np + kt) * N + c]);
+        }
+        s0 = add_mod(s0, barrett128(a0.lo, a0.hi, q, r0, r1), q);
+        s1 = add_mod(s1, barrett128(a1.lo, a1.hi, q, r0, r1), q);
+    }
+    uint64_t* o = acc + (size_t)gr * 2 * E * N + (size_t)t * N + c;
+    o[0] = s0;
+    o[(size_t)E * N] = s1;
 }
 
-// outputs: p = 0: [out0 +] sigma(c0) + (acc0 - cv0) P^-1;  p = 1: [out1 +] sigma(add1) + (acc1 - cv1) P^-1
-__global__ void k_ksb_finish(const DevItem* __restrict__ it, const uint64_t* __restrict__ acc,
-                             const uint64_t* __restrict__ cv, uint32_t n, uint32_t E, PInv pinv,
-                             const uint64_t* __restrict__ qs, uint32_t logN, int accumulate)
+// out_p = [out_p +] sum_{addends of p} add[perm(k)] + (acc_p - cv_p) P^-1
+__global__ void k_ksb_finish(const DevGroup* __restrict__ groups, const KsAdd* __restrict__ adds,
+                             const uint64_t* __restrict__ acc, const uint64_t* __restrict__ cv, uint32_t n,
+                             uint32_t E, PInv pinv, const uint64_t* __restrict__ qs, uint32_t logN, int accumulate)
 {
     const uint32_t N = 1u << logN;
-    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x, row = blockIdx.y, item = blockIdx.z;
+    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x, row = blockIdx.y, gr = blockIdx.z;
     if (k >= N) return;
     const uint32_t p = row / n, i = row % n;
-    const DevItem d = it[item];
+    const DevGroup G = groups[gr];
     const uint64_t q = qs[i];
-    const uint64_t a = acc[(((size_t)item * 2 + p) * E + i) * N + k];
-    const uint64_t v = cv[(((size_t)item * 2 + p) * n + i) * N + k];
+    const uint64_t a = acc[(((size_t)gr * 2 + p) * E + i) * N + k];
+    const uint64_t v = cv[(((size_t)gr * 2 + p) * n + i) * N + k];
     uint64_t r = mul_shoup(sub_mod(a, v, q), pinv.w[i], pinv.wp[i], q);
-    const uint64_t* addp = p ? d.add1 : d.c0;
-    if (addp) r = add_mod(r, addp[(size_t)i * N + perm_index(k, logN, d.g)], q);
-    uint64_t* o = (p ? d.out1 : d.out0) + (size_t)i * N + k;
+    for (uint32_t x = G.add0; x < G.add1; x++) {
+        const KsAdd A = adds[x];
+        if (A.poly == p) r = add_mod(r, A.ptr[(size_t)i * N + perm_index(k, logN, A.g)], q);
+    }
+    uint64_t* o = (p ? G.out1 : G.out0) + (size_t)i * N + k;
     *o = accumulate ? add_mod(*o, r, q) : r;
 }
 
 }  // namespace
 
-int keyswitch_batch(blb_ctx* ctx, uint32_t level, const KsItem* items, uint32_t count, int accumulate)
+int ks_run(blb_ctx* ctx, uint32_t level, const KsSource* sources, uint32_t n_src, const KsProduct* prods,
+           const KsGroup* groups, uint32_t n_groups, const KsAdd* adds, int accumulate)
 {
-    if (count == 0) return BLB_OK;
+    if (n_groups == 0) return BLB_OK;
     const uint32_t N = ctx->N, n = level + 1, nP = ctx->nP, E = n + nP;
     const uint32_t alpha = ctx->alpha, beta = (n + alpha - 1) / alpha;
-    // words per item: din n + coef n + ext beta E + acc 2E + cv 2n
-    const size_t per_item = ((size_t)2 * n + (size_t)beta * E + 2 * (size_t)E + 2 * (size_t)n) * N;
-    const size_t budget = (size_t)1 << 27;  // 1 GiB of words per chunk
-    const uint32_t chunk = (uint32_t)std::max<size_t>(1, std::min<size_t>(count, budget / per_item));
-    // rows to transform for one chunk of `chunk` items
-    std::vector<uint32_t> ext_rows, p_rows;
-    for (uint32_t item = 0; item < chunk; item++) {
-        for (uint32_t j = 0; j < beta; j++) {
-            const uint32_t lo = j * alpha, hi = std::min((j + 1) * alpha, n);
-            for (uint32_t t = 0; t < E; t++) {
-                if (t >= lo && t < hi) continue;
-                const uint32_t prime = t < n ? t : ctx->nQ + (t - n);
-                ext_rows.push_back((uint32_t)(((size_t)item * beta + j) * E + t) | (prime << 24));
-            }
-        }
-        for (uint32_t pp = 0; pp < 2; pp++)
-            for (uint32_t k = 0; k < nP; k++)
-                p_rows.push_back((uint32_t)(((size_t)item * 2 + pp) * E + n + k) | ((ctx->nQ + k) << 24));
+    const size_t per_src = ((size_t)2 * n + (size_t)beta * E) * N;  // din, coef, ext
+    const size_t per_grp = ((size_t)2 * E + (size_t)2 * n) * N;     // acc, cv
+    const size_t budget = (size_t)1 << 27;                           // 1 GiB of words per chunk
+    // extension rows of one source and P rows of one group (row | prime << 24)
+    std::vector<uint32_t> src_rows, grp_rows;
+    for (uint32_t j = 0; j < beta; j++) {
+        const uint32_t lo = j * alpha, hi = std::min((j + 1) * alpha, n);
+        for (uint32_t t = 0; t < E; t++)
+            if (t < lo || t >= hi) src_rows.push_back(j * E + t);
     }
-    if ((size_t)chunk * beta * E >= (1u << 24)) return blb_fail(BLB_ERR_ARG, "key-switch batch too large");
-    const size_t table_words = (ext_rows.size() + p_rows.size() + 1) / 2 + (size_t)chunk * sizeof(DevItem) / 8 + 8;
-    const size_t need = per_item * chunk + table_words;
-    if (need > ctx->batch_words) {
-        dev_free(ctx, ctx->batch, ctx->batch_words * 8);
-        ctx->batch = (uint64_t*)dev_alloc(ctx, need * 8);
-        ctx->batch_words = ctx->batch ? need : 0;
-        if (!ctx->batch) return blb_fail(BLB_ERR_OOM, "key-switch batch arena");
-    }
-    uint64_t* din = ctx->batch;
-    uint64_t* coef = din + (size_t)chunk * n * N;
-    uint64_t* ext = coef + (size_t)chunk * n * N;
-    uint64_t* acc = ext + (size_t)chunk * beta * E * N;
-    uint64_t* cv = acc + (size_t)chunk * 2 * E * N;
-    DevItem* d_items = (DevItem*)(cv + (size_t)chunk * 2 * n * N);
-    uint32_t* d_ext_rows = (uint32_t*)(d_items + chunk);
-    uint32_t* d_p_rows = d_ext_rows + ext_rows.size();
-    BLB_CUDA(cudaMemcpyAsync(d_ext_rows, ext_rows.data(), ext_rows.size() * 4, cudaMemcpyHostToDevice, ctx->stream));
-    BLB_CUDA(cudaMemcpyAsync(d_p_rows, p_rows.data(), p_rows.size() * 4, cudaMemcpyHostToDevice, ctx->stream));
+    for (uint32_t pp = 0; pp < 2; pp++)
+        for (uint32_t k = 0; k < nP; k++) grp_rows.push_back(pp * E + n + k);
+    const auto prime_of = [&](uint32_t t) { return t < n ? t : ctx->nQ + (t - n); };
     PInv pinv{};
     for (uint32_t i = 0; i < n; i++) {
         pinv.w[i] = ctx->P_inv_mod_q[i];
@@ -414,36 +416,145 @@ int keyswitch_batch(blb_ctx* ctx, uint32_t level, const KsItem* items, uint32_t 
     }
     const LimbMap emap = ctx->extmap(level);
     const uint32_t gx = (N + kT - 1) / kT;
-    for (uint32_t first = 0; first < count; first += chunk) {
-        const uint32_t cnt = std::min(chunk, count - first);
-        ProfScope prof(ctx, "keyswitch", ((uint64_t)n + 2ull * beta * E + 2ull * n) * N * 8 * cnt);
-        std::vector<DevItem> h(cnt);
-        for (uint32_t i = 0; i < cnt; i++) {
-            const KsItem& s = items[first + i];
-            h[i] = DevItem{s.c0, s.c1, s.add1, s.key, s.out0, s.out1, s.g};
+    std::vector<int32_t> local(n_src, -1);
+    for (uint32_t g0 = 0; g0 < n_groups;) {
+        // chunk: groups g0..g1 and the sources their products need
+        std::vector<uint32_t> used;
+        uint32_t g1 = g0;
+        while (g1 < n_groups) {
+            uint32_t extra = 0;
+            for (uint32_t x = groups[g1].prod0; x < groups[g1].prod1; x++)
+                if (local[prods[x].src] == -1) {
+                    local[prods[x].src] = -2;  // counted for this group, not yet placed
+                    extra++;
+                }
+            const size_t need = (used.size() + extra) * per_src + (size_t)(g1 - g0 + 1) * per_grp;
+            if (g1 > g0 && need > budget) {
+                for (uint32_t x = groups[g1].prod0; x < groups[g1].prod1; x++)
+                    if (local[prods[x].src] <= -2) local[prods[x].src] = -1;
+                break;
+            }
+            for (uint32_t x = groups[g1].prod0; x < groups[g1].prod1; x++)
+                if (local[prods[x].src] <= -2) {
+                    local[prods[x].src] = (int32_t)used.size();
+                    used.push_back(prods[x].src);
+                }
+            g1++;
         }
-        BLB_CUDA(cudaMemcpyAsync(d_items, h.data(), cnt * sizeof(DevItem), cudaMemcpyHostToDevice, ctx->stream));
-        k_ksb_gather<<<dim3(gx, n, cnt), kT, 0, ctx->stream>>>(din, coef, d_items, n, ctx->logN);
+        const uint32_t ns = (uint32_t)used.size(), ng = g1 - g0;
+        // device tables for the chunk
+        std::vector<DevSource> hs(ns);
+        for (uint32_t s = 0; s < ns; s++) hs[s] = DevSource{sources[used[s]].c1, sources[used[s]].g};
+        std::vector<DevProduct> hp;
+        std::vector<DevGroup> hg(ng);
+        std::vector<KsAdd> ha;
+        for (uint32_t g = 0; g < ng; g++) {
+            const KsGroup& G = groups[g0 + g];
+            hg[g].out0 = G.out0;
+            hg[g].out1 = G.out1;
+            hg[g].prod0 = (uint32_t)hp.size();
+            for (uint32_t x = G.prod0; x < G.prod1; x++)
+                hp.push_back(DevProduct{(uint32_t)local[prods[x].src], prods[x].g, prods[x].key});
+            hg[g].prod1 = (uint32_t)hp.size();
+            hg[g].add0 = (uint32_t)ha.size();
+            for (uint32_t x = G.add0; x < G.add1; x++) ha.push_back(adds[x]);
+            hg[g].add1 = (uint32_t)ha.size();
+        }
+        std::vector<uint32_t> ext_rows, p_rows;
+        for (uint32_t s = 0; s < ns; s++)
+            for (uint32_t r : src_rows) ext_rows.push_back((uint32_t)((size_t)s * beta * E + r) | (prime_of(r % E) << 24));
+        for (uint32_t g = 0; g < ng; g++)
+            for (uint32_t r : grp_rows) p_rows.push_back((uint32_t)((size_t)g * 2 * E + r) | (prime_of(r % E) << 24));
+        if ((size_t)ns * beta * E >= (1u << 24) || (size_t)ng * 2 * E >= (1u << 24))
+            return blb_fail(BLB_ERR_ARG, "key-switch batch too large");
+        auto words = [](size_t bytes) { return (bytes + 7) / 8; };
+        const size_t table_words = words(hs.size() * sizeof(DevSource)) + words(hp.size() * sizeof(DevProduct)) +
+                                   words(hg.size() * sizeof(DevGroup)) + words(ha.size() * sizeof(KsAdd)) +
+                                   words((ext_rows.size() + p_rows.size()) * 4) + 8;
+        const size_t need = (size_t)ns * per_src + (size_t)ng * per_grp + table_words;
+        if (need > ctx->batch_words) {
+            BLB_CUDA(cudaStreamSynchronize(ctx->stream));  // the arena may still be read by earlier launches
+            dev_free(ctx, ctx->batch, ctx->batch_words * 8);
+            ctx->batch = (uint64_t*)dev_alloc(ctx, need * 8);
+            ctx->batch_words = ctx->batch ? need : 0;
+            if (!ctx->batch) return blb_fail(BLB_ERR_OOM, "key-switch batch arena");
+        }
+        uint64_t* din = ctx->batch;
+        uint64_t* coef = din + (size_t)ns * n * N;
+        uint64_t* ext = coef + (size_t)ns * n * N;
+        uint64_t* acc = ext + (size_t)ns * beta * E * N;
+        uint64_t* cv = acc + (size_t)ng * 2 * E * N;
+        uint64_t* tw = cv + (size_t)ng * 2 * n * N;
+        DevSource* d_src = (DevSource*)tw;
+        tw += words(hs.size() * sizeof(DevSource));
+        DevProduct* d_prod = (DevProduct*)tw;
+        tw += words(hp.size() * sizeof(DevProduct));
+        DevGroup* d_grp = (DevGroup*)tw;
+        tw += words(hg.size() * sizeof(DevGroup));
+        KsAdd* d_add = (KsAdd*)tw;
+        tw += words(ha.size() * sizeof(KsAdd));
+        uint32_t* d_ext_rows = (uint32_t*)tw;
+        uint32_t* d_p_rows = d_ext_rows + ext_rows.size();
+        auto up = [&](void* dst, const void* src, size_t bytes) {
+            return bytes ? cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, ctx->stream) : cudaSuccess;
+        };
+        BLB_CUDA(up(d_src, hs.data(), hs.size() * sizeof(DevSource)));
+        BLB_CUDA(up(d_prod, hp.data(), hp.size() * sizeof(DevProduct)));
+        BLB_CUDA(up(d_grp, hg.data(), hg.size() * sizeof(DevGroup)));
+        BLB_CUDA(up(d_add, ha.data(), ha.size() * sizeof(KsAdd)));
+        BLB_CUDA(up(d_ext_rows, ext_rows.data(), ext_rows.size() * 4));
+        BLB_CUDA(up(d_p_rows, p_rows.data(), p_rows.size() * 4));
+        // algorithmic bytes: each source read and its digits written once; each
+        // product reads its digits and key; each group writes its output
+        ProfScope prof(ctx, "keyswitch",
+                       ((uint64_t)ns * (n + (uint64_t)beta * E) + (uint64_t)hp.size() * 3 * beta * E +
+                        (uint64_t)ng * 2 * n) * N * 8);
+        if (ns) {
+            k_ksb_gather<<<dim3(gx, n, ns), kT, 0, ctx->stream>>>(din, coef, d_src, n, ctx->logN);
+            BLB_LAUNCHED();
+            BLB_TRY(ntt_inverse(ctx, coef, ns * n, ctx->qmap(n)));
+            k_ksb_modup<<<dim3(gx, ns * beta), kT, 0, ctx->stream>>>(coef, ext, ctx->d_modup[(size_t)level * ctx->dnum],
+                                                                     n, E, beta, alpha, ctx->d_q, ctx->d_bar, N);
+            BLB_LAUNCHED();
+            BLB_TRY(ntt_forward_list(ctx, ext, (uint32_t)ext_rows.size(), d_ext_rows));
+            k_ksb_digit_rows<<<dim3(gx, n, ns), kT, 0, ctx->stream>>>(ext, din, n, E, beta, alpha, N);
+            BLB_LAUNCHED();
+        }
+        k_ksb_inner<<<dim3(gx, E, ng), kT, 0, ctx->stream>>>(acc, ext, d_grp, d_prod, emap, n, E, beta, ctx->nQ,
+                                                              ctx->np, ctx->d_q, ctx->d_bar, ctx->logN);
         BLB_LAUNCHED();
-        BLB_TRY(ntt_inverse(ctx, coef, cnt * n, ctx->qmap(n)));
-        k_ksb_modup<<<dim3(gx, cnt * beta), kT, 0, ctx->stream>>>(coef, ext, ctx->d_modup[(size_t)level * ctx->dnum],
-                                                                  n, E, beta, alpha, ctx->d_q, ctx->d_bar, N);
+        BLB_TRY(ntt_inverse_list(ctx, acc, (uint32_t)p_rows.size(), d_p_rows));
+        k_moddown_conv<<<dim3(gx, 2 * ng), kT, 0, ctx->stream>>>(acc + (size_t)n * N, (size_t)E * N, ctx->d_moddown, n,
+                                                                 cv, (size_t)n * N, ctx->d_q, ctx->d_bar, N);
         BLB_LAUNCHED();
-        const uint32_t ext_per_item = (uint32_t)(ext_rows.size() / chunk);
-        BLB_TRY(ntt_forward_list(ctx, ext, cnt * ext_per_item, d_ext_rows));
-        k_ksb_digit_rows<<<dim3(gx, n, cnt), kT, 0, ctx->stream>>>(ext, din, n, E, beta, alpha, N);
+        BLB_TRY(ntt_forward(ctx, cv, ng * 2 * n, ctx->qmap(n)));
+        k_ksb_finish<<<dim3(gx, 2 * n, ng), kT, 0, ctx->stream>>>(d_grp, d_add, acc, cv, n, E, pinv, ctx->d_q,
+                                                                  ctx->logN, accumulate);
         BLB_LAUNCHED();
-        k_ksb_inner<<<dim3(gx, E, cnt), kT, 0, ctx->stream>>>(acc, ext, d_items, emap, n, E, beta, ctx->nQ, ctx->np,
-                                                              ctx->d_q, ctx->d_bar, N);
-        BLB_LAUNCHED();
-        BLB_TRY(ntt_inverse_list(ctx, acc, cnt * 2 * nP, d_p_rows));
-        k_moddown_conv<<<dim3(gx, 2 * cnt), kT, 0, ctx->stream>>>(acc + (size_t)n * N, (size_t)E * N, ctx->d_moddown,
-                                                                  n, cv, (size_t)n * N, ctx->d_q, ctx->d_bar, N);
-        BLB_LAUNCHED();
-        BLB_TRY(ntt_forward(ctx, cv, cnt * 2 * n, ctx->qmap(n)));
-        k_ksb_finish<<<dim3(gx, 2 * n, cnt), kT, 0, ctx->stream>>>(d_items, acc, cv, n, E, pinv, ctx->d_q, ctx->logN,
-                                                                   accumulate);
-        BLB_LAUNCHED();
+        for (uint32_t s : used) local[s] = -1;
+        g0 = g1;
     }
     return BLB_OK;
+}
+
+int keyswitch_batch(blb_ctx* ctx, uint32_t level, const KsItem* items, uint32_t count, int accumulate)
+{
+    std::vector<KsSource> src(count);
+    std::vector<KsProduct> prod(count);
+    std::vector<KsGroup> grp(count);
+    std::vector<KsAdd> adds;
+    for (uint32_t i = 0; i < count; i++) {
+        const KsItem& it = items[i];
+        src[i] = KsSource{it.c1, it.g};
+        prod[i] = KsProduct{i, 1, it.key};
+        grp[i].out0 = it.out0;
+        grp[i].out1 = it.out1;
+        grp[i].prod0 = i;
+        grp[i].prod1 = i + 1;
+        grp[i].add0 = (uint32_t)adds.size();
+        if (it.c0) adds.push_back(KsAdd{it.c0, it.g, 0});
+        if (it.add1) adds.push_back(KsAdd{it.add1, it.g, 1});
+        grp[i].add1 = (uint32_t)adds.size();
+    }
+    return ks_run(ctx, level, src.data(), count, prod.data(), grp.data(), count, adds.data(), accumulate);
 }
