@@ -551,6 +551,20 @@ def ncu_case(seqs=1):
                       "plan": plan.info()}))
 
 
+def ncu_step():
+    """One BERT-base step bracketed by cudaProfilerStart/Stop (after one warm-up
+    step), for a launch list with `ncu --profile-from-start off`."""
+    import torch
+    w = Workload(torch.device("cuda", 0))
+    w.step()
+    w.ctx.sync()
+    torch.cuda.profiler.start()
+    w.step()
+    w.ctx.sync()
+    torch.cuda.profiler.stop()
+    print(json.dumps({"ncu_step": WORKLOAD}))
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -562,12 +576,15 @@ def main():
     ap.add_argument("--cpu-products", type=int, default=48)
     ap.add_argument("--ncu-case", action="store_true", help="run the small profiling case and exit")
     ap.add_argument("--ncu-seqs", type=int, default=1, help="sequences in the profiling case")
+    ap.add_argument("--ncu-step", action="store_true", help="run one profiled BERT-base step and exit")
     ap.add_argument("--batch", type=int, default=8, help="sequences per batched step (1 = skip)")
     ap.add_argument("--no-attention", dest="attention", action="store_false",
                     help="skip the matmul_cc attention measurement")
     args = ap.parse_args()
     if args.ncu_case:
         return ncu_case(args.ncu_seqs)
+    if args.ncu_step:
+        return ncu_step()
     args.cpu_sample = (args.cpu_rotations, args.cpu_products)
     if args.impl == "reference":
         run_reference(args)

@@ -13,6 +13,7 @@
 // conversion, without overflow correction (the overflow is a multiple of the
 // digit modulus, which the key's gadget factor cancels).  Every step is an exact integer function of d's
 // coefficients, so any correct schedule of it yields the same limbs.
+#include <algorithm>
 #include <mutex>
 #include <string>
 
@@ -398,7 +399,7 @@ int ks_run(blb_ctx* ctx, uint32_t level, const KsSource* sources, uint32_t n_src
     const uint32_t alpha = ctx->alpha, beta = (n + alpha - 1) / alpha;
     const size_t per_src = ((size_t)2 * n + (size_t)beta * E) * N;  // din, coef, ext
     const size_t per_grp = ((size_t)2 * E + (size_t)2 * n) * N;     // acc, cv
-    const size_t budget = (size_t)1 << 27;                           // 1 GiB of words per chunk
+    const size_t budget = (size_t)1 << 29;                           // 4 GiB per chunk
     // extension rows of one source and P rows of one group (row | prime << 24)
     std::vector<uint32_t> src_rows, grp_rows;
     for (uint32_t j = 0; j < beta; j++) {
@@ -442,6 +443,14 @@ int ks_run(blb_ctx* ctx, uint32_t level, const KsSource* sources, uint32_t n_src
             g1++;
         }
         const uint32_t ns = (uint32_t)used.size(), ng = g1 - g0;
+        // groups of the chunk ordered by their first key, so that the groups
+        // sharing a key run back to back and the key is read from HBM about once
+        std::vector<uint32_t> order(ng);
+        for (uint32_t g = 0; g < ng; g++) order[g] = g0 + g;
+        auto key_of = [&](uint32_t g) {
+            return groups[g].prod1 > groups[g].prod0 ? (uintptr_t)prods[groups[g].prod0].key : (uintptr_t)0;
+        };
+        std::stable_sort(order.begin(), order.end(), [&](uint32_t a, uint32_t b) { return key_of(a) < key_of(b); });
         // device tables for the chunk
         std::vector<DevSource> hs(ns);
         for (uint32_t s = 0; s < ns; s++) hs[s] = DevSource{sources[used[s]].c1, sources[used[s]].g};
@@ -449,7 +458,7 @@ int ks_run(blb_ctx* ctx, uint32_t level, const KsSource* sources, uint32_t n_src
         std::vector<DevGroup> hg(ng);
         std::vector<KsAdd> ha;
         for (uint32_t g = 0; g < ng; g++) {
-            const KsGroup& G = groups[g0 + g];
+            const KsGroup& G = groups[order[g]];
             hg[g].out0 = G.out0;
             hg[g].out1 = G.out1;
             hg[g].prod0 = (uint32_t)hp.size();
