@@ -210,45 +210,36 @@ class Workload:
         self.p1_host = torch.zeros((self.n_out, self.N), dtype=torch.uint64).pin_memory()
         self.nonce = 1000
 
+    def nonces(self, k):
+        self.nonce += k
+        return list(range(self.nonce - k + 1, self.nonce + 1))
+
     def step(self, host=False, keep=False):
         ctx, keys = self.ctx, self.keys
         Z = self.Zhost if host else self.Zdev
         p0 = self.p0_host if host else self.p0_dev
         p1 = self.p1_host if host else self.p1_dev
-        cts = []
-        for c in range(self.n_in):
-            self.nonce += 1
-            cts.append(ctx.encrypt(keys, ctx.encode(Z[c], LEVEL), self.nonce))
+        cts = ctx.encrypt_batch(keys, ctx.encode_batch(Z, LEVEL), self.nonces(self.n_in))
         Y = ctx.matmul_cp_plan(keys, self.plan_qkv, cts)
         O = ctx.matmul_cp_plan(keys, self.plan_o, Y[:self.n_in])
         outs = Y[self.n_in:] + O
-        for i, y in enumerate(outs):
-            self.nonce += 1
-            masked, _ = ctx.he2mpc(keys, y, self.nonce, share_out=p1[i])
-            ctx.decrypt(keys, masked, coeffs=True, slots=False, coeff_out=p0[i:i + 1])
+        masked, _ = ctx.he2mpc_batch(keys, outs, self.nonces(len(outs)), share_out=p1)
+        ctx.decrypt_batch(keys, masked, coeff_out=p0)
         return (Y, O) if keep else None
 
     def step_batched(self, S):
         """S sequences through the same plans in one batched pass per product."""
         ctx, keys = self.ctx, self.keys
-        seqs = []
-        for _ in range(S):
-            cts = []
-            for c in range(self.n_in):
-                self.nonce += 1
-                cts.append(ctx.encrypt(keys, ctx.encode(self.Zdev[c], LEVEL), self.nonce))
-            seqs.append(cts)
+        seqs = [ctx.encrypt_batch(keys, ctx.encode_batch(self.Zdev, LEVEL), self.nonces(self.n_in))
+                for _ in range(S)]
         Ys = ctx.matmul_cp_batch(keys, self.plan_qkv, seqs)
         Os = ctx.matmul_cp_batch(keys, self.plan_o, [Y[:self.n_in] for Y in Ys])
-        if getattr(self, "bp0", None) is None or self.bp0.shape[0] != S * self.n_out:
-            self.bp0 = self.torch.zeros((S * self.n_out, self.N), dtype=self.torch.uint64, device=self.p0_dev.device)
+        outs = [y for Y, O in zip(Ys, Os) for y in Y[self.n_in:] + O]
+        if getattr(self, "bp0", None) is None or self.bp0.shape[0] != len(outs):
+            self.bp0 = self.torch.zeros((len(outs), self.N), dtype=self.torch.uint64, device=self.p0_dev.device)
             self.bp1 = self.torch.zeros_like(self.bp0)
-        for s, (Y, O) in enumerate(zip(Ys, Os)):
-            for i, y in enumerate(Y[self.n_in:] + O):
-                self.nonce += 1
-                r = s * self.n_out + i
-                masked, _ = ctx.he2mpc(keys, y, self.nonce, share_out=self.bp1[r])
-                ctx.decrypt(keys, masked, coeffs=True, slots=False, coeff_out=self.bp0[r:r + 1])
+        masked, _ = ctx.he2mpc_batch(keys, outs, self.nonces(len(outs)), share_out=self.bp1)
+        ctx.decrypt_batch(keys, masked, coeff_out=self.bp0)
 
     def accuracy(self):
         Y, O = self.step(keep=True)

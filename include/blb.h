@@ -254,6 +254,28 @@ int blb_matmul_cc(blb_ctx* ctx, const blb_keys* keys, blb_ct* const* A, blb_ct* 
 int blb_he2mpc(blb_ctx* ctx, const blb_keys* keys, const blb_ct* ct, uint64_t nonce,
                blb_ct** masked_for_p0, uint64_t* p1_share);
 
+/* ---- batches of the calls above -----------------------------------------------
+ * Each computes, for every member, exactly what the single call computes (same
+ * Philox streams, bit-identical limbs), but runs each step once over the whole
+ * batch.  Handles in out/masked are new objects owned by the caller; on error
+ * none is returned (all entries NULL).
+ *
+ * blb_encode_batch: vals holds count x n doubles (member k at vals + k n, host
+ * or device), all at `level` and `scale`.
+ * blb_encrypt_batch: pts share one level; nonces[k] is member k's nonce. */
+int blb_encode_batch(blb_ctx* ctx, const double* vals, uint64_t n, uint32_t count, uint32_t level,
+                     double scale, blb_pt** out);
+int blb_encrypt_batch(blb_ctx* ctx, const blb_keys* keys, const blb_pt* const* pts, uint32_t count,
+                      const uint64_t* nonces, blb_ct** out);
+/* Masking of count ciphertexts (any levels): p1_shares receives count x N words
+ * (member k at p1_shares + k N), masked[k] a new level-0 ciphertext. */
+int blb_he2mpc_batch(blb_ctx* ctx, const blb_keys* keys, const blb_ct* const* cts, uint32_t count,
+                     const uint64_t* nonces, blb_ct** masked, uint64_t* p1_shares);
+/* Decryption of count ciphertexts of one level and size: coeff_limbs (nullable)
+ * receives count x (level+1) x N words, slots (nullable) count x N/2 doubles. */
+int blb_decrypt_batch(blb_ctx* ctx, const blb_keys* keys, const blb_ct* const* cts, uint32_t count,
+                      uint64_t* coeff_limbs, double* slots);
+
 /* ---- low-level transforms (parity testing) ------------------------------------
  * Forward / inverse negacyclic NTT of `rows` limbs of N words in place (host or
  * device).  Limb r uses prime q_{prime_idx[r]} (host array).  Forward output

@@ -69,6 +69,10 @@ SIGNATURES = {
     "blb_ct_export": (ctypes.c_int, [_vp, _vp, _vp]),
     "blb_ct_import": (ctypes.c_int, [_vp, _vp, _u32, _u32, _dbl, _pp]),
     "blb_decrypt": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
+    "blb_encode_batch": (ctypes.c_int, [_vp, _vp, _u64, _u32, _u32, _dbl, _vp]),
+    "blb_encrypt_batch": (ctypes.c_int, [_vp, _vp, _vp, _u32, _vp, _vp]),
+    "blb_he2mpc_batch": (ctypes.c_int, [_vp, _vp, _vp, _u32, _vp, _vp, _vp]),
+    "blb_decrypt_batch": (ctypes.c_int, [_vp, _vp, _vp, _u32, _vp, _vp]),
     "blb_rotate": (ctypes.c_int, [_vp, _vp, _vp, _i32, _pp]),
     "blb_rescale": (ctypes.c_int, [_vp, _vp]),
     "blb_add": (ctypes.c_int, [_vp, _vp, _vp, _pp]),
@@ -304,6 +308,16 @@ class Context:
         n = int(vals.numel() if hasattr(vals, "numel") else vals.size)
         return self._new(Plaintext, lib().blb_encode, _ptr(vals), _u64(n), level, _dbl(scale))
 
+    def encode_batch(self, vals, level, scale=None):
+        """vals: (count, n) host array or device tensor -> list of count plaintexts."""
+        scale = self.scale if scale is None else scale
+        if isinstance(vals, np.ndarray):
+            vals = np.ascontiguousarray(vals, np.float64)
+        count, n = int(vals.shape[0]), int(vals.shape[1])
+        out = (ctypes.c_void_p * count)()
+        _check(lib().blb_encode_batch(self.h, _ptr(vals), _u64(n), count, level, _dbl(scale), out))
+        return [Plaintext(self, p) for p in out]
+
     def pt_export(self, pt, level):
         out = np.zeros((level + 1, self.N), np.uint64)
         _check(lib().blb_pt_export(self.h, pt.h, out.ctypes.data))
@@ -312,6 +326,14 @@ class Context:
     # ciphertexts
     def encrypt(self, keys, pt, nonce):
         return self._new(Ciphertext, lib().blb_encrypt, keys.h, pt.h, _u64(nonce))
+
+    def encrypt_batch(self, keys, pts, nonces):
+        count = len(pts)
+        ps = (ctypes.c_void_p * count)(*[p.h for p in pts])
+        ns = np.ascontiguousarray(nonces, np.uint64)
+        out = (ctypes.c_void_p * count)()
+        _check(lib().blb_encrypt_batch(self.h, keys.h, ps, count, ns.ctypes.data, out))
+        return [Ciphertext(self, c) for c in out]
 
     def ct_export(self, ct, out=None):
         lv, npl, _ = ct.info()
@@ -333,6 +355,18 @@ class Context:
             slot_out = np.zeros(self.N // 2, np.float64)
         _check(lib().blb_decrypt(self.h, keys.h, ct.h, _ptr(coeff_out) if coeffs else None,
                                  _ptr(slot_out) if slots else None))
+        return coeff_out, slot_out
+
+    def decrypt_batch(self, keys, cts, coeff_out=None, slot_out=None, coeffs=True, slots=False):
+        """Ciphertexts of one level: coefficients (count, level+1, N), slots (count, N/2)."""
+        count, lv = len(cts), cts[0].level
+        if coeffs and coeff_out is None:
+            coeff_out = np.zeros((count, lv + 1, self.N), np.uint64)
+        if slots and slot_out is None:
+            slot_out = np.zeros((count, self.N // 2), np.float64)
+        cs = (ctypes.c_void_p * count)(*[c.h for c in cts])
+        _check(lib().blb_decrypt_batch(self.h, keys.h, cs, count, _ptr(coeff_out) if coeffs else None,
+                                       _ptr(slot_out) if slots else None))
         return coeff_out, slot_out
 
     # operations
@@ -423,6 +457,16 @@ class Context:
         h = ctypes.c_void_p()
         _check(lib().blb_he2mpc(self.h, keys.h, ct.h, _u64(nonce), ctypes.byref(h), _ptr(share_out)))
         return Ciphertext(self, h.value), share_out
+
+    def he2mpc_batch(self, keys, cts, nonces, share_out=None):
+        count = len(cts)
+        if share_out is None:
+            share_out = np.zeros((count, self.N), np.uint64)
+        cs = (ctypes.c_void_p * count)(*[c.h for c in cts])
+        ns = np.ascontiguousarray(nonces, np.uint64)
+        out = (ctypes.c_void_p * count)()
+        _check(lib().blb_he2mpc_batch(self.h, keys.h, cs, count, ns.ctypes.data, out, _ptr(share_out)))
+        return [Ciphertext(self, c) for c in out], share_out
 
     def profile(self, on=True):
         _check(lib().blb_profile_enable(self.h, int(on)))

@@ -13,9 +13,7 @@
 
 #include "common.cuh"
 
-namespace {
-constexpr int kT = 256;
-
+// library-internal helpers (declared in common.cuh)
 uint64_t* op_row(blb_ctx* c, size_t r) { return c->op_scratch() + r * c->N; }
 
 int copy_in(blb_ctx* c, void* dst, const void* src, size_t bytes)
@@ -50,6 +48,9 @@ int new_ct(blb_ctx* c, uint32_t level, uint32_t npolys, double scale, blb_ct** o
     *out = ct;
     return BLB_OK;
 }
+
+namespace {
+constexpr int kT = 256;
 
 bool same_scale(double a, double b) { return std::fabs(a - b) <= 1e-9 * std::max(std::fabs(a), std::fabs(b)); }
 
@@ -720,13 +721,21 @@ static int cp_run(blb_ctx* c, const blb_keys* K, const blb_cp_plan* P, blb_ct* c
             rc = ks_run(c, P->level, src.data(), (uint32_t)src.size(), prod.data(), grp.data(), (uint32_t)grp.size(),
                         adds.data(), 0);
     }
-    // rescale
-    for (uint32_t e = 0; !rc && e < S * P->nY; e++) {
+    // rescale every output in one pass (T[e][0] lie G ciphertexts apart), then
+    // hand each its own ciphertext
+    const uint32_t ny = S * P->nY;
+    const size_t yw = (size_t)2 * P->level * N;
+    uint64_t* Ys = rc ? nullptr : (uint64_t*)dev_alloc(c, ny * yw * 8);
+    if (!rc && !Ys) rc = blb_fail(BLB_ERR_OOM, "matmul_cp output stack");
+    if (!rc) rc = launch_rescale_strided(c, Ys, T, P->level, 2 * ny, 2, (size_t)P->G * ctw);
+    for (uint32_t e = 0; !rc && e < ny; e++) {
         blb_ct* y = nullptr;
         rc = new_ct(c, P->level - 1, 2, X[0]->scale, &y);
-        if (!rc) rc = launch_rescale(c, y->d, T + (size_t)e * P->G * ctw, P->level, 2);
+        if (!rc && cudaMemcpyAsync(y->d, Ys + e * yw, yw * 8, cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess)
+            rc = blb_fail(BLB_ERR_CUDA, "copy failed");
         Y[e] = y;
     }
+    dev_free(c, Ys, ny * yw * 8);
     dev_free(c, baby, baby_bytes);
     dev_free(c, T, T_bytes);
     if (rc) {

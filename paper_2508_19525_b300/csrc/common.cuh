@@ -115,6 +115,12 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k)
 enum { PURPOSE_SECRET = 1, PURPOSE_KEY_A = 2, PURPOSE_KEY_E = 3, PURPOSE_ENC_A = 4, PURPOSE_ENC_E = 5,
        PURPOSE_MASK = 6 };
 
+// one Philox draw with counter (coefficient i, sub-index j, object, purpose)
+__device__ __forceinline__ uint4 philox_draw(uint64_t seed, uint32_t i, uint32_t j, uint32_t obj, uint32_t purpose)
+{
+    return philox4x32_10(make_uint4(i, j, obj, purpose), make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
+}
+
 // ---------------------------------------------------------------------------
 // limb -> prime maps passed by value to kernels: row r of a polynomial stack uses
 // prime p[r % n].
@@ -293,9 +299,15 @@ int launch_mul_const_rows(blb_ctx* ctx, uint64_t* out, const uint64_t* a, uint32
 int launch_automorph_ntt(blb_ctx* ctx, uint64_t* out, const uint64_t* in, uint32_t rows, uint64_t g);
 int launch_signed_to_rows(blb_ctx* ctx, uint64_t* out, const int64_t* in, uint32_t rows, const LimbMap& map);
 int launch_rescale(blb_ctx* ctx, uint64_t* out, const uint64_t* in, uint32_t level, uint32_t npolys);
+int launch_rescale_strided(blb_ctx* ctx, uint64_t* out, const uint64_t* in, uint32_t level, uint32_t npolys,
+                           uint32_t ppc, size_t stride);
 int launch_rescale_stack(blb_ctx* ctx, uint64_t* out, const uint64_t* in, uint32_t level, uint32_t npolys);
 // new ciphertext object (retains the context)
 int new_ciphertext(blb_ctx* ctx, uint32_t level, uint32_t npolys, double scale, blb_ct** out);
+int new_ct(blb_ctx* c, uint32_t level, uint32_t npolys, double scale, blb_ct** out);
+uint64_t* op_row(blb_ctx* c, size_t r);                             // row r of the operation scratch
+int copy_in(blb_ctx* c, void* dst, const void* src, size_t bytes);  // host or device source
+int copy_out(blb_ctx* c, void* dst, const void* src, size_t bytes); // host (synchronises) or device target
 int launch_tensor(blb_ctx* ctx, uint64_t* out, const uint64_t* a, const uint64_t* b, uint32_t level);
 
 // sampling: counter (coefficient, j, obj, purpose), key = seed

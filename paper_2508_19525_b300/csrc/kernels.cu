@@ -76,7 +76,7 @@ __global__ void k_signed_to_rows(uint64_t* __restrict__ out, const int64_t* __re
 // --- Philox draws: counter (coefficient i, sub-index j, object, purpose) ---
 __device__ __forceinline__ uint4 draw(uint64_t seed, uint32_t i, uint32_t j, uint32_t obj, uint32_t purpose)
 {
-    return philox4x32_10(make_uint4(i, j, obj, purpose), make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
+    return philox_draw(seed, i, j, obj, purpose);
 }
 
 __global__ void k_sample_ternary(int64_t* out, uint32_t N, uint64_t seed, uint32_t obj, uint32_t purpose, uint32_t j)
@@ -124,15 +124,23 @@ __global__ void k_sample_uniform(uint64_t* out, uint32_t N, LimbMap map, const u
 struct RescaleConsts {
     uint64_t inv[BLB_MAXP], inv_sh[BLB_MAXP];
 };
+// input polynomial pp of a stack of ciphertexts with ppc polynomials each,
+// `stride` words apart
+__device__ __forceinline__ const uint64_t* stack_poly(const uint64_t* in, uint32_t pp, uint32_t ppc, size_t stride,
+                                                      uint32_t level, uint32_t N)
+{
+    return in + (size_t)(pp / ppc) * stride + (size_t)(pp % ppc) * (level + 1) * N;
+}
+
 __global__ void k_rescale_finish(uint64_t* __restrict__ out, const uint64_t* __restrict__ in,
                                  const uint64_t* __restrict__ T, const uint64_t* __restrict__ qs, uint32_t N,
-                                 uint32_t level, RescaleConsts rc)
+                                 uint32_t level, RescaleConsts rc, uint32_t ppc, size_t stride)
 {
     const uint32_t row = blockIdx.y, c = blockIdx.x * blockDim.x + threadIdx.x;  // row = poly * level + i
     if (c >= N) return;
     const uint32_t poly = row / level, i = row % level;
     const uint64_t q = qs[i];
-    uint64_t x = in[((size_t)poly * (level + 1) + i) * N + c];
+    uint64_t x = stack_poly(in, poly, ppc, stride, level, N)[(size_t)i * N + c];
     uint64_t t = T[(size_t)row * N + c];
     out[(size_t)row * N + c] = mul_shoup(sub_mod(x, t, q), rc.inv[i], rc.inv_sh[i], q);
 }
@@ -156,11 +164,12 @@ __global__ void k_lift_last(uint64_t* __restrict__ T, const uint64_t* __restrict
     T[(size_t)row * N + c] = r;
 }
 
-__global__ void k_copy_last(uint64_t* __restrict__ dst, const uint64_t* __restrict__ in, uint32_t N, uint32_t level)
+__global__ void k_copy_last(uint64_t* __restrict__ dst, const uint64_t* __restrict__ in, uint32_t N, uint32_t level,
+                            uint32_t ppc, size_t stride)
 {
     const uint32_t poly = blockIdx.y, c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= N) return;
-    dst[(size_t)poly * N + c] = in[((size_t)poly * (level + 1) + level) * N + c];
+    dst[(size_t)poly * N + c] = stack_poly(in, poly, ppc, stride, level, N)[(size_t)level * N + c];
 }
 
 __global__ void k_tensor(uint64_t* __restrict__ out, const uint64_t* __restrict__ a, const uint64_t* __restrict__ b,
@@ -291,6 +300,15 @@ int launch_sample_uniform(blb_ctx* ctx, uint64_t* out, uint32_t rows, const Limb
 // scratch when they fit, else in a temporary allocation.
 int launch_rescale_stack(blb_ctx* ctx, uint64_t* out, const uint64_t* in, uint32_t level, uint32_t npolys)
 {
+    return launch_rescale_strided(ctx, out, in, level, npolys, npolys, 0);
+}
+
+// npolys polynomials taken from ciphertexts of ppc polynomials that lie
+// `stride` words apart in `in` (0: back to back); out is one contiguous stack
+int launch_rescale_strided(blb_ctx* ctx, uint64_t* out, const uint64_t* in, uint32_t level, uint32_t npolys,
+                           uint32_t ppc, size_t stride)
+{
+    if (stride == 0) stride = (size_t)ppc * (level + 1) * ctx->N;
     if (level == 0) return blb_fail(BLB_ERR_LEVEL, "rescale at level 0");
     const uint32_t N = ctx->N;
     const size_t need = (size_t)npolys * (level + 1) * N;
@@ -305,7 +323,7 @@ int launch_rescale_stack(blb_ctx* ctx, uint64_t* out, const uint64_t* in, uint32
     uint64_t* T = last + (size_t)npolys * N;
     int rc = BLB_OK;
     do {
-        k_copy_last<<<grid_rows(N, npolys), kT, 0, ctx->stream>>>(last, in, N, level);
+        k_copy_last<<<grid_rows(N, npolys), kT, 0, ctx->stream>>>(last, in, N, level, ppc, stride);
         if (cudaGetLastError() != cudaSuccess) { rc = blb_fail(BLB_ERR_CUDA, "rescale launch failed"); break; }
         blb_count_launch();
         if ((rc = ntt_inverse(ctx, last, npolys, ctx->qmap(1, level)))) break;
@@ -319,7 +337,8 @@ int launch_rescale_stack(blb_ctx* ctx, uint64_t* out, const uint64_t* in, uint32
             rcst.inv[i] = ctx->ql_inv[level][i];
             rcst.inv_sh[i] = shoup_companion(rcst.inv[i], ctx->q[i]);
         }
-        k_rescale_finish<<<grid_rows(N, rows), kT, 0, ctx->stream>>>(out, in, T, ctx->d_q, N, level, rcst);
+        k_rescale_finish<<<grid_rows(N, rows), kT, 0, ctx->stream>>>(out, in, T, ctx->d_q, N, level, rcst, ppc,
+                                                                     stride);
         if (cudaGetLastError() != cudaSuccess) { rc = blb_fail(BLB_ERR_CUDA, "rescale launch failed"); break; }
         blb_count_launch();
     } while (0);
