@@ -64,10 +64,18 @@ class Clocks:
     def start(self):
         try:
             self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}",
-                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
                                       stdout=self.f, stderr=subprocess.DEVNULL)
         except OSError:
             self.p = None
+            return
+        # the timed region starts once the sampler has written its first line
+        t0 = time.time()
+        while time.time() - t0 < 10 and self.p.poll() is None:
+            if os.path.getsize(self.f.name) > 0:
+                break
+            time.sleep(0.02)
+        self.skip = sum(1 for _ in open(self.f.name))
 
     def stop(self):
         if self.p is None:
@@ -75,7 +83,8 @@ class Clocks:
         self.p.terminate()
         self.p.wait()
         self.f.flush()
-        rows = [l.split(",") for l in open(self.f.name).read().strip().splitlines() if l.strip()]
+        rows = [l.split(",") for l in open(self.f.name).read().strip().splitlines()[getattr(self, "skip", 0):]
+                if l.strip()]
         os.unlink(self.f.name)
         sm = [float(r[1]) for r in rows if len(r) >= 9 and r[1].strip().replace(".", "").isdigit()]
         mx = [float(r[2]) for r in rows if len(r) >= 9 and r[2].strip().replace(".", "").isdigit()]
@@ -343,6 +352,17 @@ def timed(w, steps, host, world):
     return ev0.elapsed_time(ev1) / 1e3, wall
 
 
+def traffic_ratio(path):
+    """The `traffic_ratio:` line of an ncu summary (DRAM bytes per algorithmic byte)."""
+    try:
+        for ln in open(path):
+            if ln.startswith("traffic_ratio:"):
+                return float(ln.split(":", 1)[1])
+    except OSError:
+        pass
+    return None
+
+
 def run_blb(args):
     world, rank, local = dist_env()
     import torch
@@ -373,12 +393,12 @@ def run_blb(args):
     batched = None
     if args.batch > 1:
         w.step_batched(args.batch)
-        bsec = timed_fn(w, lambda: w.step_batched(args.batch), max(1, args.steps // 2), world)
-        bsteps = max(1, args.steps // 2)
+        bsteps = max(1, min(10, args.steps // 2))
+        bsec = timed_fn(w, lambda: w.step_batched(args.batch), bsteps, world)
         bval, _ = aggregate(bsec, TOKENS_PER_STEP * args.batch * bsteps, world)
         batched = {"sequences_per_step": args.batch, "value": round(bval, 3), "unit": UNIT,
                    "ms_per_step": round(bsec * 1e3 / bsteps, 3), "speedup_vs_plain": round(bval / value, 3)}
-    attn = attention_cc(max(1, args.steps // 2)) if args.attention and world == 1 else None
+    attn = attention_cc(max(1, min(5, args.steps // 4))) if args.attention and world == 1 else None
     if rank != 0:
         return
     peaks = {}
@@ -399,10 +419,14 @@ def run_blb(args):
     # the dominant single-kernel site (the key-switch site is a pipeline of kernels)
     kernel_sites = [s for s in ("cp_mac", "ntt", "intt") if s in roof]
     dominant = max(kernel_sites, key=lambda s: roof[s]["ms_total"]) if kernel_sites else None
+    # DRAM bytes per launch site of the dominant kernel: the measured ratio of
+    # DRAM traffic to algorithmic bytes from the committed ncu summary of the
+    # same kernel on a smaller matrix, times this workload's algorithmic bytes
     traffic = None
-    tfile = os.path.join(ROOT, "profiles", "traffic.json")
-    if dominant and os.path.exists(tfile):
-        traffic = json.load(open(tfile)).get(dominant)
+    if dominant == "cp_mac":
+        ratio = traffic_ratio(os.path.join(ROOT, "profiles", "ncu_cp_mac_tc_128x768x256_N32768.md"))
+        if ratio:
+            traffic = int(ratio * roof[dominant]["algorithmic_bytes_per_call"])
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(dev_max * 1e3 / args.steps, 3), "higher_is_better": True,
@@ -559,7 +583,7 @@ def ncu_step():
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["blb", "reference"], default="blb")
     ap.add_argument("--no-cpu-baseline", action="store_true")
