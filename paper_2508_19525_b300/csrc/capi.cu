@@ -825,7 +825,15 @@ extern "C" int blb_ntt(blb_ctx* c, uint64_t* data, uint32_t rows, const uint32_t
         }
     }
     int rc = BLB_OK;
-    for (uint32_t r0 = 0; !rc && r0 < rows; r0 += BLB_MAXP) {
+    bool same = true;
+    for (uint32_t r = 1; r < rows; r++) same &= prime_idx[r] == prime_idx[0];
+    if (same && rows) {  // one launch for all rows of one prime
+        LimbMap m{};
+        m.p[0] = (uint8_t)prime_idx[0];
+        m.n = 1;
+        rc = inverse ? ntt_inverse(c, buf, rows, m) : ntt_forward(c, buf, rows, m);
+    }
+    for (uint32_t r0 = 0; !same && !rc && r0 < rows; r0 += BLB_MAXP) {
         uint32_t cnt = std::min<uint32_t>(BLB_MAXP, rows - r0);
         LimbMap m{};
         for (uint32_t r = 0; r < cnt; r++) m.p[r] = (uint8_t)prime_idx[r0 + r];

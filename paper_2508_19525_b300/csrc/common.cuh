@@ -154,7 +154,7 @@ struct blb_ctx {
     // device tables
     uint64_t* d_q = nullptr;          // [np]
     uint64_t* d_bar = nullptr;        // [np][2]: floor(2^128/q) lo, hi
-    uint64_t* d_tw = nullptr;         // [np][4][N]: psi_rev, shoup, psi_inv_rev, shoup
+    uint64_t* d_tw = nullptr;         // [np][2][N] pairs (w, shoup): psi^brv(k), then psi^-brv(k)
     uint64_t* d_ninv = nullptr;       // [np][2]: N^-1, shoup
     double2* d_zeta = nullptr;        // [N]: (cos, sin)(pi k / N)
     uint64_t* d_cdt = nullptr;        // [19]

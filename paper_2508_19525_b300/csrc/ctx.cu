@@ -381,19 +381,18 @@ extern "C" int blb_ctx_create(const blb_params* params, void* stream, blb_ctx** 
         uint64_t q = c->q[i];
         uint64_t psi = find_psi(q, N), psi_inv = host_invmod(psi, q);
         c->psi[i] = psi;
+        // [forward, inverse][k] pairs (psi^brv, Shoup companion): successive
+        // powers of psi (psi^-1) placed at bit-reversed positions k
         uint64_t* T = &tw[(size_t)i * 4 * N];
-        // successive powers, placed at bit-reversed positions
         uint64_t pw = 1, pwi = 1;
         for (uint32_t e = 0; e < N; e++) {
             uint32_t k = brv(e, c->logN);
-            T[k] = pw;
-            T[2 * N + k] = pwi;
+            T[2 * k] = pw;
+            T[2 * k + 1] = shoup_companion(pw, q);
+            T[2 * N + 2 * k] = pwi;
+            T[2 * N + 2 * k + 1] = shoup_companion(pwi, q);
             pw = host_mulmod(pw, psi, q);
             pwi = host_mulmod(pwi, psi_inv, q);
-        }
-        for (uint32_t k = 0; k < N; k++) {
-            T[N + k] = shoup_companion(T[k], q);
-            T[3 * N + k] = shoup_companion(T[2 * N + k], q);
         }
         u128_t R = (~(u128_t)0) / q;  // == floor(2^128 / q) for odd q
         bar[2 * i] = (uint64_t)R;

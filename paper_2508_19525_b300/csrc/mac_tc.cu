@@ -34,8 +34,9 @@
 // in one of two shared buffers; a streamer warp copies the tiles' plaintext
 // ranges into a ring of shared-memory stages with cp.async.bulk copies
 // completed on mbarriers, without pausing between tiles; the consumer warps
-// take the items in turn, hand each stage back right after its last mma, and
-// run the epilogue while the next copies land.  Every wait is
+// (8 for one sequence, 4 for batches, one ring stage each) take the items in
+// turn, hand each stage back right after its last mma, and run the epilogue
+// while the next copies land.  Every wait is
 // bounded: an expired wait sets a CTA abort word that ends the other waits,
 // and the status word the host reads in blb_ctx_sync.
 #include "common.cuh"
@@ -44,8 +45,13 @@
 
 namespace {
 
-constexpr int MAC_CONSUMERS = 4;  // consumer warps per CTA, plus a plaintext streamer and a B builder
-constexpr int MAC_THREADS = 32 * (MAC_CONSUMERS + 2);
+// Consumer warps per CTA (W, plus a plaintext streamer and a B builder): 8 for
+// one sequence, 4 for batches (measured on B300 at the BERT-base products); the
+// ring has one stage per consumer and a B buffer holds at most 16 KB, so two
+// CTAs fit on an SM.
+constexpr int mac_consumers(int S) { return S == 1 ? 8 : 4; }
+constexpr int mac_threads(int S) { return 32 * (mac_consumers(S) + 2); }
+constexpr uint32_t MAC_BBUF_BYTES = 16u << 10;
 constexpr int MAC_MAX_GROUP = 64;  // limbs per launch
 constexpr uint64_t MAC_WAIT_NS = 2000000000ull;  // bounded waits: 2 s
 
@@ -177,12 +183,13 @@ __device__ __forceinline__ uint32_t f32_int(float x)
 }
 
 template <int S, int NB>
-__global__ void __launch_bounds__(MAC_THREADS) k_cp_mac_tc(const __grid_constant__ MacArgs A)
+__global__ void __launch_bounds__(mac_threads(S)) k_cp_mac_tc(const __grid_constant__ MacArgs A)
 {
     constexpr int SP = 2 * S;                 // (sequence, polynomial) columns per byte plane of X
     constexpr int NT = (NB * SP + 7) / 8;     // n8 tiles
     constexpr int SLOTS = SP >= 8 ? SP / 4 : 2;
     constexpr int AG = plane_group<NB, NT>();
+    constexpr int MAC_CONSUMERS = mac_consumers(S), MAC_THREADS = mac_threads(S);
     extern __shared__ __align__(128) uint8_t smem[];
     const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t item_bytes = A.KT * NB * 256;
@@ -459,17 +466,15 @@ int launch_group(blb_ctx* c, MacArgs& a, uint32_t nlimbs)
     const uint32_t item_bytes = a.KT * NB * 256;
     a.jstride = a.KT * NT * 256 + 16;
     a.CT = 16;
-    while (a.CT > 1 && (size_t)a.CT * a.jstride > (32u << 10)) a.CT >>= 1;
+    while (a.CT > 1 && (size_t)a.CT * a.jstride > MAC_BBUF_BYTES) a.CT >>= 1;
     a.tiles_per_limb = c->N / a.CT;
     a.tiles = a.tiles_per_limb * nlimbs;
-    // ring depth a multiple of the consumer count: successive fills of a stage
-    // go to the same warp, so a parity wait never sees the phase before the one
-    // it wants
+    // one ring stage per consumer: the fills of a stage all go to the same
+    // warp, so a parity wait never sees the phase before the one it wants
+    constexpr int W = mac_consumers(S);
     const size_t bbuf = ((size_t)a.CT * a.jstride + 127) & ~(size_t)127;
-    a.R = 2 * MAC_CONSUMERS;
-    auto smem_of = [&](uint32_t R) { return 2 * bbuf + (size_t)R * item_bytes + 16 * R + 64; };
-    if (smem_of(a.R) > (200u << 10)) a.R = MAC_CONSUMERS;
-    const size_t smem = smem_of(a.R);
+    a.R = W;
+    const size_t smem = 2 * bbuf + (size_t)a.R * item_bytes + 16 * a.R + 64;
     if (smem > (227u << 10)) return blb_fail(BLB_ERR_ARG, "plaintext tile too large for shared memory");
     if (item_bytes >= (1u << 20)) return blb_fail(BLB_ERR_ARG, "too many plaintext terms per output");
     static bool attr = false;
@@ -478,12 +483,12 @@ int launch_group(blb_ctx* c, MacArgs& a, uint32_t nlimbs)
         BLB_CUDA(cudaFuncSetAttribute(k_cp_mac_tc<S, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 << 10));
         attr = true;
     }
-    BLB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cp_mac_tc<S, NB>, MAC_THREADS, smem));
+    BLB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cp_mac_tc<S, NB>, mac_threads(S), smem));
     int dev = 0, sms = 0;
     BLB_CUDA(cudaGetDevice(&dev));
     BLB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     const uint32_t grid = std::min<uint32_t>(a.tiles, (uint32_t)std::max(1, per_sm) * sms);
-    k_cp_mac_tc<S, NB><<<grid, MAC_THREADS, smem, c->stream>>>(a);
+    k_cp_mac_tc<S, NB><<<grid, mac_threads(S), smem, c->stream>>>(a);
     BLB_LAUNCHED();
     return BLB_OK;
 }

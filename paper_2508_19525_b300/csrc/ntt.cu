@@ -15,8 +15,16 @@
 // elements in registers and runs up to 4 stages on it (radix 16), so a pass
 // needs 2-3 shared-memory round trips instead of one per stage.  Shared memory
 // is padded by one word every 16 to keep strided group accesses conflict-free.
-// Butterflies reduce lazily (Harvey): forward values stay in [0, 4q), inverse
-// values in [0, 2q); the last pass returns them to [0, q).
+//
+// Each (transform size, pass) is its own template instance, so every index,
+// shift and loop bound of a pass is a compile-time constant; the twiddles are
+// stored as (w, floor(w 2^64 / q)) pairs and read with one 16-byte load.
+//
+// Reduction: for primes q >= 2^(63 - logN) the butterflies reduce lazily
+// (Harvey): forward values stay in [0, 4q), inverse values in [0, 2q).  For
+// smaller primes no butterfly needs a conditional subtraction: forward values
+// grow by at most 2q per stage, inverse sums at most double per stage, and
+// both stay below 2^64; the last pass reduces once.
 //
 // Rows: either rows 0..rows-1 of `data` with prime map.p[row % map.n], or an
 // explicit row list (entry = row index | prime index << 24) so that a batch can
@@ -27,7 +35,6 @@
 
 namespace {
 
-constexpr uint32_t kTile = 4096;  // words per CTA
 constexpr uint32_t kThreads = 256;
 constexpr uint32_t kMaxGridY = 65535;
 
@@ -52,66 +59,87 @@ __device__ __forceinline__ uint64_t mul_shoup_lazy(uint64_t x, uint64_t w, uint6
     return x * w - __umul64hi(x, wp) * q;
 }
 
-// forward: X, Y in [0, 4q) -> X + WY, X - WY in [0, 4q)
-__device__ __forceinline__ void bfly_fwd(uint64_t& X, uint64_t& Y, uint64_t w, uint64_t wp, uint64_t q, uint64_t q2)
+// forward, lazy: X, Y in [0, 4q) -> X + WY, X - WY in [0, 4q)
+__device__ __forceinline__ void bfly_fwd(uint64_t& X, uint64_t& Y, ulonglong2 w, uint64_t q, uint64_t q2)
 {
-    uint64_t x = X >= q2 ? X - q2 : X;
-    uint64_t t = mul_shoup_lazy(Y, w, wp, q);
+    const uint64_t x = X >= q2 ? X - q2 : X;
+    const uint64_t t = mul_shoup_lazy(Y, w.x, w.y, q);
     X = x + t;
-    Y = x - t + q2;
+    Y = x + q2 - t;
 }
 
-// inverse: X, Y in [0, 2q) -> X + Y, W (X - Y) in [0, 2q)
-__device__ __forceinline__ void bfly_inv(uint64_t& X, uint64_t& Y, uint64_t w, uint64_t wp, uint64_t q, uint64_t q2)
+// forward, small prime: X + t, X - t + 2q with t = W Y in [0, 2q), no reduction
+__device__ __forceinline__ void bfly_fwd_s(uint64_t& X, uint64_t& Y, ulonglong2 w, uint64_t q, uint64_t q2)
+{
+    const uint64_t t = mul_shoup_lazy(Y, w.x, w.y, q);
+    const uint64_t x = X;
+    X = x + t;
+    Y = x + q2 - t;
+}
+
+// inverse, lazy: X, Y in [0, 2q) -> X + Y, W (X - Y) in [0, 2q)
+__device__ __forceinline__ void bfly_inv(uint64_t& X, uint64_t& Y, ulonglong2 w, uint64_t q, uint64_t q2)
 {
     uint64_t s = X + Y;
     s = s >= q2 ? s - q2 : s;
-    uint64_t d = X - Y + q2;
+    const uint64_t d = X - Y + q2;
     X = s;
-    Y = mul_shoup_lazy(d, w, wp, q);
+    Y = mul_shoup_lazy(d, w.x, w.y, q);
 }
 
-struct Pass {
-    uint32_t logN;  // transform size
-    uint32_t l;     // log2 of the sub-transform length handled by this pass
-    uint32_t goff;  // global index bit of local bit 0 (logN - l for the column pass, 0 for rows)
-    uint32_t cols;  // 1: column pass (sub-transforms strided by N / L), 0: contiguous blocks
-    uint32_t lognsub;
-    uint32_t c0;    // first column (column pass) or first block (row pass) of this tile
+// inverse, small prime, stage inputs below C = 2^(lt+1) q: X + Y, W (X - Y + C)
+__device__ __forceinline__ void bfly_inv_s(uint64_t& X, uint64_t& Y, ulonglong2 w, uint64_t q, uint64_t C)
+{
+    const uint64_t x = X, y = Y;
+    X = x + y;
+    Y = mul_shoup_lazy(x + C - y, w.x, w.y, q);
+}
+
+__device__ __forceinline__ bool small_prime(uint64_t q, uint32_t logN) { return q < (1ull << (63 - logN)); }
+
+// Geometry of one pass: transform size 2^LOGN, sub-transform length 2^LP,
+// column (COLS) or row pass.
+template <int LOGN, int LP, bool COLS>
+struct Geo {
+    static constexpr uint32_t N = 1u << LOGN;
+    static constexpr int LOGTILE = LOGN < 12 ? LOGN : 12;
+    static constexpr uint32_t TILE = 1u << LOGTILE;
+    static constexpr int LOGNSUB = LOGTILE - LP;  // sub-transforms per tile
+    static constexpr uint32_t NSUB = 1u << LOGNSUB;
+    static constexpr int GOFF = COLS ? LOGN - LP : 0;  // global bit of local bit 0
+    static constexpr int LOGN2 = LOGN - LP;
 };
 
 // One round: R stages on groups of 2^R elements whose local indices differ in
-// bits [p_lo, p_lo + R).
-template <int R, bool INV>
-__device__ __forceinline__ void round(uint64_t* sm, const Pass& P, uint32_t tile, uint32_t p_lo,
-                                      const uint64_t* __restrict__ W, const uint64_t* __restrict__ Wp, uint64_t q,
+// bits [PLO, PLO + R).
+template <int LOGN, int LP, bool COLS, bool INV, bool SMALL, int PLO, int R>
+__device__ __forceinline__ void round(uint64_t* sm, uint32_t c0, const ulonglong2* __restrict__ W, uint64_t q,
                                       uint64_t q2)
 {
+    using G_ = Geo<LOGN, LP, COLS>;
     constexpr uint32_t K = 1u << R;
-    const uint32_t L = 1u << P.l, nsub = 1u << P.lognsub;
-    const uint32_t N = 1u << P.logN;
-    const uint32_t groups = tile >> R;
-    for (uint32_t G = threadIdx.x; G < groups; G += blockDim.x) {
+    constexpr uint32_t GROUPS = G_::TILE >> R;
+    constexpr int JSHIFT = G_::GOFF + PLO;
+    constexpr uint32_t e_stride = COLS ? (G_::NSUB << PLO) : (1u << PLO);
+#pragma unroll
+    for (uint32_t G = threadIdx.x; G < GROUPS; G += kThreads) {
         uint32_t sub, g;
-        if (P.cols) {
-            sub = G & (nsub - 1);
-            g = G >> P.lognsub;
+        if (COLS) {
+            sub = G & (G_::NSUB - 1);
+            g = G >> G_::LOGNSUB;
         } else {
-            g = G & ((L >> R) - 1);
-            sub = G >> (P.l - R);
+            g = G & ((1u << (LP - R)) - 1);
+            sub = G >> (LP - R);
         }
-        const uint32_t base_r = ((g >> p_lo) << (p_lo + R)) | (g & ((1u << p_lo) - 1));
-        uint32_t e_base, e_stride, j_base;
-        if (P.cols) {
-            e_base = (base_r << P.lognsub) + sub;
-            e_stride = nsub << p_lo;
-            j_base = P.c0 + sub + (base_r << P.goff);
+        const uint32_t base_r = ((g >> PLO) << (PLO + R)) | (g & ((1u << PLO) - 1));
+        uint32_t e_base, j_base;
+        if (COLS) {
+            e_base = (base_r << G_::LOGNSUB) + sub;
+            j_base = c0 + sub + (base_r << G_::GOFF);
         } else {
-            e_base = (sub << P.l) + base_r;
-            e_stride = 1u << p_lo;
-            j_base = ((P.c0 + sub) << P.l) + base_r;
+            e_base = (sub << LP) + base_r;
+            j_base = ((c0 + sub) << LP) + base_r;
         }
-        const uint32_t j_shift = P.goff + p_lo;
         uint64_t x[K];
 #pragma unroll
         for (uint32_t k = 0; k < K; k++) x[k] = sm[padi(e_base + k * e_stride)];
@@ -121,30 +149,32 @@ __device__ __forceinline__ void round(uint64_t* sm, const Pass& P, uint32_t tile
         if (!INV) {
 #pragma unroll
             for (int u = R - 1; u >= 0; u--) {
-                const uint32_t s = P.logN - 1 - (j_shift + u);
-                const uint32_t wbase = (1u << s) + (j_base >> (j_shift + u + 1));
+                const uint32_t s = LOGN - 1 - (JSHIFT + u);
+                const uint32_t wbase = (1u << s) + (j_base >> (JSHIFT + u + 1));
 #pragma unroll
                 for (uint32_t h = 0; h < (K >> (u + 1)); h++) {
-                    const uint64_t w = W[wbase + h], wp = Wp[wbase + h];
+                    const ulonglong2 w = W[wbase + h];
 #pragma unroll
                     for (uint32_t lo = 0; lo < (1u << u); lo++) {
                         const uint32_t k = (h << (u + 1)) | lo;
-                        bfly_fwd(x[k], x[k | (1u << u)], w, wp, q, q2);
+                        if (SMALL) bfly_fwd_s(x[k], x[k | (1u << u)], w, q, q2);
+                        else bfly_fwd(x[k], x[k | (1u << u)], w, q, q2);
                     }
                 }
             }
         } else {
 #pragma unroll
             for (int u = 0; u < R; u++) {
-                const uint32_t lt = j_shift + u;
-                const uint32_t wbase = (N + j_base) >> (lt + 1);
+                const uint32_t wbase = (G_::N + j_base) >> (JSHIFT + u + 1);
+                const uint64_t C = q << (JSHIFT + u + 1);  // inputs of stage lt lie below 2^(lt+1) q
 #pragma unroll
                 for (uint32_t h = 0; h < (K >> (u + 1)); h++) {
-                    const uint64_t w = W[wbase + h], wp = Wp[wbase + h];
+                    const ulonglong2 w = W[wbase + h];
 #pragma unroll
                     for (uint32_t lo = 0; lo < (1u << u); lo++) {
                         const uint32_t k = (h << (u + 1)) | lo;
-                        bfly_inv(x[k], x[k | (1u << u)], w, wp, q, q2);
+                        if (SMALL) bfly_inv_s(x[k], x[k | (1u << u)], w, q, C);
+                        else bfly_inv(x[k], x[k | (1u << u)], w, q, q2);
                     }
                 }
             }
@@ -154,130 +184,129 @@ __device__ __forceinline__ void round(uint64_t* sm, const Pass& P, uint32_t tile
     }
 }
 
-template <bool INV>
-__device__ __forceinline__ void round_r(uint32_t R, uint64_t* sm, const Pass& P, uint32_t tile, uint32_t p_lo,
-                                        const uint64_t* W, const uint64_t* Wp, uint64_t q, uint64_t q2)
+// forward rounds: local bits from the top down
+template <int LOGN, int LP, bool COLS, bool SMALL, int PHI>
+__device__ __forceinline__ void fwd_rounds(uint64_t* sm, uint32_t c0, const ulonglong2* W, uint64_t q, uint64_t q2)
 {
-    switch (R) {
-        case 4: round<4, INV>(sm, P, tile, p_lo, W, Wp, q, q2); break;
-        case 3: round<3, INV>(sm, P, tile, p_lo, W, Wp, q, q2); break;
-        case 2: round<2, INV>(sm, P, tile, p_lo, W, Wp, q, q2); break;
-        default: round<1, INV>(sm, P, tile, p_lo, W, Wp, q, q2); break;
+    if constexpr (PHI > 0) {
+        constexpr int R = PHI >= 4 ? 4 : PHI;
+        round<LOGN, LP, COLS, false, SMALL, PHI - R, R>(sm, c0, W, q, q2);
+        __syncthreads();
+        fwd_rounds<LOGN, LP, COLS, SMALL, PHI - R>(sm, c0, W, q, q2);
     }
 }
 
-// One pass over one tile of one row.  last: bring results to [0, q) (and, for
-// the inverse, multiply by N^-1).
-template <bool INV>
-__global__ void __launch_bounds__(kThreads, 3) k_ntt_pass(uint64_t* __restrict__ data, LimbMap map,
-                                                       const uint32_t* __restrict__ rowlist, uint32_t y0,
-                                                       const uint64_t* __restrict__ qs,
-                                                       const uint64_t* __restrict__ tw,
-                                                       const uint64_t* __restrict__ ninv, uint32_t logN, uint32_t l,
-                                                       uint32_t cols, int last)
+// inverse rounds: local bits from the bottom up
+template <int LOGN, int LP, bool COLS, bool SMALL, int PLO>
+__device__ __forceinline__ void inv_rounds(uint64_t* sm, uint32_t c0, const ulonglong2* W, uint64_t q, uint64_t q2)
 {
-    __shared__ uint64_t sm[kTile + kTile / 16];
+    if constexpr (PLO < LP) {
+        constexpr int R = LP - PLO >= 4 ? 4 : LP - PLO;
+        round<LOGN, LP, COLS, true, SMALL, PLO, R>(sm, c0, W, q, q2);
+        __syncthreads();
+        inv_rounds<LOGN, LP, COLS, SMALL, PLO + R>(sm, c0, W, q, q2);
+    }
+}
+
+// One pass over one tile of one row.  The last pass brings results to [0, q)
+// (and, for the inverse, multiplies by N^-1).
+template <bool INV, int LOGN, int LP, bool COLS>
+__global__ void __launch_bounds__(kThreads, 3) k_ntt(uint64_t* __restrict__ data, LimbMap map,
+                                                    const uint32_t* __restrict__ rowlist, uint32_t y0,
+                                                    const uint64_t* __restrict__ qs,
+                                                    const ulonglong2* __restrict__ tw,
+                                                    const uint64_t* __restrict__ ninv,
+                                                    const uint64_t* __restrict__ bar)
+{
+    using G_ = Geo<LOGN, LP, COLS>;
+    constexpr bool LAST = (LP == LOGN) || (INV ? COLS : !COLS);
+    __shared__ uint64_t sm[G_::TILE + G_::TILE / 16];
     uint32_t row, pi;
     row_of(rowlist, map, y0 + blockIdx.y, row, pi);
-    const uint32_t N = 1u << logN;
-    const uint32_t tile = N < kTile ? N : kTile;
-    Pass P;
-    P.logN = logN;
-    P.l = l;
-    P.goff = cols ? logN - l : 0;
-    P.cols = cols;
-    P.lognsub = __ffs(tile >> l) - 1;  // tile / L sub-transforms per tile
-    P.c0 = blockIdx.x << P.lognsub;
+    const uint32_t c0 = blockIdx.x << G_::LOGNSUB;
     const uint64_t q = qs[pi], q2 = 2 * q;
-    const uint64_t* W = tw + (size_t)pi * 4 * N + (INV ? 2 * N : 0);
-    const uint64_t* Wp = W + N;
-    uint64_t* a = data + (size_t)row * N;
+    const ulonglong2* W = tw + ((size_t)pi * 2 + (INV ? 1 : 0)) * G_::N;
+    uint64_t* a = data + (size_t)row * G_::N;
     // load the tile: element e = r * nsub + sub (columns) or sub * L + r (rows)
-    if (cols) {
-        const uint32_t logN2 = logN - l, nsub = 1u << P.lognsub;
-        for (uint32_t e = threadIdx.x; e < tile; e += blockDim.x)
-            sm[padi(e)] = a[((size_t)(e >> P.lognsub) << logN2) + P.c0 + (e & (nsub - 1))];
-    } else {
-        const uint64_t* src = a + ((size_t)P.c0 << l);
-        for (uint32_t e = threadIdx.x; e < tile; e += blockDim.x) sm[padi(e)] = src[e];
+#pragma unroll
+    for (uint32_t e = threadIdx.x; e < G_::TILE; e += kThreads) {
+        if (COLS) sm[padi(e)] = a[((size_t)(e >> G_::LOGNSUB) << G_::LOGN2) + c0 + (e & (G_::NSUB - 1))];
+        else sm[padi(e)] = a[((size_t)c0 << LP) + e];
     }
     __syncthreads();
+    const bool small = small_prime(q, LOGN);
     if (!INV) {
-        for (int p_hi = (int)l; p_hi > 0;) {
-            const uint32_t R = p_hi >= 4 ? 4 : (uint32_t)p_hi;
-            round_r<false>(R, sm, P, tile, (uint32_t)p_hi - R, W, Wp, q, q2);
-            p_hi -= (int)R;
-            __syncthreads();
-        }
+        if (small) fwd_rounds<LOGN, LP, COLS, true, LP>(sm, c0, W, q, q2);
+        else fwd_rounds<LOGN, LP, COLS, false, LP>(sm, c0, W, q, q2);
     } else {
-        for (uint32_t p_lo = 0; p_lo < l;) {
-            const uint32_t R = l - p_lo >= 4 ? 4 : l - p_lo;
-            round_r<true>(R, sm, P, tile, p_lo, W, Wp, q, q2);
-            p_lo += R;
-            __syncthreads();
-        }
+        if (small) inv_rounds<LOGN, LP, COLS, true, 0>(sm, c0, W, q, q2);
+        else inv_rounds<LOGN, LP, COLS, false, 0>(sm, c0, W, q, q2);
     }
-    uint64_t ni = 0, nis = 0;
-    if (INV && last) {
+    uint64_t ni = 0, nis = 0, r1 = 0;
+    if (INV && LAST) {
         ni = ninv[2 * pi];
         nis = ninv[2 * pi + 1];
     }
+    if (!INV && LAST) r1 = bar[2 * pi + 1];  // floor(2^64 / q)
     auto finish = [&](uint64_t v) -> uint64_t {
-        if (!last) return v;
+        if (!LAST) return v;
         if (INV) v = mul_shoup_lazy(v, ni, nis, q);
+        else if (small) v = v - __umul64hi(v, r1) * q;  // any 64-bit v -> [0, 2q)
         else v = v >= q2 ? v - q2 : v;
         return v >= q ? v - q : v;
     };
-    if (cols) {
-        const uint32_t logN2 = logN - l, nsub = 1u << P.lognsub;
-        for (uint32_t e = threadIdx.x; e < tile; e += blockDim.x)
-            a[((size_t)(e >> P.lognsub) << logN2) + P.c0 + (e & (nsub - 1))] = finish(sm[padi(e)]);
-    } else {
-        uint64_t* dst = a + ((size_t)P.c0 << l);
-        for (uint32_t e = threadIdx.x; e < tile; e += blockDim.x) dst[e] = finish(sm[padi(e)]);
+#pragma unroll
+    for (uint32_t e = threadIdx.x; e < G_::TILE; e += kThreads) {
+        if (COLS) a[((size_t)(e >> G_::LOGNSUB) << G_::LOGN2) + c0 + (e & (G_::NSUB - 1))] = finish(sm[padi(e)]);
+        else a[((size_t)c0 << LP) + e] = finish(sm[padi(e)]);
     }
 }
 
-struct Split {
-    uint32_t l1, l2;  // column pass length (0: single pass), row pass length
-};
-
-Split split(uint32_t logN)
+template <int LOGN>
+int run_n(blb_ctx* ctx, uint64_t* data, uint32_t rows, const LimbMap& map, const uint32_t* rowlist, bool inverse)
 {
-    if (logN <= 12) return {0, logN};
-    return {logN / 2, logN - logN / 2};
-}
-
-int run(blb_ctx* ctx, uint64_t* data, uint32_t rows, const LimbMap& map, const uint32_t* rowlist, bool inverse)
-{
-    const uint32_t logN = ctx->logN, N = 1u << logN;
-    const uint32_t tile = N < kTile ? N : kTile;
-    const Split sp = split(logN);
-    const uint32_t gx = N / tile;
+    constexpr uint32_t N = 1u << LOGN;
+    constexpr uint32_t TILE = N < 4096 ? N : 4096;
+    constexpr int L1 = LOGN <= 12 ? 0 : LOGN / 2, L2 = LOGN - L1;
+    const ulonglong2* tw = reinterpret_cast<const ulonglong2*>(ctx->d_tw);
     for (uint32_t y0 = 0; y0 < rows; y0 += kMaxGridY) {
-        const uint32_t ny = std::min(kMaxGridY, rows - y0);
-        const dim3 grid(gx, ny);
+        const dim3 grid(N / TILE, std::min(kMaxGridY, rows - y0));
         if (!inverse) {
-            if (sp.l1) {
-                k_ntt_pass<false><<<grid, kThreads, 0, ctx->stream>>>(data, map, rowlist, y0, ctx->d_q, ctx->d_tw,
-                                                                     ctx->d_ninv, logN, sp.l1, 1, 0);
+            if constexpr (L1 > 0) {
+                k_ntt<false, LOGN, L1, true><<<grid, kThreads, 0, ctx->stream>>>(data, map, rowlist, y0, ctx->d_q, tw,
+                                                                                ctx->d_ninv, ctx->d_bar);
                 BLB_LAUNCHED();
             }
-            k_ntt_pass<false><<<grid, kThreads, 0, ctx->stream>>>(data, map, rowlist, y0, ctx->d_q, ctx->d_tw,
-                                                                 ctx->d_ninv, logN, sp.l2, 0, 1);
+            k_ntt<false, LOGN, L2, false><<<grid, kThreads, 0, ctx->stream>>>(data, map, rowlist, y0, ctx->d_q, tw,
+                                                                             ctx->d_ninv, ctx->d_bar);
             BLB_LAUNCHED();
         } else {
-            k_ntt_pass<true><<<grid, kThreads, 0, ctx->stream>>>(data, map, rowlist, y0, ctx->d_q, ctx->d_tw,
-                                                                ctx->d_ninv, logN, sp.l2, 0, sp.l1 == 0);
+            k_ntt<true, LOGN, L2, false><<<grid, kThreads, 0, ctx->stream>>>(data, map, rowlist, y0, ctx->d_q, tw,
+                                                                            ctx->d_ninv, ctx->d_bar);
             BLB_LAUNCHED();
-            if (sp.l1) {
-                k_ntt_pass<true><<<grid, kThreads, 0, ctx->stream>>>(data, map, rowlist, y0, ctx->d_q, ctx->d_tw,
-                                                                    ctx->d_ninv, logN, sp.l1, 1, 1);
+            if constexpr (L1 > 0) {
+                k_ntt<true, LOGN, L1, true><<<grid, kThreads, 0, ctx->stream>>>(data, map, rowlist, y0, ctx->d_q, tw,
+                                                                               ctx->d_ninv, ctx->d_bar);
                 BLB_LAUNCHED();
             }
         }
     }
     return BLB_OK;
+}
+
+int run(blb_ctx* ctx, uint64_t* data, uint32_t rows, const LimbMap& map, const uint32_t* rowlist, bool inverse)
+{
+    switch (ctx->logN) {
+    case 10: return run_n<10>(ctx, data, rows, map, rowlist, inverse);
+    case 11: return run_n<11>(ctx, data, rows, map, rowlist, inverse);
+    case 12: return run_n<12>(ctx, data, rows, map, rowlist, inverse);
+    case 13: return run_n<13>(ctx, data, rows, map, rowlist, inverse);
+    case 14: return run_n<14>(ctx, data, rows, map, rowlist, inverse);
+    case 15: return run_n<15>(ctx, data, rows, map, rowlist, inverse);
+    case 16: return run_n<16>(ctx, data, rows, map, rowlist, inverse);
+    case 17: return run_n<17>(ctx, data, rows, map, rowlist, inverse);
+    default: return blb_fail(BLB_ERR_ARG, "no NTT for this ring size");
+    }
 }
 
 }  // namespace
