@@ -19,6 +19,8 @@
  * below states the one it implements.
  */
 #include "oracle.h"
+
+#define ORC_MAX_ROT 512  /* rotations per hoisted call in matmul_cc */
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
@@ -1032,6 +1034,10 @@ int orc_matmul_cp(const orc_params* p, const orc_galois_set* gk, const uint64_t*
  *      W_t = Rescale( Relin( sum_c Rot^{-g b1s2}(A_c) (x) V_c ) )
  *      -- Rot^{g b1s2}(W_t) would hold diagonal (t + kappa) mod L at block kappa;
  *   3. C_j = Rescale( sum_t m3(t, j) Rot^{g b1s2 - (t mod Kc) Hg L}(W_t) ).
+ * The rotations of one ciphertext in steps 1 and 2 (of B_c, B'_c and A_c) are
+ * hoisted (orc_rotate_hoisted) and the giant-step sum of step 1 takes one
+ * ModDown (orc_rotate_sum); step 3 and the relinearizations switch one
+ * ciphertext each.
  * Masks (0/1 slot vectors, encoded at scale q_level of the level they are
  * applied at): m1lo(g1,b0) = Rot^{-g1 b1s1}([kappa(slot) = g1 b1s1 + b0 and
  * i < L - kappa]), m1hi likewise with i >= L - kappa; m2lo(g,b) =
@@ -1133,66 +1139,94 @@ int orc_matmul_cc(const orc_params* p, const orc_galois_set* gk, const uint64_t*
         orc_rotate(p, (src), (lv), (int32_t)(r), key_, (dst));                \
     } while (0)
 
-    /* step 1 */
+    /* step 1: baby steps of B_c hoisted (one ModUp), giant steps summed with one ModDown */
     {
         uint64_t* lo = malloc(sizeof(uint64_t) * w0 * b1s1);
         uint64_t* hi = malloc(sizeof(uint64_t) * w0 * b1s1);
+        uint64_t* rot = malloc(sizeof(uint64_t) * w0 * 2 * b1s1);
         uint64_t* acc = malloc(sizeof(uint64_t) * w0);
-        uint64_t* inner = malloc(sizeof(uint64_t) * w0);
+        uint64_t* inner = malloc(sizeof(uint64_t) * w0 * G1);
+        int32_t rs[2 * ORC_MAX_ROT];
+        const uint64_t* ks[2 * ORC_MAX_ROT];
+        if (2 * b1s1 > 2 * ORC_MAX_ROT || G1 > 2 * ORC_MAX_ROT) rc = -1;
         for (uint32_t c = 0; c < n_c && !rc; c++) {
             const uint64_t* Bc = B + (size_t)c * w0;
-            for (uint32_t b0 = 0; b0 < b1s1; b0++) {
-                if (b0 == 0) memcpy(lo, Bc, sizeof(uint64_t) * w0);
-                else ROT(lo + (size_t)b0 * w0, Bc, l0, b0);
-                if (b0 > 0 || G1 > 1) ROT(hi + (size_t)b0 * w0, Bc, l0, (int32_t)b0 - (int32_t)L);
+            /* rotations b0 (b0 >= 1) and b0 - L (b0 >= 1, or all b0 when G1 > 1) */
+            uint32_t nr = 0;
+            for (uint32_t b0 = 1; b0 < b1s1; b0++) rs[nr++] = (int32_t)b0;
+            for (uint32_t b0 = (G1 > 1 ? 0 : 1); b0 < b1s1; b0++) rs[nr++] = (int32_t)b0 - (int32_t)L;
+            for (uint32_t x = 0; x < nr && !rc; x++)
+                if (!(ks[x] = find_galois(p, gk, rs[x]))) rc = -2;
+            if (rc) break;
+            orc_rotate_hoisted(p, Bc, l0, nr, rs, ks, rot);
+            memcpy(lo, Bc, sizeof(uint64_t) * w0);
+            for (uint32_t x = 0; x < nr; x++) {
+                const int32_t r = rs[x];
+                uint64_t* dst = r > 0 ? lo + (size_t)r * w0 : hi + (size_t)(r + (int32_t)L) * w0;
+                memcpy(dst, rot + (size_t)x * w0, sizeof(uint64_t) * w0);
             }
-            memset(acc, 0, sizeof(uint64_t) * w0);
             for (uint32_t g1 = 0; g1 < G1 && !rc; g1++) {
-                memset(inner, 0, sizeof(uint64_t) * w0);
+                uint64_t* in = inner + (size_t)g1 * w0;
+                memset(in, 0, sizeof(uint64_t) * w0);
                 for (uint32_t b0 = 0; b0 < b1s1 && !rc; b0++) {
                     int64_t args[4] = {L, Hg, (int64_t)(g1 * b1s1 + b0), 0};
                     if (build_mask(z, s, (int64_t)g1 * b1s1, pred_m1, args))
-                        rc = mac_mask(p, inner, lo + (size_t)b0 * w0, l0, z, pt, prod);
+                        rc = mac_mask(p, in, lo + (size_t)b0 * w0, l0, z, pt, prod);
                     args[3] = 1;
                     if (!rc && build_mask(z, s, (int64_t)g1 * b1s1, pred_m1, args))
-                        rc = mac_mask(p, inner, hi + (size_t)b0 * w0, l0, z, pt, prod);
-                }
-                if (rc) break;
-                if (g1 == 0) ct_add_inplace(p, acc, inner, l0, 2);
-                else {
-                    ROT(tmp, inner, l0, g1 * b1s1);
-                    ct_add_inplace(p, acc, tmp, l0, 2);
+                        rc = mac_mask(p, in, hi + (size_t)b0 * w0, l0, z, pt, prod);
                 }
             }
-            if (!rc) orc_rescale(p, acc, l0, 2, Bp + (size_t)c * w1);
+            for (uint32_t g1 = 1; g1 < G1 && !rc; g1++) {
+                rs[g1 - 1] = (int32_t)(g1 * b1s1);
+                if (!(ks[g1 - 1] = find_galois(p, gk, rs[g1 - 1]))) rc = -2;
+            }
+            if (rc) break;
+            orc_rotate_sum(p, inner, inner + w0, l0, G1 - 1, rs, ks, acc);
+            orc_rescale(p, acc, l0, 2, Bp + (size_t)c * w1);
         }
-        free(lo); free(hi); free(acc); free(inner);
+        free(lo); free(hi); free(rot); free(acc); free(inner);
     }
     if (rc) goto done;
 
-    /* step 2 */
+    /* step 2: baby steps of B'_c and giant steps of A_c hoisted */
     {
         const size_t w2_3 = (size_t)3 * (l2 + 1) * N;
         uint64_t* U = calloc((size_t)L * w2_3, sizeof(uint64_t));
         uint64_t* blo = malloc(sizeof(uint64_t) * w1 * b1s2);
         uint64_t* bhi = malloc(sizeof(uint64_t) * w1 * b1s2);
+        uint64_t* rot = malloc(sizeof(uint64_t) * (w1 > w2 ? w1 : w2) * 2 * (b1s2 > G2 ? b1s2 : G2));
         uint64_t* Ag = malloc(sizeof(uint64_t) * w2 * G2);
         uint64_t* A2 = malloc(sizeof(uint64_t) * w2);
         uint64_t* vacc = malloc(sizeof(uint64_t) * w1);
         uint64_t* V = malloc(sizeof(uint64_t) * w2);
         uint64_t* T3 = malloc(sizeof(uint64_t) * w2_3);
+        int32_t rs[2 * ORC_MAX_ROT];
+        const uint64_t* ks[2 * ORC_MAX_ROT];
+        if (2 * b1s2 > 2 * ORC_MAX_ROT || G2 > 2 * ORC_MAX_ROT) rc = -1;
         for (uint32_t c = 0; c < n_c && !rc; c++) {
             const uint64_t* Bc = Bp + (size_t)c * w1;
-            for (uint32_t b = 0; b < b1s2; b++) {
-                if (b == 0) memcpy(blo, Bc, sizeof(uint64_t) * w1);
-                else ROT(blo + (size_t)b * w1, Bc, l1, b);
-                if (b > 0 || G2 > 1) ROT(bhi + (size_t)b * w1, Bc, l1, (int32_t)b - (int32_t)L);
+            uint32_t nr = 0;
+            for (uint32_t b = 1; b < b1s2; b++) rs[nr++] = (int32_t)b;
+            for (uint32_t b = (G2 > 1 ? 0 : 1); b < b1s2; b++) rs[nr++] = (int32_t)b - (int32_t)L;
+            for (uint32_t x = 0; x < nr && !rc; x++)
+                if (!(ks[x] = find_galois(p, gk, rs[x]))) rc = -2;
+            if (rc) break;
+            orc_rotate_hoisted(p, Bc, l1, nr, rs, ks, rot);
+            memcpy(blo, Bc, sizeof(uint64_t) * w1);
+            for (uint32_t x = 0; x < nr; x++) {
+                const int32_t r = rs[x];
+                uint64_t* dst = r > 0 ? blo + (size_t)r * w1 : bhi + (size_t)(r + (int32_t)L) * w1;
+                memcpy(dst, rot + (size_t)x * w1, sizeof(uint64_t) * w1);
             }
             drop_limbs(p, A + (size_t)c * w0, l0, l2, 2, A2);
-            for (uint32_t g = 0; g < G2; g++) {
-                if (g == 0) memcpy(Ag, A2, sizeof(uint64_t) * w2);
-                else ROT(Ag + (size_t)g * w2, A2, l2, -(int32_t)(g * b1s2));
+            memcpy(Ag, A2, sizeof(uint64_t) * w2);
+            for (uint32_t g = 1; g < G2 && !rc; g++) {
+                rs[g - 1] = -(int32_t)(g * b1s2);
+                if (!(ks[g - 1] = find_galois(p, gk, rs[g - 1]))) rc = -2;
             }
+            if (rc) break;
+            orc_rotate_hoisted(p, A2, l2, G2 - 1, rs, ks, Ag + w2);
             for (uint32_t g = 0; g < G2 && !rc; g++) {
                 for (uint32_t b = 0; b < b1s2 && !rc; b++) {
                     const uint32_t t = g * b1s2 + b;
@@ -1224,7 +1258,7 @@ int orc_matmul_cc(const orc_params* p, const orc_galois_set* gk, const uint64_t*
             orc_rescale(p, R2, l2, 2, W + (size_t)t * w3);
             free(R2);
         }
-        free(U); free(blo); free(bhi); free(Ag); free(A2); free(vacc); free(V); free(T3);
+        free(U); free(blo); free(bhi); free(rot); free(Ag); free(A2); free(vacc); free(V); free(T3);
     }
     if (rc) goto done;
 

@@ -381,6 +381,78 @@ static const uint64_t* key_for(const blb_keys* K, uint32_t N, int32_t rot, int* 
     return k ? k->d : nullptr;
 }
 
+// Hoisted rotations: every source ciphertext srcs[i] (2 polynomials at `level`)
+// rotated by every amount rots[j] into out(i, j); one ModUp per source.
+template <typename Out>
+static int rotate_hoisted(blb_ctx* c, const blb_keys* K, uint32_t level, const std::vector<const uint64_t*>& srcs,
+                          const std::vector<int32_t>& rots, Out out)
+{
+    if (srcs.empty() || rots.empty()) return BLB_OK;
+    const size_t pw = (size_t)(level + 1) * c->N;
+    int rc = BLB_OK;
+    std::vector<const uint64_t*> keys(rots.size());
+    std::vector<uint64_t> gal(rots.size());
+    for (size_t j = 0; j < rots.size() && !rc; j++) {
+        keys[j] = key_for(K, c->N, rots[j], &rc);
+        gal[j] = galois_element(c->N, rots[j]);
+    }
+    if (rc) return rc;
+    std::vector<KsSource> src;
+    std::vector<KsProduct> prod;
+    std::vector<KsGroup> grp;
+    std::vector<KsAdd> adds;
+    for (uint32_t i = 0; i < srcs.size(); i++) {
+        src.push_back(KsSource{srcs[i] + pw, 1});
+        for (uint32_t j = 0; j < rots.size(); j++) {
+            uint64_t* o = out(i, j);
+            grp.push_back(KsGroup{o, o + pw, (uint32_t)prod.size(), (uint32_t)prod.size() + 1, (uint32_t)adds.size(),
+                                  (uint32_t)adds.size() + 1});
+            prod.push_back(KsProduct{i, gal[j], keys[j]});
+            adds.push_back(KsAdd{srcs[i], gal[j], 0});
+        }
+    }
+    return ks_run(c, level, src.data(), (uint32_t)src.size(), prod.data(), grp.data(), (uint32_t)grp.size(),
+                  adds.data(), 0);
+}
+
+// out[i] = base[i] + sum_{j >= 1} Rot^{rots[j-1]}(T(i, j)), the inner products of
+// all terms of one output summed over Q_l u P before one ModDown.
+template <typename Term>
+static int rotate_sum(blb_ctx* c, const blb_keys* K, uint32_t level, const std::vector<const uint64_t*>& base,
+                      const std::vector<uint64_t*>& out, const std::vector<int32_t>& rots, Term T)
+{
+    if (base.empty()) return BLB_OK;
+    const size_t pw = (size_t)(level + 1) * c->N;
+    int rc = BLB_OK;
+    std::vector<const uint64_t*> keys(rots.size());
+    std::vector<uint64_t> gal(rots.size());
+    for (size_t j = 0; j < rots.size() && !rc; j++) {
+        keys[j] = key_for(K, c->N, rots[j], &rc);
+        gal[j] = galois_element(c->N, rots[j]);
+    }
+    if (rc) return rc;
+    std::vector<KsSource> src;
+    std::vector<KsProduct> prod;
+    std::vector<KsGroup> grp;
+    std::vector<KsAdd> adds;
+    for (uint32_t i = 0; i < base.size(); i++) {
+        KsGroup G{out[i], out[i] + pw, (uint32_t)prod.size(), 0, (uint32_t)adds.size(), 0};
+        adds.push_back(KsAdd{base[i], 1, 0});
+        adds.push_back(KsAdd{base[i] + pw, 1, 1});
+        for (uint32_t j = 0; j < rots.size(); j++) {
+            const uint64_t* t = T(i, j + 1);
+            prod.push_back(KsProduct{(uint32_t)src.size(), 1, keys[j]});
+            src.push_back(KsSource{t + pw, gal[j]});
+            adds.push_back(KsAdd{t, gal[j], 0});
+        }
+        G.prod1 = (uint32_t)prod.size();
+        G.add1 = (uint32_t)adds.size();
+        grp.push_back(G);
+    }
+    return ks_run(c, level, src.data(), (uint32_t)src.size(), prod.data(), grp.data(), (uint32_t)grp.size(),
+                  adds.data(), 0);
+}
+
 extern "C" int blb_matmul_cc_plan(blb_ctx* c, const blb_keys* K, const blb_cc_plan* P, blb_ct* const* A,
                                   blb_ct* const* B, uint32_t n_in, blb_ct** C)
 {
@@ -410,26 +482,21 @@ extern "C" int blb_matmul_cc_plan(blb_ctx* c, const blb_keys* K, const blb_cc_pl
     if (!rc) rc = INNER.alloc(c, n_c * P->G1, l0);
     if (!rc) rc = ACC.alloc(c, n_c, l0);
     if (!rc) rc = BP.alloc(c, n_c, l1);
-    for (uint32_t ci = 0; !rc && ci < n_c; ci++) {
-        const uint64_t* Bc = B[ci]->d;
-        for (uint32_t b0 = 0; !rc && b0 < P->b1s1; b0++) {
-            uint64_t* lo = LO.at((size_t)ci * P->b1s1 + b0);
-            uint64_t* hi = HI.at((size_t)ci * P->b1s1 + b0);
-            if (b0 == 0) {
-                if (cudaMemcpyAsync(lo, Bc, 2 * pw0 * 8, cudaMemcpyDeviceToDevice, c->stream))
-                    rc = blb_fail(BLB_ERR_CUDA, "copy failed");
-            } else {
-                const uint64_t* k = key_for(K, N, (int32_t)b0, &rc);
-                if (k) items.push_back(KsItem{Bc, Bc + pw0, nullptr, k, lo, lo + pw0, galois_element(N, (int32_t)b0)});
-            }
-            if (!rc && (b0 > 0 || P->G1 > 1)) {
-                const int32_t r = (int32_t)b0 - (int32_t)L;
-                const uint64_t* k = key_for(K, N, r, &rc);
-                if (k) items.push_back(KsItem{Bc, Bc + pw0, nullptr, k, hi, hi + pw0, galois_element(N, r)});
-            }
-        }
+    {  // baby steps: Rot^{b0}(B_c) (b0 >= 1) and Rot^{b0 - L}(B_c), hoisted per B_c
+        std::vector<const uint64_t*> srcs;
+        std::vector<int32_t> rots;
+        for (uint32_t ci = 0; ci < n_c; ci++) srcs.push_back(B[ci]->d);
+        for (uint32_t b0 = 1; b0 < P->b1s1; b0++) rots.push_back((int32_t)b0);
+        for (uint32_t b0 = (P->G1 > 1 ? 0 : 1); b0 < P->b1s1; b0++) rots.push_back((int32_t)b0 - (int32_t)L);
+        for (uint32_t ci = 0; !rc && ci < n_c; ci++)
+            if (cudaMemcpyAsync(LO.at((size_t)ci * P->b1s1), B[ci]->d, 2 * pw0 * 8, cudaMemcpyDeviceToDevice, c->stream))
+                rc = blb_fail(BLB_ERR_CUDA, "copy failed");
+        if (!rc)
+            rc = rotate_hoisted(c, K, l0, srcs, rots, [&](uint32_t i, uint32_t j) {
+                const int32_t r = rots[j];
+                return r > 0 ? LO.at((size_t)i * P->b1s1 + r) : HI.at((size_t)i * P->b1s1 + (r + (int32_t)L));
+            });
     }
-    if (!rc) rc = keyswitch_batch(c, l0, items.data(), (uint32_t)items.size(), 0);
     if (!rc) {  // inner[c][g1] = sum_b0 m1lo LO + m1hi HI
         std::vector<uint32_t> start{0};
         std::vector<LcTerm> terms;
@@ -448,19 +515,23 @@ extern "C" int blb_matmul_cc_plan(blb_ctx* c, const blb_keys* K, const blb_cc_pl
             }
         rc = lincomb(c, INNER.d, n_c * P->G1, start, terms, l0);
     }
-    for (uint32_t ci = 0; !rc && ci < n_c; ci++)
-        if (cudaMemcpyAsync(ACC.at(ci), INNER.at((size_t)ci * P->G1), 2 * pw0 * 8, cudaMemcpyDeviceToDevice,
-                            c->stream))
-            rc = blb_fail(BLB_ERR_CUDA, "copy failed");
-    for (uint32_t g1 = 1; !rc && g1 < P->G1; g1++) {
-        items.clear();
-        const int32_t r = (int32_t)(g1 * P->b1s1);
-        const uint64_t* k = key_for(K, N, r, &rc);
-        for (uint32_t ci = 0; k && ci < n_c; ci++) {
-            const uint64_t* src = INNER.at((size_t)ci * P->G1 + g1);
-            items.push_back(KsItem{src, src + pw0, nullptr, k, ACC.at(ci), ACC.at(ci) + pw0, galois_element(N, r)});
+    if (!rc) {  // ACC[c] = INNER[c][0] + sum_{g1 >= 1} Rot^{g1 b1s1}(INNER[c][g1]), one ModDown per c
+        std::vector<const uint64_t*> base;
+        std::vector<uint64_t*> out;
+        std::vector<int32_t> rots;
+        for (uint32_t ci = 0; ci < n_c; ci++) {
+            base.push_back(INNER.at((size_t)ci * P->G1));
+            out.push_back(ACC.at(ci));
         }
-        if (!rc) rc = keyswitch_batch(c, l0, items.data(), (uint32_t)items.size(), 1);
+        for (uint32_t g1 = 1; g1 < P->G1; g1++) rots.push_back((int32_t)(g1 * P->b1s1));
+        if (P->G1 == 1) {
+            for (uint32_t ci = 0; !rc && ci < n_c; ci++)
+                if (cudaMemcpyAsync(ACC.at(ci), base[ci], 2 * pw0 * 8, cudaMemcpyDeviceToDevice, c->stream))
+                    rc = blb_fail(BLB_ERR_CUDA, "copy failed");
+        } else {
+            rc = rotate_sum(c, K, l0, base, out, rots,
+                            [&](uint32_t i, uint32_t j) { return INNER.at((size_t)i * P->G1 + j); });
+        }
     }
     if (!rc) rc = rescale_many(c, BP.d, ACC.d, l0, n_c, 2);
 
@@ -475,27 +546,21 @@ extern "C" int blb_matmul_cc_plan(blb_ctx* c, const blb_keys* K, const blb_cc_pl
     if (!rc) rc = U.alloc(c, L, l2, 3);
     if (!rc) rc = WP.alloc(c, L, l2);
     if (!rc) rc = W.alloc(c, L, l3);
-    items.clear();
-    for (uint32_t ci = 0; !rc && ci < n_c; ci++) {
-        const uint64_t* Bc = BP.at(ci);
-        for (uint32_t b = 0; !rc && b < P->b1s2; b++) {
-            uint64_t* lo = BLO.at((size_t)ci * P->b1s2 + b);
-            uint64_t* hi = BHI.at((size_t)ci * P->b1s2 + b);
-            if (b == 0) {
-                if (cudaMemcpyAsync(lo, Bc, 2 * pw1 * 8, cudaMemcpyDeviceToDevice, c->stream))
-                    rc = blb_fail(BLB_ERR_CUDA, "copy failed");
-            } else {
-                const uint64_t* k = key_for(K, N, (int32_t)b, &rc);
-                if (k) items.push_back(KsItem{Bc, Bc + pw1, nullptr, k, lo, lo + pw1, galois_element(N, (int32_t)b)});
-            }
-            if (!rc && (b > 0 || P->G2 > 1)) {
-                const int32_t r = (int32_t)b - (int32_t)L;
-                const uint64_t* k = key_for(K, N, r, &rc);
-                if (k) items.push_back(KsItem{Bc, Bc + pw1, nullptr, k, hi, hi + pw1, galois_element(N, r)});
-            }
-        }
+    if (!rc) {  // baby steps: Rot^{b}(B'_c) (b >= 1) and Rot^{b - L}(B'_c), hoisted per B'_c
+        std::vector<const uint64_t*> srcs;
+        std::vector<int32_t> rots;
+        for (uint32_t ci = 0; ci < n_c; ci++) srcs.push_back(BP.at(ci));
+        for (uint32_t b = 1; b < P->b1s2; b++) rots.push_back((int32_t)b);
+        for (uint32_t b = (P->G2 > 1 ? 0 : 1); b < P->b1s2; b++) rots.push_back((int32_t)b - (int32_t)L);
+        for (uint32_t ci = 0; !rc && ci < n_c; ci++)
+            if (cudaMemcpyAsync(BLO.at((size_t)ci * P->b1s2), BP.at(ci), 2 * pw1 * 8, cudaMemcpyDeviceToDevice, c->stream))
+                rc = blb_fail(BLB_ERR_CUDA, "copy failed");
+        if (!rc)
+            rc = rotate_hoisted(c, K, l1, srcs, rots, [&](uint32_t i, uint32_t j) {
+                const int32_t r = rots[j];
+                return r > 0 ? BLO.at((size_t)i * P->b1s2 + r) : BHI.at((size_t)i * P->b1s2 + (r + (int32_t)L));
+            });
     }
-    if (!rc) rc = keyswitch_batch(c, l1, items.data(), (uint32_t)items.size(), 0);
     for (uint32_t ci = 0; !rc && ci < n_c; ci++) {  // A at level l2, then its giant-step rotations
         k_drop<<<dim3((N + kT - 1) / kT, l2 + 1, 2), kT, 0, c->stream>>>(A2.at(ci), A[ci]->d, l0 + 1, l2 + 1, N);
         if (cudaGetLastError() != cudaSuccess) rc = blb_fail(BLB_ERR_CUDA, "drop launch failed");
@@ -504,15 +569,14 @@ extern "C" int blb_matmul_cc_plan(blb_ctx* c, const blb_keys* K, const blb_cc_pl
                                    c->stream))
             rc = blb_fail(BLB_ERR_CUDA, "copy failed");
     }
-    items.clear();
-    for (uint32_t ci = 0; !rc && ci < n_c; ci++)
-        for (uint32_t g = 1; !rc && g < P->G2; g++) {
-            const int32_t r = -(int32_t)(g * P->b1s2);
-            const uint64_t* k = key_for(K, N, r, &rc);
-            uint64_t* o = AG.at((size_t)ci * P->G2 + g);
-            if (k) items.push_back(KsItem{A2.at(ci), A2.at(ci) + pw2, nullptr, k, o, o + pw2, galois_element(N, r)});
-        }
-    if (!rc) rc = keyswitch_batch(c, l2, items.data(), (uint32_t)items.size(), 0);
+    if (!rc) {  // giant steps of A: Rot^{-g b1s2}(A_c), hoisted per A_c
+        std::vector<const uint64_t*> srcs;
+        std::vector<int32_t> rots;
+        for (uint32_t ci = 0; ci < n_c; ci++) srcs.push_back(A2.at(ci));
+        for (uint32_t g = 1; g < P->G2; g++) rots.push_back(-(int32_t)(g * P->b1s2));
+        rc = rotate_hoisted(c, K, l2, srcs, rots,
+                            [&](uint32_t i, uint32_t j) { return AG.at((size_t)i * P->G2 + j + 1); });
+    }
     if (!rc) {  // VPRE[c][t] = m2lo BLO + m2hi BHI
         std::vector<uint32_t> start{0};
         std::vector<LcTerm> terms;
