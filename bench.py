@@ -46,7 +46,7 @@ TOKENS_PER_STEP = 128
 def config(world):
     return {"workload": WORKLOAD, "global_batch": world, "seq_len": M,
             "parallelism": "replicas" if world > 1 else "single",
-            "l2": "working set larger than L2 (36.6 GB of plaintext diagonals read per step)",
+            "l2": "working set larger than L2 (25.2 GB of byte-sliced plaintext diagonals read per step)",
             "bsgs_b1": B1}
 
 
@@ -336,6 +336,66 @@ def attention_cc(steps):
             "max_abs_err_vs_fp64": err, "rotation_keys": rot}
 
 
+def serving_bench(n_requests=64, rate=20.0, sat_rate=400.0, budget_gb=24, max_batch=8):
+    """Continuous batching of encrypted linear-layer requests (one client and key
+    set per request) against one request per launch; BERT-base-shaped and
+    GPT2-base-shaped weights (hidden 768), sequence lengths U[16, 128] padded to
+    32 / 64 / 128, N=2^15, 8 primes.  Poisson arrivals (seeded)."""
+    import torch
+    from paper_2508_19525_b300 import blb
+    from paper_2508_19525_b300 import workloads as wl
+    from paper_2508_19525_b300.serving import GpuEngine, Request, Server, bucket, percentile
+    prm = wl.BERT_CP
+    stream = torch.cuda.Stream()
+    ctx = blb.Context(prm.logN, prm.q_bits, prm.p_bits, prm.dnum, prm.scale, stream=stream)
+    buckets = (32, 64, 128)
+    rng = np.random.default_rng(2024)
+    plans = {}
+    for name, seed in (("bert", 0), ("gpt2", 1)):
+        Wq = rng.uniform(-1, 1, (D, D_QKV))
+        Wo = rng.uniform(-1, 1, (D, D_O))
+        for m in buckets:
+            k = ctx.N // 2 // m
+            b1 = 1
+            while b1 * b1 < k:
+                b1 *= 2
+            rots = [b * m for b in range(1, b1)] + [g * b1 * m for g in range(1, k // b1)]
+            plans[(name, m)] = (ctx.cp_plan(m, D, Wq, D_QKV, LEVEL, b1), ctx.cp_plan(m, D, Wo, D_O, LEVEL - 1, b1), rots)
+    ctx.sync()
+
+    def requests(rate_rps, seed):
+        r = np.random.default_rng(seed)
+        t, out = 0.0, []
+        for i in range(n_requests):
+            t += r.exponential(1.0 / rate_rps)
+            seq = int(r.integers(16, max(buckets) + 1))
+            out.append(Request(rid=i, client_seed=10_000 + i, model="bert" if i % 2 else "gpt2", seq=seq,
+                               m=bucket(seq, buckets), arrival=t, X=r.uniform(-1, 1, (seq, D))))
+        return out
+
+    def run(rate_rps, mb):
+        reqs = requests(rate_rps, seed=int(rate_rps))
+        srv = Server(GpuEngine(ctx, plans, LEVEL, D, D_QKV), budget_bytes=budget_gb << 30, max_batch=mb)
+        t0 = time.perf_counter()
+        done = srv.run(reqs)
+        span = time.perf_counter() - t0
+        lat = [r.latency * 1e3 for r in done]
+        return {"p50_ms": round(percentile(lat, 50), 2), "p99_ms": round(percentile(lat, 99), 2),
+                "tokens_per_s": round(sum(r.seq for r in done) / span, 1),
+                "mean_batch": round(float(np.mean([n for _, n in srv.iterations])), 2),
+                "iterations": len(srv.iterations)}
+
+    run(rate, max_batch)  # warm-up (plans, kernels, allocator)
+    out = {"workload": f"{n_requests} requests, Poisson {rate:g} req/s, half BERT-base- and half GPT2-base-shaped "
+                       "weights (768 -> 2304 then 768 -> 768, masking of every output), sequence lengths "
+                       "U[16,128] padded to 32/64/128, each request its own client key set; N=2^15, 8 primes",
+           "budget_gb": budget_gb, "max_batch": max_batch,
+           "batched": run(rate, max_batch), "plain": run(rate, 1),
+           "saturated": {"rate_rps": sat_rate, "batched": run(sat_rate, max_batch), "plain": run(sat_rate, 1)}}
+    ctx.sync()
+    return out
+
+
 def timed(w, steps, host, world):
     torch = w.torch
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -399,6 +459,7 @@ def run_blb(args):
         batched = {"sequences_per_step": args.batch, "value": round(bval, 3), "unit": UNIT,
                    "ms_per_step": round(bsec * 1e3 / bsteps, 3), "speedup_vs_plain": round(bval / value, 3)}
     attn = attention_cc(max(1, min(5, args.steps // 4))) if args.attention and world == 1 else None
+    serving = serving_bench() if args.serving and world == 1 else None
     if rank != 0:
         return
     peaks = {}
@@ -442,6 +503,7 @@ def run_blb(args):
         "accuracy": {"max_abs_err_vs_fp64": max_err, "mse": mse, "bound": 1e-4},
         "batched": batched,
         "attention_cc": attn,
+        "serving": serving,
         "counts_per_step": w.counts(),
         "weights": {"plaintext_bytes": w.plan_bytes, "encode_s": round(w.plan_s, 2), "timed": False},
     }
@@ -595,6 +657,8 @@ def main():
     ap.add_argument("--batch", type=int, default=8, help="sequences per batched step (1 = skip)")
     ap.add_argument("--no-attention", dest="attention", action="store_false",
                     help="skip the matmul_cc attention measurement")
+    ap.add_argument("--no-serving", dest="serving", action="store_false",
+                    help="skip the continuous-batching serving measurement")
     args = ap.parse_args()
     if args.ncu_case:
         return ncu_case(args.ncu_seqs)

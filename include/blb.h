@@ -210,6 +210,13 @@ int blb_matmul_cp_plan(blb_ctx* ctx, const blb_keys* keys, const blb_cp_plan* pl
  * applied to all sequences; results equal n_seq calls of blb_matmul_cp_plan. */
 int blb_matmul_cp_batch(blb_ctx* ctx, const blb_keys* keys, const blb_cp_plan* plan,
                         blb_ct* const* X, uint32_t n_seq, blb_ct** Y);
+/* The same product for sequences of different clients: keys[s] is the key set
+ * of sequence s (Galois keys for the plan's rotations, same context).  The
+ * plaintext diagonals are shared, so they stream from HBM once for the whole
+ * batch; each key switch uses its own client's key.  Member s's outputs are
+ * bit-identical to blb_matmul_cp_plan with keys[s]. */
+int blb_matmul_cp_multi(blb_ctx* ctx, const blb_keys* const* keys, const blb_cp_plan* plan, blb_ct* const* X,
+                        uint32_t n_seq, blb_ct** Y /* n_seq x nY handles */);
 int blb_matmul_cp(blb_ctx* ctx, const blb_keys* keys, blb_ct* const* X, uint32_t nX, uint32_t m,
                   uint32_t d, const double* W, uint32_t d_out, const blb_sched* sched, blb_ct** Y);
 

@@ -86,6 +86,7 @@ SIGNATURES = {
     "blb_cp_plan_info": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "blb_matmul_cp_plan": (ctypes.c_int, [_vp, _vp, _vp, _pp, _u32, _pp]),
     "blb_matmul_cp_batch": (ctypes.c_int, [_vp, _vp, _vp, _pp, _u32, _pp]),
+    "blb_matmul_cp_multi": (ctypes.c_int, [_vp, _pp, _vp, _pp, _u32, _pp]),
     "blb_matmul_cp": (ctypes.c_int, [_vp, _vp, _pp, _u32, _u32, _u32, _vp, _u32, ctypes.POINTER(_Sched), _pp]),
     "blb_cc_plan_create": (ctypes.c_int, [_vp, _u32, _u32, _u32, _u32, ctypes.POINTER(_CcSched), _pp]),
     "blb_cc_plan_free": (None, [_vp]),
@@ -281,6 +282,10 @@ class Context:
         _check(fn(self.h, *args, ctypes.byref(h)))
         return cls(self, h.value)
 
+    def key_bytes(self):
+        """Device bytes of one switching key: dnum x 2 x (nQ + nP) x N words."""
+        return self.dnum * 2 * (self.nQ + self.nP) * self.N * 8
+
     def sync(self):
         _check(lib().blb_ctx_sync(self.h))
 
@@ -424,6 +429,17 @@ class Context:
         xs = (ctypes.c_void_p * len(flat))(*[x.h for x in flat])
         ys = (ctypes.c_void_p * (len(X_seqs) * info["nY"]))()
         _check(lib().blb_matmul_cp_batch(self.h, keys.h, plan.h, xs, len(X_seqs), ys))
+        out = [Ciphertext(self, y) for y in ys]
+        return [out[s * info["nY"]:(s + 1) * info["nY"]] for s in range(len(X_seqs))]
+
+    def matmul_cp_multi(self, keys_list, plan, X_seqs):
+        """One key set per sequence (different clients) -> list of lists of nY."""
+        info = plan.info()
+        flat = [x for seq in X_seqs for x in seq]
+        xs = (ctypes.c_void_p * len(flat))(*[x.h for x in flat])
+        ks = (ctypes.c_void_p * len(keys_list))(*[k.h for k in keys_list])
+        ys = (ctypes.c_void_p * (len(X_seqs) * info["nY"]))()
+        _check(lib().blb_matmul_cp_multi(self.h, ks, plan.h, xs, len(X_seqs), ys))
         out = [Ciphertext(self, y) for y in ys]
         return [out[s * info["nY"]:(s + 1) * info["nY"]] for s in range(len(X_seqs))]
 

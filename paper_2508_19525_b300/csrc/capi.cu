@@ -634,9 +634,12 @@ extern "C" int blb_cp_plan_info(const blb_cp_plan* P, uint32_t* nX, uint32_t* nY
 
 // Y_e = Rescale( sum_g Rot^{g b1 m}( sum_{c,b} Rot^{b m}(X_c) (.) D'_{c,e,g,b} ) ), for S
 // sequences at once (X: S x nX handles, sequence-major; Y: S x nY)
-static int cp_run(blb_ctx* c, const blb_keys* K, const blb_cp_plan* P, blb_ct* const* X, uint32_t S, blb_ct** Y)
+static int cp_run(blb_ctx* c, const blb_keys* const* Ks, const blb_cp_plan* P, blb_ct* const* X, uint32_t S,
+                  blb_ct** Y)
 {
     const uint32_t nX = P->nX, n = P->level + 1, N = c->N;
+    for (uint32_t s = 0; s < S; s++)
+        if (!Ks[s] || Ks[s]->ctx != c) return blb_fail(BLB_ERR_ARG, "key set missing or from another context");
     for (uint32_t i = 0; i < S * nX; i++) {
         if (!X[i] || X[i]->level != P->level || X[i]->npolys != 2)
             return blb_fail(BLB_ERR_LEVEL, "input ciphertext level does not match the plan");
@@ -652,12 +655,14 @@ static int cp_run(blb_ctx* c, const blb_keys* K, const blb_cp_plan* P, blb_ct* c
     // decomposition and ModUp of X_c serve all its b1 - 1 rotations
     const uint32_t nb = P->b1 - 1;
     std::vector<uint64_t> gb(nb);
-    std::vector<const uint64_t*> kb(nb);
+    std::vector<const uint64_t*> kb((size_t)S * nb);  // [sequence][b - 1]
     for (uint32_t b = 1; !rc && b <= nb; b++) {
         gb[b - 1] = galois_element(N, (int32_t)(b * P->m));
-        const KeyEntry* k = K->find(gb[b - 1]);
-        if (!k) rc = blb_fail(BLB_ERR_NO_KEY, "no Galois key for rotation " + std::to_string(b * P->m));
-        else kb[b - 1] = k->d;
+        for (uint32_t s = 0; !rc && s < S; s++) {
+            const KeyEntry* k = Ks[s]->find(gb[b - 1]);
+            if (!k) rc = blb_fail(BLB_ERR_NO_KEY, "no Galois key for rotation " + std::to_string(b * P->m));
+            else kb[(size_t)s * nb + b - 1] = k->d;
+        }
     }
     {
         std::vector<KsSource> src;
@@ -673,7 +678,7 @@ static int cp_run(blb_ctx* c, const blb_keys* K, const blb_cp_plan* P, blb_ct* c
                 uint64_t* o = dst0 + (size_t)b * ctw;
                 grp.push_back(KsGroup{o, o + (size_t)n * N, (uint32_t)prod.size(), (uint32_t)prod.size() + 1,
                                       (uint32_t)adds.size(), (uint32_t)adds.size() + 1});
-                prod.push_back(KsProduct{ci, gb[b - 1], kb[b - 1]});
+                prod.push_back(KsProduct{ci, gb[b - 1], kb[(size_t)(ci / nX) * nb + b - 1]});
                 adds.push_back(KsAdd{X[ci]->d, gb[b - 1], 0});
             }
         }
@@ -695,12 +700,14 @@ static int cp_run(blb_ctx* c, const blb_keys* K, const blb_cp_plan* P, blb_ct* c
         std::vector<KsGroup> grp;
         std::vector<KsAdd> adds;
         std::vector<uint64_t> gg(P->G);
-        std::vector<const uint64_t*> kg(P->G);
+        std::vector<const uint64_t*> kg((size_t)S * P->G);  // [sequence][g]
         for (uint32_t g = 1; !rc && g < P->G; g++) {
             gg[g] = galois_element(N, (int32_t)(g * P->b1 * P->m));
-            const KeyEntry* k = K->find(gg[g]);
-            if (!k) rc = blb_fail(BLB_ERR_NO_KEY, "no Galois key for rotation " + std::to_string(g * P->b1 * P->m));
-            else kg[g] = k->d;
+            for (uint32_t s = 0; !rc && s < S; s++) {
+                const KeyEntry* k = Ks[s]->find(gg[g]);
+                if (!k) rc = blb_fail(BLB_ERR_NO_KEY, "no Galois key for rotation " + std::to_string(g * P->b1 * P->m));
+                else kg[(size_t)s * P->G + g] = k->d;
+            }
         }
         for (uint32_t e = 0; !rc && e < S * P->nY; e++) {
             uint64_t* T0 = T + (size_t)e * P->G * ctw;
@@ -709,7 +716,7 @@ static int cp_run(blb_ctx* c, const blb_keys* K, const blb_cp_plan* P, blb_ct* c
             adds.push_back(KsAdd{T0 + (size_t)n * N, 1, 1});
             for (uint32_t g = 1; g < P->G; g++) {
                 const uint64_t* Tg = T0 + (size_t)g * ctw;
-                prod.push_back(KsProduct{(uint32_t)src.size(), 1, kg[g]});
+                prod.push_back(KsProduct{(uint32_t)src.size(), 1, kg[(size_t)(e / P->nY) * P->G + g]});
                 src.push_back(KsSource{Tg + (size_t)n * N, gg[g]});
                 adds.push_back(KsAdd{Tg, gg[g], 0});
             }
@@ -753,14 +760,22 @@ extern "C" int blb_matmul_cp_plan(blb_ctx* c, const blb_keys* K, const blb_cp_pl
 {
     if (!c || !K || !P || !X || !Y) return blb_fail(BLB_ERR_ARG, "null argument");
     if (nX != P->nX) return blb_fail(BLB_ERR_ARG, "number of input ciphertexts does not match the plan");
-    return cp_run(c, K, P, X, 1, Y);
+    return cp_run(c, &K, P, X, 1, Y);
 }
 
 extern "C" int blb_matmul_cp_batch(blb_ctx* c, const blb_keys* K, const blb_cp_plan* P, blb_ct* const* X,
                                    uint32_t n_seq, blb_ct** Y)
 {
     if (!c || !K || !P || !X || !Y || n_seq == 0) return blb_fail(BLB_ERR_ARG, "null argument or empty batch");
-    return cp_run(c, K, P, X, n_seq, Y);
+    std::vector<const blb_keys*> Ks(n_seq, K);
+    return cp_run(c, Ks.data(), P, X, n_seq, Y);
+}
+
+extern "C" int blb_matmul_cp_multi(blb_ctx* c, const blb_keys* const* keys, const blb_cp_plan* P, blb_ct* const* X,
+                                   uint32_t n_seq, blb_ct** Y)
+{
+    if (!c || !keys || !P || !X || !Y || n_seq == 0) return blb_fail(BLB_ERR_ARG, "null argument or empty batch");
+    return cp_run(c, keys, P, X, n_seq, Y);
 }
 
 extern "C" int blb_matmul_cp(blb_ctx* c, const blb_keys* K, blb_ct* const* X, uint32_t nX, uint32_t m, uint32_t d,
