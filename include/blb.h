@@ -202,6 +202,18 @@ int blb_cp_plan_create(blb_ctx* ctx, uint32_t m, uint32_t d, const double* W, ui
 void blb_cp_plan_free(blb_cp_plan* plan);
 int blb_cp_plan_info(const blb_cp_plan* plan, uint32_t* nX, uint32_t* nY, uint32_t* b1,
                      uint32_t* G, uint64_t* plaintext_bytes);
+/* Plan of the diagonal-input product (App. C.2): E = Concat_h(Att_h) W for
+ * Att_h (L x Dh, L = 2 Dh) in matmul_cc's multi-head diagonal packing.  The
+ * input, per head group g (Hg[g] heads, Kc = N/2/(L Hg[g])), is the Dh/Kc
+ * dense-diagonal ciphertexts of matmul_cc's output with V_h padded to L
+ * columns: outputs j and j + Dh/Kc added (blb_add), so that block h + Hg kappa
+ * of ciphertext j holds Att_h[i][(i + delta) mod Dh], delta = j Kc + kappa.  W
+ * is (sum Hg) Dh x d_out, row-major (host or device).  The product runs with
+ * blb_matmul_cp_plan on the groups' ciphertexts in order; E comes back
+ * spatial-first (L rows, N/2/L columns per ciphertext) at level - 1. */
+int blb_cp_plan_create_diag(blb_ctx* ctx, uint32_t L, uint32_t n_groups, const uint32_t* Hg, uint32_t Dh,
+                            const double* W, uint32_t d_out, uint32_t level, const blb_sched* sched,
+                            blb_cp_plan** out);
 int blb_matmul_cp_plan(blb_ctx* ctx, const blb_keys* keys, const blb_cp_plan* plan,
                        blb_ct* const* X, uint32_t nX, blb_ct** Y);
 /* Batched form: n_seq sequences (same m and d, e.g. the sequences of one

@@ -294,6 +294,29 @@ class Oracle:
             raise ValueError(f"orc_matmul_cp failed: {rc}")
         return Y
 
+    def matmul_cp_diag(self, X_cts, L, groups, Dh, W, d_out, b1, galois, out_idx=None):
+        """Diagonal-input product (App. C.2).  X_cts: the dense-diagonal
+        ciphertexts of every head group in order; groups: heads per group."""
+        X_cts = np.ascontiguousarray(X_cts, np.uint64)
+        level = X_cts.shape[2] - 1
+        k = (self.N // 2) // L
+        nY = (d_out + k - 1) // k
+        out_idx = list(range(nY)) if out_idx is None else list(out_idx)
+        W = np.ascontiguousarray(W, np.float64)
+        hg = np.array(groups, np.uint32)
+        gals = np.array(list(galois.keys()), np.uint64)
+        keys = [np.ascontiguousarray(galois[int(g)], np.uint64) for g in gals]
+        ptrs = (_u64p * max(1, len(keys)))(*[_p(kk, _u64p) for kk in keys])
+        gs = _GaloisSet(len(keys), _p(gals, _u64p), ptrs)
+        oi = np.array(out_idx, np.uint32)
+        Y = np.zeros((len(out_idx), 2, level, self.N), np.uint64)
+        rc = lib().orc_matmul_cp_diag(self._pp, ctypes.byref(gs), _p(X_cts, _u64p), level, L, len(groups),
+                                      _p(hg, _u32p), Dh, _p(W, _f64p), d_out, b1, _p(oi, _u32p), len(out_idx),
+                                      _p(Y, _u64p))
+        if rc:
+            raise ValueError(f"orc_matmul_cp_diag failed: {rc}")
+        return Y
+
     def matmul_cc(self, A_cts, B_cts, L, Hg, b1s1, b1s2, galois, relin):
         """A_cts, B_cts: (n_c, 2, level+1, N) -> C: (L/Kc, 2, level-3, N)."""
         A_cts = np.ascontiguousarray(A_cts, np.uint64)

@@ -950,14 +950,33 @@ static const uint64_t* find_galois(const orc_params* p, const orc_galois_set* gk
     return NULL;
 }
 
-int orc_matmul_cp(const orc_params* p, const orc_galois_set* gk, const uint64_t* X, uint32_t nX,
-                  uint32_t level, uint32_t m, uint32_t d, const double* W, uint32_t d_out,
-                  uint32_t b1, const uint32_t* out_idx, uint32_t n_out, uint64_t* Y)
+/* Weight at row i of input column r and output column col of a BSGS diagonal;
+ * the plain product's weight does not depend on i. */
+typedef double (*cp_weight_fn)(const void* w, uint32_t i, uint32_t r, uint32_t col);
+
+typedef struct {
+    const double* W;
+    uint32_t d, d_out;
+} plain_weights;
+
+static double plain_weight(const void* w, uint32_t i, uint32_t r, uint32_t col)
+{
+    const plain_weights* P = (const plain_weights*)w;
+    (void)i;
+    return (r < P->d && col < P->d_out) ? P->W[(size_t)r * P->d_out + col] : 0.0;
+}
+
+/* BSGS diagonal product (Sec. 4.2.1 / 5.2) for any weight function:
+ *   Y_e = Rescale( sum_g Rot^{g b1 m}( sum_c sum_b Rot^{b m}(X_c) (.) D'_{c,e,g,b} ) )
+ * with D'_{c,e,g,b}[i + m beta] = w(i, c k + (beta + b) mod k, e k + (beta - g b1) mod k). */
+static int matmul_cp_w(const orc_params* p, const orc_galois_set* gk, const uint64_t* X, uint32_t nX,
+                       uint32_t level, uint32_t m, cp_weight_fn wf, const void* wctx, uint32_t b1,
+                       const uint32_t* out_idx, uint32_t n_out, uint64_t* Y)
 {
     const uint32_t N = p->N, s = N / 2, n = level + 1;
     if (level < 1 || m == 0 || s % m) return -1;
     const uint32_t k = s / m;
-    if (b1 == 0 || k % b1 || nX != (d + k - 1) / k) return -1;
+    if (b1 == 0 || k % b1) return -1;
     const uint32_t G = k / b1;
     const size_t ctw = (size_t)2 * n * N;
 
@@ -999,8 +1018,7 @@ int orc_matmul_cp(const orc_params* p, const orc_galois_set* gk, const uint64_t*
                     for (uint32_t beta = 0; beta < k; beta++) {
                         uint32_t row = c * k + (beta + b) % k;
                         uint32_t col = e * k + (beta + k - (g * b1) % k) % k;
-                        double w = (row < d && col < d_out) ? W[(size_t)row * d_out + col] : 0.0;
-                        for (uint32_t i = 0; i < m; i++) z[i + m * beta] = w;
+                        for (uint32_t i = 0; i < m; i++) z[i + m * beta] = wf(wctx, i, row, col);
                     }
                     if (orc_encode(p, z, s, level, pt_scale, pt)) rc = -3;
                     orc_mul_plain(p, baby + ((size_t)c * b1 + b) * ctw, pt, level, prod);
@@ -1013,6 +1031,86 @@ int orc_matmul_cp(const orc_params* p, const orc_galois_set* gk, const uint64_t*
         orc_rescale(p, acc, level, 2, Y + (size_t)oi * 2 * level * N);
     }
     free(baby); free(rots); free(keys); free(z); free(pt); free(prod); free(T); free(acc);
+    return rc;
+}
+
+int orc_matmul_cp(const orc_params* p, const orc_galois_set* gk, const uint64_t* X, uint32_t nX,
+                  uint32_t level, uint32_t m, uint32_t d, const double* W, uint32_t d_out,
+                  uint32_t b1, const uint32_t* out_idx, uint32_t n_out, uint64_t* Y)
+{
+    const uint32_t s = p->N / 2;
+    if (m == 0 || s % m || nX != (d + s / m - 1) / (s / m)) return -1;
+    plain_weights w = {W, d, d_out};
+    return matmul_cp_w(p, gk, X, nX, level, m, plain_weight, &w, b1, out_idx, n_out, Y);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Diagonal-input matmul_cp (App. C.2): E = Concat_h(Att_h) W_O for Att_h in   */
+/* the multi-head diagonal packing that matmul_cc returns.                     */
+/* ------------------------------------------------------------------------- */
+/* Input: for each head group (Hg heads, Kc = s/(L Hg)), the Dh/Kc ciphertexts
+ * of Att_h in *dense* diagonal packing: matmul_cc's outputs j and j + Dh/Kc
+ * added (V_h padded from Dh to L = 2 Dh columns makes diagonals delta and
+ * delta + Dh complementary), so merged ciphertext j holds, at block
+ * h + Hg kappa, element i = Att_h[i][(i + delta) mod Dh], delta = j Kc + kappa.
+ * Input column r = c k + beta (k = s/L) of the product is that block; with
+ * (h, delta) its head (global index) and diagonal,
+ *   E[i][o] = sum_{h, delta} Att_h[i][(i + delta) mod Dh] W_O[h Dh + (i + delta) mod Dh][o],
+ * i.e. the BSGS product with the row-dependent weight
+ *   w(i, r, o) = W_O[h Dh + (i + delta) mod Dh][o]. */
+typedef struct {
+    const double* W;      /* (H Dh) x d_out */
+    uint32_t Dh, d_out, ncols;
+    const int32_t* head;  /* per input column: global head, -1 = unused */
+    const int32_t* delta; /* per input column: diagonal */
+} diag_weights;
+
+static double diag_weight(const void* w, uint32_t i, uint32_t r, uint32_t col)
+{
+    const diag_weights* D = (const diag_weights*)w;
+    if (r >= D->ncols || col >= D->d_out || D->head[r] < 0) return 0.0;
+    const uint32_t row = (uint32_t)D->head[r] * D->Dh + (i + (uint32_t)D->delta[r]) % D->Dh;
+    return D->W[(size_t)row * D->d_out + col];
+}
+
+uint32_t orc_cp_diag_inputs(uint32_t s, uint32_t L, uint32_t n_groups, const uint32_t* Hg, uint32_t Dh)
+{
+    uint32_t nX = 0;
+    for (uint32_t g = 0; g < n_groups; g++) {
+        const uint32_t Kc = s / (L * Hg[g]);
+        nX += Dh / Kc;
+    }
+    return nX;
+}
+
+int orc_matmul_cp_diag(const orc_params* p, const orc_galois_set* gk, const uint64_t* X, uint32_t level, uint32_t L,
+                       uint32_t n_groups, const uint32_t* Hg, uint32_t Dh, const double* W, uint32_t d_out,
+                       uint32_t b1, const uint32_t* out_idx, uint32_t n_out, uint64_t* Y)
+{
+    const uint32_t s = p->N / 2;
+    if (L == 0 || s % L || L != 2 * Dh) return -1;
+    const uint32_t k = s / L, nX = orc_cp_diag_inputs(s, L, n_groups, Hg, Dh);
+    int32_t* head = malloc(sizeof(int32_t) * nX * k);
+    int32_t* delta = malloc(sizeof(int32_t) * nX * k);
+    uint32_t c = 0, h0 = 0;
+    int rc = 0;
+    for (uint32_t g = 0; g < n_groups && !rc; g++) {
+        if (s % (L * Hg[g])) { rc = -1; break; }
+        const uint32_t Kc = s / (L * Hg[g]);
+        if (Dh % Kc) { rc = -1; break; }
+        for (uint32_t j = 0; j < Dh / Kc; j++, c++)
+            for (uint32_t beta = 0; beta < k; beta++) {
+                head[c * k + beta] = (int32_t)(h0 + beta % Hg[g]);
+                delta[c * k + beta] = (int32_t)(j * Kc + beta / Hg[g]);
+            }
+        h0 += Hg[g];
+    }
+    if (!rc) {
+        diag_weights w = {W, Dh, d_out, nX * k, head, delta};
+        rc = matmul_cp_w(p, gk, X, nX, level, L, diag_weight, &w, b1, out_idx, n_out, Y);
+    }
+    free(head);
+    free(delta);
     return rc;
 }
 

@@ -120,6 +120,14 @@ uint32_t orc_cp_num_rotations(uint32_t nX, uint32_t nY, uint32_t b1, uint32_t G)
 int orc_matmul_cp(const orc_params* p, const orc_galois_set* gk, const uint64_t* X, uint32_t nX,
                   uint32_t level, uint32_t m, uint32_t d, const double* W, uint32_t d_out,
                   uint32_t b1, const uint32_t* out_idx, uint32_t n_out, uint64_t* Y);
+/* Diagonal-input matmul_cp (App. C.2): X holds, per head group g (Hg[g] heads,
+ * Kc = s/(L Hg[g])), the Dh/Kc dense-diagonal ciphertexts of Att_h (matmul_cc's
+ * outputs j and j + Dh/Kc added; L = 2 Dh); W is (sum Hg) Dh x d_out.  Output
+ * as orc_matmul_cp: spatial-first E = Concat_h(Att_h) W, level - 1. */
+uint32_t orc_cp_diag_inputs(uint32_t s, uint32_t L, uint32_t n_groups, const uint32_t* Hg, uint32_t Dh);
+int orc_matmul_cp_diag(const orc_params* p, const orc_galois_set* gk, const uint64_t* X, uint32_t level, uint32_t L,
+                       uint32_t n_groups, const uint32_t* Hg, uint32_t Dh, const double* W, uint32_t d_out,
+                       uint32_t b1, const uint32_t* out_idx, uint32_t n_out, uint64_t* Y);
 uint32_t orc_cc_num_rotations(uint32_t n_c, uint32_t L, uint32_t Kc, uint32_t b1s1, uint32_t b1s2);
 int orc_matmul_cc(const orc_params* p, const orc_galois_set* gk, const uint64_t* relin_ksk, const uint64_t* A,
                   const uint64_t* B, uint32_t n_c, uint32_t level, uint32_t L, uint32_t Hg, uint32_t b1s1,

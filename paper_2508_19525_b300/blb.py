@@ -82,6 +82,7 @@ SIGNATURES = {
     "blb_keyswitch_coeffs": (ctypes.c_int, [_vp, _vp, _i32, _vp, _u32, _vp]),
     "blb_keyswitch_noalloc": (ctypes.c_int, [_vp, _vp, _i32, _vp, _u32, _vp]),
     "blb_cp_plan_create": (ctypes.c_int, [_vp, _u32, _u32, _vp, _u32, _u32, ctypes.POINTER(_Sched), _pp]),
+    "blb_cp_plan_create_diag": (ctypes.c_int, [_vp, _u32, _u32, _vp, _u32, _vp, _u32, _u32, ctypes.POINTER(_Sched), _pp]),
     "blb_cp_plan_free": (None, [_vp]),
     "blb_cp_plan_info": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "blb_matmul_cp_plan": (ctypes.c_int, [_vp, _vp, _vp, _pp, _u32, _pp]),
@@ -414,6 +415,14 @@ class Context:
             W = np.ascontiguousarray(W, np.float64)
         s = _Sched(b1)
         return self._new(CpPlan, lib().blb_cp_plan_create, m, d, _ptr(W), d_out, level, ctypes.byref(s))
+
+    def cp_plan_diag(self, L, groups, Dh, W, d_out, level, b1=0):
+        """Diagonal-input plan (App. C.2): groups = heads per head group."""
+        W = np.ascontiguousarray(W, np.float64) if isinstance(W, np.ndarray) else W
+        hg = np.ascontiguousarray(groups, np.uint32)
+        s = _Sched(b1)
+        return self._new(CpPlan, lib().blb_cp_plan_create_diag, L, len(groups), hg.ctypes.data, Dh, _ptr(W), d_out,
+                         level, ctypes.byref(s))
 
     def matmul_cp_plan(self, keys, plan, X):
         info = plan.info()

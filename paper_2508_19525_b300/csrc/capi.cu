@@ -530,8 +530,15 @@ extern "C" int blb_keyswitch_coeffs(blb_ctx* c, const blb_keys* K, int32_t rot, 
 // ===========================================================================
 // matmul_cp
 // ===========================================================================
-extern "C" int blb_cp_plan_create(blb_ctx* c, uint32_t m, uint32_t d, const double* W, uint32_t d_out,
-                                  uint32_t level, const blb_sched* sched, blb_cp_plan** out)
+// diag: optional per-input-column (head, diagonal) of a diagonal-packed input
+// (head -1 = unused column) and the head dimension; nX then comes from it
+struct DiagLayout {
+    std::vector<int32_t> head, delta;
+    uint32_t Dh, nX;
+};
+
+static int cp_plan_build(blb_ctx* c, uint32_t m, uint32_t d, const double* W, uint32_t d_out, uint32_t level,
+                         const blb_sched* sched, const DiagLayout* diag, blb_cp_plan** out)
 {
     if (!c || !W || !out) return blb_fail(BLB_ERR_ARG, "null argument");
     *out = nullptr;
@@ -554,7 +561,7 @@ extern "C" int blb_cp_plan_create(blb_ctx* c, uint32_t m, uint32_t d, const doub
     P->d_out = d_out;
     P->level = level;
     P->k = k;
-    P->nX = (d + k - 1) / k;
+    P->nX = diag ? diag->nX : (d + k - 1) / k;
     P->nY = (d_out + k - 1) / k;
     P->b1 = b1;
     P->G = k / b1;
@@ -586,6 +593,17 @@ extern "C" int blb_cp_plan_create(blb_ctx* c, uint32_t m, uint32_t d, const doub
     // slice them into the byte layout of the tensor-core product
     const uint64_t blk_pts = (uint64_t)16 * terms;
     const size_t blk_bytes = blk_pts * n * c->N * 8;
+    int32_t* d_head = nullptr;
+    int32_t* d_delta = nullptr;
+    const size_t lbytes = diag ? diag->head.size() * 4 : 0;
+    if (!rc && diag) {
+        d_head = (int32_t*)dev_alloc(c, lbytes);
+        d_delta = (int32_t*)dev_alloc(c, lbytes);
+        if (!d_head || !d_delta) rc = blb_fail(BLB_ERR_OOM, "diagonal layout");
+        else if (cudaMemcpyAsync(d_head, diag->head.data(), lbytes, cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
+                 cudaMemcpyAsync(d_delta, diag->delta.data(), lbytes, cudaMemcpyHostToDevice, c->stream) != cudaSuccess)
+            rc = blb_fail(BLB_ERR_CUDA, "layout upload failed");
+    }
     const uint32_t chunk = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(blk_pts, (64ull << 20) / ((uint64_t)s * 8)));
     double* z = rc ? nullptr : (double*)dev_alloc(c, (size_t)chunk * s * 8);
     uint64_t* blk = rc ? nullptr : (uint64_t*)dev_alloc(c, blk_bytes);
@@ -594,7 +612,7 @@ extern "C" int blb_cp_plan_create(blb_ctx* c, uint32_t m, uint32_t d, const doub
         const uint64_t first = (uint64_t)eb * blk_pts, npts = (uint64_t)std::min<uint32_t>(16, neg - eb * 16) * terms;
         for (uint64_t f = 0; !rc && f < npts; f += chunk) {
             uint32_t cnt = (uint32_t)std::min<uint64_t>(chunk, npts - f);
-            rc = cp_build_diagonals(c, P, dW, (uint32_t)(first + f), cnt, z);
+            rc = cp_build_diagonals(c, P, dW, (uint32_t)(first + f), cnt, z, d_head, d_delta, diag ? diag->Dh : 0);
             if (!rc) rc = encode_slots(c, z, cnt, s, level, (double)c->q[level], blk + f * n * c->N);
         }
         if (!rc) rc = cp_plan_store_block(c, P, blk, eb);
@@ -603,12 +621,47 @@ extern "C" int blb_cp_plan_create(blb_ctx* c, uint32_t m, uint32_t d, const doub
     dev_free(c, z, (size_t)chunk * s * 8);
     dev_free(c, blk, blk_bytes);
     dev_free(c, Wcopy, wbytes);
+    dev_free(c, d_head, lbytes);
+    dev_free(c, d_delta, lbytes);
     if (rc) {
         blb_cp_plan_free(P);
         return rc;
     }
     *out = P;
     return BLB_OK;
+}
+
+extern "C" int blb_cp_plan_create(blb_ctx* c, uint32_t m, uint32_t d, const double* W, uint32_t d_out,
+                                  uint32_t level, const blb_sched* sched, blb_cp_plan** out)
+{
+    return cp_plan_build(c, m, d, W, d_out, level, sched, nullptr, out);
+}
+
+extern "C" int blb_cp_plan_create_diag(blb_ctx* c, uint32_t L, uint32_t n_groups, const uint32_t* Hg, uint32_t Dh,
+                                       const double* W, uint32_t d_out, uint32_t level, const blb_sched* sched,
+                                       blb_cp_plan** out)
+{
+    if (!c || !Hg || !W || !out || n_groups == 0) return blb_fail(BLB_ERR_ARG, "null argument");
+    *out = nullptr;
+    const uint32_t s = c->N / 2;
+    if (L == 0 || s % L || L != 2 * Dh) return blb_fail(BLB_ERR_ARG, "L must divide N/2 and equal 2 Dh");
+    const uint32_t k = s / L;
+    DiagLayout lay;
+    lay.Dh = Dh;
+    uint32_t H = 0;
+    for (uint32_t g = 0; g < n_groups; g++) {
+        if (Hg[g] == 0 || s % (L * Hg[g])) return blb_fail(BLB_ERR_ARG, "L Hg must divide N/2");
+        const uint32_t Kc = s / (L * Hg[g]);
+        if (Dh % Kc) return blb_fail(BLB_ERR_ARG, "the head dimension must be a multiple of Kc");
+        for (uint32_t j = 0; j < Dh / Kc; j++)
+            for (uint32_t beta = 0; beta < k; beta++) {
+                lay.head.push_back((int32_t)(H + beta % Hg[g]));
+                lay.delta.push_back((int32_t)(j * Kc + beta / Hg[g]));
+            }
+        H += Hg[g];
+    }
+    lay.nX = (uint32_t)(lay.head.size() / k);
+    return cp_plan_build(c, L, H * Dh, W, d_out, level, sched, &lay, out);
 }
 
 extern "C" void blb_cp_plan_free(blb_cp_plan* P)

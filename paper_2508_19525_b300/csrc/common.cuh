@@ -371,7 +371,8 @@ int encode_slots(blb_ctx* ctx, const double* d_z, uint32_t npts, uint32_t n, uin
 int decode_limb0(blb_ctx* ctx, const uint64_t* d_coef0, double scale, double* d_slots);
 // matmul_cp plaintext diagonals for pts [first, first+count) of a plan (slot vectors)
 int cp_build_diagonals(blb_ctx* ctx, const blb_cp_plan* plan, const double* d_W, uint32_t first, uint32_t count,
-                       double* d_z);
+                       double* d_z, const int32_t* d_head = nullptr, const int32_t* d_delta = nullptr,
+                       uint32_t Dh = 0);
 int launch_cp_mac(blb_ctx* ctx, const blb_cp_plan* plan, const uint64_t* baby, uint64_t* T, uint32_t S);
 int cp_plan_layout(blb_ctx* ctx, blb_cp_plan* plan);
 int cp_plan_store_block(blb_ctx* ctx, blb_cp_plan* plan, const uint64_t* src, uint32_t eblk);

@@ -165,6 +165,27 @@ __global__ void k_cp_diag(double* __restrict__ z, const double* __restrict__ W, 
     z[(size_t)pl * s + slot] = (row < d && col < d_out) ? W[(size_t)row * d_out + col] : 0.0;
 }
 
+// Diagonal-input weights (App. C.2): input column r holds head head[r] and
+// dense diagonal delta[r] of Att in diagonal packing; the weight at row i is
+// W[head Dh + (i + delta) mod Dh][col].
+__global__ void k_cp_diag_rows(double* __restrict__ z, const double* __restrict__ W, uint32_t m, uint32_t d_out,
+                               uint32_t k, uint32_t b1, uint32_t G, uint32_t nX, uint32_t first,
+                               const int32_t* __restrict__ head, const int32_t* __restrict__ delta, uint32_t Dh)
+{
+    const uint32_t s = m * k;
+    const uint32_t slot = blockIdx.x * blockDim.x + threadIdx.x, pl = blockIdx.y;
+    if (slot >= s) return;
+    const uint32_t p = first + pl;
+    const uint32_t b = p % b1, c = (p / b1) % nX, g = (p / (b1 * nX)) % G, e = p / (b1 * nX * G);
+    const uint32_t beta = slot / m, i = slot % m;
+    const uint32_t r = c * k + (beta + b) % k;
+    const uint32_t col = e * k + (beta + k - (g * b1) % k) % k;
+    double w = 0.0;
+    if (col < d_out && head[r] >= 0)
+        w = W[((size_t)head[r] * Dh + (i + (uint32_t)delta[r]) % Dh) * d_out + col];
+    z[(size_t)pl * s + slot] = w;
+}
+
 int run_dit(blb_ctx* ctx, double2* A, uint32_t npts, int inverse, const double2* zeta)
 {
     const uint32_t logs = ctx->logN - 1, s = 1u << logs;
@@ -232,11 +253,15 @@ int decode_limb0(blb_ctx* ctx, const uint64_t* d_coef0, double scale, double* d_
 }
 
 int cp_build_diagonals(blb_ctx* ctx, const blb_cp_plan* plan, const double* d_W, uint32_t first, uint32_t count,
-                       double* d_z)
+                       double* d_z, const int32_t* d_head, const int32_t* d_delta, uint32_t Dh)
 {
     const uint32_t s = ctx->N / 2;
-    k_cp_diag<<<dim3((s + kT - 1) / kT, count), kT, 0, ctx->stream>>>(d_z, d_W, plan->m, plan->d, plan->d_out,
-                                                                    plan->k, plan->b1, plan->G, plan->nX, first);
+    if (d_head)
+        k_cp_diag_rows<<<dim3((s + kT - 1) / kT, count), kT, 0, ctx->stream>>>(
+            d_z, d_W, plan->m, plan->d_out, plan->k, plan->b1, plan->G, plan->nX, first, d_head, d_delta, Dh);
+    else
+        k_cp_diag<<<dim3((s + kT - 1) / kT, count), kT, 0, ctx->stream>>>(d_z, d_W, plan->m, plan->d, plan->d_out,
+                                                                        plan->k, plan->b1, plan->G, plan->nX, first);
     BLB_LAUNCHED();
     return BLB_OK;
 }
