@@ -16,7 +16,8 @@ _f64p = ctypes.POINTER(ctypes.c_double)
 _u32p = ctypes.POINTER(ctypes.c_uint32)
 
 MAX_PRIMES = 32
-SECRET, KEY_A, KEY_E, ENC_A, ENC_E, MASK = 1, 2, 3, 4, 5, 6
+SECRET, KEY_A, KEY_E, ENC_A, ENC_E, MASK, WRAP = 1, 2, 3, 4, 5, 6, 7
+FX_F, FX_P = 30, 26  # fraction bits of the share-FFT roots; resolution of its data
 
 
 class _Params(ctypes.Structure):
@@ -56,6 +57,60 @@ def philox(ctr, key):
     o = (ctypes.c_uint32 * 4)()
     lib().orc_philox(c, k, o)
     return list(o)
+
+
+def u128_words(vals):
+    """Python ints (any sign) -> (n, 2) uint64 words of their residues mod 2^128."""
+    v = [int(x) % (1 << 128) for x in vals]
+    return np.array([[x & (2**64 - 1), x >> 64] for x in v], np.uint64).reshape(len(v), 2)
+
+
+def words_u128(w):
+    """(n, 2) uint64 words -> Python ints in [0, 2^128)."""
+    w = np.asarray(w, np.uint64).reshape(-1, 2)
+    return [int(a) | (int(b) << 64) for a, b in w]
+
+
+def share_trunc(party, x, k):
+    """Party's local truncation of 128-bit shares ((n, 2) words) by k bits."""
+    x = np.ascontiguousarray(x, np.uint64).reshape(-1, 2)
+    out = np.zeros_like(x)
+    lib().orc_share_trunc(party, _p(x, _u64p), ctypes.c_uint64(len(x)), k, _p(out, _u64p))
+    return out
+
+
+def f2r_wrap_sim(q, t0, t1, seed, nonce):
+    t0 = np.ascontiguousarray(t0, np.uint64)
+    t1 = np.ascontiguousarray(t1, np.uint64)
+    w0, w1 = np.zeros((len(t0), 2), np.uint64), np.zeros((len(t0), 2), np.uint64)
+    lib().orc_f2r_wrap_sim(len(t0), ctypes.c_uint64(q), _p(t0, _u64p), _p(t1, _u64p), ctypes.c_uint64(seed),
+                           nonce, _p(w0, _u64p), _p(w1, _u64p))
+    return w0, w1
+
+
+def f2r_local(party, q, t, wsh):
+    t = np.ascontiguousarray(t, np.uint64)
+    wsh = np.ascontiguousarray(wsh, np.uint64)
+    U = np.zeros((len(t), 2), np.uint64)
+    lib().orc_f2r_local(party, len(t), ctypes.c_uint64(q), _p(t, _u64p), _p(wsh, _u64p), _p(U, _u64p))
+    return U
+
+
+def ext_wrap_sim(l, x0, x1, seed, nonce):
+    x0 = np.ascontiguousarray(x0, np.uint64)
+    x1 = np.ascontiguousarray(x1, np.uint64)
+    w0, w1 = np.zeros((len(x0), 2), np.uint64), np.zeros((len(x0), 2), np.uint64)
+    lib().orc_ext_wrap_sim(len(x0), l, _p(x0, _u64p), _p(x1, _u64p), ctypes.c_uint64(seed), nonce,
+                           _p(w0, _u64p), _p(w1, _u64p))
+    return w0, w1
+
+
+def ext_local(party, l, x, wsh):
+    x = np.ascontiguousarray(x, np.uint64)
+    wsh = np.ascontiguousarray(wsh, np.uint64)
+    X = np.zeros((len(x), 2), np.uint64)
+    lib().orc_ext_local(party, len(x), l, _p(x, _u64p), _p(wsh, _u64p), _p(X, _u64p))
+    return X
 
 
 def is_prime(n):
@@ -339,6 +394,33 @@ class Oracle:
 
     def cp_num_rotations(self, nX, nY, b1, G):
         return int(lib().orc_cp_num_rotations(nX, nY, b1, G))
+
+    # -- local parts of the conversions (Alg. 1 steps 3-4, Alg. 2, App. C.3) --
+    def r2f_local(self, party, M, level):
+        M = np.ascontiguousarray(M, np.uint64).reshape(-1, 2)
+        out = np.zeros((level + 1, len(M)), np.uint64)
+        lib().orc_r2f_local(self._pp, party, len(M), _p(M, _u64p), level, _p(out, _u64p))
+        return out
+
+    def c2m_local(self, party, t, wsh, scale, l=43, sf=13):
+        t = np.ascontiguousarray(t, np.uint64)
+        wsh = np.ascontiguousarray(wsh, np.uint64)
+        out = np.zeros(self.N // 2, np.uint64)
+        rc = lib().orc_c2m_local(self._pp, party, _p(t, _u64p), _p(wsh, _u64p), ctypes.c_double(scale), l, sf,
+                                 _p(out, _u64p))
+        if rc:
+            raise ValueError(f"c2m_local failed {rc}")
+        return out
+
+    def m2c_local(self, party, x, wsh, level, scale, l=43, sf=13):
+        x = np.ascontiguousarray(x, np.uint64)
+        wsh = np.ascontiguousarray(wsh, np.uint64)
+        out = np.zeros((level + 1, self.N), np.uint64)
+        rc = lib().orc_m2c_local(self._pp, party, _p(x, _u64p), _p(wsh, _u64p), len(x), level,
+                                 ctypes.c_double(scale), l, sf, _p(out, _u64p))
+        if rc:
+            raise ValueError(f"m2c_local failed {rc}")
+        return out
 
     def he2mpc(self, ct, seed, nonce):
         ct = np.ascontiguousarray(ct, np.uint64)

@@ -14,6 +14,9 @@
  *             here is the standard diagonal method with baby-step giant-step,
  *             App. C.1)
  *   Sec. 6.3 / Alg. 1  secure CKKS-to-MPC masking with a uniform mask
+ *   Alg. 1 steps 3-4, Alg. 2, App. C.3  the parties' local steps of the
+ *             conversions: field to ring, ring to field, fixed-point decoding
+ *             and encoding of shares with local truncations
  * Where the paper is silent (key switching, sampling, prime choice, rounding
  * modes) the readings are the ones listed in the design notes; each function
  * below states the one it implements.
@@ -1407,4 +1410,294 @@ void orc_he2mpc(const orc_params* p, const uint64_t* ct, uint32_t level, uint64_
         p1_share[i] = negmod(r[i], q0);
     }
     free(r);
+}
+
+/* ------------------------------------------------------------------------- */
+/* local parts of the conversions between CKKS and additive shares            */
+/* (Alg. 1 steps 3-4, Alg. 2, Sec. 6.3, App. C.3)                              */
+/* ------------------------------------------------------------------------- */
+/* Shares of the extended ring Z_{2^128} are unsigned 128-bit integers, stored
+ * as two words (low, high) per element.  The paper extends the l-bit MPC ring
+ * (l = 43, fixed-point scale 2^13, Sec. 7.1) to a larger ring so that every
+ * local truncation inside the share FFTs fails with probability below 2^-40
+ * (its example width is l + 40).  A truncated product here is the FFT datum
+ * (resolution 2^-ORC_FX_P slot units) times a root with ORC_FX_F fraction bits,
+ * about 2^87 for slot values up to 2^31, so the ring taken is Z_{2^128}: the
+ * failure probability of one truncation of m is |m| / 2^128.
+ *
+ * The interactive comparisons inside the ring/field extensions (Pi_Ext of
+ * SiRNN, as BOLT adapts it) are MPC protocols; here only their ideal
+ * functionality is simulated (orc_*_wrap_sim), and everything each party then
+ * computes on its own share is written out step by step. */
+
+static u128 ld128(const uint64_t* w, size_t i) { return (u128)w[2 * i] | ((u128)w[2 * i + 1] << 64); }
+static void st128(uint64_t* w, size_t i, u128 v)
+{
+    w[2 * i] = (uint64_t)v;
+    w[2 * i + 1] = (uint64_t)(v >> 64);
+}
+
+/* Probabilistic truncation by k bits (SecureML, as App. C.3 specifies it: the
+ * result is floor(m / 2^k) + u with Pr[u = 1] = (m mod 2^k) / 2^k).  Each party
+ * reads its share as a signed 128-bit integer; P0 takes floor(x / 2^k) (an
+ * arithmetic shift right), P1 takes ceil(x / 2^k) = -floor(-x / 2^k), SecureML's
+ * two local operations.  Shifting both shares alone would subtract one more
+ * unit on average, a bias that the FFTs below would accumulate.  The result
+ * is wrong (off by about 2^(128-k)) only when the two signed shares overflow
+ * when added, with probability |m| / 2^128. */
+static u128 trunc_share(u128 x, uint32_t k, uint32_t party)
+{
+    if (party == 0) return (u128)((__int128)x >> k);
+    return (u128)0 - (u128)((__int128)((u128)0 - x) >> k);
+}
+
+void orc_share_trunc(uint32_t party, const uint64_t* x, uint64_t n, uint32_t k, uint64_t* out)
+{
+    for (uint64_t i = 0; i < n; i++) st128(out, i, trunc_share(ld128(x, i), k, party));
+}
+
+/* Fixed-point root c zeta^k = (round(2^F c cos(pi k/N)), round(2^F c sin(pi k/N)))
+ * from the C library's cos and sin, rounded half to even. */
+static void fx_zeta(uint32_t N, uint32_t k, double c, int64_t* re, int64_t* im)
+{
+    double ang = M_PI * (double)k / (double)N;
+    *re = (int64_t)rint(ldexp(cos(ang) * c, ORC_FX_F));
+    *im = (int64_t)rint(ldexp(sin(ang) * c, ORC_FX_F));
+}
+
+typedef struct { u128 re, im; } cshare;
+
+/* share times a signed integer, mod 2^128 */
+static u128 smul(u128 a, int64_t w) { return a * (u128)(__int128)w; }
+
+/* (v.re + i v.im)(wr + i wi) before truncation */
+static cshare cmul_share(cshare v, int64_t wr, int64_t wi)
+{
+    cshare r = {smul(v.re, wr) - smul(v.im, wi), smul(v.re, wi) + smul(v.im, wr)};
+    return r;
+}
+
+/* Arithmetic shares over Z_{2^128} of the bit w, as the comparison inside
+ * Pi_Ext hands them out (ideal functionality): P0 receives rho, the 128-bit
+ * Philox draw (i, 0, nonce, WRAP) keyed by seed (word 3 most significant), P1
+ * receives w - rho. */
+static void share_bit(uint32_t w, uint64_t seed, uint32_t i, uint32_t nonce, uint64_t* w0, uint64_t* w1)
+{
+    uint32_t d[4];
+    draw(seed, i, 0, nonce, ORC_WRAP, d);
+    u128 rho = ((u128)d[3] << 96) | ((u128)d[2] << 64) | ((u128)d[1] << 32) | (u128)d[0];
+    st128(w0, i, rho);
+    st128(w1, i, (u128)w - rho);
+}
+
+/* Field to ring, signed form of Pi_Ext^{q, 2^128} (App. C.3): the message m
+ * is centered in [-h, h], h = (q-1)/2.  P0 adds h to its share, so the two
+ * shares sum (mod q) to m + h in [0, q); the comparison yields the wrap bit
+ * w = [(t0 + h mod q) + t1 >= q], shared over Z_{2^128}. */
+void orc_f2r_wrap_sim(uint32_t n, uint64_t q, const uint64_t* t0, const uint64_t* t1, uint64_t seed,
+                      uint32_t nonce, uint64_t* w0, uint64_t* w1)
+{
+    const uint64_t h = (q - 1) / 2;
+    for (uint32_t i = 0; i < n; i++) {
+        uint64_t a = addmod(t0[i], h, q);
+        share_bit(a + t1[i] >= q, seed, i, nonce, w0, w1);
+    }
+}
+
+/* Local step of party b: U_b = t_b' - <w>_b q - [b = 0] h (mod 2^128) with
+ * t_0' = t_0 + h mod q and t_1' = t_1, so U_0 + U_1 = (t_0' + t_1 - w q) - h = m. */
+void orc_f2r_local(uint32_t party, uint32_t n, uint64_t q, const uint64_t* t, const uint64_t* wsh, uint64_t* U)
+{
+    const uint64_t h = (q - 1) / 2;
+    for (uint32_t i = 0; i < n; i++) {
+        u128 tp = party == 0 ? addmod(t[i], h, q) : t[i];
+        u128 u = tp - ld128(wsh, i) * (u128)q - (party == 0 ? (u128)h : 0);
+        st128(U, i, u);
+    }
+}
+
+/* Signed extension Pi_Ext^{2^l, 2^128} (SiRNN) with the same offset: P0 adds
+ * 2^(l-1) to its share, the comparison yields w = [x0' + x1 >= 2^l]. */
+void orc_ext_wrap_sim(uint32_t n, uint32_t l, const uint64_t* x0, const uint64_t* x1, uint64_t seed,
+                      uint32_t nonce, uint64_t* w0, uint64_t* w1)
+{
+    const uint64_t M = 1ull << l, mask = M - 1;
+    for (uint32_t i = 0; i < n; i++) {
+        uint64_t a = (x0[i] + (M >> 1)) & mask;
+        share_bit(a + (x1[i] & mask) >= M, seed, i, nonce, w0, w1);
+    }
+}
+
+/* X_b = x_b' - <w>_b 2^l - [b = 0] 2^(l-1) (mod 2^128), x_0' = x_0 + 2^(l-1) mod 2^l,
+ * x_1' = x_1: X_0 + X_1 is the signed value of x_0 + x_1 mod 2^l. */
+void orc_ext_local(uint32_t party, uint32_t n, uint32_t l, const uint64_t* x, const uint64_t* wsh, uint64_t* X)
+{
+    const uint64_t M = 1ull << l, mask = M - 1;
+    for (uint32_t i = 0; i < n; i++) {
+        u128 xp = party == 0 ? ((x[i] + (M >> 1)) & mask) : (x[i] & mask);
+        u128 v = xp - (ld128(wsh, i) << l) - (party == 0 ? (u128)(M >> 1) : 0);
+        st128(X, i, v);
+    }
+}
+
+/* Ring to field (App. C.3).  The paper's equation takes [m]_0 = M_0 mod q and
+ * [m]_1 = M_1 - 2^128 mod q, which is right when M_0 + M_1 = m + 2^128 as
+ * integers, i.e. when exactly one of the two shares, read as a signed integer,
+ * is negative.  Each party here reads its own share as a signed integer in
+ * [-2^127, 2^127) and reduces that mod q_i: the same residues in that case, and
+ * also right when both shares have one sign (two zero shares of a coefficient
+ * the FFT leaves structurally zero, or two truncated shares that happen to be
+ * small); it fails only when the signed shares overflow when added, with
+ * probability |m| / 2^128.  Output for every prime q_0..q_level. */
+void orc_r2f_local(const orc_params* p, uint32_t party, uint32_t n, const uint64_t* M, uint32_t level,
+                   uint64_t* out /* (level+1) x n */)
+{
+    (void)party;
+    for (uint32_t li = 0; li <= level; li++) {
+        const uint64_t q = p->prime[li];
+        const uint64_t two64 = (uint64_t)(((u128)1 << 64) % q);
+        const uint64_t two128 = mulmod(two64, two64, q);
+        for (uint32_t i = 0; i < n; i++) {
+            u128 v = ld128(M, i);
+            uint64_t r = (uint64_t)(v % q);
+            out[(size_t)li * n + i] = (v >> 127) ? submod(r, two128, q) : r;
+        }
+    }
+}
+
+/* CKKS -> MPC, what party b computes after masking and decryption (Alg. 1
+ * steps 3-4): t is its share of the coefficients of Encode(x) mod q_0 (P0: the
+ * decryption of the masked ciphertext, P1: minus the mask), wsh its share of
+ * the field-to-ring wrap bits.  Then
+ *   1. field to ring: U = shares of the centered coefficients m over Z_{2^128};
+ *   2. y_t = U_t / 2^(e-P) (local truncation; a shift left when e < P), where
+ *      the scale is Delta = mu 2^e with mu in [1, 2);
+ *   3. twist: c_t = (y_t + i y_{t+s}) * round(2^F zeta^t / mu) / 2^F;
+ *   4. the s-point DFT of the decoding (see orc_decode) as radix-2
+ *      decimation in time on bit-reversed input, every product by a root
+ *      round(2^F omega^k) truncated by F before the butterfly's sum and
+ *      difference;
+ *   5. slot j: the real part at k_j = (5^j - 1)/4, truncated from 2^-P to the
+ *      MPC scale 2^-sf and reduced mod 2^l.
+ * out receives the N/2 slot shares in Z_{2^l}. */
+int orc_c2m_local(const orc_params* p, uint32_t party, const uint64_t* t, const uint64_t* wsh, double scale,
+                  uint32_t l, uint32_t sf, uint64_t* out)
+{
+    const uint32_t N = p->N, s = N / 2, logs = p->logN - 1;
+    const uint32_t F = ORC_FX_F, P = ORC_FX_P;
+    if (l > 62 || sf > P || l < sf + 2 || !(scale > 0)) return -1;
+    int ex;
+    const double mu = 2.0 * frexp(scale, &ex); /* scale = mu 2^e, mu in [1, 2) */
+    const int e = ex - 1;
+    if (e - (int)P >= 64 || (int)P - e >= 64) return -1;
+    uint64_t* U = malloc(sizeof(uint64_t) * 2 * N);
+    cshare* A = malloc(sizeof(cshare) * s);
+    orc_f2r_local(party, N, p->prime[0], t, wsh, U);
+    const double c = 1.0 / mu;
+    for (uint32_t k = 0; k < s; k++) {
+        cshare y = {ld128(U, k), ld128(U, k + s)};
+        if (e >= (int)P) {
+            y.re = trunc_share(y.re, (uint32_t)(e - (int)P), party);
+            y.im = trunc_share(y.im, (uint32_t)(e - (int)P), party);
+        } else {
+            y.re <<= (uint32_t)((int)P - e);
+            y.im <<= (uint32_t)((int)P - e);
+        }
+        int64_t wr, wi;
+        fx_zeta(N, k, c, &wr, &wi);
+        cshare v = cmul_share(y, wr, wi);
+        A[bitrev(k, logs)] = (cshare){trunc_share(v.re, F, party), trunc_share(v.im, F, party)};
+    }
+    for (uint32_t len = 2; len <= s; len <<= 1) {
+        const uint32_t half = len / 2, step = s / len;
+        for (uint32_t i = 0; i < s; i += len) {
+            for (uint32_t j = 0; j < half; j++) {
+                int64_t wr, wi;
+                fx_zeta(N, 4 * j * step, 1.0, &wr, &wi);
+                cshare pr = cmul_share(A[i + j + half], wr, wi);
+                u128 vr = trunc_share(pr.re, F, party), vi = trunc_share(pr.im, F, party);
+                cshare u = A[i + j];
+                A[i + j] = (cshare){u.re + vr, u.im + vi};
+                A[i + j + half] = (cshare){u.re - vr, u.im - vi};
+            }
+        }
+    }
+    const uint64_t mask = (1ull << l) - 1;
+    uint64_t g = 1;
+    for (uint32_t j = 0; j < s; j++) {
+        out[j] = (uint64_t)trunc_share(A[(g - 1) / 4].re, P - sf, party) & mask;
+        g = (g * 5) % (2ull * N);
+    }
+    free(U);
+    free(A);
+    return 0;
+}
+
+/* MPC -> CKKS, what party b computes before encryption (Alg. 2 steps 1-2):
+ * x holds its shares of n <= N/2 slot values in Z_{2^l} at the MPC scale
+ * 2^-sf, wsh its share of the extension wrap bits.  Then
+ *   1. extension to Z_{2^128} (signed), and a shift up to resolution 2^-P;
+ *   2. V[k_j] = x_j (slots past n are 0), the inverse of the decoding's DFT
+ *      as radix-2 decimation in time on bit-reversed input, each butterfly
+ *      halved: (u 2^F +- v conj(omega^k)) / 2^(F+1), one truncation per output;
+ *      the result is the inverse DFT divided by s;
+ *   3. twist and scale: with Delta = mu 2^e, mu in [0.5, 1),
+ *      c_t = A_t round(2^F mu zeta^-t) / 2^(P+F-e) (a shift left when negative),
+ *      m_t = Re c_t and m_{t+s} = Im c_t, the shares of Encode(x) = round(Delta pi^-1(x));
+ *   4. ring to field for q_0..q_level.
+ * out receives (level+1) x N residues in coefficient form. */
+int orc_m2c_local(const orc_params* p, uint32_t party, const uint64_t* x, const uint64_t* wsh, uint32_t n,
+                  uint32_t level, double scale, uint32_t l, uint32_t sf, uint64_t* out)
+{
+    const uint32_t N = p->N, s = N / 2, logs = p->logN - 1;
+    const uint32_t F = ORC_FX_F, P = ORC_FX_P;
+    if (n > s || l > 62 || sf > P || l < sf + 2 || !(scale > 0) || level >= p->nQ) return -1;
+    int ex;
+    const double mu = frexp(scale, &ex); /* scale = mu 2^ex, mu in [0.5, 1) */
+    const int sh = (int)(P + F) - ex;
+    if (sh >= 64 || sh <= -64) return -1;
+    uint64_t* X = malloc(sizeof(uint64_t) * 2 * (n ? n : 1));
+    cshare* V = calloc(s, sizeof(cshare));
+    cshare* A = malloc(sizeof(cshare) * s);
+    uint64_t* M = malloc(sizeof(uint64_t) * 2 * N);
+    orc_ext_local(party, n, l, x, wsh, X);
+    uint64_t g = 1;
+    for (uint32_t j = 0; j < s; j++) {
+        if (j < n) V[(g - 1) / 4].re = ld128(X, j) << (P - sf);
+        g = (g * 5) % (2ull * N);
+    }
+    for (uint32_t k = 0; k < s; k++) A[bitrev(k, logs)] = V[k];
+    for (uint32_t len = 2; len <= s; len <<= 1) {
+        const uint32_t half = len / 2, step = s / len;
+        for (uint32_t i = 0; i < s; i += len) {
+            for (uint32_t j = 0; j < half; j++) {
+                int64_t wr, wi;
+                fx_zeta(N, 4 * j * step, 1.0, &wr, &wi);
+                cshare pr = cmul_share(A[i + j + half], wr, -wi);
+                u128 ur = A[i + j].re << F, ui = A[i + j].im << F;
+                A[i + j] = (cshare){trunc_share(ur + pr.re, F + 1, party), trunc_share(ui + pr.im, F + 1, party)};
+                A[i + j + half] = (cshare){trunc_share(ur - pr.re, F + 1, party), trunc_share(ui - pr.im, F + 1, party)};
+            }
+        }
+    }
+    for (uint32_t k = 0; k < s; k++) {
+        int64_t wr, wi;
+        fx_zeta(N, k, mu, &wr, &wi);
+        cshare c = cmul_share(A[k], wr, -wi);
+        if (sh >= 0) {
+            c.re = trunc_share(c.re, (uint32_t)sh, party);
+            c.im = trunc_share(c.im, (uint32_t)sh, party);
+        } else {
+            c.re <<= (uint32_t)(-sh);
+            c.im <<= (uint32_t)(-sh);
+        }
+        st128(M, k, c.re);
+        st128(M, k + s, c.im);
+    }
+    orc_r2f_local(p, party, N, M, level, out);
+    free(X);
+    free(V);
+    free(A);
+    free(M);
+    return 0;
 }

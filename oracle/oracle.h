@@ -1,8 +1,9 @@
 /*
  * oracle.h -- plain, slow CPU oracle of the RNS-CKKS linear path of BLB
  * (arXiv 2508.19525): ciphertext-plaintext and ciphertext-ciphertext matrix
- * products (Sec. 5), the CKKS primitives beneath them (Sec. 2.4, Eq. 2) and the
- * CKKS-to-MPC masking step (Alg. 1, Sec. 6.3).
+ * products (Sec. 5), the CKKS primitives beneath them (Sec. 2.4, Eq. 2), the
+ * CKKS-to-MPC masking step (Alg. 1, Sec. 6.3) and the local steps of both
+ * conversions between CKKS and additive shares (Alg. 1-2, App. C.3).
  *
  * TEST INFRASTRUCTURE ONLY.  Nothing in the product library links, includes or
  * calls this code; only the test suite, the smoke check and the CPU-baseline leg
@@ -22,7 +23,12 @@
 #define ORC_MAX_PRIMES 32
 
 /* Sampling purposes (the fourth Philox counter word). */
-enum { ORC_SECRET = 1, ORC_KEY_A = 2, ORC_KEY_E = 3, ORC_ENC_A = 4, ORC_ENC_E = 5, ORC_MASK = 6 };
+enum { ORC_SECRET = 1, ORC_KEY_A = 2, ORC_KEY_E = 3, ORC_ENC_A = 4, ORC_ENC_E = 5, ORC_MASK = 6, ORC_WRAP = 7 };
+
+/* Fixed point of the share FFTs of the conversions: roots carry ORC_FX_F
+ * fraction bits, FFT data a resolution of 2^-ORC_FX_P slot units. */
+#define ORC_FX_F 30
+#define ORC_FX_P 26
 
 typedef struct {
     uint32_t logN, N;
@@ -134,5 +140,21 @@ int orc_matmul_cc(const orc_params* p, const orc_galois_set* gk, const uint64_t*
                   uint32_t b1s2, uint64_t* C /* (L/Kc) x 2 x (level-3) x N */);
 void orc_he2mpc(const orc_params* p, const uint64_t* ct, uint32_t level, uint64_t seed,
                 uint32_t nonce, uint64_t* masked /* 2 x N */, uint64_t* p1_share /* N */);
+
+/* ---- local parts of the CKKS <-> MPC conversions (Alg. 1 steps 3-4, Alg. 2,
+ * App. C.3).  Extended-ring shares are 2 words (low, high) per element. ----- */
+void orc_share_trunc(uint32_t party, const uint64_t* x, uint64_t n, uint32_t k, uint64_t* out);
+void orc_f2r_wrap_sim(uint32_t n, uint64_t q, const uint64_t* t0, const uint64_t* t1, uint64_t seed,
+                      uint32_t nonce, uint64_t* w0, uint64_t* w1);
+void orc_f2r_local(uint32_t party, uint32_t n, uint64_t q, const uint64_t* t, const uint64_t* wsh, uint64_t* U);
+void orc_ext_wrap_sim(uint32_t n, uint32_t l, const uint64_t* x0, const uint64_t* x1, uint64_t seed,
+                      uint32_t nonce, uint64_t* w0, uint64_t* w1);
+void orc_ext_local(uint32_t party, uint32_t n, uint32_t l, const uint64_t* x, const uint64_t* wsh, uint64_t* X);
+void orc_r2f_local(const orc_params* p, uint32_t party, uint32_t n, const uint64_t* M, uint32_t level,
+                   uint64_t* out);
+int orc_c2m_local(const orc_params* p, uint32_t party, const uint64_t* t, const uint64_t* wsh, double scale,
+                  uint32_t l, uint32_t sf, uint64_t* out /* N/2, mod 2^l */);
+int orc_m2c_local(const orc_params* p, uint32_t party, const uint64_t* x, const uint64_t* wsh, uint32_t n,
+                  uint32_t level, double scale, uint32_t l, uint32_t sf, uint64_t* out /* (level+1) x N */);
 
 #endif
