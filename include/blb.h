@@ -273,6 +273,67 @@ int blb_matmul_cc(blb_ctx* ctx, const blb_keys* keys, blb_ct* const* A, blb_ct* 
 int blb_he2mpc(blb_ctx* ctx, const blb_keys* keys, const blb_ct* ct, uint64_t nonce,
                blb_ct** masked_for_p0, uint64_t* p1_share);
 
+/* ---- local steps of the conversions between CKKS and shares -----------------
+ * (Alg. 1 steps 3-4, Alg. 2, Sec. 6.3, App. C.3.)  Both parties' local
+ * computations; the interactive comparisons inside the ring/field extensions
+ * (Pi_Ext) are MPC protocols outside this library, and the *_wrap_sim calls
+ * stand in for their ideal functionality.
+ *
+ * Rings: the MPC ring Z_{2^l} with fixed-point scale 2^-sf (the paper uses
+ * l = 43, sf = 13; here sf <= 26 and sf + 2 <= l <= 62), values stored one per
+ * uint64 word; the extended ring Z_{2^128}, each element two words (low,
+ * high), arrays 16-byte aligned.  Shares are additive: x = x_0 + x_1 in the
+ * ring.  Probabilistic truncation (SecureML): party 0 shifts its share (read
+ * as a signed integer) right, party 1 takes the ceiling, so the sum is
+ * floor(m / 2^k) + u with Pr[u = 1] = (m mod 2^k) / 2^k; it is wrong (by about
+ * 2^(128-k)) only when the signed shares overflow, probability |m| / 2^128.
+ * Fixed point of the share FFTs: roots round(2^30 zeta^k), data at 2^-26.
+ *
+ * Every array may be host or device memory; `count` members are stored one
+ * after another.  Needs 2^12 <= N <= 2^17.  Errors: BLB_ERR_ARG for bad
+ * sizes, ring widths, party or alignment, BLB_ERR_LEVEL, BLB_ERR_OOM.
+ *
+ * blb_f2r_wrap_sim: ideal functionality of the comparison inside field to
+ * ring (signed Pi_Ext^{q_0, 2^128}).  t0, t1: count x N shares mod q_0 (party
+ * 0 and 1) of centered coefficients.  Outputs w0, w1 (count x N x 2 words):
+ * arithmetic shares of w = [(t0 + (q_0-1)/2 mod q_0) + t1 >= q_0], P0's share
+ * rho the 128-bit Philox draw (i, 0, nonces[k] low 32 bits, purpose 7) keyed
+ * by seed, P1's w - rho. */
+int blb_f2r_wrap_sim(blb_ctx* ctx, const uint64_t* t0, const uint64_t* t1, uint32_t count, uint64_t seed,
+                     const uint64_t* nonces, uint64_t* w0, uint64_t* w1);
+/* blb_c2m_local (Alg. 1 steps 3-4): party's share t (count x N residues mod
+ * q_0 in coefficient form: P0 the decryption of the masked ciphertext, P1 the
+ * share blb_he2mpc returned) and its wrap-bit shares wsh (count x N x 2 words)
+ * -> out (count x N/2 words mod 2^l): its share of the decoded slots at scale
+ * 2^-sf.  Steps: field to ring; division by Delta / 2^26 (Delta = `scale`,
+ * the ciphertext's scale) by truncation; the twist by zeta^t; the decoding FFT
+ * with every root product truncated; slot j = real part at k_j = (5^j - 1)/4,
+ * truncated to 2^-sf. */
+int blb_c2m_local(blb_ctx* ctx, uint32_t party, const uint64_t* t, const uint64_t* wsh, uint32_t count,
+                  double scale, uint32_t l, uint32_t sf, uint64_t* out);
+/* blb_ext_wrap_sim: ideal functionality of the comparison inside the signed
+ * extension Pi_Ext^{2^l, 2^128}: x0, x1 count x n shares mod 2^l, w0, w1 (count
+ * x n x 2 words) shares of w = [(x0 + 2^(l-1) mod 2^l) + x1 >= 2^l]; Philox as
+ * for blb_f2r_wrap_sim. */
+int blb_ext_wrap_sim(blb_ctx* ctx, const uint64_t* x0, const uint64_t* x1, uint32_t n, uint32_t count, uint32_t l,
+                     uint64_t seed, const uint64_t* nonces, uint64_t* w0, uint64_t* w1);
+/* blb_m2c_local (Alg. 2 steps 1-2): party's shares x (count x n <= N/2 slot
+ * values mod 2^l at scale 2^-sf; missing slots are 0) and wrap-bit shares wsh
+ * (count x n x 2 words) -> out (count x (level+1) x N residues, coefficient
+ * form): its share of Encode(x) = round(scale pi^-1(x)) mod q_0..q_level.
+ * Steps: extension; the inverse FFT with each butterfly halved by a
+ * truncation; the twist by scale zeta^-t; ring to field (each share read as a
+ * signed 128-bit integer, reduced mod q_i).  P0 then encrypts its share
+ * (blb_pt_import, blb_encrypt) and P1 adds its own (blb_pt_import,
+ * blb_add_plain): Alg. 2 steps 3-4. */
+int blb_m2c_local(blb_ctx* ctx, uint32_t party, const uint64_t* x, const uint64_t* wsh, uint32_t n, uint32_t count,
+                  uint32_t level, double scale, uint32_t l, uint32_t sf, uint64_t* out);
+/* Plaintext from (level+1) x N residues in coefficient form (host or device). */
+int blb_pt_import(blb_ctx* ctx, const uint64_t* coeffs, uint32_t level, double scale, blb_pt** out);
+/* a + b for a plaintext at the ciphertext's level or above (first polynomial
+ * only); the scales must match. */
+int blb_add_plain(blb_ctx* ctx, const blb_ct* a, const blb_pt* b, blb_ct** out);
+
 /* ---- batches of the calls above -----------------------------------------------
  * Each computes, for every member, exactly what the single call computes (same
  * Philox streams, bit-identical limbs), but runs each step once over the whole

@@ -96,6 +96,12 @@ SIGNATURES = {
     "blb_matmul_cc_plan": (ctypes.c_int, [_vp, _vp, _vp, _pp, _pp, _u32, _pp]),
     "blb_matmul_cc": (ctypes.c_int, [_vp, _vp, _pp, _pp, _u32, _u32, _u32, _u32, ctypes.POINTER(_CcSched), _pp]),
     "blb_he2mpc": (ctypes.c_int, [_vp, _vp, _vp, _u64, _pp, _vp]),
+    "blb_f2r_wrap_sim": (ctypes.c_int, [_vp, _vp, _vp, _u32, _u64, _vp, _vp, _vp]),
+    "blb_c2m_local": (ctypes.c_int, [_vp, _u32, _vp, _vp, _u32, _dbl, _u32, _u32, _vp]),
+    "blb_ext_wrap_sim": (ctypes.c_int, [_vp, _vp, _vp, _u32, _u32, _u32, _u64, _vp, _vp, _vp]),
+    "blb_m2c_local": (ctypes.c_int, [_vp, _u32, _vp, _vp, _u32, _u32, _u32, _dbl, _u32, _u32, _vp]),
+    "blb_pt_import": (ctypes.c_int, [_vp, _vp, _u32, _dbl, _pp]),
+    "blb_add_plain": (ctypes.c_int, [_vp, _vp, _vp, _pp]),
     "blb_ntt": (ctypes.c_int, [_vp, _vp, _u32, _vp, ctypes.c_int]),
     "blb_kernel_launches": (_u64, []),
     "blb_profile_enable": (ctypes.c_int, [_vp, ctypes.c_int]),
@@ -385,6 +391,67 @@ class Context:
 
     def add(self, a, b):
         return self._new(Ciphertext, lib().blb_add, a.h, b.h)
+
+    def add_plain(self, a, pt):
+        return self._new(Ciphertext, lib().blb_add_plain, a.h, pt.h)
+
+    def pt_import(self, coeffs, level, scale=None):
+        """Plaintext from (level+1, N) residues in coefficient form (host or device)."""
+        scale = self.scale if scale is None else scale
+        if isinstance(coeffs, np.ndarray):
+            coeffs = np.ascontiguousarray(coeffs, np.uint64)
+        return self._new(Plaintext, lib().blb_pt_import, _ptr(coeffs), level, _dbl(scale))
+
+    # -- local steps of the conversions (Alg. 1 steps 3-4, Alg. 2, App. C.3) --
+    # 128-bit shares are (..., 2) uint64 arrays (low, high); every array may be
+    # a numpy array or a torch tensor (host or device).
+    @staticmethod
+    def _count(a, per):
+        n = int(a.numel() if hasattr(a, "numel") else np.asarray(a).size)
+        if n % per:
+            raise ValueError(f"array of {n} words is not a whole number of {per}-word members")
+        return n // per
+
+    @staticmethod
+    def _c(a):
+        return np.ascontiguousarray(a, np.uint64) if isinstance(a, np.ndarray) else a
+
+    def f2r_wrap_sim(self, t0, t1, seed, nonces, w0=None, w1=None):
+        t0, t1 = self._c(t0), self._c(t1)
+        count = self._count(t0, self.N)
+        w0 = np.zeros((count, self.N, 2), np.uint64) if w0 is None else w0
+        w1 = np.zeros((count, self.N, 2), np.uint64) if w1 is None else w1
+        ns = np.ascontiguousarray(nonces, np.uint64).reshape(-1)
+        assert len(ns) == count
+        _check(lib().blb_f2r_wrap_sim(self.h, _ptr(t0), _ptr(t1), count, _u64(seed), ns.ctypes.data,
+                                      _ptr(w0), _ptr(w1)))
+        return w0, w1
+
+    def c2m_local(self, party, t, wsh, scale, l=43, sf=13, out=None):
+        t, wsh = self._c(t), self._c(wsh)
+        count = self._count(t, self.N)
+        out = np.zeros((count, self.N // 2), np.uint64) if out is None else out
+        _check(lib().blb_c2m_local(self.h, party, _ptr(t), _ptr(wsh), count, _dbl(scale), l, sf, _ptr(out)))
+        return out
+
+    def ext_wrap_sim(self, x0, x1, n, l, seed, nonces, w0=None, w1=None):
+        x0, x1 = self._c(x0), self._c(x1)
+        count = self._count(x0, n) if n else len(nonces)
+        w0 = np.zeros((count, n, 2), np.uint64) if w0 is None else w0
+        w1 = np.zeros((count, n, 2), np.uint64) if w1 is None else w1
+        ns = np.ascontiguousarray(nonces, np.uint64).reshape(-1)
+        assert len(ns) == count
+        _check(lib().blb_ext_wrap_sim(self.h, _ptr(x0), _ptr(x1), n, count, l, _u64(seed), ns.ctypes.data,
+                                      _ptr(w0), _ptr(w1)))
+        return w0, w1
+
+    def m2c_local(self, party, x, wsh, n, level, scale, l=43, sf=13, count=None, out=None):
+        x, wsh = self._c(x), self._c(wsh)
+        count = (self._count(x, n) if n else 1) if count is None else count
+        out = np.zeros((count, level + 1, self.N), np.uint64) if out is None else out
+        _check(lib().blb_m2c_local(self.h, party, _ptr(x), _ptr(wsh), n, count, level, _dbl(scale), l, sf,
+                                   _ptr(out)))
+        return out
 
     def mul_plain(self, a, pt):
         return self._new(Ciphertext, lib().blb_mul_plain, a.h, pt.h)

@@ -109,31 +109,6 @@ __global__ void k_dec_rows(uint64_t* __restrict__ H, const uint64_t* const* __re
 }
 
 // device scratch for one batch call, freed on every return path
-struct Scratch {
-    blb_ctx* c;
-    std::vector<std::pair<void*, size_t>> bufs;
-    explicit Scratch(blb_ctx* ctx) : c(ctx) {}
-    void* get(size_t bytes)
-    {
-        bytes = std::max<size_t>(bytes, 16);
-        void* p = dev_alloc(c, bytes);
-        if (p) bufs.push_back({p, bytes});
-        return p;
-    }
-    template <typename T>
-    T* upload(const std::vector<T>& v)
-    {
-        T* d = (T*)get(v.size() * sizeof(T));
-        if (d && !v.empty() &&
-            cudaMemcpyAsync(d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, c->stream) != cudaSuccess)
-            return nullptr;
-        return d;
-    }
-    ~Scratch()
-    {
-        for (auto& b : bufs) dev_free(c, b.first, b.second);
-    }
-};
 
 }  // namespace
 

@@ -16,6 +16,18 @@
 // library-internal helpers (declared in common.cuh)
 uint64_t* op_row(blb_ctx* c, size_t r) { return c->op_scratch() + r * c->N; }
 
+void* Scratch::get(size_t bytes)
+{
+    bytes = std::max<size_t>(bytes, 16);
+    void* p = dev_alloc(c, bytes);
+    if (p) bufs.push_back({p, bytes});
+    return p;
+}
+Scratch::~Scratch()
+{
+    for (auto& b : bufs) dev_free(c, b.first, b.second);
+}
+
 int copy_in(blb_ctx* c, void* dst, const void* src, size_t bytes)
 {
     BLB_CUDA(cudaMemcpyAsync(dst, src, bytes, is_device_ptr(src) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
@@ -283,6 +295,29 @@ extern "C" int blb_pt_export(blb_ctx* c, const blb_pt* pt, uint64_t* out)
     return copy_out(c, out, tmp, pt->bytes);
 }
 
+extern "C" int blb_pt_import(blb_ctx* c, const uint64_t* coeffs, uint32_t level, double scale, blb_pt** out)
+{
+    if (!c || !coeffs || !out) return blb_fail(BLB_ERR_ARG, "null argument");
+    if (level >= c->nQ) return blb_fail(BLB_ERR_LEVEL, "level out of range");
+    if (!(scale > 0)) return blb_fail(BLB_ERR_ARG, "scale must be positive");
+    blb_pt* pt = new blb_pt();
+    pt->ctx = c;
+    ctx_retain(c);
+    pt->level = level;
+    pt->scale = scale;
+    pt->bytes = (size_t)(level + 1) * c->N * 8;
+    pt->d = (uint64_t*)dev_alloc(c, pt->bytes);
+    int rc = pt->d ? BLB_OK : blb_fail(BLB_ERR_OOM, "plaintext allocation failed");
+    if (!rc) rc = copy_in(c, pt->d, coeffs, pt->bytes);
+    if (!rc) rc = ntt_forward(c, pt->d, level + 1, c->qmap(level + 1));
+    if (rc) {
+        blb_pt_free(pt);
+        return rc;
+    }
+    *out = pt;
+    return BLB_OK;
+}
+
 // ===========================================================================
 // ciphertexts
 // ===========================================================================
@@ -433,6 +468,29 @@ extern "C" int blb_add(blb_ctx* c, const blb_ct* a, const blb_ct* b, blb_ct** ou
     blb_ct* r;
     BLB_TRY(new_ct(c, a->level, a->npolys, a->scale, &r));
     int rc = launch_add_rows(c, r->d, a->d, b->d, a->npolys * (a->level + 1), c->qmap(a->level + 1));
+    if (rc) {
+        blb_ct_free(r);
+        return rc;
+    }
+    *out = r;
+    return BLB_OK;
+}
+
+extern "C" int blb_add_plain(blb_ctx* c, const blb_ct* a, const blb_pt* p, blb_ct** out)
+{
+    if (!c || !a || !p || !out) return blb_fail(BLB_ERR_ARG, "null argument");
+    if (p->level < a->level) return blb_fail(BLB_ERR_LEVEL, "plaintext below the ciphertext's level");
+    if (!same_scale(a->scale, p->scale)) return blb_fail(BLB_ERR_SCALE, "operands have different scales");
+    const uint32_t n = a->level + 1;
+    blb_ct* r;
+    BLB_TRY(new_ct(c, a->level, a->npolys, a->scale, &r));
+    const size_t poly = (size_t)n * c->N;
+    int rc = launch_add_rows(c, r->d, a->d, p->d, n, c->qmap(n));
+    if (!rc && a->npolys > 1)
+        rc = cudaMemcpyAsync(r->d + poly, a->d + poly, (a->npolys - 1) * poly * 8, cudaMemcpyDeviceToDevice,
+                             c->stream) == cudaSuccess
+                 ? BLB_OK
+                 : blb_fail(BLB_ERR_CUDA, "copy of the remaining polynomials failed");
     if (rc) {
         blb_ct_free(r);
         return rc;

@@ -113,7 +113,7 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k)
 }
 
 enum { PURPOSE_SECRET = 1, PURPOSE_KEY_A = 2, PURPOSE_KEY_E = 3, PURPOSE_ENC_A = 4, PURPOSE_ENC_E = 5,
-       PURPOSE_MASK = 6 };
+       PURPOSE_MASK = 6, PURPOSE_WRAP = 7 };
 
 // one Philox draw with counter (coefficient i, sub-index j, object, purpose)
 __device__ __forceinline__ uint4 philox_draw(uint64_t seed, uint32_t i, uint32_t j, uint32_t obj, uint32_t purpose)
@@ -161,6 +161,16 @@ struct blb_ctx {
     uint32_t* d_kperm = nullptr;      // [N/2]: k_j = (5^j mod 2N - 1)/4
     int* d_flag = nullptr;            // device status word (encoding overflow)
     uint32_t* d_status = nullptr;     // set by a kernel whose bounded wait expired
+    // conversions between CKKS and shares (built on first use): fixed-point
+    // roots zeta^k (k < N), the inverse slot permutation, and twist tables
+    // round(2^30 c zeta^t) (t < N/2) for the last multipliers c used
+    int2* d_fx_root = nullptr;
+    uint32_t* d_kinv = nullptr;
+    struct FxTwist {
+        double mul;
+        int2* d;
+    };
+    std::vector<FxTwist> fx_twist;
     // host-side constants
     std::vector<uint64_t> P_mod_q;              // [nQ]  P mod q_i
     std::vector<uint64_t> P_inv_mod_q;          // [nQ]  P^-1 mod q_i
@@ -247,6 +257,24 @@ struct blb_cp_plan {
     std::vector<uint8_t> nb;    // bytes per word of each limb
     std::vector<uint64_t> off;  // byte offset of each limb's region in d_ptb
     size_t bytes;
+};
+
+// stream-ordered temporary device buffers of one call, freed at scope exit
+struct Scratch {
+    blb_ctx* c;
+    std::vector<std::pair<void*, size_t>> bufs;
+    explicit Scratch(blb_ctx* ctx) : c(ctx) {}
+    void* get(size_t bytes);
+    template <typename T>
+    T* upload(const std::vector<T>& v)
+    {
+        T* d = (T*)get(v.size() * sizeof(T));
+        if (d && !v.empty() &&
+            cudaMemcpyAsync(d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, c->stream) != cudaSuccess)
+            return nullptr;
+        return d;
+    }
+    ~Scratch();
 };
 
 // RAII timer around a launch site (no-op unless the context is profiling)

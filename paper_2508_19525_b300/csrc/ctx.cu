@@ -549,6 +549,9 @@ static void ctx_destroy(blb_ctx* c)
     dev_free(c, c->d_kperm, (size_t)c->N / 2 * 4);
     dev_free(c, c->d_flag, sizeof(int));
     dev_free(c, c->d_status, sizeof(uint32_t));
+    dev_free(c, c->d_fx_root, (size_t)c->N * sizeof(int2));
+    dev_free(c, c->d_kinv, (size_t)c->N / 2 * 4);
+    for (auto& t : c->fx_twist) dev_free(c, t.d, (size_t)c->N / 2 * sizeof(int2));
     dev_free(c, c->d_modup_all, c->h_modup.size() * sizeof(ConvTable));
     dev_free(c, c->d_moddown, sizeof(ConvTable));
     dev_free(c, c->scratch, c->scratch_words * 8);
