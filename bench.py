@@ -336,6 +336,60 @@ def attention_cc(steps):
             "max_abs_err_vs_fp64": err, "rotation_keys": rot}
 
 
+def conversion_bench(w, reps):
+    """The parties' local steps of both conversions (Alg. 1 steps 3-4, Alg. 2
+    steps 1-2, App. C.3) for one BERT-base step: C2M of the 18 masked outputs
+    (field to ring + decoding of shares, both parties) and M2C of 6 slot-share
+    vectors back to the next layer's input level (extension + encoding of
+    shares + ring to field, both parties), MPC ring l = 43 at scale 2^-13.  The
+    wrap-bit comparisons (MPC protocols) run through their simulated ideal
+    functionality and are timed apart."""
+    torch, ctx = w.torch, w.ctx
+    n_out, n_in, N, s = w.n_out, w.n_in, w.N, w.N // 2
+    dev = w.p0_dev.device
+    u64 = dict(dtype=torch.uint64, device=dev)
+    W0, W1 = torch.zeros((n_out, N, 2), **u64), torch.zeros((n_out, N, 2), **u64)
+    Y0, Y1 = torch.zeros((n_out, s), **u64), torch.zeros((n_out, s), **u64)
+    V0, V1 = torch.zeros((n_in, s, 2), **u64), torch.zeros((n_in, s, 2), **u64)
+    M0 = torch.zeros((n_in, LEVEL + 1, N), **u64)
+    M1 = torch.zeros_like(M0)
+    scale = ctx.scale
+    w.step()
+    ids = list(range(n_out))
+
+    def sim_c2m():
+        ctx.f2r_wrap_sim(w.p0_dev, w.p1_dev, 7, ids, W0, W1)
+
+    def c2m():
+        ctx.c2m_local(0, w.p0_dev, W0, scale, 43, 13, out=Y0)
+        ctx.c2m_local(1, w.p1_dev, W1, scale, 43, 13, out=Y1)
+
+    def sim_m2c():
+        ctx.ext_wrap_sim(Y0[:n_in], Y1[:n_in], s, 43, 7, ids[:n_in], V0, V1)
+
+    def m2c():
+        ctx.m2c_local(0, Y0[:n_in], V0, s, LEVEL, scale, 43, 13, out=M0)
+        ctx.m2c_local(1, Y1[:n_in], V1, s, LEVEL, scale, 43, 13, out=M1)
+
+    for f in (sim_c2m, c2m, sim_m2c, m2c):
+        f()
+    ctx.sync()
+    ctx.profile(True)
+    t = {name: timed_fn(w, f, reps, 1) / reps * 1e3
+         for name, f in (("f2r_wrap_sim", sim_c2m), ("c2m", c2m), ("ext_wrap_sim", sim_m2c), ("m2c", m2c))}
+    sites = {site: ctx.profile_read(site) for site in ("c2m", "m2c")}
+    ctx.profile(False)
+    out = {"workload": f"C2M of {n_out} masked outputs (N=2^15, q_0 60 bits) and M2C of {n_in} slot vectors "
+                       f"back to level {LEVEL}, both parties, l=43, sf=13, extended ring Z_2^128",
+           "ms": {k: round(v, 4) for k, v in t.items()}, "sites": {}}
+    for site, (ms, cnt, nbytes) in sites.items():
+        if cnt and ms > 0:
+            out["sites"][site] = {"ms_per_call": round(ms / cnt, 4), "calls": cnt,
+                                  "algorithmic_bytes_per_call": nbytes // cnt,
+                                  "achieved_gbs": round(nbytes / (ms / 1e3) / 1e9, 1)}
+    return out
+
+
 def serving_bench(n_requests=64, rate=20.0, sat_rate=400.0, budget_gb=24, max_batch=8):
     """Continuous batching of encrypted linear-layer requests (one client and key
     set per request) against one request per launch; BERT-base-shaped and
@@ -458,6 +512,7 @@ def run_blb(args):
         bval, _ = aggregate(bsec, TOKENS_PER_STEP * args.batch * bsteps, world)
         batched = {"sequences_per_step": args.batch, "value": round(bval, 3), "unit": UNIT,
                    "ms_per_step": round(bsec * 1e3 / bsteps, 3), "speedup_vs_plain": round(bval / value, 3)}
+    conv = conversion_bench(w, 20) if args.conversion else None
     attn = attention_cc(max(1, min(5, args.steps // 4))) if args.attention and world == 1 else None
     serving = serving_bench() if args.serving and world == 1 else None
     if rank != 0:
@@ -504,6 +559,8 @@ def run_blb(args):
         "batched": batched,
         "attention_cc": attn,
         "serving": serving,
+        "conversion": dict(conv, sites={k: dict(v, frac_of_hbm=round(v["achieved_gbs"] / hbm, 4), peak_kind=peak_note)
+                                        for k, v in conv["sites"].items()}) if conv else None,
         "counts_per_step": w.counts(),
         "weights": {"plaintext_bytes": w.plan_bytes, "encode_s": round(w.plan_s, 2), "timed": False},
     }
@@ -642,6 +699,34 @@ def ncu_step():
     print(json.dumps({"ncu_step": WORKLOAD}))
 
 
+def ncu_conv(count=18):
+    """Profiling case of the conversion kernels: C2M and M2C of `count`
+    random share vectors at N = 2^15 (the BERT-base matmul_cp parameters),
+    both parties, once."""
+    import torch
+    from paper_2508_19525_b300 import blb
+    from paper_2508_19525_b300 import workloads as wl
+    prm = wl.BERT_CP
+    ctx = blb.Context(prm.logN, prm.q_bits, prm.p_bits, prm.dnum, prm.scale)
+    N, s, q = ctx.N, ctx.N // 2, ctx.primes[0]
+    g = torch.Generator(device="cuda").manual_seed(1)
+    t0 = torch.randint(0, q, (count, N), generator=g, device="cuda", dtype=torch.int64)
+    t1 = torch.randint(0, q, (count, N), generator=g, device="cuda", dtype=torch.int64)
+    u64 = dict(dtype=torch.int64, device="cuda")
+    W0, W1 = torch.zeros((count, N, 2), **u64), torch.zeros((count, N, 2), **u64)
+    Y0, Y1 = torch.zeros((count, s), **u64), torch.zeros((count, s), **u64)
+    ctx.f2r_wrap_sim(t0, t1, 3, list(range(count)), W0, W1)
+    ctx.c2m_local(0, t0, W0, prm.scale, 43, 13, out=Y0)
+    ctx.c2m_local(1, t1, W1, prm.scale, 43, 13, out=Y1)
+    V0, V1 = torch.zeros((count, s, 2), **u64), torch.zeros((count, s, 2), **u64)
+    M = torch.zeros((count, ctx.nQ, N), **u64)
+    ctx.ext_wrap_sim(Y0, Y1, s, 43, 3, list(range(count)), V0, V1)
+    ctx.m2c_local(0, Y0, V0, s, ctx.nQ - 1, prm.scale, 43, 13, out=M)
+    ctx.m2c_local(1, Y1, V1, s, ctx.nQ - 1, prm.scale, 43, 13, out=M)
+    ctx.sync()
+    print(json.dumps({"ncu_conv": count}))
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -654,9 +739,12 @@ def main():
     ap.add_argument("--ncu-case", action="store_true", help="run the small profiling case and exit")
     ap.add_argument("--ncu-seqs", type=int, default=1, help="sequences in the profiling case")
     ap.add_argument("--ncu-step", action="store_true", help="run one profiled BERT-base step and exit")
+    ap.add_argument("--ncu-conv", action="store_true", help="run the conversion profiling case and exit")
     ap.add_argument("--batch", type=int, default=8, help="sequences per batched step (1 = skip)")
     ap.add_argument("--no-attention", dest="attention", action="store_false",
                     help="skip the matmul_cc attention measurement")
+    ap.add_argument("--no-conversion", dest="conversion", action="store_false",
+                    help="skip the CKKS <-> MPC conversion measurement")
     ap.add_argument("--no-serving", dest="serving", action="store_false",
                     help="skip the continuous-batching serving measurement")
     args = ap.parse_args()
@@ -664,6 +752,8 @@ def main():
         return ncu_case(args.ncu_seqs)
     if args.ncu_step:
         return ncu_step()
+    if args.ncu_conv:
+        return ncu_conv()
     args.cpu_sample = (args.cpu_rotations, args.cpu_products)
     if args.impl == "reference":
         run_reference(args)

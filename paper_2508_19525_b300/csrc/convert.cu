@@ -31,7 +31,7 @@ namespace {
 
 constexpr int FX_F = 30;    // fraction bits of the roots
 constexpr int FX_P = 26;    // resolution 2^-26 of the FFT data
-constexpr int FX_T = 256;   // threads per CTA
+constexpr int FX_T = 512;   // threads per CTA: one butterfly each per stage
 constexpr int FX_E = 1024;  // complex elements per CTA tile
 
 struct u128 {
@@ -69,7 +69,12 @@ __device__ __forceinline__ u128 sar(u128 a, int k)
 }
 // probabilistic truncation (SecureML): party 0 floor(x / 2^k), party 1
 // ceil(x / 2^k), the share read as a signed 128-bit integer
-__device__ __forceinline__ u128 trunc(u128 a, int k, bool p1) { return p1 ? neg(sar(neg(a), k)) : sar(a, k); }
+template <bool P1>
+__device__ __forceinline__ u128 trunc(u128 a, int k)
+{
+    if (P1) return neg(sar(neg(a), k));
+    return sar(a, k);
+}
 
 // a * w mod 2^128 for |w| < 2^31, from 32 x 32 -> 64-bit products
 __device__ __forceinline__ u128 mul_s(u128 a, int32_t w)
@@ -95,82 +100,85 @@ __device__ __forceinline__ u128 ld2(const uint64_t* p, size_t i)
 __device__ __forceinline__ uint32_t brev(uint32_t x, int bits) { return __brev(x) >> (32 - bits); }
 
 // field to ring, party's local step: U = t' - <w> q - [P0] h, t' = t + h mod q for P0
-__device__ __forceinline__ u128 f2r(uint64_t t, u128 ws, uint64_t q, uint64_t h, bool p1)
+template <bool P1>
+__device__ __forceinline__ u128 f2r(uint64_t t, u128 ws, uint64_t q, uint64_t h)
 {
-    const uint64_t tp = p1 ? t : add_mod(t, h, q);
+    const uint64_t tp = P1 ? t : add_mod(t, h, q);
     const u128 wq{ws.lo * q, __umul64hi(ws.lo, q) + ws.hi * q};
     const u128 u = sub(u128{tp, 0}, wq);
-    return p1 ? u : sub(u, u128{h, 0});
+    return P1 ? u : sub(u, u128{h, 0});
 }
 // signed extension, party's local step: X = x' - <w> 2^l - [P0] 2^(l-1)
-__device__ __forceinline__ u128 ext(uint64_t x, u128 ws, int l, bool p1)
+template <bool P1>
+__device__ __forceinline__ u128 ext(uint64_t x, u128 ws, int l)
 {
     const uint64_t M = 1ull << l, mask = M - 1, half = M >> 1;
-    const uint64_t xp = p1 ? (x & mask) : ((x + half) & mask);
+    const uint64_t xp = P1 ? (x & mask) : ((x + half) & mask);
     const u128 v = sub(u128{xp, 0}, shl(ws, l));
-    return p1 ? v : sub(v, u128{half, 0});
+    return P1 ? v : sub(v, u128{half, 0});
 }
 
 // decoding butterfly: v' = trunc(v w, F); (u, v) <- (u + v', u - v')
-__device__ __forceinline__ void fwd_bfly(c128& u, c128& v, int2 w, bool p1)
-{
-    const c128 pr = cmul(v, w);
-    const u128 vr = trunc(pr.re, FX_F, p1), vi = trunc(pr.im, FX_F, p1);
-    const c128 a = u;
-    u = c128{add(a.re, vr), add(a.im, vi)};
-    v = c128{sub(a.re, vr), sub(a.im, vi)};
-}
 // encoding butterfly: p = v conj(w); (u, v) <- trunc(u 2^F +- p, F + 1)
-__device__ __forceinline__ void inv_bfly(c128& u, c128& v, int2 w, bool p1)
+template <bool INV, bool P1>
+__device__ __forceinline__ void bfly(c128& u, c128& v, int2 w)
 {
-    const c128 pr = cmul(v, make_int2(w.x, -w.y));
-    const u128 ur = shl(u.re, FX_F), ui = shl(u.im, FX_F);
-    u = c128{trunc(add(ur, pr.re), FX_F + 1, p1), trunc(add(ui, pr.im), FX_F + 1, p1)};
-    v = c128{trunc(sub(ur, pr.re), FX_F + 1, p1), trunc(sub(ui, pr.im), FX_F + 1, p1)};
+    if (!INV) {
+        const c128 pr = cmul(v, w);
+        const u128 vr = trunc<P1>(pr.re, FX_F), vi = trunc<P1>(pr.im, FX_F);
+        const c128 a = u;
+        u = c128{add(a.re, vr), add(a.im, vi)};
+        v = c128{sub(a.re, vr), sub(a.im, vi)};
+    } else {
+        const c128 pr = cmul(v, make_int2(w.x, -w.y));
+        const u128 ur = shl(u.re, FX_F), ui = shl(u.im, FX_F);
+        u = c128{trunc<P1>(add(ur, pr.re), FX_F + 1), trunc<P1>(add(ui, pr.im), FX_F + 1)};
+        v = c128{trunc<P1>(sub(ur, pr.re), FX_F + 1), trunc<P1>(sub(ui, pr.im), FX_F + 1)};
+    }
 }
 
-// stages 1..H1 on the CTA's 1024 >> H1 contiguous blocks of 2^H1 elements
-template <int LOGS, bool INV>
-__device__ __forceinline__ void stages_pass1(c128* sm, const int2* __restrict__ root, bool p1)
+// stages 1..H1 on the CTA's 1024 >> H1 contiguous blocks of 2^H1 elements,
+// thread b owning butterfly b of every stage; the next stage's root is
+// fetched before the current stage's butterfly so its latency overlaps it
+template <int LOGS, bool INV, bool P1>
+__device__ __forceinline__ void stages_pass1(c128* sm, const int2* __restrict__ root)
 {
     constexpr int H1 = (LOGS + 1) / 2;
-#pragma unroll 1
+    const int b = threadIdx.x;
+    const int col = b >> (H1 - 1), bb = b & ((1 << (H1 - 1)) - 1);
+    c128* base = sm + (col << H1);
+    int2 w = root[0];
+#pragma unroll
     for (int sg = 1; sg <= H1; sg++) {
         const int half = 1 << (sg - 1);
-        for (int b = threadIdx.x; b < FX_E / 2; b += FX_T) {
-            const int col = b >> (H1 - 1), bb = b & ((1 << (H1 - 1)) - 1);
-            const int j = bb & (half - 1), i0 = ((bb >> (sg - 1)) << sg) + j;
-            c128* base = sm + (col << H1);
-            const int2 w = root[j << (LOGS - sg + 2)];
-            if (INV)
-                inv_bfly(base[i0], base[i0 + half], w, p1);
-            else
-                fwd_bfly(base[i0], base[i0 + half], w, p1);
-        }
+        const int j = bb & (half - 1), i0 = ((bb >> (sg - 1)) << sg) + j;
+        int2 wn = w;
+        if (sg < H1) wn = root[(bb & (2 * half - 1)) << (LOGS - sg + 1)];
+        bfly<INV, P1>(base[i0], base[i0 + half], w);
+        w = wn;
         __syncthreads();
     }
 }
 
 // stages H1+1..LOGS on the CTA's 1024 >> H2 interleaved sub-problems r0.. (element
 // i = r + 2^H1 b', stored at sm[(r - r0) 2^H2 + b'])
-template <int LOGS, bool INV>
-__device__ __forceinline__ void stages_pass2(c128* sm, const int2* __restrict__ root, uint32_t r0, bool p1)
+template <int LOGS, bool INV, bool P1>
+__device__ __forceinline__ void stages_pass2(c128* sm, const int2* __restrict__ root, uint32_t r0)
 {
     constexpr int H1 = (LOGS + 1) / 2, H2 = LOGS - H1;
-#pragma unroll 1
+    const int b = threadIdx.x;
+    const int row = b >> (H2 - 1), bb = b & ((1 << (H2 - 1)) - 1);
+    c128* base = sm + (row << H2);
+    const uint32_t r = r0 + row;
+    int2 w = root[r << (LOGS - H1 + 1)];
+#pragma unroll
     for (int sg = H1 + 1; sg <= LOGS; sg++) {
         const int sl = sg - H1, half = 1 << (sl - 1);
-        for (int b = threadIdx.x; b < FX_E / 2; b += FX_T) {
-            const int row = b >> (H2 - 1), bb = b & ((1 << (H2 - 1)) - 1);
-            const int jj = bb & (half - 1), i0 = ((bb >> (sl - 1)) << sl) + jj;
-            const uint32_t j = r0 + row + ((uint32_t)jj << H1);
-            c128* base = sm + (row << H2);
-            const int2 w = root[j << (LOGS - sg + 2)];
-            if (INV)
-                inv_bfly(base[i0], base[i0 + half], w, p1);
-            else
-                fwd_bfly(base[i0], base[i0 + half], w, p1);
-        }
+        const int jj = bb & (half - 1), i0 = ((bb >> (sl - 1)) << sl) + jj;
+        int2 wn = w;
+        if (sg < LOGS) wn = root[(r + ((uint32_t)(bb & (2 * half - 1)) << H1)) << (LOGS - sg + 1)];
+        bfly<INV, P1>(base[i0], base[i0 + half], w);
+        w = wn;
         __syncthreads();
     }
 }
@@ -178,15 +186,14 @@ __device__ __forceinline__ void stages_pass2(c128* sm, const int2* __restrict__ 
 // CKKS -> MPC pass 1: field to ring, scaling to 2^-P, twist, bit reversal and
 // the first H1 stages.  T: count x N residues mod q_0; W: count x N wrap-bit
 // shares (2 words each); A: count x s complex shares in bit-reversed order.
-template <int LOGS>
+template <int LOGS, bool P1>
 __global__ void __launch_bounds__(FX_T) k_c2m_pass1(const uint64_t* __restrict__ T, const uint64_t* __restrict__ W,
                                                     c128* __restrict__ A, const int2* __restrict__ root,
-                                                    const int2* __restrict__ twist, uint64_t q, int sh_in, uint32_t party)
+                                                    const int2* __restrict__ twist, uint64_t q, int sh_in)
 {
     constexpr int H1 = (LOGS + 1) / 2, H2 = LOGS - H1, C = FX_E >> H1;
     constexpr uint32_t S = 1u << LOGS;
     __shared__ c128 sm[FX_E];
-    const bool p1 = party != 0;
     const uint32_t c0 = blockIdx.x * C;
     const size_t mem = blockIdx.y;
     const uint64_t* Tm = T + mem * 2 * S;
@@ -195,19 +202,19 @@ __global__ void __launch_bounds__(FX_T) k_c2m_pass1(const uint64_t* __restrict__
     for (int e = threadIdx.x; e < FX_E; e += FX_T) {
         const uint32_t co = e % C, rp = e / C;
         const uint32_t t = (rp << H2) + c0 + co;
-        u128 y0 = f2r(Tm[t], ld2(Wm, t), q, h, p1), y1 = f2r(Tm[t + S], ld2(Wm, t + S), q, h, p1);
+        u128 y0 = f2r<P1>(Tm[t], ld2(Wm, t), q, h), y1 = f2r<P1>(Tm[t + S], ld2(Wm, t + S), q, h);
         if (sh_in >= 0) {
-            y0 = trunc(y0, sh_in, p1);
-            y1 = trunc(y1, sh_in, p1);
+            y0 = trunc<P1>(y0, sh_in);
+            y1 = trunc<P1>(y1, sh_in);
         } else {
             y0 = shl(y0, -sh_in);
             y1 = shl(y1, -sh_in);
         }
         const c128 v = cmul(c128{y0, y1}, twist[t]);
-        sm[(co << H1) + brev(rp, H1)] = c128{trunc(v.re, FX_F, p1), trunc(v.im, FX_F, p1)};
+        sm[(co << H1) + brev(rp, H1)] = c128{trunc<P1>(v.re, FX_F), trunc<P1>(v.im, FX_F)};
     }
     __syncthreads();
-    stages_pass1<LOGS, false>(sm, root, p1);
+    stages_pass1<LOGS, false, P1>(sm, root);
     c128* Am = A + mem * S;
     for (int e = threadIdx.x; e < FX_E; e += FX_T) {
         const uint32_t col = e >> H1, r = e & ((1 << H1) - 1);
@@ -217,15 +224,14 @@ __global__ void __launch_bounds__(FX_T) k_c2m_pass1(const uint64_t* __restrict__
 
 // CKKS -> MPC pass 2: the remaining stages, then slot j = Re A[k_j] truncated
 // to 2^-sf and reduced mod 2^l.  out: count x s words.
-template <int LOGS>
+template <int LOGS, bool P1>
 __global__ void __launch_bounds__(FX_T) k_c2m_pass2(const c128* __restrict__ A, uint64_t* __restrict__ out,
                                                     const int2* __restrict__ root, const uint32_t* __restrict__ kinv,
-                                                    int sh_out, uint64_t mask, uint32_t party)
+                                                    int sh_out, uint64_t mask)
 {
     constexpr int H1 = (LOGS + 1) / 2, H2 = LOGS - H1, C2 = FX_E >> H2;
     constexpr uint32_t S = 1u << LOGS;
     __shared__ c128 sm[FX_E];
-    const bool p1 = party != 0;
     const uint32_t r0 = blockIdx.x * C2;
     const size_t mem = blockIdx.y;
     const c128* Am = A + mem * S;
@@ -234,28 +240,26 @@ __global__ void __launch_bounds__(FX_T) k_c2m_pass2(const c128* __restrict__ A, 
         sm[(ro << H2) + bp] = Am[r0 + ro + (bp << H1)];
     }
     __syncthreads();
-    stages_pass2<LOGS, false>(sm, root, r0, p1);
+    stages_pass2<LOGS, false, P1>(sm, root, r0);
     uint64_t* om = out + mem * S;
     for (int e = threadIdx.x; e < FX_E; e += FX_T) {
         const uint32_t ro = e % C2, bp = e / C2;
         const uint32_t i = r0 + ro + (bp << H1);
-        om[kinv[i]] = trunc(sm[(ro << H2) + bp].re, sh_out, p1).lo & mask;
+        om[kinv[i]] = trunc<P1>(sm[(ro << H2) + bp].re, sh_out).lo & mask;
     }
 }
 
 // MPC -> CKKS pass 1: extension, shift to 2^-P, placement V[k_j] = x_j in
 // bit-reversed order, the first H1 halved inverse stages.  X: count x n words;
 // W: count x n wrap-bit shares.
-template <int LOGS>
+template <int LOGS, bool P1>
 __global__ void __launch_bounds__(FX_T) k_m2c_pass1(const uint64_t* __restrict__ X, const uint64_t* __restrict__ W,
                                                     c128* __restrict__ A, const int2* __restrict__ root,
-                                                    const uint32_t* __restrict__ kinv, uint32_t n, int l, int sh_up,
-                                                    uint32_t party)
+                                                    const uint32_t* __restrict__ kinv, uint32_t n, int l, int sh_up)
 {
     constexpr int H1 = (LOGS + 1) / 2, H2 = LOGS - H1, C = FX_E >> H1;
     constexpr uint32_t S = 1u << LOGS;
     __shared__ c128 sm[FX_E];
-    const bool p1 = party != 0;
     const uint32_t c0 = blockIdx.x * C;
     const size_t mem = blockIdx.y;
     const uint64_t* Xm = X + mem * n;
@@ -265,11 +269,11 @@ __global__ void __launch_bounds__(FX_T) k_m2c_pass1(const uint64_t* __restrict__
         const uint32_t k = (rp << H2) + c0 + co;
         const uint32_t j = kinv[k];
         u128 v{0, 0};
-        if (j < n) v = shl(ext(Xm[j], ld2(Wm, j), l, p1), sh_up);
+        if (j < n) v = shl(ext<P1>(Xm[j], ld2(Wm, j), l), sh_up);
         sm[(co << H1) + brev(rp, H1)] = c128{v, u128{0, 0}};
     }
     __syncthreads();
-    stages_pass1<LOGS, true>(sm, root, p1);
+    stages_pass1<LOGS, true, P1>(sm, root);
     c128* Am = A + mem * S;
     for (int e = threadIdx.x; e < FX_E; e += FX_T) {
         const uint32_t col = e >> H1, r = e & ((1 << H1) - 1);
@@ -290,16 +294,14 @@ __device__ __forceinline__ uint64_t r2f(u128 v, uint64_t q, uint64_t b0, uint64_
 
 // MPC -> CKKS pass 2: the remaining stages, the twist and scaling to Delta,
 // then ring to field for every prime of the level.  out: count x nl x N words.
-template <int LOGS>
+template <int LOGS, bool P1>
 __global__ void __launch_bounds__(FX_T) k_m2c_pass2(const c128* __restrict__ A, uint64_t* __restrict__ out,
                                                     const int2* __restrict__ root, const int2* __restrict__ twist,
-                                                    const __grid_constant__ R2FConsts K, uint32_t nl, int sh,
-                                                    uint32_t party)
+                                                    const __grid_constant__ R2FConsts K, uint32_t nl, int sh)
 {
     constexpr int H1 = (LOGS + 1) / 2, H2 = LOGS - H1, C2 = FX_E >> H2;
     constexpr uint32_t S = 1u << LOGS;
     __shared__ c128 sm[FX_E];
-    const bool p1 = party != 0;
     const uint32_t r0 = blockIdx.x * C2;
     const size_t mem = blockIdx.y;
     const c128* Am = A + mem * S;
@@ -308,7 +310,7 @@ __global__ void __launch_bounds__(FX_T) k_m2c_pass2(const c128* __restrict__ A, 
         sm[(ro << H2) + bp] = Am[r0 + ro + (bp << H1)];
     }
     __syncthreads();
-    stages_pass2<LOGS, true>(sm, root, r0, p1);
+    stages_pass2<LOGS, true, P1>(sm, root, r0);
     uint64_t* om = out + mem * nl * 2 * S;
     for (int e = threadIdx.x; e < FX_E; e += FX_T) {
         const uint32_t ro = e % C2, bp = e / C2;
@@ -316,8 +318,8 @@ __global__ void __launch_bounds__(FX_T) k_m2c_pass2(const c128* __restrict__ A, 
         const int2 w = twist[t];
         c128 c = cmul(sm[(ro << H2) + bp], make_int2(w.x, -w.y));
         if (sh >= 0) {
-            c.re = trunc(c.re, sh, p1);
-            c.im = trunc(c.im, sh, p1);
+            c.re = trunc<P1>(c.re, sh);
+            c.im = trunc<P1>(c.im, sh);
         } else {
             c.re = shl(c.re, -sh);
             c.im = shl(c.im, -sh);
@@ -461,6 +463,7 @@ int check_fixed(blb_ctx* c, uint32_t l, uint32_t sf)
 
 // run the statement with L_ = log2(N/2) as a compile-time constant
 #define FX_DISPATCH(LOGS, ...)                                           \
+    do {                                                                 \
     switch (LOGS) {                                                      \
     case 11: { constexpr int L_ = 11; __VA_ARGS__; } break;              \
     case 12: { constexpr int L_ = 12; __VA_ARGS__; } break;              \
@@ -469,7 +472,8 @@ int check_fixed(blb_ctx* c, uint32_t l, uint32_t sf)
     case 15: { constexpr int L_ = 15; __VA_ARGS__; } break;              \
     case 16: { constexpr int L_ = 16; __VA_ARGS__; } break;              \
     default: return blb_fail(BLB_ERR_ARG, "unsupported ring degree");    \
-    }
+    }                                                                    \
+    } while (0)
 
 // 128-bit share arrays in device memory are read and written as 16-byte
 // vectors (host arrays are staged through aligned scratch)
@@ -561,11 +565,19 @@ extern "C" int blb_c2m_local(blb_ctx* c, uint32_t party, const uint64_t* t, cons
     const dim3 grid(s / FX_E, count);
     {
         ProfScope ps(c, "c2m", (uint64_t)count * (N * 24ull + s * 8ull));
-        FX_DISPATCH(logs, k_c2m_pass1<L_><<<grid, FX_T, 0, c->stream>>>(dt, dw, A, c->d_fx_root, twist, c->q[0],
-                                                                         sh_in, party));
+        if (party)
+            FX_DISPATCH(logs, k_c2m_pass1<L_, true><<<grid, FX_T, 0, c->stream>>>(dt, dw, A, c->d_fx_root, twist,
+                                                                                  c->q[0], sh_in));
+        else
+            FX_DISPATCH(logs, k_c2m_pass1<L_, false><<<grid, FX_T, 0, c->stream>>>(dt, dw, A, c->d_fx_root, twist,
+                                                                                   c->q[0], sh_in));
         BLB_LAUNCHED();
-        FX_DISPATCH(logs, k_c2m_pass2<L_><<<grid, FX_T, 0, c->stream>>>(A, dout, c->d_fx_root, c->d_kinv,
-                                                                         FX_P - (int)sf, mask, party));
+        if (party)
+            FX_DISPATCH(logs, k_c2m_pass2<L_, true><<<grid, FX_T, 0, c->stream>>>(A, dout, c->d_fx_root, c->d_kinv,
+                                                                                  FX_P - (int)sf, mask));
+        else
+            FX_DISPATCH(logs, k_c2m_pass2<L_, false><<<grid, FX_T, 0, c->stream>>>(A, dout, c->d_fx_root, c->d_kinv,
+                                                                                   FX_P - (int)sf, mask));
         BLB_LAUNCHED();
     }
     if (dout != out) BLB_TRY(copy_out(c, out, dout, (size_t)count * s * 8));
@@ -619,11 +631,20 @@ extern "C" int blb_m2c_local(blb_ctx* c, uint32_t party, const uint64_t* x, cons
     const dim3 grid(s / FX_E, count);
     {
         ProfScope ps(c, "m2c", (uint64_t)count * (n * 24ull + out_bytes / count));
-        FX_DISPATCH(logs, k_m2c_pass1<L_><<<grid, FX_T, 0, c->stream>>>(dx, dw, A, c->d_fx_root, c->d_kinv, n,
-                                                                         (int)l, FX_P - (int)sf, party));
+        if (party)
+            FX_DISPATCH(logs, k_m2c_pass1<L_, true><<<grid, FX_T, 0, c->stream>>>(dx, dw, A, c->d_fx_root, c->d_kinv,
+                                                                                  n, (int)l, FX_P - (int)sf));
+        else
+            FX_DISPATCH(logs, k_m2c_pass1<L_, false><<<grid, FX_T, 0, c->stream>>>(dx, dw, A, c->d_fx_root,
+                                                                                   c->d_kinv, n, (int)l,
+                                                                                   FX_P - (int)sf));
         BLB_LAUNCHED();
-        FX_DISPATCH(logs, k_m2c_pass2<L_><<<grid, FX_T, 0, c->stream>>>(A, dout, c->d_fx_root, twist, K, nl, sh,
-                                                                         party));
+        if (party)
+            FX_DISPATCH(logs, k_m2c_pass2<L_, true><<<grid, FX_T, 0, c->stream>>>(A, dout, c->d_fx_root, twist, K,
+                                                                                  nl, sh));
+        else
+            FX_DISPATCH(logs, k_m2c_pass2<L_, false><<<grid, FX_T, 0, c->stream>>>(A, dout, c->d_fx_root, twist, K,
+                                                                                   nl, sh));
         BLB_LAUNCHED();
     }
     if (dout != out) BLB_TRY(copy_out(c, out, dout, out_bytes));
