@@ -606,19 +606,23 @@ static void base_convert(uint32_t N, const uint64_t* const* x, const uint64_t* s
  * base conversion of Halevi, Polyakov and Shoup (2019): with
  * y_k = [x_k (P/p_k)^-1]_{p_k}, sum_k y_k (P/p_k) = [x]_P + v P and
  * v = round(sum_k y_k / p_k), so X = sum_k y_k (P/p_k) - v P.  The sum is
- * taken in double precision in the order k = 0, 1, ... (IEEE division and
- * addition, round half to even).  The result is round(x / P) mod q_i (up to
- * a misrounding of v when the fraction is within ~2^-50 of 1/2). */
+ * taken in 128-bit fixed point: y_k / p_k as y_k floor(2^128 / p_k) (below
+ * 2^128 since y_k < p_k), added with the carries counted, v = carries + the
+ * top fraction bit.  Each term is low by less than y_k 2^-128, so v is the
+ * exact rounding unless the fraction is within 2^-65 of 1/2 (it is never
+ * exactly 1/2: P is odd).  The result is round(x / P) mod q_i. */
 void orc_moddown(const orc_params* p, const uint64_t* acc, uint32_t level, uint64_t* out)
 {
     const uint32_t N = p->N, n = level + 1, nP = p->nP, ext = n + nP;
     const uint64_t* pp = p->prime + p->nQ;
     uint64_t hat_inv[ORC_MAX_PRIMES];
+    u128 recip[ORC_MAX_PRIMES]; /* floor(2^128 / p_k) */
     for (uint32_t k = 0; k < nP; k++) {
         uint64_t h = 1 % pp[k];
         for (uint32_t l = 0; l < nP; l++)
             if (l != k) h = mulmod(h, pp[l] % pp[k], pp[k]);
         hat_inv[k] = invmod(h, pp[k]);
+        recip[k] = ~(u128)0 / pp[k];
     }
     #pragma omp parallel for
     for (uint32_t i = 0; i < n; i++) {
@@ -637,12 +641,16 @@ void orc_moddown(const orc_params* p, const uint64_t* acc, uint32_t level, uint6
             uint64_t* o = out + ((size_t)poly * n + i) * N;
             for (uint32_t c = 0; c < N; c++) {
                 uint64_t y[ORC_MAX_PRIMES];
-                double frac = 0.0;
+                u128 frac = 0;
+                uint64_t whole = 0;
                 for (uint32_t k = 0; k < nP; k++) {
                     y[k] = mulmod(A[(size_t)(n + k) * N + c], hat_inv[k], pp[k]);
-                    frac += (double)y[k] / (double)pp[k];
+                    u128 f = (u128)y[k] * recip[k];
+                    u128 t = frac + f;
+                    whole += t < frac;
+                    frac = t;
                 }
-                uint64_t v = (uint64_t)rint(frac);
+                uint64_t v = whole + (uint64_t)(frac >> 127);
                 uint64_t X = 0;
                 for (uint32_t k = 0; k < nP; k++) X = addmod(X, mulmod(y[k] % q, hat_q[k], q), q);
                 X = submod(X, mulmod(v % q, P_q, q), q);

@@ -46,10 +46,12 @@ __global__ void k_conv(const uint64_t* __restrict__ src, size_t src_ps, const Co
 }
 
 // ModDown conversion with rounding (Halevi, Polyakov, Shoup 2019): for the P
-// limbs x_k, y_k = [x_k (P/p_k)^-1]_{p_k}, v = round(sum_k y_k / p_k) in double
-// precision (IEEE division and addition, in the order k = 0, 1, ...), and
+// limbs x_k, y_k = [x_k (P/p_k)^-1]_{p_k}, v = round(sum_k y_k / p_k), and
 // X = sum_k y_k (P/p_k) - v P is the representative of x mod P in (-P/2, P/2];
-// dst row t gets X mod q_t.
+// dst row t gets X mod q_t.  The sum is taken in 128-bit fixed point, y_k / p_k
+// as y_k floor(2^128 / p_k) (the Barrett constant of p_k, below 2^128 since
+// y_k < p_k) with the carries counted: the exact rounding unless the fraction
+// is within 2^-65 of 1/2, and no FP64 (a small fraction of B300's integer rate).
 __global__ void k_moddown_conv(const uint64_t* __restrict__ src, size_t src_ps, const ConvTable* __restrict__ tab,
                                uint32_t nt, uint64_t* __restrict__ dst, size_t dst_ps,
                                const uint64_t* __restrict__ qs, const uint64_t* __restrict__ bar, uint32_t N)
@@ -58,13 +60,23 @@ __global__ void k_moddown_conv(const uint64_t* __restrict__ src, size_t src_ps, 
     if (c >= N) return;
     const uint32_t ns = tab->ns;
     uint64_t y[BLB_MAXP];
-    double frac = 0.0;
+    uint64_t f_lo = 0, f_hi = 0, whole = 0;
     for (uint32_t k = 0; k < ns; k++) {
-        const uint64_t pk = qs[tab->src[k]];
+        const uint32_t pk_i = tab->src[k];
+        const uint64_t pk = qs[pk_i];
         y[k] = mul_shoup(src[poly * src_ps + (size_t)k * N + c], tab->hat_inv[k], tab->hat_inv_sh[k], pk);
-        frac = __dadd_rn(frac, __ddiv_rn(__ull2double_rn(y[k]), __ull2double_rn(pk)));
+        const uint64_t b0 = bar[2 * pk_i], b1 = bar[2 * pk_i + 1];
+        const uint64_t lo = y[k] * b0, hi = __umul64hi(y[k], b0) + y[k] * b1;  // y_k floor(2^128/p_k)
+        const uint64_t s_lo = f_lo + lo;
+        const uint64_t c0 = s_lo < f_lo;
+        const uint64_t s_hi = f_hi + hi;
+        const uint64_t c1 = s_hi < f_hi;
+        const uint64_t s_hi2 = s_hi + c0;
+        whole += c1 + (s_hi2 < s_hi);
+        f_lo = s_lo;
+        f_hi = s_hi2;
     }
-    const uint64_t v = (uint64_t)__double2ll_rn(frac);
+    const uint64_t v = whole + (f_hi >> 63);
     for (uint32_t t = 0; t < nt; t++) {
         const uint32_t pt = tab->dst[t];
         const uint64_t q = qs[pt], r0 = bar[2 * pt], r1 = bar[2 * pt + 1];
