@@ -395,6 +395,33 @@ class Oracle:
     def cp_num_rotations(self, nX, nY, b1, G):
         return int(lib().orc_cp_num_rotations(nX, nY, b1, G))
 
+    # -- rotate-and-sum packing (Sec. 4.2.1) and the LayerNorm head ------------
+    def rs_packing(self, ct, L, D, direction, mask, gks):
+        """gks: Galois keys of the rotations 2^i L (left, direction 0) or -2^i L (right)."""
+        ct = np.ascontiguousarray(ct, np.uint64)
+        level = ct.shape[1] - 1
+        out = np.zeros((2, level + (0 if mask else 1), self.N), np.uint64)
+        keys = [np.ascontiguousarray(k, np.uint64) for k in gks]
+        arr = (_u64p * max(1, len(keys)))(*[_p(k, _u64p) for k in keys])
+        rc = lib().orc_rs_packing(self._pp, _p(ct, _u64p), level, L, D, int(direction), int(mask), arr, _p(out, _u64p))
+        if rc:
+            raise ValueError(f"rs_packing failed {rc}")
+        return out
+
+    def layernorm_head(self, X_cts, L, D, gks, relin):
+        X = np.ascontiguousarray(X_cts, np.uint64)
+        nc, level = X.shape[0], X.shape[2] - 1
+        X_mu = np.zeros((nc, 2, level, self.N), np.uint64)
+        var = np.zeros((2, level - 2, self.N), np.uint64)
+        keys = [np.ascontiguousarray(k, np.uint64) for k in gks]
+        arr = (_u64p * max(1, len(keys)))(*[_p(k, _u64p) for k in keys])
+        relin = np.ascontiguousarray(relin, np.uint64)
+        rc = lib().orc_layernorm_head(self._pp, _p(X, _u64p), nc, level, L, D, arr, _p(relin, _u64p),
+                                      _p(X_mu, _u64p), _p(var, _u64p))
+        if rc:
+            raise ValueError(f"layernorm_head failed {rc}")
+        return X_mu, var
+
     # -- local parts of the conversions (Alg. 1 steps 3-4, Alg. 2, App. C.3) --
     def r2f_local(self, party, M, level):
         M = np.ascontiguousarray(M, np.uint64).reshape(-1, 2)

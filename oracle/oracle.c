@@ -14,6 +14,8 @@
  *             here is the standard diagonal method with baby-step giant-step,
  *             App. C.1)
  *   Sec. 6.3 / Alg. 1  secure CKKS-to-MPC masking with a uniform mask
+ *   Sec. 4.2.1 rotate-and-sum sum / broadcast packing; the HE steps of the
+ *             secure LayerNorm before rsqrt (Alg. LayerNorm lines 1-6)
  *   Alg. 1 steps 3-4, Alg. 2, App. C.3  the parties' local steps of the
  *             conversions: field to ring, ring to field, fixed-point decoding
  *             and encoding of shares with local truncations
@@ -1707,5 +1709,138 @@ int orc_m2c_local(const orc_params* p, uint32_t party, const uint64_t* x, const 
     free(V);
     free(A);
     free(M);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* rotate-and-sum packing (Sec. 4.2.1) and the LayerNorm head it serves      */
+/* ------------------------------------------------------------------------- */
+/* Spatial-first packing puts block b (L consecutive slots) of a ciphertext at
+ * slots [b L, (b+1) L).  m^0 = m, m^i = m^{i-1} + Rot^{2^{i-1} L}(m^{i-1}) for
+ * i = 1..log2 D, with left rotations (dir = 0: sum) or right rotations
+ * (dir = 1: broadcast); gk[i-1] is the Galois key of that rotation.  After the
+ * last round block b holds the sum of blocks b, b+1, ..., b+D-1 (left) or
+ * b, b-1, ..., b-D+1 (right), indices mod N/(2L).  With mask != 0 (the sum) the
+ * result is multiplied by the plaintext [1 (L slots), 0, ...] encoded at scale
+ * q_level and rescaled, so only block 0 remains and out is at level - 1. */
+int orc_rs_packing(const orc_params* p, const uint64_t* ct, uint32_t level, uint32_t L, uint32_t D, int dir,
+                   int mask, const uint64_t* const* gk, uint64_t* out)
+{
+    const uint32_t N = p->N, s = N / 2, n = level + 1;
+    if (L == 0 || D == 0 || (D & (D - 1)) || (uint64_t)L * D > s || (mask && (dir || level == 0))) return -1;
+    const size_t words = (size_t)2 * n * N;
+    uint64_t* m = malloc(sizeof(uint64_t) * words);
+    uint64_t* r = malloc(sizeof(uint64_t) * words);
+    memcpy(m, ct, sizeof(uint64_t) * words);
+    uint32_t i = 0;
+    for (uint32_t step = 1; step < D; step <<= 1, i++) {
+        int32_t amount = (int32_t)(step * L);
+        orc_rotate(p, m, level, dir ? -amount : amount, gk[i], r);
+        ct_add_inplace(p, m, r, level, 2);
+    }
+    if (mask) {
+        double* z = calloc(s, sizeof(double));
+        uint64_t* pt = malloc(sizeof(uint64_t) * (size_t)n * N);
+        for (uint32_t j = 0; j < L; j++) z[j] = 1.0;
+        orc_encode(p, z, s, level, (double)p->prime[level], pt);
+        orc_mul_plain(p, m, pt, level, r);
+        orc_rescale(p, r, level, 2, out);
+        free(z);
+        free(pt);
+    } else {
+        memcpy(out, m, sizeof(uint64_t) * words);
+    }
+    free(m);
+    free(r);
+    return 0;
+}
+
+/* ct * (the constant c in every slot, encoded at scale q_level), rescaled: the
+ * scalar multiplications ewmul_cp(., 1/D) of the LayerNorm. */
+static void mul_const_rescale(const orc_params* p, const uint64_t* ct, uint32_t level, double c, uint64_t* out)
+{
+    const uint32_t N = p->N, s = N / 2, n = level + 1;
+    double* z = malloc(sizeof(double) * s);
+    uint64_t* pt = malloc(sizeof(uint64_t) * (size_t)n * N);
+    uint64_t* t = malloc(sizeof(uint64_t) * (size_t)2 * n * N);
+    for (uint32_t j = 0; j < s; j++) z[j] = c;
+    orc_encode(p, z, s, level, (double)p->prime[level], pt);
+    orc_mul_plain(p, ct, pt, level, t);
+    orc_rescale(p, t, level, 2, out);
+    free(z);
+    free(pt);
+    free(t);
+}
+
+/* ct at level l -> the same ciphertext at level l - 1 (drop the last limb). */
+static void drop_limb(const orc_params* p, const uint64_t* ct, uint32_t level, uint64_t* out)
+{
+    const uint32_t N = p->N, n = level + 1;
+    for (uint32_t poly = 0; poly < 2; poly++)
+        memcpy(out + (size_t)poly * level * N, ct + (size_t)poly * n * N, sizeof(uint64_t) * (size_t)level * N);
+}
+
+/* The HE steps of the secure LayerNorm before rsqrt (Alg. LayerNorm lines 1-6),
+ * on X (L rows x D columns) packed spatial-first in nc ciphertexts of k = N/(2L)
+ * columns each (k a power of two, nc = ceil(D/k)), at `level`:
+ *   X_sum = sum_j X_ij: the nc ciphertexts added, then rotate-and-sum over the
+ *           k blocks without the mask (the sum feeds a scalar operator, so every
+ *           block keeping the row sum is the broadcast, Sec. 4.2.1);
+ *   mu    = ewmul_cp(X_sum, 1/D)                              (level - 1)
+ *   X_mu  = sadd_cc(X, -mu): each X_c dropped one level minus mu  (level - 1)
+ *   X_mu^2 = ewmul_cc(X_mu, X_mu): tensor, relinearize, rescale  (level - 2)
+ *   X_tmp = sum_j X_mu^2 as for X_sum;  var = ewmul_cp(X_tmp, 1/D) (level - 3).
+ * Out: X_mu (nc ciphertexts, level - 1) and var (one ciphertext, level - 3,
+ * every block holding the row variances); gk[i] is the key of rotation 2^i L. */
+int orc_layernorm_head(const orc_params* p, const uint64_t* X, uint32_t nc, uint32_t level, uint32_t L, uint32_t D,
+                       const uint64_t* const* gk, const uint64_t* relin_ksk, uint64_t* X_mu, uint64_t* var)
+{
+    const uint32_t N = p->N, s = N / 2;
+    if (L == 0 || s % L || level < 3 || nc == 0) return -1;
+    const uint32_t k = s / L;
+    if (k & (k - 1)) return -1;
+    const size_t w0 = (size_t)2 * (level + 1) * N, w1 = (size_t)2 * level * N, w2 = (size_t)2 * (level - 1) * N;
+    uint64_t* acc = malloc(sizeof(uint64_t) * w0);
+    uint64_t* tmp = malloc(sizeof(uint64_t) * w0);
+    uint64_t* mu = malloc(sizeof(uint64_t) * w1);
+    uint64_t* t3 = malloc(sizeof(uint64_t) * 3 * (size_t)level * N);
+    uint64_t* sq = malloc(sizeof(uint64_t) * w1);
+    uint64_t* acc2 = malloc(sizeof(uint64_t) * w2);
+    uint64_t* tmp2 = malloc(sizeof(uint64_t) * w2);
+    /* lines 1-2 */
+    memcpy(acc, X, sizeof(uint64_t) * w0);
+    for (uint32_t c = 1; c < nc; c++) ct_add_inplace(p, acc, X + c * w0, level, 2);
+    orc_rs_packing(p, acc, level, L, k, 0, 0, gk, tmp);
+    mul_const_rescale(p, tmp, level, 1.0 / (double)D, mu);
+    /* lines 3-6 */
+    for (uint32_t c = 0; c < nc; c++) {
+        uint64_t* xm = X_mu + c * w1;
+        drop_limb(p, X + c * w0, level, xm);
+        for (uint32_t poly = 0; poly < 2; poly++)
+            for (uint32_t l = 0; l < level; l++) {
+                const uint64_t q = p->prime[l];
+                for (uint32_t i = 0; i < N; i++) {
+                    size_t o = ((size_t)poly * level + l) * N + i;
+                    xm[o] = submod(xm[o], mu[o], q);
+                }
+            }
+        orc_tensor(p, xm, xm, level - 1, t3);
+        orc_relinearize(p, t3, level - 1, relin_ksk, sq);
+        if (c == 0)
+            orc_rescale(p, sq, level - 1, 2, acc2);
+        else {
+            orc_rescale(p, sq, level - 1, 2, tmp2);
+            ct_add_inplace(p, acc2, tmp2, level - 2, 2);
+        }
+    }
+    orc_rs_packing(p, acc2, level - 2, L, k, 0, 0, gk, tmp2);
+    mul_const_rescale(p, tmp2, level - 2, 1.0 / (double)D, var);
+    free(acc);
+    free(tmp);
+    free(mu);
+    free(t3);
+    free(sq);
+    free(acc2);
+    free(tmp2);
     return 0;
 }

@@ -154,6 +154,12 @@ void orc_r2f_local(const orc_params* p, uint32_t party, uint32_t n, const uint64
                    uint64_t* out);
 int orc_c2m_local(const orc_params* p, uint32_t party, const uint64_t* t, const uint64_t* wsh, double scale,
                   uint32_t l, uint32_t sf, uint64_t* out /* N/2, mod 2^l */);
+/* ---- rotate-and-sum packing (Sec. 4.2.1) and the LayerNorm head ---------- */
+int orc_rs_packing(const orc_params* p, const uint64_t* ct, uint32_t level, uint32_t L, uint32_t D, int dir,
+                   int mask, const uint64_t* const* gk, uint64_t* out);
+int orc_layernorm_head(const orc_params* p, const uint64_t* X, uint32_t nc, uint32_t level, uint32_t L, uint32_t D,
+                       const uint64_t* const* gk, const uint64_t* relin_ksk,
+                       uint64_t* X_mu /* nc x 2 x level x N */, uint64_t* var /* 2 x (level-2) x N */);
 int orc_m2c_local(const orc_params* p, uint32_t party, const uint64_t* x, const uint64_t* wsh, uint32_t n,
                   uint32_t level, double scale, uint32_t l, uint32_t sf, uint64_t* out /* (level+1) x N */);
 
