@@ -273,6 +273,39 @@ int blb_matmul_cc(blb_ctx* ctx, const blb_keys* keys, blb_ct* const* A, blb_ct* 
 int blb_he2mpc(blb_ctx* ctx, const blb_keys* keys, const blb_ct* ct, uint64_t nonce,
                blb_ct** masked_for_p0, uint64_t* p1_share);
 
+/* ---- rotate-and-sum packing (Sec. 4.2.1) -------------------------------------
+ * Spatial-first packing puts block b (L consecutive slots) of a ciphertext at
+ * slots [b L, (b+1) L).  For each of the count input ciphertexts (one level,
+ * two polynomials): m^0 = m, m^i = m^{i-1} + Rot^{2^{i-1} L}(m^{i-1}) for
+ * i = 1..log2 D, with left rotations (dir = 0: sum) or right rotations
+ * (dir = 1: broadcast).  Block b then holds the sum of blocks b .. b+D-1
+ * (left) or b-D+1 .. b (right), indices mod N/(2L).  mask != 0 (sum only)
+ * multiplies by the plaintext [1 (L slots), 0, ...] encoded at scale q_level and
+ * rescales: only block 0 remains, one level lower.  D must be a power of two
+ * with L D <= N/2; the keys must hold the rotations +-2^i L.  out[k] receives
+ * new ciphertexts (all NULL on error).  Errors: BLB_ERR_ARG, BLB_ERR_NO_KEY,
+ * BLB_ERR_OOM, BLB_ERR_CUDA. */
+int blb_rotate_sum_packing(blb_ctx* ctx, const blb_keys* keys, blb_ct* const* in, uint32_t count, uint32_t L,
+                           uint32_t D, int dir, int mask, blb_ct** out);
+/* The HE steps of the secure LayerNorm before rsqrt (Alg. LayerNorm lines 1-6)
+ * for count sequences, each L rows x D columns packed spatial-first in nc
+ * ciphertexts X[j nc + c] of k = N/(2L) columns (k a power of two) at one
+ * level >= 3:
+ *   X_sum = the nc ciphertexts added, then rotate-and-sum over the k blocks
+ *           without mask (the sum feeds a scalar operator, so every block
+ *           keeping the row sums is the broadcast, Sec. 4.2.1);
+ *   mu    = X_sum times the plaintext 1/D (scale q_level), rescaled;
+ *   X_mu[j nc + c] = X[j nc + c] one level down, minus mu;
+ *   X_mu^2: tensor product, relinearization, rescale;
+ *   var[j] = the rotate-and-sum of the nc squares, times 1/D, rescaled
+ *            (level - 3, scale scale^2 / q_{level-1}, every block holding the
+ *            row variances).
+ * Needs the relinearization key and the rotations 2^i L, i < log2 k.  With
+ * zero-padded columns (D < nc k) each padded column adds mu^2 to the sum of
+ * squares.  Outputs are new ciphertexts (all NULL on error). */
+int blb_layernorm_head(blb_ctx* ctx, const blb_keys* keys, blb_ct* const* X, uint32_t count, uint32_t nc,
+                       uint32_t L, uint32_t D, blb_ct** X_mu, blb_ct** var);
+
 /* ---- local steps of the conversions between CKKS and shares -----------------
  * (Alg. 1 steps 3-4, Alg. 2, Sec. 6.3, App. C.3.)  Both parties' local
  * computations; the interactive comparisons inside the ring/field extensions

@@ -96,6 +96,8 @@ SIGNATURES = {
     "blb_matmul_cc_plan": (ctypes.c_int, [_vp, _vp, _vp, _pp, _pp, _u32, _pp]),
     "blb_matmul_cc": (ctypes.c_int, [_vp, _vp, _pp, _pp, _u32, _u32, _u32, _u32, ctypes.POINTER(_CcSched), _pp]),
     "blb_he2mpc": (ctypes.c_int, [_vp, _vp, _vp, _u64, _pp, _vp]),
+    "blb_rotate_sum_packing": (ctypes.c_int, [_vp, _vp, _pp, _u32, _u32, _u32, ctypes.c_int, ctypes.c_int, _pp]),
+    "blb_layernorm_head": (ctypes.c_int, [_vp, _vp, _pp, _u32, _u32, _u32, _u32, _pp, _pp]),
     "blb_f2r_wrap_sim": (ctypes.c_int, [_vp, _vp, _vp, _u32, _u64, _vp, _vp, _vp]),
     "blb_c2m_local": (ctypes.c_int, [_vp, _u32, _vp, _vp, _u32, _dbl, _u32, _u32, _vp]),
     "blb_ext_wrap_sim": (ctypes.c_int, [_vp, _vp, _vp, _u32, _u32, _u32, _u64, _vp, _vp, _vp]),
@@ -401,6 +403,27 @@ class Context:
         if isinstance(coeffs, np.ndarray):
             coeffs = np.ascontiguousarray(coeffs, np.uint64)
         return self._new(Plaintext, lib().blb_pt_import, _ptr(coeffs), level, _dbl(scale))
+
+    # -- rotate-and-sum packing (Sec. 4.2.1) and the LayerNorm head ----------
+    def rotate_sum_packing(self, keys, cts, L, D, direction=0, mask=False):
+        count = len(cts)
+        ins = (ctypes.c_void_p * count)(*[c.h for c in cts])
+        out = (ctypes.c_void_p * count)()
+        _check(lib().blb_rotate_sum_packing(self.h, keys.h, ins, count, L, D, int(direction), int(mask), out))
+        return [Ciphertext(self, c) for c in out]
+
+    def layernorm_head(self, keys, X, L, D, nc):
+        """X: count sequences x nc ciphertexts (flat list, sequence-major).
+        Returns (X_mu as a flat list, var one per sequence)."""
+        total = len(X)
+        if total % nc:
+            raise ValueError("X must hold nc ciphertexts per sequence")
+        count = total // nc
+        ins = (ctypes.c_void_p * total)(*[c.h for c in X])
+        xm = (ctypes.c_void_p * total)()
+        var = (ctypes.c_void_p * count)()
+        _check(lib().blb_layernorm_head(self.h, keys.h, ins, count, nc, L, D, xm, var))
+        return [Ciphertext(self, c) for c in xm], [Ciphertext(self, c) for c in var]
 
     # -- local steps of the conversions (Alg. 1 steps 3-4, Alg. 2, App. C.3) --
     # 128-bit shares are (..., 2) uint64 arrays (low, high); every array may be
