@@ -390,6 +390,49 @@ def conversion_bench(w, reps):
     return out
 
 
+def layernorm_bench(steps, seqs=(1, 8)):
+    """The HE steps of the secure LayerNorm before rsqrt (Alg. LayerNorm lines
+    1-6) on BERT-base activations: 128 tokens x 768 features packed
+    spatial-first in 6 ciphertexts of 128 columns at N = 2^15, level 7: row
+    sums by rotate-and-sum (7 rotations, no mask: Sec. 4.2.1's sum -> scalar
+    fusion), mean, centring, squares, variance.  Timed for one sequence and
+    for a batch of sequences per call."""
+    import torch
+    from paper_2508_19525_b300 import blb
+    from paper_2508_19525_b300 import workloads as wl
+    prm = wl.BERT_CP
+    stream = torch.cuda.Stream()
+    ctx = blb.Context(prm.logN, prm.q_bits, prm.p_bits, prm.dnum, prm.scale, stream=stream)
+    s, L = ctx.N // 2, M
+    k = s // L
+    nc = D // k
+    keys = ctx.keygen(2, [L << i for i in range(int(np.log2(k)))], relin=True)
+    rng = np.random.default_rng(4)
+    X = rng.uniform(-1, 1, (L, D))
+    Z = np.zeros((nc, s))
+    for c in range(nc):
+        Z[c] = X[:, c * k:(c + 1) * k].T.reshape(-1)
+    cts = ctx.encrypt_batch(keys, ctx.encode_batch(Z, LEVEL), list(range(nc)))
+    out = {"workload": f"LayerNorm head (Alg. LayerNorm lines 1-6): {L} tokens x {D} features in {nc} "
+                       f"ciphertexts, N=2^15, level {LEVEL} -> 4, {int(np.log2(k))} rotations per sum", "per_call": {}}
+    for S in seqs:
+        X_in = cts * S
+        ctx.layernorm_head(keys, X_in, L, D, nc)
+        ctx.sync()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(steps):
+            ctx.layernorm_head(keys, X_in, L, D, nc)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1) / steps
+        out["per_call"][str(S)] = {"ms": round(ms, 3), "tokens_per_s": round(S * L / (ms / 1e3), 1)}
+    Xm, var = ctx.layernorm_head(keys, cts, L, D, nc)
+    v = ctx.decrypt(keys, var[0], coeffs=False)[1].reshape(k, L)
+    out["max_abs_err_var_vs_fp64"] = float(np.abs(v - X.var(axis=1)[None, :]).max())
+    return out
+
+
 def serving_bench(n_requests=64, rate=20.0, sat_rate=400.0, budget_gb=24, max_batch=8):
     """Continuous batching of encrypted linear-layer requests (one client and key
     set per request) against one request per launch; BERT-base-shaped and
@@ -513,6 +556,7 @@ def run_blb(args):
         batched = {"sequences_per_step": args.batch, "value": round(bval, 3), "unit": UNIT,
                    "ms_per_step": round(bsec * 1e3 / bsteps, 3), "speedup_vs_plain": round(bval / value, 3)}
     conv = conversion_bench(w, 20) if args.conversion else None
+    lnorm = layernorm_bench(max(2, min(10, args.steps // 5))) if args.layernorm and world == 1 else None
     attn = attention_cc(max(1, min(5, args.steps // 4))) if args.attention and world == 1 else None
     serving = serving_bench() if args.serving and world == 1 else None
     if rank != 0:
@@ -559,6 +603,7 @@ def run_blb(args):
         "batched": batched,
         "attention_cc": attn,
         "serving": serving,
+        "layernorm_head": lnorm,
         "conversion": dict(conv, sites={k: dict(v, frac_of_hbm=round(v["achieved_gbs"] / hbm, 4), peak_kind=peak_note)
                                         for k, v in conv["sites"].items()}) if conv else None,
         "counts_per_step": w.counts(),
@@ -743,6 +788,8 @@ def main():
     ap.add_argument("--batch", type=int, default=8, help="sequences per batched step (1 = skip)")
     ap.add_argument("--no-attention", dest="attention", action="store_false",
                     help="skip the matmul_cc attention measurement")
+    ap.add_argument("--no-layernorm", dest="layernorm", action="store_false",
+                    help="skip the LayerNorm-head (rotate-and-sum) measurement")
     ap.add_argument("--no-conversion", dest="conversion", action="store_false",
                     help="skip the CKKS <-> MPC conversion measurement")
     ap.add_argument("--no-serving", dest="serving", action="store_false",
