@@ -539,6 +539,7 @@ def run_blb(args):
     launches = blb.kernel_launches() - launches0
     sites = {s: w.ctx.profile_read(s) for s in ("cp_mac", "keyswitch", "ntt", "intt")}
     w.ctx.profile(False)
+    int_peaks = w.ctx.int_peaks()
     value, dev_max = aggregate(dev_s, TOKENS_PER_STEP * args.steps, world)
     # end to end from pinned host buffers
     for _ in range(max(1, args.warmup // 2)):
@@ -576,6 +577,18 @@ def run_blb(args):
                        "frac": round(gbs / hbm, 4), "ms_total": round(ms, 3), "launch_sites": cnt,
                        "share_of_step": round(ms / (dev_s * 1e3), 4),
                        "algorithmic_bytes_per_call": nbytes // cnt, "peak_kind": peak_note}
+    # ALU roofline of the NTT sites: butterflies (rows x N/2 x log2 N; the site
+    # records 16 B per coefficient per row) per second against the measured
+    # register-only butterfly rate of the same instruction mix
+    logn = int(np.log2(w.N))
+    for s_ in ("ntt", "intt"):
+        if s_ in roof:
+            ms, cnt, nbytes = sites[s_]
+            bfly = nbytes / 16 * logn / 2
+            ach = bfly / (ms / 1e3)
+            roof[s_]["alu"] = {"bound": "alu", "achieved": round(ach / 1e9, 2), "peak": round(int_peaks["bfly_per_s"] / 1e9, 2),
+                               "unit": "Gbutterfly/s", "frac": round(ach / int_peaks["bfly_per_s"], 4),
+                               "peak_kind": "measured (register-only lazy butterfly, blb_int_peaks)"}
     # the dominant single-kernel site (the key-switch site is a pipeline of kernels)
     kernel_sites = [s for s in ("cp_mac", "ntt", "intt") if s in roof]
     dominant = max(kernel_sites, key=lambda s: roof[s]["ms_total"]) if kernel_sites else None
@@ -599,6 +612,7 @@ def run_blb(args):
         "gpu_launches": int(launches),
         "roofline": dict(roof[dominant], kernel=dominant, traffic=traffic) if dominant else None,
         "roofline_sites": roof,
+        "int_peaks": {k: (round(v / 1e9, 2) if k.endswith("_s") else round(v, 3)) for k, v in int_peaks.items()},
         "accuracy": {"max_abs_err_vs_fp64": max_err, "mse": mse, "bound": 1e-4},
         "batched": batched,
         "attention_cc": attn,

@@ -1,0 +1,143 @@
+// peaks.cu -- integer-pipe throughput of the arithmetic units the NTT and the
+// base conversions are built from, for their ALU rooflines.
+//
+// The NTT's unit of work is the lazy Cooley-Tukey butterfly on 64-bit words
+// (one Shoup product by a constant twiddle, then X + WY and X - WY + 2q); the
+// base conversions' unit is a 64 x 64 -> 128-bit multiply-accumulate.  Each
+// kernel runs independent chains of one unit entirely in registers (eight per
+// thread, enough CTAs for every SM), so the measured rate is the integer
+// pipes' throughput for that instruction mix with no memory traffic.  Every
+// CTA also reports its SM cycles and nanoseconds, whose ratio is the SM clock
+// during the run, so the rate is also known per SM cycle:
+// peak = rate per SM cycle x SMs x SM clock.
+#include "common.cuh"
+
+namespace {
+
+constexpr int PK_T = 256;
+constexpr int PK_CHAINS = 8;
+
+__device__ __forceinline__ uint64_t pk_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__global__ void __launch_bounds__(PK_T) k_peak_bfly(uint64_t* __restrict__ out, unsigned long long* __restrict__ cycles,
+                                                    uint64_t w, uint64_t wp, uint64_t q, uint32_t iters)
+{
+    const uint64_t q2 = 2 * q;
+    uint64_t x[PK_CHAINS], y[PK_CHAINS];
+#pragma unroll
+    for (int k = 0; k < PK_CHAINS; k++) {
+        x[k] = (threadIdx.x * 7919ull + k * 104729ull + blockIdx.x) % q;
+        y[k] = (threadIdx.x * 15485863ull + k * 32452843ull) % q;
+    }
+    const long long t0 = clock64();
+    const uint64_t n0 = pk_ns();
+    for (uint32_t it = 0; it < iters; it++) {
+#pragma unroll
+        for (int k = 0; k < PK_CHAINS; k++) {
+            const uint64_t xr = x[k] >= q2 ? x[k] - q2 : x[k];
+            const uint64_t t = y[k] * w - __umul64hi(y[k], wp) * q;
+            x[k] = xr + t;
+            y[k] = xr + q2 - t;
+        }
+    }
+    const long long t1 = clock64();
+    const uint64_t n1 = pk_ns();
+    uint64_t r = 0;
+#pragma unroll
+    for (int k = 0; k < PK_CHAINS; k++) r ^= x[k] ^ y[k];
+    out[blockIdx.x * PK_T + threadIdx.x] = r;
+    if (threadIdx.x == 0) {
+        atomicAdd(cycles, (unsigned long long)(t1 - t0));
+        atomicAdd(cycles + 1, (unsigned long long)(n1 - n0));
+    }
+}
+
+__global__ void __launch_bounds__(PK_T) k_peak_mad128(uint64_t* __restrict__ out,
+                                                      unsigned long long* __restrict__ cycles, uint64_t h0,
+                                                      uint64_t h1, uint32_t iters)
+{
+    uint64_t y[PK_CHAINS];
+    acc128 a[PK_CHAINS];
+#pragma unroll
+    for (int k = 0; k < PK_CHAINS; k++) {
+        y[k] = threadIdx.x * 2654435761ull + k * 40503ull + blockIdx.x;
+        a[k] = acc128{0, 0};
+    }
+    const long long t0 = clock64();
+    const uint64_t n0 = pk_ns();
+    for (uint32_t it = 0; it < iters; it++) {
+#pragma unroll
+        for (int k = 0; k < PK_CHAINS; k++) {
+            mad128(a[k], y[k], (it & 1) ? h1 : h0);
+            y[k] += a[k].hi;
+        }
+    }
+    const long long t1 = clock64();
+    const uint64_t n1 = pk_ns();
+    uint64_t r = 0;
+#pragma unroll
+    for (int k = 0; k < PK_CHAINS; k++) r ^= a[k].lo ^ a[k].hi;
+    out[blockIdx.x * PK_T + threadIdx.x] = r;
+    if (threadIdx.x == 0) {
+        atomicAdd(cycles, (unsigned long long)(t1 - t0));
+        atomicAdd(cycles + 1, (unsigned long long)(n1 - n0));
+    }
+}
+
+}  // namespace
+
+extern "C" int blb_int_peaks(blb_ctx* c, double* bfly_per_s, double* mad128_per_s, double* bfly_per_sm_cycle,
+                             double* mad128_per_sm_cycle)
+{
+    if (!c) return blb_fail(BLB_ERR_ARG, "null argument");
+    int dev, sms;
+    BLB_CUDA(cudaGetDevice(&dev));
+    BLB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const uint32_t blocks = (uint32_t)sms * 8, iters = 4096;
+    Scratch S(c);
+    uint64_t* out = (uint64_t*)S.get((size_t)blocks * PK_T * 8);
+    unsigned long long* cyc = (unsigned long long*)S.get(16);
+    if (!out || !cyc) return blb_fail(BLB_ERR_OOM, "peak buffers");
+    cudaEvent_t e0, e1;
+    BLB_CUDA(cudaEventCreate(&e0));
+    BLB_CUDA(cudaEventCreate(&e1));
+    const uint64_t q = c->q[0];
+    const uint64_t w = (q >> 3) + 12345, wp = shoup_companion(w, q);
+    double res[2][2] = {{0, 0}, {0, 0}};
+    int rc = BLB_OK;
+    for (int kind = 0; kind < 2 && !rc; kind++) {
+        for (int rep = 0; rep < 2 && !rc; rep++) {  // the first run warms up the clocks
+            if (cudaMemsetAsync(cyc, 0, 16, c->stream) != cudaSuccess) rc = blb_fail(BLB_ERR_CUDA, "memset");
+            cudaEventRecord(e0, c->stream);
+            if (kind == 0)
+                k_peak_bfly<<<blocks, PK_T, 0, c->stream>>>(out, cyc, w, wp, q, iters);
+            else
+                k_peak_mad128<<<blocks, PK_T, 0, c->stream>>>(out, cyc, w, wp, iters);
+            if (cudaGetLastError() != cudaSuccess) rc = blb_fail(BLB_ERR_CUDA, "peak kernel launch failed");
+            blb_count_launch();
+            cudaEventRecord(e1, c->stream);
+            if (cudaEventSynchronize(e1) != cudaSuccess) rc = blb_fail(BLB_ERR_CUDA, "peak kernel failed");
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            unsigned long long cn[2] = {0, 0};
+            if (cudaMemcpy(cn, cyc, 16, cudaMemcpyDeviceToHost) != cudaSuccess) rc = blb_fail(BLB_ERR_CUDA, "copy");
+            const double ops = (double)blocks * PK_T * iters * PK_CHAINS;
+            const double ghz = cn[1] ? (double)cn[0] / (double)cn[1] : 1.0;  // SM cycles per ns
+            res[kind][0] = ops / (ms / 1e3);
+            res[kind][1] = res[kind][0] / ((double)sms * ghz * 1e9);
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    if (bfly_per_s) *bfly_per_s = res[0][0];
+    if (bfly_per_sm_cycle) *bfly_per_sm_cycle = res[0][1];
+    if (mad128_per_s) *mad128_per_s = res[1][0];
+    if (mad128_per_sm_cycle) *mad128_per_sm_cycle = res[1][1];
+    return BLB_OK;
+}
