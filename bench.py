@@ -390,6 +390,89 @@ def conversion_bench(w, reps):
     return out
 
 
+def cfg4_batching(n_seqs=8, plain_chunks=6, candidates=(16, 32, 64, 128), groups=(1, 2, 4, 8, 16)):
+    """Batching of uneven-length BERT-large-shaped sequences of one client:
+    n_seqs sequences with lengths U[16, 512] (seeded), hidden 1024, FFN 4096;
+    the ct-pt products QKV (1024 x 3072), FFN up (1024 x 4096) and FFN down
+    (4096 x 1024) over all their tokens, cut into m = 32-row chunks (one
+    ciphertext holds a chunk's 1024 features), N = 2^16, 12 primes, dnum 4.
+    Batched: a group of chunks per blb_matmul_cp_batch call, every plaintext
+    streamed once per group (at most 8 chunks per MAC launch).  Plain: one
+    chunk per call.  b1 (baby steps, b1 G = 1024) and the group size are
+    autotuned per product by timing every pair on the product."""
+    import torch
+    from paper_2508_19525_b300 import batching as bt
+    from paper_2508_19525_b300 import blb
+    from paper_2508_19525_b300 import workloads as wl
+    prm = wl.BERT_CC
+    stream = torch.cuda.Stream()
+    ctx = blb.Context(prm.logN, prm.q_bits, prm.p_bits, prm.dnum, prm.scale, stream=stream)
+    m, level = 32, ctx.nQ - 1
+    k = ctx.N // 2 // m
+    rng = np.random.default_rng(44)
+    lengths = rng.integers(16, 513, n_seqs)
+    T = int(lengths.sum())
+    t0 = time.perf_counter()
+    rots = sorted({r for b1 in candidates for r in bt.cp_rotations(m, k, b1)})
+    keys = ctx.keygen(6, rots)
+    ctx.sync()
+    keygen_s = time.perf_counter() - t0
+    products = [("qkv", 1024, 3072, 41), ("ffn_up", 1024, 4096, 42), ("ffn_down", 4096, 1024, 43)]
+    out = {"workload": f"{n_seqs} BERT-large-shaped sequences, lengths U[16,512] (total {T} tokens), "
+                       f"QKV 1024x3072 + FFN 1024x4096 + 4096x1024 ct-pt products, m={m}-row chunks, "
+                       f"N=2^16, 12 primes, dnum 4", "lengths": [int(x) for x in lengths], "tokens": T,
+           "rotation_keys": len(rots),
+           "keygen_s": round(keygen_s, 2), "products": {}}
+    tot_b = tot_p = 0.0
+    for name, d, d_out, seed in products:
+        X = wl.uniform((T, d), seed=seed)
+        W = wl.uniform((d, d_out), seed=seed + 100)
+        n_cts = d // k
+        Z = bt.pack_chunks(X, m, k, n_cts)
+        chunks = [ctx.encrypt_batch(keys, ctx.encode_batch(Z[c], level), [1000 * c + i for i in range(n_cts)])
+                  for c in range(len(Z))]
+        grp = [x for x in groups if x * n_cts * 128 * ctx.N * 8 * 2 * ctx.nQ < 40e9] or [1]
+        (b1, g), tune = bt.autotune(ctx, keys, m, d, W, d_out, level, chunks, candidates, grp)
+        plan = ctx.cp_plan(m, d, W, d_out, level, b1)
+        bt.run_batched(ctx, keys, plan, chunks[:g], g)
+        ctx.sync()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        Y = bt.run_batched(ctx, keys, plan, chunks, g)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        batched_s = ev0.elapsed_time(ev1) / 1e3
+        npl = min(plain_chunks, len(chunks))
+        ev0.record(stream)
+        for c in range(npl):
+            ctx.matmul_cp_plan(keys, plan, chunks[c])
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        plain_per_chunk = ev0.elapsed_time(ev1) / 1e3 / npl
+        err = 0.0
+        for c in (0, len(chunks) - 1):
+            got = bt.unpack_chunk([ctx.decrypt(keys, y, coeffs=False)[1] for y in Y[c]], m, k, d_out)
+            rows = min(m, T - c * m)
+            err = max(err, float(np.abs(got[:rows] - X[c * m:c * m + rows] @ W).max()))
+        out["products"][name] = {
+            "b1": b1, "G": k // b1,
+            "autotune_s_per_chunk": {f"b1={b},group={gg}": round(t, 4) for (b, gg), t in tune.items()},
+            "chunks": len(chunks), "chunks_per_call": g,
+            "batched_s": round(batched_s, 3), "batched_tokens_per_s": round(T / batched_s, 1),
+            "plain_s_per_chunk": round(plain_per_chunk, 4),
+            "plain_tokens_per_s": round(m / plain_per_chunk, 1),
+            "speedup": round(plain_per_chunk * len(chunks) / batched_s, 3),
+            "plaintext_bytes": plan.info()["plaintext_bytes"], "max_abs_err_vs_fp64": err}
+        tot_b += batched_s
+        tot_p += plain_per_chunk * len(chunks)
+        del chunks, Y
+        plan.free()
+    out["batched_tokens_per_s"] = round(T / tot_b, 1)
+    out["plain_tokens_per_s"] = round(T / tot_p, 1)
+    out["speedup"] = round(tot_p / tot_b, 3)
+    return out
+
+
 def layernorm_bench(steps, seqs=(1, 8)):
     """The HE steps of the secure LayerNorm before rsqrt (Alg. LayerNorm lines
     1-6) on BERT-base activations: 128 tokens x 768 features packed
@@ -557,6 +640,7 @@ def run_blb(args):
         batched = {"sequences_per_step": args.batch, "value": round(bval, 3), "unit": UNIT,
                    "ms_per_step": round(bsec * 1e3 / bsteps, 3), "speedup_vs_plain": round(bval / value, 3)}
     conv = conversion_bench(w, 20) if args.conversion else None
+    cfg4 = cfg4_batching(args.cfg4_seqs) if args.cfg4_seqs and world == 1 else None
     lnorm = layernorm_bench(max(2, min(10, args.steps // 5))) if args.layernorm and world == 1 else None
     attn = attention_cc(max(1, min(5, args.steps // 4))) if args.attention and world == 1 else None
     serving = serving_bench() if args.serving and world == 1 else None
@@ -618,6 +702,7 @@ def run_blb(args):
         "attention_cc": attn,
         "serving": serving,
         "layernorm_head": lnorm,
+        "cfg4_batching": cfg4,
         "conversion": dict(conv, sites={k: dict(v, frac_of_hbm=round(v["achieved_gbs"] / hbm, 4), peak_kind=peak_note)
                                         for k, v in conv["sites"].items()}) if conv else None,
         "counts_per_step": w.counts(),
@@ -802,6 +887,8 @@ def main():
     ap.add_argument("--batch", type=int, default=8, help="sequences per batched step (1 = skip)")
     ap.add_argument("--no-attention", dest="attention", action="store_false",
                     help="skip the matmul_cc attention measurement")
+    ap.add_argument("--cfg4-seqs", type=int, default=8,
+                    help="BERT-large uneven-length sequences of the batching measurement (0 = skip; 32 = the full config)")
     ap.add_argument("--no-layernorm", dest="layernorm", action="store_false",
                     help="skip the LayerNorm-head (rotate-and-sum) measurement")
     ap.add_argument("--no-conversion", dest="conversion", action="store_false",

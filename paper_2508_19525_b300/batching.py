@@ -1,0 +1,101 @@
+"""Batched ciphertext-plaintext products over many uneven-length sequences of
+one client.
+
+matmul_cp (Sec. 4.2.1 / 5.2) multiplies every row (token) of the activation
+by the same weight matrix, independently of the other rows, so the tokens of
+all sequences of a batch are laid end to end and cut into chunks of m rows:
+chunk c holds tokens [c m, (c+1) m) of the concatenation (the last chunk is
+zero-padded).  Every chunk is packed spatial-first like one m-row activation
+(ciphertext i holds columns [i k, (i+1) k), k = N/(2m), column j of the chunk
+at slots [j m, (j+1) m) of its ciphertext), so one plan serves every chunk,
+whatever the sequence lengths, and the batched product
+(blb_matmul_cp_batch) streams each plaintext diagonal once for a whole group
+of chunks.  Attention (matmul_cc) mixes the rows of one sequence and stays
+per sequence.
+
+The split of each product's rotations into baby and giant steps (b1, G with
+b1 G = k) and the number of chunks per batched call are chosen by `autotune`:
+every b1 candidate is encoded and every (b1, group) pair timed on the product
+itself, the fastest kept.  The group size matters because the plaintext MAC
+reads each plaintext once per call but its epilogue work grows with the number
+of chunks per call: for products with few terms per output a large group
+turns the MAC from memory-bound into compute-bound.
+"""
+import time
+
+import numpy as np
+
+
+def chunk_layout(lengths, m):
+    """Token t of sequence s -> (chunk, row).  Returns (starts, n_chunks):
+    starts[s] is the global index of the sequence's first token."""
+    starts = np.concatenate([[0], np.cumsum(lengths)[:-1]]).astype(np.int64)
+    total = int(np.sum(lengths))
+    return starts, -(-total // m)
+
+
+def pack_chunks(X, m, k, n_cts):
+    """X: (T, d) tokens -> (n_chunks, n_cts, m k) slot vectors."""
+    T, d = X.shape
+    n_chunks = -(-T // m)
+    Z = np.zeros((n_chunks, n_cts, m * k))
+    Xp = np.zeros((n_chunks * m, n_cts * k))
+    Xp[:T, :d] = X
+    for c in range(n_chunks):
+        blk = Xp[c * m:(c + 1) * m]                  # m x (n_cts k)
+        for i in range(n_cts):
+            Z[c, i] = blk[:, i * k:(i + 1) * k].T.reshape(-1)
+    return Z
+
+
+def unpack_chunk(slots, m, k, d_out):
+    """slots: (n_out_cts, m k) of one chunk -> (m, d_out)."""
+    cols = [z.reshape(k, m).T for z in slots]
+    return np.concatenate(cols, axis=1)[:, :d_out]
+
+
+def cp_rotations(m, k, b1):
+    """Rotations of one plan: baby steps b m (b < b1), giant steps g b1 m."""
+    G = k // b1
+    return [b * m for b in range(1, b1)] + [g * b1 * m for g in range(1, G)]
+
+
+def run_batched(ctx, keys, plan, chunks, group):
+    """chunks: list of per-chunk input ciphertext lists.  Runs the product in
+    groups of `group` chunks; returns the per-chunk output lists."""
+    out = []
+    for g0 in range(0, len(chunks), group):
+        part = chunks[g0:g0 + group]
+        out += ctx.matmul_cp_batch(keys, plan, part) if len(part) > 1 else [ctx.matmul_cp_plan(keys, plan, part[0])]
+    return out
+
+
+def autotune(ctx, keys, m, d, W, d_out, level, chunks, b1_candidates, group_candidates, reps=1):
+    """Encode the plan for every baby-step count b1 (powers of two dividing
+    k = N/(2m)) and time the product on `chunks` for every group size (chunks
+    per call; 1 is the plain product); return ((b1, group), {(b1, group):
+    seconds per chunk})."""
+    from .blb import BlbError
+    timings = {}
+    for b1 in b1_candidates:
+        try:
+            plan = ctx.cp_plan(m, d, W, d_out, level, b1)
+        except BlbError:
+            continue                                             # shape the library refuses
+        for group in group_candidates:
+            g = min(group, len(chunks))
+            try:
+                run_batched(ctx, keys, plan, chunks[:g], g)      # warm-up
+            except BlbError:
+                break
+            ctx.sync()
+            t0 = time.perf_counter()
+            for _ in range(reps):
+                run_batched(ctx, keys, plan, chunks[:g], g)
+            ctx.sync()
+            timings[(b1, group)] = (time.perf_counter() - t0) / (reps * g)
+        plan.free()
+    if not timings:
+        raise ValueError("no candidate (b1, group) runs on this product")
+    best = min(timings, key=timings.get)
+    return best, timings

@@ -1,0 +1,44 @@
+"""Token-chunked batching on the GPU: uneven-length sequences cut into m-row
+chunks; the batched product equals the per-chunk product limb for limb and
+every token's output is X W within 1e-4; the autotuner returns a measured
+(b1, chunks per call) choice whose results decode to the same product."""
+import numpy as np
+import pytest
+
+from paper_2508_19525_b300 import batching as bt
+from paper_2508_19525_b300 import workloads as wl
+
+from _helpers import make_ctx
+
+pytestmark = pytest.mark.gpu
+SEED = 0xBA7C
+
+
+def test_batched_chunks_equal_plain_and_fp64():
+    prm = wl.SMALL
+    ctx = make_ctx(prm)
+    m, d, d_out = 8, 64, 96
+    s = ctx.N // 2
+    k = s // m
+    lengths = [3, 17, 9, 30, 1, 12]
+    rng = np.random.default_rng(2)
+    X = rng.uniform(-1, 1, (sum(lengths), d))
+    W = rng.uniform(-1, 1, (d, d_out))
+    level = ctx.nQ - 1
+    n_cts = -(-d // k)
+    cands = (8, 16)
+    keys = ctx.keygen(SEED, sorted({r for b1 in cands for r in bt.cp_rotations(m, k, b1)}))
+    Z = bt.pack_chunks(X, m, k, n_cts)
+    chunks = [ctx.encrypt_batch(keys, ctx.encode_batch(Z[c], level), [100 * c + i for i in range(n_cts)])
+              for c in range(len(Z))]
+    (b1, group), timings = bt.autotune(ctx, keys, m, d, W, d_out, level, chunks, cands, (1, 2, 4))
+    assert b1 in cands and group in (1, 2, 4) and len(timings) == 6 and all(t > 0 for t in timings.values())
+    plan = ctx.cp_plan(m, d, W, d_out, level, b1)
+    batched = bt.run_batched(ctx, keys, plan, chunks, 4)
+    plain = [ctx.matmul_cp_plan(keys, plan, ch) for ch in chunks]
+    for c in range(len(chunks)):
+        for yb, yp in zip(batched[c], plain[c]):
+            assert np.array_equal(ctx.ct_export(yb), ctx.ct_export(yp)), c
+    Y = np.concatenate([bt.unpack_chunk([ctx.decrypt(keys, y, coeffs=False)[1] for y in batched[c]], m, k, d_out)
+                        for c in range(len(chunks))])[:len(X)]
+    assert np.abs(Y - X @ W).max() < 1e-4
