@@ -423,7 +423,7 @@ def cfg4_batching(n_seqs=8, plain_chunks=6, candidates=(16, 32, 64, 128), groups
                        f"N=2^16, 12 primes, dnum 4", "lengths": [int(x) for x in lengths], "tokens": T,
            "rotation_keys": len(rots),
            "keygen_s": round(keygen_s, 2), "products": {}}
-    tot_b = tot_p = 0.0
+    tot_b = tot_p = tot_g = 0.0
     for name, d, d_out, seed in products:
         X = wl.uniform((T, d), seed=seed)
         W = wl.uniform((d, d_out), seed=seed + 100)
@@ -449,6 +449,21 @@ def cfg4_batching(n_seqs=8, plain_chunks=6, candidates=(16, 32, 64, 128), groups
         ev1.record(stream)
         torch.cuda.synchronize()
         plain_per_chunk = ev0.elapsed_time(ev1) / 1e3 / npl
+        # the product over every chunk captured once as one CUDA graph (the
+        # arenas are already sized by the eager run), replayed and timed
+        l0 = blb.kernel_launches()
+        graph, Yg = ctx.capture(lambda: bt.run_batched(ctx, keys, plan, chunks, g), warmup=False)
+        graph_kernels = blb.kernel_launches() - l0
+        with torch.cuda.stream(stream):
+            graph.replay()
+            ev0.record(stream)
+            graph.replay()
+            ev1.record(stream)
+        torch.cuda.synchronize()
+        graph_s = ev0.elapsed_time(ev1) / 1e3
+        graph_same = all(np.array_equal(ctx.ct_export(a), ctx.ct_export(b))
+                         for c in (0, len(chunks) - 1) for a, b in zip(Yg[c], Y[c]))
+        del graph, Yg
         err = 0.0
         for c in (0, len(chunks) - 1):
             got = bt.unpack_chunk([ctx.decrypt(keys, y, coeffs=False)[1] for y in Y[c]], m, k, d_out)
@@ -462,12 +477,17 @@ def cfg4_batching(n_seqs=8, plain_chunks=6, candidates=(16, 32, 64, 128), groups
             "plain_s_per_chunk": round(plain_per_chunk, 4),
             "plain_tokens_per_s": round(m / plain_per_chunk, 1),
             "speedup": round(plain_per_chunk * len(chunks) / batched_s, 3),
+            "graph_s": round(graph_s, 3), "graph_tokens_per_s": round(T / graph_s, 1),
+            "graph_kernel_nodes": int(graph_kernels), "graph_equals_eager": bool(graph_same),
             "plaintext_bytes": plan.info()["plaintext_bytes"], "max_abs_err_vs_fp64": err}
         tot_b += batched_s
+        tot_g += graph_s
         tot_p += plain_per_chunk * len(chunks)
         del chunks, Y
         plan.free()
     out["batched_tokens_per_s"] = round(T / tot_b, 1)
+    out["graph_tokens_per_s"] = round(T / tot_g, 1)
+    out["graph_speedup_vs_plain"] = round(tot_p / tot_g, 3)
     out["plain_tokens_per_s"] = round(T / tot_p, 1)
     out["speedup"] = round(tot_p / tot_b, 3)
     return out

@@ -136,6 +136,10 @@ int blb_ct_export(blb_ctx* ctx, const blb_ct* ct, uint64_t* out);
  * npolys x (level+1) x N, residues in [0, q_i)). */
 int blb_ct_import(blb_ctx* ctx, const uint64_t* coeffs, uint32_t level, uint32_t npolys,
                   double scale, blb_ct** out);
+/* Overwrite dst's limbs (and scale) with src's, in the context's stream order
+ * (both of one level and size).  Useful to feed new inputs to ciphertexts a
+ * captured CUDA graph reads. */
+int blb_ct_copy(blb_ctx* ctx, blb_ct* dst, const blb_ct* src);
 /* Decrypt (m = c0 + c1 s [+ c2 s^2]).  coeff_limbs (nullable, host or device):
  * (level+1) x N words, coefficient form.  slots (nullable, host or device):
  * N/2 doubles, the decoding of the q_0 limb lifted to (-q_0/2, q_0/2] and divided
@@ -366,6 +370,18 @@ int blb_pt_import(blb_ctx* ctx, const uint64_t* coeffs, uint32_t level, double s
 /* a + b for a plaintext at the ciphertext's level or above (first polynomial
  * only); the scales must match. */
 int blb_add_plain(blb_ctx* ctx, const blb_ct* a, const blb_pt* b, blb_ct** out);
+
+/* ---- CUDA graphs ---------------------------------------------------------------
+ * Every call that runs only kernels on device data (the matmul_cp / matmul_cc
+ * products and their batched forms, key switching, rescale, the element-wise
+ * operations) can be captured into a CUDA graph on the context's stream, with
+ * the capture in relaxed mode and an allocator that serves stream-ordered
+ * allocations of the capture from a private pool (the binding does this with
+ * PyTorch's graph capture).  During a capture the key-switch tables go to
+ * buffers of their own (freed with the context); the key-switch arena must
+ * already be large enough, so run the call once before capturing it
+ * (BLB_ERR_ARG otherwise).  Ciphertexts created during the capture hold the
+ * results of the latest replay and must outlive the graph. */
 
 /* ---- batches of the calls above -----------------------------------------------
  * Each computes, for every member, exactly what the single call computes (same

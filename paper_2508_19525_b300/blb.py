@@ -69,6 +69,7 @@ SIGNATURES = {
     "blb_ct_export": (ctypes.c_int, [_vp, _vp, _vp]),
     "blb_ct_import": (ctypes.c_int, [_vp, _vp, _u32, _u32, _dbl, _pp]),
     "blb_decrypt": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
+    "blb_ct_copy": (ctypes.c_int, [_vp, _vp, _vp]),
     "blb_encode_batch": (ctypes.c_int, [_vp, _vp, _u64, _u32, _u32, _dbl, _vp]),
     "blb_encrypt_batch": (ctypes.c_int, [_vp, _vp, _vp, _u32, _vp, _vp]),
     "blb_he2mpc_batch": (ctypes.c_int, [_vp, _vp, _vp, _u32, _vp, _vp, _vp]),
@@ -394,6 +395,26 @@ class Context:
 
     def add(self, a, b):
         return self._new(Ciphertext, lib().blb_add, a.h, b.h)
+
+    def ct_copy(self, dst, src):
+        _check(lib().blb_ct_copy(self.h, dst.h, src.h))
+
+    def capture(self, fn, warmup=True):
+        """Run fn once (sizing the library's arenas), then capture it into a
+        CUDA graph on the context's stream; PyTorch's graph-private pool serves
+        the library's allocations.  Returns (graph, fn's result): graph.replay()
+        reruns every kernel on the same buffers, so the ciphertexts fn returned
+        hold the latest replay's result (keep them alive with the graph)."""
+        import torch
+        if self.stream == torch.cuda.default_stream(self.stream.device):
+            raise ValueError("graph capture needs a context created on a non-default stream")
+        if warmup:
+            fn()
+            self.sync()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=self.stream, capture_error_mode="relaxed"):
+            out = fn()
+        return g, out
 
     def add_plain(self, a, pt):
         return self._new(Ciphertext, lib().blb_add_plain, a.h, pt.h)

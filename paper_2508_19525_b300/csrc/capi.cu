@@ -16,6 +16,25 @@
 // library-internal helpers (declared in common.cuh)
 uint64_t* op_row(blb_ctx* c, size_t r) { return c->op_scratch() + r * c->N; }
 
+bool capturing(blb_ctx* c)
+{
+    cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+    return cudaStreamIsCapturing(c->stream, &st) == cudaSuccess && st == cudaStreamCaptureStatusActive;
+}
+
+int persist_upload(blb_ctx* c, const void* host, size_t bytes, void** dev)
+{
+    *dev = nullptr;
+    if (!c->upload_stream) BLB_CUDA(cudaStreamCreateWithFlags(&c->upload_stream, cudaStreamNonBlocking));
+    BLB_CUDA(cudaMalloc(dev, bytes ? bytes : 16));
+    c->graph_keep.push_back({*dev, 0});
+    if (bytes) {
+        BLB_CUDA(cudaMemcpyAsync(*dev, host, bytes, cudaMemcpyHostToDevice, c->upload_stream));
+        BLB_CUDA(cudaStreamSynchronize(c->upload_stream));
+    }
+    return BLB_OK;
+}
+
 void* Scratch::get(size_t bytes)
 {
     bytes = std::max<size_t>(bytes, 16);
@@ -457,6 +476,16 @@ extern "C" int blb_rescale(blb_ctx* c, blb_ct* ct)
     ct->bytes = bytes;
     ct->scale /= (double)c->q[ct->level];
     ct->level -= 1;
+    return BLB_OK;
+}
+
+extern "C" int blb_ct_copy(blb_ctx* c, blb_ct* dst, const blb_ct* src)
+{
+    if (!c || !dst || !src) return blb_fail(BLB_ERR_ARG, "null argument");
+    if (dst->level != src->level || dst->npolys != src->npolys)
+        return blb_fail(BLB_ERR_ARG, "copy needs ciphertexts of one level and size");
+    BLB_CUDA(cudaMemcpyAsync(dst->d, src->d, src->bytes, cudaMemcpyDeviceToDevice, c->stream));
+    dst->scale = src->scale;
     return BLB_OK;
 }
 

@@ -199,6 +199,13 @@ struct blb_ctx {
     uint64_t* scratch = nullptr;
     size_t scratch_words = 0;
     size_t bytes_in_use = 0;
+    // CUDA-graph capture of the context's stream: tables uploaded during a
+    // capture live in buffers of their own (graph_keep, freed with the
+    // context), filled through a private non-blocking stream; once anything
+    // was captured, a grown key-switch arena keeps the old one alive too
+    cudaStream_t upload_stream = nullptr;
+    std::vector<std::pair<void*, size_t>> graph_keep;  // (pointer, bytes); bytes 0 = cudaMalloc'd
+    bool captured = false;
     // lifetime: objects (keys, plaintexts, ciphertexts, plans) hold the
     // context; blb_ctx_free releases it once the last of them is freed
     uint64_t live_objects = 0;
@@ -294,6 +301,11 @@ void ctx_retain(blb_ctx* ctx);
 void ctx_release(blb_ctx* ctx);
 void dev_free(blb_ctx* ctx, void* p, size_t bytes);
 bool is_device_ptr(const void* p);
+// is the context's stream being captured into a CUDA graph?
+bool capturing(blb_ctx* ctx);
+// host data into a device buffer that outlives every replay of the graph being
+// captured (freed with the context); synchronous
+int persist_upload(blb_ctx* ctx, const void* host, size_t bytes, void** dev);
 
 uint64_t host_mulmod(uint64_t a, uint64_t b, uint64_t q);
 uint64_t host_powmod(uint64_t b, uint64_t e, uint64_t q);

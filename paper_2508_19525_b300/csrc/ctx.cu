@@ -549,6 +549,11 @@ static void ctx_destroy(blb_ctx* c)
     dev_free(c, c->d_kperm, (size_t)c->N / 2 * 4);
     dev_free(c, c->d_flag, sizeof(int));
     dev_free(c, c->d_status, sizeof(uint32_t));
+    for (auto& k : c->graph_keep) {
+        if (k.second) dev_free(c, k.first, k.second);
+        else cudaFree(k.first);
+    }
+    if (c->upload_stream) cudaStreamDestroy(c->upload_stream);
     dev_free(c, c->d_fx_root, (size_t)c->N * sizeof(int2));
     dev_free(c, c->d_kinv, (size_t)c->N / 2 * 4);
     for (auto& t : c->fx_twist) dev_free(c, t.d, (size_t)c->N / 2 * sizeof(int2));

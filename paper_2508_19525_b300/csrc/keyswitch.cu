@@ -14,6 +14,7 @@
 // digit modulus, which the key's gadget factor cancels).  Every step is an exact integer function of d's
 // coefficients, so any correct schedule of it yields the same limbs.
 #include <algorithm>
+#include <cstring>
 #include <mutex>
 #include <string>
 
@@ -492,10 +493,18 @@ int ks_run(blb_ctx* ctx, uint32_t level, const KsSource* sources, uint32_t n_src
         const size_t table_words = words(hs.size() * sizeof(DevSource)) + words(hp.size() * sizeof(DevProduct)) +
                                    words(hg.size() * sizeof(DevGroup)) + words(ha.size() * sizeof(KsAdd)) +
                                    words((ext_rows.size() + p_rows.size()) * 4) + 8;
-        const size_t need = (size_t)ns * per_src + (size_t)ng * per_grp + table_words;
+        const bool cap = capturing(ctx);
+        if (cap) ctx->captured = true;
+        // under capture the tables go to a buffer of their own, so the arena
+        // holds only the data every replay rewrites
+        const size_t need = (size_t)ns * per_src + (size_t)ng * per_grp + (cap ? 0 : table_words);
         if (need > ctx->batch_words) {
+            if (cap)
+                return blb_fail(BLB_ERR_ARG, "key-switch arena too small during graph capture: run the call once "
+                                             "before capturing it");
             BLB_CUDA(cudaStreamSynchronize(ctx->stream));  // the arena may still be read by earlier launches
-            dev_free(ctx, ctx->batch, ctx->batch_words * 8);
+            if (ctx->captured) ctx->graph_keep.push_back({ctx->batch, ctx->batch_words * 8});  // graphs read it
+            else dev_free(ctx, ctx->batch, ctx->batch_words * 8);
             ctx->batch = (uint64_t*)dev_alloc(ctx, need * 8);
             ctx->batch_words = ctx->batch ? need : 0;
             if (!ctx->batch) return blb_fail(BLB_ERR_OOM, "key-switch batch arena");
@@ -505,7 +514,13 @@ int ks_run(blb_ctx* ctx, uint32_t level, const KsSource* sources, uint32_t n_src
         uint64_t* ext = coef + (size_t)ns * n * N;
         uint64_t* acc = ext + (size_t)ns * beta * E * N;
         uint64_t* cv = acc + (size_t)ng * 2 * E * N;
+        std::vector<uint64_t> host_tables;
         uint64_t* tw = cv + (size_t)ng * 2 * n * N;
+        uint64_t* tw0 = tw;
+        if (cap) {
+            host_tables.assign(table_words, 0);
+            tw = tw0 = host_tables.data();
+        }
         DevSource* d_src = (DevSource*)tw;
         tw += words(hs.size() * sizeof(DevSource));
         DevProduct* d_prod = (DevProduct*)tw;
@@ -516,15 +531,34 @@ int ks_run(blb_ctx* ctx, uint32_t level, const KsSource* sources, uint32_t n_src
         tw += words(ha.size() * sizeof(KsAdd));
         uint32_t* d_ext_rows = (uint32_t*)tw;
         uint32_t* d_p_rows = d_ext_rows + ext_rows.size();
-        auto up = [&](void* dst, const void* src, size_t bytes) {
-            return bytes ? cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, ctx->stream) : cudaSuccess;
-        };
-        BLB_CUDA(up(d_src, hs.data(), hs.size() * sizeof(DevSource)));
-        BLB_CUDA(up(d_prod, hp.data(), hp.size() * sizeof(DevProduct)));
-        BLB_CUDA(up(d_grp, hg.data(), hg.size() * sizeof(DevGroup)));
-        BLB_CUDA(up(d_add, ha.data(), ha.size() * sizeof(KsAdd)));
-        BLB_CUDA(up(d_ext_rows, ext_rows.data(), ext_rows.size() * 4));
-        BLB_CUDA(up(d_p_rows, p_rows.data(), p_rows.size() * 4));
+        if (cap) {
+            // fill the host image, copy it once, and point every table into the copy
+            memcpy(d_src, hs.data(), hs.size() * sizeof(DevSource));
+            memcpy(d_prod, hp.data(), hp.size() * sizeof(DevProduct));
+            memcpy(d_grp, hg.data(), hg.size() * sizeof(DevGroup));
+            memcpy(d_add, ha.data(), ha.size() * sizeof(KsAdd));
+            memcpy(d_ext_rows, ext_rows.data(), ext_rows.size() * 4);
+            memcpy(d_p_rows, p_rows.data(), p_rows.size() * 4);
+            void* dev = nullptr;
+            BLB_TRY(persist_upload(ctx, host_tables.data(), table_words * 8, &dev));
+            auto rebase = [&](auto* p) { return (decltype(p))((uint8_t*)dev + ((uint8_t*)p - (uint8_t*)tw0)); };
+            d_src = rebase(d_src);
+            d_prod = rebase(d_prod);
+            d_grp = rebase(d_grp);
+            d_add = rebase(d_add);
+            d_ext_rows = rebase(d_ext_rows);
+            d_p_rows = rebase(d_p_rows);
+        } else {
+            auto up = [&](void* dst, const void* src, size_t bytes) {
+                return bytes ? cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, ctx->stream) : cudaSuccess;
+            };
+            BLB_CUDA(up(d_src, hs.data(), hs.size() * sizeof(DevSource)));
+            BLB_CUDA(up(d_prod, hp.data(), hp.size() * sizeof(DevProduct)));
+            BLB_CUDA(up(d_grp, hg.data(), hg.size() * sizeof(DevGroup)));
+            BLB_CUDA(up(d_add, ha.data(), ha.size() * sizeof(KsAdd)));
+            BLB_CUDA(up(d_ext_rows, ext_rows.data(), ext_rows.size() * 4));
+            BLB_CUDA(up(d_p_rows, p_rows.data(), p_rows.size() * 4));
+        }
         // algorithmic bytes: each source read and its digits written once; each
         // product reads its digits and key; each group writes its output
         ProfScope prof(ctx, "keyswitch",

@@ -42,3 +42,46 @@ def test_batched_chunks_equal_plain_and_fp64():
     Y = np.concatenate([bt.unpack_chunk([ctx.decrypt(keys, y, coeffs=False)[1] for y in batched[c]], m, k, d_out)
                         for c in range(len(chunks))])[:len(X)]
     assert np.abs(Y - X @ W).max() < 1e-4
+
+
+def test_captured_graph_replays_the_batched_product():
+    """The batched product over all chunks captured once: a replay gives the
+    eager result limb for limb, and after new inputs are copied into the same
+    ciphertexts a replay gives the eager result for those."""
+    import torch
+    from paper_2508_19525_b300 import blb
+    prm = wl.SMALL
+    ctx = blb.Context(prm.logN, prm.q_bits, prm.p_bits, prm.dnum, prm.scale, stream=torch.cuda.Stream())
+    m, d, d_out, b1 = 8, 64, 96, 8
+    s = ctx.N // 2
+    k = s // m
+    level = ctx.nQ - 1
+    keys = ctx.keygen(SEED, bt.cp_rotations(m, k, b1))
+    rng = np.random.default_rng(9)
+    W = rng.uniform(-1, 1, (d, d_out))
+    plan = ctx.cp_plan(m, d, W, d_out, level, b1)
+
+    def encrypt(X, base):
+        Z = bt.pack_chunks(X, m, k, 1)
+        return [ctx.encrypt_batch(keys, ctx.encode_batch(Z[c], level), [base + c]) for c in range(len(Z))]
+
+    X1, X2 = rng.uniform(-1, 1, (40, d)), rng.uniform(-1, 1, (40, d))
+    chunks, new = encrypt(X1, 0), encrypt(X2, 100)
+    graph, Yg = ctx.capture(lambda: bt.run_batched(ctx, keys, plan, chunks, 2))
+    graph.replay()
+    torch.cuda.synchronize()
+    eager = bt.run_batched(ctx, keys, plan, chunks, 2)
+    for a, b in zip(Yg, eager):
+        for ya, yb in zip(a, b):
+            assert np.array_equal(ctx.ct_export(ya), ctx.ct_export(yb))
+    for dst, src in zip(chunks, new):
+        ctx.ct_copy(dst[0], src[0])
+    graph.replay()
+    torch.cuda.synchronize()
+    eager2 = bt.run_batched(ctx, keys, plan, new, 2)
+    for a, b in zip(Yg, eager2):
+        for ya, yb in zip(a, b):
+            assert np.array_equal(ctx.ct_export(ya), ctx.ct_export(yb))
+    got = np.concatenate([bt.unpack_chunk([ctx.decrypt(keys, y, coeffs=False)[1] for y in Yg[c]], m, k, d_out)
+                          for c in range(len(Yg))])[:40]
+    assert np.abs(got - X2 @ W).max() < 1e-4
