@@ -199,6 +199,8 @@ class Workload:
         G = self.k // B1
         rots = [b * M for b in range(1, B1)] + [g * B1 * M for g in range(1, G)]
         self.keys = self.ctx.keygen(0, rots)
+        # pick the NTT pass split for this ring on the device before anything is timed
+        self.ntt_split, self.ntt_split_us = self.ctx.ntt_autotune(256)
         self.X, Wqkv, Wo = wl.bert_base_cp(seed=0)
         self.ref_qkv = self.X @ Wqkv
         self.ref_o = self.ref_qkv[:, :D_O] @ Wo
@@ -406,7 +408,12 @@ def cfg4_batching(n_seqs=8, plain_chunks=6, candidates=(16, 32, 64, 128), groups
     from paper_2508_19525_b300 import workloads as wl
     prm = wl.BERT_CC
     stream = torch.cuda.Stream()
-    ctx = blb.Context(prm.logN, prm.q_bits, prm.p_bits, prm.dnum, prm.scale, stream=stream)
+    # digit count of key switching, timed on the device (the special primes fix
+    # alpha = ceil(12 / dnum) <= 3, so dnum in {4, 6, 12})
+    dnum, dnum_t = bt.autotune_dnum(
+        lambda dn: blb.Context(prm.logN, prm.q_bits, prm.p_bits, dn, prm.scale, stream=stream), (4, 6, 12), 32)
+    ctx = blb.Context(prm.logN, prm.q_bits, prm.p_bits, dnum, prm.scale, stream=stream)
+    ntt_split, ntt_us = ctx.ntt_autotune(256)
     m, level = 32, ctx.nQ - 1
     k = ctx.N // 2 // m
     rng = np.random.default_rng(44)
@@ -420,8 +427,10 @@ def cfg4_batching(n_seqs=8, plain_chunks=6, candidates=(16, 32, 64, 128), groups
     products = [("qkv", 1024, 3072, 41), ("ffn_up", 1024, 4096, 42), ("ffn_down", 4096, 1024, 43)]
     out = {"workload": f"{n_seqs} BERT-large-shaped sequences, lengths U[16,512] (total {T} tokens), "
                        f"QKV 1024x3072 + FFN 1024x4096 + 4096x1024 ct-pt products, m={m}-row chunks, "
-                       f"N=2^16, 12 primes, dnum 4", "lengths": [int(x) for x in lengths], "tokens": T,
+                       f"N=2^16, 12 primes, dnum autotuned", "lengths": [int(x) for x in lengths], "tokens": T,
            "rotation_keys": len(rots),
+           "autotuned": {"dnum": dnum, "dnum_s_per_rotation": {str(k): round(v, 5) for k, v in dnum_t.items()},
+                         "ntt_split": ntt_split, "ntt_us_per_row_direction": {str(k): round(v, 4) for k, v in ntt_us.items()}},
            "keygen_s": round(keygen_s, 2), "products": {}}
     tot_b = tot_p = tot_g = 0.0
     for name, d, d_out, seed in products:
@@ -716,6 +725,7 @@ def run_blb(args):
         "gpu_launches": int(launches),
         "roofline": dict(roof[dominant], kernel=dominant, traffic=traffic) if dominant else None,
         "roofline_sites": roof,
+        "ntt_autotune": {"split": w.ntt_split, "us_per_row_direction": {str(k): round(v, 4) for k, v in w.ntt_split_us.items()}},
         "int_peaks": {k: (round(v / 1e9, 2) if k.endswith("_s") else round(v, 3)) for k, v in int_peaks.items()},
         "accuracy": {"max_abs_err_vs_fp64": max_err, "mse": mse, "bound": 1e-4},
         "batched": batched,

@@ -99,3 +99,36 @@ def autotune(ctx, keys, m, d, W, d_out, level, chunks, b1_candidates, group_cand
         raise ValueError("no candidate (b1, group) runs on this product")
     best = min(timings, key=timings.get)
     return best, timings
+
+
+def autotune_dnum(make_ctx, candidates, m, reps=3, rotations=8):
+    """Key-switch digit count: for every dnum in `candidates` build a context
+    (make_ctx(dnum)), keys for `rotations` rotations by multiples of m slots,
+    and time rotations of one ciphertext at the top level (each one a full
+    key switch: decomposition, ModUp, inner product, ModDown).  Returns (best dnum, {dnum:
+    seconds per rotation}).  Candidates the library refuses (more primes per
+    digit than special primes) are skipped."""
+    from .blb import BlbError
+    timings = {}
+    for dnum in candidates:
+        try:
+            ctx = make_ctx(dnum)
+        except BlbError:
+            continue
+        rots = [b * m for b in range(1, rotations + 1)]
+        keys = ctx.keygen(7, rots)
+        level = ctx.nQ - 1
+        ct = ctx.encrypt(keys, ctx.encode(np.ones(ctx.N // 2) * 0.5, level), 1)
+        for r in rots:                                    # warm-up
+            ctx.rotate(keys, ct, r)
+        ctx.sync()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            for r in rots:
+                ctx.rotate(keys, ct, r)
+        ctx.sync()
+        timings[dnum] = (time.perf_counter() - t0) / (reps * len(rots))
+        del keys, ct
+        ctx.free()
+    best = min(timings, key=timings.get)
+    return best, timings

@@ -106,6 +106,8 @@ SIGNATURES = {
     "blb_pt_import": (ctypes.c_int, [_vp, _vp, _u32, _dbl, _pp]),
     "blb_add_plain": (ctypes.c_int, [_vp, _vp, _vp, _pp]),
     "blb_ntt": (ctypes.c_int, [_vp, _vp, _u32, _vp, ctypes.c_int]),
+    "blb_ntt_autotune": (ctypes.c_int, [_vp, _u32, _vp, _vp]),
+    "blb_ntt_set_split": (ctypes.c_int, [_vp, ctypes.c_int]),
     "blb_kernel_launches": (_u64, []),
     "blb_int_peaks": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
     "blb_profile_enable": (ctypes.c_int, [_vp, ctypes.c_int]),
@@ -620,6 +622,16 @@ class Context:
         ms, cnt, nb = _dbl(), _u64(), _u64()
         _check(lib().blb_profile_read(self.h, site.encode(), ctypes.byref(ms), ctypes.byref(cnt), ctypes.byref(nb)))
         return ms.value, cnt.value, nb.value
+
+    def ntt_autotune(self, rows=64):
+        """Time the NTT's three pass splits; keep the fastest.  Returns
+        (split, {split: microseconds per row and direction})."""
+        sp, us = ctypes.c_int(), (_dbl * 3)()
+        _check(lib().blb_ntt_autotune(self.h, rows, ctypes.byref(sp), us))
+        return sp.value, {k - 1: us[k] for k in range(3) if us[k] > 0}
+
+    def ntt_set_split(self, split):
+        _check(lib().blb_ntt_set_split(self.h, int(split)))
 
     def ntt(self, data, prime_idx, inverse=False):
         data = np.ascontiguousarray(data, np.uint64).copy()

@@ -262,12 +262,15 @@ __global__ void __launch_bounds__(kThreads, 3) k_ntt(uint64_t* __restrict__ data
     }
 }
 
-template <int LOGN>
-int run_n(blb_ctx* ctx, uint64_t* data, uint32_t rows, const LimbMap& map, const uint32_t* rowlist, bool inverse)
+// One forward or inverse transform with the column pass over 2^L1-point
+// sub-transforms and the row pass over 2^(LOGN - L1) points (L1 = 0: one pass).
+template <int LOGN, int L1>
+int run_split(blb_ctx* ctx, uint64_t* data, uint32_t rows, const LimbMap& map, const uint32_t* rowlist, bool inverse)
 {
     constexpr uint32_t N = 1u << LOGN;
     constexpr uint32_t TILE = N < 4096 ? N : 4096;
-    constexpr int L1 = LOGN <= 12 ? 0 : LOGN / 2, L2 = LOGN - L1;
+    constexpr int L2 = LOGN - L1;
+    static_assert(L2 <= 12 && (L1 == 0 || L1 <= 12), "pass longer than a tile");
     const ulonglong2* tw = reinterpret_cast<const ulonglong2*>(ctx->d_tw);
     for (uint32_t y0 = 0; y0 < rows; y0 += kMaxGridY) {
         const dim3 grid(N / TILE, std::min(kMaxGridY, rows - y0));
@@ -294,6 +297,26 @@ int run_n(blb_ctx* ctx, uint64_t* data, uint32_t rows, const LimbMap& map, const
     return BLB_OK;
 }
 
+// Transforms above one tile have three splits around the middle, chosen per
+// context (ctx->ntt_split: 0 the middle, -1 / +1 a shorter / longer column
+// pass); blb_ntt_autotune times them.
+template <int LOGN>
+int run_n(blb_ctx* ctx, uint64_t* data, uint32_t rows, const LimbMap& map, const uint32_t* rowlist, bool inverse)
+{
+    if constexpr (LOGN <= 12) {
+        return run_split<LOGN, 0>(ctx, data, rows, map, rowlist, inverse);
+    } else {
+        constexpr int M = LOGN / 2;
+        switch (ctx->ntt_split) {
+        case -1: return run_split<LOGN, M - 1>(ctx, data, rows, map, rowlist, inverse);
+        case 1:
+            if constexpr (LOGN - (M + 1) >= 1) return run_split<LOGN, M + 1>(ctx, data, rows, map, rowlist, inverse);
+            else return run_split<LOGN, M>(ctx, data, rows, map, rowlist, inverse);
+        default: return run_split<LOGN, M>(ctx, data, rows, map, rowlist, inverse);
+        }
+    }
+}
+
 int run(blb_ctx* ctx, uint64_t* data, uint32_t rows, const LimbMap& map, const uint32_t* rowlist, bool inverse)
 {
     switch (ctx->logN) {
@@ -310,6 +333,59 @@ int run(blb_ctx* ctx, uint64_t* data, uint32_t rows, const LimbMap& map, const u
 }
 
 }  // namespace
+
+extern "C" int blb_ntt_autotune(blb_ctx* ctx, uint32_t rows, int* split_out, double* us_per_row)  // us_per_row[3]
+{
+    if (!ctx || rows == 0) return blb_fail(BLB_ERR_ARG, "null argument or no rows");
+    const size_t words = (size_t)rows * ctx->N;
+    uint64_t* buf = (uint64_t*)dev_alloc(ctx, words * 8);
+    if (!buf) return blb_fail(BLB_ERR_OOM, "autotune buffer");
+    BLB_CUDA(cudaMemsetAsync(buf, 0, words * 8, ctx->stream));
+    const LimbMap map = ctx->qmap(ctx->nQ);
+    cudaEvent_t e0, e1;
+    BLB_CUDA(cudaEventCreate(&e0));
+    BLB_CUDA(cudaEventCreate(&e1));
+    const int keep = ctx->ntt_split;
+    int best = 0, rc = BLB_OK;
+    float best_ms = 1e30f;
+    double per[3] = {0, 0, 0};
+    for (int sp = -1; sp <= 1 && !rc; sp++) {
+        if (ctx->logN <= 12 && sp) continue;
+        ctx->ntt_split = sp;
+        float ms = 0;
+        for (int rep = 0; rep < 3 && !rc; rep++) {  // the first run is a warm-up
+            cudaEventRecord(e0, ctx->stream);
+            rc = run(ctx, buf, rows, map, nullptr, false);
+            if (!rc) rc = run(ctx, buf, rows, map, nullptr, true);
+            cudaEventRecord(e1, ctx->stream);
+            if (!rc && cudaEventSynchronize(e1) != cudaSuccess) rc = blb_fail(BLB_ERR_CUDA, "autotune run failed");
+            float t = 0;
+            cudaEventElapsedTime(&t, e0, e1);
+            if (rep) ms += t;
+        }
+        per[sp + 1] = ms * 1e3 / (2.0 * 2.0 * rows);  // two timed runs, forward + inverse
+        if (!rc && ms < best_ms) {
+            best_ms = ms;
+            best = sp;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    dev_free(ctx, buf, words * 8);
+    ctx->ntt_split = rc ? keep : best;
+    if (rc) return rc;
+    if (split_out) *split_out = best;
+    if (us_per_row)
+        for (int k = 0; k < 3; k++) us_per_row[k] = per[k];
+    return BLB_OK;
+}
+
+extern "C" int blb_ntt_set_split(blb_ctx* ctx, int split)
+{
+    if (!ctx || split < -1 || split > 1) return blb_fail(BLB_ERR_ARG, "split must be -1, 0 or 1");
+    ctx->ntt_split = split;
+    return BLB_OK;
+}
 
 int ntt_forward(blb_ctx* ctx, uint64_t* data, uint32_t rows, const LimbMap& map)
 {
