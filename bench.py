@@ -502,6 +502,40 @@ def cfg4_batching(n_seqs=8, plain_chunks=6, candidates=(16, 32, 64, 128), groups
     return out
 
 
+def layer_bench():
+    """One BERT-base encoder layer the hybrid way (paper_2508_19525_b300/layer.py):
+    the linear operators in fused HE blocks (QKV, Q K^T, softmax exponential,
+    normalisation + P V + W_O + residual + LN1 head, LN1 tail + W_1 + GeLU
+    polynomials, W_2 + residual + LN2 head, LN2 tail) with CKKS <-> MPC
+    conversions at every boundary; MPC nonlinear steps simulated.  Returns the
+    seconds per segment (HE kernels; conversions + simulated MPC) and the error
+    against the FP64 layer with the same approximations."""
+    import torch
+    from paper_2508_19525_b300 import blb
+    from paper_2508_19525_b300 import layer as ly
+    from paper_2508_19525_b300 import workloads as wl
+    ctx = blb.Context(*[getattr(wl.BERT_CP, a) for a in ("logN", "q_bits", "p_bits", "dnum", "scale")])
+    big = blb.Context(*[getattr(wl.BERT_CC, a) for a in ("logN", "q_bits", "p_bits", "dnum", "scale")])
+    t0 = time.perf_counter()
+    lay = ly.BertLayer(ctx, big)
+    rs, rb = lay.rotations()
+    keys, keysb = ctx.keygen(21, rs, relin=True), big.keygen(22, rb, relin=True)
+    ctx.sync()
+    setup_s = time.perf_counter() - t0
+    X = np.random.default_rng(23).uniform(-1, 1, (lay.L, lay.d))
+    lay.forward(X, keys, keysb, ly.Mpc(24))                     # warm-up
+    Y, he, conv = lay.forward(X, keys, keysb, ly.Mpc(25))
+    err = float(np.abs(Y - lay.reference(X)).max())
+    del lay, keys, keysb
+    torch.cuda.empty_cache()
+    return {"workload": "BERT-base encoder layer (128 tokens, 768 hidden, 12 heads, FFN 3072): fused HE blocks "
+                        "on N=2^15 / 8 primes and N=2^16 / 12 primes, CKKS<->MPC conversions at every boundary, "
+                        "MPC nonlinear steps simulated",
+            "he_s": {k: round(v, 4) for k, v in he.items()}, "conversion_and_mpc_s": {k: round(v, 4) for k, v in conv.items()},
+            "he_total_s": round(sum(he.values()), 4), "conversion_total_s": round(sum(conv.values()), 4),
+            "setup_s": round(setup_s, 2), "rotation_keys": [len(rs), len(rb)], "max_abs_err_vs_fp64": err}
+
+
 def layernorm_bench(steps, seqs=(1, 8)):
     """The HE steps of the secure LayerNorm before rsqrt (Alg. LayerNorm lines
     1-6) on BERT-base activations: 128 tokens x 768 features packed
@@ -671,6 +705,7 @@ def run_blb(args):
     conv = conversion_bench(w, 20) if args.conversion else None
     cfg4 = cfg4_batching(args.cfg4_seqs) if args.cfg4_seqs and world == 1 else None
     lnorm = layernorm_bench(max(2, min(10, args.steps // 5))) if args.layernorm and world == 1 else None
+    layer = layer_bench() if args.layer and world == 1 else None
     attn = attention_cc(max(1, min(5, args.steps // 4))) if args.attention and world == 1 else None
     serving = serving_bench() if args.serving and world == 1 else None
     if rank != 0:
@@ -732,6 +767,7 @@ def run_blb(args):
         "attention_cc": attn,
         "serving": serving,
         "layernorm_head": lnorm,
+        "encoder_layer": layer,
         "cfg4_batching": cfg4,
         "conversion": dict(conv, sites={k: dict(v, frac_of_hbm=round(v["achieved_gbs"] / hbm, 4), peak_kind=peak_note)
                                         for k, v in conv["sites"].items()}) if conv else None,
@@ -919,6 +955,8 @@ def main():
                     help="skip the matmul_cc attention measurement")
     ap.add_argument("--cfg4-seqs", type=int, default=8,
                     help="BERT-large uneven-length sequences of the batching measurement (0 = skip; 32 = the full config)")
+    ap.add_argument("--no-layer", dest="layer", action="store_false",
+                    help="skip the hybrid encoder-layer measurement")
     ap.add_argument("--no-layernorm", dest="layernorm", action="store_false",
                     help="skip the LayerNorm-head (rotate-and-sum) measurement")
     ap.add_argument("--no-conversion", dest="conversion", action="store_false",

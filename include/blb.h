@@ -154,6 +154,19 @@ int blb_rotate(blb_ctx* ctx, const blb_keys* keys, const blb_ct* in, int32_t ste
 int blb_rescale(blb_ctx* ctx, blb_ct* inout);
 int blb_add(blb_ctx* ctx, const blb_ct* a, const blb_ct* b, blb_ct** out);
 int blb_mul_plain(blb_ctx* ctx, const blb_ct* a, const blb_pt* b, blb_ct** out);
+/* a - b (one level, size and scale). */
+int blb_sub(blb_ctx* ctx, const blb_ct* a, const blb_ct* b, blb_ct** out);
+/* The same message at a lower level: the limbs past `level` are dropped
+ * (modulus switching without scaling; the scale is kept). */
+int blb_drop_level(blb_ctx* ctx, const blb_ct* a, uint32_t level, blb_ct** out);
+/* a times the slot vector vals (n values: n = 1 broadcasts the one value to
+ * every slot, otherwise slots past n are 0), then rescaled: the constant is
+ * encoded at scale target_scale q_level / scale(a), so the result (one level
+ * down) has scale target_scale; this aligns the scales of terms that went
+ * through different numbers of rescales before they are added (the
+ * ewmul_cp / smul_cp operators of Sec. 4.1 with a chosen output scale). */
+int blb_mul_const(blb_ctx* ctx, const blb_ct* a, const double* vals, uint64_t n, double target_scale,
+                  blb_ct** out);
 /* ct x ct: tensor product (3 polynomials) followed by relinearization when
  * relin != 0 (needs the relinearization key). */
 int blb_mul(blb_ctx* ctx, const blb_keys* keys, const blb_ct* a, const blb_ct* b, int relin,

@@ -78,6 +78,9 @@ SIGNATURES = {
     "blb_rescale": (ctypes.c_int, [_vp, _vp]),
     "blb_add": (ctypes.c_int, [_vp, _vp, _vp, _pp]),
     "blb_mul_plain": (ctypes.c_int, [_vp, _vp, _vp, _pp]),
+    "blb_sub": (ctypes.c_int, [_vp, _vp, _vp, _pp]),
+    "blb_drop_level": (ctypes.c_int, [_vp, _vp, _u32, _pp]),
+    "blb_mul_const": (ctypes.c_int, [_vp, _vp, _vp, _u64, _dbl, _pp]),
     "blb_mul": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.c_int, _pp]),
     "blb_relinearize": (ctypes.c_int, [_vp, _vp, _vp, _pp]),
     "blb_keyswitch_coeffs": (ctypes.c_int, [_vp, _vp, _i32, _vp, _u32, _vp]),
@@ -499,6 +502,19 @@ class Context:
         _check(lib().blb_m2c_local(self.h, party, _ptr(x), _ptr(wsh), n, count, level, _dbl(scale), l, sf,
                                    _ptr(out)))
         return out
+
+    def sub(self, a, b):
+        return self._new(Ciphertext, lib().blb_sub, a.h, b.h)
+
+    def drop_level(self, a, level):
+        return self._new(Ciphertext, lib().blb_drop_level, a.h, level)
+
+    def mul_const(self, a, vals, target_scale=None):
+        """a times the slot vector vals (a scalar broadcasts), rescaled to
+        target_scale (default: a's scale)."""
+        v = np.ascontiguousarray(np.atleast_1d(vals), np.float64)
+        ts = a.scale if target_scale is None else target_scale
+        return self._new(Ciphertext, lib().blb_mul_const, a.h, v.ctypes.data, _u64(len(v)), _dbl(ts))
 
     def mul_plain(self, a, pt):
         return self._new(Ciphertext, lib().blb_mul_plain, a.h, pt.h)

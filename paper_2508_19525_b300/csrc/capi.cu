@@ -528,6 +528,73 @@ extern "C" int blb_add_plain(blb_ctx* c, const blb_ct* a, const blb_pt* p, blb_c
     return BLB_OK;
 }
 
+extern "C" int blb_sub(blb_ctx* c, const blb_ct* a, const blb_ct* b, blb_ct** out)
+{
+    if (!c || !a || !b || !out) return blb_fail(BLB_ERR_ARG, "null argument");
+    if (a->level != b->level || a->npolys != b->npolys) return blb_fail(BLB_ERR_ARG, "level or size mismatch");
+    if (!same_scale(a->scale, b->scale)) return blb_fail(BLB_ERR_SCALE, "operands have different scales");
+    blb_ct* r;
+    BLB_TRY(new_ct(c, a->level, a->npolys, a->scale, &r));
+    int rc = launch_sub_rows(c, r->d, a->d, b->d, a->npolys * (a->level + 1), c->qmap(a->level + 1));
+    if (rc) {
+        blb_ct_free(r);
+        return rc;
+    }
+    *out = r;
+    return BLB_OK;
+}
+
+extern "C" int blb_drop_level(blb_ctx* c, const blb_ct* a, uint32_t level, blb_ct** out)
+{
+    if (!c || !a || !out) return blb_fail(BLB_ERR_ARG, "null argument");
+    if (level > a->level) return blb_fail(BLB_ERR_LEVEL, "cannot raise a ciphertext's level");
+    blb_ct* r;
+    BLB_TRY(new_ct(c, level, a->npolys, a->scale, &r));
+    const size_t N = c->N, n_in = a->level + 1, n_out = level + 1;
+    for (uint32_t p = 0; p < a->npolys; p++)
+        if (cudaMemcpyAsync(r->d + p * n_out * N, a->d + p * n_in * N, n_out * N * 8, cudaMemcpyDeviceToDevice,
+                            c->stream) != cudaSuccess) {
+            blb_ct_free(r);
+            return blb_fail(BLB_ERR_CUDA, "copy failed");
+        }
+    *out = r;
+    return BLB_OK;
+}
+
+extern "C" int blb_mul_const(blb_ctx* c, const blb_ct* a, const double* vals, uint64_t n, double target_scale,
+                             blb_ct** out)
+{
+    if (!c || !a || !out || (n && !vals)) return blb_fail(BLB_ERR_ARG, "null argument");
+    if (a->level == 0) return blb_fail(BLB_ERR_LEVEL, "no level left to rescale");
+    if (a->npolys != 2) return blb_fail(BLB_ERR_ARG, "mul_const needs a 2-polynomial ciphertext");
+    if (n > c->N / 2 || n == 0) return blb_fail(BLB_ERR_ARG, "1 to N/2 values");
+    if (!(target_scale > 0)) return blb_fail(BLB_ERR_ARG, "target scale must be positive");
+    const uint32_t lv = a->level, nl = lv + 1, N = c->N;
+    // the constant's scale makes (scale_a x s_c) / q_level equal the target
+    const double s_c = target_scale * (double)c->q[lv] / a->scale;
+    Scratch S(c);
+    const uint32_t s = N / 2;
+    std::vector<double> z(s);
+    for (uint32_t j = 0; j < s; j++) z[j] = vals[n == 1 ? 0 : (j < n ? j : 0)] * (n == 1 || j < n ? 1.0 : 0.0);
+    double* dz = (double*)S.get((size_t)s * 8);
+    uint64_t* pt = (uint64_t*)S.get((size_t)nl * N * 8);
+    uint64_t* prod = (uint64_t*)S.get((size_t)2 * nl * N * 8);
+    if (!dz || !pt || !prod) return blb_fail(BLB_ERR_OOM, "mul_const buffers");
+    BLB_CUDA(cudaMemcpyAsync(dz, z.data(), (size_t)s * 8, cudaMemcpyHostToDevice, c->stream));
+    BLB_TRY(encode_slots(c, dz, 1, s, lv, s_c, pt));
+    BLB_TRY(launch_mul_rows(c, prod, a->d, pt, 2 * nl, c->qmap(nl), nl));
+    blb_ct* r;
+    BLB_TRY(new_ct(c, lv - 1, 2, target_scale, &r));
+    int rc = launch_rescale_stack(c, r->d, prod, lv, 2);
+    if (!rc) rc = cudaStreamSynchronize(c->stream) == cudaSuccess ? BLB_OK : blb_fail(BLB_ERR_CUDA, "sync failed");
+    if (rc) {
+        blb_ct_free(r);
+        return rc;
+    }
+    *out = r;
+    return BLB_OK;
+}
+
 extern "C" int blb_mul_plain(blb_ctx* c, const blb_ct* a, const blb_pt* p, blb_ct** out)
 {
     if (!c || !a || !p || !out) return blb_fail(BLB_ERR_ARG, "null argument");
