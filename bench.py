@@ -186,7 +186,7 @@ def unpack_head_diagonals(Z, L, Hg, Kc):
 
 
 class Workload:
-    def __init__(self, device):
+    def __init__(self, device, ntt_split=None):
         import torch
         from paper_2508_19525_b300 import blb
         from paper_2508_19525_b300 import workloads as wl
@@ -199,8 +199,12 @@ class Workload:
         G = self.k // B1
         rots = [b * M for b in range(1, B1)] + [g * B1 * M for g in range(1, G)]
         self.keys = self.ctx.keygen(0, rots)
-        # pick the NTT pass split for this ring on the device before anything is timed
+        # pick the NTT pass split for this ring on the device before anything is
+        # timed (or take the given one, so that profiles capture known kernels)
         self.ntt_split, self.ntt_split_us = self.ctx.ntt_autotune(256)
+        if ntt_split is not None:
+            self.ctx.ntt_set_split(ntt_split)
+            self.ntt_split = ntt_split
         self.X, Wqkv, Wo = wl.bert_base_cp(seed=0)
         self.ref_qkv = self.X @ Wqkv
         self.ref_o = self.ref_qkv[:, :D_O] @ Wo
@@ -865,7 +869,7 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def ncu_case(seqs=1):
+def ncu_case(seqs=1, ntt_split=None):
     """Small profiling case of the same kernels for `ncu --profile-from-start off`:
     N = 2^15, 8 primes, matmul_cp 128x768 @ 768x256 (96 plaintext terms per
     output as in the BERT-base products, 2.2 GB of byte-sliced diagonals, larger
@@ -876,6 +880,8 @@ def ncu_case(seqs=1):
     from paper_2508_19525_b300 import workloads as wl
     prm = wl.BERT_CP
     ctx = blb.Context(prm.logN, prm.q_bits, prm.p_bits, prm.dnum, prm.scale)
+    if ntt_split is not None:
+        ctx.ntt_set_split(ntt_split)
     k = ctx.N // 2 // M
     rots = [b * M for b in range(1, B1)] + [g * B1 * M for g in range(1, k // B1)]
     keys = ctx.keygen(0, rots)
@@ -895,11 +901,11 @@ def ncu_case(seqs=1):
                       "plan": plan.info()}))
 
 
-def ncu_step():
+def ncu_step(ntt_split=None):
     """One BERT-base step bracketed by cudaProfilerStart/Stop (after one warm-up
     step), for a launch list with `ncu --profile-from-start off`."""
     import torch
-    w = Workload(torch.device("cuda", 0))
+    w = Workload(torch.device("cuda", 0), ntt_split)
     w.step()
     w.ctx.sync()
     torch.cuda.profiler.start()
@@ -950,6 +956,8 @@ def main():
     ap.add_argument("--ncu-seqs", type=int, default=1, help="sequences in the profiling case")
     ap.add_argument("--ncu-step", action="store_true", help="run one profiled BERT-base step and exit")
     ap.add_argument("--ncu-conv", action="store_true", help="run the conversion profiling case and exit")
+    ap.add_argument("--ntt-split", type=int, default=None, choices=(-1, 0, 1),
+                    help="fix the NTT pass split of the profiling cases (default: autotuned)")
     ap.add_argument("--batch", type=int, default=8, help="sequences per batched step (1 = skip)")
     ap.add_argument("--no-attention", dest="attention", action="store_false",
                     help="skip the matmul_cc attention measurement")
@@ -965,9 +973,9 @@ def main():
                     help="skip the continuous-batching serving measurement")
     args = ap.parse_args()
     if args.ncu_case:
-        return ncu_case(args.ncu_seqs)
+        return ncu_case(args.ncu_seqs, args.ntt_split)
     if args.ncu_step:
-        return ncu_step()
+        return ncu_step(args.ntt_split)
     if args.ncu_conv:
         return ncu_conv()
     args.cpu_sample = (args.cpu_rotations, args.cpu_products)
