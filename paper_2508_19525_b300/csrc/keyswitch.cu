@@ -350,16 +350,19 @@ __global__ void k_ksb_digit_rows(uint64_t* __restrict__ ext, const uint64_t* __r
 }
 
 // acc[group][p][t] = sum over the group's products x of sum_j sigma_x(ext[src_x][j][t]) key_x[j][p][kt]
+// for the special-prime rows t = n + blockIdx.y only: they are the input of
+// the ModDown conversion.  The ciphertext-prime rows are summed where they are
+// used, in k_ksb_finish, so they are never written out.
 __global__ void k_ksb_inner(uint64_t* __restrict__ acc, const uint64_t* __restrict__ ext,
                             const DevGroup* __restrict__ groups, const DevProduct* __restrict__ prods, LimbMap emap,
                             uint32_t n, uint32_t E, uint32_t beta, uint32_t nQ, uint32_t np,
                             const uint64_t* __restrict__ qs, const uint64_t* __restrict__ bar, uint32_t logN)
 {
     const uint32_t N = 1u << logN;
-    const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x, t = blockIdx.y, gr = blockIdx.z;
+    const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x, t = n + blockIdx.y, gr = blockIdx.z;
     if (c >= N) return;
     const uint32_t pi = emap.p[t];
-    const uint32_t kt = t < n ? t : nQ + (t - n);
+    const uint32_t kt = nQ + (t - n);
     const uint64_t q = qs[pi], r0 = bar[2 * pi], r1 = bar[2 * pi + 1];
     const DevGroup G = groups[gr];
     uint64_t s0 = 0, s1 = 0;
@@ -380,26 +383,45 @@ __global__ void k_ksb_inner(uint64_t* __restrict__ acc, const uint64_t* __restri
     o[(size_t)E * N] = s1;
 }
 
+// Ciphertext prime i of group gr, both polynomials: the inner product
+// acc_p = sum over the group's products of sum_j sigma_x(ext[src_x][j][i]) key_x[j][p][i]
+// (the same sums k_ksb_inner forms for the special primes), then
 // out_p = [out_p +] sum_{addends of p} add[perm(k)] + (acc_p - cv_p) P^-1
-__global__ void k_ksb_finish(const DevGroup* __restrict__ groups, const KsAdd* __restrict__ adds,
-                             const uint64_t* __restrict__ acc, const uint64_t* __restrict__ cv, uint32_t n,
-                             uint32_t E, PInv pinv, const uint64_t* __restrict__ qs, uint32_t logN, int accumulate)
+__global__ void k_ksb_finish(const DevGroup* __restrict__ groups, const DevProduct* __restrict__ prods,
+                             const uint64_t* __restrict__ ext, const KsAdd* __restrict__ adds,
+                             const uint64_t* __restrict__ cv, uint32_t n, uint32_t E, uint32_t beta, uint32_t np,
+                             PInv pinv, const uint64_t* __restrict__ qs, const uint64_t* __restrict__ bar,
+                             uint32_t logN, int accumulate)
 {
     const uint32_t N = 1u << logN;
-    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x, row = blockIdx.y, gr = blockIdx.z;
+    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x, i = blockIdx.y, gr = blockIdx.z;
     if (k >= N) return;
-    const uint32_t p = row / n, i = row % n;
     const DevGroup G = groups[gr];
-    const uint64_t q = qs[i];
-    const uint64_t a = acc[(((size_t)gr * 2 + p) * E + i) * N + k];
-    const uint64_t v = cv[(((size_t)gr * 2 + p) * n + i) * N + k];
-    uint64_t r = mul_shoup(sub_mod(a, v, q), pinv.w[i], pinv.wp[i], q);
-    for (uint32_t x = G.add0; x < G.add1; x++) {
-        const KsAdd A = adds[x];
-        if (A.poly == p) r = add_mod(r, A.ptr[(size_t)i * N + perm_index(k, logN, A.g)], q);
+    const uint64_t q = qs[i], r0 = bar[2 * i], r1 = bar[2 * i + 1];
+    uint64_t s[2] = {0, 0};
+    for (uint32_t x = G.prod0; x < G.prod1; x++) {
+        const DevProduct P = prods[x];
+        const uint64_t* xs = ext + (size_t)P.src * beta * E * N + (size_t)i * N + perm_index(k, logN, P.g);
+        acc128 a0{0, 0}, a1{0, 0};
+        for (uint32_t j = 0; j < beta; j++) {
+            const uint64_t v = xs[(size_t)j * E * N];
+            mad128(a0, v, P.key[(((size_t)j * 2 + 0) * np + i) * N + k]);
+            mad128(a1, v, P.key[(((size_t)j * 2 + 1) * np + i) * N + k]);
+        }
+        s[0] = add_mod(s[0], barrett128(a0.lo, a0.hi, q, r0, r1), q);
+        s[1] = add_mod(s[1], barrett128(a1.lo, a1.hi, q, r0, r1), q);
     }
-    uint64_t* o = (p ? G.out1 : G.out0) + (size_t)i * N + k;
-    *o = accumulate ? add_mod(*o, r, q) : r;
+#pragma unroll
+    for (uint32_t p = 0; p < 2; p++) {
+        const uint64_t v = cv[(((size_t)gr * 2 + p) * n + i) * N + k];
+        uint64_t r = mul_shoup(sub_mod(s[p], v, q), pinv.w[i], pinv.wp[i], q);
+        for (uint32_t x = G.add0; x < G.add1; x++) {
+            const KsAdd A = adds[x];
+            if (A.poly == p) r = add_mod(r, A.ptr[(size_t)i * N + perm_index(k, logN, A.g)], q);
+        }
+        uint64_t* o = (p ? G.out1 : G.out0) + (size_t)i * N + k;
+        *o = accumulate ? add_mod(*o, r, q) : r;
+    }
 }
 
 }  // namespace
@@ -575,16 +597,16 @@ int ks_run(blb_ctx* ctx, uint32_t level, const KsSource* sources, uint32_t n_src
             k_ksb_digit_rows<<<dim3(gx, n, ns), kT, 0, ctx->stream>>>(ext, din, n, E, beta, alpha, N);
             BLB_LAUNCHED();
         }
-        k_ksb_inner<<<dim3(gx, E, ng), kT, 0, ctx->stream>>>(acc, ext, d_grp, d_prod, emap, n, E, beta, ctx->nQ,
-                                                              ctx->np, ctx->d_q, ctx->d_bar, ctx->logN);
+        k_ksb_inner<<<dim3(gx, nP, ng), kT, 0, ctx->stream>>>(acc, ext, d_grp, d_prod, emap, n, E, beta, ctx->nQ,
+                                                               ctx->np, ctx->d_q, ctx->d_bar, ctx->logN);
         BLB_LAUNCHED();
         BLB_TRY(ntt_inverse_list(ctx, acc, (uint32_t)p_rows.size(), d_p_rows));
         k_moddown_conv<<<dim3(gx, 2 * ng), kT, 0, ctx->stream>>>(acc + (size_t)n * N, (size_t)E * N, ctx->d_moddown, n,
                                                                  cv, (size_t)n * N, ctx->d_q, ctx->d_bar, N);
         BLB_LAUNCHED();
         BLB_TRY(ntt_forward(ctx, cv, ng * 2 * n, ctx->qmap(n)));
-        k_ksb_finish<<<dim3(gx, 2 * n, ng), kT, 0, ctx->stream>>>(d_grp, d_add, acc, cv, n, E, pinv, ctx->d_q,
-                                                                  ctx->logN, accumulate);
+        k_ksb_finish<<<dim3(gx, n, ng), kT, 0, ctx->stream>>>(d_grp, d_prod, ext, d_add, cv, n, E, beta, ctx->np,
+                                                              pinv, ctx->d_q, ctx->d_bar, ctx->logN, accumulate);
         BLB_LAUNCHED();
         for (uint32_t s : used) local[s] = -1;
         g0 = g1;
