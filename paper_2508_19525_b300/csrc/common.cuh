@@ -141,6 +141,7 @@ struct ConvTable {
     uint64_t hat_inv_sh[BLB_MAXP];     // Shoup companions
     uint64_t hat[BLB_MAXP][BLB_MAXP];  // [i][t] = S/s_i mod t
     uint64_t prod_mod_t[BLB_MAXP];     // S mod t
+    uint64_t neg_prod_mod_t[BLB_MAXP]; // (t - S mod t) mod t
 };
 
 // ---------------------------------------------------------------------------

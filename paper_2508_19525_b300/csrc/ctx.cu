@@ -341,6 +341,7 @@ static void build_conv(const blb_ctx* c, const std::vector<uint32_t>& src, const
         uint64_t tq = c->q[dst[k]], v = 1 % tq;
         for (uint32_t l = 0; l < t.ns; l++) v = host_mulmod(v, c->q[src[l]] % tq, tq);
         t.prod_mod_t[k] = v;
+        t.neg_prod_mod_t[k] = (tq - v) % tq;
     }
 }
 

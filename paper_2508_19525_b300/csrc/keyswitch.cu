@@ -81,11 +81,12 @@ __global__ void k_moddown_conv(const uint64_t* __restrict__ src, size_t src_ps, 
     for (uint32_t t = 0; t < nt; t++) {
         const uint32_t pt = tab->dst[t];
         const uint64_t q = qs[pt], r0 = bar[2 * pt], r1 = bar[2 * pt + 1];
+        // sum_k y_k (P/p_k) - v P, the subtraction folded into the lazy sum as
+        // v (q_t - P mod q_t): one reduction per target
         acc128 a{0, 0};
         for (uint32_t k = 0; k < ns; k++) mad128(a, y[k], tab->hat[k][t]);
-        const uint64_t x = barrett128(a.lo, a.hi, q, r0, r1);
-        const uint64_t vp = mul_mod(v, tab->prod_mod_t[t], q, r0, r1);
-        dst[poly * dst_ps + (size_t)tab->dst_row[t] * N + c] = sub_mod(x, vp, q);
+        mad128(a, v, tab->neg_prod_mod_t[t]);
+        dst[poly * dst_ps + (size_t)tab->dst_row[t] * N + c] = barrett128(a.lo, a.hi, q, r0, r1);
     }
 }
 
