@@ -264,15 +264,23 @@ int blb_matmul_cp(blb_ctx* ctx, const blb_keys* keys, blb_ct* const* X, uint32_t
  *   3. one rotation Rot^{g b1s2 - (t mod Kc) Hg L} per t, two routing masks.
  * Depth 4: inputs at `level` (>= 4), outputs at level-4 with scale
  * scale(A) scale(B) / q_{level-2}.  Needs the relinearization key and the Galois
- * keys of blb_cc_plan_rotations.  Masks are encoded once per plan. */
+ * keys of blb_cc_plan_rotations.  Masks are encoded once per plan: the 2 Kc
+ * step-1 and 2 L step-2 masks, and the distinct step-3 masks (at most 2 Kc: a
+ * step-3 mask is constant on each block and splits the blocks at kappa = t mod Kc).
+ * Steps 1-2 run over chunks of c_chunk input ciphertexts and, inside, t_chunk
+ * diagonals, their tensor products summed mod q (the result does not depend on
+ * the chunking); by default the chunks are the largest whose workspace stays
+ * within workspace_bytes (0 = 24 GiB), the whole product when it fits. */
 typedef struct {
-    uint32_t b1s1, b1s2; /* 0 = about sqrt(Kc/2), sqrt(L/2) */
+    uint32_t b1s1, b1s2;      /* 0 = about sqrt(Kc/2), sqrt(L/2) */
+    uint32_t c_chunk, t_chunk; /* 0 = from the workspace budget */
+    uint64_t workspace_bytes;  /* 0 = 24 GiB */
 } blb_cc_sched;
 int blb_cc_plan_create(blb_ctx* ctx, uint32_t L, uint32_t Hg, uint32_t R, uint32_t level,
                        const blb_cc_sched* sched, blb_cc_plan** out);
 void blb_cc_plan_free(blb_cc_plan* plan);
 int blb_cc_plan_info(const blb_cc_plan* plan, uint32_t* n_c, uint32_t* Kc, uint32_t* nout, uint32_t* b1s1,
-                     uint32_t* b1s2, uint64_t* mask_bytes);
+                     uint32_t* b1s2, uint64_t* mask_bytes, uint32_t* c_chunk, uint32_t* t_chunk);
 /* Left-rotation amounts the plan needs keys for; out may be NULL to query count. */
 int blb_cc_plan_rotations(const blb_cc_plan* plan, int32_t* out, uint32_t cap, uint32_t* count);
 int blb_matmul_cc_plan(blb_ctx* ctx, const blb_keys* keys, const blb_cc_plan* plan, blb_ct* const* A,

@@ -39,7 +39,7 @@ class _Sched(ctypes.Structure):
 
 
 class _CcSched(ctypes.Structure):
-    _fields_ = [("b1s1", _u32), ("b1s2", _u32)]
+    _fields_ = [("b1s1", _u32), ("b1s2", _u32), ("c_chunk", _u32), ("t_chunk", _u32), ("workspace_bytes", _u64)]
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(_vp, ctypes.c_size_t, _vp, _vp)
@@ -95,7 +95,7 @@ SIGNATURES = {
     "blb_matmul_cp": (ctypes.c_int, [_vp, _vp, _pp, _u32, _u32, _u32, _vp, _u32, ctypes.POINTER(_Sched), _pp]),
     "blb_cc_plan_create": (ctypes.c_int, [_vp, _u32, _u32, _u32, _u32, ctypes.POINTER(_CcSched), _pp]),
     "blb_cc_plan_free": (None, [_vp]),
-    "blb_cc_plan_info": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "blb_cc_plan_info": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "blb_cc_plan_rotations": (ctypes.c_int, [_vp, _vp, _u32, _vp]),
     "blb_matmul_cc_plan": (ctypes.c_int, [_vp, _vp, _vp, _pp, _pp, _u32, _pp]),
     "blb_matmul_cc": (ctypes.c_int, [_vp, _vp, _pp, _pp, _u32, _u32, _u32, _u32, ctypes.POINTER(_CcSched), _pp]),
@@ -250,10 +250,10 @@ class CcPlan(_Handle):
     _free = "blb_cc_plan_free"
 
     def info(self):
-        v = [_u32() for _ in range(5)] + [_u64()]
+        v = [_u32() for _ in range(5)] + [_u64()] + [_u32() for _ in range(2)]
         _check(lib().blb_cc_plan_info(self.h, *[ctypes.byref(x) for x in v]))
         return dict(n_c=v[0].value, Kc=v[1].value, nout=v[2].value, b1s1=v[3].value, b1s2=v[4].value,
-                    mask_bytes=v[5].value)
+                    mask_bytes=v[5].value, c_chunk=v[6].value, t_chunk=v[7].value)
 
     def rotations(self):
         n = _u32()
@@ -593,8 +593,8 @@ class Context:
         return [Ciphertext(self, y) for y in ys]
 
     # matmul_cc
-    def cc_plan(self, L, Hg, R, level, b1s1=0, b1s2=0):
-        s = _CcSched(b1s1, b1s2)
+    def cc_plan(self, L, Hg, R, level, b1s1=0, b1s2=0, c_chunk=0, t_chunk=0, workspace_bytes=0):
+        s = _CcSched(b1s1, b1s2, c_chunk, t_chunk, workspace_bytes)
         return self._new(CcPlan, lib().blb_cc_plan_create, L, Hg, R, level, ctypes.byref(s))
 
     def matmul_cc_plan(self, keys, plan, A, B):

@@ -20,20 +20,27 @@
 //   m2lo(g,b)   = Rot^{-g b1s2}[i < L - t]                                    (hi: i >= L - t)
 //   m3(t,j)     = [the block landing at kappa' comes from kappa = (kappa' - t) mod Kc and
 //                  carries diagonal (t + kappa) mod L of output j]
+// m3(t,j) is constant on every block and depends on the block's kappa' only;
+// for t = a Kc + r it is [kappa' >= r] for j = a and [kappa' < r] for
+// j = a + 1 (mod L/Kc), so the L^2/Kc step-3 masks hold at most 2 Kc distinct
+// plaintexts and each is encoded and stored once.
 // Depth 4: step-1 masks, step-2 masks, the tensor product, step-3 masks.
 #include <algorithm>
 #include <cstring>
+#include <map>
 
 #include "common.cuh"
 
 struct blb_cc_plan {
     blb_ctx* ctx;
     uint32_t L, Hg, R, level, Kc, n_c, nout, b1s1, b1s2, G1, G2;
+    uint32_t c_chunk, t_chunk;  // input ciphertexts and diagonals per pass of steps 1-2
     uint64_t* d_m1;  // [G1][b1s1][2] at level, (level+1) x N each
     uint64_t* d_m2;  // [G2][b1s2][2] at level-1
-    uint64_t* d_m3;  // [L][nout] at level-3
-    std::vector<uint8_t> nz1, nz2, nz3;
-    size_t bytes;
+    uint64_t* d_m3;  // [n3] distinct step-3 masks at level-3
+    std::vector<uint8_t> nz1, nz2;
+    std::vector<int32_t> m3_index;  // [L][nout]: row of d_m3, -1 for an all-zero mask
+    size_t b1, b2, b3, bytes;
 };
 
 namespace {
@@ -70,12 +77,14 @@ __host__ __device__ inline uint32_t mask_shift(const MaskSpec& m, int type, uint
     return 0;
 }
 
-// z[m][slot] = mask(type, first + m) at slot (slot - shift) mod s
-__global__ void k_cc_masks(double* __restrict__ z, MaskSpec spec, int type, uint32_t first)
+// z[m][slot] = mask(type, id) at slot (slot - shift) mod s, id = ids[first + m]
+// (first + m without a table)
+__global__ void k_cc_masks(double* __restrict__ z, MaskSpec spec, int type, uint32_t first,
+                           const uint32_t* __restrict__ ids)
 {
     const uint32_t slot = blockIdx.x * blockDim.x + threadIdx.x, m = blockIdx.y;
     if (slot >= spec.s) return;
-    const uint32_t id = first + m;
+    const uint32_t id = ids ? ids[first + m] : first + m;
     const uint32_t src = (slot + spec.s - mask_shift(spec, type, id) % spec.s) % spec.s;
     z[(size_t)m * spec.s + slot] = mask_pred(spec, type, id, src) ? 1.0 : 0.0;
 }
@@ -114,15 +123,22 @@ struct TensorPair {
     const uint64_t* a;
     const uint64_t* b;
 };
+// (accumulate: U[t] += the sum)
 __global__ void k_tensor_acc(uint64_t* __restrict__ U, const TensorPair* __restrict__ pairs, uint32_t n_c,
                              uint32_t n, uint32_t N, const uint64_t* __restrict__ qs,
-                             const uint64_t* __restrict__ bar)
+                             const uint64_t* __restrict__ bar, bool accumulate)
 {
     const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x, i = blockIdx.y, t = blockIdx.z;
     if (c >= N) return;
     const uint64_t q = qs[i], r0 = bar[2 * i], r1 = bar[2 * i + 1];
     const size_t nN = (size_t)n * N, off = (size_t)i * N + c;
+    uint64_t* dst = U + (size_t)t * 3 * nN + off;
     acc128 x0{0, 0}, x1{0, 0}, x2{0, 0};
+    if (accumulate) {
+        x0.lo = dst[0];
+        x1.lo = dst[nN];
+        x2.lo = dst[2 * nN];
+    }
     for (uint32_t k = 0; k < n_c; k++) {
         const TensorPair p = pairs[(size_t)t * n_c + k];
         const uint64_t a0 = p.a[off], a1 = p.a[nN + off], b0 = p.b[off], b1 = p.b[nN + off];
@@ -136,7 +152,6 @@ __global__ void k_tensor_acc(uint64_t* __restrict__ U, const TensorPair* __restr
             x2 = acc128{barrett128(x2.lo, x2.hi, q, r0, r1), 0};
         }
     }
-    uint64_t* dst = U + (size_t)t * 3 * nN + off;
     dst[0] = barrett128(x0.lo, x0.hi, q, r0, r1);
     dst[nN] = barrett128(x1.lo, x1.hi, q, r0, r1);
     dst[2 * nN] = barrett128(x2.lo, x2.hi, q, r0, r1);
@@ -200,7 +215,8 @@ static MaskSpec spec_of(const blb_cc_plan* P)
     return MaskSpec{P->L, P->Hg, P->Kc, P->ctx->N / 2, P->b1s1, P->b1s2, P->nout};
 }
 
-static int encode_masks(blb_ctx* c, const MaskSpec& spec, int type, uint32_t count, uint32_t level, uint64_t* out)
+static int encode_masks(blb_ctx* c, const MaskSpec& spec, int type, uint32_t count, uint32_t level, uint64_t* out,
+                        const uint32_t* d_ids = nullptr)
 {
     const uint32_t s = spec.s, n = level + 1;
     const uint32_t chunk = std::max<uint32_t>(1, std::min<uint32_t>(count, (uint32_t)((32ull << 20) / ((uint64_t)s * 8))));
@@ -209,7 +225,7 @@ static int encode_masks(blb_ctx* c, const MaskSpec& spec, int type, uint32_t cou
     int rc = BLB_OK;
     for (uint32_t first = 0; !rc && first < count; first += chunk) {
         const uint32_t cnt = std::min(chunk, count - first);
-        k_cc_masks<<<dim3((s + kT - 1) / kT, cnt), kT, 0, c->stream>>>(z, spec, type, first);
+        k_cc_masks<<<dim3((s + kT - 1) / kT, cnt), kT, 0, c->stream>>>(z, spec, type, first, d_ids);
         if (cudaGetLastError() != cudaSuccess) rc = blb_fail(BLB_ERR_CUDA, "mask kernel launch failed");
         else {
             blb_count_launch();
@@ -258,14 +274,57 @@ extern "C" int blb_cc_plan_create(blb_ctx* c, uint32_t L, uint32_t Hg, uint32_t 
     P->G2 = L / b1s2;
     P->d_m1 = P->d_m2 = P->d_m3 = nullptr;
     const uint32_t N = c->N;
-    const size_t n1 = 2ull * Kc, n2 = 2ull * L, n3 = (size_t)L * P->nout;
-    const size_t b1 = n1 * (level + 1) * N * 8, b2 = n2 * level * N * 8, b3 = n3 * (level - 2) * N * 8;
-    P->bytes = b1 + b2 + b3;
-    P->d_m1 = (uint64_t*)dev_alloc(c, b1);
-    P->d_m2 = (uint64_t*)dev_alloc(c, b2);
-    P->d_m3 = (uint64_t*)dev_alloc(c, b3);
-    int rc = (P->d_m1 && P->d_m2 && P->d_m3) ? BLB_OK : blb_fail(BLB_ERR_OOM, "mask plaintexts do not fit");
+    {  // chunking of steps 1-2 under the workspace budget
+        const uint64_t l0 = level + 1, l1 = level, l2 = level - 1;
+        const uint64_t per_c = 16ull * N *
+                               ((2ull * b1s1 + P->G1 + 1) * l0 + (1 + 2ull * b1s2) * l1 + (1ull + P->G2) * l2);
+        const uint64_t per_ct = 16ull * N * (l1 + l2);
+        const uint64_t budget = (sched && sched->workspace_bytes) ? sched->workspace_bytes : (24ull << 30);
+        uint32_t Cc = P->n_c, Tc = L;
+        if ((uint64_t)P->n_c * (per_c + L * per_ct) > budget) {
+            Cc = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(P->n_c, budget / 2 / per_c));
+            const uint64_t left = budget > Cc * per_c ? budget - Cc * per_c : 0;
+            Tc = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(L, left / ((uint64_t)Cc * per_ct)));
+        }
+        if (sched && sched->c_chunk) Cc = std::min(sched->c_chunk, P->n_c);
+        if (sched && sched->t_chunk) Tc = std::min(sched->t_chunk, L);
+        P->c_chunk = Cc;
+        P->t_chunk = Tc;
+    }
     const MaskSpec spec = spec_of(P);
+    // distinct step-3 masks: the predicate depends on the block's kappa' only,
+    // so a mask is identified by its values on the Kc blocks (slot kappa' Hg L)
+    std::vector<uint32_t> rep3;
+    {
+        std::map<std::vector<uint8_t>, int32_t> seen;
+        P->m3_index.assign((size_t)L * P->nout, -1);
+        std::vector<uint8_t> sig(Kc);
+        for (uint32_t t = 0; t < L; t++)
+            for (uint32_t j = 0; j < P->nout; j++) {
+                const uint32_t id = t * P->nout + j;
+                bool any = false;
+                for (uint32_t kap = 0; kap < Kc; kap++) {
+                    sig[kap] = mask_pred(spec, 3, id, kap * Hg * L) ? 1 : 0;
+                    any |= sig[kap] != 0;
+                }
+                if (!any) continue;
+                auto it = seen.find(sig);
+                if (it == seen.end()) {
+                    it = seen.emplace(sig, (int32_t)rep3.size()).first;
+                    rep3.push_back(id);
+                }
+                P->m3_index[id] = it->second;
+            }
+    }
+    const size_t n1 = 2ull * Kc, n2 = 2ull * L, n3 = rep3.size();
+    P->b1 = n1 * (level + 1) * N * 8;
+    P->b2 = n2 * level * N * 8;
+    P->b3 = std::max<size_t>(n3 * (level - 2) * N * 8, 16);
+    P->bytes = P->b1 + P->b2 + P->b3;
+    P->d_m1 = (uint64_t*)dev_alloc(c, P->b1);
+    P->d_m2 = (uint64_t*)dev_alloc(c, P->b2);
+    P->d_m3 = (uint64_t*)dev_alloc(c, P->b3);
+    int rc = (P->d_m1 && P->d_m2 && P->d_m3) ? BLB_OK : blb_fail(BLB_ERR_OOM, "mask plaintexts do not fit");
     // which masks are non-zero (host evaluation of the same predicates)
     auto nonzero = [&](int type, uint32_t id) {
         for (uint32_t slot = 0; slot < s; slot++)
@@ -274,13 +333,17 @@ extern "C" int blb_cc_plan_create(blb_ctx* c, uint32_t L, uint32_t Hg, uint32_t 
     };
     P->nz1.resize(n1);
     P->nz2.resize(n2);
-    P->nz3.resize(n3);
     for (size_t k = 0; k < n1; k++) P->nz1[k] = nonzero(1, (uint32_t)k);
     for (size_t k = 0; k < n2; k++) P->nz2[k] = nonzero(2, (uint32_t)k);
-    for (size_t k = 0; k < n3; k++) P->nz3[k] = nonzero(3, (uint32_t)k);
     if (!rc) rc = encode_masks(c, spec, 1, (uint32_t)n1, level, P->d_m1);
     if (!rc) rc = encode_masks(c, spec, 2, (uint32_t)n2, level - 1, P->d_m2);
-    if (!rc) rc = encode_masks(c, spec, 3, (uint32_t)n3, level - 3, P->d_m3);
+    if (!rc && n3) {
+        uint32_t* d_ids = nullptr;
+        size_t bi = 0;
+        rc = upload_table(c, rep3, &d_ids, &bi);
+        if (!rc) rc = encode_masks(c, spec, 3, (uint32_t)n3, level - 3, P->d_m3, d_ids);
+        dev_free(c, d_ids, bi);
+    }
     if (rc) {
         blb_cc_plan_free(P);
         return rc;
@@ -293,10 +356,9 @@ extern "C" void blb_cc_plan_free(blb_cc_plan* P)
 {
     if (!P) return;
     blb_ctx* c = P->ctx;
-    const uint32_t N = c->N;
-    dev_free(c, P->d_m1, 2ull * P->Kc * (P->level + 1) * N * 8);
-    dev_free(c, P->d_m2, 2ull * P->L * P->level * N * 8);
-    dev_free(c, P->d_m3, (size_t)P->L * P->nout * (P->level - 2) * N * 8);
+    dev_free(c, P->d_m1, P->b1);
+    dev_free(c, P->d_m2, P->b2);
+    dev_free(c, P->d_m3, P->b3);
     delete P;
     ctx_release(c);
 }
@@ -328,7 +390,7 @@ static std::vector<int32_t> plan_rotations(const blb_cc_plan* P)
 }
 
 extern "C" int blb_cc_plan_info(const blb_cc_plan* P, uint32_t* n_c, uint32_t* Kc, uint32_t* nout, uint32_t* b1s1,
-                                uint32_t* b1s2, uint64_t* mask_bytes)
+                                uint32_t* b1s2, uint64_t* mask_bytes, uint32_t* c_chunk, uint32_t* t_chunk)
 {
     if (!P) return blb_fail(BLB_ERR_ARG, "null plan");
     if (n_c) *n_c = P->n_c;
@@ -337,6 +399,8 @@ extern "C" int blb_cc_plan_info(const blb_cc_plan* P, uint32_t* n_c, uint32_t* K
     if (b1s1) *b1s1 = P->b1s1;
     if (b1s2) *b1s2 = P->b1s2;
     if (mask_bytes) *mask_bytes = P->bytes;
+    if (c_chunk) *c_chunk = P->c_chunk;
+    if (t_chunk) *t_chunk = P->t_chunk;
     return BLB_OK;
 }
 
@@ -475,140 +539,153 @@ extern "C" int blb_matmul_cc_plan(blb_ctx* c, const blb_keys* K, const blb_cc_pl
     int rc = BLB_OK;
     std::vector<KsItem> items;
 
-    // ---- step 1 ----
-    Stack LO, HI, INNER, ACC, BP;
-    rc = LO.alloc(c, n_c * P->b1s1, l0);
-    if (!rc) rc = HI.alloc(c, n_c * P->b1s1, l0);
-    if (!rc) rc = INNER.alloc(c, n_c * P->G1, l0);
-    if (!rc) rc = ACC.alloc(c, n_c, l0);
-    if (!rc) rc = BP.alloc(c, n_c, l1);
-    {  // baby steps: Rot^{b0}(B_c) (b0 >= 1) and Rot^{b0 - L}(B_c), hoisted per B_c
-        std::vector<const uint64_t*> srcs;
-        std::vector<int32_t> rots;
-        for (uint32_t ci = 0; ci < n_c; ci++) srcs.push_back(B[ci]->d);
-        for (uint32_t b0 = 1; b0 < P->b1s1; b0++) rots.push_back((int32_t)b0);
-        for (uint32_t b0 = (P->G1 > 1 ? 0 : 1); b0 < P->b1s1; b0++) rots.push_back((int32_t)b0 - (int32_t)L);
-        for (uint32_t ci = 0; !rc && ci < n_c; ci++)
-            if (cudaMemcpyAsync(LO.at((size_t)ci * P->b1s1), B[ci]->d, 2 * pw0 * 8, cudaMemcpyDeviceToDevice, c->stream))
-                rc = blb_fail(BLB_ERR_CUDA, "copy failed");
-        if (!rc)
-            rc = rotate_hoisted(c, K, l0, srcs, rots, [&](uint32_t i, uint32_t j) {
-                const int32_t r = rots[j];
-                return r > 0 ? LO.at((size_t)i * P->b1s1 + r) : HI.at((size_t)i * P->b1s1 + (r + (int32_t)L));
-            });
-    }
-    if (!rc) {  // inner[c][g1] = sum_b0 m1lo LO + m1hi HI
-        std::vector<uint32_t> start{0};
-        std::vector<LcTerm> terms;
-        for (uint32_t ci = 0; ci < n_c; ci++)
-            for (uint32_t g1 = 0; g1 < P->G1; g1++) {
-                for (uint32_t b0 = 0; b0 < P->b1s1; b0++) {
-                    const uint32_t kappa = g1 * P->b1s1 + b0;
-                    for (uint32_t hi = 0; hi < 2; hi++) {
-                        const uint32_t id = kappa * 2 + hi;
-                        if (!P->nz1[id]) continue;
-                        const uint64_t* ct = (hi ? HI : LO).at((size_t)ci * P->b1s1 + b0);
-                        terms.push_back(LcTerm{ct, P->d_m1 + (size_t)id * pw0});
-                    }
-                }
-                start.push_back((uint32_t)terms.size());
-            }
-        rc = lincomb(c, INNER.d, n_c * P->G1, start, terms, l0);
-    }
-    if (!rc) {  // ACC[c] = INNER[c][0] + sum_{g1 >= 1} Rot^{g1 b1s1}(INNER[c][g1]), one ModDown per c
-        std::vector<const uint64_t*> base;
-        std::vector<uint64_t*> out;
-        std::vector<int32_t> rots;
-        for (uint32_t ci = 0; ci < n_c; ci++) {
-            base.push_back(INNER.at((size_t)ci * P->G1));
-            out.push_back(ACC.at(ci));
-        }
-        for (uint32_t g1 = 1; g1 < P->G1; g1++) rots.push_back((int32_t)(g1 * P->b1s1));
-        if (P->G1 == 1) {
-            for (uint32_t ci = 0; !rc && ci < n_c; ci++)
-                if (cudaMemcpyAsync(ACC.at(ci), base[ci], 2 * pw0 * 8, cudaMemcpyDeviceToDevice, c->stream))
-                    rc = blb_fail(BLB_ERR_CUDA, "copy failed");
-        } else {
-            rc = rotate_sum(c, K, l0, base, out, rots,
-                            [&](uint32_t i, uint32_t j) { return INNER.at((size_t)i * P->G1 + j); });
-        }
-    }
-    if (!rc) rc = rescale_many(c, BP.d, ACC.d, l0, n_c, 2);
-
-    // ---- step 2 ----
-    Stack BLO, BHI, A2, AG, VPRE, V, U, WP, W;
-    if (!rc) rc = BLO.alloc(c, n_c * P->b1s2, l1);
-    if (!rc) rc = BHI.alloc(c, n_c * P->b1s2, l1);
-    if (!rc) rc = A2.alloc(c, n_c, l2);
-    if (!rc) rc = AG.alloc(c, n_c * P->G2, l2);
-    if (!rc) rc = VPRE.alloc(c, n_c * L, l1);
-    if (!rc) rc = V.alloc(c, n_c * L, l2);
+    // Steps 1 and 2 run over chunks of Cc input ciphertexts and, inside, of Tc
+    // diagonals t; the tensor products of every chunk are summed into U mod q,
+    // so the result does not depend on the chunking.
+    const uint32_t Cc = P->c_chunk, Tc = P->t_chunk;
+    Stack LO, HI, INNER, ACC, BP, BLO, BHI, A2, AG, VPRE, V, U, WP, W;
+    rc = LO.alloc(c, Cc * P->b1s1, l0);
+    if (!rc) rc = HI.alloc(c, Cc * P->b1s1, l0);
+    if (!rc) rc = INNER.alloc(c, Cc * P->G1, l0);
+    if (!rc) rc = ACC.alloc(c, Cc, l0);
+    if (!rc) rc = BP.alloc(c, Cc, l1);
+    if (!rc) rc = BLO.alloc(c, Cc * P->b1s2, l1);
+    if (!rc) rc = BHI.alloc(c, Cc * P->b1s2, l1);
+    if (!rc) rc = A2.alloc(c, Cc, l2);
+    if (!rc) rc = AG.alloc(c, Cc * P->G2, l2);
+    if (!rc) rc = VPRE.alloc(c, Cc * Tc, l1);
+    if (!rc) rc = V.alloc(c, Cc * Tc, l2);
     if (!rc) rc = U.alloc(c, L, l2, 3);
     if (!rc) rc = WP.alloc(c, L, l2);
     if (!rc) rc = W.alloc(c, L, l3);
-    if (!rc) {  // baby steps: Rot^{b}(B'_c) (b >= 1) and Rot^{b - L}(B'_c), hoisted per B'_c
-        std::vector<const uint64_t*> srcs;
-        std::vector<int32_t> rots;
-        for (uint32_t ci = 0; ci < n_c; ci++) srcs.push_back(BP.at(ci));
-        for (uint32_t b = 1; b < P->b1s2; b++) rots.push_back((int32_t)b);
-        for (uint32_t b = (P->G2 > 1 ? 0 : 1); b < P->b1s2; b++) rots.push_back((int32_t)b - (int32_t)L);
-        for (uint32_t ci = 0; !rc && ci < n_c; ci++)
-            if (cudaMemcpyAsync(BLO.at((size_t)ci * P->b1s2), BP.at(ci), 2 * pw1 * 8, cudaMemcpyDeviceToDevice, c->stream))
-                rc = blb_fail(BLB_ERR_CUDA, "copy failed");
-        if (!rc)
-            rc = rotate_hoisted(c, K, l1, srcs, rots, [&](uint32_t i, uint32_t j) {
-                const int32_t r = rots[j];
-                return r > 0 ? BLO.at((size_t)i * P->b1s2 + r) : BHI.at((size_t)i * P->b1s2 + (r + (int32_t)L));
-            });
-    }
-    for (uint32_t ci = 0; !rc && ci < n_c; ci++) {  // A at level l2, then its giant-step rotations
-        k_drop<<<dim3((N + kT - 1) / kT, l2 + 1, 2), kT, 0, c->stream>>>(A2.at(ci), A[ci]->d, l0 + 1, l2 + 1, N);
-        if (cudaGetLastError() != cudaSuccess) rc = blb_fail(BLB_ERR_CUDA, "drop launch failed");
-        else blb_count_launch();
-        if (!rc && cudaMemcpyAsync(AG.at((size_t)ci * P->G2), A2.at(ci), 2 * pw2 * 8, cudaMemcpyDeviceToDevice,
-                                   c->stream))
-            rc = blb_fail(BLB_ERR_CUDA, "copy failed");
-    }
-    if (!rc) {  // giant steps of A: Rot^{-g b1s2}(A_c), hoisted per A_c
-        std::vector<const uint64_t*> srcs;
-        std::vector<int32_t> rots;
-        for (uint32_t ci = 0; ci < n_c; ci++) srcs.push_back(A2.at(ci));
-        for (uint32_t g = 1; g < P->G2; g++) rots.push_back(-(int32_t)(g * P->b1s2));
-        rc = rotate_hoisted(c, K, l2, srcs, rots,
-                            [&](uint32_t i, uint32_t j) { return AG.at((size_t)i * P->G2 + j + 1); });
-    }
-    if (!rc) {  // VPRE[c][t] = m2lo BLO + m2hi BHI
-        std::vector<uint32_t> start{0};
-        std::vector<LcTerm> terms;
-        for (uint32_t ci = 0; ci < n_c; ci++)
-            for (uint32_t t = 0; t < L; t++) {
-                const uint32_t b = t % P->b1s2;
-                for (uint32_t hi = 0; hi < 2; hi++) {
-                    const uint32_t id = t * 2 + hi;
-                    if (!P->nz2[id]) continue;
-                    const uint64_t* ct = (hi ? BHI : BLO).at((size_t)ci * P->b1s2 + b);
-                    terms.push_back(LcTerm{ct, P->d_m2 + (size_t)id * pw1});
-                }
-                start.push_back((uint32_t)terms.size());
-            }
-        rc = lincomb(c, VPRE.d, n_c * L, start, terms, l1);
-    }
-    if (!rc) rc = rescale_many(c, V.d, VPRE.d, l1, n_c * L, 2);
-    if (!rc) {  // U[t] = sum_c AG[c][g] (x) V[c][t]
-        std::vector<TensorPair> pairs;
-        for (uint32_t t = 0; t < L; t++)
-            for (uint32_t ci = 0; ci < n_c; ci++)
-                pairs.push_back(TensorPair{AG.at((size_t)ci * P->G2 + t / P->b1s2), V.at((size_t)ci * L + t)});
-        TensorPair* d_pairs = nullptr;
-        size_t bp = 0;
-        rc = upload_table(c, pairs, &d_pairs, &bp);
-        if (!rc) {
-            k_tensor_acc<<<dim3((N + kT - 1) / kT, l2 + 1, L), kT, 0, c->stream>>>(U.d, d_pairs, n_c, l2 + 1, N,
-                                                                                c->d_q, c->d_bar);
-            if (cudaGetLastError() != cudaSuccess) rc = blb_fail(BLB_ERR_CUDA, "tensor launch failed");
-            else blb_count_launch();
+    for (uint32_t c0 = 0; !rc && c0 < n_c; c0 += Cc) {
+        const uint32_t cn = std::min(Cc, n_c - c0);
+        // ---- step 1 ----
+        {  // baby steps: Rot^{b0}(B_c) (b0 >= 1) and Rot^{b0 - L}(B_c), hoisted per B_c
+            std::vector<const uint64_t*> srcs;
+            std::vector<int32_t> rots;
+            for (uint32_t ci = 0; ci < cn; ci++) srcs.push_back(B[c0 + ci]->d);
+            for (uint32_t b0 = 1; b0 < P->b1s1; b0++) rots.push_back((int32_t)b0);
+            for (uint32_t b0 = (P->G1 > 1 ? 0 : 1); b0 < P->b1s1; b0++) rots.push_back((int32_t)b0 - (int32_t)L);
+            for (uint32_t ci = 0; !rc && ci < cn; ci++)
+                if (cudaMemcpyAsync(LO.at((size_t)ci * P->b1s1), B[c0 + ci]->d, 2 * pw0 * 8, cudaMemcpyDeviceToDevice,
+                                    c->stream))
+                    rc = blb_fail(BLB_ERR_CUDA, "copy failed");
+            if (!rc)
+                rc = rotate_hoisted(c, K, l0, srcs, rots, [&](uint32_t i, uint32_t j) {
+                    const int32_t r = rots[j];
+                    return r > 0 ? LO.at((size_t)i * P->b1s1 + r) : HI.at((size_t)i * P->b1s1 + (r + (int32_t)L));
+                });
         }
-        dev_free(c, d_pairs, bp);
+        if (!rc) {  // inner[c][g1] = sum_b0 m1lo LO + m1hi HI
+            std::vector<uint32_t> start{0};
+            std::vector<LcTerm> terms;
+            for (uint32_t ci = 0; ci < cn; ci++)
+                for (uint32_t g1 = 0; g1 < P->G1; g1++) {
+                    for (uint32_t b0 = 0; b0 < P->b1s1; b0++) {
+                        const uint32_t kappa = g1 * P->b1s1 + b0;
+                        for (uint32_t hi = 0; hi < 2; hi++) {
+                            const uint32_t id = kappa * 2 + hi;
+                            if (!P->nz1[id]) continue;
+                            const uint64_t* ct = (hi ? HI : LO).at((size_t)ci * P->b1s1 + b0);
+                            terms.push_back(LcTerm{ct, P->d_m1 + (size_t)id * pw0});
+                        }
+                    }
+                    start.push_back((uint32_t)terms.size());
+                }
+            rc = lincomb(c, INNER.d, cn * P->G1, start, terms, l0);
+        }
+        if (!rc) {  // ACC[c] = INNER[c][0] + sum_{g1 >= 1} Rot^{g1 b1s1}(INNER[c][g1]), one ModDown per c
+            std::vector<const uint64_t*> base;
+            std::vector<uint64_t*> out;
+            std::vector<int32_t> rots;
+            for (uint32_t ci = 0; ci < cn; ci++) {
+                base.push_back(INNER.at((size_t)ci * P->G1));
+                out.push_back(ACC.at(ci));
+            }
+            for (uint32_t g1 = 1; g1 < P->G1; g1++) rots.push_back((int32_t)(g1 * P->b1s1));
+            if (P->G1 == 1) {
+                for (uint32_t ci = 0; !rc && ci < cn; ci++)
+                    if (cudaMemcpyAsync(ACC.at(ci), base[ci], 2 * pw0 * 8, cudaMemcpyDeviceToDevice, c->stream))
+                        rc = blb_fail(BLB_ERR_CUDA, "copy failed");
+            } else {
+                rc = rotate_sum(c, K, l0, base, out, rots,
+                                [&](uint32_t i, uint32_t j) { return INNER.at((size_t)i * P->G1 + j); });
+            }
+        }
+        if (!rc) rc = rescale_many(c, BP.d, ACC.d, l0, cn, 2);
+
+        // ---- step 2 ----
+        if (!rc) {  // baby steps: Rot^{b}(B'_c) (b >= 1) and Rot^{b - L}(B'_c), hoisted per B'_c
+            std::vector<const uint64_t*> srcs;
+            std::vector<int32_t> rots;
+            for (uint32_t ci = 0; ci < cn; ci++) srcs.push_back(BP.at(ci));
+            for (uint32_t b = 1; b < P->b1s2; b++) rots.push_back((int32_t)b);
+            for (uint32_t b = (P->G2 > 1 ? 0 : 1); b < P->b1s2; b++) rots.push_back((int32_t)b - (int32_t)L);
+            for (uint32_t ci = 0; !rc && ci < cn; ci++)
+                if (cudaMemcpyAsync(BLO.at((size_t)ci * P->b1s2), BP.at(ci), 2 * pw1 * 8, cudaMemcpyDeviceToDevice,
+                                    c->stream))
+                    rc = blb_fail(BLB_ERR_CUDA, "copy failed");
+            if (!rc)
+                rc = rotate_hoisted(c, K, l1, srcs, rots, [&](uint32_t i, uint32_t j) {
+                    const int32_t r = rots[j];
+                    return r > 0 ? BLO.at((size_t)i * P->b1s2 + r) : BHI.at((size_t)i * P->b1s2 + (r + (int32_t)L));
+                });
+        }
+        for (uint32_t ci = 0; !rc && ci < cn; ci++) {  // A at level l2, then its giant-step rotations
+            k_drop<<<dim3((N + kT - 1) / kT, l2 + 1, 2), kT, 0, c->stream>>>(A2.at(ci), A[c0 + ci]->d, l0 + 1, l2 + 1,
+                                                                             N);
+            if (cudaGetLastError() != cudaSuccess) rc = blb_fail(BLB_ERR_CUDA, "drop launch failed");
+            else blb_count_launch();
+            if (!rc && cudaMemcpyAsync(AG.at((size_t)ci * P->G2), A2.at(ci), 2 * pw2 * 8, cudaMemcpyDeviceToDevice,
+                                       c->stream))
+                rc = blb_fail(BLB_ERR_CUDA, "copy failed");
+        }
+        if (!rc) {  // giant steps of A: Rot^{-g b1s2}(A_c), hoisted per A_c
+            std::vector<const uint64_t*> srcs;
+            std::vector<int32_t> rots;
+            for (uint32_t ci = 0; ci < cn; ci++) srcs.push_back(A2.at(ci));
+            for (uint32_t g = 1; g < P->G2; g++) rots.push_back(-(int32_t)(g * P->b1s2));
+            rc = rotate_hoisted(c, K, l2, srcs, rots,
+                                [&](uint32_t i, uint32_t j) { return AG.at((size_t)i * P->G2 + j + 1); });
+        }
+        for (uint32_t t0 = 0; !rc && t0 < L; t0 += Tc) {
+            const uint32_t tn = std::min(Tc, L - t0);
+            {  // VPRE[c][t] = m2lo BLO + m2hi BHI
+                std::vector<uint32_t> start{0};
+                std::vector<LcTerm> terms;
+                for (uint32_t ci = 0; ci < cn; ci++)
+                    for (uint32_t t = t0; t < t0 + tn; t++) {
+                        const uint32_t b = t % P->b1s2;
+                        for (uint32_t hi = 0; hi < 2; hi++) {
+                            const uint32_t id = t * 2 + hi;
+                            if (!P->nz2[id]) continue;
+                            const uint64_t* ct = (hi ? BHI : BLO).at((size_t)ci * P->b1s2 + b);
+                            terms.push_back(LcTerm{ct, P->d_m2 + (size_t)id * pw1});
+                        }
+                        start.push_back((uint32_t)terms.size());
+                    }
+                rc = lincomb(c, VPRE.d, cn * tn, start, terms, l1);
+            }
+            if (!rc) rc = rescale_many(c, V.d, VPRE.d, l1, cn * tn, 2);
+            if (!rc) {  // U[t] (+)= sum_c AG[c][g] (x) V[c][t]
+                std::vector<TensorPair> pairs;
+                for (uint32_t t = t0; t < t0 + tn; t++)
+                    for (uint32_t ci = 0; ci < cn; ci++)
+                        pairs.push_back(
+                            TensorPair{AG.at((size_t)ci * P->G2 + t / P->b1s2), V.at((size_t)ci * tn + (t - t0))});
+                TensorPair* d_pairs = nullptr;
+                size_t bp = 0;
+                rc = upload_table(c, pairs, &d_pairs, &bp);
+                if (!rc) {
+                    k_tensor_acc<<<dim3((N + kT - 1) / kT, l2 + 1, tn), kT, 0, c->stream>>>(
+                        U.at(t0), d_pairs, cn, l2 + 1, N, c->d_q, c->d_bar, c0 > 0);
+                    if (cudaGetLastError() != cudaSuccess) rc = blb_fail(BLB_ERR_CUDA, "tensor launch failed");
+                    else blb_count_launch();
+                }
+                dev_free(c, d_pairs, bp);
+            }
+        }
     }
     if (!rc) {  // relinearize: (d0, d1, d2) -> (d0 + k0, d1 + k1)
         items.clear();
@@ -643,8 +720,8 @@ extern "C" int blb_matmul_cc_plan(blb_ctx* c, const blb_keys* K, const blb_cc_pl
         std::vector<LcTerm> terms;
         for (uint32_t j = 0; j < P->nout; j++) {
             for (uint32_t t = 0; t < L; t++) {
-                const uint32_t id = t * P->nout + j;
-                if (P->nz3[id]) terms.push_back(LcTerm{RT.at(t), P->d_m3 + (size_t)id * pw3});
+                const int32_t m = P->m3_index[(size_t)t * P->nout + j];
+                if (m >= 0) terms.push_back(LcTerm{RT.at(t), P->d_m3 + (size_t)m * pw3});
             }
             start.push_back((uint32_t)terms.size());
         }

@@ -1,6 +1,7 @@
 """GPU matmul_cc (Sec. 5.1, App. C.1) against the oracle, bit-exact on every
-RNS limb, and at the BERT-base attention size (N = 2^16, 12 primes, 12 heads
-in groups of 8 and 4, L = 128, head dim 64) against FP64 within 1e-4."""
+RNS limb (also with steps 1-2 in chunks), and at the BERT-base attention size
+(N = 2^16, 12 primes, 12 heads in groups of 8 and 4, L = 128, head dim 64) and
+a BERT-large one (16 heads, L = 256) against FP64 within 1e-4."""
 import numpy as np
 import pytest
 
@@ -33,14 +34,22 @@ def gpu_cc(ctx, keys, plan, A, B, L, Hg, level, scale):
     return C, cs.unpack_diagonals(zs, L, Hg, Kc), Az, Bz
 
 
-@pytest.mark.parametrize("kind,R,b1s1,b1s2", [("qk", 16, 4, 8), ("qk", 32, 2, 4), ("pv", 16, 4, 8)])
-def test_matmul_cc_parity_with_oracle(kind, R, b1s1, b1s2):
+@pytest.mark.parametrize("kind,R,b1s1,b1s2,L,Hg,chunks", [
+    ("qk", 16, 4, 8, 32, 4, (0, 0)), ("qk", 32, 2, 4, 32, 4, (0, 0)), ("pv", 16, 4, 8, 32, 4, (0, 0)),
+    ("pv", 16, 4, 8, 32, 4, (1, 5)),      # one input ciphertext per pass, ragged diagonal chunks
+    ("qk", 16, 2, 4, 64, 2, (0, 24)),     # Kc = 16, four output ciphertexts
+    ("qk", 32, 4, 4, 32, 2, (0, 0))])     # Kc = L: one output, all-ones step-3 masks
+def test_matmul_cc_parity_with_oracle(kind, R, b1s1, b1s2, L, Hg, chunks):
     prm = wl.SMALL
     o, ctx = make_oracle(prm), make_ctx(prm)
-    L, Hg = 32, 4
     level = o.nQ - 1
     A, B = operands(kind, L, Hg, R, seed=R)
-    plan = ctx.cc_plan(L, Hg, R if kind == "qk" else L, level, b1s1, b1s2)
+    plan = ctx.cc_plan(L, Hg, R if kind == "qk" else L, level, b1s1, b1s2, *chunks)
+    info = plan.info()
+    if chunks[0]:
+        assert info["c_chunk"] == chunks[0] < info["n_c"]
+    if chunks[1]:
+        assert info["t_chunk"] == chunks[1]
     rots = plan.rotations()
     keys = ctx.keygen(SEED, rots, relin=True)
     C, got, Az, Bz = gpu_cc(ctx, keys, plan, A, B, L, Hg, level, prm.scale)
@@ -71,3 +80,37 @@ def test_matmul_cc_bert_base_attention_size():
             _, got, _, _ = gpu_cc(ctx, keys, plan, A, B, L, Hg, level, prm.scale)
             err = np.abs(got - np.einsum("hik,hkj->hij", A, B))
             assert err.max() <= 1e-4, (kind, Hg, err.max())
+
+
+def test_matmul_cc_bert_large_long_sequence():
+    """BERT-large attention shape, 16 heads in one group at L = 256 (Kc = 8):
+    Q K^T (8 input ciphertexts per operand for head dim 64) and P V (32, steps
+    1-2 in chunks under the default workspace budget) against FP64."""
+    prm = wl.BERT_CC
+    ctx = make_ctx(prm)
+    L, Dh, Hg, level = 256, 64, 16, ctx.nQ - 1
+    pq, pv = ctx.cc_plan(L, Hg, Dh, level), ctx.cc_plan(L, Hg, L, level)
+    info = pv.info()
+    assert info["Kc"] == 8 and info["n_c"] == 32
+    assert info["c_chunk"] < info["n_c"]
+    rots = sorted(set(pq.rotations()) | set(pv.rotations()))
+    keys = ctx.keygen(SEED, rots, relin=True)
+    for kind, plan in (("qk", pq), ("pv", pv)):
+        A, B = operands(kind, L, Hg, Dh, seed=3)
+        _, got, _, _ = gpu_cc(ctx, keys, plan, A, B, L, Hg, level, prm.scale)
+        err = np.abs(got - np.einsum("hik,hkj->hij", A, B))
+        assert err.max() <= 1e-4, (kind, err.max())
+
+
+def test_cc_plan_masks_at_512_tokens():
+    """At L = 512 (16 heads, Kc = 4) the plan stores 2 Kc step-1 masks, 2 L
+    step-2 masks and at most 2 Kc distinct step-3 masks (of L^2/Kc)."""
+    prm = wl.BERT_CC
+    ctx = make_ctx(prm)
+    L, Hg, level = 512, 16, ctx.nQ - 1
+    plan = ctx.cc_plan(L, Hg, L, level)
+    info = plan.info()
+    Kc, N = info["Kc"], ctx.N
+    assert Kc == 4
+    limbs = 2 * Kc * (level + 1) + 2 * L * level
+    assert (limbs * N * 8) < info["mask_bytes"] <= (limbs + 2 * Kc * (level - 2)) * N * 8
