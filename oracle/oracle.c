@@ -1141,8 +1141,11 @@ int orc_matmul_cp_diag(const orc_params* p, const orc_galois_set* gk, const uint
  *                                                + m1hi(g1,b0) Rot^{b0-L}(B_c) ) )
  *      -- block kappa = g1 b1s1 + b0 of B'_c holds B[k][(i + kappa) mod L];
  *   2. for t = g b1s2 + b:
- *      V_c = Rescale( m2lo(g,b) Rot^{b}(B'_c) + m2hi(g,b) Rot^{b-L}(B'_c) ),
- *      W_t = Rescale( Relin( sum_c Rot^{-g b1s2}(A_c) (x) V_c ) )
+ *      V_c = m2lo(g,b) Rot^{b}(B'_c) + m2hi(g,b) Rot^{b-L}(B'_c)     (level l-1),
+ *      W_t = Rescale( Relin( Rescale( sum_c Rot^{-g b1s2}(A_c) (x) V_c ) ) )
+ *      with A_c dropped to level l-1: the masked copies are multiplied before
+ *      rescaling and the sum over c is rescaled once (the paper fixes the depth,
+ *      4, not where the rescales fall; this placement keeps it)
  *      -- Rot^{g b1s2}(W_t) would hold diagonal (t + kappa) mod L at block kappa;
  *   3. C_j = Rescale( sum_t m3(t, j) Rot^{g b1s2 - (t mod Kc) Hg L}(W_t) ).
  * The rotations of one ciphertext in steps 1 and 2 (of B_c, B'_c and A_c) are
@@ -1302,16 +1305,15 @@ int orc_matmul_cc(const orc_params* p, const orc_galois_set* gk, const uint64_t*
 
     /* step 2: baby steps of B'_c and giant steps of A_c hoisted */
     {
-        const size_t w2_3 = (size_t)3 * (l2 + 1) * N;
-        uint64_t* U = calloc((size_t)L * w2_3, sizeof(uint64_t));
+        const size_t w1_3 = (size_t)3 * (l1 + 1) * N, w2_3 = (size_t)3 * (l2 + 1) * N;
+        uint64_t* U = calloc((size_t)L * w1_3, sizeof(uint64_t));
         uint64_t* blo = malloc(sizeof(uint64_t) * w1 * b1s2);
         uint64_t* bhi = malloc(sizeof(uint64_t) * w1 * b1s2);
-        uint64_t* rot = malloc(sizeof(uint64_t) * (w1 > w2 ? w1 : w2) * 2 * (b1s2 > G2 ? b1s2 : G2));
-        uint64_t* Ag = malloc(sizeof(uint64_t) * w2 * G2);
-        uint64_t* A2 = malloc(sizeof(uint64_t) * w2);
+        uint64_t* rot = malloc(sizeof(uint64_t) * w1 * 2 * (b1s2 > G2 ? b1s2 : G2));
+        uint64_t* Ag = malloc(sizeof(uint64_t) * w1 * G2);
+        uint64_t* A1 = malloc(sizeof(uint64_t) * w1);
         uint64_t* vacc = malloc(sizeof(uint64_t) * w1);
-        uint64_t* V = malloc(sizeof(uint64_t) * w2);
-        uint64_t* T3 = malloc(sizeof(uint64_t) * w2_3);
+        uint64_t* T3 = malloc(sizeof(uint64_t) * w1_3);
         int32_t rs[2 * ORC_MAX_ROT];
         const uint64_t* ks[2 * ORC_MAX_ROT];
         if (2 * b1s2 > 2 * ORC_MAX_ROT || G2 > 2 * ORC_MAX_ROT) rc = -1;
@@ -1330,14 +1332,14 @@ int orc_matmul_cc(const orc_params* p, const orc_galois_set* gk, const uint64_t*
                 uint64_t* dst = r > 0 ? blo + (size_t)r * w1 : bhi + (size_t)(r + (int32_t)L) * w1;
                 memcpy(dst, rot + (size_t)x * w1, sizeof(uint64_t) * w1);
             }
-            drop_limbs(p, A + (size_t)c * w0, l0, l2, 2, A2);
-            memcpy(Ag, A2, sizeof(uint64_t) * w2);
+            drop_limbs(p, A + (size_t)c * w0, l0, l1, 2, A1);
+            memcpy(Ag, A1, sizeof(uint64_t) * w1);
             for (uint32_t g = 1; g < G2 && !rc; g++) {
                 rs[g - 1] = -(int32_t)(g * b1s2);
                 if (!(ks[g - 1] = find_galois(p, gk, rs[g - 1]))) rc = -2;
             }
             if (rc) break;
-            orc_rotate_hoisted(p, A2, l2, G2 - 1, rs, ks, Ag + w2);
+            orc_rotate_hoisted(p, A1, l1, G2 - 1, rs, ks, Ag + w1);
             for (uint32_t g = 0; g < G2 && !rc; g++) {
                 for (uint32_t b = 0; b < b1s2 && !rc; b++) {
                     const uint32_t t = g * b1s2 + b;
@@ -1354,22 +1356,24 @@ int orc_matmul_cc(const orc_params* p, const orc_galois_set* gk, const uint64_t*
                         used = 1;
                     }
                     if (rc || !used) continue;
-                    orc_rescale(p, vacc, l1, 2, V);
-                    orc_tensor(p, Ag + (size_t)g * w2, V, l2, T3);
-                    uint64_t* Ut = U + (size_t)t * w2_3;
+                    orc_tensor(p, Ag + (size_t)g * w1, vacc, l1, T3);
+                    uint64_t* Ut = U + (size_t)t * w1_3;
                     for (uint32_t poly = 0; poly < 3; poly++)
-                        orc_add(p, Ut + (size_t)poly * (l2 + 1) * N, T3 + (size_t)poly * (l2 + 1) * N, l2 + 1,
-                                Ut + (size_t)poly * (l2 + 1) * N);
+                        orc_add(p, Ut + (size_t)poly * (l1 + 1) * N, T3 + (size_t)poly * (l1 + 1) * N, l1 + 1,
+                                Ut + (size_t)poly * (l1 + 1) * N);
                 }
             }
         }
         for (uint32_t t = 0; t < L && !rc; t++) {
+            uint64_t* U2 = malloc(sizeof(uint64_t) * w2_3);
             uint64_t* R2 = malloc(sizeof(uint64_t) * w2);
-            orc_relinearize(p, U + (size_t)t * w2_3, l2, relin_ksk, R2);
+            orc_rescale(p, U + (size_t)t * w1_3, l1, 3, U2);
+            orc_relinearize(p, U2, l2, relin_ksk, R2);
             orc_rescale(p, R2, l2, 2, W + (size_t)t * w3);
+            free(U2);
             free(R2);
         }
-        free(U); free(blo); free(bhi); free(rot); free(Ag); free(A2); free(vacc); free(V); free(T3);
+        free(U); free(blo); free(bhi); free(rot); free(Ag); free(A1); free(vacc); free(T3);
     }
     if (rc) goto done;
 

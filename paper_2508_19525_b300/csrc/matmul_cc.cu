@@ -11,8 +11,12 @@
 //   1. B'_c = Rescale( sum_{g1} Rot^{g1 b1s1}( sum_{b0} m1lo(g1,b0) Rot^{b0}(B_c)
 //                                               + m1hi(g1,b0) Rot^{b0-L}(B_c) ) )
 //      (block kappa of B'_c holds B[k][(i + kappa) mod L]);
-//   2. for t = g b1s2 + b: V_{c,t} = Rescale( m2lo(g,b) Rot^{b}(B'_c) + m2hi(g,b) Rot^{b-L}(B'_c) ),
-//      W_t = Rescale( Relin( sum_c Rot^{-g b1s2}(A_c) (x) V_{c,t} ) );
+//   2. for t = g b1s2 + b: V_{c,t} = m2lo(g,b) Rot^{b}(B'_c) + m2hi(g,b) Rot^{b-L}(B'_c),
+//      W_t = Rescale( Relin( Rescale( sum_c Rot^{-g b1s2}(A_c) (x) V_{c,t} ) ) ), A_c at
+//      level-1 (one rescale of the sum over c instead of one per V_{c,t}; the
+//      depth, 4, is unchanged).  The tensor product is bilinear, so the sum is
+//      m2lo(t) (.) sum_c AG_{c,g} (x) BLO_{c,b} + m2hi(t) (.) sum_c AG_{c,g} (x) BHI_{c,b}:
+//      one kernel forms both sums and applies the masks (k_cc_step2);
 //   3. C_j = Rescale( sum_t m3(t,j) Rot^{g b1s2 - (t mod Kc) Hg L}(W_t) ).
 // Masks are 0/1 slot vectors encoded at scale q_l of the level they are applied
 // at (so masking and its rescale leave the scale unchanged):
@@ -118,43 +122,80 @@ __global__ void k_lincomb(uint64_t* __restrict__ out, const uint32_t* __restrict
     dst[nN] = barrett128(a1.lo, a1.hi, q, r0, r1);
 }
 
-// U[t] = sum_c a[t][c] (x) b[t][c]: (a0 b0, a0 b1 + a1 b0, a1 b1), n limbs
-struct TensorPair {
-    const uint64_t* a;
-    const uint64_t* b;
+// Step 2 for diagonals t in [t0, t0 + gridDim.x): with g = t / b1s2, b = t % b1s2,
+//   X = sum_{c < cn} AG[c][g] (x) BLO[c][b],  Y = sum_{c < cn} AG[c][g] (x) BHI[c][b]
+//   U[t] (+)= mlo(t) (.) X + mhi(t) (.) Y
+// (x) = (a0 b0, a0 b1 + a1 b0, a1 b1); the middle term by Karatsuba as
+// (a0 + a1)(b0 + b1) - a0 b0 - a1 b1 (three products, operand sums < 2q, lazy
+// 128-bit sums reduced every 8 terms: at most 8 (2q)^2 + q < 2^126 for q < 2^60).
+// AG, BLO, BHI: stacks of 2-polynomial ciphertexts of n limbs (stride 2 n N),
+// indexed c G2 + g and c b1s2 + b; U: 3-polynomial ciphertexts, U[t - t0] at
+// U + (t - t0) 3 n N.  The diagonal is the fastest grid index so that the
+// blocks running together share their AG / BLO / BHI tiles in L2.
+struct MaskPair {
+    const uint64_t* lo;  // (n) x N words at the mask level, nullptr = all-zero mask
+    const uint64_t* hi;
 };
-// (accumulate: U[t] += the sum)
-__global__ void k_tensor_acc(uint64_t* __restrict__ U, const TensorPair* __restrict__ pairs, uint32_t n_c,
-                             uint32_t n, uint32_t N, const uint64_t* __restrict__ qs,
-                             const uint64_t* __restrict__ bar, bool accumulate)
+constexpr int kS2 = 128;
+__global__ void __launch_bounds__(kS2) k_cc_step2(uint64_t* __restrict__ U, const uint64_t* __restrict__ AG,
+                                                  const uint64_t* __restrict__ BLO, const uint64_t* __restrict__ BHI,
+                                                  const MaskPair* __restrict__ masks, uint32_t t0, uint32_t cn,
+                                                  uint32_t b1s2, uint32_t G2, uint32_t n, uint32_t N,
+                                                  const uint64_t* __restrict__ qs, const uint64_t* __restrict__ bar,
+                                                  bool accumulate)
 {
-    const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x, i = blockIdx.y, t = blockIdx.z;
-    if (c >= N) return;
+    const uint32_t t = t0 + blockIdx.x, k = blockIdx.y * kS2 + threadIdx.x, i = blockIdx.z;
+    if (k >= N) return;
+    const uint32_t g = t / b1s2, b = t % b1s2;
     const uint64_t q = qs[i], r0 = bar[2 * i], r1 = bar[2 * i + 1];
-    const size_t nN = (size_t)n * N, off = (size_t)i * N + c;
-    uint64_t* dst = U + (size_t)t * 3 * nN + off;
-    acc128 x0{0, 0}, x1{0, 0}, x2{0, 0};
-    if (accumulate) {
-        x0.lo = dst[0];
-        x1.lo = dst[nN];
-        x2.lo = dst[2 * nN];
-    }
-    for (uint32_t k = 0; k < n_c; k++) {
-        const TensorPair p = pairs[(size_t)t * n_c + k];
-        const uint64_t a0 = p.a[off], a1 = p.a[nN + off], b0 = p.b[off], b1 = p.b[nN + off];
-        mad128(x0, a0, b0);
-        mad128(x1, a0, b1);
-        mad128(x1, a1, b0);
-        mad128(x2, a1, b1);
-        if ((k & 7) == 7) {
-            x0 = acc128{barrett128(x0.lo, x0.hi, q, r0, r1), 0};
-            x1 = acc128{barrett128(x1.lo, x1.hi, q, r0, r1), 0};
-            x2 = acc128{barrett128(x2.lo, x2.hi, q, r0, r1), 0};
+    const size_t nN = (size_t)n * N, off = (size_t)i * N + k, cw = 2 * nN;
+    const MaskPair mp = masks[t];
+    const bool use_lo = mp.lo != nullptr, use_hi = mp.hi != nullptr;
+    acc128 x0{0, 0}, xs{0, 0}, x2{0, 0}, y0{0, 0}, ys{0, 0}, y2{0, 0};
+    const uint64_t* pa = AG + (size_t)g * cw + off;
+    const uint64_t* pl = BLO + (size_t)b * cw + off;
+    const uint64_t* ph = BHI + (size_t)b * cw + off;
+    const size_t sa = (size_t)G2 * cw, sb = (size_t)b1s2 * cw;
+    for (uint32_t c = 0; c < cn; c++) {
+        const uint64_t a0 = pa[0], a1 = pa[nN], as = a0 + a1;
+        if (use_lo) {
+            const uint64_t v0 = pl[0], v1 = pl[nN];
+            mad128(x0, a0, v0);
+            mad128(x2, a1, v1);
+            mad128(xs, as, v0 + v1);
         }
+        if (use_hi) {
+            const uint64_t v0 = ph[0], v1 = ph[nN];
+            mad128(y0, a0, v0);
+            mad128(y2, a1, v1);
+            mad128(ys, as, v0 + v1);
+        }
+        if ((c & 7) == 7) {
+            x0 = acc128{barrett128(x0.lo, x0.hi, q, r0, r1), 0};
+            xs = acc128{barrett128(xs.lo, xs.hi, q, r0, r1), 0};
+            x2 = acc128{barrett128(x2.lo, x2.hi, q, r0, r1), 0};
+            y0 = acc128{barrett128(y0.lo, y0.hi, q, r0, r1), 0};
+            ys = acc128{barrett128(ys.lo, ys.hi, q, r0, r1), 0};
+            y2 = acc128{barrett128(y2.lo, y2.hi, q, r0, r1), 0};
+        }
+        pa += sa;
+        pl += sb;
+        ph += sb;
     }
-    dst[0] = barrett128(x0.lo, x0.hi, q, r0, r1);
-    dst[nN] = barrett128(x1.lo, x1.hi, q, r0, r1);
-    dst[2 * nN] = barrett128(x2.lo, x2.hi, q, r0, r1);
+    const uint64_t X0 = barrett128(x0.lo, x0.hi, q, r0, r1), X2 = barrett128(x2.lo, x2.hi, q, r0, r1);
+    const uint64_t X1 = sub_mod(sub_mod(barrett128(xs.lo, xs.hi, q, r0, r1), X0, q), X2, q);
+    const uint64_t Y0 = barrett128(y0.lo, y0.hi, q, r0, r1), Y2 = barrett128(y2.lo, y2.hi, q, r0, r1);
+    const uint64_t Y1 = sub_mod(sub_mod(barrett128(ys.lo, ys.hi, q, r0, r1), Y0, q), Y2, q);
+    const uint64_t ml = use_lo ? mp.lo[off] : 0, mh = use_hi ? mp.hi[off] : 0;
+    uint64_t* dst = U + (size_t)blockIdx.x * 3 * nN + off;
+    const uint64_t Xv[3] = {X0, X1, X2}, Yv[3] = {Y0, Y1, Y2};
+#pragma unroll
+    for (int poly = 0; poly < 3; poly++) {
+        acc128 u{accumulate ? dst[poly * nN] : 0, 0};
+        mad128(u, ml, Xv[poly]);
+        mad128(u, mh, Yv[poly]);
+        dst[poly * nN] = barrett128(u.lo, u.hi, q, r0, r1);
+    }
 }
 
 // copy polynomials from `from` limbs per polynomial to `to` limbs (drop the top limbs)
@@ -276,16 +317,10 @@ extern "C" int blb_cc_plan_create(blb_ctx* c, uint32_t L, uint32_t Hg, uint32_t 
     const uint32_t N = c->N;
     {  // chunking of steps 1-2 under the workspace budget
         const uint64_t l0 = level + 1, l1 = level, l2 = level - 1;
-        const uint64_t per_c = 16ull * N *
-                               ((2ull * b1s1 + P->G1 + 1) * l0 + (1 + 2ull * b1s2) * l1 + (1ull + P->G2) * l2);
-        const uint64_t per_ct = 16ull * N * (l1 + l2);
+        const uint64_t per_c = 16ull * N * ((2ull * b1s1 + P->G1 + 1) * l0 + (2ull + 2ull * b1s2 + P->G2) * l1);
+        (void)l2;
         const uint64_t budget = (sched && sched->workspace_bytes) ? sched->workspace_bytes : (24ull << 30);
-        uint32_t Cc = P->n_c, Tc = L;
-        if ((uint64_t)P->n_c * (per_c + L * per_ct) > budget) {
-            Cc = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(P->n_c, budget / 2 / per_c));
-            const uint64_t left = budget > Cc * per_c ? budget - Cc * per_c : 0;
-            Tc = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(L, left / ((uint64_t)Cc * per_ct)));
-        }
+        uint32_t Cc = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(P->n_c, budget / per_c)), Tc = L;
         if (sched && sched->c_chunk) Cc = std::min(sched->c_chunk, P->n_c);
         if (sched && sched->t_chunk) Tc = std::min(sched->t_chunk, L);
         P->c_chunk = Cc;
@@ -539,11 +574,11 @@ extern "C" int blb_matmul_cc_plan(blb_ctx* c, const blb_keys* K, const blb_cc_pl
     int rc = BLB_OK;
     std::vector<KsItem> items;
 
-    // Steps 1 and 2 run over chunks of Cc input ciphertexts and, inside, of Tc
-    // diagonals t; the tensor products of every chunk are summed into U mod q,
-    // so the result does not depend on the chunking.
+    // Steps 1 and 2 run over chunks of Cc input ciphertexts; the step-2 sums of
+    // every chunk are added into U mod q, so the result does not depend on the
+    // chunking.  Step 2 is launched for Tc diagonals at a time.
     const uint32_t Cc = P->c_chunk, Tc = P->t_chunk;
-    Stack LO, HI, INNER, ACC, BP, BLO, BHI, A2, AG, VPRE, V, U, WP, W;
+    Stack LO, HI, INNER, ACC, BP, BLO, BHI, A1, AG, U, U2, WP, W;
     rc = LO.alloc(c, Cc * P->b1s1, l0);
     if (!rc) rc = HI.alloc(c, Cc * P->b1s1, l0);
     if (!rc) rc = INNER.alloc(c, Cc * P->G1, l0);
@@ -551,11 +586,17 @@ extern "C" int blb_matmul_cc_plan(blb_ctx* c, const blb_keys* K, const blb_cc_pl
     if (!rc) rc = BP.alloc(c, Cc, l1);
     if (!rc) rc = BLO.alloc(c, Cc * P->b1s2, l1);
     if (!rc) rc = BHI.alloc(c, Cc * P->b1s2, l1);
-    if (!rc) rc = A2.alloc(c, Cc, l2);
-    if (!rc) rc = AG.alloc(c, Cc * P->G2, l2);
-    if (!rc) rc = VPRE.alloc(c, Cc * Tc, l1);
-    if (!rc) rc = V.alloc(c, Cc * Tc, l2);
-    if (!rc) rc = U.alloc(c, L, l2, 3);
+    if (!rc) rc = A1.alloc(c, Cc, l1);
+    if (!rc) rc = AG.alloc(c, Cc * P->G2, l1);
+    if (!rc) rc = U.alloc(c, L, l1, 3);
+    if (!rc) rc = U2.alloc(c, L, l2, 3);
+    std::vector<MaskPair> mpairs(L);
+    for (uint32_t t = 0; t < L; t++)
+        mpairs[t] = MaskPair{P->nz2[2 * t] ? P->d_m2 + (size_t)(2 * t) * pw1 : nullptr,
+                             P->nz2[2 * t + 1] ? P->d_m2 + (size_t)(2 * t + 1) * pw1 : nullptr};
+    MaskPair* d_mpairs = nullptr;
+    size_t bmp = 0;
+    if (!rc) rc = upload_table(c, mpairs, &d_mpairs, &bmp);
     if (!rc) rc = WP.alloc(c, L, l2);
     if (!rc) rc = W.alloc(c, L, l3);
     for (uint32_t c0 = 0; !rc && c0 < n_c; c0 += Cc) {
@@ -632,72 +673,44 @@ extern "C" int blb_matmul_cc_plan(blb_ctx* c, const blb_keys* K, const blb_cc_pl
                     return r > 0 ? BLO.at((size_t)i * P->b1s2 + r) : BHI.at((size_t)i * P->b1s2 + (r + (int32_t)L));
                 });
         }
-        for (uint32_t ci = 0; !rc && ci < cn; ci++) {  // A at level l2, then its giant-step rotations
-            k_drop<<<dim3((N + kT - 1) / kT, l2 + 1, 2), kT, 0, c->stream>>>(A2.at(ci), A[c0 + ci]->d, l0 + 1, l2 + 1,
+        for (uint32_t ci = 0; !rc && ci < cn; ci++) {  // A at level l1, then its giant-step rotations
+            k_drop<<<dim3((N + kT - 1) / kT, l1 + 1, 2), kT, 0, c->stream>>>(A1.at(ci), A[c0 + ci]->d, l0 + 1, l1 + 1,
                                                                              N);
             if (cudaGetLastError() != cudaSuccess) rc = blb_fail(BLB_ERR_CUDA, "drop launch failed");
             else blb_count_launch();
-            if (!rc && cudaMemcpyAsync(AG.at((size_t)ci * P->G2), A2.at(ci), 2 * pw2 * 8, cudaMemcpyDeviceToDevice,
+            if (!rc && cudaMemcpyAsync(AG.at((size_t)ci * P->G2), A1.at(ci), 2 * pw1 * 8, cudaMemcpyDeviceToDevice,
                                        c->stream))
                 rc = blb_fail(BLB_ERR_CUDA, "copy failed");
         }
         if (!rc) {  // giant steps of A: Rot^{-g b1s2}(A_c), hoisted per A_c
             std::vector<const uint64_t*> srcs;
             std::vector<int32_t> rots;
-            for (uint32_t ci = 0; ci < cn; ci++) srcs.push_back(A2.at(ci));
+            for (uint32_t ci = 0; ci < cn; ci++) srcs.push_back(A1.at(ci));
             for (uint32_t g = 1; g < P->G2; g++) rots.push_back(-(int32_t)(g * P->b1s2));
-            rc = rotate_hoisted(c, K, l2, srcs, rots,
+            rc = rotate_hoisted(c, K, l1, srcs, rots,
                                 [&](uint32_t i, uint32_t j) { return AG.at((size_t)i * P->G2 + j + 1); });
         }
-        for (uint32_t t0 = 0; !rc && t0 < L; t0 += Tc) {
+        for (uint32_t t0 = 0; !rc && t0 < L; t0 += Tc) {  // U[t] (+)= masked tensor sums of this chunk
             const uint32_t tn = std::min(Tc, L - t0);
-            {  // VPRE[c][t] = m2lo BLO + m2hi BHI
-                std::vector<uint32_t> start{0};
-                std::vector<LcTerm> terms;
-                for (uint32_t ci = 0; ci < cn; ci++)
-                    for (uint32_t t = t0; t < t0 + tn; t++) {
-                        const uint32_t b = t % P->b1s2;
-                        for (uint32_t hi = 0; hi < 2; hi++) {
-                            const uint32_t id = t * 2 + hi;
-                            if (!P->nz2[id]) continue;
-                            const uint64_t* ct = (hi ? BHI : BLO).at((size_t)ci * P->b1s2 + b);
-                            terms.push_back(LcTerm{ct, P->d_m2 + (size_t)id * pw1});
-                        }
-                        start.push_back((uint32_t)terms.size());
-                    }
-                rc = lincomb(c, VPRE.d, cn * tn, start, terms, l1);
-            }
-            if (!rc) rc = rescale_many(c, V.d, VPRE.d, l1, cn * tn, 2);
-            if (!rc) {  // U[t] (+)= sum_c AG[c][g] (x) V[c][t]
-                std::vector<TensorPair> pairs;
-                for (uint32_t t = t0; t < t0 + tn; t++)
-                    for (uint32_t ci = 0; ci < cn; ci++)
-                        pairs.push_back(
-                            TensorPair{AG.at((size_t)ci * P->G2 + t / P->b1s2), V.at((size_t)ci * tn + (t - t0))});
-                TensorPair* d_pairs = nullptr;
-                size_t bp = 0;
-                rc = upload_table(c, pairs, &d_pairs, &bp);
-                if (!rc) {
-                    k_tensor_acc<<<dim3((N + kT - 1) / kT, l2 + 1, tn), kT, 0, c->stream>>>(
-                        U.at(t0), d_pairs, cn, l2 + 1, N, c->d_q, c->d_bar, c0 > 0);
-                    if (cudaGetLastError() != cudaSuccess) rc = blb_fail(BLB_ERR_CUDA, "tensor launch failed");
-                    else blb_count_launch();
-                }
-                dev_free(c, d_pairs, bp);
-            }
+            k_cc_step2<<<dim3(tn, (N + kS2 - 1) / kS2, l1 + 1), kS2, 0, c->stream>>>(
+                U.at(t0), AG.d, BLO.d, BHI.d, d_mpairs, t0, cn, P->b1s2, P->G2, l1 + 1, N, c->d_q, c->d_bar, c0 > 0);
+            if (cudaGetLastError() != cudaSuccess) rc = blb_fail(BLB_ERR_CUDA, "step-2 launch failed");
+            else blb_count_launch();
         }
     }
+    if (!rc) rc = rescale_many(c, U2.d, U.d, l1, L, 3);
     if (!rc) {  // relinearize: (d0, d1, d2) -> (d0 + k0, d1 + k1)
         items.clear();
         const uint64_t* rk = K->find(0)->d;
         for (uint32_t t = 0; t < L; t++) {
-            const uint64_t* u = U.at(t);
+            const uint64_t* u = U2.at(t);
             uint64_t* o = WP.at(t);
             items.push_back(KsItem{u, u + 2 * pw2, u + pw2, rk, o, o + pw2, 1});
         }
         rc = keyswitch_batch(c, l2, items.data(), (uint32_t)items.size(), 0);
     }
     if (!rc) rc = rescale_many(c, W.d, WP.d, l2, L, 2);
+    dev_free(c, d_mpairs, bmp);
 
     // ---- step 3 ----
     Stack RT, CP;
