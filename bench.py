@@ -503,7 +503,96 @@ def cfg4_batching(n_seqs=8, plain_chunks=6, candidates=(16, 32, 64, 128), groups
     out["graph_speedup_vs_plain"] = round(tot_p / tot_g, 3)
     out["plain_tokens_per_s"] = round(T / tot_p, 1)
     out["speedup"] = round(tot_p / tot_b, 3)
+    del keys
+    torch.cuda.empty_cache()
+    att = cfg4_attention(ctx, stream, [int(x) for x in lengths])
+    out["attention"] = att
+    out["ct_pt_and_attention_tokens_per_s"] = round(T / (tot_b + att["s_total"]), 1)
     return out
+
+
+def cfg4_attention(ctx, stream, lengths, heads=16, dh=64, seed=45, check=2):
+    """The ct-ct attention products of the BERT-large-shaped sequences: per
+    sequence, Q_h K_h^T and P_h V_h for its 16 heads in one group (matmul_cc,
+    Sec. 5.1), the length padded to a power of two L >= 64 (Kc = N/2/(16 L) <= L)
+    with zero rows and columns past the sequence's end, V_h padded to L columns
+    for the square diagonal-packed output.  One plan pair per padded length,
+    the Galois keys of all of them; each product timed with CUDA events after
+    one warm-up product per plan; the first `check` sequences decrypted against
+    FP64."""
+    import torch
+    from paper_2508_19525_b300 import layer as ly
+    from paper_2508_19525_b300 import workloads as wl
+    level = ctx.nQ - 1
+    pad = [max(64, 1 << int(np.ceil(np.log2(x)))) for x in lengths]
+    plans = {Lp: (ctx.cc_plan(Lp, heads, dh, level), ctx.cc_plan(Lp, heads, Lp, level)) for Lp in sorted(set(pad))}
+    rots = sorted({r for pq, pv in plans.values() for r in pq.rotations() + pv.rotations()})
+    t0 = time.perf_counter()
+    keys = ctx.keygen(46, rots, relin=True)
+    ctx.sync()
+    keygen_s = time.perf_counter() - t0
+
+    def operands(si, l, Lp):
+        Q, K, V, P = wl.attention_operands(Lp, heads, dh, seed=seed + si)
+        for M in (Q, K, V):
+            M[:, l:] = 0.0
+        P[:, l:, :] = 0.0
+        P[:, :, l:] = 0.0
+        P[:, :l] /= P[:, :l].sum(axis=2, keepdims=True)
+        Vp = np.concatenate([V, np.zeros((heads, Lp, Lp - dh))], axis=2)
+        return (("qk", Q, np.transpose(K, (0, 2, 1))), ("pv", P, Vp))
+
+    def encrypt(plan, A, B, Lp, nonce):
+        info = plan.info()
+        Az = ly.pack_heads(A, Lp, heads, info["Kc"], info["n_c"], rows=False)
+        Bz = ly.pack_heads(B, Lp, heads, info["Kc"], info["n_c"], rows=True)
+        n = info["n_c"]
+        return (ctx.encrypt_batch(keys, ctx.encode_batch(Az, level), [nonce + c for c in range(n)]),
+                ctx.encrypt_batch(keys, ctx.encode_batch(Bz, level), [nonce + 1000 + c for c in range(n)]))
+
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    warm = set()
+    per_len = {}
+    total, err = 0.0, 0.0
+    for si, (l, Lp) in enumerate(zip(lengths, pad)):
+        for (kind, A, B), plan in zip(operands(si, l, Lp), plans[Lp]):
+            Ac, Bc = encrypt(plan, A, B, Lp, 10000 * si)
+            if (Lp, kind) not in warm:
+                ctx.matmul_cc_plan(keys, plan, Ac, Bc)
+                warm.add((Lp, kind))
+            ctx.sync()
+            ev0.record(stream)
+            C = ctx.matmul_cc_plan(keys, plan, Ac, Bc)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            sec = ev0.elapsed_time(ev1) / 1e3
+            total += sec
+            e = per_len.setdefault(str(Lp), {"sequences": 0, "qk_ms": 0.0, "pv_ms": 0.0})
+            e[kind + "_ms"] += sec * 1e3
+            if kind == "qk":
+                e["sequences"] += 1
+            if si < check:
+                Kc = plan.info()["Kc"]
+                Z = np.stack([ctx.decrypt(keys, c, coeffs=False)[1] for c in C])
+                got = ly.unpack_diagonals(Z, Lp, heads, Kc)
+                err = max(err, float(np.abs(got - np.einsum("hik,hkj->hij", A, B)).max()))
+            del Ac, Bc, C
+    for e in per_len.values():
+        e["qk_ms"] = round(e["qk_ms"] / e["sequences"], 2)
+        e["pv_ms"] = round(e["pv_ms"] / e["sequences"], 2)
+    info = {str(Lp): {k: v for k, v in pv.info().items() if k in ("Kc", "n_c", "b1s2", "c_chunk", "t_chunk")}
+            for Lp, (_, pv) in plans.items()}
+    for pq, pv in plans.values():
+        pq.free()
+        pv.free()
+    del keys
+    torch.cuda.empty_cache()
+    T = int(sum(lengths))
+    return {"workload": f"{len(lengths)} sequences, Q K^T and P V per sequence, {heads} heads of dim {dh} in one "
+                        f"group, lengths padded to powers of two >= 64, N=2^16, 12 primes",
+            "padded_lengths": pad, "rotation_keys": len(rots), "keygen_s": round(keygen_s, 2),
+            "per_padded_length_ms": per_len, "pv_plans": info, "s_total": round(total, 4),
+            "tokens_per_s": round(T / total, 1), "max_abs_err_vs_fp64": err}
 
 
 def layer_bench():
