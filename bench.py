@@ -1032,6 +1032,45 @@ def ncu_conv(count=18):
     print(json.dumps({"ncu_conv": count}))
 
 
+def ncu_cc(L, kind="pv", heads=16, dh=64):
+    """Profiling case of matmul_cc at the BERT-large attention shape: one Q K^T
+    (kind "qk", inner dimension 64) or P V ("pv", inner dimension L) product of
+    16 heads in one group at L tokens, N = 2^16, 12 primes, dnum 4; one untimed
+    product, then one bracketed by cudaProfilerStart/Stop."""
+    import torch
+    from paper_2508_19525_b300 import blb
+    from paper_2508_19525_b300 import layer as ly
+    from paper_2508_19525_b300 import workloads as wl
+    prm = wl.BERT_CC
+    stream = torch.cuda.Stream()
+    ctx = blb.Context(prm.logN, prm.q_bits, prm.p_bits, 4, prm.scale, stream=stream)
+    level = ctx.nQ - 1
+    plan = ctx.cc_plan(L, heads, dh if kind == "qk" else L, level)
+    keys = ctx.keygen(46, plan.rotations(), relin=True)
+    Q, K, V, P = wl.attention_operands(L, heads, dh, seed=1)
+    if kind == "qk":
+        A, B = Q, np.transpose(K, (0, 2, 1))
+    else:
+        A, B = P, np.concatenate([V, np.zeros((heads, L, L - dh))], axis=2)
+    info = plan.info()
+    Az = ly.pack_heads(A, L, heads, info["Kc"], info["n_c"], rows=False)
+    Bz = ly.pack_heads(B, L, heads, info["Kc"], info["n_c"], rows=True)
+    Ac = ctx.encrypt_batch(keys, ctx.encode_batch(Az, level), list(range(info["n_c"])))
+    Bc = ctx.encrypt_batch(keys, ctx.encode_batch(Bz, level), [1000 + c for c in range(info["n_c"])])
+    C = ctx.matmul_cc_plan(keys, plan, Ac, Bc)
+    ctx.sync()
+    del C
+    l0 = blb.kernel_launches()
+    torch.cuda.profiler.start()
+    t0 = time.perf_counter()
+    C = ctx.matmul_cc_plan(keys, plan, Ac, Bc)
+    ctx.sync()
+    sec = time.perf_counter() - t0
+    torch.cuda.profiler.stop()
+    print(json.dumps({"ncu_cc": f"{kind} L={L} heads={heads}", "s": round(sec, 4),
+                      "launches": blb.kernel_launches() - l0, "plan": info}))
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -1045,6 +1084,9 @@ def main():
     ap.add_argument("--ncu-seqs", type=int, default=1, help="sequences in the profiling case")
     ap.add_argument("--ncu-step", action="store_true", help="run one profiled BERT-base step and exit")
     ap.add_argument("--ncu-conv", action="store_true", help="run the conversion profiling case and exit")
+    ap.add_argument("--ncu-cc", type=int, default=0, metavar="L",
+                    help="run one profiled BERT-large matmul_cc product at L tokens and exit")
+    ap.add_argument("--ncu-cc-kind", choices=("qk", "pv"), default="pv")
     ap.add_argument("--ntt-split", type=int, default=None, choices=(-1, 0, 1),
                     help="fix the NTT pass split of the profiling cases (default: autotuned)")
     ap.add_argument("--batch", type=int, default=8, help="sequences per batched step (1 = skip)")
@@ -1067,6 +1109,8 @@ def main():
         return ncu_step(args.ntt_split)
     if args.ncu_conv:
         return ncu_conv()
+    if args.ncu_cc:
+        return ncu_cc(args.ncu_cc, args.ncu_cc_kind)
     args.cpu_sample = (args.cpu_rotations, args.cpu_products)
     if args.impl == "reference":
         run_reference(args)
