@@ -1032,18 +1032,20 @@ def ncu_conv(count=18):
     print(json.dumps({"ncu_conv": count}))
 
 
-def ncu_cc(L, kind="pv", heads=16, dh=64):
-    """Profiling case of matmul_cc at the BERT-large attention shape: one Q K^T
-    (kind "qk", inner dimension 64) or P V ("pv", inner dimension L) product of
-    16 heads in one group at L tokens, N = 2^16, 12 primes, dnum 4; one untimed
+def ncu_cc(L, kind="pv", params="large", dh=64):
+    """Profiling case of matmul_cc: one Q K^T (kind "qk", inner dimension 64) or
+    P V ("pv", inner dimension L) product at L tokens; params "large": the
+    BERT-large attention shape (16 heads in one group, N = 2^16, 12 primes,
+    dnum 4), "base": 8 heads at the BERT-base ct-pt parameters (N = 2^15,
+    8 primes, dnum 3), small enough for full ncu captures.  One untimed
     product, then one bracketed by cudaProfilerStart/Stop."""
     import torch
     from paper_2508_19525_b300 import blb
     from paper_2508_19525_b300 import layer as ly
     from paper_2508_19525_b300 import workloads as wl
-    prm = wl.BERT_CC
+    prm, heads, dnum = (wl.BERT_CC, 16, 4) if params == "large" else (wl.BERT_CP, 8, wl.BERT_CP.dnum)
     stream = torch.cuda.Stream()
-    ctx = blb.Context(prm.logN, prm.q_bits, prm.p_bits, 4, prm.scale, stream=stream)
+    ctx = blb.Context(prm.logN, prm.q_bits, prm.p_bits, dnum, prm.scale, stream=stream)
     level = ctx.nQ - 1
     plan = ctx.cc_plan(L, heads, dh if kind == "qk" else L, level)
     keys = ctx.keygen(46, plan.rotations(), relin=True)
@@ -1067,7 +1069,7 @@ def ncu_cc(L, kind="pv", heads=16, dh=64):
     ctx.sync()
     sec = time.perf_counter() - t0
     torch.cuda.profiler.stop()
-    print(json.dumps({"ncu_cc": f"{kind} L={L} heads={heads}", "s": round(sec, 4),
+    print(json.dumps({"ncu_cc": f"{kind} L={L} heads={heads} N={ctx.N}", "s": round(sec, 4),
                       "launches": blb.kernel_launches() - l0, "plan": info}))
 
 
@@ -1087,6 +1089,7 @@ def main():
     ap.add_argument("--ncu-cc", type=int, default=0, metavar="L",
                     help="run one profiled BERT-large matmul_cc product at L tokens and exit")
     ap.add_argument("--ncu-cc-kind", choices=("qk", "pv"), default="pv")
+    ap.add_argument("--ncu-cc-params", choices=("large", "base"), default="large")
     ap.add_argument("--ntt-split", type=int, default=None, choices=(-1, 0, 1),
                     help="fix the NTT pass split of the profiling cases (default: autotuned)")
     ap.add_argument("--batch", type=int, default=8, help="sequences per batched step (1 = skip)")
@@ -1110,7 +1113,7 @@ def main():
     if args.ncu_conv:
         return ncu_conv()
     if args.ncu_cc:
-        return ncu_cc(args.ncu_cc, args.ncu_cc_kind)
+        return ncu_cc(args.ncu_cc, args.ncu_cc_kind, args.ncu_cc_params)
     args.cpu_sample = (args.cpu_rotations, args.cpu_products)
     if args.impl == "reference":
         run_reference(args)

@@ -88,12 +88,14 @@ __device__ __forceinline__ uint64_t mul_mod(uint64_t a, uint64_t b, uint64_t q, 
 struct acc128 {
     uint64_t lo, hi;
 };
+// acc += a b (mod 2^128): the low word with carry out, the high word with the
+// carry in, as one multiply-add pair (the additions ride on the multiplies)
 __device__ __forceinline__ void mad128(acc128& acc, uint64_t a, uint64_t b)
 {
-    uint64_t p_lo = a * b, p_hi = __umul64hi(a, b);
-    uint64_t lo = acc.lo + p_lo;
-    acc.hi += p_hi + (lo < p_lo);
-    acc.lo = lo;
+    asm("mad.lo.cc.u64 %0, %2, %3, %0;\n\t"
+        "madc.hi.u64 %1, %2, %3, %1;"
+        : "+l"(acc.lo), "+l"(acc.hi)
+        : "l"(a), "l"(b));
 }
 
 // ---------------------------------------------------------------------------

@@ -399,18 +399,28 @@ __global__ void k_ksb_finish(const DevGroup* __restrict__ groups, const DevProdu
     if (k >= N) return;
     const DevGroup G = groups[gr];
     const uint64_t q = qs[i], r0 = bar[2 * i], r1 = bar[2 * i + 1];
+    // lazy 128-bit sums: reduced after every product for q >= 2^50 (beta terms
+    // below 2^120 each), once at the end below that (terms below 2^100)
+    const bool per_product = q >= (1ull << 50);
     uint64_t s[2] = {0, 0};
+    acc128 a0{0, 0}, a1{0, 0};
     for (uint32_t x = G.prod0; x < G.prod1; x++) {
         const DevProduct P = prods[x];
         const uint64_t* xs = ext + (size_t)P.src * beta * E * N + (size_t)i * N + perm_index(k, logN, P.g);
-        acc128 a0{0, 0}, a1{0, 0};
         for (uint32_t j = 0; j < beta; j++) {
             const uint64_t v = xs[(size_t)j * E * N];
             mad128(a0, v, P.key[(((size_t)j * 2 + 0) * np + i) * N + k]);
             mad128(a1, v, P.key[(((size_t)j * 2 + 1) * np + i) * N + k]);
         }
-        s[0] = add_mod(s[0], barrett128(a0.lo, a0.hi, q, r0, r1), q);
-        s[1] = add_mod(s[1], barrett128(a1.lo, a1.hi, q, r0, r1), q);
+        if (per_product) {
+            s[0] = add_mod(s[0], barrett128(a0.lo, a0.hi, q, r0, r1), q);
+            s[1] = add_mod(s[1], barrett128(a1.lo, a1.hi, q, r0, r1), q);
+            a0 = a1 = acc128{0, 0};
+        }
+    }
+    if (!per_product) {
+        s[0] = barrett128(a0.lo, a0.hi, q, r0, r1);
+        s[1] = barrett128(a1.lo, a1.hi, q, r0, r1);
     }
 #pragma unroll
     for (uint32_t p = 0; p < 2; p++) {
