@@ -732,6 +732,80 @@ def serving_bench(n_requests=64, rate=20.0, sat_rate=400.0, budget_gb=24, max_ba
     return out
 
 
+def serving_cfg5_bench(n_requests=32, rate=20.0, budget_gb=120, max_batch=4, group=2, m=32, b1=32):
+    """Continuous batching at the serving configuration's own parameters:
+    N = 2^16, 12 primes, dnum 4; Poisson arrivals at `rate` req/s, half
+    GPT2-base-shaped requests (hidden 768, lengths U[32, 1024]) and half
+    BERT-base-shaped ones (U[16, 512]), each its own client key set.  Every
+    request is cut into m-row chunks (k = 1024 columns per ciphertext hold a
+    chunk's 768 features), one plan pair per model (QKV 768 -> 2304, output
+    projection 768 -> 768); a stage of up to `max_batch` requests runs as
+    cross-client products over `group` chunks each.  Plain: one request per
+    iteration and one chunk per product."""
+    import torch
+    from paper_2508_19525_b300 import blb
+    from paper_2508_19525_b300 import batching as bt
+    from paper_2508_19525_b300 import workloads as wl
+    from paper_2508_19525_b300.serving import ChunkEngine, Request, Server, percentile
+    prm = wl.BERT_CC
+    stream = torch.cuda.Stream()
+    ctx = blb.Context(prm.logN, prm.q_bits, prm.p_bits, 4, prm.scale, stream=stream)
+    level = ctx.nQ - 1
+    k = ctx.N // 2 // m
+    rots = bt.cp_rotations(m, k, b1)
+    rng = np.random.default_rng(2025)
+    t0 = time.perf_counter()
+    plans = {}
+    for name in ("bert", "gpt2"):
+        Wq = rng.uniform(-1, 1, (D, D_QKV))
+        Wo = rng.uniform(-1, 1, (D, D_O))
+        plans[name] = (ctx.cp_plan(m, D, Wq, D_QKV, level, b1), ctx.cp_plan(m, D, Wo, D_O, level - 1, b1), rots)
+    ctx.sync()
+    encode_s = time.perf_counter() - t0
+    plaintext_gb = sum(p.info()["plaintext_bytes"] for q, o, _ in plans.values() for p in (q, o)) / 1e9
+
+    def requests(n, seed):
+        r = np.random.default_rng(seed)
+        t, out = 0.0, []
+        for i in range(n):
+            t += r.exponential(1.0 / rate)
+            gpt = i % 2 == 0
+            seq = int(r.integers(32, 1025)) if gpt else int(r.integers(16, 513))
+            out.append(Request(rid=i, client_seed=20_000 + i, model="gpt2" if gpt else "bert", seq=seq, m=m,
+                               arrival=t, X=r.uniform(-1, 1, (seq, D))))
+        return out
+
+    def run(reqs, mb, grp):
+        srv = Server(ChunkEngine(ctx, plans, level, D, D_QKV, m, group=grp), budget_bytes=budget_gb << 30,
+                     max_batch=mb)
+        t0 = time.perf_counter()
+        done = srv.run(reqs)
+        span = time.perf_counter() - t0
+        lat = [r.latency * 1e3 for r in done]
+        return {"p50_ms": round(percentile(lat, 50), 1), "p99_ms": round(percentile(lat, 99), 1),
+                "tokens_per_s": round(sum(r.seq for r in done) / span, 1), "span_s": round(span, 2),
+                "mean_batch": round(float(np.mean([n for _, n in srv.iterations])), 2),
+                "iterations": len(srv.iterations)}
+
+    run(requests(4, seed=1), max_batch, group)  # warm-up (kernels, arenas)
+    reqs = requests(n_requests, seed=7)
+    out = {"workload": f"{n_requests} requests, Poisson {rate:g} req/s, half GPT2-base-shaped (lengths U[32,1024]) "
+                       f"and half BERT-base-shaped (U[16,512]); QKV 768x2304 then output projection 768x768 and "
+                       f"masking of every output; {m}-row chunks, N=2^16, 12 primes, dnum 4, each request its own "
+                       f"client key set ({len(rots)} rotation keys, {len(rots) * ctx.key_bytes() / 1e9:.1f} GB)",
+           "tokens": int(sum(r.seq for r in reqs)), "plaintext_gb": round(plaintext_gb, 1),
+           "encode_s": round(encode_s, 2), "budget_gb": budget_gb, "max_batch": max_batch,
+           "chunks_per_product": group,
+           "batched": run(requests(n_requests, seed=7), max_batch, group),
+           "plain": run(requests(n_requests, seed=7), 1, 1)}
+    out["speedup"] = round(out["batched"]["tokens_per_s"] / out["plain"]["tokens_per_s"], 3)
+    for q, o, _ in plans.values():
+        q.free()
+        o.free()
+    torch.cuda.empty_cache()
+    return out
+
+
 def timed(w, steps, host, world):
     torch = w.torch
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -801,6 +875,7 @@ def run_blb(args):
     layer = layer_bench() if args.layer and world == 1 else None
     attn = attention_cc(max(1, min(5, args.steps // 4))) if args.attention and world == 1 else None
     serving = serving_bench() if args.serving and world == 1 else None
+    serving5 = serving_cfg5_bench() if args.serving_cfg5 and world == 1 else None
     if rank != 0:
         return
     peaks = {}
@@ -859,6 +934,7 @@ def run_blb(args):
         "batched": batched,
         "attention_cc": attn,
         "serving": serving,
+        "serving_n65536": serving5,
         "layernorm_head": lnorm,
         "encoder_layer": layer,
         "cfg4_batching": cfg4,
@@ -1103,6 +1179,8 @@ def main():
                     help="skip the LayerNorm-head (rotate-and-sum) measurement")
     ap.add_argument("--no-conversion", dest="conversion", action="store_false",
                     help="skip the CKKS <-> MPC conversion measurement")
+    ap.add_argument("--no-serving-n65536", dest="serving_cfg5", action="store_false",
+                    help="skip the continuous-batching measurement at N=2^16 (lengths up to 1024, chunked)")
     ap.add_argument("--no-serving", dest="serving", action="store_false",
                     help="skip the continuous-batching serving measurement")
     args = ap.parse_args()

@@ -20,8 +20,11 @@ iteration of their group, so requests at different stages interleave on the
 device.  Every result is bit-identical to the same request served alone.
 
 The scheduler is independent of the GPU: `Server` drives an engine with the
-methods `admit`, `run` and `release` (`GpuEngine` below; the tests use a fake
-engine on CPU).
+methods `admit`, `run` and `release` (`GpuEngine` and `ChunkEngine` below; the
+tests use a fake engine on CPU).  `GpuEngine` packs a whole request into one
+product of its padded length; `ChunkEngine` cuts every request into m-row
+chunks (one plan pair per model serves every length) and runs a stage of a
+batch as cross-client products over groups of chunks.
 """
 from dataclasses import dataclass, field
 import time
@@ -211,6 +214,102 @@ class GpuEngine:
 
     def release(self, r):
         # the masked outputs and P1's shares stay with the request; keys go
+        keys = r.state["keys"] if self.keep_outputs else r.state.pop("keys")
+        r.state["p0"] = self.ctx.decrypt_batch(keys, r.state["masked"])[0]
+        if not self.keep_outputs:
+            keys.free()
+
+    def idle(self, seconds):
+        time.sleep(max(0.0, min(seconds, 0.002)))
+
+
+class ChunkEngine:
+    """Token-chunked requests: a request of `seq` tokens is cut into
+    ceil(seq / m) chunks of m rows (the last zero-padded), each packed
+    spatial-first into ceil(d / k) ciphertexts (k = N / (2 m) columns per
+    ciphertext), so one plan pair per model, plans[model] = (plan_qkv, plan_o,
+    rotations), serves every sequence length.  A stage of a batch of requests
+    runs as `blb_matmul_cp_multi` calls over up to `group` chunks each, every
+    chunk key-switched with its own client's keys; chunk c of a request returns
+    the limbs of its single product.  The requests' `m` is the chunk size.
+    Masking covers, per chunk, the QKV output ciphertexts after the first
+    ceil(d / k) and the output projection."""
+
+    def __init__(self, ctx, plans, level, d, d_out_qkv, m, group=4, sync=True, keep_outputs=False):
+        self.ctx = ctx
+        self.plans = plans
+        self.level = level
+        self.d = d
+        self.d_out_qkv = d_out_qkv
+        self.m = m
+        self.k = ctx.N // 2 // m
+        self.nX = -(-d // self.k)
+        self.group = group
+        self.sync = sync
+        self.keep_outputs = keep_outputs
+        self.key_bytes = ctx.key_bytes()
+
+    def chunks(self, r):
+        return -(-r.seq // self.m)
+
+    def footprint(self, r):
+        qkv, o, rots = self.plans[r.model]
+        ct = lambda lv: 2 * (lv + 1) * self.ctx.N * 8
+        i, io = qkv.info(), o.info()
+        per_chunk = (i["nX"] * ct(self.level) + i["nY"] * ct(self.level - 1) + io["nY"] * ct(self.level - 2)
+                     + 2 * (i["nY"] - i["nX"] + io["nY"]) * self.ctx.N * 8)
+        return len(rots) * self.key_bytes + self.chunks(r) * per_chunk
+
+    def admit(self, r):
+        from .batching import pack_chunks
+        ctx = self.ctx
+        _, _, rots = self.plans[r.model]
+        keys = ctx.keygen(r.client_seed, rots)
+        r.state["keys"] = keys
+        Z = pack_chunks(r.X, self.m, self.k, self.nX).reshape(-1, self.m * self.k)
+        base = 1_000_000 + 10_000 * r.rid
+        cts = ctx.encrypt_batch(keys, ctx.encode_batch(Z, self.level), [base + i for i in range(len(Z))])
+        r.state["in"] = [cts[c * self.nX:(c + 1) * self.nX] for c in range(self.chunks(r))]
+
+    def run(self, key, batch):
+        ctx = self.ctx
+        model, _, stage = key
+        qkv, o, _ = self.plans[model]
+        items = [(r, c) for r in batch for c in range(self.chunks(r))]
+        for g0 in range(0, len(items), self.group):
+            part = items[g0:g0 + self.group]
+            keys = [r.state["keys"] for r, _ in part]
+            if stage == 0:
+                outs = ctx.matmul_cp_multi(keys, qkv, [r.state["in"][c] for r, c in part])
+                for (r, c), Y in zip(part, outs):
+                    r.state.setdefault("qkv", {})[c] = Y
+            else:
+                outs = ctx.matmul_cp_multi(keys, o, [r.state["qkv"][c][:self.nX] for r, c in part])
+                for (r, c), O in zip(part, outs):
+                    r.state.setdefault("o", {})[c] = O
+        for r in batch:
+            if stage == 0:
+                del r.state["in"]
+                continue
+            outs_r = []
+            for c in range(self.chunks(r)):
+                outs_r += r.state["qkv"][c][self.nX:] + r.state["o"][c]
+            del r.state["qkv"], r.state["o"]
+            if self.keep_outputs:
+                r.state["outs"] = outs_r
+            masked, shares = [], []
+            for lv in sorted({c.level for c in outs_r}):
+                cs = [c for c in outs_r if c.level == lv]
+                base = 2_000_000 + 10_000 * r.rid + 5_000 * (lv % 2)
+                mk, sh = ctx.he2mpc_batch(r.state["keys"], cs, [base + j for j in range(len(cs))])
+                masked += mk
+                shares.append(sh)
+            r.state["masked"] = masked
+            r.state["shares"] = np.concatenate(shares, axis=0)
+        if self.sync:
+            ctx.sync()
+
+    def release(self, r):
         keys = r.state["keys"] if self.keep_outputs else r.state.pop("keys")
         r.state["p0"] = self.ctx.decrypt_batch(keys, r.state["masked"])[0]
         if not self.keep_outputs:

@@ -1,12 +1,13 @@
 """Cross-client batching on the GPU: blb_matmul_cp_multi gives each client the
 limbs of its own single product, and a request served among others (arriving
 at random, batched with other clients' requests at other stages) returns the
-same limbs as when it is served alone; its decrypted result matches FP64."""
+same limbs as when it is served alone; its decrypted result matches FP64.
+Both engines: whole requests padded to a bucket, and token-chunked requests."""
 import numpy as np
 import pytest
 
 from paper_2508_19525_b300 import workloads as wl
-from paper_2508_19525_b300.serving import GpuEngine, Request, Server, bucket
+from paper_2508_19525_b300.serving import ChunkEngine, GpuEngine, Request, Server, bucket
 
 from _helpers import cp_rotations, make_ctx, pack_cols
 
@@ -92,3 +93,60 @@ def test_result_alone_equals_result_in_the_mix():
         got_o = got[:, (nY - nX) * k: (nY - nX) * k + D]
         assert np.abs(got_q - Yq[:, nX * k:]).max() <= 1e-4
         assert np.abs(got_o - Yq[:, :D] @ Wo).max() <= 1e-4
+
+
+def test_chunked_result_alone_equals_result_in_the_mix():
+    """Requests of 8-60 tokens cut into 16-row chunks (1-4 chunks, one plan pair
+    per model), served in a mix with up to 3 chunks per cross-client product
+    and alone: same masked limbs and shares; every chunk's outputs decrypt to
+    the FP64 products."""
+    prm = wl.SMALL
+    ctx = make_ctx(prm)
+    level, m = ctx.nQ - 1, 16
+    k = ctx.N // 2 // m
+    b1 = 8
+    weights = {name: (wl.uniform((D, D_QKV), seed=s), wl.uniform((D, D), seed=s + 1))
+               for name, s in (("a", 31), ("b", 41))}
+    plans = {name: (ctx.cp_plan(m, D, Wq, D_QKV, level, b1), ctx.cp_plan(m, D, Wo, D, level - 1, b1),
+                    cp_rotations(m, b1, k // b1))
+             for name, (Wq, Wo) in weights.items()}
+
+    def reqs():
+        rng = np.random.default_rng(8)
+        t, out = 0.0, []
+        for i in range(6):
+            t += rng.exponential(0.005)
+            seq = int(rng.integers(8, 61))
+            out.append(Request(rid=i, client_seed=700 + i, model="a" if i % 2 else "b", seq=seq, m=m,
+                               arrival=t, X=wl.uniform((seq, D), seed=950 + i)))
+        return out
+
+    def server(keep=False):
+        return Server(ChunkEngine(ctx, plans, level, D, D_QKV, m, group=3, keep_outputs=keep),
+                      budget_bytes=8 << 30, max_batch=4)
+
+    mix = reqs()
+    srv = server(keep=True)
+    done = srv.run(mix)
+    assert len(done) == 6 and max(n for _, n in srv.iterations) > 1
+    nX, nY = (D + k - 1) // k, (D_QKV + k - 1) // k
+    for r in mix:
+        alone = reqs()[r.rid]
+        server().run([alone])
+        assert np.array_equal(r.state["p0"], alone.state["p0"]), r.rid
+        assert np.array_equal(r.state["shares"], alone.state["shares"]), r.rid
+        Wq, Wo = weights[r.model]
+        per = nY - nX + 1
+        n_ch = -(-r.seq // m)
+        assert len(r.state["outs"]) == n_ch * per
+        Xp = np.zeros((n_ch * m, D))
+        Xp[: r.seq] = r.X
+        for c in range(n_ch):
+            Yq = Xp[c * m:(c + 1) * m] @ Wq
+            cts = r.state["outs"][c * per:(c + 1) * per]
+            slots = np.stack([ctx.decrypt(r.state["keys"], x, coeffs=False)[1] for x in cts])
+            got = np.concatenate([z.reshape(k, m).T for z in slots], axis=1)
+            got_q = got[:, : D_QKV - nX * k]
+            got_o = got[:, (nY - nX) * k: (nY - nX) * k + D]
+            assert np.abs(got_q - Yq[:, nX * k:]).max() <= 1e-4, (r.rid, c)
+            assert np.abs(got_o - Yq[:, :D] @ Wo).max() <= 1e-4, (r.rid, c)
