@@ -210,14 +210,26 @@ __global__ void k_drop(uint64_t* __restrict__ out, const uint64_t* __restrict__ 
     out[((size_t)poly * to + i) * N + c] = in[((size_t)poly * from + i) * N + c];
 }
 
+// Device copy of a host table.  Under stream capture the copy goes to a buffer
+// the context keeps (a graph replays the launches that read it) and *bytes is
+// 0, so free_table leaves it alone.
 template <class T>
 int upload_table(blb_ctx* c, const std::vector<T>& v, T** d, size_t* bytes)
 {
+    if (capturing(c)) {
+        *bytes = 0;
+        return persist_upload(c, v.data(), v.size() * sizeof(T), (void**)d);
+    }
     *bytes = std::max<size_t>(v.size() * sizeof(T), 16);
     *d = (T*)dev_alloc(c, *bytes);
     if (!*d) return blb_fail(BLB_ERR_OOM, "table allocation failed");
     BLB_CUDA(cudaMemcpyAsync(*d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, c->stream));
     return BLB_OK;
+}
+
+void free_table(blb_ctx* c, void* d, size_t bytes)
+{
+    if (d && bytes) dev_free(c, d, bytes);
 }
 
 // Device buffer holding `count` ciphertexts of 2 polynomials at `level`
@@ -380,7 +392,7 @@ extern "C" int blb_cc_plan_create(blb_ctx* c, uint32_t L, uint32_t Hg, uint32_t 
         size_t bi = 0;
         rc = upload_table(c, rep3, &d_ids, &bi);
         if (!rc) rc = encode_masks(c, spec, 3, (uint32_t)n3, level - 3, P->d_m3, d_ids);
-        dev_free(c, d_ids, bi);
+        free_table(c, d_ids, bi);
     }
     if (rc) {
         blb_cc_plan_free(P);
@@ -471,8 +483,8 @@ static int lincomb(blb_ctx* c, uint64_t* out, uint32_t nout, const std::vector<u
         if (cudaGetLastError() != cudaSuccess) rc = blb_fail(BLB_ERR_CUDA, "lincomb launch failed");
         else blb_count_launch();
     }
-    dev_free(c, d_start, bs);
-    dev_free(c, d_terms, bt);
+    free_table(c, d_start, bs);
+    free_table(c, d_terms, bt);
     return rc;
 }
 
@@ -713,7 +725,7 @@ extern "C" int blb_matmul_cc_plan(blb_ctx* c, const blb_keys* K, const blb_cc_pl
         rc = keyswitch_batch(c, l2, items.data(), (uint32_t)items.size(), 0);
     }
     if (!rc) rc = rescale_many(c, W.d, WP.d, l2, L, 2);
-    dev_free(c, d_mpairs, bmp);
+    free_table(c, d_mpairs, bmp);
 
     // ---- step 3 ----
     Stack RT, CP;

@@ -114,3 +114,45 @@ def test_cc_plan_masks_at_512_tokens():
     assert Kc == 4
     limbs = 2 * Kc * (level + 1) + 2 * L * level
     assert (limbs * N * 8) < info["mask_bytes"] <= (limbs + 2 * Kc * (level - 2)) * N * 8
+
+
+def test_matmul_cc_captured_graph_replays_the_product():
+    """P V at N = 2^12 (two input ciphertexts, steps 1-2 in chunks of one)
+    captured as one CUDA graph: a replay gives the eager limbs, and after new
+    operands are copied into the captured inputs a replay gives the eager
+    limbs for those."""
+    import torch
+    from paper_2508_19525_b300 import blb
+    prm = wl.SMALL
+    ctx = blb.Context(prm.logN, prm.q_bits, prm.p_bits, prm.dnum, prm.scale, stream=torch.cuda.Stream())
+    L, Hg, R = 32, 4, 32
+    level = ctx.nQ - 1
+    plan = ctx.cc_plan(L, Hg, R, level, 4, 8, 1, 0)
+    keys = ctx.keygen(SEED, plan.rotations(), relin=True)
+    info = plan.info()
+    Kc, n_c = info["Kc"], info["n_c"]
+
+    def encrypt(seed, base):
+        A, B = operands("pv", L, Hg, 16, seed=seed)
+        Az, Bz = cs.pack(A, L, Hg, Kc, n_c, rows=False), cs.pack(B, L, Hg, Kc, n_c, rows=True)
+        return ([ctx.encrypt(keys, ctx.encode(z, level, prm.scale), base + c) for c, z in enumerate(Az)],
+                [ctx.encrypt(keys, ctx.encode(z, level, prm.scale), base + 50 + c) for c, z in enumerate(Bz)],
+                np.einsum("hik,hkj->hij", A, B))
+
+    Ac, Bc, _ = encrypt(1, 0)
+    An, Bn, want = encrypt(2, 200)
+    graph, Cg = ctx.capture(lambda: ctx.matmul_cc_plan(keys, plan, Ac, Bc))
+    graph.replay()
+    torch.cuda.synchronize()
+    eager = ctx.matmul_cc_plan(keys, plan, Ac, Bc)
+    for a, b in zip(Cg, eager):
+        assert np.array_equal(ctx.ct_export(a), ctx.ct_export(b))
+    for dst, src in zip(Ac + Bc, An + Bn):
+        ctx.ct_copy(dst, src)
+    graph.replay()
+    torch.cuda.synchronize()
+    eager2 = ctx.matmul_cc_plan(keys, plan, An, Bn)
+    for a, b in zip(Cg, eager2):
+        assert np.array_equal(ctx.ct_export(a), ctx.ct_export(b))
+    zs = np.stack([ctx.decrypt(keys, c, coeffs=False)[1] for c in Cg])
+    assert np.abs(cs.unpack_diagonals(zs, L, Hg, Kc) - want).max() <= 1e-4
