@@ -755,7 +755,8 @@ def serving_bench(n_requests=64, rate=20.0, sat_rate=400.0, budget_gb=24, max_ba
     return out
 
 
-def serving_cfg5_bench(n_requests=32, rate=20.0, budget_gb=120, max_batch=4, group=2, m=32, b1=32):
+def serving_cfg5_bench(n_requests=32, rate=20.0, light_rate=2.0, n_light=12, budget_gb=120, max_batch=4, group=2,
+                       m=32, b1=32):
     """Continuous batching at the serving configuration's own parameters:
     N = 2^16, 12 primes, dnum 4; Poisson arrivals at `rate` req/s, half
     GPT2-base-shaped requests (hidden 768, lengths U[32, 1024]) and half
@@ -764,7 +765,9 @@ def serving_cfg5_bench(n_requests=32, rate=20.0, budget_gb=120, max_batch=4, gro
     chunk's 768 features), one plan pair per model (QKV 768 -> 2304, output
     projection 768 -> 768); a stage of up to `max_batch` requests runs as
     cross-client products over `group` chunks each.  Plain: one request per
-    iteration and one chunk per product."""
+    iteration and one chunk per product.  A second, shorter run at
+    `light_rate` req/s (below what one GPU serves) shows the latency without
+    queueing."""
     import torch
     from paper_2508_19525_b300 import blb
     from paper_2508_19525_b300 import batching as bt
@@ -787,11 +790,11 @@ def serving_cfg5_bench(n_requests=32, rate=20.0, budget_gb=120, max_batch=4, gro
     encode_s = time.perf_counter() - t0
     plaintext_gb = sum(p.info()["plaintext_bytes"] for q, o, _ in plans.values() for p in (q, o)) / 1e9
 
-    def requests(n, seed):
+    def requests(n, seed, rps=rate):
         r = np.random.default_rng(seed)
         t, out = 0.0, []
         for i in range(n):
-            t += r.exponential(1.0 / rate)
+            t += r.exponential(1.0 / rps)
             gpt = i % 2 == 0
             seq = int(r.integers(32, 1025)) if gpt else int(r.integers(16, 513))
             out.append(Request(rid=i, client_seed=20_000 + i, model="gpt2" if gpt else "bert", seq=seq, m=m,
@@ -822,6 +825,9 @@ def serving_cfg5_bench(n_requests=32, rate=20.0, budget_gb=120, max_batch=4, gro
            "batched": run(requests(n_requests, seed=7), max_batch, group),
            "plain": run(requests(n_requests, seed=7), 1, 1)}
     out["speedup"] = round(out["batched"]["tokens_per_s"] / out["plain"]["tokens_per_s"], 3)
+    light = requests(n_light, seed=11, rps=light_rate)
+    out["light"] = {"rate_rps": light_rate, "requests": n_light, "tokens": int(sum(r.seq for r in light)),
+                    "batched": run(light, max_batch, group)}
     for q, o, _ in plans.values():
         q.free()
         o.free()
