@@ -240,7 +240,7 @@ class Workload:
         outs = Y[self.n_in:] + O
         masked, _ = ctx.he2mpc_batch(keys, outs, self.nonces(len(outs)), share_out=p1)
         ctx.decrypt_batch(keys, masked, coeff_out=p0)
-        return (Y, O) if keep else None
+        return (Y, O, cts) if keep else None
 
     def step_batched(self, S):
         """S sequences through the same plans in one batched pass per product."""
@@ -257,7 +257,7 @@ class Workload:
         ctx.decrypt_batch(keys, masked, coeff_out=self.bp0)
 
     def accuracy(self):
-        Y, O = self.step(keep=True)
+        Y, O, _ = self.step(keep=True)
         got_qkv = unpack_columns(np.stack([self.ctx.decrypt(self.keys, y, coeffs=False)[1] for y in Y]), M, self.k, D_QKV)
         got_o = unpack_columns(np.stack([self.ctx.decrypt(self.keys, y, coeffs=False)[1] for y in O]), M, self.k, D_O)
         err = np.concatenate([(got_qkv - self.ref_qkv).ravel(), (got_o - self.ref_o).ravel()])
