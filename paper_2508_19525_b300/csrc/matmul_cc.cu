@@ -127,9 +127,7 @@ __global__ void k_lincomb(uint64_t* __restrict__ out, const uint32_t* __restrict
 //   U[t] (+)= mlo(t) (.) X + mhi(t) (.) Y
 // (x) = (a0 b0, a0 b1 + a1 b0, a1 b1); the middle term by Karatsuba as
 // (a0 + a1)(b0 + b1) - a0 b0 - a1 b1 (three products, operand sums < 2q, lazy
-// 128-bit sums).  For q >= 2^50 the sums are reduced every 8 terms (at most
-// 8 (2q)^2 + q < 2^126 for q < 2^60); for q < 2^50 a term is below 2^102 and
-// they are reduced once, at the end (cn < 2^20).
+// 128-bit sums reduced every 8 terms: at most 8 (2q)^2 + q < 2^126 for q < 2^60).
 // AG, BLO, BHI: stacks of 2-polynomial ciphertexts of n limbs (stride 2 n N),
 // indexed c G2 + g and c b1s2 + b; U: 3-polynomial ciphertexts, U[t - t0] at
 // U + (t - t0) 3 n N.  The diagonal is the fastest grid index so that the
@@ -158,7 +156,6 @@ __global__ void __launch_bounds__(kS2) k_cc_step2(uint64_t* __restrict__ U, cons
     const uint64_t* pl = BLO + (size_t)b * cw + off;
     const uint64_t* ph = BHI + (size_t)b * cw + off;
     const size_t sa = (size_t)G2 * cw, sb = (size_t)b1s2 * cw;
-    const bool big = q >= (1ull << 50);
     for (uint32_t c = 0; c < cn; c++) {
         const uint64_t a0 = pa[0], a1 = pa[nN], as = a0 + a1;
         if (use_lo) {
@@ -173,7 +170,7 @@ __global__ void __launch_bounds__(kS2) k_cc_step2(uint64_t* __restrict__ U, cons
             mad128(y2, a1, v1);
             mad128(ys, as, v0 + v1);
         }
-        if (big && (c & 7) == 7) {
+        if ((c & 7) == 7) {
             x0 = acc128{barrett128(x0.lo, x0.hi, q, r0, r1), 0};
             xs = acc128{barrett128(xs.lo, xs.hi, q, r0, r1), 0};
             x2 = acc128{barrett128(x2.lo, x2.hi, q, r0, r1), 0};
