@@ -47,16 +47,39 @@ Scratch::~Scratch()
     for (auto& b : bufs) dev_free(c, b.first, b.second);
 }
 
+int host_upload(blb_ctx* c, void* dst, const void* src, size_t bytes)
+{
+    if (!bytes) return BLB_OK;
+    if (!capturing(c)) {
+        BLB_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, c->stream));
+        return BLB_OK;
+    }
+    void* kept = nullptr;
+    BLB_TRY(persist_upload(c, src, bytes, &kept));
+    BLB_CUDA(cudaMemcpyAsync(dst, kept, bytes, cudaMemcpyDeviceToDevice, c->stream));
+    return BLB_OK;
+}
+
+int refuse_capture(blb_ctx* c, const char* what)
+{
+    if (!capturing(c)) return BLB_OK;
+    return blb_fail(BLB_ERR_ARG, std::string(what) + " cannot run inside a graph capture");
+}
+
 int copy_in(blb_ctx* c, void* dst, const void* src, size_t bytes)
 {
-    BLB_CUDA(cudaMemcpyAsync(dst, src, bytes, is_device_ptr(src) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
-                             c->stream));
+    const bool dev = is_device_ptr(src);
+    if (!dev && capturing(c))
+        return blb_fail(BLB_ERR_ARG, "host input buffer during graph capture: pass device memory");
+    BLB_CUDA(cudaMemcpyAsync(dst, src, bytes, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
     return BLB_OK;
 }
 
 int copy_out(blb_ctx* c, void* dst, const void* src, size_t bytes)
 {
     bool dev = is_device_ptr(dst);
+    if (!dev && capturing(c))
+        return blb_fail(BLB_ERR_ARG, "host output buffer during graph capture: pass device memory");
     BLB_CUDA(cudaMemcpyAsync(dst, src, bytes, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
     if (!dev) BLB_CUDA(cudaStreamSynchronize(c->stream));
     return BLB_OK;
@@ -580,7 +603,7 @@ extern "C" int blb_mul_const(blb_ctx* c, const blb_ct* a, const double* vals, ui
     uint64_t* pt = (uint64_t*)S.get((size_t)nl * N * 8);
     uint64_t* prod = (uint64_t*)S.get((size_t)2 * nl * N * 8);
     if (!dz || !pt || !prod) return blb_fail(BLB_ERR_OOM, "mul_const buffers");
-    BLB_CUDA(cudaMemcpyAsync(dz, z.data(), (size_t)s * 8, cudaMemcpyHostToDevice, c->stream));
+    BLB_TRY(host_upload(c, dz, z.data(), (size_t)s * 8));
     BLB_TRY(encode_slots(c, dz, 1, s, lv, s_c, pt));
     BLB_TRY(launch_mul_rows(c, prod, a->d, pt, 2 * nl, c->qmap(nl), nl));
     blb_ct* r;
@@ -788,6 +811,7 @@ static int cp_plan_build(blb_ctx* c, uint32_t m, uint32_t d, const double* W, ui
 extern "C" int blb_cp_plan_create(blb_ctx* c, uint32_t m, uint32_t d, const double* W, uint32_t d_out,
                                   uint32_t level, const blb_sched* sched, blb_cp_plan** out)
 {
+    if (c) BLB_TRY(refuse_capture(c, "plan creation"));
     return cp_plan_build(c, m, d, W, d_out, level, sched, nullptr, out);
 }
 
@@ -795,6 +819,7 @@ extern "C" int blb_cp_plan_create_diag(blb_ctx* c, uint32_t L, uint32_t n_groups
                                        const double* W, uint32_t d_out, uint32_t level, const blb_sched* sched,
                                        blb_cp_plan** out)
 {
+    if (c) BLB_TRY(refuse_capture(c, "plan creation"));
     if (!c || !Hg || !W || !out || n_groups == 0) return blb_fail(BLB_ERR_ARG, "null argument");
     *out = nullptr;
     const uint32_t s = c->N / 2;
@@ -1031,6 +1056,7 @@ extern "C" int blb_he2mpc(blb_ctx* c, const blb_keys* K, const blb_ct* ct, uint6
 // ===========================================================================
 extern "C" int blb_ntt(blb_ctx* c, uint64_t* data, uint32_t rows, const uint32_t* prime_idx, int inverse)
 {
+    if (c && data && !is_device_ptr(data)) BLB_TRY(refuse_capture(c, "blb_ntt on host data"));
     if (!c || !data || !prime_idx) return blb_fail(BLB_ERR_ARG, "null argument");
     for (uint32_t r = 0; r < rows; r++)
         if (prime_idx[r] >= c->np) return blb_fail(BLB_ERR_ARG, "prime index out of range");

@@ -270,15 +270,24 @@ struct blb_cp_plan {
     size_t bytes;
 };
 
+bool capturing(blb_ctx* ctx);
+int persist_upload(blb_ctx* ctx, const void* host, size_t bytes, void** dev);
+
 // stream-ordered temporary device buffers of one call, freed at scope exit
 struct Scratch {
     blb_ctx* c;
     std::vector<std::pair<void*, size_t>> bufs;
     explicit Scratch(blb_ctx* ctx) : c(ctx) {}
     void* get(size_t bytes);
+    // a device copy of a host table; under stream capture it goes to a buffer
+    // the context keeps, since a replay reads it after the host vector is gone
     template <typename T>
     T* upload(const std::vector<T>& v)
     {
+        if (capturing(c)) {
+            void* p = nullptr;
+            return persist_upload(c, v.data(), v.size() * sizeof(T), &p) == BLB_OK ? (T*)p : nullptr;
+        }
         T* d = (T*)get(v.size() * sizeof(T));
         if (d && !v.empty() &&
             cudaMemcpyAsync(d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, c->stream) != cudaSuccess)
@@ -350,6 +359,15 @@ int launch_rescale_stack(blb_ctx* ctx, uint64_t* out, const uint64_t* in, uint32
 int new_ciphertext(blb_ctx* ctx, uint32_t level, uint32_t npolys, double scale, blb_ct** out);
 int new_ct(blb_ctx* c, uint32_t level, uint32_t npolys, double scale, blb_ct** out);
 uint64_t* op_row(blb_ctx* c, size_t r);                             // row r of the operation scratch
+// a host table of the library into device memory on the stream; under stream
+// capture through a buffer the context keeps (a replay copies it from there)
+int host_upload(blb_ctx* c, void* dst, const void* src, size_t bytes);
+// an error if the context's stream is being captured (for calls that read
+// results back on the host, create cached tables or plans, or take caller host
+// memory)
+int refuse_capture(blb_ctx* c, const char* what);
+// caller buffers: host or device; a host buffer is refused while the stream is
+// being captured (a graph cannot keep reading or writing caller host memory)
 int copy_in(blb_ctx* c, void* dst, const void* src, size_t bytes);  // host or device source
 int copy_out(blb_ctx* c, void* dst, const void* src, size_t bytes); // host (synchronises) or device target
 int launch_tensor(blb_ctx* ctx, uint64_t* out, const uint64_t* a, const uint64_t* b, uint32_t level);

@@ -384,6 +384,7 @@ int2 fx_root(uint32_t N, uint32_t k, double c)
 int fx_tables(blb_ctx* c)
 {
     if (c->d_fx_root) return BLB_OK;
+    BLB_TRY(refuse_capture(c, "the first conversion of a context"));  // the tables it caches
     const uint32_t N = c->N, s = N / 2;
     std::vector<int2> root(N);
     for (uint32_t k = 0; k < N; k++) root[k] = fx_root(N, k, 1.0);
@@ -416,6 +417,7 @@ int fx_twist(blb_ctx* c, double mul, const int2** out)
             *out = t.d;
             return BLB_OK;
         }
+    BLB_TRY(refuse_capture(c, "the first conversion with this scale"));  // the table it caches
     const uint32_t N = c->N, s = N / 2;
     std::vector<int2> tw(s);
     for (uint32_t k = 0; k < s; k++) tw[k] = fx_root(N, k, mul);

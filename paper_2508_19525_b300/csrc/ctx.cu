@@ -44,7 +44,7 @@ static cudaEvent_t pool_event(blb_ctx* c)
 
 ProfScope::ProfScope(blb_ctx* ctx, const char* name, uint64_t algorithmic_bytes) : c(ctx), site(-1)
 {
-    if (!c || !c->profiling) return;
+    if (!c || !c->profiling || capturing(c)) return;  // a captured launch has no time of its own
     for (size_t i = 0; i < c->prof.size(); i++)
         if (c->prof[i].name == name) site = (int)i;
     if (site < 0) {

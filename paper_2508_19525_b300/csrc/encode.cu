@@ -206,6 +206,8 @@ int encode_slots(blb_ctx* ctx, const double* d_z, uint32_t npts, uint32_t n, uin
                  uint64_t* d_out)
 {
     if (npts == 0) return BLB_OK;
+    if (capturing(ctx))  // the overflow flag is read back on the host
+        return blb_fail(BLB_ERR_ARG, "encoding cannot run inside a graph capture");
     const uint32_t logs = ctx->logN - 1, s = 1u << logs, nl = level + 1;
     if (n > s) return blb_fail(BLB_ERR_ARG, "more values than slots");
     const size_t words = (size_t)npts * s * 2;  // double2 per slot

@@ -235,6 +235,8 @@ static int noalloc_scratch(uint64_t** out)
 extern "C" int blb_keyswitch_noalloc(blb_ctx* c, const blb_keys* K, int32_t rot, const uint64_t* d, uint32_t level,
                                      uint64_t* out)
 {
+    if (c && ((d && !is_device_ptr(d)) || (out && !is_device_ptr(out))))
+        BLB_TRY(refuse_capture(c, "blb_keyswitch_noalloc on host buffers"));
     if (!c || !K || !d || !out) return blb_fail(BLB_ERR_ARG, "null argument");
     if (level >= c->nQ) return blb_fail(BLB_ERR_LEVEL, "level out of range");
     const KeyEntry* k = K->find(galois_element(c->N, rot));

@@ -294,6 +294,7 @@ extern "C" int blb_cc_plan_create(blb_ctx* c, uint32_t L, uint32_t Hg, uint32_t 
 {
     if (!c || !out) return blb_fail(BLB_ERR_ARG, "null argument");
     *out = nullptr;
+    BLB_TRY(refuse_capture(c, "plan creation"));
     const uint32_t s = c->N / 2;
     if (L == 0 || Hg == 0 || (L & (L - 1)) || (Hg & (Hg - 1)) || s % (L * Hg))
         return blb_fail(BLB_ERR_ARG, "L and Hg must be powers of two with L Hg dividing N/2");

@@ -109,7 +109,7 @@ int mul_slots_rescale(blb_ctx* c, Scratch& S, const uint64_t* stack, uint32_t co
     uint64_t* pt = (uint64_t*)S.get((size_t)n * N * 8);
     uint64_t* prod = (uint64_t*)S.get((size_t)count * 2 * n * N * 8);
     if (!dz || !pt || !prod) return blb_fail(BLB_ERR_OOM, "rotate-and-sum scalar buffers");
-    BLB_CUDA(cudaMemcpyAsync(dz, z.data(), z.size() * 8, cudaMemcpyHostToDevice, c->stream));
+    BLB_TRY(host_upload(c, dz, z.data(), z.size() * 8));
     BLB_TRY(encode_slots(c, dz, 1, (uint32_t)z.size(), level, (double)c->q[level], pt));
     BLB_TRY(launch_mul_rows(c, prod, stack, pt, count * 2 * n, c->qmap(n), n));
     BLB_CUDA(cudaStreamSynchronize(c->stream));  // z's host memory is read by the copy above

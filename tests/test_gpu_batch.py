@@ -64,3 +64,40 @@ def test_batch_rejects_mixed_levels():
         ctx.decrypt_batch(keys, [a, b])
     with pytest.raises(blb.BlbError):
         ctx.encrypt_batch(keys, [ctx.encode(v, level), ctx.encode(v, level - 1)], [1, 2])
+
+
+def test_masking_and_decryption_replay_from_a_graph():
+    """The batched masking and decryption captured into a CUDA graph (their
+    host tables go to buffers the context keeps, so a replay never reads
+    freed host memory): a replay gives the eager P1 shares and P0
+    coefficients.  A host output buffer and encoding are refused during
+    capture."""
+    import torch
+    from paper_2508_19525_b300 import blb
+    prm = wl.SMALL
+    ctx = blb.Context(prm.logN, prm.q_bits, prm.p_bits, prm.dnum, prm.scale, stream=torch.cuda.Stream())
+    keys = ctx.keygen(SEED, [1])
+    level = ctx.nQ - 1
+    vals = np.stack([wl.slot_vector(ctx.N // 2, seed=70 + k) for k in range(3)])
+    cts = ctx.encrypt_batch(keys, ctx.encode_batch(vals, level), [10, 11, 12])
+
+    def fn(share, p0):
+        masked, _ = ctx.he2mpc_batch(keys, cts, [20, 21, 22], share_out=share)
+        ctx.decrypt_batch(keys, masked, coeff_out=p0)
+        return masked
+
+    u64 = dict(dtype=torch.uint64, device="cuda")
+    share_e, p0_e = torch.zeros((3, ctx.N), **u64), torch.zeros((3, ctx.N), **u64)
+    fn(share_e, p0_e)
+    ctx.sync()
+    share_g, p0_g = torch.zeros((3, ctx.N), **u64), torch.zeros((3, ctx.N), **u64)
+    graph, masked = ctx.capture(lambda: fn(share_g, p0_g), warmup=False)
+    torch.cuda.synchronize()
+    graph.replay()
+    torch.cuda.synchronize()
+    assert np.array_equal(share_g.cpu().numpy(), share_e.cpu().numpy())
+    assert np.array_equal(p0_g.cpu().numpy(), p0_e.cpu().numpy())
+    with pytest.raises(blb.BlbError):  # P1's shares into a host array
+        ctx.capture(lambda: ctx.he2mpc_batch(keys, cts, [30, 31, 32]), warmup=False)
+    with pytest.raises(blb.BlbError):  # encoding reads its overflow flag on the host
+        ctx.capture(lambda: ctx.encode_batch(vals, level), warmup=False)
