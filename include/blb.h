@@ -395,14 +395,19 @@ int blb_add_plain(blb_ctx* ctx, const blb_ct* a, const blb_pt* b, blb_ct** out);
 /* ---- CUDA graphs ---------------------------------------------------------------
  * Every call that runs only kernels on device data (the matmul_cp / matmul_cc
  * products and their batched forms, key switching, rescale, the element-wise
- * operations) can be captured into a CUDA graph on the context's stream, with
- * the capture in relaxed mode and an allocator that serves stream-ordered
- * allocations of the capture from a private pool (the binding does this with
- * PyTorch's graph capture).  During a capture the key-switch tables go to
- * buffers of their own (freed with the context); the key-switch arena must
- * already be large enough, so run the call once before capturing it
- * (BLB_ERR_ARG otherwise).  Ciphertexts created during the capture hold the
- * results of the latest replay and must outlive the graph. */
+ * operations, the batched masking and decryption into device buffers) can be
+ * captured into a CUDA graph on the context's stream, with the capture in
+ * relaxed mode and an allocator that serves stream-ordered allocations of the
+ * capture from a private pool (the binding does this with PyTorch's graph
+ * capture).  During a capture every table the library builds on the host goes
+ * to a device buffer of its own (freed with the context), so a replay never
+ * reads host memory; the key-switch arena must already be large enough, so run
+ * the call once before capturing it (BLB_ERR_ARG otherwise).  During a capture
+ * these return BLB_ERR_ARG before doing anything: a host input or output
+ * buffer, encoding (it reads its overflow flag back), plan creation, the first
+ * conversion of a context or with a new scale (they cache tables), blb_ntt and
+ * blb_keyswitch_noalloc on host data.  Ciphertexts created during the capture
+ * hold the results of the latest replay and must outlive the graph. */
 
 /* ---- batches of the calls above -----------------------------------------------
  * Each computes, for every member, exactly what the single call computes (same
