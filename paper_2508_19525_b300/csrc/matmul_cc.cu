@@ -151,41 +151,32 @@ __global__ void __launch_bounds__(kS2) k_cc_step2(uint64_t* __restrict__ U, cons
     const size_t nN = (size_t)n * N, off = (size_t)i * N + k, cw = 2 * nN;
     const MaskPair mp = masks[t];
     const bool use_lo = mp.lo != nullptr, use_hi = mp.hi != nullptr;
-    acc128 x0{0, 0}, xs{0, 0}, x2{0, 0}, y0{0, 0}, ys{0, 0}, y2{0, 0};
-    const uint64_t* pa = AG + (size_t)g * cw + off;
-    const uint64_t* pl = BLO + (size_t)b * cw + off;
-    const uint64_t* ph = BHI + (size_t)b * cw + off;
     const size_t sa = (size_t)G2 * cw, sb = (size_t)b1s2 * cw;
-    for (uint32_t c = 0; c < cn; c++) {
-        const uint64_t a0 = pa[0], a1 = pa[nN], as = a0 + a1;
-        if (use_lo) {
-            const uint64_t v0 = pl[0], v1 = pl[nN];
-            mad128(x0, a0, v0);
-            mad128(x2, a1, v1);
-            mad128(xs, as, v0 + v1);
+    // one pass over the input ciphertexts per mask (three 128-bit sums live at
+    // a time): sum_c AG (x) V for V = BLO, then V = BHI
+    auto tensor_sum = [&](const uint64_t* pv, uint64_t& Z0, uint64_t& Z1, uint64_t& Z2) {
+        acc128 z0{0, 0}, zs{0, 0}, z2{0, 0};
+        const uint64_t* pa = AG + (size_t)g * cw + off;
+        for (uint32_t c = 0; c < cn; c++) {
+            const uint64_t a0 = pa[0], a1 = pa[nN], v0 = pv[0], v1 = pv[nN];
+            mad128(z0, a0, v0);
+            mad128(z2, a1, v1);
+            mad128(zs, a0 + a1, v0 + v1);
+            if ((c & 7) == 7) {
+                z0 = acc128{barrett128(z0.lo, z0.hi, q, r0, r1), 0};
+                zs = acc128{barrett128(zs.lo, zs.hi, q, r0, r1), 0};
+                z2 = acc128{barrett128(z2.lo, z2.hi, q, r0, r1), 0};
+            }
+            pa += sa;
+            pv += sb;
         }
-        if (use_hi) {
-            const uint64_t v0 = ph[0], v1 = ph[nN];
-            mad128(y0, a0, v0);
-            mad128(y2, a1, v1);
-            mad128(ys, as, v0 + v1);
-        }
-        if ((c & 7) == 7) {
-            x0 = acc128{barrett128(x0.lo, x0.hi, q, r0, r1), 0};
-            xs = acc128{barrett128(xs.lo, xs.hi, q, r0, r1), 0};
-            x2 = acc128{barrett128(x2.lo, x2.hi, q, r0, r1), 0};
-            y0 = acc128{barrett128(y0.lo, y0.hi, q, r0, r1), 0};
-            ys = acc128{barrett128(ys.lo, ys.hi, q, r0, r1), 0};
-            y2 = acc128{barrett128(y2.lo, y2.hi, q, r0, r1), 0};
-        }
-        pa += sa;
-        pl += sb;
-        ph += sb;
-    }
-    const uint64_t X0 = barrett128(x0.lo, x0.hi, q, r0, r1), X2 = barrett128(x2.lo, x2.hi, q, r0, r1);
-    const uint64_t X1 = sub_mod(sub_mod(barrett128(xs.lo, xs.hi, q, r0, r1), X0, q), X2, q);
-    const uint64_t Y0 = barrett128(y0.lo, y0.hi, q, r0, r1), Y2 = barrett128(y2.lo, y2.hi, q, r0, r1);
-    const uint64_t Y1 = sub_mod(sub_mod(barrett128(ys.lo, ys.hi, q, r0, r1), Y0, q), Y2, q);
+        Z0 = barrett128(z0.lo, z0.hi, q, r0, r1);
+        Z2 = barrett128(z2.lo, z2.hi, q, r0, r1);
+        Z1 = sub_mod(sub_mod(barrett128(zs.lo, zs.hi, q, r0, r1), Z0, q), Z2, q);
+    };
+    uint64_t X0 = 0, X1 = 0, X2 = 0, Y0 = 0, Y1 = 0, Y2 = 0;
+    if (use_lo) tensor_sum(BLO + (size_t)b * cw + off, X0, X1, X2);
+    if (use_hi) tensor_sum(BHI + (size_t)b * cw + off, Y0, Y1, Y2);
     const uint64_t ml = use_lo ? mp.lo[off] : 0, mh = use_hi ? mp.hi[off] : 0;
     uint64_t* dst = U + (size_t)blockIdx.x * 3 * nN + off;
     const uint64_t Xv[3] = {X0, X1, X2}, Yv[3] = {Y0, Y1, Y2};
