@@ -53,16 +53,22 @@ __global__ void k_conv(const uint64_t* __restrict__ src, size_t src_ps, const Co
 // as y_k floor(2^128 / p_k) (the Barrett constant of p_k, below 2^128 since
 // y_k < p_k) with the carries counted: the exact rounding unless the fraction
 // is within 2^-65 of 1/2, and no FP64 (a small fraction of B300's integer rate).
+// NS > 0: at most NS source primes, the y_k in registers (NS = 0: any count,
+// the y_k in a local array)
+template <int NS>
 __global__ void k_moddown_conv(const uint64_t* __restrict__ src, size_t src_ps, const ConvTable* __restrict__ tab,
                                uint32_t nt, uint64_t* __restrict__ dst, size_t dst_ps,
                                const uint64_t* __restrict__ qs, const uint64_t* __restrict__ bar, uint32_t N)
 {
+    constexpr int YN = NS > 0 ? NS : BLB_MAXP;
     const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x, poly = blockIdx.y;
     if (c >= N) return;
     const uint32_t ns = tab->ns;
-    uint64_t y[BLB_MAXP];
+    uint64_t y[YN];
     uint64_t f_lo = 0, f_hi = 0, whole = 0;
-    for (uint32_t k = 0; k < ns; k++) {
+#pragma unroll
+    for (uint32_t k = 0; k < (NS > 0 ? (uint32_t)NS : ns); k++) {
+        if (k >= ns) break;
         const uint32_t pk_i = tab->src[k];
         const uint64_t pk = qs[pk_i];
         y[k] = mul_shoup(src[poly * src_ps + (size_t)k * N + c], tab->hat_inv[k], tab->hat_inv_sh[k], pk);
@@ -84,9 +90,27 @@ __global__ void k_moddown_conv(const uint64_t* __restrict__ src, size_t src_ps, 
         // sum_k y_k (P/p_k) - v P, the subtraction folded into the lazy sum as
         // v (q_t - P mod q_t): one reduction per target
         acc128 a{0, 0};
-        for (uint32_t k = 0; k < ns; k++) mad128(a, y[k], tab->hat[k][t]);
+#pragma unroll
+        for (uint32_t k = 0; k < (NS > 0 ? (uint32_t)NS : ns); k++) {
+            if (k >= ns) break;
+            mad128(a, y[k], tab->hat[k][t]);
+        }
         mad128(a, v, tab->neg_prod_mod_t[t]);
         dst[poly * dst_ps + (size_t)tab->dst_row[t] * N + c] = barrett128(a.lo, a.hi, q, r0, r1);
+    }
+}
+
+// launches with the register form when the source count allows it (ModDown: nP
+// sources; ModUp below: alpha)
+template <typename... Args>
+void launch_moddown_conv(uint32_t ns, dim3 grid, cudaStream_t st, Args... args)
+{
+    switch (ns) {
+    case 1: k_moddown_conv<1><<<grid, kT, 0, st>>>(args...); break;
+    case 2: k_moddown_conv<2><<<grid, kT, 0, st>>>(args...); break;
+    case 3: k_moddown_conv<3><<<grid, kT, 0, st>>>(args...); break;
+    case 4: k_moddown_conv<4><<<grid, kT, 0, st>>>(args...); break;
+    default: k_moddown_conv<0><<<grid, kT, 0, st>>>(args...); break;
     }
 }
 
@@ -172,9 +196,9 @@ static int keyswitch_impl(blb_ctx* ctx, const uint64_t* d_ntt, uint32_t level, c
     // 4. ModDown: P limbs to coefficient form, convert to Q_l, back to evaluation
     BLB_TRY(ntt_inverse(ctx, acc + (size_t)n * N, nP, ctx->pmap()));
     BLB_TRY(ntt_inverse(ctx, acc + ((size_t)E + n) * N, nP, ctx->pmap()));
-    k_moddown_conv<<<dim3((N + kT - 1) / kT, 2), kT, 0, ctx->stream>>>(acc + (size_t)n * N, (size_t)E * N,
-                                                                       ctx->d_moddown, n, cv, (size_t)n * N, ctx->d_q,
-                                                                       ctx->d_bar, N);
+    launch_moddown_conv(nP, dim3((N + kT - 1) / kT, 2), ctx->stream, (const uint64_t*)(acc + (size_t)n * N),
+                        (size_t)E * N, (const ConvTable*)ctx->d_moddown, n, cv, (size_t)n * N,
+                        (const uint64_t*)ctx->d_q, (const uint64_t*)ctx->d_bar, N);
     BLB_LAUNCHED();
     BLB_TRY(ntt_forward(ctx, cv, 2 * n, ctx->qmap(n)));
     PInv pinv{};
@@ -319,11 +343,13 @@ __global__ void k_ksb_gather(uint64_t* __restrict__ din, uint64_t* __restrict__ 
 }
 
 // ModUp of every digit of every source: grid.y = source * beta + j
+template <int NS>  // as for k_moddown_conv: at most NS primes per digit, 0 = any
 __global__ void k_ksb_modup(const uint64_t* __restrict__ coef, uint64_t* __restrict__ ext,
                             const ConvTable* __restrict__ tabs, uint32_t n, uint32_t E, uint32_t beta,
                             uint32_t alpha, const uint64_t* __restrict__ qs, const uint64_t* __restrict__ bar,
                             uint32_t N)
 {
+    constexpr int YN = NS > 0 ? NS : BLB_MAXP;
     const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= N) return;
     const uint32_t src = blockIdx.y / beta, j = blockIdx.y % beta;
@@ -331,14 +357,33 @@ __global__ void k_ksb_modup(const uint64_t* __restrict__ coef, uint64_t* __restr
     const uint32_t ns = tab->ns, nt = tab->nt;
     const uint64_t* in = coef + ((size_t)src * n + j * alpha) * N + c;
     uint64_t* dst = ext + ((size_t)src * beta + j) * E * N + c;
-    uint64_t y[BLB_MAXP];
-    for (uint32_t i = 0; i < ns; i++)
+    uint64_t y[YN];
+#pragma unroll
+    for (uint32_t i = 0; i < (NS > 0 ? (uint32_t)NS : ns); i++) {
+        if (i >= ns) break;
         y[i] = mul_shoup(in[(size_t)i * N], tab->hat_inv[i], tab->hat_inv_sh[i], qs[tab->src[i]]);
+    }
     for (uint32_t t = 0; t < nt; t++) {
         const uint32_t pt = tab->dst[t];
         acc128 a{0, 0};
-        for (uint32_t i = 0; i < ns; i++) mad128(a, y[i], tab->hat[i][t]);
+#pragma unroll
+        for (uint32_t i = 0; i < (NS > 0 ? (uint32_t)NS : ns); i++) {
+            if (i >= ns) break;
+            mad128(a, y[i], tab->hat[i][t]);
+        }
         dst[(size_t)tab->dst_row[t] * N] = barrett128(a.lo, a.hi, qs[pt], bar[2 * pt], bar[2 * pt + 1]);
+    }
+}
+
+template <typename... Args>
+void launch_modup(uint32_t alpha, dim3 grid, cudaStream_t st, Args... args)
+{
+    switch (alpha) {
+    case 1: k_ksb_modup<1><<<grid, kT, 0, st>>>(args...); break;
+    case 2: k_ksb_modup<2><<<grid, kT, 0, st>>>(args...); break;
+    case 3: k_ksb_modup<3><<<grid, kT, 0, st>>>(args...); break;
+    case 4: k_ksb_modup<4><<<grid, kT, 0, st>>>(args...); break;
+    default: k_ksb_modup<0><<<grid, kT, 0, st>>>(args...); break;
     }
 }
 
@@ -603,8 +648,9 @@ int ks_run(blb_ctx* ctx, uint32_t level, const KsSource* sources, uint32_t n_src
             k_ksb_gather<<<dim3(gx, n, ns), kT, 0, ctx->stream>>>(din, coef, d_src, n, ctx->logN);
             BLB_LAUNCHED();
             BLB_TRY(ntt_inverse(ctx, coef, ns * n, ctx->qmap(n)));
-            k_ksb_modup<<<dim3(gx, ns * beta), kT, 0, ctx->stream>>>(coef, ext, ctx->d_modup[(size_t)level * ctx->dnum],
-                                                                     n, E, beta, alpha, ctx->d_q, ctx->d_bar, N);
+            launch_modup(alpha, dim3(gx, ns * beta), ctx->stream, (const uint64_t*)coef, ext,
+                         (const ConvTable*)ctx->d_modup[(size_t)level * ctx->dnum], n, E, beta, alpha,
+                         (const uint64_t*)ctx->d_q, (const uint64_t*)ctx->d_bar, N);
             BLB_LAUNCHED();
             BLB_TRY(ntt_forward_list(ctx, ext, (uint32_t)ext_rows.size(), d_ext_rows));
             k_ksb_digit_rows<<<dim3(gx, n, ns), kT, 0, ctx->stream>>>(ext, din, n, E, beta, alpha, N);
@@ -614,8 +660,9 @@ int ks_run(blb_ctx* ctx, uint32_t level, const KsSource* sources, uint32_t n_src
                                                                ctx->np, ctx->d_q, ctx->d_bar, ctx->logN);
         BLB_LAUNCHED();
         BLB_TRY(ntt_inverse_list(ctx, acc, (uint32_t)p_rows.size(), d_p_rows));
-        k_moddown_conv<<<dim3(gx, 2 * ng), kT, 0, ctx->stream>>>(acc + (size_t)n * N, (size_t)E * N, ctx->d_moddown, n,
-                                                                 cv, (size_t)n * N, ctx->d_q, ctx->d_bar, N);
+        launch_moddown_conv(nP, dim3(gx, 2 * ng), ctx->stream, (const uint64_t*)(acc + (size_t)n * N),
+                            (size_t)E * N, (const ConvTable*)ctx->d_moddown, n, cv, (size_t)n * N,
+                            (const uint64_t*)ctx->d_q, (const uint64_t*)ctx->d_bar, N);
         BLB_LAUNCHED();
         BLB_TRY(ntt_forward(ctx, cv, ng * 2 * n, ctx->qmap(n)));
         k_ksb_finish<<<dim3(gx, n, ng), kT, 0, ctx->stream>>>(d_grp, d_prod, ext, d_add, cv, n, E, beta, ctx->np,
