@@ -9,7 +9,7 @@ constexpr int kT = 256;
 inline dim3 grid_rows(uint32_t N, uint32_t rows) { return dim3((N + kT - 1) / kT, rows); }
 
 __global__ void k_mul_rows(uint64_t* __restrict__ out, const uint64_t* __restrict__ a,
-                           const uint64_t* __restrict__ b, LimbMap map, const uint64_t* __restrict__ qs,
+                           const uint64_t* __restrict__ b, const __grid_constant__ LimbMap map, const uint64_t* __restrict__ qs,
                            const uint64_t* __restrict__ bar, uint32_t N, uint32_t b_rows, int accumulate)
 {
     const uint32_t row = blockIdx.y, c = blockIdx.x * blockDim.x + threadIdx.x;
@@ -23,7 +23,7 @@ __global__ void k_mul_rows(uint64_t* __restrict__ out, const uint64_t* __restric
 
 // op: 0 add, 1 sub, 2 neg (b unused)
 __global__ void k_addsub_rows(uint64_t* __restrict__ out, const uint64_t* __restrict__ a,
-                              const uint64_t* __restrict__ b, LimbMap map, const uint64_t* __restrict__ qs,
+                              const uint64_t* __restrict__ b, const __grid_constant__ LimbMap map, const uint64_t* __restrict__ qs,
                               uint32_t N, int op)
 {
     const uint32_t row = blockIdx.y, c = blockIdx.x * blockDim.x + threadIdx.x;
@@ -37,7 +37,7 @@ __global__ void k_addsub_rows(uint64_t* __restrict__ out, const uint64_t* __rest
 struct RowConst {
     uint64_t w[BLB_MAXP * 4], wp[BLB_MAXP * 4];
 };
-__global__ void k_mul_const_rows(uint64_t* __restrict__ out, const uint64_t* __restrict__ a, LimbMap map,
+__global__ void k_mul_const_rows(uint64_t* __restrict__ out, const uint64_t* __restrict__ a, const __grid_constant__ LimbMap map,
                                  const uint64_t* __restrict__ qs, uint32_t N, RowConst rc)
 {
     const uint32_t row = blockIdx.y, c = blockIdx.x * blockDim.x + threadIdx.x;
@@ -62,7 +62,7 @@ __global__ void k_automorph_ntt(uint64_t* __restrict__ out, const uint64_t* __re
     out[(size_t)row * N + k] = in[(size_t)row * N + src];
 }
 
-__global__ void k_signed_to_rows(uint64_t* __restrict__ out, const int64_t* __restrict__ in, LimbMap map,
+__global__ void k_signed_to_rows(uint64_t* __restrict__ out, const int64_t* __restrict__ in, const __grid_constant__ LimbMap map,
                                  const uint64_t* __restrict__ qs, uint32_t N)
 {
     const uint32_t row = blockIdx.y, c = blockIdx.x * blockDim.x + threadIdx.x;
@@ -107,7 +107,7 @@ struct RowJ {
 };
 
 // uniform residue: the 128-bit draw (word 3 most significant) mod q
-__global__ void k_sample_uniform(uint64_t* out, uint32_t N, LimbMap map, const uint64_t* __restrict__ qs,
+__global__ void k_sample_uniform(uint64_t* out, uint32_t N, const __grid_constant__ LimbMap map, const uint64_t* __restrict__ qs,
                                  const uint64_t* __restrict__ bar, uint64_t seed, uint32_t obj, uint32_t purpose,
                                  RowJ rj)
 {

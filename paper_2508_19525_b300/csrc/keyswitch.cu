@@ -116,7 +116,7 @@ void launch_moddown_conv(uint32_t ns, dim3 grid, cudaStream_t st, Args... args)
 
 // acc_p[t] = sum_{j < beta} ext[j][t] * key[j][p][kt],  p in {0, 1}
 __global__ void k_ks_inner(uint64_t* __restrict__ acc, const uint64_t* __restrict__ ext,
-                           const uint64_t* __restrict__ key, LimbMap emap, uint32_t n, uint32_t E, uint32_t beta,
+                           const uint64_t* __restrict__ key, const __grid_constant__ LimbMap emap, uint32_t n, uint32_t E, uint32_t beta,
                            uint32_t nQ, uint32_t np, const uint64_t* __restrict__ qs,
                            const uint64_t* __restrict__ bar, uint32_t N)
 {
@@ -402,7 +402,7 @@ __global__ void k_ksb_digit_rows(uint64_t* __restrict__ ext, const uint64_t* __r
 // the ModDown conversion.  The ciphertext-prime rows are summed where they are
 // used, in k_ksb_finish, so they are never written out.
 __global__ void k_ksb_inner(uint64_t* __restrict__ acc, const uint64_t* __restrict__ ext,
-                            const DevGroup* __restrict__ groups, const DevProduct* __restrict__ prods, LimbMap emap,
+                            const DevGroup* __restrict__ groups, const DevProduct* __restrict__ prods, const __grid_constant__ LimbMap emap,
                             uint32_t n, uint32_t E, uint32_t beta, uint32_t nQ, uint32_t np,
                             const uint64_t* __restrict__ qs, const uint64_t* __restrict__ bar, uint32_t logN)
 {

@@ -211,7 +211,7 @@ __device__ __forceinline__ void inv_rounds(uint64_t* sm, uint32_t c0, const ulon
 // One pass over one tile of one row.  The last pass brings results to [0, q)
 // (and, for the inverse, multiplies by N^-1).
 template <bool INV, int LOGN, int LP, bool COLS>
-__global__ void __launch_bounds__(kThreads, 3) k_ntt(uint64_t* __restrict__ data, LimbMap map,
+__global__ void __launch_bounds__(kThreads, 3) k_ntt(uint64_t* __restrict__ data, const __grid_constant__ LimbMap map,
                                                     const uint32_t* __restrict__ rowlist, uint32_t y0,
                                                     const uint64_t* __restrict__ qs,
                                                     const ulonglong2* __restrict__ tw,
