@@ -11,10 +11,12 @@
 // shared memory: the "column" pass runs the log2(N1) stages whose butterflies
 // pair elements N2 or more apart on sub-transforms {c + N2 r}, the "row" pass
 // runs the remaining stages on contiguous blocks of N2.  Every pass reads and
-// writes each word once.  Inside a pass each thread holds a group of up to 16
-// elements in registers and runs up to 4 stages on it (radix 16), so a pass
-// needs 2-3 shared-memory round trips instead of one per stage.  Shared memory
-// is padded by one word every 16 to keep strided group accesses conflict-free.
+// writes each word once.  Inside a pass each thread holds a group of up to 8
+// elements in registers and runs up to 3 stages on it (radix 8), so a pass
+// needs 2-3 shared-memory round trips instead of one per stage; radix 8 fits
+// 64 registers, so four CTAs run per SM (measured on the B300 against radix 16
+// at three CTAs and radix 8 at three or five).  Shared memory is padded by one
+// word every 16 to keep strided group accesses conflict-free.
 //
 // Each (transform size, pass) is its own template instance, so every index,
 // shift and loop bound of a pass is a compile-time constant; the twiddles are
@@ -189,7 +191,7 @@ template <int LOGN, int LP, bool COLS, bool SMALL, int PHI>
 __device__ __forceinline__ void fwd_rounds(uint64_t* sm, uint32_t c0, const ulonglong2* W, uint64_t q, uint64_t q2)
 {
     if constexpr (PHI > 0) {
-        constexpr int R = PHI >= 4 ? 4 : PHI;
+        constexpr int R = PHI >= 3 ? 3 : PHI;
         round<LOGN, LP, COLS, false, SMALL, PHI - R, R>(sm, c0, W, q, q2);
         __syncthreads();
         fwd_rounds<LOGN, LP, COLS, SMALL, PHI - R>(sm, c0, W, q, q2);
@@ -201,7 +203,7 @@ template <int LOGN, int LP, bool COLS, bool SMALL, int PLO>
 __device__ __forceinline__ void inv_rounds(uint64_t* sm, uint32_t c0, const ulonglong2* W, uint64_t q, uint64_t q2)
 {
     if constexpr (PLO < LP) {
-        constexpr int R = LP - PLO >= 4 ? 4 : LP - PLO;
+        constexpr int R = LP - PLO >= 3 ? 3 : LP - PLO;
         round<LOGN, LP, COLS, true, SMALL, PLO, R>(sm, c0, W, q, q2);
         __syncthreads();
         inv_rounds<LOGN, LP, COLS, SMALL, PLO + R>(sm, c0, W, q, q2);
@@ -211,7 +213,7 @@ __device__ __forceinline__ void inv_rounds(uint64_t* sm, uint32_t c0, const ulon
 // One pass over one tile of one row.  The last pass brings results to [0, q)
 // (and, for the inverse, multiplies by N^-1).
 template <bool INV, int LOGN, int LP, bool COLS>
-__global__ void __launch_bounds__(kThreads, 3) k_ntt(uint64_t* __restrict__ data, const __grid_constant__ LimbMap map,
+__global__ void __launch_bounds__(kThreads, 4) k_ntt(uint64_t* __restrict__ data, const __grid_constant__ LimbMap map,
                                                     const uint32_t* __restrict__ rowlist, uint32_t y0,
                                                     const uint64_t* __restrict__ qs,
                                                     const ulonglong2* __restrict__ tw,
