@@ -435,7 +435,7 @@ __global__ void k_ksb_inner(uint64_t* __restrict__ acc, const uint64_t* __restri
 // acc_p = sum over the group's products of sum_j sigma_x(ext[src_x][j][i]) key_x[j][p][i]
 // (the same sums k_ksb_inner forms for the special primes), then
 // out_p = [out_p +] sum_{addends of p} add[perm(k)] + (acc_p - cv_p) P^-1
-__global__ void k_ksb_finish(const DevGroup* __restrict__ groups, const DevProduct* __restrict__ prods,
+__global__ void __launch_bounds__(256, 6) k_ksb_finish(const DevGroup* __restrict__ groups, const DevProduct* __restrict__ prods,
                              const uint64_t* __restrict__ ext, const KsAdd* __restrict__ adds,
                              const uint64_t* __restrict__ cv, uint32_t n, uint32_t E, uint32_t beta, uint32_t np,
                              PInv pinv, const uint64_t* __restrict__ qs, const uint64_t* __restrict__ bar,
