@@ -186,7 +186,7 @@ def unpack_head_diagonals(Z, L, Hg, Kc):
 
 
 class Workload:
-    def __init__(self, device, ntt_split=None):
+    def __init__(self, device, ntt_split=None, ntt_radix=None):
         import torch
         from paper_2508_19525_b300 import blb
         from paper_2508_19525_b300 import workloads as wl
@@ -199,12 +199,16 @@ class Workload:
         G = self.k // B1
         rots = [b * M for b in range(1, B1)] + [g * B1 * M for g in range(1, G)]
         self.keys = self.ctx.keygen(0, rots)
-        # pick the NTT pass split for this ring on the device before anything is
-        # timed (or take the given one, so that profiles capture known kernels)
-        self.ntt_split, self.ntt_split_us = self.ctx.ntt_autotune(256)
+        # pick the NTT radix and pass split for this ring on the device before
+        # anything is timed (or take the given ones, so that profiles capture
+        # known kernels)
+        self.ntt_split, self.ntt_radix, self.ntt_us = self.ctx.ntt_autotune(256)
         if ntt_split is not None:
             self.ctx.ntt_set_split(ntt_split)
             self.ntt_split = ntt_split
+        if ntt_radix is not None:
+            self.ctx.ntt_set_radix(ntt_radix)
+            self.ntt_radix = ntt_radix
         self.X, Wqkv, Wo = wl.bert_base_cp(seed=0)
         self.ref_qkv = self.X @ Wqkv
         self.ref_o = self.ref_qkv[:, :D_O] @ Wo
@@ -445,7 +449,7 @@ def cfg4_batching(n_seqs=8, plain_chunks=6, candidates=(16, 32, 64, 128), groups
     dnum, dnum_t = bt.autotune_dnum(
         lambda dn: blb.Context(prm.logN, prm.q_bits, prm.p_bits, dn, prm.scale, stream=stream), (4, 6, 12), 32)
     ctx = blb.Context(prm.logN, prm.q_bits, prm.p_bits, dnum, prm.scale, stream=stream)
-    ntt_split, ntt_us = ctx.ntt_autotune(256)
+    ntt_split, ntt_radix, ntt_us = ctx.ntt_autotune(256)
     m, level = 32, ctx.nQ - 1
     k = ctx.N // 2 // m
     rng = np.random.default_rng(44)
@@ -462,7 +466,7 @@ def cfg4_batching(n_seqs=8, plain_chunks=6, candidates=(16, 32, 64, 128), groups
                        f"N=2^16, 12 primes, dnum autotuned", "lengths": [int(x) for x in lengths], "tokens": T,
            "rotation_keys": len(rots),
            "autotuned": {"dnum": dnum, "dnum_s_per_rotation": {str(k): round(v, 5) for k, v in dnum_t.items()},
-                         "ntt_split": ntt_split, "ntt_us_per_row_direction": {str(k): round(v, 4) for k, v in ntt_us.items()}},
+                         "ntt_split": ntt_split, "ntt_radix": ntt_radix, "ntt_us_per_row_direction": ntt_us_json(ntt_us)},
            "keygen_s": round(keygen_s, 2), "products": {}}
     tot_b = tot_p = tot_g = 0.0
     for name, d, d_out, seed in products:
@@ -997,7 +1001,7 @@ def run_blb(args):
         "gpu_launches": int(launches),
         "roofline": dict(roof[dominant], kernel=dominant, traffic=traffic) if dominant else None,
         "roofline_sites": roof,
-        "ntt_autotune": {"split": w.ntt_split, "us_per_row_direction": {str(k): round(v, 4) for k, v in w.ntt_split_us.items()}},
+        "ntt_autotune": {"split": w.ntt_split, "radix": w.ntt_radix, "us_per_row_direction": ntt_us_json(w.ntt_us)},
         "int_peaks": {k: (round(v / 1e9, 2) if k.endswith("_s") else round(v, 3)) for k, v in int_peaks.items()},
         "accuracy": {"max_abs_err_vs_fp64": max_err, "mse": mse, "bound": 1e-4},
         "batched": batched,
@@ -1104,7 +1108,13 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def ncu_case(seqs=1, ntt_split=None):
+def ntt_us_json(us):
+    """{(radix, split): microseconds} of the NTT autotuner as JSON keys
+    "r<radix>/<split>"."""
+    return {f"r{r}/{sp}": round(v, 4) for (r, sp), v in sorted(us.items())}
+
+
+def ncu_case(seqs=1, ntt_split=None, ntt_radix=None):
     """Small profiling case of the same kernels for `ncu --profile-from-start off`:
     N = 2^15, 8 primes, matmul_cp 128x768 @ 768x256 (96 plaintext terms per
     output as in the BERT-base products, 2.2 GB of byte-sliced diagonals, larger
@@ -1117,6 +1127,8 @@ def ncu_case(seqs=1, ntt_split=None):
     ctx = blb.Context(prm.logN, prm.q_bits, prm.p_bits, prm.dnum, prm.scale)
     if ntt_split is not None:
         ctx.ntt_set_split(ntt_split)
+    if ntt_radix is not None:
+        ctx.ntt_set_radix(ntt_radix)
     k = ctx.N // 2 // M
     rots = [b * M for b in range(1, B1)] + [g * B1 * M for g in range(1, k // B1)]
     keys = ctx.keygen(0, rots)
@@ -1136,11 +1148,11 @@ def ncu_case(seqs=1, ntt_split=None):
                       "plan": plan.info()}))
 
 
-def ncu_step(ntt_split=None):
+def ncu_step(ntt_split=None, ntt_radix=None):
     """One BERT-base step bracketed by cudaProfilerStart/Stop (after one warm-up
     step), for a launch list with `ncu --profile-from-start off`."""
     import torch
-    w = Workload(torch.device("cuda", 0), ntt_split)
+    w = Workload(torch.device("cuda", 0), ntt_split, ntt_radix)
     w.step()
     w.ctx.sync()
     torch.cuda.profiler.start()
@@ -1238,6 +1250,8 @@ def main():
     ap.add_argument("--ncu-cc-params", choices=("large", "base"), default="large")
     ap.add_argument("--ntt-split", type=int, default=None, choices=(-1, 0, 1),
                     help="fix the NTT pass split of the profiling cases (default: autotuned)")
+    ap.add_argument("--ntt-radix", type=int, default=None, choices=(8, 16),
+                    help="fix the NTT radix of the profiling cases (default: autotuned)")
     ap.add_argument("--batch", type=int, default=8, help="sequences per batched step (1 = skip)")
     ap.add_argument("--no-attention", dest="attention", action="store_false",
                     help="skip the matmul_cc attention measurement")
@@ -1255,9 +1269,9 @@ def main():
                     help="skip the continuous-batching serving measurement")
     args = ap.parse_args()
     if args.ncu_case:
-        return ncu_case(args.ncu_seqs, args.ntt_split)
+        return ncu_case(args.ncu_seqs, args.ntt_split, args.ntt_radix)
     if args.ncu_step:
-        return ncu_step(args.ntt_split)
+        return ncu_step(args.ntt_split, args.ntt_radix)
     if args.ncu_conv:
         return ncu_conv()
     if args.ncu_cc:

@@ -439,14 +439,20 @@ int blb_decrypt_batch(blb_ctx* ctx, const blb_keys* keys, const blb_ct* const* c
 int blb_ntt(blb_ctx* ctx, uint64_t* data, uint32_t rows, const uint32_t* prime_idx, int inverse);
 /* Transforms above 4096 points run in two passes over 4096-word tiles: a
  * column pass over 2^L1-point sub-transforms and a row pass over the rest.
- * split -1 / 0 / +1 puts L1 one below, at, or one above log2(N)/2; every split
- * computes the same butterflies, so the limbs are identical.
+ * split -1 / 0 / +1 puts L1 one below, at, or one above log2(N)/2.  Inside a
+ * tile the butterfly stages run in register rounds of up to 3 stages (radix
+ * 8, four CTAs per SM) or up to 4 (radix 16, three CTAs per SM).  Every split
+ * and radix computes the same butterflies, so the limbs are identical.
  * blb_ntt_autotune times forward + inverse transforms of `rows` rows for each
- * split, keeps the fastest for the context and returns it (split_out) and the
- * time of each split per row and direction in microseconds (us_per_row[3], for
- * splits -1, 0, +1; 0 where a ring has one pass); both nullable. */
-int blb_ntt_autotune(blb_ctx* ctx, uint32_t rows, int* split_out, double* us_per_row);
+ * radix and split, keeps the fastest pair for the context and returns it
+ * (split_out, radix_out) with the time of each per row and direction in
+ * microseconds (us_per_row[6]: radix 8 at splits -1, 0, +1, then radix 16 at
+ * the same; 0 where a ring has one pass); all nullable.  Refused inside a
+ * graph capture.  blb_ntt_set_split / blb_ntt_set_radix fix one by hand
+ * (BLB_ERR_ARG outside {-1, 0, 1} / {8, 16}). */
+int blb_ntt_autotune(blb_ctx* ctx, uint32_t rows, int* split_out, int* radix_out, double* us_per_row);
 int blb_ntt_set_split(blb_ctx* ctx, int split);
+int blb_ntt_set_radix(blb_ctx* ctx, int radix);
 
 /* ---- measurement ------------------------------------------------------------
  * Total kernel launches issued by this library in this process. */

@@ -109,8 +109,9 @@ SIGNATURES = {
     "blb_pt_import": (ctypes.c_int, [_vp, _vp, _u32, _dbl, _pp]),
     "blb_add_plain": (ctypes.c_int, [_vp, _vp, _vp, _pp]),
     "blb_ntt": (ctypes.c_int, [_vp, _vp, _u32, _vp, ctypes.c_int]),
-    "blb_ntt_autotune": (ctypes.c_int, [_vp, _u32, _vp, _vp]),
+    "blb_ntt_autotune": (ctypes.c_int, [_vp, _u32, _vp, _vp, _vp]),
     "blb_ntt_set_split": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "blb_ntt_set_radix": (ctypes.c_int, [_vp, ctypes.c_int]),
     "blb_kernel_launches": (_u64, []),
     "blb_int_peaks": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
     "blb_profile_enable": (ctypes.c_int, [_vp, ctypes.c_int]),
@@ -640,14 +641,18 @@ class Context:
         return ms.value, cnt.value, nb.value
 
     def ntt_autotune(self, rows=64):
-        """Time the NTT's three pass splits; keep the fastest.  Returns
-        (split, {split: microseconds per row and direction})."""
-        sp, us = ctypes.c_int(), (_dbl * 3)()
-        _check(lib().blb_ntt_autotune(self.h, rows, ctypes.byref(sp), us))
-        return sp.value, {k - 1: us[k] for k in range(3) if us[k] > 0}
+        """Time the NTT's radices (8, 16) and pass splits (-1, 0, +1); keep
+        the fastest pair.  Returns (split, radix, {(radix, split):
+        microseconds per row and direction})."""
+        sp, rx, us = ctypes.c_int(), ctypes.c_int(), (_dbl * 6)()
+        _check(lib().blb_ntt_autotune(self.h, rows, ctypes.byref(sp), ctypes.byref(rx), us))
+        return sp.value, rx.value, {((8, 16)[k // 3], k % 3 - 1): us[k] for k in range(6) if us[k] > 0}
 
     def ntt_set_split(self, split):
         _check(lib().blb_ntt_set_split(self.h, int(split)))
+
+    def ntt_set_radix(self, radix):
+        _check(lib().blb_ntt_set_radix(self.h, int(radix)))
 
     def ntt(self, data, prime_idx, inverse=False):
         data = np.ascontiguousarray(data, np.uint64).copy()

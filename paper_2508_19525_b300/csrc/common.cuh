@@ -210,6 +210,7 @@ struct blb_ctx {
     std::vector<std::pair<void*, size_t>> graph_keep;  // (pointer, bytes); bytes 0 = cudaMalloc'd
     bool captured = false;
     int ntt_split = 0;  // split of the two-pass NTT around the middle (-1, 0, +1), see ntt.cu
+    int ntt_radix = 8;  // largest radix of the NTT's register rounds (8 or 16), see ntt.cu
     // lifetime: objects (keys, plaintexts, ciphertexts, plans) hold the
     // context; blb_ctx_free releases it once the last of them is freed
     uint64_t live_objects = 0;

@@ -186,34 +186,38 @@ __device__ __forceinline__ void round(uint64_t* sm, uint32_t c0, const ulonglong
     }
 }
 
-// forward rounds: local bits from the top down
-template <int LOGN, int LP, bool COLS, bool SMALL, int PHI>
+// forward rounds: local bits from the top down, up to RB stages per round
+// (radix 2^RB)
+template <int LOGN, int LP, bool COLS, bool SMALL, int PHI, int RB>
 __device__ __forceinline__ void fwd_rounds(uint64_t* sm, uint32_t c0, const ulonglong2* W, uint64_t q, uint64_t q2)
 {
     if constexpr (PHI > 0) {
-        constexpr int R = PHI >= 3 ? 3 : PHI;
+        constexpr int R = PHI >= RB ? RB : PHI;
         round<LOGN, LP, COLS, false, SMALL, PHI - R, R>(sm, c0, W, q, q2);
         __syncthreads();
-        fwd_rounds<LOGN, LP, COLS, SMALL, PHI - R>(sm, c0, W, q, q2);
+        fwd_rounds<LOGN, LP, COLS, SMALL, PHI - R, RB>(sm, c0, W, q, q2);
     }
 }
 
 // inverse rounds: local bits from the bottom up
-template <int LOGN, int LP, bool COLS, bool SMALL, int PLO>
+template <int LOGN, int LP, bool COLS, bool SMALL, int PLO, int RB>
 __device__ __forceinline__ void inv_rounds(uint64_t* sm, uint32_t c0, const ulonglong2* W, uint64_t q, uint64_t q2)
 {
     if constexpr (PLO < LP) {
-        constexpr int R = LP - PLO >= 3 ? 3 : LP - PLO;
+        constexpr int R = LP - PLO >= RB ? RB : LP - PLO;
         round<LOGN, LP, COLS, true, SMALL, PLO, R>(sm, c0, W, q, q2);
         __syncthreads();
-        inv_rounds<LOGN, LP, COLS, SMALL, PLO + R>(sm, c0, W, q, q2);
+        inv_rounds<LOGN, LP, COLS, SMALL, PLO + R, RB>(sm, c0, W, q, q2);
     }
 }
 
+// CTAs per SM for a radix: 16 needs the registers of three, 8 fits four
+constexpr int ntt_ctas(int RB) { return RB >= 4 ? 3 : 4; }
+
 // One pass over one tile of one row.  The last pass brings results to [0, q)
 // (and, for the inverse, multiplies by N^-1).
-template <bool INV, int LOGN, int LP, bool COLS>
-__global__ void __launch_bounds__(kThreads, 4) k_ntt(uint64_t* __restrict__ data, const __grid_constant__ LimbMap map,
+template <bool INV, int LOGN, int LP, bool COLS, int RB>
+__global__ void __launch_bounds__(kThreads, ntt_ctas(RB)) k_ntt(uint64_t* __restrict__ data, const __grid_constant__ LimbMap map,
                                                     const uint32_t* __restrict__ rowlist, uint32_t y0,
                                                     const uint64_t* __restrict__ qs,
                                                     const ulonglong2* __restrict__ tw,
@@ -238,11 +242,11 @@ __global__ void __launch_bounds__(kThreads, 4) k_ntt(uint64_t* __restrict__ data
     __syncthreads();
     const bool small = small_prime(q, LOGN);
     if (!INV) {
-        if (small) fwd_rounds<LOGN, LP, COLS, true, LP>(sm, c0, W, q, q2);
-        else fwd_rounds<LOGN, LP, COLS, false, LP>(sm, c0, W, q, q2);
+        if (small) fwd_rounds<LOGN, LP, COLS, true, LP, RB>(sm, c0, W, q, q2);
+        else fwd_rounds<LOGN, LP, COLS, false, LP, RB>(sm, c0, W, q, q2);
     } else {
-        if (small) inv_rounds<LOGN, LP, COLS, true, 0>(sm, c0, W, q, q2);
-        else inv_rounds<LOGN, LP, COLS, false, 0>(sm, c0, W, q, q2);
+        if (small) inv_rounds<LOGN, LP, COLS, true, 0, RB>(sm, c0, W, q, q2);
+        else inv_rounds<LOGN, LP, COLS, false, 0, RB>(sm, c0, W, q, q2);
     }
     uint64_t ni = 0, nis = 0, r1 = 0;
     if (INV && LAST) {
@@ -266,7 +270,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_ntt(uint64_t* __restrict__ data
 
 // One forward or inverse transform with the column pass over 2^L1-point
 // sub-transforms and the row pass over 2^(LOGN - L1) points (L1 = 0: one pass).
-template <int LOGN, int L1>
+template <int LOGN, int L1, int RB>
 int run_split(blb_ctx* ctx, uint64_t* data, uint32_t rows, const LimbMap& map, const uint32_t* rowlist, bool inverse)
 {
     constexpr uint32_t N = 1u << LOGN;
@@ -278,19 +282,19 @@ int run_split(blb_ctx* ctx, uint64_t* data, uint32_t rows, const LimbMap& map, c
         const dim3 grid(N / TILE, std::min(kMaxGridY, rows - y0));
         if (!inverse) {
             if constexpr (L1 > 0) {
-                k_ntt<false, LOGN, L1, true><<<grid, kThreads, 0, ctx->stream>>>(data, map, rowlist, y0, ctx->d_q, tw,
+                k_ntt<false, LOGN, L1, true, RB><<<grid, kThreads, 0, ctx->stream>>>(data, map, rowlist, y0, ctx->d_q, tw,
                                                                                 ctx->d_ninv, ctx->d_bar);
                 BLB_LAUNCHED();
             }
-            k_ntt<false, LOGN, L2, false><<<grid, kThreads, 0, ctx->stream>>>(data, map, rowlist, y0, ctx->d_q, tw,
+            k_ntt<false, LOGN, L2, false, RB><<<grid, kThreads, 0, ctx->stream>>>(data, map, rowlist, y0, ctx->d_q, tw,
                                                                              ctx->d_ninv, ctx->d_bar);
             BLB_LAUNCHED();
         } else {
-            k_ntt<true, LOGN, L2, false><<<grid, kThreads, 0, ctx->stream>>>(data, map, rowlist, y0, ctx->d_q, tw,
+            k_ntt<true, LOGN, L2, false, RB><<<grid, kThreads, 0, ctx->stream>>>(data, map, rowlist, y0, ctx->d_q, tw,
                                                                             ctx->d_ninv, ctx->d_bar);
             BLB_LAUNCHED();
             if constexpr (L1 > 0) {
-                k_ntt<true, LOGN, L1, true><<<grid, kThreads, 0, ctx->stream>>>(data, map, rowlist, y0, ctx->d_q, tw,
+                k_ntt<true, LOGN, L1, true, RB><<<grid, kThreads, 0, ctx->stream>>>(data, map, rowlist, y0, ctx->d_q, tw,
                                                                                ctx->d_ninv, ctx->d_bar);
                 BLB_LAUNCHED();
             }
@@ -301,22 +305,30 @@ int run_split(blb_ctx* ctx, uint64_t* data, uint32_t rows, const LimbMap& map, c
 
 // Transforms above one tile have three splits around the middle, chosen per
 // context (ctx->ntt_split: 0 the middle, -1 / +1 a shorter / longer column
-// pass); blb_ntt_autotune times them.
-template <int LOGN>
-int run_n(blb_ctx* ctx, uint64_t* data, uint32_t rows, const LimbMap& map, const uint32_t* rowlist, bool inverse)
+// pass), and two radices of the register rounds (ctx->ntt_radix: 8, four CTAs
+// per SM, or 16, three); blb_ntt_autotune times all of them.
+template <int LOGN, int RB>
+int run_nr(blb_ctx* ctx, uint64_t* data, uint32_t rows, const LimbMap& map, const uint32_t* rowlist, bool inverse)
 {
     if constexpr (LOGN <= 12) {
-        return run_split<LOGN, 0>(ctx, data, rows, map, rowlist, inverse);
+        return run_split<LOGN, 0, RB>(ctx, data, rows, map, rowlist, inverse);
     } else {
         constexpr int M = LOGN / 2;
         switch (ctx->ntt_split) {
-        case -1: return run_split<LOGN, M - 1>(ctx, data, rows, map, rowlist, inverse);
+        case -1: return run_split<LOGN, M - 1, RB>(ctx, data, rows, map, rowlist, inverse);
         case 1:
-            if constexpr (LOGN - (M + 1) >= 1) return run_split<LOGN, M + 1>(ctx, data, rows, map, rowlist, inverse);
-            else return run_split<LOGN, M>(ctx, data, rows, map, rowlist, inverse);
-        default: return run_split<LOGN, M>(ctx, data, rows, map, rowlist, inverse);
+            if constexpr (LOGN - (M + 1) >= 1) return run_split<LOGN, M + 1, RB>(ctx, data, rows, map, rowlist, inverse);
+            else return run_split<LOGN, M, RB>(ctx, data, rows, map, rowlist, inverse);
+        default: return run_split<LOGN, M, RB>(ctx, data, rows, map, rowlist, inverse);
         }
     }
+}
+
+template <int LOGN>
+int run_n(blb_ctx* ctx, uint64_t* data, uint32_t rows, const LimbMap& map, const uint32_t* rowlist, bool inverse)
+{
+    if (ctx->ntt_radix == 16) return run_nr<LOGN, 4>(ctx, data, rows, map, rowlist, inverse);
+    return run_nr<LOGN, 3>(ctx, data, rows, map, rowlist, inverse);
 }
 
 int run(blb_ctx* ctx, uint64_t* data, uint32_t rows, const LimbMap& map, const uint32_t* rowlist, bool inverse)
@@ -336,9 +348,11 @@ int run(blb_ctx* ctx, uint64_t* data, uint32_t rows, const LimbMap& map, const u
 
 }  // namespace
 
-extern "C" int blb_ntt_autotune(blb_ctx* ctx, uint32_t rows, int* split_out, double* us_per_row)  // us_per_row[3]
+// us_per_row[6]: radix 8 at splits -1, 0, +1, then radix 16 at the same splits
+extern "C" int blb_ntt_autotune(blb_ctx* ctx, uint32_t rows, int* split_out, int* radix_out, double* us_per_row)
 {
     if (!ctx || rows == 0) return blb_fail(BLB_ERR_ARG, "null argument or no rows");
+    BLB_TRY(refuse_capture(ctx, "NTT autotuning"));
     const size_t words = (size_t)rows * ctx->N;
     uint64_t* buf = (uint64_t*)dev_alloc(ctx, words * 8);
     if (!buf) return blb_fail(BLB_ERR_OOM, "autotune buffer");
@@ -347,38 +361,53 @@ extern "C" int blb_ntt_autotune(blb_ctx* ctx, uint32_t rows, int* split_out, dou
     cudaEvent_t e0, e1;
     BLB_CUDA(cudaEventCreate(&e0));
     BLB_CUDA(cudaEventCreate(&e1));
-    const int keep = ctx->ntt_split;
-    int best = 0, rc = BLB_OK;
+    const int keep_split = ctx->ntt_split, keep_radix = ctx->ntt_radix;
+    int best = 0, best_radix = 8, rc = BLB_OK;
     float best_ms = 1e30f;
-    double per[3] = {0, 0, 0};
-    for (int sp = -1; sp <= 1 && !rc; sp++) {
-        if (ctx->logN <= 12 && sp) continue;
-        ctx->ntt_split = sp;
-        float ms = 0;
-        for (int rep = 0; rep < 3 && !rc; rep++) {  // the first run is a warm-up
-            cudaEventRecord(e0, ctx->stream);
-            rc = run(ctx, buf, rows, map, nullptr, false);
-            if (!rc) rc = run(ctx, buf, rows, map, nullptr, true);
-            cudaEventRecord(e1, ctx->stream);
-            if (!rc && cudaEventSynchronize(e1) != cudaSuccess) rc = blb_fail(BLB_ERR_CUDA, "autotune run failed");
-            float t = 0;
-            cudaEventElapsedTime(&t, e0, e1);
-            if (rep) ms += t;
-        }
-        per[sp + 1] = ms * 1e3 / (2.0 * 2.0 * rows);  // two timed runs, forward + inverse
-        if (!rc && ms < best_ms) {
-            best_ms = ms;
-            best = sp;
+    double per[6] = {0, 0, 0, 0, 0, 0};
+    const int radices[2] = {8, 16};
+    for (int ri = 0; ri < 2 && !rc; ri++) {
+        for (int sp = -1; sp <= 1 && !rc; sp++) {
+            if (ctx->logN <= 12 && sp) continue;
+            ctx->ntt_split = sp;
+            ctx->ntt_radix = radices[ri];
+            float ms = 0;
+            for (int rep = 0; rep < 3 && !rc; rep++) {  // the first run is a warm-up
+                cudaEventRecord(e0, ctx->stream);
+                rc = run(ctx, buf, rows, map, nullptr, false);
+                if (!rc) rc = run(ctx, buf, rows, map, nullptr, true);
+                cudaEventRecord(e1, ctx->stream);
+                if (!rc && cudaEventSynchronize(e1) != cudaSuccess) rc = blb_fail(BLB_ERR_CUDA, "autotune run failed");
+                float t = 0;
+                cudaEventElapsedTime(&t, e0, e1);
+                if (rep) ms += t;
+            }
+            per[3 * ri + sp + 1] = ms * 1e3 / (2.0 * 2.0 * rows);  // two timed runs, forward + inverse
+            if (!rc && ms < best_ms) {
+                best_ms = ms;
+                best = sp;
+                best_radix = radices[ri];
+            }
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     dev_free(ctx, buf, words * 8);
-    ctx->ntt_split = rc ? keep : best;
+    ctx->ntt_split = rc ? keep_split : best;
+    ctx->ntt_radix = rc ? keep_radix : best_radix;
     if (rc) return rc;
     if (split_out) *split_out = best;
+    if (radix_out) *radix_out = best_radix;
     if (us_per_row)
-        for (int k = 0; k < 3; k++) us_per_row[k] = per[k];
+        for (int k = 0; k < 6; k++) us_per_row[k] = per[k];
+    return BLB_OK;
+}
+
+extern "C" int blb_ntt_set_radix(blb_ctx* ctx, int radix)
+{
+    if (!ctx) return blb_fail(BLB_ERR_ARG, "null context");
+    if (radix != 8 && radix != 16) return blb_fail(BLB_ERR_ARG, "NTT radix must be 8 or 16");
+    ctx->ntt_radix = radix;
     return BLB_OK;
 }
 

@@ -38,22 +38,27 @@ def test_ntt_parity(logN):
 
 @pytest.mark.parametrize("logN", [13, 15, 16, 17])
 def test_ntt_every_pass_split_matches_the_oracle(logN):
-    """The three column/row pass splits compute the same butterflies: every one
-    gives the oracle's forward transform, and the inverse restores the input;
-    the autotuner keeps one of them."""
+    """The three column/row pass splits and both radices of the register
+    rounds compute the same butterflies: every pair gives the oracle's forward
+    transform, and the inverse restores the input; the autotuner keeps one."""
     prm = wl.HEParams(logN, (60, 40), (60,), 2)
     o, ctx = make_oracle(prm), make_ctx(prm)
     data = wl.random_residues(o.primes, o.N, seed=logN + 7)[0]
     pidx = list(range(len(o.primes)))
     ref = [o.ntt(data[r], r) for r in range(len(pidx))]
-    for split in (-1, 0, 1):
-        ctx.ntt_set_split(split)
-        fwd = ctx.ntt(data, pidx)
-        for r in range(len(pidx)):
-            assert np.array_equal(fwd[r], ref[r]), (split, r)
-        assert np.array_equal(ctx.ntt(fwd, pidx, inverse=True), data), split
-    split, us = ctx.ntt_autotune(16)
-    assert split in (-1, 0, 1) and set(us) == {-1, 0, 1} and us[split] == min(us.values())
+    for radix in (8, 16):
+        ctx.ntt_set_radix(radix)
+        for split in (-1, 0, 1):
+            ctx.ntt_set_split(split)
+            fwd = ctx.ntt(data, pidx)
+            for r in range(len(pidx)):
+                assert np.array_equal(fwd[r], ref[r]), (radix, split, r)
+            assert np.array_equal(ctx.ntt(fwd, pidx, inverse=True), data), (radix, split)
+    split, radix, us = ctx.ntt_autotune(16)
+    want = {(rx, sp) for rx in (8, 16) for sp in ((-1, 0, 1) if logN > 12 else (0,))}
+    assert set(us) == want and us[(radix, split)] == min(us.values())
+    with pytest.raises(Exception):
+        ctx.ntt_set_radix(4)
 
 
 # ------------------------------------------------------------------ keys
