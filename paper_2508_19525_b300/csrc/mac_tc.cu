@@ -15,12 +15,16 @@
 //
 //     sum_t D X = sum_{a,b} 2^{8(a+b)} (sum_t D_a X_b).
 //
+// The bytes of D enter as fp16 subnormals (XX 2^-24, one byte permute per
+// pair), so the fp32 sums come out scaled by 2^-24, still exact.
 // The byte planes of D are the GEMM's M dimension (rows (a, eg)), those of X
 // are part of N (columns (b, s, p)).  The epilogue reads the exact fp32 sums
 // back as integers, adds them with their shifts 2^{8(a+b)} into four 64-bit
 // columns of weight 2^{32c} (no carries on the way), assembles the 128-bit sum
-// and reduces it mod q_i (Barrett).  Segments of at most 8 term tiles (4 for
-// primes above 2^60) keep the fp32 sums below 2^23 and the 128-bit sums exact.
+// and, once the lanes that hold other byte planes of the same sums have added
+// theirs (a transposing shuffle), reduces it mod q_i (Barrett).  Segments of at
+// most 8 term tiles (4 for primes above 2^60) keep the fp32 sums below 2^23
+// and the 128-bit sums exact.
 //
 // Plan layout (bytes): for limb i a region at off[i]; inside it, for each
 // coefficient j, each 16-output block, each 16-term tile kt and each byte
@@ -128,20 +132,17 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
                  : "memory");
 }
 
-// 8 bytes -> 4 registers of fp16 pairs (low half = lower byte): 0x64XX is the
-// fp16 number 1024 + XX, so one byte permute and one subtraction per pair.
+// 8 bytes -> 4 registers of fp16 pairs (low half = lower byte), one byte
+// permute per pair: the bit pattern 0x00XX is the subnormal fp16 number
+// XX 2^-24, so the mma sums of A are the integer sums scaled by 2^-24 (exact:
+// the tensor cores take fp16 subnormals as they are, and the scale only moves
+// the exponent of every fp32 partial sum)
 __device__ __forceinline__ void bytes_to_f16x2(uint2 v, uint32_t (&f)[4])
 {
-    const uint32_t k = 0x64646464u;
-    uint32_t h[4] = {__byte_perm(v.x, k, 0x5140), __byte_perm(v.x, k, 0x5342), __byte_perm(v.y, k, 0x5140),
-                     __byte_perm(v.y, k, 0x5342)};
-    const __half2 off = __halves2half2(__ushort_as_half(0x6400), __ushort_as_half(0x6400));
-#pragma unroll
-    for (int r = 0; r < 4; r++) {
-        __half2 x = *reinterpret_cast<__half2*>(&h[r]);
-        x = __hsub2(x, off);
-        f[r] = *reinterpret_cast<uint32_t*>(&x);
-    }
+    f[0] = __byte_perm(v.x, 0, 0x4140);
+    f[1] = __byte_perm(v.x, 0, 0x4342);
+    f[2] = __byte_perm(v.y, 0, 0x4140);
+    f[3] = __byte_perm(v.y, 0, 0x4342);
 }
 
 __device__ __forceinline__ void mma16816(float (&c)[4], const uint32_t (&a)[4], uint2 b)
@@ -159,12 +160,6 @@ __device__ __forceinline__ uint64_t reduce128(uint64_t lo, uint64_t hi, uint64_t
     return barrett128(lo, h, q, r0, r1);
 }
 
-__device__ __forceinline__ uint64_t add_mod(uint64_t a, uint64_t b, uint64_t q)
-{
-    const uint64_t s = a + b;
-    return s >= q ? s - q : s;
-}
-
 // byte planes of D accumulated together: all of them when the accumulators fit
 // 64 registers, else the largest divisor of NB that does
 template <int NB, int NT>
@@ -175,11 +170,32 @@ constexpr int plane_group()
     return 1;
 }
 
-// exact fp32 integer x < 2^23 -> uint32: x + 2^23 has exponent 23, so its
-// mantissa field is x (one add and one mask instead of a conversion)
+// exact fp32 x = n 2^-24 with an integer n < 2^23 -> n: x + 1/2 lies in
+// [1/2, 1), where the spacing of fp32 numbers is 2^-24, so its mantissa field is
+// n (one add and one mask instead of a conversion)
 __device__ __forceinline__ uint32_t f32_int(float x)
 {
-    return __float_as_uint(x + 8388608.0f) & 0x7FFFFFu;
+    return __float_as_uint(x + 0.5f) & 0x7FFFFFu;
+}
+
+__device__ __forceinline__ void add128(acc128& t, uint64_t lo, uint64_t hi)
+{
+    const uint64_t l = t.lo + lo;
+    t.hi += hi + (l < lo);
+    t.lo = l;
+}
+
+__device__ __forceinline__ acc128 shfl_xor128(acc128 v, int m)
+{
+    return {__shfl_xor_sync(0xffffffffu, v.lo, m), __shfl_xor_sync(0xffffffffu, v.hi, m)};
+}
+
+// 128-bit sum -> residue: below q 2^64 for byte planes of at most 6 (the sums
+// of one item stay below 16 KT q^2 with KT < 2^20 / (256 NB)), any value else
+template <int NB>
+__device__ __forceinline__ uint64_t reduce_sum(acc128 t, uint64_t q, uint64_t r0, uint64_t r1)
+{
+    return NB <= 6 ? barrett128(t.lo, t.hi, q, r0, r1) : reduce128(t.lo, t.hi, q, r0, r1);
 }
 
 template <int S, int NB>
@@ -320,11 +336,13 @@ __global__ void __launch_bounds__(mac_threads(S)) k_cp_mac_tc(const __grid_const
             const uint32_t jj = it / A.NEB, eblk = it % A.NEB;
             const uint8_t* As = ring + (size_t)st * item_bytes + lane * 8;
             const uint8_t* Bj = Bt + (size_t)jj * A.jstride;
-            uint64_t fin[2][SLOTS];
+            // 128-bit sums over the segments: raw for byte planes of at most
+            // 6, segment residues above
+            acc128 fin[2][SLOTS];
 #pragma unroll
             for (int r = 0; r < 2; r++)
 #pragma unroll
-                for (int u = 0; u < SLOTS; u++) fin[r][u] = 0;
+                for (int u = 0; u < SLOTS; u++) fin[r][u] = {0, 0};
             for (uint32_t ks = 0; ks < A.KT; ks += A.kseg) {
                 const uint32_t ke = min(A.KT, ks + A.kseg);
                 const bool last_seg = ke == A.KT;
@@ -397,18 +415,8 @@ __global__ void __launch_bounds__(mac_threads(S)) k_cp_mac_tc(const __grid_const
                             hi = (hi << sh) | (lo >> (64 - sh));
                             lo <<= sh;
                         }
-                        const uint64_t v = NB <= 6 ? barrett128(lo, hi, q, r0, r1) : reduce128(lo, hi, q, r0, r1);
-                        fin[r][u] = add_mod(fin[r][u], v, q);
-                    }
-            }
-            // partial sums of the byte planes that other lanes of the quad hold
-            if (SP < 8) {
-#pragma unroll
-                for (int r = 0; r < 2; r++)
-#pragma unroll
-                    for (int u = 0; u < SLOTS; u++) {
-                        if (SP == 2) fin[r][u] = add_mod(fin[r][u], __shfl_xor_sync(0xffffffffu, fin[r][u], 1), q);
-                        fin[r][u] = add_mod(fin[r][u], __shfl_xor_sync(0xffffffffu, fin[r][u], 2), q);
+                        if (NB <= 6) add128(fin[r][u], lo, hi);
+                        else add128(fin[r][u], reduce128(lo, hi, q, r0, r1), 0);
                     }
             }
             const size_t jcol = (size_t)i * A.N + j0 + jj;
@@ -416,18 +424,38 @@ __global__ void __launch_bounds__(mac_threads(S)) k_cp_mac_tc(const __grid_const
                 const uint32_t eg = eblk * 16 + row;
                 if (eg < A.neg) A.T[((size_t)((sp >> 1) * A.neg + eg) * 2 + (sp & 1)) * A.nN + jcol] = v;
             };
-            if (SP == 2) {
-                const uint32_t r = h4 >> 1, h = h4 & 1;
-                store(g8 + 8 * r, h, r ? (h ? fin[1][1] : fin[1][0]) : (h ? fin[0][1] : fin[0][0]));
-            } else if (SP == 4) {
-                const uint32_t r = h4 >> 1;
+            if (SP < 8) {
+                // the other lanes of the quad hold other byte planes of the same
+                // sums: a transposing reduction leaves each lane the sums it
+                // stores, so each of them is reduced once.  Lanes h4, h4 ^ 2
+                // exchange rows (keep row half r = h4 >> 1) ...
+                const bool rhi = h4 & 2;
+                acc128 k[2];
 #pragma unroll
-                for (int h = 0; h < 2; h++) store(g8 + 8 * r, 2 * (h4 & 1) + h, r ? fin[1][h] : fin[0][h]);
+                for (int u = 0; u < 2; u++) {
+                    k[u] = rhi ? fin[1][u] : fin[0][u];
+                    const acc128 o = shfl_xor128(rhi ? fin[0][u] : fin[1][u], 2);
+                    add128(k[u], o.lo, o.hi);
+                }
+                const uint32_t row = g8 + 8 * (h4 >> 1);
+                if (SP == 2) {
+                    // ... and for one sequence lanes h4, h4 ^ 1 hold the other
+                    // planes too: exchange polynomials (keep p = h4 & 1)
+                    const bool phi = h4 & 1;
+                    acc128 w = phi ? k[1] : k[0];
+                    const acc128 o = shfl_xor128(phi ? k[0] : k[1], 1);
+                    add128(w, o.lo, o.hi);
+                    store(row, h4 & 1, reduce_sum<NB>(w, q, r0, r1));
+                } else {
+#pragma unroll
+                    for (int h = 0; h < 2; h++) store(row, 2 * (h4 & 1) + h, reduce_sum<NB>(k[h], q, r0, r1));
+                }
             } else {
 #pragma unroll
                 for (int r = 0; r < 2; r++)
 #pragma unroll
-                    for (int u = 0; u < SLOTS; u++) store(g8 + 8 * r, 8 * (u >> 1) + 2 * h4 + (u & 1), fin[r][u]);
+                    for (int u = 0; u < SLOTS; u++)
+                        store(g8 + 8 * r, 8 * (u >> 1) + 2 * h4 + (u & 1), reduce_sum<NB>(fin[r][u], q, r0, r1));
             }
         }
         if (!ok) break;
