@@ -15,8 +15,8 @@
 //
 //     sum_t D X = sum_{a,b} 2^{8(a+b)} (sum_t D_a X_b).
 //
-// The bytes of D enter as fp16 subnormals (XX 2^-24, one byte permute per
-// pair), so the fp32 sums come out scaled by 2^-24, still exact.
+// The bytes of D and X enter as fp16 subnormals (XX 2^-24, one byte permute
+// per pair), so the fp32 sums come out scaled by 2^-48, still exact.
 // The byte planes of D are the GEMM's M dimension (rows (a, eg)), those of X
 // are part of N (columns (b, s, p)).  The epilogue reads the exact fp32 sums
 // back as integers, adds them with their shifts 2^{8(a+b)} into four 64-bit
@@ -134,9 +134,8 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
 
 // 8 bytes -> 4 registers of fp16 pairs (low half = lower byte), one byte
 // permute per pair: the bit pattern 0x00XX is the subnormal fp16 number
-// XX 2^-24, so the mma sums of A are the integer sums scaled by 2^-24 (exact:
-// the tensor cores take fp16 subnormals as they are, and the scale only moves
-// the exponent of every fp32 partial sum)
+// XX 2^-24 (exact: the tensor cores take fp16 subnormals as they are, and the
+// scale only moves the exponent of every fp32 partial sum)
 __device__ __forceinline__ void bytes_to_f16x2(uint2 v, uint32_t (&f)[4])
 {
     f[0] = __byte_perm(v.x, 0, 0x4140);
@@ -170,12 +169,35 @@ constexpr int plane_group()
     return 1;
 }
 
-// exact fp32 x = n 2^-24 with an integer n < 2^23 -> n: x + 1/2 lies in
-// [1/2, 1), where the spacing of fp32 numbers is 2^-24, so its mantissa field is
-// n (one add and one mask instead of a conversion)
-__device__ __forceinline__ uint32_t f32_int(float x)
+// Both operands are fp16 subnormals (bytes XX as XX 2^-24), so an mma sum is
+// x = n 2^-48 with an integer n < 2^23.  x + 2^-25 lies in [2^-25, 2^-24), where
+// the spacing of fp32 numbers is 2^-48: its bit pattern is MAC_BIAS_BITS + n.
+// The fold adds these patterns unmasked and starts every 64-bit column at
+// minus the sum of the MAC_BIAS_BITS terms that land on it (fold_bias), so the
+// columns end at the exact sums of the n with one add per accumulator.
+constexpr float MAC_BIAS = 2.98023223876953125e-08f;  // 2^-25
+constexpr uint32_t MAC_BIAS_BITS = 0x33000000u;
+
+__device__ __forceinline__ uint32_t f32_bits(float x)
 {
-    return __float_as_uint(x + 0.5f) & 0x7FFFFFu;
+    return __float_as_uint(x + MAC_BIAS);
+}
+
+// the (compile-time) sum of the bias patterns that the fold adds to column c
+// of slot u: the same shifts as the fold's, over every plane of D and tile of X
+template <int SP, int NB>
+__host__ __device__ constexpr uint64_t fold_bias(int u, int c)
+{
+    uint64_t s = 0;
+    for (int a = 0; a < NB; a++)
+        for (int nt = 0; nt < (NB * SP + 7) / 8; nt++)
+            for (int h = 0; h < 2; h++) {
+                const int uu = SP >= 8 ? (nt % (SP / 8)) * 2 + h : h;
+                const int b = SP >= 8 ? nt / (SP / 8) : nt * 8 / SP;
+                const int sh = 8 * (a + b);
+                if (uu == u && (sh >> 5) == c) s += (uint64_t)MAC_BIAS_BITS << (sh & 31);
+            }
+    return s;
 }
 
 __device__ __forceinline__ void add128(acc128& t, uint64_t lo, uint64_t hi)
@@ -275,12 +297,9 @@ __global__ void __launch_bounds__(mac_threads(S)) k_cp_mac_tc(const __grid_const
                         for (int b = 0; b < NB; b++) {
                             const uint32_t x0 = b < 4 ? w0[u].x : w0[u].y, x1 = b < 4 ? w1[u].x : w1[u].y;
                             const uint32_t two = __byte_perm(x0, x1, (b & 3) | ((4 + (b & 3)) << 4));
-                            uint32_t hv = __byte_perm(two, 0x64646464u, 0x5140);
-                            __half2 hx = *reinterpret_cast<__half2*>(&hv);
-                            hx = __hsub2(hx, __halves2half2(__ushort_as_half(0x6400), __ushort_as_half(0x6400)));
-                            const uint32_t col = b * SP + sp;
+                            const uint32_t col = b * SP + sp;  // two bytes as fp16 subnormals
                             *reinterpret_cast<uint32_t*>(base + (col >> 3) * 256 + (col & 7) * 32) =
-                                *reinterpret_cast<uint32_t*>(&hx);
+                                __byte_perm(two, 0, 0x4140);
                         }
                     }
                 }
@@ -353,7 +372,7 @@ __global__ void __launch_bounds__(mac_threads(S)) k_cp_mac_tc(const __grid_const
 #pragma unroll
                     for (int u = 0; u < SLOTS; u++)
 #pragma unroll
-                        for (int c = 0; c < 4; c++) col[r][u][c] = 0;
+                        for (int c = 0; c < 4; c++) col[r][u][c] = 0 - fold_bias<SP, NB>(u, c);
 #pragma unroll
                 for (int a0 = 0; a0 < NB; a0 += AG) {
                     float acc[AG][NT][4];
@@ -401,7 +420,7 @@ __global__ void __launch_bounds__(mac_threads(S)) k_cp_mac_tc(const __grid_const
                                 const int u = SP >= 8 ? (nt % (SP / 8)) * 2 + h : h;
                                 const int b = SP >= 8 ? nt / (SP / 8) : nt * 8 / SP;
                                 const int sh = 8 * (a0 + a + b);
-                                col[r][u][sh >> 5] += (uint64_t)f32_int(acc[a][nt][e]) << (sh & 31);
+                                col[r][u][sh >> 5] += (uint64_t)f32_bits(acc[a][nt][e]) << (sh & 31);
                             }
                 }
 #pragma unroll
