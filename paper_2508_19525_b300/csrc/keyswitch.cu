@@ -401,6 +401,9 @@ __global__ void k_ksb_digit_rows(uint64_t* __restrict__ ext, const uint64_t* __r
 // for the special-prime rows t = n + blockIdx.y only: they are the input of
 // the ModDown conversion.  The ciphertext-prime rows are summed where they are
 // used, in k_ksb_finish, so they are never written out.
+// NB: the digit count beta as a compile-time loop bound (0 = any), so that
+// every digit's loads are in flight together.
+template <int NB>
 __global__ void k_ksb_inner(uint64_t* __restrict__ acc, const uint64_t* __restrict__ ext,
                             const DevGroup* __restrict__ groups, const DevProduct* __restrict__ prods, const __grid_constant__ LimbMap emap,
                             uint32_t n, uint32_t E, uint32_t beta, uint32_t nQ, uint32_t np,
@@ -418,7 +421,8 @@ __global__ void k_ksb_inner(uint64_t* __restrict__ acc, const uint64_t* __restri
         const DevProduct P = prods[x];
         const uint64_t* xs = ext + (size_t)P.src * beta * E * N + (size_t)t * N + perm_index(c, logN, P.g);
         acc128 a0{0, 0}, a1{0, 0};
-        for (uint32_t j = 0; j < beta; j++) {
+#pragma unroll
+        for (uint32_t j = 0; j < (NB > 0 ? (uint32_t)NB : beta); j++) {
             const uint64_t v = xs[(size_t)j * E * N];
             mad128(a0, v, P.key[(((size_t)j * 2 + 0) * np + kt) * N + c]);
             mad128(a1, v, P.key[(((size_t)j * 2 + 1) * np + kt) * N + c]);
@@ -435,6 +439,7 @@ __global__ void k_ksb_inner(uint64_t* __restrict__ acc, const uint64_t* __restri
 // acc_p = sum over the group's products of sum_j sigma_x(ext[src_x][j][i]) key_x[j][p][i]
 // (the same sums k_ksb_inner forms for the special primes), then
 // out_p = [out_p +] sum_{addends of p} add[perm(k)] + (acc_p - cv_p) P^-1
+template <int NB>  // as for k_ksb_inner
 __global__ void __launch_bounds__(256, 6) k_ksb_finish(const DevGroup* __restrict__ groups, const DevProduct* __restrict__ prods,
                              const uint64_t* __restrict__ ext, const KsAdd* __restrict__ adds,
                              const uint64_t* __restrict__ cv, uint32_t n, uint32_t E, uint32_t beta, uint32_t np,
@@ -454,7 +459,8 @@ __global__ void __launch_bounds__(256, 6) k_ksb_finish(const DevGroup* __restric
     for (uint32_t x = G.prod0; x < G.prod1; x++) {
         const DevProduct P = prods[x];
         const uint64_t* xs = ext + (size_t)P.src * beta * E * N + (size_t)i * N + perm_index(k, logN, P.g);
-        for (uint32_t j = 0; j < beta; j++) {
+#pragma unroll
+        for (uint32_t j = 0; j < (NB > 0 ? (uint32_t)NB : beta); j++) {
             const uint64_t v = xs[(size_t)j * E * N];
             mad128(a0, v, P.key[(((size_t)j * 2 + 0) * np + i) * N + k]);
             mad128(a1, v, P.key[(((size_t)j * 2 + 1) * np + i) * N + k]);
@@ -479,6 +485,31 @@ __global__ void __launch_bounds__(256, 6) k_ksb_finish(const DevGroup* __restric
         }
         uint64_t* o = (p ? G.out1 : G.out0) + (size_t)i * N + k;
         *o = accumulate ? add_mod(*o, r, q) : r;
+    }
+}
+
+// launches with the digit count as a compile-time bound where it is small
+template <typename... Args>
+void launch_inner(uint32_t beta, dim3 grid, cudaStream_t st, Args... args)
+{
+    switch (beta) {
+    case 1: k_ksb_inner<1><<<grid, kT, 0, st>>>(args...); break;
+    case 2: k_ksb_inner<2><<<grid, kT, 0, st>>>(args...); break;
+    case 3: k_ksb_inner<3><<<grid, kT, 0, st>>>(args...); break;
+    case 4: k_ksb_inner<4><<<grid, kT, 0, st>>>(args...); break;
+    default: k_ksb_inner<0><<<grid, kT, 0, st>>>(args...); break;
+    }
+}
+
+template <typename... Args>
+void launch_finish(uint32_t beta, dim3 grid, cudaStream_t st, Args... args)
+{
+    switch (beta) {
+    case 1: k_ksb_finish<1><<<grid, kT, 0, st>>>(args...); break;
+    case 2: k_ksb_finish<2><<<grid, kT, 0, st>>>(args...); break;
+    case 3: k_ksb_finish<3><<<grid, kT, 0, st>>>(args...); break;
+    case 4: k_ksb_finish<4><<<grid, kT, 0, st>>>(args...); break;
+    default: k_ksb_finish<0><<<grid, kT, 0, st>>>(args...); break;
     }
 }
 
@@ -656,8 +687,9 @@ int ks_run(blb_ctx* ctx, uint32_t level, const KsSource* sources, uint32_t n_src
             k_ksb_digit_rows<<<dim3(gx, n, ns), kT, 0, ctx->stream>>>(ext, din, n, E, beta, alpha, N);
             BLB_LAUNCHED();
         }
-        k_ksb_inner<<<dim3(gx, nP, ng), kT, 0, ctx->stream>>>(acc, ext, d_grp, d_prod, emap, n, E, beta, ctx->nQ,
-                                                               ctx->np, ctx->d_q, ctx->d_bar, ctx->logN);
+        launch_inner(beta, dim3(gx, nP, ng), ctx->stream, acc, (const uint64_t*)ext, (const DevGroup*)d_grp,
+                     (const DevProduct*)d_prod, emap, n, E, beta, ctx->nQ, ctx->np, (const uint64_t*)ctx->d_q,
+                     (const uint64_t*)ctx->d_bar, ctx->logN);
         BLB_LAUNCHED();
         BLB_TRY(ntt_inverse_list(ctx, acc, (uint32_t)p_rows.size(), d_p_rows));
         launch_moddown_conv(nP, dim3(gx, 2 * ng), ctx->stream, (const uint64_t*)(acc + (size_t)n * N),
@@ -665,8 +697,9 @@ int ks_run(blb_ctx* ctx, uint32_t level, const KsSource* sources, uint32_t n_src
                             (const uint64_t*)ctx->d_q, (const uint64_t*)ctx->d_bar, N);
         BLB_LAUNCHED();
         BLB_TRY(ntt_forward(ctx, cv, ng * 2 * n, ctx->qmap(n)));
-        k_ksb_finish<<<dim3(gx, n, ng), kT, 0, ctx->stream>>>(d_grp, d_prod, ext, d_add, cv, n, E, beta, ctx->np,
-                                                              pinv, ctx->d_q, ctx->d_bar, ctx->logN, accumulate);
+        launch_finish(beta, dim3(gx, n, ng), ctx->stream, (const DevGroup*)d_grp, (const DevProduct*)d_prod,
+                      (const uint64_t*)ext, (const KsAdd*)d_add, (const uint64_t*)cv, n, E, beta, ctx->np, pinv,
+                      (const uint64_t*)ctx->d_q, (const uint64_t*)ctx->d_bar, ctx->logN, accumulate);
         BLB_LAUNCHED();
         for (uint32_t s : used) local[s] = -1;
         g0 = g1;
