@@ -274,7 +274,7 @@ __global__ void __launch_bounds__(mac_threads(S)) k_cp_mac_tc(const __grid_const
             uint8_t* Bjj = Bt + (size_t)jj * A.jstride;
 #pragma unroll
             for (int s = 0; s < S; s++) {
-                constexpr int U = 8;
+                constexpr int U = S == 1 ? 12 : 8;
                 for (uint32_t v0 = lane / A.CT; v0 < TP2; v0 += U * rstep) {
                     uint2 w0[U], w1[U];
 #pragma unroll
