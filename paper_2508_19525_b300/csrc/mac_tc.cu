@@ -57,6 +57,7 @@ constexpr int mac_consumers(int S) { return S == 1 ? 8 : 4; }
 constexpr int mac_threads(int S) { return 32 * (mac_consumers(S) + 2); }
 constexpr uint32_t MAC_BBUF_BYTES = 16u << 10;
 constexpr int MAC_MAX_GROUP = 64;  // limbs per launch
+constexpr uint32_t MAC_MAX_BBUFS = 4;
 constexpr uint64_t MAC_WAIT_NS = 2000000000ull;  // bounded waits: 2 s
 
 struct MacArgs {
@@ -69,6 +70,7 @@ struct MacArgs {
     uint64_t nN, seq_words;
     uint32_t N, terms, KT, neg, NEB, CT, kseg, R, jstride;
     uint32_t tiles_per_limb, tiles;  // coefficient tiles of CT per limb, over all limbs of the launch
+    uint32_t nbb;                    // B fragment buffers (2 .. MAC_MAX_BBUFS)
     uint32_t limb[MAC_MAX_GROUP];
     uint64_t off[MAC_MAX_GROUP];
 };
@@ -234,22 +236,23 @@ __global__ void __launch_bounds__(mac_threads(S)) k_cp_mac_tc(const __grid_const
     const uint32_t IPT = A.CT * A.NEB;  // items (coefficient, output block) per tile
     const uint32_t R = A.R;
     const size_t bbuf = ((size_t)A.CT * A.jstride + 127) & ~(size_t)127;
-    uint8_t* Bs = smem;  // two buffers of B fragments
-    uint8_t* ring = smem + 2 * bbuf;
+    const uint32_t NBB = S == 1 ? 2 : A.nbb;  // one sequence: always two (the launcher's choice)
+    uint8_t* Bs = smem;  // NBB buffers of B fragments
+    uint8_t* ring = smem + NBB * bbuf;
     uint64_t* bars = reinterpret_cast<uint64_t*>(ring + (size_t)R * item_bytes);
-    volatile uint32_t* abort = reinterpret_cast<volatile uint32_t*>(bars + 2 * R + 4);
+    volatile uint32_t* abort = reinterpret_cast<volatile uint32_t*>(bars + 2 * R + 2 * MAC_MAX_BBUFS);
     const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + R), bfull0 = smem_u32(bars + 2 * R),
-                   bempty0 = smem_u32(bars + 2 * R + 2), ring0 = smem_u32(ring);
+                   bempty0 = smem_u32(bars + 2 * R + MAC_MAX_BBUFS), ring0 = smem_u32(ring);
 
     // B padding (terms beyond the last term, columns beyond NB SP) stays zero
-    for (uint32_t x = threadIdx.x; x < 2 * bbuf / 16; x += MAC_THREADS)
+    for (uint32_t x = threadIdx.x; x < NBB * bbuf / 16; x += MAC_THREADS)
         reinterpret_cast<uint4*>(Bs)[x] = make_uint4(0, 0, 0, 0);
     if (threadIdx.x == 0) {
         for (uint32_t r = 0; r < R; r++) {
             mbar_init(full0 + 8 * r, 1);
             mbar_init(empty0 + 8 * r, 1);
         }
-        for (uint32_t r = 0; r < 2; r++) {
+        for (uint32_t r = 0; r < NBB; r++) {
             mbar_init(bfull0 + 8 * r, 1);
             mbar_init(bempty0 + 8 * r, MAC_CONSUMERS);
         }
@@ -259,38 +262,86 @@ __global__ void __launch_bounds__(mac_threads(S)) k_cp_mac_tc(const __grid_const
     __syncthreads();
 
     if (warp == MAC_CONSUMERS + 1) {
-        // ---- B builder: per tile, X's byte planes as mma B fragments, one tile
-        // ahead of the consumers (two buffers)
+        // ---- B builder: per tile, X's byte planes as mma B fragments, up to
+        // NBB - 1 tiles ahead of the consumers
         for (uint32_t lt = 0, tau = blockIdx.x; tau < A.tiles; lt++, tau += gridDim.x) {
-            const uint32_t buf = lt & 1, gi = tau / A.tiles_per_limb, i = A.limb[gi];
+            const uint32_t buf = lt % NBB, gi = tau / A.tiles_per_limb, i = A.limb[gi];
             const uint32_t j0 = (tau % A.tiles_per_limb) * A.CT;
-            if (lt >= 2 && !mbar_wait(bempty0 + 8 * buf, ((lt >> 1) - 1) & 1, abort)) break;
+            if (lt >= NBB && !mbar_wait(bempty0 + 8 * buf, ((lt / NBB) - 1) & 1, abort)) break;
             uint8_t* Bt = Bs + buf * bbuf;
             // lane -> coefficient jj = lane % CT and a stride of 32 / CT over the
-            // rows (s, term pair, p); baby-step row r = (s terms + t) 2 + p lives
-            // at r nN, and terms 2 tp, 2 tp + 1 share one fp16 pair per byte plane
+            // rows f = (s, term pair, p) of all sequences, U of them per batch of
+            // loads; baby-step row r = (s terms + t) 2 + p lives at r nN, and
+            // terms 2 tp, 2 tp + 1 share one fp16 pair per byte plane
             const uint32_t jj = lane % A.CT, rstep = 32 / A.CT, TP2 = ((A.terms + 1) >> 1) * 2;
             const uint64_t* col0 = A.baby + (size_t)i * A.N + j0 + jj;
             uint8_t* Bjj = Bt + (size_t)jj * A.jstride;
-#pragma unroll
-            for (int s = 0; s < S; s++) {
-                constexpr int U = S == 1 ? 12 : 8;
-                for (uint32_t v0 = lane / A.CT; v0 < TP2; v0 += U * rstep) {
-                    uint2 w0[U], w1[U];
-#pragma unroll
-                    for (int u = 0; u < U; u++) {
-                        const uint32_t v = v0 + u * rstep, p = v & 1, t = (v >> 1) * 2;
-                        const size_t r = ((size_t)s * A.terms + t) * 2 + p;
-                        w0[u] = w1[u] = make_uint2(0, 0);
-                        if (v < TP2) {
-                            w0[u] = *reinterpret_cast<const uint2*>(col0 + r * A.nN);
-                            if (t + 1 < A.terms) w1[u] = *reinterpret_cast<const uint2*>(col0 + (r + 2) * A.nN);
+            if constexpr (S == 1) {
+                // one sequence: rows (term pair, p) in batches of U loads
+    #pragma unroll
+                for (int s = 0; s < S; s++) {
+                    constexpr int U = 12;
+                    for (uint32_t v0 = lane / A.CT; v0 < TP2; v0 += U * rstep) {
+                        uint2 w0[U], w1[U];
+    #pragma unroll
+                        for (int u = 0; u < U; u++) {
+                            const uint32_t v = v0 + u * rstep, p = v & 1, t = (v >> 1) * 2;
+                            const size_t r = ((size_t)s * A.terms + t) * 2 + p;
+                            w0[u] = w1[u] = make_uint2(0, 0);
+                            if (v < TP2) {
+                                w0[u] = *reinterpret_cast<const uint2*>(col0 + r * A.nN);
+                                if (t + 1 < A.terms) w1[u] = *reinterpret_cast<const uint2*>(col0 + (r + 2) * A.nN);
+                            }
+                        }
+    #pragma unroll
+                        for (int u = 0; u < U; u++) {
+                            const uint32_t v = v0 + u * rstep;
+                            if (v >= TP2) break;
+                            const uint32_t p = v & 1, t = (v >> 1) * 2, sp = 2 * s + p, kr = t & 15;
+                            uint8_t* base = Bjj + (size_t)(t >> 4) * NT * 256 + ((kr & 7) >> 1) * 8 + (kr >> 3) * 4;
+    #pragma unroll
+                            for (int b = 0; b < NB; b++) {
+                                const uint32_t x0 = b < 4 ? w0[u].x : w0[u].y, x1 = b < 4 ? w1[u].x : w1[u].y;
+                                const uint32_t two = __byte_perm(x0, x1, (b & 3) | ((4 + (b & 3)) << 4));
+                                const uint32_t col = b * SP + sp;  // two bytes as fp16 subnormals
+                                *reinterpret_cast<uint32_t*>(base + (col >> 3) * 256 + (col & 7) * 32) =
+                                    __byte_perm(two, 0, 0x4140);
+                            }
                         }
                     }
+                }
+            } else {
+                // batches: the rows f = (s, term pair, p) of all sequences in
+                // one index, so that a tile's loads go out in few batches
+                auto next = [&](uint32_t& s, uint32_t& v) {  // f += rstep as (s, v)
+                    v += rstep;
+                    while (v >= TP2) {
+                        v -= TP2;
+                        s++;
+                    }
+                };
+                constexpr int U = 12;
+                for (uint32_t f0 = lane / A.CT; f0 < S * TP2; f0 += U * rstep) {
+                    const uint32_t s0 = f0 / TP2, v0 = f0 - s0 * TP2;
+                    uint2 w0[U], w1[U];
+                    {
+                        uint32_t s = s0, v = v0;
 #pragma unroll
-                    for (int u = 0; u < U; u++) {
-                        const uint32_t v = v0 + u * rstep;
-                        if (v >= TP2) break;
+                        for (int u = 0; u < U; u++) {
+                            const uint32_t p = v & 1, t = (v >> 1) * 2;
+                            const size_t r = ((size_t)s * A.terms + t) * 2 + p;
+                            w0[u] = w1[u] = make_uint2(0, 0);
+                            if (s < S) {
+                                w0[u] = *reinterpret_cast<const uint2*>(col0 + r * A.nN);
+                                if (t + 1 < A.terms) w1[u] = *reinterpret_cast<const uint2*>(col0 + (r + 2) * A.nN);
+                            }
+                            next(s, v);
+                        }
+                    }
+                    uint32_t s = s0, v = v0;
+#pragma unroll
+                    for (int u = 0; u < U; u++, next(s, v)) {
+                        if (s >= S) break;
                         const uint32_t p = v & 1, t = (v >> 1) * 2, sp = 2 * s + p, kr = t & 15;
                         uint8_t* base = Bjj + (size_t)(t >> 4) * NT * 256 + ((kr & 7) >> 1) * 8 + (kr >> 3) * 4;
 #pragma unroll
@@ -339,10 +390,10 @@ __global__ void __launch_bounds__(mac_threads(S)) k_cp_mac_tc(const __grid_const
     const uint32_t g8 = lane >> 2, h4 = lane & 3;
     const uint32_t lane_b = SP >= 8 ? 0 : (2 * h4) / SP;  // byte plane offset of this lane's columns
     for (uint32_t lt = 0, tau = blockIdx.x; tau < A.tiles; lt++, tau += gridDim.x) {
-        const uint32_t buf = lt & 1, gi = tau / A.tiles_per_limb, i = A.limb[gi];
+        const uint32_t buf = lt % NBB, gi = tau / A.tiles_per_limb, i = A.limb[gi];
         const uint32_t j0 = (tau % A.tiles_per_limb) * A.CT;
         const uint64_t q = A.q[i], r0 = A.bar[2 * i], r1 = A.bar[2 * i + 1];
-        if (!mbar_wait(bfull0 + 8 * buf, (lt >> 1) & 1, abort)) break;
+        if (!mbar_wait(bfull0 + 8 * buf, (lt / NBB) & 1, abort)) break;
         const uint8_t* Bt = Bs + buf * bbuf + lane * 8;
         uint32_t it = (warp + MAC_CONSUMERS - (lt * IPT) % MAC_CONSUMERS) % MAC_CONSUMERS;
         bool ok = true;
@@ -521,7 +572,17 @@ int launch_group(blb_ctx* c, MacArgs& a, uint32_t nlimbs)
     constexpr int W = mac_consumers(S);
     const size_t bbuf = ((size_t)a.CT * a.jstride + 127) & ~(size_t)127;
     a.R = W;
-    const size_t smem = 2 * bbuf + (size_t)a.R * item_bytes + 16 * a.R + 64;
+    // B buffers: two, and for batches whose tiles hold fewer items than there
+    // are consumers, as many more (up to MAC_MAX_BBUFS) as keep two CTAs per SM
+    // in shared memory, so that every consumer has a tile to work on
+    const auto smem_for = [&](uint32_t nbb) {
+        return nbb * bbuf + (size_t)a.R * item_bytes + 16 * (a.R + MAC_MAX_BBUFS) + 16;
+    };
+    a.nbb = 2;
+    while (S > 1 && a.nbb < MAC_MAX_BBUFS && (size_t)a.CT * a.NEB * a.nbb < (size_t)W &&
+           smem_for(a.nbb + 1) <= (113u << 10))
+        a.nbb++;
+    const size_t smem = smem_for(a.nbb);
     if (smem > (227u << 10)) return blb_fail(BLB_ERR_ARG, "plaintext tile too large for shared memory");
     if (item_bytes >= (1u << 20)) return blb_fail(BLB_ERR_ARG, "too many plaintext terms per output");
     static bool attr = false;
