@@ -71,6 +71,7 @@ struct MacArgs {
     uint32_t N, terms, KT, neg, NEB, CT, kseg, R, jstride;
     uint32_t tiles_per_limb, tiles;  // coefficient tiles of CT per limb, over all limbs of the launch
     uint32_t nbb;                    // B fragment buffers (2 .. MAC_MAX_BBUFS)
+    uint32_t selfb;                  // batches of one item per tile: each consumer builds its own B
     uint32_t limb[MAC_MAX_GROUP];
     uint64_t off[MAC_MAX_GROUP];
 };
@@ -222,6 +223,103 @@ __device__ __forceinline__ uint64_t reduce_sum(acc128 t, uint64_t q, uint64_t r0
     return NB <= 6 ? barrett128(t.lo, t.hi, q, r0, r1) : reduce128(t.lo, t.hi, q, r0, r1);
 }
 
+// B builder body: tile tau's baby-step coefficients as mma B fragments of the
+// X byte planes in the buffer Bt (one warp; padding stays as it was)
+template <int S, int NB>
+__device__ __forceinline__ void build_b(const MacArgs& A, uint8_t* Bt, uint32_t tau, uint32_t lane)
+{
+    constexpr int SP = 2 * S;
+    constexpr int NT = (NB * SP + 7) / 8;
+    const uint32_t gi = tau / A.tiles_per_limb, i = A.limb[gi];
+    const uint32_t j0 = (tau % A.tiles_per_limb) * A.CT;
+    // lane -> coefficient jj = lane % CT and a stride of 32 / CT over the
+    // rows f = (s, term pair, p) of all sequences, U of them per batch of
+    // loads; baby-step row r = (s terms + t) 2 + p lives at r nN, and
+    // terms 2 tp, 2 tp + 1 share one fp16 pair per byte plane
+    const uint32_t jj = lane % A.CT, rstep = 32 / A.CT, TP2 = ((A.terms + 1) >> 1) * 2;
+    const uint64_t* col0 = A.baby + (size_t)i * A.N + j0 + jj;
+    uint8_t* Bjj = Bt + (size_t)jj * A.jstride;
+    if constexpr (S == 1) {
+        // one sequence: rows (term pair, p) in batches of U loads
+#pragma unroll
+        for (int s = 0; s < S; s++) {
+            constexpr int U = 12;
+            for (uint32_t v0 = lane / A.CT; v0 < TP2; v0 += U * rstep) {
+                uint2 w0[U], w1[U];
+#pragma unroll
+                for (int u = 0; u < U; u++) {
+                    const uint32_t v = v0 + u * rstep, p = v & 1, t = (v >> 1) * 2;
+                    const size_t r = ((size_t)s * A.terms + t) * 2 + p;
+                    w0[u] = w1[u] = make_uint2(0, 0);
+                    if (v < TP2) {
+                        w0[u] = *reinterpret_cast<const uint2*>(col0 + r * A.nN);
+                        if (t + 1 < A.terms) w1[u] = *reinterpret_cast<const uint2*>(col0 + (r + 2) * A.nN);
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < U; u++) {
+                    const uint32_t v = v0 + u * rstep;
+                    if (v >= TP2) break;
+                    const uint32_t p = v & 1, t = (v >> 1) * 2, sp = 2 * s + p, kr = t & 15;
+                    uint8_t* base = Bjj + (size_t)(t >> 4) * NT * 256 + ((kr & 7) >> 1) * 8 + (kr >> 3) * 4;
+#pragma unroll
+                    for (int b = 0; b < NB; b++) {
+                        const uint32_t x0 = b < 4 ? w0[u].x : w0[u].y, x1 = b < 4 ? w1[u].x : w1[u].y;
+                        const uint32_t two = __byte_perm(x0, x1, (b & 3) | ((4 + (b & 3)) << 4));
+                        const uint32_t col = b * SP + sp;  // two bytes as fp16 subnormals
+                        *reinterpret_cast<uint32_t*>(base + (col >> 3) * 256 + (col & 7) * 32) =
+                            __byte_perm(two, 0, 0x4140);
+                    }
+                }
+            }
+        }
+    } else {
+        // batches: the rows f = (s, term pair, p) of all sequences in
+        // one index, so that a tile's loads go out in few batches
+        auto next = [&](uint32_t& s, uint32_t& v) {  // f += rstep as (s, v)
+            v += rstep;
+            while (v >= TP2) {
+                v -= TP2;
+                s++;
+            }
+        };
+        constexpr int U = 12;
+        for (uint32_t f0 = lane / A.CT; f0 < S * TP2; f0 += U * rstep) {
+            const uint32_t s0 = f0 / TP2, v0 = f0 - s0 * TP2;
+            uint2 w0[U], w1[U];
+            {
+                uint32_t s = s0, v = v0;
+#pragma unroll
+                for (int u = 0; u < U; u++) {
+                    const uint32_t p = v & 1, t = (v >> 1) * 2;
+                    const size_t r = ((size_t)s * A.terms + t) * 2 + p;
+                    w0[u] = w1[u] = make_uint2(0, 0);
+                    if (s < S) {
+                        w0[u] = *reinterpret_cast<const uint2*>(col0 + r * A.nN);
+                        if (t + 1 < A.terms) w1[u] = *reinterpret_cast<const uint2*>(col0 + (r + 2) * A.nN);
+                    }
+                    next(s, v);
+                }
+            }
+            uint32_t s = s0, v = v0;
+#pragma unroll
+            for (int u = 0; u < U; u++, next(s, v)) {
+                if (s >= S) break;
+                const uint32_t p = v & 1, t = (v >> 1) * 2, sp = 2 * s + p, kr = t & 15;
+                uint8_t* base = Bjj + (size_t)(t >> 4) * NT * 256 + ((kr & 7) >> 1) * 8 + (kr >> 3) * 4;
+#pragma unroll
+                for (int b = 0; b < NB; b++) {
+                    const uint32_t x0 = b < 4 ? w0[u].x : w0[u].y, x1 = b < 4 ? w1[u].x : w1[u].y;
+                    const uint32_t two = __byte_perm(x0, x1, (b & 3) | ((4 + (b & 3)) << 4));
+                    const uint32_t col = b * SP + sp;  // two bytes as fp16 subnormals
+                    *reinterpret_cast<uint32_t*>(base + (col >> 3) * 256 + (col & 7) * 32) =
+                        __byte_perm(two, 0, 0x4140);
+                }
+            }
+        }
+    }
+}
+
 template <int S, int NB>
 __global__ void __launch_bounds__(mac_threads(S)) k_cp_mac_tc(const __grid_constant__ MacArgs A)
 {
@@ -237,6 +335,7 @@ __global__ void __launch_bounds__(mac_threads(S)) k_cp_mac_tc(const __grid_const
     const uint32_t R = A.R;
     const size_t bbuf = ((size_t)A.CT * A.jstride + 127) & ~(size_t)127;
     const uint32_t NBB = S == 1 ? 2 : A.nbb;  // one sequence: always two (the launcher's choice)
+    const bool selfb = S > 1 && A.selfb != 0;  // then NBB = consumers, one private buffer each
     uint8_t* Bs = smem;  // NBB buffers of B fragments
     uint8_t* ring = smem + NBB * bbuf;
     uint64_t* bars = reinterpret_cast<uint64_t*>(ring + (size_t)R * item_bytes);
@@ -262,99 +361,13 @@ __global__ void __launch_bounds__(mac_threads(S)) k_cp_mac_tc(const __grid_const
     __syncthreads();
 
     if (warp == MAC_CONSUMERS + 1) {
+        if (selfb) return;
         // ---- B builder: per tile, X's byte planes as mma B fragments, up to
         // NBB - 1 tiles ahead of the consumers
         for (uint32_t lt = 0, tau = blockIdx.x; tau < A.tiles; lt++, tau += gridDim.x) {
-            const uint32_t buf = lt % NBB, gi = tau / A.tiles_per_limb, i = A.limb[gi];
-            const uint32_t j0 = (tau % A.tiles_per_limb) * A.CT;
+            const uint32_t buf = lt % NBB;
             if (lt >= NBB && !mbar_wait(bempty0 + 8 * buf, ((lt / NBB) - 1) & 1, abort)) break;
-            uint8_t* Bt = Bs + buf * bbuf;
-            // lane -> coefficient jj = lane % CT and a stride of 32 / CT over the
-            // rows f = (s, term pair, p) of all sequences, U of them per batch of
-            // loads; baby-step row r = (s terms + t) 2 + p lives at r nN, and
-            // terms 2 tp, 2 tp + 1 share one fp16 pair per byte plane
-            const uint32_t jj = lane % A.CT, rstep = 32 / A.CT, TP2 = ((A.terms + 1) >> 1) * 2;
-            const uint64_t* col0 = A.baby + (size_t)i * A.N + j0 + jj;
-            uint8_t* Bjj = Bt + (size_t)jj * A.jstride;
-            if constexpr (S == 1) {
-                // one sequence: rows (term pair, p) in batches of U loads
-    #pragma unroll
-                for (int s = 0; s < S; s++) {
-                    constexpr int U = 12;
-                    for (uint32_t v0 = lane / A.CT; v0 < TP2; v0 += U * rstep) {
-                        uint2 w0[U], w1[U];
-    #pragma unroll
-                        for (int u = 0; u < U; u++) {
-                            const uint32_t v = v0 + u * rstep, p = v & 1, t = (v >> 1) * 2;
-                            const size_t r = ((size_t)s * A.terms + t) * 2 + p;
-                            w0[u] = w1[u] = make_uint2(0, 0);
-                            if (v < TP2) {
-                                w0[u] = *reinterpret_cast<const uint2*>(col0 + r * A.nN);
-                                if (t + 1 < A.terms) w1[u] = *reinterpret_cast<const uint2*>(col0 + (r + 2) * A.nN);
-                            }
-                        }
-    #pragma unroll
-                        for (int u = 0; u < U; u++) {
-                            const uint32_t v = v0 + u * rstep;
-                            if (v >= TP2) break;
-                            const uint32_t p = v & 1, t = (v >> 1) * 2, sp = 2 * s + p, kr = t & 15;
-                            uint8_t* base = Bjj + (size_t)(t >> 4) * NT * 256 + ((kr & 7) >> 1) * 8 + (kr >> 3) * 4;
-    #pragma unroll
-                            for (int b = 0; b < NB; b++) {
-                                const uint32_t x0 = b < 4 ? w0[u].x : w0[u].y, x1 = b < 4 ? w1[u].x : w1[u].y;
-                                const uint32_t two = __byte_perm(x0, x1, (b & 3) | ((4 + (b & 3)) << 4));
-                                const uint32_t col = b * SP + sp;  // two bytes as fp16 subnormals
-                                *reinterpret_cast<uint32_t*>(base + (col >> 3) * 256 + (col & 7) * 32) =
-                                    __byte_perm(two, 0, 0x4140);
-                            }
-                        }
-                    }
-                }
-            } else {
-                // batches: the rows f = (s, term pair, p) of all sequences in
-                // one index, so that a tile's loads go out in few batches
-                auto next = [&](uint32_t& s, uint32_t& v) {  // f += rstep as (s, v)
-                    v += rstep;
-                    while (v >= TP2) {
-                        v -= TP2;
-                        s++;
-                    }
-                };
-                constexpr int U = 12;
-                for (uint32_t f0 = lane / A.CT; f0 < S * TP2; f0 += U * rstep) {
-                    const uint32_t s0 = f0 / TP2, v0 = f0 - s0 * TP2;
-                    uint2 w0[U], w1[U];
-                    {
-                        uint32_t s = s0, v = v0;
-#pragma unroll
-                        for (int u = 0; u < U; u++) {
-                            const uint32_t p = v & 1, t = (v >> 1) * 2;
-                            const size_t r = ((size_t)s * A.terms + t) * 2 + p;
-                            w0[u] = w1[u] = make_uint2(0, 0);
-                            if (s < S) {
-                                w0[u] = *reinterpret_cast<const uint2*>(col0 + r * A.nN);
-                                if (t + 1 < A.terms) w1[u] = *reinterpret_cast<const uint2*>(col0 + (r + 2) * A.nN);
-                            }
-                            next(s, v);
-                        }
-                    }
-                    uint32_t s = s0, v = v0;
-#pragma unroll
-                    for (int u = 0; u < U; u++, next(s, v)) {
-                        if (s >= S) break;
-                        const uint32_t p = v & 1, t = (v >> 1) * 2, sp = 2 * s + p, kr = t & 15;
-                        uint8_t* base = Bjj + (size_t)(t >> 4) * NT * 256 + ((kr & 7) >> 1) * 8 + (kr >> 3) * 4;
-#pragma unroll
-                        for (int b = 0; b < NB; b++) {
-                            const uint32_t x0 = b < 4 ? w0[u].x : w0[u].y, x1 = b < 4 ? w1[u].x : w1[u].y;
-                            const uint32_t two = __byte_perm(x0, x1, (b & 3) | ((4 + (b & 3)) << 4));
-                            const uint32_t col = b * SP + sp;  // two bytes as fp16 subnormals
-                            *reinterpret_cast<uint32_t*>(base + (col >> 3) * 256 + (col & 7) * 32) =
-                                __byte_perm(two, 0, 0x4140);
-                        }
-                    }
-                }
-            }
+            build_b<S, NB>(A, Bs + buf * bbuf, tau, lane);
             __syncwarp();
             if (lane == 0) mbar_arrive(bfull0 + 8 * buf);
         }
@@ -390,11 +403,19 @@ __global__ void __launch_bounds__(mac_threads(S)) k_cp_mac_tc(const __grid_const
     const uint32_t g8 = lane >> 2, h4 = lane & 3;
     const uint32_t lane_b = SP >= 8 ? 0 : (2 * h4) / SP;  // byte plane offset of this lane's columns
     for (uint32_t lt = 0, tau = blockIdx.x; tau < A.tiles; lt++, tau += gridDim.x) {
+        // building its own B, a consumer visits only the tiles whose single
+        // item is its own
+        if (selfb && lt % MAC_CONSUMERS != warp) continue;
         const uint32_t buf = lt % NBB, gi = tau / A.tiles_per_limb, i = A.limb[gi];
         const uint32_t j0 = (tau % A.tiles_per_limb) * A.CT;
         const uint64_t q = A.q[i], r0 = A.bar[2 * i], r1 = A.bar[2 * i + 1];
-        if (!mbar_wait(bfull0 + 8 * buf, (lt / NBB) & 1, abort)) break;
-        const uint8_t* Bt = Bs + buf * bbuf + lane * 8;
+        if (selfb) {
+            build_b<S, NB>(A, Bs + warp * bbuf, tau, lane);
+            __syncwarp();
+        } else if (!mbar_wait(bfull0 + 8 * buf, (lt / NBB) & 1, abort)) {
+            break;
+        }
+        const uint8_t* Bt = Bs + (selfb ? warp : buf) * bbuf + lane * 8;
         uint32_t it = (warp + MAC_CONSUMERS - (lt * IPT) % MAC_CONSUMERS) % MAC_CONSUMERS;
         bool ok = true;
         for (; it < IPT; it += MAC_CONSUMERS) {
@@ -529,8 +550,8 @@ __global__ void __launch_bounds__(mac_threads(S)) k_cp_mac_tc(const __grid_const
             }
         }
         if (!ok) break;
-        __syncwarp();
-        if (lane == 0) mbar_arrive(bempty0 + 8 * buf);
+        __syncwarp();  // (self-built B: every lane's reads end before the next build)
+        if (!selfb && lane == 0) mbar_arrive(bempty0 + 8 * buf);
     }
 }
 
@@ -578,8 +599,14 @@ int launch_group(blb_ctx* c, MacArgs& a, uint32_t nlimbs)
     const auto smem_for = [&](uint32_t nbb) {
         return nbb * bbuf + (size_t)a.R * item_bytes + 16 * (a.R + MAC_MAX_BBUFS) + 16;
     };
+    // tiles of a single item (batches whose coefficient fills a B buffer):
+    // each consumer builds its tile's B itself, in a buffer of its own, when
+    // those fit two CTAs per SM; the builder warp alone could not keep four
+    // consumers busy
     a.nbb = 2;
-    while (S > 1 && a.nbb < MAC_MAX_BBUFS && (size_t)a.CT * a.NEB * a.nbb < (size_t)W &&
+    a.selfb = S > 1 && a.CT * a.NEB == 1 && W <= (int)MAC_MAX_BBUFS && smem_for(W) <= (113u << 10);
+    if (a.selfb) a.nbb = W;
+    while (!a.selfb && S > 1 && a.nbb < MAC_MAX_BBUFS && (size_t)a.CT * a.NEB * a.nbb < (size_t)W &&
            smem_for(a.nbb + 1) <= (113u << 10))
         a.nbb++;
     const size_t smem = smem_for(a.nbb);

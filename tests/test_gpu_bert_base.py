@@ -77,3 +77,29 @@ def test_narrow_matmul_cp_at_the_step_parameters_matches_the_oracle():
     assert np.array_equal(ctx.ct_export(Y[0]), ref[0])
     got = unpack_cols([ctx.decrypt(keys, Y[0], coeffs=False)[1]], m, k, d_out)
     assert np.abs(got - X @ W).max() <= 1e-4
+
+
+def test_nine_sequence_batch_at_the_step_parameters_equals_single_calls():
+    """matmul_cp over 9 sequences in one batched call (an 8-sequence launch and
+    a 1-sequence launch) gives every sequence the limbs of its own call, at the
+    step's ring, primes, dnum, m, b1 and 96 plaintext terms per output (where a
+    tile of the 8-sequence launch holds one coefficient)."""
+    prm = wl.BERT_CP
+    ctx = make_ctx(prm)
+    m, d, d_out, b1 = 128, 768, 128, 16
+    k = ctx.N // 2 // m
+    level = ctx.nQ - 1
+    keys = ctx.keygen(3, cp_rotations(m, b1, k // b1))
+    _, W = wl.cp_operands(m, d, d_out, seed=78)
+    plan = ctx.cp_plan(m, d, W, d_out, level, b1)
+    seqs = []
+    for s in range(9):
+        X = wl.cp_operands(m, d, d_out, seed=90 + s)[0]
+        seqs.append([ctx.encrypt(keys, ctx.encode(z, level), 100 * s + c)
+                     for c, z in enumerate(pack_cols(X, m, k, d // k))])
+    batched = ctx.matmul_cp_batch(keys, plan, seqs)
+    for s, cts in enumerate(seqs):
+        single = ctx.matmul_cp_plan(keys, plan, cts)
+        assert len(batched[s]) == len(single)
+        for a, b in zip(batched[s], single):
+            assert np.array_equal(ctx.ct_export(a), ctx.ct_export(b)), s
