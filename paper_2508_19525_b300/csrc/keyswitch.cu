@@ -404,7 +404,7 @@ __global__ void k_ksb_digit_rows(uint64_t* __restrict__ ext, const uint64_t* __r
 // NB: the digit count beta as a compile-time loop bound (0 = any), so that
 // every digit's loads are in flight together.
 template <int NB>
-__global__ void k_ksb_inner(uint64_t* __restrict__ acc, const uint64_t* __restrict__ ext,
+__global__ void __launch_bounds__(256, 6) k_ksb_inner(uint64_t* __restrict__ acc, const uint64_t* __restrict__ ext,
                             const DevGroup* __restrict__ groups, const DevProduct* __restrict__ prods, const __grid_constant__ LimbMap emap,
                             uint32_t n, uint32_t E, uint32_t beta, uint32_t nQ, uint32_t np,
                             const uint64_t* __restrict__ qs, const uint64_t* __restrict__ bar, uint32_t logN)
