@@ -84,6 +84,17 @@ __device__ __forceinline__ uint64_t mul_mod(uint64_t a, uint64_t b, uint64_t q, 
     return barrett128(a * b, __umul64hi(a, b), q, r0, r1);
 }
 
+// Programmatic dependent launch (launch_pdl below): a kernel launched this way
+// may be scheduled while the previous kernel of its stream drains, so it must
+// call pdl_begin before touching memory; pdl_begin also lets the next such
+// kernel be scheduled early.  Both instructions are no-ops for kernels
+// launched the ordinary way.
+__device__ __forceinline__ void pdl_begin()
+{
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
 // 128-bit accumulator for lazy sums of products
 struct acc128 {
     uint64_t lo, hi;
@@ -367,6 +378,24 @@ int host_upload(blb_ctx* c, void* dst, const void* src, size_t bytes);
 // results back on the host, create cached tables or plans, or take caller host
 // memory)
 int refuse_capture(blb_ctx* c, const char* what);
+
+// launch with programmatic stream serialization (the kernel calls pdl_begin first)
+template <typename... Params, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(Params...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                       Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
 // caller buffers: host or device; a host buffer is refused while the stream is
 // being captured (a graph cannot keep reading or writing caller host memory)
 int copy_in(blb_ctx* c, void* dst, const void* src, size_t bytes);  // host or device source

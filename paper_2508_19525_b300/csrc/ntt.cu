@@ -28,6 +28,9 @@
 // grow by at most 2q per stage, inverse sums at most double per stage, and
 // both stay below 2^64; the last pass reduces once.
 //
+// Every pass is launched with programmatic stream serialization and starts
+// with pdl_begin, so it can be scheduled while the previous kernel drains.
+//
 // Rows: either rows 0..rows-1 of `data` with prime map.p[row % map.n], or an
 // explicit row list (entry = row index | prime index << 24) so that a batch can
 // transform exactly the rows it needs in one launch.
@@ -227,6 +230,7 @@ __global__ void __launch_bounds__(kThreads, ntt_ctas(RB)) k_ntt(uint64_t* __rest
     using G_ = Geo<LOGN, LP, COLS>;
     constexpr bool LAST = (LP == LOGN) || (INV ? COLS : !COLS);
     __shared__ uint64_t sm[G_::TILE + G_::TILE / 16];
+    pdl_begin();  // launched with programmatic stream serialization
     uint32_t row, pi;
     row_of(rowlist, map, y0 + blockIdx.y, row, pi);
     const uint32_t c0 = blockIdx.x << G_::LOGNSUB;
@@ -282,20 +286,20 @@ int run_split(blb_ctx* ctx, uint64_t* data, uint32_t rows, const LimbMap& map, c
         const dim3 grid(N / TILE, std::min(kMaxGridY, rows - y0));
         if (!inverse) {
             if constexpr (L1 > 0) {
-                k_ntt<false, LOGN, L1, true, RB><<<grid, kThreads, 0, ctx->stream>>>(data, map, rowlist, y0, ctx->d_q, tw,
-                                                                                ctx->d_ninv, ctx->d_bar);
+                BLB_CUDA(launch_pdl(k_ntt<false, LOGN, L1, true, RB>, grid, dim3(kThreads), 0, ctx->stream, data, map, rowlist, y0,
+                           (const uint64_t*)ctx->d_q, tw, (const uint64_t*)ctx->d_ninv, (const uint64_t*)ctx->d_bar));
                 BLB_LAUNCHED();
             }
-            k_ntt<false, LOGN, L2, false, RB><<<grid, kThreads, 0, ctx->stream>>>(data, map, rowlist, y0, ctx->d_q, tw,
-                                                                             ctx->d_ninv, ctx->d_bar);
+            BLB_CUDA(launch_pdl(k_ntt<false, LOGN, L2, false, RB>, grid, dim3(kThreads), 0, ctx->stream, data, map, rowlist, y0,
+                       (const uint64_t*)ctx->d_q, tw, (const uint64_t*)ctx->d_ninv, (const uint64_t*)ctx->d_bar));
             BLB_LAUNCHED();
         } else {
-            k_ntt<true, LOGN, L2, false, RB><<<grid, kThreads, 0, ctx->stream>>>(data, map, rowlist, y0, ctx->d_q, tw,
-                                                                            ctx->d_ninv, ctx->d_bar);
+            BLB_CUDA(launch_pdl(k_ntt<true, LOGN, L2, false, RB>, grid, dim3(kThreads), 0, ctx->stream, data, map, rowlist, y0,
+                       (const uint64_t*)ctx->d_q, tw, (const uint64_t*)ctx->d_ninv, (const uint64_t*)ctx->d_bar));
             BLB_LAUNCHED();
             if constexpr (L1 > 0) {
-                k_ntt<true, LOGN, L1, true, RB><<<grid, kThreads, 0, ctx->stream>>>(data, map, rowlist, y0, ctx->d_q, tw,
-                                                                               ctx->d_ninv, ctx->d_bar);
+                BLB_CUDA(launch_pdl(k_ntt<true, LOGN, L1, true, RB>, grid, dim3(kThreads), 0, ctx->stream, data, map, rowlist, y0,
+                           (const uint64_t*)ctx->d_q, tw, (const uint64_t*)ctx->d_ninv, (const uint64_t*)ctx->d_bar));
                 BLB_LAUNCHED();
             }
         }
