@@ -36,7 +36,7 @@ def test_ntt_parity(logN):
     assert np.array_equal(back, data)
 
 
-@pytest.mark.parametrize("logN", [13, 15, 16, 17])
+@pytest.mark.parametrize("logN", [10, 12, 13, 15, 16, 17])
 def test_ntt_every_pass_split_matches_the_oracle(logN):
     """The three column/row pass splits and both radices of the register
     rounds compute the same butterflies: every pair gives the oracle's forward
