@@ -51,8 +51,8 @@ namespace {
 
 // Consumer warps per CTA (W, plus a plaintext streamer and a B builder): 8 for
 // one sequence, 4 for batches (measured on B300 at the BERT-base products); the
-// ring has one stage per consumer and a B buffer holds at most 16 KB, so two
-// CTAs fit on an SM.
+// ring has one stage per consumer and a B buffer holds 16 KB (more for batches
+// whose tiles the launcher widens, as long as two CTAs still fit on an SM).
 constexpr int mac_consumers(int S) { return S == 1 ? 8 : 4; }
 constexpr int mac_threads(int S) { return 32 * (mac_consumers(S) + 2); }
 constexpr uint32_t MAC_BBUF_BYTES = 16u << 10;
@@ -586,6 +586,13 @@ int launch_group(blb_ctx* c, MacArgs& a, uint32_t nlimbs)
     a.jstride = a.KT * NT * 256 + 16;
     a.CT = 16;
     while (a.CT > 1 && (size_t)a.CT * a.jstride > MAC_BBUF_BYTES) a.CT >>= 1;
+    // batches: widen tiles towards four coefficients (one 32-byte sector of
+    // every baby-step row per load) while two B buffers and the ring still fit
+    // two CTAs per SM
+    while (S > 1 && a.CT < 4 &&
+           2 * (((size_t)2 * a.CT * a.jstride + 127) & ~(size_t)127) + (size_t)mac_consumers(S) * item_bytes +
+                   16 * (mac_consumers(S) + MAC_MAX_BBUFS) + 16 <= (113u << 10))
+        a.CT <<= 1;
     a.tiles_per_limb = c->N / a.CT;
     a.tiles = a.tiles_per_limb * nlimbs;
     // one ring stage per consumer: the fills of a stage all go to the same
