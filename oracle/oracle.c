@@ -601,62 +601,107 @@ static void base_convert(uint32_t N, const uint64_t* const* x, const uint64_t* s
     }
 }
 
+/* Multi-word unsigned integers (little-endian 64-bit words), used only by the
+ * exact CRT of ModDown below: P, a product of at most ORC_MP_WORDS - 1 primes
+ * below 2^64, and sums of nP multiples of P/p_k fit with room to spare. */
+#define ORC_MP_WORDS 8
+typedef struct {
+    uint64_t w[ORC_MP_WORDS];
+} mpint;
+
+static void mp_set(mpint* a, uint64_t v)
+{
+    memset(a, 0, sizeof *a);
+    a->w[0] = v;
+}
+static void mp_mul_u64(mpint* a, uint64_t m)
+{
+    u128 carry = 0;
+    for (int i = 0; i < ORC_MP_WORDS; i++) {
+        u128 t = (u128)a->w[i] * m + carry;
+        a->w[i] = (uint64_t)t;
+        carry = t >> 64;
+    }
+}
+static void mp_add(mpint* a, const mpint* b)
+{
+    uint64_t carry = 0;
+    for (int i = 0; i < ORC_MP_WORDS; i++) {
+        u128 t = (u128)a->w[i] + b->w[i] + carry;
+        a->w[i] = (uint64_t)t;
+        carry = (uint64_t)(t >> 64);
+    }
+}
+static void mp_sub(mpint* a, const mpint* b) /* requires a >= b */
+{
+    uint64_t borrow = 0;
+    for (int i = 0; i < ORC_MP_WORDS; i++) {
+        uint64_t bi = b->w[i] + borrow;
+        uint64_t nb = (bi < borrow) || (a->w[i] < bi);
+        a->w[i] -= bi;
+        borrow = nb;
+    }
+}
+static int mp_cmp(const mpint* a, const mpint* b)
+{
+    for (int i = ORC_MP_WORDS - 1; i >= 0; i--)
+        if (a->w[i] != b->w[i]) return a->w[i] < b->w[i] ? -1 : 1;
+    return 0;
+}
+static uint64_t mp_mod_u64(const mpint* a, uint64_t q)
+{
+    u128 r = 0;
+    for (int i = ORC_MP_WORDS - 1; i >= 0; i--) r = ((r << 64) | a->w[i]) % q;
+    return (uint64_t)r;
+}
+
 /* ModDown: divide a polynomial pair given over Q_l u P (coefficient form,
  * 2 x (n + nP) rows, Q rows first) by P with rounding:
- *   out_i = (x_i - X mod q_i) * P^-1 mod q_i,
- * where X is the representative of x mod P in (-P/2, P/2], obtained by the
- * base conversion of Halevi, Polyakov and Shoup (2019): with
- * y_k = [x_k (P/p_k)^-1]_{p_k}, sum_k y_k (P/p_k) = [x]_P + v P and
- * v = round(sum_k y_k / p_k), so X = sum_k y_k (P/p_k) - v P.  The sum is
- * taken in 128-bit fixed point: y_k / p_k as y_k floor(2^128 / p_k) (below
- * 2^128 since y_k < p_k), added with the carries counted, v = carries + the
- * top fraction bit.  Each term is low by less than y_k 2^-128, so v is the
- * exact rounding unless the fraction is within 2^-65 of 1/2 (it is never
- * exactly 1/2: P is odd).  The result is round(x / P) mod q_i. */
+ *   out_i = (x_i - X) * P^-1 mod q_i = round(x / P) mod q_i,
+ * where X is the representative of x mod P in (-P/2, P/2] (P is odd, so no
+ * value sits exactly between two integers).  X is computed exactly, by the
+ * Chinese remainder theorem in multi-word integers:
+ *   [x]_P = sum_k [x_k (P/p_k)^-1]_{p_k} (P/p_k)  reduced into [0, P),
+ * minus P when twice it exceeds P. */
 void orc_moddown(const orc_params* p, const uint64_t* acc, uint32_t level, uint64_t* out)
 {
     const uint32_t N = p->N, n = level + 1, nP = p->nP, ext = n + nP;
     const uint64_t* pp = p->prime + p->nQ;
-    uint64_t hat_inv[ORC_MAX_PRIMES];
-    u128 recip[ORC_MAX_PRIMES]; /* floor(2^128 / p_k) */
+    if (nP >= ORC_MP_WORDS) abort(); /* P would not fit the multi-word integers */
+    mpint P, hat[ORC_MAX_PRIMES];
+    uint64_t hat_inv[ORC_MAX_PRIMES], P_q[ORC_MAX_PRIMES], Pinv[ORC_MAX_PRIMES];
+    mp_set(&P, 1);
+    for (uint32_t k = 0; k < nP; k++) mp_mul_u64(&P, pp[k]);
     for (uint32_t k = 0; k < nP; k++) {
-        uint64_t h = 1 % pp[k];
+        mp_set(&hat[k], 1);
         for (uint32_t l = 0; l < nP; l++)
-            if (l != k) h = mulmod(h, pp[l] % pp[k], pp[k]);
-        hat_inv[k] = invmod(h, pp[k]);
-        recip[k] = ~(u128)0 / pp[k];
+            if (l != k) mp_mul_u64(&hat[k], pp[l]);
+        hat_inv[k] = invmod(mp_mod_u64(&hat[k], pp[k]), pp[k]);
     }
-    #pragma omp parallel for
     for (uint32_t i = 0; i < n; i++) {
-        const uint64_t q = p->prime[i];
-        uint64_t hat_q[ORC_MAX_PRIMES], P_q = 1 % q;
-        for (uint32_t k = 0; k < nP; k++) {
-            uint64_t h = 1 % q;
-            for (uint32_t l = 0; l < nP; l++)
-                if (l != k) h = mulmod(h, pp[l] % q, q);
-            hat_q[k] = h;
-            P_q = mulmod(P_q, pp[k] % q, q);
-        }
-        const uint64_t Pinv = invmod(P_q, q);
-        for (uint32_t poly = 0; poly < 2; poly++) {
-            const uint64_t* A = acc + (size_t)poly * ext * N;
-            uint64_t* o = out + ((size_t)poly * n + i) * N;
-            for (uint32_t c = 0; c < N; c++) {
-                uint64_t y[ORC_MAX_PRIMES];
-                u128 frac = 0;
-                uint64_t whole = 0;
-                for (uint32_t k = 0; k < nP; k++) {
-                    y[k] = mulmod(A[(size_t)(n + k) * N + c], hat_inv[k], pp[k]);
-                    u128 f = (u128)y[k] * recip[k];
-                    u128 t = frac + f;
-                    whole += t < frac;
-                    frac = t;
-                }
-                uint64_t v = whole + (uint64_t)(frac >> 127);
-                uint64_t X = 0;
-                for (uint32_t k = 0; k < nP; k++) X = addmod(X, mulmod(y[k] % q, hat_q[k], q), q);
-                X = submod(X, mulmod(v % q, P_q, q), q);
-                o[c] = mulmod(submod(A[(size_t)i * N + c], X, q), Pinv, q);
+        P_q[i] = mp_mod_u64(&P, p->prime[i]);
+        Pinv[i] = invmod(P_q[i], p->prime[i]);
+    }
+    for (uint32_t poly = 0; poly < 2; poly++) {
+        const uint64_t* A = acc + (size_t)poly * ext * N;
+        #pragma omp parallel for
+        for (uint32_t c = 0; c < N; c++) {
+            mpint X, t;
+            mp_set(&X, 0);
+            for (uint32_t k = 0; k < nP; k++) {
+                t = hat[k];
+                mp_mul_u64(&t, mulmod(A[(size_t)(n + k) * N + c], hat_inv[k], pp[k]));
+                mp_add(&X, &t);
+            }
+            while (mp_cmp(&X, &P) >= 0) mp_sub(&X, &P);
+            t = X;
+            mp_add(&t, &X);
+            const int negative = mp_cmp(&t, &P) > 0; /* X > P/2: the representative is X - P */
+            for (uint32_t i = 0; i < n; i++) {
+                const uint64_t q = p->prime[i];
+                uint64_t Xq = mp_mod_u64(&X, q);
+                if (negative) Xq = submod(Xq, P_q[i], q);
+                out[((size_t)poly * n + i) * N + c] = mulmod(submod(A[(size_t)i * N + c], Xq, q), Pinv[i], q);
             }
         }
     }
