@@ -99,6 +99,21 @@ int blb_ctx_primes(const blb_ctx* ctx, uint64_t* out /* host, nQ + nP words */);
 int blb_ctx_sync(blb_ctx* ctx);
 /* Device memory currently held by this context and its objects (bytes). */
 uint64_t blb_ctx_bytes_in_use(const blb_ctx* ctx);
+/* Bounded device waits (failure detection; no counterpart in the paper, whose
+ * protocols assume kernels that finish).  The plaintext-product pipeline of
+ * matmul_cp (copy ring, fragment builder, tensor-core consumers) waits on
+ * shared-memory barriers; each wait gives up after limit_ns nanoseconds
+ * (0 = the default, 2 s), ends its thread block early, and makes the next
+ * blb_ctx_sync return BLB_ERR_TIMEOUT (and clear the condition).  The outputs
+ * of the calls since the previous sync are then invalid; the context stays
+ * usable.  Copies already in flight are always waited for (up to 2 s) before a
+ * block exits, whatever the limit.  Applies to calls made after it. */
+int blb_ctx_set_wait_limit(blb_ctx* ctx, uint64_t limit_ns);
+/* Test hook for that error path: with withhold != 0 the pipeline's copy
+ * stage issues no copies, so the consumers' waits run out (after the limit
+ * above) instead of completing.  Products computed meanwhile are invalid.
+ * 0 restores normal operation. */
+int blb_ctx_test_withhold_copies(blb_ctx* ctx, int withhold);
 
 /* ---- keys (Sec. 2.4: rotations and products need switching keys) -----------
  * Secret key s (ternary) and switching keys drawn from Philox4x32-10 with key
@@ -190,9 +205,10 @@ int blb_keyswitch_coeffs(blb_ctx* ctx, const blb_keys* keys, int32_t rot, const 
  * (3(l+1) + (l+1) + beta (l+1+nP) + 2 (l+1+nP) + 2 (l+1)) N words, beta =
  * ceil((l+1)/alpha), and returns BLB_ERR_ARG when that exceeds 32 MiB (for
  * example N = 2^16 with 12 primes); N = 2^15 with 8 primes and 3 special primes
- * fits at every level.  The first call on a device looks up the array's device
- * address with that device current, so make that first call before any stream
- * capture.  All calls on a GPU share the array and it keeps the previous
+ * fits at every level.  blb_ctx_create, with the context's device current,
+ * looks up the array's device address (loading the array with the library's
+ * module, under lazy module loading too) and loads this call's kernels, so the
+ * call itself neither allocates nor loads anything.  All calls on a GPU share the array and it keeps the previous
  * call's contents (nothing in it needs to start at zero): calls that can
  * overlap on the GPU -- other streams, other contexts, other threads -- race
  * and must be serialized by the caller.  d and out may be host or device

@@ -1291,12 +1291,6 @@ int orc_matmul_cc(const orc_params* p, const orc_galois_set* gk, const uint64_t*
     uint64_t* Bp = calloc((size_t)n_c * w1, sizeof(uint64_t));
     uint64_t* W = calloc((size_t)L * w3, sizeof(uint64_t));
     int rc = 0;
-#define ROT(dst, src, lv, r)                                                  \
-    do {                                                                      \
-        const uint64_t* key_ = find_galois(p, gk, (int32_t)(r));              \
-        if (!key_) { rc = -2; goto done; }                                    \
-        orc_rotate(p, (src), (lv), (int32_t)(r), key_, (dst));                \
-    } while (0)
 
     /* step 1: baby steps of B_c hoisted (one ModUp), giant steps summed with one ModDown */
     {
@@ -1357,8 +1351,6 @@ int orc_matmul_cc(const orc_params* p, const orc_galois_set* gk, const uint64_t*
         uint64_t* rot = malloc(sizeof(uint64_t) * w1 * 2 * (b1s2 > G2 ? b1s2 : G2));
         uint64_t* Ag = malloc(sizeof(uint64_t) * w1 * G2);
         uint64_t* A1 = malloc(sizeof(uint64_t) * w1);
-        uint64_t* vacc = malloc(sizeof(uint64_t) * w1);
-        uint64_t* T3 = malloc(sizeof(uint64_t) * w1_3);
         int32_t rs[2 * ORC_MAX_ROT];
         const uint64_t* ks[2 * ORC_MAX_ROT];
         if (2 * b1s2 > 2 * ORC_MAX_ROT || G2 > 2 * ORC_MAX_ROT) rc = -1;
@@ -1385,52 +1377,80 @@ int orc_matmul_cc(const orc_params* p, const orc_galois_set* gk, const uint64_t*
             }
             if (rc) break;
             orc_rotate_hoisted(p, A1, l1, G2 - 1, rs, ks, Ag + w1);
-            for (uint32_t g = 0; g < G2 && !rc; g++) {
-                for (uint32_t b = 0; b < b1s2 && !rc; b++) {
-                    const uint32_t t = g * b1s2 + b;
-                    memset(vacc, 0, sizeof(uint64_t) * w1);
+            /* the L diagonals t = g b1s2 + b are independent: each adds into its own U_t */
+            #pragma omp parallel
+            {
+                double* zt = malloc(sizeof(double) * s);
+                uint64_t* ptt = malloc(sizeof(uint64_t) * (l0 + 1) * N);
+                uint64_t* prodt = malloc(sizeof(uint64_t) * w0);
+                uint64_t* vt = malloc(sizeof(uint64_t) * w1);
+                uint64_t* T3t = malloc(sizeof(uint64_t) * w1_3);
+                #pragma omp for schedule(dynamic)
+                for (uint32_t t = 0; t < L; t++) {
+                    const uint32_t g = t / b1s2, b = t % b1s2;
+                    int trc = 0, used = 0;
+                    memset(vt, 0, sizeof(uint64_t) * w1);
                     int64_t args[3] = {L, t, 0};
-                    int used = 0;
-                    if (build_mask(z, s, (int64_t)g * b1s2, pred_m2, args)) {
-                        rc = mac_mask(p, vacc, blo + (size_t)b * w1, l1, z, pt, prod);
+                    if (build_mask(zt, s, (int64_t)g * b1s2, pred_m2, args)) {
+                        trc = mac_mask(p, vt, blo + (size_t)b * w1, l1, zt, ptt, prodt);
                         used = 1;
                     }
                     args[2] = 1;
-                    if (!rc && build_mask(z, s, (int64_t)g * b1s2, pred_m2, args)) {
-                        rc = mac_mask(p, vacc, bhi + (size_t)b * w1, l1, z, pt, prod);
+                    if (!trc && build_mask(zt, s, (int64_t)g * b1s2, pred_m2, args)) {
+                        trc = mac_mask(p, vt, bhi + (size_t)b * w1, l1, zt, ptt, prodt);
                         used = 1;
                     }
-                    if (rc || !used) continue;
-                    orc_tensor(p, Ag + (size_t)g * w1, vacc, l1, T3);
+                    if (trc) {
+                        #pragma omp atomic write
+                        rc = trc;
+                    }
+                    if (trc || !used) continue;
+                    orc_tensor(p, Ag + (size_t)g * w1, vt, l1, T3t);
                     uint64_t* Ut = U + (size_t)t * w1_3;
                     for (uint32_t poly = 0; poly < 3; poly++)
-                        orc_add(p, Ut + (size_t)poly * (l1 + 1) * N, T3 + (size_t)poly * (l1 + 1) * N, l1 + 1,
+                        orc_add(p, Ut + (size_t)poly * (l1 + 1) * N, T3t + (size_t)poly * (l1 + 1) * N, l1 + 1,
                                 Ut + (size_t)poly * (l1 + 1) * N);
                 }
+                free(zt); free(ptt); free(prodt); free(vt); free(T3t);
             }
         }
-        for (uint32_t t = 0; t < L && !rc; t++) {
-            uint64_t* U2 = malloc(sizeof(uint64_t) * w2_3);
-            uint64_t* R2 = malloc(sizeof(uint64_t) * w2);
-            orc_rescale(p, U + (size_t)t * w1_3, l1, 3, U2);
-            orc_relinearize(p, U2, l2, relin_ksk, R2);
-            orc_rescale(p, R2, l2, 2, W + (size_t)t * w3);
-            free(U2);
-            free(R2);
+        if (!rc) {
+            #pragma omp parallel for schedule(dynamic)
+            for (uint32_t t = 0; t < L; t++) {
+                uint64_t* U2 = malloc(sizeof(uint64_t) * w2_3);
+                uint64_t* R2 = malloc(sizeof(uint64_t) * w2);
+                orc_rescale(p, U + (size_t)t * w1_3, l1, 3, U2);
+                orc_relinearize(p, U2, l2, relin_ksk, R2);
+                orc_rescale(p, R2, l2, 2, W + (size_t)t * w3);
+                free(U2);
+                free(R2);
+            }
         }
-        free(U); free(blo); free(bhi); free(rot); free(Ag); free(A1); free(vacc); free(T3);
+        free(U); free(blo); free(bhi); free(rot); free(Ag); free(A1);
     }
     if (rc) goto done;
 
     /* step 3 */
     {
         uint64_t* Cacc = calloc((size_t)nout * w3, sizeof(uint64_t));
-        uint64_t* Rt = malloc(sizeof(uint64_t) * w3);
+        uint64_t* Rall = malloc(sizeof(uint64_t) * w3 * L);
+        /* the L rotations first (independent), then the masked sums */
         for (uint32_t t = 0; t < L && !rc; t++) {
             const uint32_t g = t / b1s2;
             const int64_t r = (((int64_t)g * b1s2 - (int64_t)(t % Kc) * Hg * L) % (int64_t)s + s) % s;
+            if (r != 0 && !find_galois(p, gk, (int32_t)r)) rc = -2;
+        }
+        if (rc) { free(Cacc); free(Rall); goto done; }
+        #pragma omp parallel for schedule(dynamic)
+        for (uint32_t t = 0; t < L; t++) {
+            const uint32_t g = t / b1s2;
+            const int64_t r = (((int64_t)g * b1s2 - (int64_t)(t % Kc) * Hg * L) % (int64_t)s + s) % s;
+            uint64_t* Rt = Rall + (size_t)t * w3;
             if (r == 0) memcpy(Rt, W + (size_t)t * w3, sizeof(uint64_t) * w3);
-            else ROT(Rt, W + (size_t)t * w3, l3, (int32_t)r);
+            else orc_rotate(p, W + (size_t)t * w3, l3, (int32_t)r, find_galois(p, gk, (int32_t)r), Rt);
+        }
+        for (uint32_t t = 0; t < L && !rc; t++) {
+            const uint64_t* Rt = Rall + (size_t)t * w3;
             for (uint32_t j = 0; j < nout && !rc; j++) {
                 int64_t args[5] = {L, Hg, Kc, t, j};
                 if (build_mask(z, s, 0, pred_m3, args))
@@ -1439,10 +1459,9 @@ int orc_matmul_cc(const orc_params* p, const orc_galois_set* gk, const uint64_t*
         }
         for (uint32_t j = 0; j < nout && !rc; j++)
             orc_rescale(p, Cacc + (size_t)j * w3, l3, 2, C + (size_t)j * 2 * l3 * N);
-        free(Cacc); free(Rt);
+        free(Cacc); free(Rall);
     }
 done:
-#undef ROT
     free(z); free(pt); free(prod); free(tmp); free(Bp); free(W);
     return rc;
 }

@@ -85,6 +85,8 @@ SIGNATURES = {
     "blb_relinearize": (ctypes.c_int, [_vp, _vp, _vp, _pp]),
     "blb_keyswitch_coeffs": (ctypes.c_int, [_vp, _vp, _i32, _vp, _u32, _vp]),
     "blb_keyswitch_noalloc": (ctypes.c_int, [_vp, _vp, _i32, _vp, _u32, _vp]),
+    "blb_ctx_set_wait_limit": (ctypes.c_int, [_vp, _u64]),
+    "blb_ctx_test_withhold_copies": (ctypes.c_int, [_vp, ctypes.c_int]),
     "blb_cp_plan_create": (ctypes.c_int, [_vp, _u32, _u32, _vp, _u32, _u32, ctypes.POINTER(_Sched), _pp]),
     "blb_cp_plan_create_diag": (ctypes.c_int, [_vp, _u32, _u32, _vp, _u32, _vp, _u32, _u32, ctypes.POINTER(_Sched), _pp]),
     "blb_cp_plan_free": (None, [_vp]),
@@ -308,6 +310,14 @@ class Context:
 
     def bytes_in_use(self):
         return int(lib().blb_ctx_bytes_in_use(self.h))
+
+    def set_wait_limit(self, limit_ns):
+        """Limit of the bounded device waits in nanoseconds (0 = 2 s)."""
+        _check(lib().blb_ctx_set_wait_limit(self.h, _u64(limit_ns)))
+
+    def test_withhold_copies(self, withhold):
+        """Test hook: the matmul_cp copy stage issues nothing, so waits expire."""
+        _check(lib().blb_ctx_test_withhold_copies(self.h, int(withhold)))
 
     # keys
     def keygen(self, seed, rot_steps=(), relin=False):

@@ -175,6 +175,9 @@ struct blb_ctx {
     uint32_t* d_kperm = nullptr;      // [N/2]: k_j = (5^j mod 2N - 1)/4
     int* d_flag = nullptr;            // device status word (encoding overflow)
     uint32_t* d_status = nullptr;     // set by a kernel whose bounded wait expired
+    uint64_t wait_ns = 0;             // limit of the bounded device waits (0: the 2 s default)
+    uint32_t mac_withhold = 0;        // test hook: the plaintext streamer issues nothing (waits run out)
+    uint64_t* noalloc_scratch = nullptr;  // device address of the allocation-free key switch's array
     // conversions between CKKS and shares (built on first use): fixed-point
     // roots zeta^k (k < N), the inverse slot permutation, and twist tables
     // round(2^30 c zeta^t) (t < N/2) for the last multipliers c used
@@ -430,6 +433,10 @@ struct KsItem {
     uint64_t g;
 };
 int keyswitch_batch(blb_ctx* ctx, uint32_t level, const KsItem* items, uint32_t count, int accumulate);
+// resolves, with the context's device current, the device address of the
+// allocation-free key switch's array and loads that entry point's kernels
+// (called by blb_ctx_create, where allocating is allowed)
+int keyswitch_noalloc_prepare(blb_ctx* ctx);
 
 // General key-switching pass (keyswitch.cu): sources are ModUp'd once (after
 // the automorphism g), products apply g to the extended digits and multiply by

@@ -430,6 +430,7 @@ extern "C" int blb_ctx_create(const blb_params* params, void* stream, blb_ctx** 
         uint32_t uzero = 0;
         if ((rc = upload(c, &c->d_status, &uzero, 1))) return fail(rc);
     }
+    if ((rc = keyswitch_noalloc_prepare(c))) return fail(rc);
 
     // discrete Gaussian table: floor(2^64 P(|e| <= k)), sigma 3.2, |e| <= 19
     {
@@ -596,3 +597,17 @@ extern "C" int blb_ctx_sync(blb_ctx* c)
 }
 
 extern "C" uint64_t blb_ctx_bytes_in_use(const blb_ctx* c) { return c ? c->bytes_in_use : 0; }
+
+extern "C" int blb_ctx_set_wait_limit(blb_ctx* c, uint64_t limit_ns)
+{
+    if (!c) return blb_fail(BLB_ERR_ARG, "null context");
+    c->wait_ns = limit_ns;
+    return BLB_OK;
+}
+
+extern "C" int blb_ctx_test_withhold_copies(blb_ctx* c, int withhold)
+{
+    if (!c) return blb_fail(BLB_ERR_ARG, "null context");
+    c->mac_withhold = withhold ? 1u : 0u;
+    return BLB_OK;
+}

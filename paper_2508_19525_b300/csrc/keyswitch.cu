@@ -15,7 +15,6 @@
 // coefficients, so any correct schedule of it yields the same limbs.
 #include <algorithm>
 #include <cstring>
-#include <mutex>
 #include <string>
 
 #include "common.cuh"
@@ -232,27 +231,32 @@ int keyswitch(blb_ctx* ctx, const uint64_t* d_ntt, uint32_t level, const uint64_
 static constexpr size_t kNoAllocScratchWords = (size_t)4 << 20;  // 32 MiB of uint64 words
 static __device__ __align__(256) uint64_t blb_noalloc_scratch[kNoAllocScratchWords];
 
-static std::mutex g_noalloc_mu;
-static uint64_t* g_noalloc_ptr[64];  // device address of the array, per device ordinal
-
-// The array's host-side name is not a device address; the first call on a
-// device asks the runtime for the real one (with that device current) and
-// caches it.
-static int noalloc_scratch(uint64_t** out)
+// The array's host-side name is not a device address.  Context creation asks
+// the runtime for the real one, with the context's device current, and keeps
+// it in the context; that lookup is also what loads this file's module (and
+// with it the array) under lazy module loading, so the load happens there and
+// not inside an allocation-free call.  The kernels of the entry point are
+// loaded at the same time, for the same reason.
+int keyswitch_noalloc_prepare(blb_ctx* c)
 {
-    int dev = -1;
-    BLB_CUDA(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= 64) return blb_fail(BLB_ERR_ARG, "device ordinal beyond the scratch table (64)");
-    std::lock_guard<std::mutex> lk(g_noalloc_mu);
-    if (!g_noalloc_ptr[dev]) {
-        void* p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, blb_noalloc_scratch);
-        if (e != cudaSuccess || !p)
-            return blb_fail(BLB_ERR_CUDA, std::string("cudaGetSymbolAddress of the key-switch scratch failed: ") +
-                                              cudaGetErrorString(e));
-        g_noalloc_ptr[dev] = (uint64_t*)p;
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, blb_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+        cudaGetLastError();
+        return blb_fail(BLB_ERR_CUDA, std::string("cudaGetSymbolAddress of the key-switch scratch failed: ") +
+                                          cudaGetErrorString(e));
     }
-    *out = g_noalloc_ptr[dev];
+    cudaFuncAttributes fa;
+    const void* kernels[] = {(const void*)k_conv,
+                             (const void*)k_ks_inner,
+                             (const void*)k_moddown_finish,
+                             (const void*)k_moddown_conv<0>,
+                             (const void*)k_moddown_conv<1>,
+                             (const void*)k_moddown_conv<2>,
+                             (const void*)k_moddown_conv<3>,
+                             (const void*)k_moddown_conv<4>};
+    for (const void* k : kernels) BLB_CUDA(cudaFuncGetAttributes(&fa, k));
+    c->noalloc_scratch = (uint64_t*)p;
     return BLB_OK;
 }
 
@@ -272,8 +276,8 @@ extern "C" int blb_keyswitch_noalloc(blb_ctx* c, const blb_keys* K, int32_t rot,
         return blb_fail(BLB_ERR_ARG, "blb_keyswitch_noalloc: this level and ring size need " +
                                          std::to_string(need * 8 >> 20) + " MiB of scratch; the fixed area holds " +
                                          std::to_string(kNoAllocScratchWords * 8 >> 20) + " MiB");
-    uint64_t* S = nullptr;
-    BLB_TRY(noalloc_scratch(&S));
+    uint64_t* S = c->noalloc_scratch;
+    if (!S) return blb_fail(BLB_ERR_CUDA, "the context holds no address of the key-switch scratch array");
     uint64_t* dd = S;
     uint64_t* o = S + (size_t)n * N;
     uint64_t* body = S + (size_t)3 * n * N;

@@ -47,6 +47,8 @@
 
 #include <cuda_fp16.h>
 
+#include <atomic>
+
 namespace {
 
 // Consumer warps per CTA (W, plus a plaintext streamer and a B builder): 8 for
@@ -58,7 +60,7 @@ constexpr int mac_threads(int S) { return 32 * (mac_consumers(S) + 2); }
 constexpr uint32_t MAC_BBUF_BYTES = 16u << 10;
 constexpr int MAC_MAX_GROUP = 64;  // limbs per launch
 constexpr uint32_t MAC_MAX_BBUFS = 4;
-constexpr uint64_t MAC_WAIT_NS = 2000000000ull;  // bounded waits: 2 s
+constexpr uint64_t MAC_WAIT_NS = 2000000000ull;  // bounded waits: 2 s by default
 
 struct MacArgs {
     uint64_t* T;
@@ -72,6 +74,8 @@ struct MacArgs {
     uint32_t tiles_per_limb, tiles;  // coefficient tiles of CT per limb, over all limbs of the launch
     uint32_t nbb;                    // B fragment buffers (2 .. MAC_MAX_BBUFS)
     uint32_t selfb;                  // batches of one item per tile: each consumer builds its own B
+    uint32_t withhold;               // test hook: the streamer issues no copy, so the consumers' waits run out
+    uint64_t wait_ns;                // limit of the pipeline's waits (the final drain always allows MAC_WAIT_NS)
     uint32_t limb[MAC_MAX_GROUP];
     uint64_t off[MAC_MAX_GROUP];
 };
@@ -104,9 +108,9 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar)
 }
 
 // Wait for the phase of the given parity to complete.  Returns false after
-// MAC_WAIT_NS, or as soon as another thread of the CTA has given up (abort
-// word in shared memory), so that one expired wait ends the whole CTA quickly.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile uint32_t* abort)
+// limit_ns, or as soon as another thread of the CTA has given up (abort word
+// in shared memory), so that one expired wait ends the whole CTA quickly.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile uint32_t* abort, uint64_t limit_ns)
 {
     uint64_t t0 = 0;
     for (uint32_t it = 0;; it++) {
@@ -120,7 +124,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatil
         if (it == 0) {
             t0 = globaltimer();
         } else if ((it & 63) == 0) {
-            if (*abort || globaltimer() - t0 > MAC_WAIT_NS) {
+            if (*abort || globaltimer() - t0 > limit_ns) {
                 *abort = 1;
                 return false;
             }
@@ -366,23 +370,26 @@ __global__ void __launch_bounds__(mac_threads(S)) k_cp_mac_tc(const __grid_const
         // NBB - 1 tiles ahead of the consumers
         for (uint32_t lt = 0, tau = blockIdx.x; tau < A.tiles; lt++, tau += gridDim.x) {
             const uint32_t buf = lt % NBB;
-            if (lt >= NBB && !mbar_wait(bempty0 + 8 * buf, ((lt / NBB) - 1) & 1, abort)) break;
+            // the lanes leave together (one lane's wait may expire as another's succeeds)
+            if (lt >= NBB && !__all_sync(0xffffffffu, mbar_wait(bempty0 + 8 * buf, ((lt / NBB) - 1) & 1, abort, A.wait_ns)))
+                break;
             build_b<S, NB>(A, Bs + buf * bbuf, tau, lane);
             __syncwarp();
             if (lane == 0) mbar_arrive(bfull0 + 8 * buf);
         }
+        if (lane == 0 && *abort) atomicExch(A.status, 1u);
         return;
     }
     if (warp == MAC_CONSUMERS) {
         // ---- streamer (lane 0): each tile's contiguous plaintext range into the ring
         if (lane == 0) {
             uint32_t issued = 0;
-            for (uint32_t lt = 0, tau = blockIdx.x; tau < A.tiles && !*abort; lt++, tau += gridDim.x) {
+            for (uint32_t lt = 0, tau = blockIdx.x; !A.withhold && tau < A.tiles && !*abort; lt++, tau += gridDim.x) {
                 const uint32_t gi = tau / A.tiles_per_limb, j0 = (tau % A.tiles_per_limb) * A.CT;
                 const uint8_t* src = A.ptb + A.off[gi] + (size_t)j0 * A.NEB * item_bytes;
                 for (uint32_t it = 0; it < IPT; it++) {
                     const uint32_t kg = lt * IPT + it, st = kg % R;
-                    if (kg >= R && !mbar_wait(empty0 + 8 * st, ((kg / R) - 1) & 1, abort)) break;
+                    if (kg >= R && !mbar_wait(empty0 + 8 * st, ((kg / R) - 1) & 1, abort, A.wait_ns)) break;
                     mbar_expect_tx(full0 + 8 * st, item_bytes);
                     bulk_g2s(ring0 + st * item_bytes, src + (size_t)it * item_bytes, item_bytes, full0 + 8 * st);
                     issued = kg + 1;
@@ -392,7 +399,7 @@ __global__ void __launch_bounds__(mac_threads(S)) k_cp_mac_tc(const __grid_const
             // even after an abort (the copies land whatever the consumers do)
             for (uint32_t kg = issued > R ? issued - R : 0; kg < issued; kg++) {
                 uint32_t dummy = 0;
-                mbar_wait(full0 + 8 * (kg % R), (kg / R) & 1, &dummy);
+                mbar_wait(full0 + 8 * (kg % R), (kg / R) & 1, &dummy, MAC_WAIT_NS);
             }
             if (*abort) atomicExch(A.status, 1u);
         }
@@ -412,7 +419,7 @@ __global__ void __launch_bounds__(mac_threads(S)) k_cp_mac_tc(const __grid_const
         if (selfb) {
             build_b<S, NB>(A, Bs + warp * bbuf, tau, lane);
             __syncwarp();
-        } else if (!mbar_wait(bfull0 + 8 * buf, (lt / NBB) & 1, abort)) {
+        } else if (!__all_sync(0xffffffffu, mbar_wait(bfull0 + 8 * buf, (lt / NBB) & 1, abort, A.wait_ns))) {
             break;
         }
         const uint8_t* Bt = Bs + (selfb ? warp : buf) * bbuf + lane * 8;
@@ -420,7 +427,7 @@ __global__ void __launch_bounds__(mac_threads(S)) k_cp_mac_tc(const __grid_const
         bool ok = true;
         for (; it < IPT; it += MAC_CONSUMERS) {
             const uint32_t kg = lt * IPT + it, st = kg % R;
-            if (!mbar_wait(full0 + 8 * st, (kg / R) & 1, abort)) {
+            if (!__all_sync(0xffffffffu, mbar_wait(full0 + 8 * st, (kg / R) & 1, abort, A.wait_ns))) {
                 ok = false;
                 break;
             }
@@ -553,6 +560,7 @@ __global__ void __launch_bounds__(mac_threads(S)) k_cp_mac_tc(const __grid_const
         __syncwarp();  // (self-built B: every lane's reads end before the next build)
         if (!selfb && lane == 0) mbar_arrive(bempty0 + 8 * buf);
     }
+    if (lane == 0 && *abort) atomicExch(A.status, 1u);
 }
 
 // one thread per 8-byte fragment word of one output block: ((j KT + kt) nb + a) 32 + lane
@@ -619,15 +627,16 @@ int launch_group(blb_ctx* c, MacArgs& a, uint32_t nlimbs)
     const size_t smem = smem_for(a.nbb);
     if (smem > (227u << 10)) return blb_fail(BLB_ERR_ARG, "plaintext tile too large for shared memory");
     if (item_bytes >= (1u << 20)) return blb_fail(BLB_ERR_ARG, "too many plaintext terms per output");
-    static bool attr = false;
-    static int per_sm = 0;
-    if (!attr) {
+    // the shared-memory opt-in is a property of each device
+    static std::atomic<bool> attr[64];
+    int per_sm = 0, dev = 0, sms = 0;
+    BLB_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return blb_fail(BLB_ERR_ARG, "device ordinal beyond 64");
+    if (!attr[dev].load()) {
         BLB_CUDA(cudaFuncSetAttribute(k_cp_mac_tc<S, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 << 10));
-        attr = true;
+        attr[dev].store(true);
     }
     BLB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cp_mac_tc<S, NB>, mac_threads(S), smem));
-    int dev = 0, sms = 0;
-    BLB_CUDA(cudaGetDevice(&dev));
     BLB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     const uint32_t grid = std::min<uint32_t>(a.tiles, (uint32_t)std::max(1, per_sm) * sms);
     k_cp_mac_tc<S, NB><<<grid, mac_threads(S), smem, c->stream>>>(a);
@@ -704,6 +713,8 @@ int launch_cp_mac(blb_ctx* c, const blb_cp_plan* P, const uint64_t* baby, uint64
     a.q = c->d_q;
     a.bar = c->d_bar;
     a.status = c->d_status;
+    a.wait_ns = c->wait_ns ? c->wait_ns : MAC_WAIT_NS;
+    a.withhold = c->mac_withhold;
     a.nN = (uint64_t)n * N;
     a.seq_words = terms * 2 * a.nN;
     a.N = N;

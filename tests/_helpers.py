@@ -43,3 +43,18 @@ def cp_rotations(m, b1, G):
 
 def oracle_galois(o, sk, seed, rots):
     return {o.galois_elt(r): o.keygen_galois(seed, sk, o.galois_elt(r)) for r in rots}
+
+
+def assert_limbs_consistent(coeffs, primes, bound_bits=56):
+    """The limbs of a decrypted polynomial (level+1, N; coefficient form) must
+    be the residues of one small integer: limb 0 centered mod q_0, reduced mod
+    q_i, equals limb i for every i (a ciphertext with a wrong residue in any
+    limb decrypts to an unrelated value there).  The message + noise stays
+    below 2^bound_bits in magnitude."""
+    q0 = int(primes[0])
+    c0 = coeffs[0].astype(np.int64)
+    v = np.where(coeffs[0] > q0 // 2, c0 - q0, c0)
+    assert np.abs(v).max() < (1 << bound_bits)
+    for i in range(1, coeffs.shape[0]):
+        qi = np.int64(primes[i])
+        assert np.array_equal(np.mod(v, qi).astype(np.uint64), coeffs[i]), f"limb {i} disagrees with limb 0"

@@ -11,7 +11,8 @@ import pytest
 
 from paper_2508_19525_b300 import workloads as wl
 
-from _helpers import cp_rotations, make_ctx, make_oracle, oracle_galois, pack_cols, unpack_cols
+from _helpers import (assert_limbs_consistent, cp_rotations, make_ctx, make_oracle, oracle_galois, pack_cols,
+                      unpack_cols)
 
 pytestmark = pytest.mark.gpu
 
@@ -37,6 +38,11 @@ def test_step_outputs_match_fp64(run):
                                  bench.D_O)
     assert np.abs(got_qkv - w.ref_qkv).max() <= 1e-4
     assert np.abs(got_o - w.ref_o).max() <= 1e-4
+    # the slots above decode limb 0 only: every other limb of every output must
+    # hold the residues of the same decrypted integers
+    primes = ctx.primes
+    for y in Y + O:
+        assert_limbs_consistent(ctx.decrypt(keys, y, slots=False)[0], primes)
 
 
 def test_step_inputs_masks_and_shares_match_the_oracle(run):

@@ -9,7 +9,7 @@ import cc_schedule as cs
 import oracle
 from paper_2508_19525_b300 import workloads as wl
 
-from _helpers import make_ctx, make_oracle
+from _helpers import assert_limbs_consistent, make_ctx, make_oracle
 
 pytestmark = pytest.mark.gpu
 SEED = 0xCC
@@ -30,8 +30,12 @@ def gpu_cc(ctx, keys, plan, A, B, L, Hg, level, scale):
     Ac = [ctx.encrypt(keys, ctx.encode(z, level, scale), c) for c, z in enumerate(Az)]
     Bc = [ctx.encrypt(keys, ctx.encode(z, level, scale), 100 + c) for c, z in enumerate(Bz)]
     C = ctx.matmul_cc_plan(keys, plan, Ac, Bc)
-    zs = np.stack([ctx.decrypt(keys, c, coeffs=False)[1] for c in C])
-    return C, cs.unpack_diagonals(zs, L, Hg, Kc), Az, Bz
+    zs = []
+    for c in C:
+        coeffs, z = ctx.decrypt(keys, c)
+        assert_limbs_consistent(coeffs, ctx.primes)  # every limb, not only the decoded q_0
+        zs.append(z)
+    return C, cs.unpack_diagonals(np.stack(zs), L, Hg, Kc), Az, Bz
 
 
 @pytest.mark.parametrize("kind,R,b1s1,b1s2,L,Hg,chunks", [

@@ -1,0 +1,55 @@
+"""Failure detection of the bounded device waits (no GPU fault involved).
+
+The plaintext-product pipeline of matmul_cp waits on shared-memory barriers
+that its copy stage and fragment builder complete.  With the copy stage told to
+withhold its copies (a condition that nothing else completes) and a 1 ms wait
+limit, every consumer's wait runs out: the kernel ends early, the copies it had
+in flight (none here) are drained, and blb_ctx_sync reports BLB_ERR_TIMEOUT
+once.  The context stays usable: the same product with normal settings then
+equals the oracle limb for limb."""
+import time
+
+import numpy as np
+import pytest
+
+from paper_2508_19525_b300 import workloads as wl
+
+from _helpers import cp_rotations, make_ctx, make_oracle, oracle_galois, pack_cols
+
+pytestmark = pytest.mark.gpu
+SEED = 0x7173
+
+
+def test_expired_wait_reports_timeout_and_the_context_recovers():
+    from paper_2508_19525_b300 import blb
+    prm, m, d, d_out, b1 = wl.SMALL, 64, 80, 40, 4
+    o, ctx = make_oracle(prm), make_ctx(prm)
+    k = o.N // 2 // m
+    level = o.nQ - 1
+    rots = cp_rotations(m, b1, k // b1)
+    keys = ctx.keygen(SEED, rots)
+    X, W = wl.cp_operands(m, d, d_out, seed=3)
+    zs = pack_cols(X, m, k, (d + k - 1) // k)
+    cts = [ctx.encrypt(keys, ctx.encode(z, level), nonce=c) for c, z in enumerate(zs)]
+    plan = ctx.cp_plan(m, d, W, d_out, level, b1)
+    ctx.sync()
+
+    ctx.set_wait_limit(1_000_000)  # 1 ms
+    ctx.test_withhold_copies(True)
+    t0 = time.time()
+    ctx.matmul_cp_plan(keys, plan, cts)
+    with pytest.raises(blb.BlbError) as e:
+        ctx.sync()
+    assert e.value.code == blb.ERR_TIMEOUT
+    assert time.time() - t0 < 30
+    ctx.sync()  # reported once, then cleared
+
+    ctx.test_withhold_copies(False)
+    ctx.set_wait_limit(0)  # back to the 2 s default
+    Y = ctx.matmul_cp_plan(keys, plan, cts)
+    ctx.sync()
+    sk = o.keygen_secret(SEED)
+    ref_in = np.stack([o.encrypt(sk, o.encode(z, level, prm.scale), SEED, c) for c, z in enumerate(zs)])
+    ref = o.matmul_cp(ref_in, m, d, W, d_out, b1, oracle_galois(o, sk, SEED, rots))
+    for e_, y in enumerate(Y):
+        assert np.array_equal(ctx.ct_export(y), ref[e_]), e_

@@ -307,3 +307,17 @@ def test_moddown_is_rounded_division_by_P(level):
             r = (2 * x + P) // (2 * P)  # round(x / P), x in [0, QP)
             for i in range(n):
                 assert int(out[poly, i, c]) == r % o.primes[i], (poly, c, i)
+
+
+def test_limb_consistency_check_catches_a_wrong_residue():
+    """The full-size GPU tests check every limb of each decryption against
+    limb 0 (assert_limbs_consistent); on the oracle, a clean decryption passes
+    and one residue changed in limb 3 of the ciphertext fails."""
+    from _helpers import assert_limbs_consistent
+    o = make(wl.SMALL)
+    sk = o.keygen_secret(1)
+    ct = o.encrypt(sk, o.encode(wl.slot_vector(o.N // 2, seed=3), 4, 2.0 ** 40), 1, 1)
+    assert_limbs_consistent(o.decrypt(sk, ct), o.primes)
+    ct[0, 3, 7] = (int(ct[0, 3, 7]) + 1) % o.primes[3]
+    with pytest.raises(AssertionError):
+        assert_limbs_consistent(o.decrypt(sk, ct), o.primes)

@@ -67,3 +67,50 @@ def test_noalloc_refuses_sizes_beyond_its_array():
     out = np.zeros((2, 3, ctx.N), np.uint64)
     ctx.keyswitch_noalloc(keys, 1, d, out)
     assert np.array_equal(out, ctx.keyswitch_coeffs(keys, 1, d))
+
+
+_FRESH = r"""
+import gc, sys
+sys.path[:0] = [{root!r}, {tests!r}]
+import numpy as np
+import torch
+from paper_2508_19525_b300 import workloads as wl
+from _helpers import make_ctx
+ctx = make_ctx(wl.BERT_CP)
+keys = ctx.keygen({seed}, [3])
+n = ctx.nQ
+d = wl.random_residues(ctx.primes[:n], ctx.N, seed=5)[0]
+d_dev = torch.from_numpy(d).cuda()
+out = torch.zeros((2, n, ctx.N), dtype=torch.uint64, device="cuda")
+# the NTT kernels are shared with every other operation; run them once, as any
+# earlier operation of a real caller would have
+ctx.ntt(d[:1], [0])
+ctx.ntt(d[:1], [0], inverse=True)
+torch.cuda.synchronize()
+gc.collect()
+gc.disable()
+free0 = torch.cuda.mem_get_info()[0]
+ctx.keyswitch_noalloc(keys, 3, d_dev, out)  # the first key switch of this process
+ctx.sync()
+free1 = torch.cuda.mem_get_info()[0]
+gc.enable()
+ref = ctx.keyswitch_coeffs(keys, 3, d)
+print("FREE", free0, free1, "EQUAL", bool(np.array_equal(out.cpu().numpy(), ref)))
+"""
+
+
+def test_noalloc_first_call_of_a_fresh_process_leaves_device_memory_unchanged():
+    """Run in a process of its own, so that blb_keyswitch_noalloc is the first
+    key switch there: the free device memory reported by the driver
+    (cudaMemGetInfo) is the same before and after the call, i.e. neither the
+    call nor a module load inside it allocated anything."""
+    import os
+    import subprocess
+    import sys
+    tests = os.path.dirname(os.path.abspath(__file__))
+    code = _FRESH.format(root=os.path.dirname(tests), tests=tests, seed=SEED)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-3000:]
+    line = [x for x in r.stdout.splitlines() if x.startswith("FREE")][-1].split()
+    assert line[1] == line[2], f"free device memory changed: {line[1]} -> {line[2]}"
+    assert line[4] == "True"
