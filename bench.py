@@ -1018,80 +1018,106 @@ def run_blb(args):
         "weights": {"plaintext_bytes": w.plan_bytes, "encode_s": round(w.plan_s, 2), "timed": False},
     }
     if not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(args.cpu_sample)
+        line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line), flush=True)
 
 
 # --------------------------------------------------------------------------- CPU oracle
-def oracle_step_estimate(sample):
-    """Time the CPU oracle on a bounded sample of one step and extrapolate by
-    operation counts: returns (seconds per step, sample description)."""
-    import oracle
-    from paper_2508_19525_b300 import workloads as wl
-    prm = wl.BERT_CP
-    o = oracle.Oracle(prm.logN, prm.q_bits, prm.p_bits, prm.dnum)
-    sk = o.keygen_secret(0)
-    gk = {}
-    for r in (M, 2 * M):
-        gk[r] = o.keygen_galois(0, sk, o.galois_elt(r))
-    Z = pack_columns(wl.bert_base_cp(0)[0], M, (o.N // 2) // M)
-    t = {}
-    n_rot, n_pt = sample
-    for lv in (LEVEL, LEVEL - 1):
+class OracleSample:
+    """The CPU oracle's own matmul_cp method, phase by phase (orc_cp_baby_steps,
+    orc_cp_inner_sum, orc_rotate_sum, orc_rescale: the calls orc_matmul_cp is
+    made of), on a bounded sample of the BERT-base step with the weights'
+    plaintext diagonals encoded once outside the timed region (as the GPU arm's
+    plans are).  One sample times, at level 7 (N = 2^15, 8 primes): the hoisted
+    baby steps of input 0 (15 rotations), the inner sum of QKV output block 0's
+    giant step 0 over all 6 inputs (96 plaintext products), that block's 7
+    giant-step rotations summed with one ModDown and its rescale, one
+    encryption, and one masking + decryption.  The step is extrapolated by its
+    own counts: QKV = 6 x baby steps + 18 x (8 inner sums + giant sum + rescale);
+    W_O at level 6 = 6 x baby steps + 6 x (the same), scaled by its limb count
+    (7/8); 6 encryptions; 18 maskings + decryptions.  (The giant sum's inputs
+    are 7 copies of the inner sum: its cost does not depend on the values.)"""
+
+    def __init__(self):
+        import oracle
+        from paper_2508_19525_b300 import workloads as wl
+        prm = wl.BERT_CP
+        self.o = o = oracle.Oracle(prm.logN, prm.q_bits, prm.p_bits, prm.dnum)
+        self.scale = prm.scale
+        self.sk = o.keygen_secret(0)
+        self.k = (o.N // 2) // M
+        self.G = G = self.k // B1
+        self.baby_rots = [b * M for b in range(1, B1)]
+        self.giant_rots = [g * B1 * M for g in range(1, G)]
+        self.gal = {o.galois_elt(r): o.keygen_galois(0, self.sk, o.galois_elt(r))
+                    for r in self.baby_rots + self.giant_rots}
+        X, Wqkv, _ = wl.bert_base_cp(0)
+        self.Z = pack_columns(X, M, self.k)
+        self.cts = np.stack([o.encrypt(self.sk, o.encode(z, LEVEL, prm.scale), 0, c) for c, z in enumerate(self.Z)])
+        self.baby = o.cp_baby_steps(self.cts, M, B1, self.gal)           # all inputs, once
+        self.pts = o.cp_encode_diagonals(LEVEL, M, D, Wqkv, D_QKV, B1, [0])[0, 0]  # block 0, giant step 0
+
+    def run(self):
+        o = self.o
         t0 = time.perf_counter()
-        ct = o.encrypt(sk, o.encode(Z[0], lv, prm.scale), 0, lv)
-        t[("enc", lv)] = time.perf_counter() - t0
+        o.cp_baby_steps(self.cts[:1], M, B1, self.gal)
+        t_baby = time.perf_counter() - t0
         t0 = time.perf_counter()
-        for i in range(n_rot):
-            r = M if i % 2 == 0 else 2 * M
-            o.rotate(ct, r, gk[r])
-        t[("rot", lv)] = (time.perf_counter() - t0) / n_rot
+        T = o.cp_inner_sum(self.baby, self.pts)
+        t_inner = time.perf_counter() - t0
         t0 = time.perf_counter()
-        acc = np.zeros_like(ct)
-        for i in range(n_pt):
-            pt = o.encode(Z[i % len(Z)], lv, float(o.primes[lv]))
-            prod = o.mul_plain(ct, pt)
-            acc = prod  # accumulation is a limb-wise add, negligible next to the product
-        t[("pt", lv)] = (time.perf_counter() - t0) / n_pt
+        acc = o.rotate_sum(T, np.stack([T] * (self.G - 1)), self.giant_rots,
+                           [self.gal[o.galois_elt(r)] for r in self.giant_rots])
+        y = o.rescale(acc)
+        t_giant = time.perf_counter() - t0
         t0 = time.perf_counter()
-        o.rescale(acc)
-        t[("rs", lv)] = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    m, sh = o.he2mpc(ct, 0, 1)
-    o.decrypt(sk, m)
-    t_mask = time.perf_counter() - t0
-    # BERT-base step: 6 encryptions; QKV at level 7: 90 + 126 rotations, 13824
-    # plaintext products, 18 rescales; W_O at level 6: 90 + 42 rotations, 4608
-    # products, 6 rescales; 18 maskings + decryptions
-    est = (6 * t[("enc", LEVEL)] + 216 * t[("rot", LEVEL)] + 13824 * t[("pt", LEVEL)] + 18 * t[("rs", LEVEL)]
-           + 132 * t[("rot", LEVEL - 1)] + 4608 * t[("pt", LEVEL - 1)] + 6 * t[("rs", LEVEL - 1)] + 18 * t_mask)
-    desc = (f"{n_rot} rotations + {n_pt} plaintext encode-and-multiply + 1 rescale + 1 encryption at each of "
-            f"levels {LEVEL} and {LEVEL - 1}, 1 he2mpc + decryption (N=2^15); extrapolated to the step's "
-            f"348 rotations, 18432 plaintext products, 24 rescales, 6 encryptions, 18 maskings")
-    return est, desc
+        o.encrypt(self.sk, o.encode(self.Z[0], LEVEL, self.scale), 0, 99)
+        t_enc = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        masked, _ = o.he2mpc(y, 0, 1)
+        o.decrypt(self.sk, masked)
+        t_mask = time.perf_counter() - t0
+        block = self.G * t_inner + t_giant
+        est = (6 * t_baby + 18 * block) + (7 / 8) * (6 * t_baby + 6 * block) + 6 * t_enc + 18 * t_mask
+        return est, {"baby_steps_one_input_s": round(t_baby, 3), "inner_sum_s": round(t_inner, 3),
+                     "giant_sum_and_rescale_s": round(t_giant, 3), "encrypt_s": round(t_enc, 4),
+                     "mask_decrypt_s": round(t_mask, 4)}
+
+    @staticmethod
+    def describe():
+        return ("oracle calls of matmul_cp's phases on the BERT-base step (N=2^15, level 7, plaintexts pre-encoded): "
+                "orc_cp_baby_steps (input 0, 15 hoisted rotations), orc_cp_inner_sum (QKV block 0, giant step 0: 96 "
+                "plaintext products), orc_rotate_sum (7 giant rotations, one ModDown) + orc_rescale, 1 encryption, "
+                "1 he2mpc + decryption; extrapolated as QKV = 6 baby + 18 x (8 inner sums + giant sum), "
+                "W_O = 7/8 x (6 baby + 6 x the same), 6 encryptions, 18 maskings")
+
+    def threads(self):
+        """OpenMP threads the sample keeps busy: the oracle's limb loops (8 limbs
+        at level 7, 11 with the special primes in key switching)."""
+        n = os.environ.get("OMP_NUM_THREADS")
+        avail = int(n) if n and n.isdigit() else (os.cpu_count() or 1)
+        return min(avail, LEVEL + 1)
 
 
-def oracle_threads():
-    n = os.environ.get("OMP_NUM_THREADS")
-    return int(n) if n and n.isdigit() else (os.cpu_count() or 1)
-
-
-def cpu_baseline(sample):
-    est, desc = oracle_step_estimate(sample)
-    return {"value": round(TOKENS_PER_STEP / est, 6), "unit": UNIT, "cores": oracle_threads(), "kind": "oracle",
-            "sample": desc, "est_s_per_step": round(est, 1)}
+def cpu_baseline():
+    smp = OracleSample()
+    est, parts = smp.run()
+    return {"value": round(TOKENS_PER_STEP / est, 6), "unit": UNIT, "cores": smp.threads(),
+            "host_cores": os.cpu_count(), "kind": "oracle", "sample": smp.describe(),
+            "sample_parts_s": parts, "est_s_per_step": round(est, 2)}
 
 
 def run_reference(args):
     world, rank, local = dist_env()
     if rank != 0:
         return
+    smp = OracleSample()
     for _ in range(args.warmup):
-        oracle_step_estimate((1, 2))
+        smp.run()
     ests = []
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        e, desc = oracle_step_estimate(args.cpu_sample)
+        e, parts = smp.run()
         ests.append(e)
     wall = time.perf_counter() - t0
     est = sum(ests) / len(ests)
@@ -1101,8 +1127,9 @@ def run_reference(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "u64 (RNS residues; FP64 encode/decode)",
             "data": "synthetic (seeded U[-1,1] BERT-base-shaped operands)", "config": config(1),
             "impl": "reference",
-            "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": oracle_threads(), "kind": "oracle",
-                             "sample": desc},
+            "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": smp.threads(),
+                             "host_cores": os.cpu_count(), "kind": "oracle", "sample": smp.describe(),
+                             "sample_parts_s": parts},
             "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "sample_wall_s": round(wall, 1)}
     print(json.dumps(line), flush=True)
@@ -1238,8 +1265,6 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["blb", "reference"], default="blb")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-rotations", type=int, default=6)
-    ap.add_argument("--cpu-products", type=int, default=48)
     ap.add_argument("--ncu-case", action="store_true", help="run the small profiling case and exit")
     ap.add_argument("--ncu-seqs", type=int, default=1, help="sequences in the profiling case")
     ap.add_argument("--ncu-step", action="store_true", help="run one profiled BERT-base step and exit")
@@ -1276,7 +1301,6 @@ def main():
         return ncu_conv()
     if args.ncu_cc:
         return ncu_cc(args.ncu_cc, args.ncu_cc_kind, args.ncu_cc_params)
-    args.cpu_sample = (args.cpu_rotations, args.cpu_products)
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -349,6 +349,61 @@ class Oracle:
             raise ValueError(f"orc_matmul_cp failed: {rc}")
         return Y
 
+    @staticmethod
+    def _galois_set(galois):
+        gals = np.array(list(galois.keys()), np.uint64)
+        keys = [np.ascontiguousarray(galois[int(g)], np.uint64) for g in gals]
+        ptrs = (_u64p * max(1, len(keys)))(*[_p(kk, _u64p) for kk in keys])
+        return _GaloisSet(len(keys), _p(gals, _u64p), ptrs), (gals, keys, ptrs)
+
+    def cp_baby_steps(self, X_cts, m, b1, galois):
+        """The baby steps of matmul_cp: (nX, b1, 2, level+1, N), [c][b] = Rot^{b m}(X_c)."""
+        X_cts = np.ascontiguousarray(X_cts, np.uint64)
+        nX, level = X_cts.shape[0], X_cts.shape[2] - 1
+        gs, _keep = self._galois_set(galois)
+        baby = np.zeros((nX, b1, 2, level + 1, self.N), np.uint64)
+        rc = lib().orc_cp_baby_steps(self._pp, ctypes.byref(gs), _p(X_cts, _u64p), nX, level, m, b1, _p(baby, _u64p))
+        if rc:
+            raise ValueError(f"orc_cp_baby_steps failed: {rc}")
+        return baby
+
+    def cp_encode_diagonals(self, level, m, d, W, d_out, b1, out_idx):
+        """Plaintext diagonals of the given outputs: (n_out, G, nX, b1, level+1, N)."""
+        k = (self.N // 2) // m
+        G, nX = k // b1, (d + k - 1) // k
+        W = np.ascontiguousarray(W, np.float64)
+        oi = np.array(list(out_idx), np.uint32)
+        pts = np.zeros((len(oi), G, nX, b1, level + 1, self.N), np.uint64)
+        rc = lib().orc_cp_encode_diagonals(self._pp, level, m, d, _p(W, _f64p), d_out, b1, _p(oi, _u32p), len(oi),
+                                           _p(pts, _u64p))
+        if rc:
+            raise ValueError(f"orc_cp_encode_diagonals failed: {rc}")
+        return pts
+
+    def cp_outputs(self, baby, m, b1, pts, galois):
+        """Outputs of matmul_cp from its baby steps and pre-encoded plaintexts."""
+        baby = np.ascontiguousarray(baby, np.uint64)
+        pts = np.ascontiguousarray(pts, np.uint64)
+        nX, level = baby.shape[0], baby.shape[3] - 1
+        gs, _keep = self._galois_set(galois)
+        Y = np.zeros((pts.shape[0], 2, level, self.N), np.uint64)
+        rc = lib().orc_cp_outputs(self._pp, ctypes.byref(gs), _p(baby, _u64p), nX, level, m, b1, _p(pts, _u64p),
+                                  pts.shape[0], _p(Y, _u64p))
+        if rc:
+            raise ValueError(f"orc_cp_outputs failed: {rc}")
+        return Y
+
+    def cp_inner_sum(self, baby, pts):
+        """sum_c sum_b baby[c][b] (.) pts[c][b]: baby (nX, b1, 2, l+1, N), pts (nX, b1, l+1, N)."""
+        baby = np.ascontiguousarray(baby, np.uint64)
+        pts = np.ascontiguousarray(pts, np.uint64)
+        nX, b1, level = baby.shape[0], baby.shape[1], baby.shape[3] - 1
+        T = np.zeros((2, level + 1, self.N), np.uint64)
+        rc = lib().orc_cp_inner_sum(self._pp, _p(baby, _u64p), nX, level, b1, _p(pts, _u64p), _p(T, _u64p))
+        if rc:
+            raise ValueError(f"orc_cp_inner_sum failed: {rc}")
+        return T
+
     def matmul_cp_diag(self, X_cts, L, groups, Dh, W, d_out, b1, galois, out_idx=None):
         """Diagonal-input product (App. C.2).  X_cts: the dense-diagonal
         ciphertexts of every head group in order; groups: heads per group."""

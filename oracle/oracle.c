@@ -650,8 +650,10 @@ static int mp_cmp(const mpint* a, const mpint* b)
 }
 static uint64_t mp_mod_u64(const mpint* a, uint64_t q)
 {
+    int top = ORC_MP_WORDS - 1;
+    while (top > 0 && a->w[top] == 0) top--;
     u128 r = 0;
-    for (int i = ORC_MP_WORDS - 1; i >= 0; i--) r = ((r << 64) | a->w[i]) % q;
+    for (int i = top; i >= 0; i--) r = ((r << 64) | a->w[i]) % q;
     return (uint64_t)r;
 }
 
@@ -1024,9 +1026,128 @@ static double plain_weight(const void* w, uint32_t i, uint32_t r, uint32_t col)
     return (r < P->d && col < P->d_out) ? P->W[(size_t)r * P->d_out + col] : 0.0;
 }
 
+/* Baby steps of the BSGS product (App. C.1): baby[c][b] = Rot^{b m}(X_c) for
+ * b < b1 (b = 0 is X_c itself), the b1 - 1 rotations of X_c hoisted (one
+ * decomposition and ModUp of X_c serves all of them).  The inputs c are
+ * independent (OpenMP over c). */
+int orc_cp_baby_steps(const orc_params* p, const orc_galois_set* gk, const uint64_t* X, uint32_t nX,
+                      uint32_t level, uint32_t m, uint32_t b1, uint64_t* baby)
+{
+    const uint32_t N = p->N, s = N / 2, n = level + 1;
+    if (level < 1 || m == 0 || s % m || b1 == 0 || (s / m) % b1) return -1;
+    const size_t ctw = (size_t)2 * n * N;
+    int32_t* rots = malloc(sizeof(int32_t) * b1);
+    const uint64_t** keys = malloc(sizeof(uint64_t*) * b1);
+    int rc = 0;
+    for (uint32_t b = 1; b < b1; b++) {
+        rots[b - 1] = (int32_t)(b * m);
+        keys[b - 1] = find_galois(p, gk, rots[b - 1]);
+        if (!keys[b - 1]) rc = -2;
+    }
+    if (!rc) {
+        #pragma omp parallel for schedule(dynamic) if (nX > 1)
+        for (uint32_t c = 0; c < nX; c++) {
+            memcpy(baby + ((size_t)c * b1) * ctw, X + (size_t)c * ctw, sizeof(uint64_t) * ctw);
+            orc_rotate_hoisted(p, X + (size_t)c * ctw, level, b1 - 1, rots, keys, baby + ((size_t)c * b1 + 1) * ctw);
+        }
+    }
+    free(rots); free(keys);
+    return rc;
+}
+
+/* The plaintext diagonal D'_{c,e,g,b} as slot values (see above). */
+static void cp_diagonal(uint32_t m, uint32_t k, uint32_t b1, cp_weight_fn wf, const void* wctx, uint32_t c,
+                        uint32_t e, uint32_t g, uint32_t b, double* z)
+{
+    for (uint32_t beta = 0; beta < k; beta++) {
+        uint32_t row = c * k + (beta + b) % k;
+        uint32_t col = e * k + (beta + k - (g * b1) % k) % k;
+        for (uint32_t i = 0; i < m; i++) z[i + m * beta] = wf(wctx, i, row, col);
+    }
+}
+
+/* Inner sum of one giant step of one output (the baby-step sum of App. C.1):
+ *   T_g = sum_c sum_b baby[c][b] (.) D'_{c,e,g,b}
+ * with the plaintexts D' read from pts ([nX][b1] plaintexts of (level+1) x N
+ * words) or, when pts is NULL, encoded here from wf (z and pt are scratch). */
+static int cp_inner_sum(const orc_params* p, const uint64_t* baby, uint32_t nX, uint32_t level, uint32_t m,
+                        uint32_t b1, const uint64_t* pts, cp_weight_fn wf, const void* wctx, uint32_t e, uint32_t g,
+                        double* z, uint64_t* pt, uint64_t* prod, uint64_t* T)
+{
+    const uint32_t N = p->N, s = N / 2, n = level + 1, k = s / m;
+    const size_t ctw = (size_t)2 * n * N, ptw = (size_t)n * N;
+    int rc = 0;
+    memset(T, 0, sizeof(uint64_t) * ctw);
+    for (uint32_t c = 0; c < nX; c++) {
+        for (uint32_t b = 0; b < b1; b++) {
+            const uint64_t* P;
+            if (pts) {
+                P = pts + ((size_t)c * b1 + b) * ptw;
+            } else {
+                cp_diagonal(m, k, b1, wf, wctx, c, e, g, b, z);
+                if (orc_encode(p, z, s, level, (double)p->prime[level], pt)) rc = -3;
+                P = pt;
+            }
+            orc_mul_plain(p, baby + ((size_t)c * b1 + b) * ctw, P, level, prod);
+            ct_add_inplace(p, T, prod, level, 2);
+        }
+    }
+    return rc;
+}
+
+int orc_cp_inner_sum(const orc_params* p, const uint64_t* baby, uint32_t nX, uint32_t level, uint32_t b1,
+                     const uint64_t* pts, uint64_t* T)
+{
+    if (level < 1 || !pts || b1 == 0) return -1;
+    uint64_t* prod = malloc(sizeof(uint64_t) * (size_t)2 * (level + 1) * p->N);
+    int rc = cp_inner_sum(p, baby, nX, level, 1, b1, pts, NULL, NULL, 0, 0, NULL, NULL, prod, T);
+    free(prod);
+    return rc;
+}
+
+/* Giant steps of the BSGS product for the outputs out_idx[0..n_out):
+ *   T_g = the inner sum of giant step g (above), g < G
+ *   Y_e = Rescale( T_0 + sum_{g >= 1} Rot^{g b1 m}(T_g) )  (one ModDown for the sum)
+ * The plaintexts are read from pts ([n_out][G][nX][b1] plaintexts) when pts is
+ * not NULL, else encoded from wf as they are used. */
+static int cp_outputs(const orc_params* p, const orc_galois_set* gk, const uint64_t* baby, uint32_t nX,
+                      uint32_t level, uint32_t m, uint32_t b1, cp_weight_fn wf, const void* wctx,
+                      const uint32_t* out_idx, const uint64_t* pts, uint32_t n_out, uint64_t* Y)
+{
+    const uint32_t N = p->N, s = N / 2, n = level + 1;
+    const uint32_t k = s / m, G = k / b1;
+    const size_t ctw = (size_t)2 * n * N, ptw = (size_t)n * N;
+    int32_t* rots = malloc(sizeof(int32_t) * G);
+    const uint64_t** keys = malloc(sizeof(uint64_t*) * G);
+    int rc = 0;
+    for (uint32_t g = 1; g < G; g++) {
+        rots[g - 1] = (int32_t)(g * b1 * m);
+        keys[g - 1] = find_galois(p, gk, rots[g - 1]);
+        if (!keys[g - 1]) rc = -2;
+    }
+    uint64_t* T = malloc(sizeof(uint64_t) * ctw * G);
+    uint64_t* acc = malloc(sizeof(uint64_t) * ctw);
+    double* z = malloc(sizeof(double) * s);
+    uint64_t* pt = malloc(sizeof(uint64_t) * ptw);
+    uint64_t* prod = malloc(sizeof(uint64_t) * ctw);
+    for (uint32_t oi = 0; oi < n_out && !rc; oi++) {
+        const uint32_t e = out_idx ? out_idx[oi] : oi;
+        for (uint32_t g = 0; g < G && !rc; g++)
+            rc = cp_inner_sum(p, baby, nX, level, m, b1, pts ? pts + ((size_t)oi * G + g) * nX * b1 * ptw : NULL,
+                              wf, wctx, e, g, z, pt, prod, T + (size_t)g * ctw);
+        if (rc) break;
+        orc_rotate_sum(p, T, T + ctw, level, G - 1, rots, keys, acc);
+        orc_rescale(p, acc, level, 2, Y + (size_t)oi * 2 * level * N);
+    }
+    free(rots); free(keys); free(T); free(acc); free(z); free(pt); free(prod);
+    return rc;
+}
+
 /* BSGS diagonal product (Sec. 4.2.1 / 5.2) for any weight function:
  *   Y_e = Rescale( sum_g Rot^{g b1 m}( sum_c sum_b Rot^{b m}(X_c) (.) D'_{c,e,g,b} ) )
- * with D'_{c,e,g,b}[i + m beta] = w(i, c k + (beta + b) mod k, e k + (beta - g b1) mod k). */
+ * with D'_{c,e,g,b}[i + m beta] = w(i, c k + (beta + b) mod k, e k + (beta - g b1) mod k):
+ * the baby steps, then the giant steps of each output with its plaintexts
+ * encoded as they are used. */
 static int matmul_cp_w(const orc_params* p, const orc_galois_set* gk, const uint64_t* X, uint32_t nX,
                        uint32_t level, uint32_t m, cp_weight_fn wf, const void* wctx, uint32_t b1,
                        const uint32_t* out_idx, uint32_t n_out, uint64_t* Y)
@@ -1035,61 +1156,53 @@ static int matmul_cp_w(const orc_params* p, const orc_galois_set* gk, const uint
     if (level < 1 || m == 0 || s % m) return -1;
     const uint32_t k = s / m;
     if (b1 == 0 || k % b1) return -1;
-    const uint32_t G = k / b1;
-    const size_t ctw = (size_t)2 * n * N;
+    uint64_t* baby = malloc(sizeof(uint64_t) * (size_t)2 * n * N * nX * b1);
+    int rc = orc_cp_baby_steps(p, gk, X, nX, level, m, b1, baby);
+    if (!rc) rc = cp_outputs(p, gk, baby, nX, level, m, b1, wf, wctx, out_idx, NULL, n_out, Y);
+    free(baby);
+    return rc;
+}
 
-    /* baby steps: Rot^{b m}(X_c), b < b1, hoisted (one ModUp of X_c serves all b) */
-    uint64_t* baby = malloc(sizeof(uint64_t) * ctw * nX * b1);
-    int32_t* rots = malloc(sizeof(int32_t) * (b1 > G ? b1 : G));
-    const uint64_t** keys = malloc(sizeof(uint64_t*) * (b1 > G ? b1 : G));
+/* The plaintexts D'_{c,e,g,b} of the outputs out_idx[0..n_out) of X W (d x d_out,
+ * row-major), encoded at `level` with scale q_level, laid out as orc_cp_outputs
+ * reads them: [n_out][G][nX][b1] x (level+1) x N words. */
+int orc_cp_encode_diagonals(const orc_params* p, uint32_t level, uint32_t m, uint32_t d, const double* W,
+                            uint32_t d_out, uint32_t b1, const uint32_t* out_idx, uint32_t n_out, uint64_t* pts)
+{
+    const uint32_t N = p->N, s = N / 2, n = level + 1;
+    if (level < 1 || m == 0 || s % m) return -1;
+    const uint32_t k = s / m;
+    if (b1 == 0 || k % b1) return -1;
+    const uint32_t G = k / b1, nX = (d + k - 1) / k;
+    plain_weights w = {W, d, d_out};
     int rc = 0;
-    for (uint32_t b = 1; b < b1; b++) {
-        rots[b - 1] = (int32_t)(b * m);
-        keys[b - 1] = find_galois(p, gk, rots[b - 1]);
-        if (!keys[b - 1]) rc = -2;
-    }
-    for (uint32_t c = 0; c < nX && !rc; c++) {
-        memcpy(baby + ((size_t)c * b1) * ctw, X + (size_t)c * ctw, sizeof(uint64_t) * ctw);
-        orc_rotate_hoisted(p, X + (size_t)c * ctw, level, b1 - 1, rots, keys, baby + ((size_t)c * b1 + 1) * ctw);
-    }
-    /* giant steps: Rot^{g b1 m}, g >= 1, summed with one ModDown per output */
-    for (uint32_t g = 1; g < G && !rc; g++) {
-        rots[g - 1] = (int32_t)(g * b1 * m);
-        keys[g - 1] = find_galois(p, gk, rots[g - 1]);
-        if (!keys[g - 1]) rc = -2;
-    }
-
-    double* z = malloc(sizeof(double) * s);
-    uint64_t* pt = malloc(sizeof(uint64_t) * n * N);
-    uint64_t* prod = malloc(sizeof(uint64_t) * ctw);
-    uint64_t* T = malloc(sizeof(uint64_t) * ctw * G);
-    uint64_t* acc = malloc(sizeof(uint64_t) * ctw);
-    const double pt_scale = (double)p->prime[level];
-    for (uint32_t oi = 0; oi < n_out && !rc; oi++) {
-        const uint32_t e = out_idx[oi];
-        /* T_g = sum_{c,b} Rot^{b m}(X_c) (.) D'_{c,e,g,b} */
-        for (uint32_t g = 0; g < G && !rc; g++) {
-            uint64_t* Tg = T + (size_t)g * ctw;
-            memset(Tg, 0, sizeof(uint64_t) * ctw);
-            for (uint32_t c = 0; c < nX; c++) {
-                for (uint32_t b = 0; b < b1; b++) {
-                    for (uint32_t beta = 0; beta < k; beta++) {
-                        uint32_t row = c * k + (beta + b) % k;
-                        uint32_t col = e * k + (beta + k - (g * b1) % k) % k;
-                        for (uint32_t i = 0; i < m; i++) z[i + m * beta] = wf(wctx, i, row, col);
-                    }
-                    if (orc_encode(p, z, s, level, pt_scale, pt)) rc = -3;
-                    orc_mul_plain(p, baby + ((size_t)c * b1 + b) * ctw, pt, level, prod);
-                    ct_add_inplace(p, Tg, prod, level, 2);
-                }
+    const size_t total = (size_t)n_out * G * nX * b1;
+    #pragma omp parallel
+    {
+        double* z = malloc(sizeof(double) * s);
+        #pragma omp for schedule(dynamic)
+        for (size_t x = 0; x < total; x++) {
+            const uint32_t b = (uint32_t)(x % b1), c = (uint32_t)((x / b1) % nX), g = (uint32_t)((x / b1 / nX) % G);
+            const uint32_t oi = (uint32_t)(x / b1 / nX / G);
+            cp_diagonal(m, k, b1, plain_weight, &w, c, out_idx ? out_idx[oi] : oi, g, b, z);
+            if (orc_encode(p, z, s, level, (double)p->prime[level], pts + x * (size_t)n * N)) {
+                #pragma omp atomic write
+                rc = -3;
             }
         }
-        /* Y_e = Rescale( T_0 + sum_{g >= 1} Rot^{g b1 m}(T_g) ) */
-        orc_rotate_sum(p, T, T + ctw, level, G - 1, rots, keys, acc);
-        orc_rescale(p, acc, level, 2, Y + (size_t)oi * 2 * level * N);
+        free(z);
     }
-    free(baby); free(rots); free(keys); free(z); free(pt); free(prod); free(T); free(acc);
     return rc;
+}
+
+/* Giant steps from baby steps (orc_cp_baby_steps) and pre-encoded plaintexts
+ * (orc_cp_encode_diagonals): Y holds n_out ciphertexts at level - 1. */
+int orc_cp_outputs(const orc_params* p, const orc_galois_set* gk, const uint64_t* baby, uint32_t nX,
+                   uint32_t level, uint32_t m, uint32_t b1, const uint64_t* pts, uint32_t n_out, uint64_t* Y)
+{
+    const uint32_t s = p->N / 2;
+    if (level < 1 || m == 0 || s % m || b1 == 0 || (s / m) % b1 || !pts) return -1;
+    return cp_outputs(p, gk, baby, nX, level, m, b1, NULL, NULL, NULL, pts, n_out, Y);
 }
 
 int orc_matmul_cp(const orc_params* p, const orc_galois_set* gk, const uint64_t* X, uint32_t nX,

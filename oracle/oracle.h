@@ -123,6 +123,21 @@ typedef struct {
 } orc_galois_set;
 
 uint32_t orc_cp_num_rotations(uint32_t nX, uint32_t nY, uint32_t b1, uint32_t G);
+/* The two phases of orc_matmul_cp, for callers that encode the weights once:
+ * baby steps baby[c][b] = Rot^{b m}(X_c) (nX x b1 ciphertexts, hoisted); the
+ * plaintext diagonals of the outputs out_idx[0..n_out) ([n_out][G][nX][b1]
+ * plaintexts at `level`, scale q_level); and the outputs from both (n_out
+ * ciphertexts at level - 1, the same limbs as orc_matmul_cp). */
+int orc_cp_baby_steps(const orc_params* p, const orc_galois_set* gk, const uint64_t* X, uint32_t nX,
+                      uint32_t level, uint32_t m, uint32_t b1, uint64_t* baby);
+int orc_cp_encode_diagonals(const orc_params* p, uint32_t level, uint32_t m, uint32_t d, const double* W,
+                            uint32_t d_out, uint32_t b1, const uint32_t* out_idx, uint32_t n_out, uint64_t* pts);
+int orc_cp_outputs(const orc_params* p, const orc_galois_set* gk, const uint64_t* baby, uint32_t nX,
+                   uint32_t level, uint32_t m, uint32_t b1, const uint64_t* pts, uint32_t n_out, uint64_t* Y);
+/* One inner sum of the giant steps: T = sum_c sum_b baby[c][b] (.) pts[c][b]
+ * (nX x b1 plaintexts at `level`). */
+int orc_cp_inner_sum(const orc_params* p, const uint64_t* baby, uint32_t nX, uint32_t level, uint32_t b1,
+                     const uint64_t* pts, uint64_t* T);
 int orc_matmul_cp(const orc_params* p, const orc_galois_set* gk, const uint64_t* X, uint32_t nX,
                   uint32_t level, uint32_t m, uint32_t d, const double* W, uint32_t d_out,
                   uint32_t b1, const uint32_t* out_idx, uint32_t n_out, uint64_t* Y);

@@ -168,3 +168,36 @@ def test_mp2ml_encoded_mask_is_concentrated():
     u = rng.integers(0, q, size=N, dtype=np.uint64).astype(np.float64)
     u = np.where(u > q / 2, u - q, u)
     assert np.mean(np.abs(u) <= q / np.sqrt(N)) < 0.05
+
+
+def test_matmul_cp_phases_equal_the_one_call_product():
+    """orc_matmul_cp's two phases (baby steps; outputs from pre-encoded
+    plaintext diagonals) give the one-call product's limbs, for a subset of
+    outputs in any order."""
+    prm = wl.SMALL
+    o = oracle.Oracle(prm.logN, prm.q_bits, prm.p_bits, prm.dnum)
+    m, d, d_out, b1 = 64, 80, 100, 4
+    k = o.N // 2 // m
+    G, level = k // b1, o.nQ - 1
+    sk = o.keygen_secret(4)
+    rots = [b * m for b in range(1, b1)] + [g * b1 * m for g in range(1, G)]
+    gal = {o.galois_elt(r): o.keygen_galois(4, sk, o.galois_elt(r)) for r in rots}
+    X, W = wl.cp_operands(m, d, d_out, seed=8)
+    nX = (d + k - 1) // k
+    Z = np.zeros((nX, o.N // 2))
+    for c in range(nX):
+        for b in range(k):
+            if c * k + b < d:
+                Z[c, b * m:(b + 1) * m] = X[:, c * k + b]
+    cts = np.stack([o.encrypt(sk, o.encode(z, level, prm.scale), 4, c) for c, z in enumerate(Z)])
+    ref = o.matmul_cp(cts, m, d, W, d_out, b1, gal)
+    baby = o.cp_baby_steps(cts, m, b1, gal)
+    pts = o.cp_encode_diagonals(level, m, d, W, d_out, b1, [1, 0])
+    Y = o.cp_outputs(baby, m, b1, pts, gal)
+    assert np.array_equal(Y[0], ref[1]) and np.array_equal(Y[1], ref[0])
+    # and the finest phases: one inner sum per giant step, then the giant-step
+    # rotations summed with one ModDown, then the rescale
+    T = [o.cp_inner_sum(baby, pts[0, g]) for g in range(G)]
+    acc = o.rotate_sum(T[0], np.stack(T[1:]), [g * b1 * m for g in range(1, G)],
+                       [gal[o.galois_elt(g * b1 * m)] for g in range(1, G)])
+    assert np.array_equal(o.rescale(acc), ref[1])
