@@ -199,6 +199,7 @@ class Workload:
         G = self.k // B1
         rots = [b * M for b in range(1, B1)] + [g * B1 * M for g in range(1, G)]
         self.keys = self.ctx.keygen(0, rots)
+        self.keys_bytes = len(rots) * prm.dnum * 2 * (len(prm.q_bits) + len(prm.p_bits)) * self.N * 8
         # pick the NTT radix and pass split for this ring on the device before
         # anything is timed (or take the given ones, so that profiles capture
         # known kernels)
@@ -294,6 +295,25 @@ class Workload:
         got_o = unpack_columns(np.stack([self.ctx.decrypt(self.keys, y, coeffs=False)[1] for y in O]), M, self.k, D_O)
         err = np.concatenate([(got_qkv - self.ref_qkv).ravel(), (got_o - self.ref_o).ravel()])
         return float(np.max(np.abs(err))), float(np.mean(err ** 2))
+
+    def cp_bytes(self):
+        """HBM bytes of the step's two matmul_cp products: the algorithmic
+        minimum (compact FP64 weights, input and output ciphertexts, the
+        rotation keys once) beside what the implementation streams (the
+        pre-encoded byte-plane plaintext diagonals, the baby-step ciphertexts and
+        the partial sums of the MAC)."""
+        N, w8 = self.N, 8
+        ct = lambda lv: 2 * (lv + 1) * N * w8
+        keys = self.keys_bytes
+        alg = ((D * D_QKV + D * D_O) * w8 + self.n_in * ct(LEVEL) + 18 * ct(LEVEL - 1)
+               + self.n_in * ct(LEVEL - 1) + 6 * ct(LEVEL - 2) + keys)
+        qkv, o = self.plan_qkv.info(), self.plan_o.info()
+        mac = 0
+        for info, lv, nY in ((qkv, LEVEL, 18), (o, LEVEL - 1, 6)):
+            mac += info["plaintext_bytes"] + (info["nX"] * info["b1"] + nY * info["G"]) * ct(lv)
+        return {"algorithmic_min": int(alg), "as_implemented_mac": int(mac),
+                "note": "algorithmic = weights d x d' x 8 B + ciphertexts in/out + 22 rotation keys; "
+                        "as implemented = byte-plane plaintexts + baby-step ciphertexts + partial sums (MAC only)"}
 
     def counts(self):
         qkv, o = self.plan_qkv.info(), self.plan_o.info()
@@ -1015,6 +1035,7 @@ def run_blb(args):
         "conversion": dict(conv, sites={k: dict(v, frac_of_hbm=round(v["achieved_gbs"] / hbm, 4), peak_kind=peak_note)
                                         for k, v in conv["sites"].items()}) if conv else None,
         "counts_per_step": w.counts(),
+        "matmul_cp_bytes_per_step": w.cp_bytes(),
         "weights": {"plaintext_bytes": w.plan_bytes, "encode_s": round(w.plan_s, 2), "timed": False},
     }
     if not args.no_cpu_baseline:
