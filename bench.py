@@ -672,7 +672,7 @@ def cfg4_attention(ctx, stream, lengths, heads=16, dh=64, seed=45, check=2):
 
 def layer_bench():
     """One BERT-base encoder layer the hybrid way (paper_2508_19525_b300/layer.py):
-    the linear operators in fused HE blocks (QKV, Q K^T, softmax exponential,
+    the linear operators in fused HE blocks (QKV + Q K^T, softmax exponential,
     normalisation + P V + W_O + residual + LN1 head, LN1 tail + W_1 + GeLU
     polynomials, W_2 + residual + LN2 head, LN2 tail) with CKKS <-> MPC
     conversions at every boundary; MPC nonlinear steps simulated.  Returns the

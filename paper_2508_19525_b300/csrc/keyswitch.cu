@@ -332,18 +332,20 @@ __device__ __forceinline__ uint32_t perm_index(uint32_t k, uint32_t logN, uint64
     return __brev((ge - 1) >> 1) >> (32 - logN);
 }
 
-// din[src][i][k] = c1[i][perm(k)] and coef = din (the latter transformed in place)
-__global__ void k_ksb_gather(uint64_t* __restrict__ din, uint64_t* __restrict__ coef,
-                             const DevSource* __restrict__ srcs, uint32_t n, uint32_t logN)
+// v = c1[i][perm(k)] (evaluation domain) goes to coef[src][i][k] (transformed
+// to coefficient form in place next) and to the extended digit of limb i's
+// digit j = i / alpha, whose own rows are the input's evaluation rows
+__global__ void k_ksb_gather(uint64_t* __restrict__ coef, uint64_t* __restrict__ ext,
+                             const DevSource* __restrict__ srcs, uint32_t n, uint32_t E, uint32_t beta,
+                             uint32_t alpha, uint32_t logN)
 {
     const uint32_t N = 1u << logN;
     const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x, i = blockIdx.y, s = blockIdx.z;
     if (k >= N) return;
     const DevSource d = srcs[s];
     const uint64_t v = d.c1[(size_t)i * N + perm_index(k, logN, d.g)];
-    const size_t o = ((size_t)s * n + i) * N + k;
-    din[o] = v;
-    coef[o] = v;
+    coef[((size_t)s * n + i) * N + k] = v;
+    ext[(((size_t)s * beta + i / alpha) * E + i) * N + k] = v;
 }
 
 // ModUp of every digit of every source: grid.y = source * beta + j
@@ -389,16 +391,6 @@ void launch_modup(uint32_t alpha, dim3 grid, cudaStream_t st, Args... args)
     case 4: k_ksb_modup<4><<<grid, kT, 0, st>>>(args...); break;
     default: k_ksb_modup<0><<<grid, kT, 0, st>>>(args...); break;
     }
-}
-
-// the digit's own rows of the extended digit are the input's evaluation rows
-__global__ void k_ksb_digit_rows(uint64_t* __restrict__ ext, const uint64_t* __restrict__ din, uint32_t n, uint32_t E,
-                                 uint32_t beta, uint32_t alpha, uint32_t N)
-{
-    const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x, t = blockIdx.y, src = blockIdx.z;
-    if (c >= N) return;
-    const uint32_t j = t / alpha;
-    ext[(((size_t)src * beta + j) * E + t) * N + c] = din[((size_t)src * n + t) * N + c];
 }
 
 // acc[group][p][t] = sum over the group's products x of sum_j sigma_x(ext[src_x][j][t]) key_x[j][p][kt]
@@ -525,7 +517,7 @@ int ks_run(blb_ctx* ctx, uint32_t level, const KsSource* sources, uint32_t n_src
     if (n_groups == 0) return BLB_OK;
     const uint32_t N = ctx->N, n = level + 1, nP = ctx->nP, E = n + nP;
     const uint32_t alpha = ctx->alpha, beta = (n + alpha - 1) / alpha;
-    const size_t per_src = ((size_t)2 * n + (size_t)beta * E) * N;  // din, coef, ext
+    const size_t per_src = ((size_t)n + (size_t)beta * E) * N;      // coef, ext
     const size_t per_grp = ((size_t)2 * E + (size_t)2 * n) * N;     // acc, cv
     const size_t budget = (size_t)1 << 29;                           // 4 GiB per chunk
     // extension rows of one source and P rows of one group (row | prime << 24)
@@ -624,8 +616,7 @@ int ks_run(blb_ctx* ctx, uint32_t level, const KsSource* sources, uint32_t n_src
             ctx->batch_words = ctx->batch ? need : 0;
             if (!ctx->batch) return blb_fail(BLB_ERR_OOM, "key-switch batch arena");
         }
-        uint64_t* din = ctx->batch;
-        uint64_t* coef = din + (size_t)ns * n * N;
+        uint64_t* coef = ctx->batch;
         uint64_t* ext = coef + (size_t)ns * n * N;
         uint64_t* acc = ext + (size_t)ns * beta * E * N;
         uint64_t* cv = acc + (size_t)ng * 2 * E * N;
@@ -680,7 +671,7 @@ int ks_run(blb_ctx* ctx, uint32_t level, const KsSource* sources, uint32_t n_src
                        ((uint64_t)ns * (n + (uint64_t)beta * E) + (uint64_t)hp.size() * 3 * beta * E +
                         (uint64_t)ng * 2 * n) * N * 8);
         if (ns) {
-            k_ksb_gather<<<dim3(gx, n, ns), kT, 0, ctx->stream>>>(din, coef, d_src, n, ctx->logN);
+            k_ksb_gather<<<dim3(gx, n, ns), kT, 0, ctx->stream>>>(coef, ext, d_src, n, E, beta, alpha, ctx->logN);
             BLB_LAUNCHED();
             BLB_TRY(ntt_inverse(ctx, coef, ns * n, ctx->qmap(n)));
             launch_modup(alpha, dim3(gx, ns * beta), ctx->stream, (const uint64_t*)coef, ext,
@@ -688,8 +679,6 @@ int ks_run(blb_ctx* ctx, uint32_t level, const KsSource* sources, uint32_t n_src
                          (const uint64_t*)ctx->d_q, (const uint64_t*)ctx->d_bar, N);
             BLB_LAUNCHED();
             BLB_TRY(ntt_forward_list(ctx, ext, (uint32_t)ext_rows.size(), d_ext_rows));
-            k_ksb_digit_rows<<<dim3(gx, n, ns), kT, 0, ctx->stream>>>(ext, din, n, E, beta, alpha, N);
-            BLB_LAUNCHED();
         }
         launch_inner(beta, dim3(gx, nP, ng), ctx->stream, acc, (const uint64_t*)ext, (const DevGroup*)d_grp,
                      (const DevProduct*)d_prod, emap, n, E, beta, ctx->nQ, ctx->np, (const uint64_t*)ctx->d_q,

@@ -16,13 +16,15 @@ tail counted into the next layer's first block:
   4  LayerNorm-1 tail + W_1 (matmul_cp) + the GeLU polynomials F_0, F_1
   5  W_2 (matmul_cp) + residual + LayerNorm-2 head
 
-whose depths (4, 7, 7, 7, ~6) match the table.  Two places differ from the
-paper: QKV and Q K^T run as two HE segments with a conversion between them
-(the paper gives no protocol for changing the spatial-first packing of the
-matmul_cp output into matmul_cc's head packing), and the LN2 tail runs as a
-last segment of this layer (segment 6 below).  Segments 1, 2, 4, 5, 6 run on
-`ctx` (BERT-base: N = 2^15, 8 primes), segment 3 (depth 9 here, matmul_cc
-taking four levels) on `ctx_big` (N = 2^16, 12 primes).
+whose depths (4, 7, 7, 7, ~6) match the table.  Block 1 is one HE segment:
+the columns of W_Q and W_K are reordered in plaintext (Sec. 5.1, multi-head
+packing) so that the spatial-first output ciphertexts of the QKV matmul_cp
+are already the head-packed operands of Q K^T (column b = h + Hg kappa of
+output ciphertext c of a head group holds column c Kc + kappa of head h), and
+matmul_cc runs on them directly; only V and Q K^T leave the block.  The LN2
+tail runs as a last segment of this layer (segment 6 below).  Segments 1, 2,
+4, 5, 6 run on `ctx` (BERT-base: N = 2^15, 8 primes), segment 3 (depth 9
+here, matmul_cc taking four levels) on `ctx_big` (N = 2^16, 12 primes).
 
 MPC is simulated: both parties live in this process, every value between
 blocks is held as additive shares over Z_{2^43} at scale 2^-13 (Sec. 7.1),
@@ -72,6 +74,24 @@ def pack_heads(mats, L, Hg, Kc, n_c, rows):
                     b = h + Hg * kappa
                     Z[c, b * L:(b + 1) * L] = mats[h, k, :] if rows else mats[h, :, k]
     return Z
+
+
+def head_permutation(groups, Dh, k):
+    """Column order of W_Q / W_K (Sec. 5.1, multi-head packing): output column
+    e k + b of the reordered weight is column perm[e k + b] of the original, so
+    that output ciphertext e of head group g (first head h0, Kc = k / Hg) holds
+    at block b = h + Hg kappa the column c Kc + kappa of head h0 + h, c = e - (the
+    group's first ciphertext)."""
+    perm, h0 = [], 0
+    for Hg in groups:
+        Kc = k // Hg
+        assert Kc * Hg == k and Dh % Kc == 0, "head dimension must be a multiple of k / Hg"
+        for c in range(Dh // Kc):
+            for b in range(k):
+                h, kappa = b % Hg, b // Hg
+                perm.append((h0 + h) * Dh + c * Kc + kappa)
+        h0 += Hg
+    return np.array(perm)
 
 
 def diag_index(L, Hg, Kc, n_out):
@@ -216,7 +236,12 @@ class BertLayer:
         assert self.k > 0 and self.kb > 0
         self.top, self.topb = top, topb
         t0 = time.perf_counter()
-        self.p_qkv = ctx.cp_plan(L, d, self.Wqkv, 3 * d, top, b1)
+        # W_Q, W_K columns in the head-packed order (block 1 runs Q K^T on the
+        # QKV product's output ciphertexts), W_V in the natural order
+        self.perm = head_permutation(self.groups, Dh, self.k)
+        self.Wqkv_he = np.concatenate([self.Wqkv[:, :d][:, self.perm], self.Wqkv[:, d:2 * d][:, self.perm],
+                                       self.Wqkv[:, 2 * d:]], axis=1)
+        self.p_qkv = ctx.cp_plan(L, d, self.Wqkv_he, 3 * d, top, b1)
         self.p_w1 = ctx.cp_plan(L, d, self.W1, f, top - 2, b1)      # after the LN1 tail (two rescales)
         # the W_2 product has f / k input ciphertexts: fewer baby steps keep its
         # terms per output (inputs x b1) within the MAC's shared-memory tile
@@ -225,7 +250,7 @@ class BertLayer:
             while b1_down > 1 and (f // self.k) * b1_down > 96:
                 b1_down //= 2
         self.p_w2 = ctx.cp_plan(L, f, self.W2, d, top, b1_down)
-        self.cc_qk = {Hg: ctx.cc_plan(L, Hg, Dh, top) for Hg in self.groups}
+        self.cc_qk = {Hg: ctx.cc_plan(L, Hg, Dh, top - 1) for Hg in self.groups}
         self.cc_pv = {Hg: ctx_big.cc_plan(L, Hg, L, topb - 1) for Hg in self.groups}
         self.p_o = ctx_big.cp_plan_diag(L, self.groups, Dh, self.Wo, d, topb - 5, b1)
         ctx.sync()
@@ -261,6 +286,22 @@ class BertLayer:
         h = layernorm(X + np.concatenate(list(Att), axis=1) @ self.Wo, self.g1, self.b1)
         return layernorm(h + gelu_approx(h @ self.W1) @ self.W2, self.g2, self.b2)
 
+    # -- block 1 in HE: QKV, then Q K^T on its output ciphertexts --------------
+    def he_block1(self, keys, Xc):
+        """Xc: the d / k input ciphertexts of X (spatial-first, top level).
+        Returns (the 3 d / k QKV output ciphertexts, [Q K^T outputs per head
+        group]).  Q's ciphertexts of group g are the A operand and K's the B
+        operand (K_h^T in reduce-first packing) of that group's matmul_cc."""
+        ctx = self.ctx
+        Y = ctx.matmul_cp_plan(keys, self.p_qkv, Xc)
+        nq = self.d // self.k
+        outs, e0 = [], 0
+        for Hg in self.groups:
+            n_c = self.cc_qk[Hg].info()["n_c"]
+            outs.append(ctx.matmul_cc_plan(keys, self.cc_qk[Hg], Y[e0:e0 + n_c], Y[nq + e0:nq + e0 + n_c]))
+            e0 += n_c
+        return Y, outs
+
     # -- the hybrid evaluation --------------------------------------------------
     def forward(self, X, keys, keys_big, mpc, seed=11):
         """X: (L, d) activation (the previous layer's output, as MPC shares).
@@ -281,25 +322,16 @@ class BertLayer:
             store[name] = store.get(name, 0.0) + time.perf_counter() - t0
             return r
 
-        # segment 1a: QKV
-        Xc = timed("1 QKV", lambda: br.to_ckks(pack_columns(X, L, k), self.top), conv)
-        Y = timed("1 QKV", lambda: ctx.matmul_cp_plan(keys, self.p_qkv, Xc), he)
-        QKV = unpack_columns(timed("1 QKV", lambda: br.to_mpc(Y), conv), L, k, 3 * d)
-        Q = QKV[:, :d].reshape(L, H, Dh).transpose(1, 0, 2)
-        K = QKV[:, d:2 * d].reshape(L, H, Dh).transpose(1, 0, 2)
-        V = QKV[:, 2 * d:].reshape(L, H, Dh).transpose(1, 0, 2)
-        # segment 1b: Q K^T per head group
+        # segment 1: QKV and Q K^T in one HE block; V and the scores go to MPC
+        Xc = timed("1 QKV + QK^T", lambda: br.to_ckks(pack_columns(X, L, k), self.top), conv)
+        Y, Cs = timed("1 QKV + QK^T", lambda: self.he_block1(keys, Xc), he)
+        V = unpack_columns(timed("1 QKV + QK^T", lambda: br.to_mpc(Y[2 * d // k:]), conv), L, k, d)
+        V = V.reshape(L, H, Dh).transpose(1, 0, 2)
         S = np.zeros((H, L, L))
         h0 = 0
-        for Hg in self.groups:
-            pl = self.cc_qk[Hg]
-            inf = pl.info()
-            Az = pack_heads(Q[h0:h0 + Hg], L, Hg, inf["Kc"], inf["n_c"], rows=False)
-            Bz = pack_heads(K[h0:h0 + Hg].transpose(0, 2, 1), L, Hg, inf["Kc"], inf["n_c"], rows=True)
-            A = timed("1 QK^T", lambda: br.to_ckks(Az, self.top), conv)
-            B = timed("1 QK^T", lambda: br.to_ckks(Bz, self.top), conv)
-            C = timed("1 QK^T", lambda: ctx.matmul_cc_plan(keys, pl, A, B), he)
-            S[h0:h0 + Hg] = unpack_diagonals(timed("1 QK^T", lambda: br.to_mpc(C), conv), L, Hg, inf["Kc"])
+        for Hg, C in zip(self.groups, Cs):
+            Kc = self.cc_qk[Hg].info()["Kc"]
+            S[h0:h0 + Hg] = unpack_diagonals(timed("1 QKV + QK^T", lambda: br.to_mpc(C), conv), L, Hg, Kc)
             h0 += Hg
         # MPC: row maxima
         mx = S.max(axis=2)
