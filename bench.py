@@ -948,8 +948,16 @@ def run_blb(args):
         bsteps = max(1, min(10, args.steps // 2))
         bsec = timed_fn(w, lambda: w.step_batched(args.batch), bsteps, world)
         bval, _ = aggregate(bsec, TOKENS_PER_STEP * args.batch * bsteps, world)
+        # where a batched step's time goes (CUDA events per launch site, one step)
+        w.ctx.profile(True)
+        w.step_batched(args.batch)
+        w.ctx.sync()
+        bsites = {s_: round(w.ctx.profile_read(s_)[0], 3) for s_ in ("cp_mac", "keyswitch", "ntt", "intt")}
+        w.ctx.profile(False)
         batched = {"sequences_per_step": args.batch, "value": round(bval, 3), "unit": UNIT,
-                   "ms_per_step": round(bsec * 1e3 / bsteps, 3), "speedup_vs_plain": round(bval / value, 3)}
+                   "ms_per_step": round(bsec * 1e3 / bsteps, 3), "speedup_vs_plain": round(bval / value, 3),
+                   "site_ms_one_step": bsites,
+                   "mac_kernel": "tcgen05.mma (tensor memory accumulators) for 2, 4 and 8 sequences per launch"}
     # the same step with its products, masking and decryption replayed from a
     # CUDA graph (inputs encrypted eagerly every step)
     gstep = w.graph_step()
@@ -1162,7 +1170,7 @@ def ntt_us_json(us):
     return {f"r{r}/{sp}": round(v, 4) for (r, sp), v in sorted(us.items())}
 
 
-def ncu_case(seqs=1, ntt_split=None, ntt_radix=None):
+def ncu_case(seqs=1, ntt_split=None, ntt_radix=None, d_out=256):
     """Small profiling case of the same kernels for `ncu --profile-from-start off`:
     N = 2^15, 8 primes, matmul_cp 128x768 @ 768x256 (96 plaintext terms per
     output as in the BERT-base products, 2.2 GB of byte-sliced diagonals, larger
@@ -1180,8 +1188,8 @@ def ncu_case(seqs=1, ntt_split=None, ntt_radix=None):
     k = ctx.N // 2 // M
     rots = [b * M for b in range(1, B1)] + [g * B1 * M for g in range(1, k // B1)]
     keys = ctx.keygen(0, rots)
-    X, W = wl.cp_operands(M, D, 256, seed=1)
-    plan = ctx.cp_plan(M, D, W, 256, LEVEL, B1)
+    X, W = wl.cp_operands(M, D, d_out, seed=1)
+    plan = ctx.cp_plan(M, D, W, d_out, LEVEL, B1)
     seq = [[ctx.encrypt(keys, ctx.encode(z, LEVEL), 100 * s + i) for i, z in enumerate(pack_columns(X, M, k))]
            for s in range(seqs)]
     run = (lambda: ctx.matmul_cp_plan(keys, plan, seq[0])) if seqs == 1 else \
@@ -1192,7 +1200,7 @@ def ncu_case(seqs=1, ntt_split=None, ntt_radix=None):
     run()
     ctx.sync()
     torch.cuda.profiler.stop()
-    print(json.dumps({"ncu_case": f"matmul_cp 128x768 @ 768x256, N=2^15, level 7, {seqs} sequence(s)",
+    print(json.dumps({"ncu_case": f"matmul_cp 128x768 @ 768x{d_out}, N=2^15, level 7, {seqs} sequence(s)",
                       "plan": plan.info()}))
 
 
@@ -1288,6 +1296,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ncu-case", action="store_true", help="run the small profiling case and exit")
     ap.add_argument("--ncu-seqs", type=int, default=1, help="sequences in the profiling case")
+    ap.add_argument("--ncu-dout", type=int, default=256, help="output columns of the profiling case (2304: QKV)")
     ap.add_argument("--ncu-step", action="store_true", help="run one profiled BERT-base step and exit")
     ap.add_argument("--ncu-conv", action="store_true", help="run the conversion profiling case and exit")
     ap.add_argument("--ncu-cc", type=int, default=0, metavar="L",
@@ -1315,7 +1324,7 @@ def main():
                     help="skip the continuous-batching serving measurement")
     args = ap.parse_args()
     if args.ncu_case:
-        return ncu_case(args.ncu_seqs, args.ntt_split, args.ntt_radix)
+        return ncu_case(args.ncu_seqs, args.ntt_split, args.ntt_radix, args.ncu_dout)
     if args.ncu_step:
         return ncu_step(args.ntt_split, args.ntt_radix)
     if args.ncu_conv:

@@ -114,6 +114,13 @@ int blb_ctx_set_wait_limit(blb_ctx* ctx, uint64_t limit_ns);
  * above) instead of completing.  Products computed meanwhile are invalid.
  * 0 restores normal operation. */
 int blb_ctx_test_withhold_copies(blb_ctx* ctx, int withhold);
+/* Kernel of the plaintext products of batched matmul_cp calls (2, 4 or 8
+ * sequences per launch; single sequences always use the mma.sync kernel):
+ * 0 = automatic (tcgen05 for 8 sequences of a plan with one 16-output block,
+ * where it measured faster; mma.sync otherwise), 1 = the
+ * mma.sync kernel, 2 = the tcgen05 kernel (tensor-memory accumulators) where
+ * its operands fit shared memory.  Both give the same limbs. */
+int blb_ctx_set_batch_mac(blb_ctx* ctx, int kind);
 
 /* ---- keys (Sec. 2.4: rotations and products need switching keys) -----------
  * Secret key s (ternary) and switching keys drawn from Philox4x32-10 with key

@@ -87,6 +87,7 @@ SIGNATURES = {
     "blb_keyswitch_noalloc": (ctypes.c_int, [_vp, _vp, _i32, _vp, _u32, _vp]),
     "blb_ctx_set_wait_limit": (ctypes.c_int, [_vp, _u64]),
     "blb_ctx_test_withhold_copies": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "blb_ctx_set_batch_mac": (ctypes.c_int, [_vp, ctypes.c_int]),
     "blb_cp_plan_create": (ctypes.c_int, [_vp, _u32, _u32, _vp, _u32, _u32, ctypes.POINTER(_Sched), _pp]),
     "blb_cp_plan_create_diag": (ctypes.c_int, [_vp, _u32, _u32, _vp, _u32, _vp, _u32, _u32, ctypes.POINTER(_Sched), _pp]),
     "blb_cp_plan_free": (None, [_vp]),
@@ -314,6 +315,10 @@ class Context:
     def set_wait_limit(self, limit_ns):
         """Limit of the bounded device waits in nanoseconds (0 = 2 s)."""
         _check(lib().blb_ctx_set_wait_limit(self.h, _u64(limit_ns)))
+
+    def set_batch_mac(self, kind):
+        """MAC kernel of batched products: 0 automatic, 1 mma.sync, 2 tcgen05."""
+        _check(lib().blb_ctx_set_batch_mac(self.h, int(kind)))
 
     def test_withhold_copies(self, withhold):
         """Test hook: the matmul_cp copy stage issues nothing, so waits expire."""

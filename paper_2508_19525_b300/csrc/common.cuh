@@ -177,6 +177,7 @@ struct blb_ctx {
     uint32_t* d_status = nullptr;     // set by a kernel whose bounded wait expired
     uint64_t wait_ns = 0;             // limit of the bounded device waits (0: the 2 s default)
     uint32_t mac_withhold = 0;        // test hook: the plaintext streamer issues nothing (waits run out)
+    int batch_mac = 0;                // MAC kernel of batches: 0 automatic, 1 mma.sync, 2 tcgen05
     uint64_t* noalloc_scratch = nullptr;  // device address of the allocation-free key switch's array
     // conversions between CKKS and shares (built on first use): fixed-point
     // roots zeta^k (k < N), the inverse slot permutation, and twist tables
@@ -473,5 +474,8 @@ int cp_build_diagonals(blb_ctx* ctx, const blb_cp_plan* plan, const double* d_W,
                        double* d_z, const int32_t* d_head = nullptr, const int32_t* d_delta = nullptr,
                        uint32_t Dh = 0);
 int launch_cp_mac(blb_ctx* ctx, const blb_cp_plan* plan, const uint64_t* baby, uint64_t* T, uint32_t S);
+// the batched MAC on tcgen05 (mac_umma.cu); *used = false when the plan's
+// shape does not fit it
+int launch_cp_mac_umma(blb_ctx* c, const blb_cp_plan* P, const uint64_t* baby, uint64_t* T, uint32_t S, bool* used);
 int cp_plan_layout(blb_ctx* ctx, blb_cp_plan* plan);
 int cp_plan_store_block(blb_ctx* ctx, blb_cp_plan* plan, const uint64_t* src, uint32_t eblk);

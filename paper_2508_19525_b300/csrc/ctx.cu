@@ -605,6 +605,13 @@ extern "C" int blb_ctx_set_wait_limit(blb_ctx* c, uint64_t limit_ns)
     return BLB_OK;
 }
 
+extern "C" int blb_ctx_set_batch_mac(blb_ctx* c, int kind)
+{
+    if (!c || kind < 0 || kind > 2) return blb_fail(BLB_ERR_ARG, "kind must be 0, 1 or 2");
+    c->batch_mac = kind;
+    return BLB_OK;
+}
+
 extern "C" int blb_ctx_test_withhold_copies(blb_ctx* c, int withhold)
 {
     if (!c) return blb_fail(BLB_ERR_ARG, "null context");

@@ -706,6 +706,15 @@ int launch_cp_mac(blb_ctx* c, const blb_cp_plan* P, const uint64_t* baby, uint64
     // algorithmic bytes: the byte-sliced plaintexts once, the baby-step
     // ciphertexts once, the (e, g) partial sums written once
     ProfScope prof(c, "cp_mac", P->bytes + (S * terms * 2 * n + S * neg * 2 * n) * N * 8);
+    // batches: the tcgen05 kernel when chosen (blb_ctx_set_batch_mac) or, by
+    // default, for 8 sequences and a single 16-output block, where it measured
+    // faster on the B300 (wider plans and smaller batches: the mma.sync
+    // kernel); its operands must fit shared memory
+    if (S > 1 && (c->batch_mac == 2 || (c->batch_mac == 0 && S == 8 && P->NEB == 1))) {
+        bool used = false;
+        BLB_TRY(launch_cp_mac_umma(c, P, baby, T, S, &used));
+        if (used) return BLB_OK;
+    }
     MacArgs a{};
     a.T = T;
     a.baby = baby;

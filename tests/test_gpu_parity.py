@@ -288,8 +288,14 @@ def test_matmul_cp_batch_equals_per_sequence():
         X = wl.cp_operands(m, d, d_out, seed=10 + s)[0]
         seqs.append([ctx.encrypt(keys, ctx.encode(z, level), 10 * s + c)
                      for c, z in enumerate(pack_cols(X, m, k, (d + k - 1) // k))])
-    batched = ctx.matmul_cp_batch(keys, plan, seqs)
-    for s, X in enumerate(seqs):
-        single = ctx.matmul_cp_plan(keys, plan, X)
-        for a, b in zip(batched[s], single):
-            assert np.array_equal(ctx.ct_export(a), ctx.ct_export(b)), s
+    singles = [ctx.matmul_cp_plan(keys, plan, X) for X in seqs]
+    # both kernels of batched plaintext products: mma.sync (1) and tcgen05 (2),
+    # at 4 + 1 and at 2 sequences per launch
+    for kind in (0, 1, 2):
+        ctx.set_batch_mac(kind)
+        for group in (seqs, seqs[:2]):
+            batched = ctx.matmul_cp_batch(keys, plan, group)
+            for s in range(len(group)):
+                for a, b in zip(batched[s], singles[s]):
+                    assert np.array_equal(ctx.ct_export(a), ctx.ct_export(b)), (kind, len(group), s)
+    ctx.set_batch_mac(0)

@@ -94,6 +94,14 @@ def test_matmul_cp_batch_of_nine_at_96_terms_matches_the_oracle():
             assert np.array_equal(ctx.ct_export(y), ref[e]), (s, e)
         got = unpack_cols([ctx.decrypt(keys, y, coeffs=False)[1] for y in batched[s]], m, k, d_out)
         assert np.abs(got - X @ W).max() <= 1e-4
+    # both kernels of batched plaintext products (mma.sync and tcgen05) give these limbs
+    for kind in (1, 2):
+        ctx.set_batch_mac(kind)
+        again = ctx.matmul_cp_batch(keys, plan, [cts for _, _, cts in seqs])
+        for s in range(9):
+            for a, b in zip(again[s], batched[s]):
+                assert np.array_equal(ctx.ct_export(a), ctx.ct_export(b)), (kind, s)
+    ctx.set_batch_mac(0)
 
 
 @pytest.mark.parametrize("kind,L,Hg,R,b1s1,b1s2,c_chunk", [
