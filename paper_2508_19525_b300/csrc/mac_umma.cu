@@ -65,6 +65,7 @@ struct UmArgs {
     uint64_t nN, seq_words, wait_ns;
     uint32_t N, terms, KT, neg, NEB, CT;
     uint32_t tiles_per_limb, tiles, withhold, R;
+    uint32_t nacc, accw;  // tensor-memory accumulators and their column stride
     uint32_t limb[64];
     uint64_t off[64];
 };
@@ -124,6 +125,8 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
 
 // shared-memory matrix descriptor: canonical K-major layout without swizzle,
 // lbo = byte distance of core matrices adjacent along K, sbo = along M / N
+// (here the row-group stride: kc core matrices plus 16 bytes of padding, so
+// that the builders' stores to the 8 row groups hit different banks)
 __device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
 {
     return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
@@ -131,10 +134,10 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t
 }
 
 // byte offset of element (row, k) in a canonical K-major tile with kc core
-// matrices along K
+// matrices along K and a padded row-group stride
 __device__ __forceinline__ uint32_t canon(uint32_t row, uint32_t k, uint32_t kc)
 {
-    return ((row >> 3) * kc + (k >> 3)) * 128u + (row & 7u) * 16u + (k & 7u) * 2u;
+    return (row >> 3) * (kc * 128u + 16u) + (k >> 3) * 128u + (row & 7u) * 16u + (k & 7u) * 2u;
 }
 
 __device__ __forceinline__ uint64_t reduce128u(uint64_t lo, uint64_t hi, uint64_t q, uint64_t r0, uint64_t r1)
@@ -159,10 +162,10 @@ __global__ void __launch_bounds__(UM_THREADS, 1) k_cp_mac_umma(const __grid_cons
     constexpr int SP = G_::SP, NPAD = G_::NPAD;
     extern __shared__ __align__(1024) uint8_t smem[];
     const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const uint32_t KP = A.KT * 16, KC = A.KT * 2;
+    const uint32_t KC = A.KT * 2;
     const uint32_t item_bytes = A.KT * NB * 256;
-    const uint32_t a_bytes = 128 * KP * 2;          // one A operand
-    const uint32_t b_bytes = (uint32_t)NPAD * KP * 2;  // one coefficient's B operand
+    const uint32_t a_bytes = 16 * (KC * 128 + 16);             // one A operand (16 row groups)
+    const uint32_t b_bytes = (uint32_t)(NPAD / 8) * (KC * 128 + 16);  // one coefficient's B operand
     const uint32_t IPT = A.CT * A.NEB;
     // layout: ring | A[NA] | B[2][CT] | barriers
     uint8_t* ring = smem;
@@ -173,9 +176,10 @@ __global__ void __launch_bounds__(UM_THREADS, 1) k_cp_mac_umma(const __grid_cons
     const uint32_t UM_R = A.R;
     const uint32_t full0 = su32(bars), empty0 = full0 + 8 * UM_R, afull0 = empty0 + 8 * UM_R,
                    afree0 = afull0 + 8 * NA, bfull0 = afree0 + 8 * NA, bdone0 = bfull0 + 16, accf0 = bdone0 + 16,
-                   acce0 = accf0 + 16, fin = acce0 + 16;
-    volatile uint32_t* abort = reinterpret_cast<volatile uint32_t*>(bars + 2 * UM_R + 2 * NA + 9);
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 2 * UM_R + 2 * NA + 10);
+                   acce0 = accf0 + 8 * A.nacc, fin = acce0 + 8 * A.nacc;
+    const uint32_t NACC = A.nacc;
+    volatile uint32_t* abort = reinterpret_cast<volatile uint32_t*>(bars + 2 * UM_R + 2 * NA + 2 * NACC + 5);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 2 * UM_R + 2 * NA + 2 * NACC + 6);
 
     // zero A and B (padding rows and terms stay zero)
     for (uint32_t x = threadIdx.x; x < (NA * a_bytes + 2 * A.CT * b_bytes) / 16; x += UM_THREADS)
@@ -192,6 +196,8 @@ __global__ void __launch_bounds__(UM_THREADS, 1) k_cp_mac_umma(const __grid_cons
         for (int b = 0; b < 2; b++) {
             mb_init(bfull0 + 8 * b, 8);
             mb_init(bdone0 + 8 * b, 1);
+        }
+        for (uint32_t b = 0; b < NACC; b++) {
             mb_init(accf0 + 8 * b, 1);
             mb_init(acce0 + 8 * b, 8);
         }
@@ -200,7 +206,7 @@ __global__ void __launch_bounds__(UM_THREADS, 1) k_cp_mac_umma(const __grid_cons
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 1) {  // 256 columns: two accumulators of up to 128 fp32 columns
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tslot)), "r"(256)
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tslot)), "r"(512)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -242,16 +248,16 @@ __global__ void __launch_bounds__(UM_THREADS, 1) k_cp_mac_umma(const __grid_cons
                 if (!mb_wait(bfull0 + 8 * bb, (lt >> 1) & 1, abort, wlim)) break;
                 bool ok = true;
                 for (uint32_t it = 0; it < IPT && ok; it++) {
-                    const uint32_t g = lt * IPT + it, ab = g & 1, jj = it / A.NEB, an = g % NA;
+                    const uint32_t g = lt * IPT + it, ab = g % NACC, jj = it / A.NEB, an = g % NA;
                     ok = mb_wait(afull0 + 8 * an, (g / NA) & 1, abort, wlim);
-                    if (ok && g >= 2) ok = mb_wait(acce0 + 8 * ab, ((g >> 1) - 1) & 1, abort, wlim);
+                    if (ok && g >= NACC) ok = mb_wait(acce0 + 8 * ab, ((g / NACC) - 1) & 1, abort, wlim);
                     if (!ok) break;
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                     const uint32_t a0 = su32(abuf + an * a_bytes), b0 = su32(bbuf + (bb * A.CT + jj) * b_bytes);
-                    const uint32_t d = tmem + ab * 128;
+                    const uint32_t d = tmem + ab * A.accw;
                     for (uint32_t ks = 0; ks < A.KT; ks++) {
-                        const uint64_t ad = sdesc(a0 + ks * 256, 128, KC * 128);
-                        const uint64_t bd = sdesc(b0 + ks * 256, 128, KC * 128);
+                        const uint64_t ad = sdesc(a0 + ks * 256, 128, KC * 128 + 16);
+                        const uint64_t bd = sdesc(b0 + ks * 256, 128, KC * 128 + 16);
                         asm volatile(
                             "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
                             " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d),
@@ -413,8 +419,8 @@ __global__ void __launch_bounds__(UM_THREADS, 1) k_cp_mac_umma(const __grid_cons
             const uint64_t q = A.q[i], r0 = A.bar[2 * i], r1 = A.bar[2 * i + 1];
             bool ok = true;
             for (uint32_t it = 0; it < IPT; it++) {
-                const uint32_t g = lt * IPT + it, ab = g & 1, jj = it / A.NEB, eblk = it % A.NEB;
-                ok = mb_wait(accf0 + 8 * ab, (g >> 1) & 1, abort, wlim);
+                const uint32_t g = lt * IPT + it, ab = g % NACC, jj = it / A.NEB, eblk = it % A.NEB;
+                ok = mb_wait(accf0 + 8 * ab, (g / NACC) & 1, abort, wlim);
                 if (!__all_sync(0xffffffffu, ok)) {
                     ok = false;
                     break;
@@ -423,7 +429,7 @@ __global__ void __launch_bounds__(UM_THREADS, 1) k_cp_mac_umma(const __grid_cons
                 uint64_t P0[SH], P1[SH];
 #pragma unroll
                 for (int u = 0; u < SH; u++) P0[u] = P1[u] = 0;
-                const uint32_t taddr = tmem + ((quarter * 32u) << 16) + ab * 128 + h * SH;
+                const uint32_t taddr = tmem + ((quarter * 32u) << 16) + ab * A.accw + h * SH;
                 uint32_t r[NB][SH];
 #pragma unroll
                 for (int b = 0; b < NB; b++) {
@@ -517,14 +523,14 @@ __global__ void __launch_bounds__(UM_THREADS, 1) k_cp_mac_umma(const __grid_cons
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (warp == 1)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
 }
 
 // shared memory of one CTA: ring, two A operands, two tiles of CT B operands, barriers
 size_t umma_smem(uint32_t S, uint32_t NB, uint32_t KT, uint32_t CT, uint32_t NA = 2, uint32_t R = 4)
 {
-    const size_t KP = (size_t)KT * 16, npad = (NB * 2 * S + 15) / 16 * 16;
-    return R * (size_t)KT * NB * 256 + NA * 128 * KP * 2 + 2 * CT * npad * KP * 2 + 8 * (2 * R + 2 * NA + 11);
+    const size_t grp = (size_t)KT * 2 * 128 + 16, npad = (NB * 2 * S + 15) / 16 * 16;  // padded row-group stride
+    return R * (size_t)KT * NB * 256 + NA * 16 * grp + 2 * CT * (npad / 8) * grp + 8 * (2 * R + 2 * NA + 2 * 8 + 7);
 }
 constexpr size_t UM_SMEM_MAX = 225u << 10;
 
@@ -542,6 +548,11 @@ int launch_umma(blb_ctx* c, UmArgs& a, uint32_t nlimbs, bool* used)
     if (umma_smem(S, NB, a.KT, a.CT, 3, R) <= UM_SMEM_MAX) NA = 3;
     a.R = R;
     const bool three = NA == 3;
+    // accumulators: as many as the 512 tensor-memory columns hold, up to 8, at
+    // a power-of-two column stride
+    a.accw = 32;
+    while (a.accw < (uint32_t)UmShape<S, NB>::NPAD) a.accw <<= 1;
+    a.nacc = std::min<uint32_t>(8, 512 / a.accw);
     a.tiles_per_limb = c->N / a.CT;
     a.tiles = a.tiles_per_limb * nlimbs;
     static std::atomic<bool> attr[64];
@@ -555,8 +566,11 @@ int launch_umma(blb_ctx* c, UmArgs& a, uint32_t nlimbs, bool* used)
     }
     BLB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     const uint32_t grid = std::min<uint32_t>(a.tiles, (uint32_t)sms);
-    if (three) k_cp_mac_umma<S, NB, 3><<<grid, UM_THREADS, umma_smem(S, NB, a.KT, a.CT, 3, R), c->stream>>>(a);
-    else k_cp_mac_umma<S, NB, 2><<<grid, UM_THREADS, umma_smem(S, NB, a.KT, a.CT, 2, R), c->stream>>>(a);
+    // one CTA per SM (it allocates all 512 tensor-memory columns): the request
+    // never lets a second CTA fit next to it
+    const size_t smem = std::max<size_t>(umma_smem(S, NB, a.KT, a.CT, three ? 3 : 2, R), 120u << 10);
+    if (three) k_cp_mac_umma<S, NB, 3><<<grid, UM_THREADS, smem, c->stream>>>(a);
+    else k_cp_mac_umma<S, NB, 2><<<grid, UM_THREADS, smem, c->stream>>>(a);
     BLB_LAUNCHED();
     *used = true;
     return BLB_OK;
