@@ -918,9 +918,13 @@ static int cp_run(blb_ctx* c, const blb_keys* const* Ks, const blb_cp_plan* P, b
             rc = ks_run(c, P->level, src.data(), (uint32_t)src.size(), prod.data(), grp.data(), (uint32_t)grp.size(),
                         adds.data(), 0);
     }
-    // plaintext products for every (sequence, e, g), at most 8 sequences per launch
+    // plaintext products for every (sequence, e, g): at most 8 sequences per
+    // launch, and by default at most 4 for plans of several 16-output blocks,
+    // where two 4-sequence launches measured faster than one of 8 on the B300
+    // (the 8-sequence mma.sync kernel runs out of registers for its warps)
+    const uint32_t maxw = (c->batch_mac == 0 && P->NEB > 1) ? 4 : 8;
     for (uint32_t s0 = 0; !rc && s0 < S;) {
-        uint32_t chunk = S - s0 >= 8 ? 8 : S - s0 >= 4 ? 4 : S - s0 >= 2 ? 2 : 1;
+        uint32_t chunk = S - s0 >= 8 && maxw >= 8 ? 8 : S - s0 >= 4 ? 4 : S - s0 >= 2 ? 2 : 1;
         rc = launch_cp_mac(c, P, baby + (size_t)s0 * nX * P->b1 * ctw, T + (size_t)s0 * P->nY * P->G * ctw, chunk);
         s0 += chunk;
     }
