@@ -957,7 +957,8 @@ def run_blb(args):
         batched = {"sequences_per_step": args.batch, "value": round(bval, 3), "unit": UNIT,
                    "ms_per_step": round(bsec * 1e3 / bsteps, 3), "speedup_vs_plain": round(bval / value, 3),
                    "site_ms_one_step": bsites,
-                   "mac_kernel": "tcgen05.mma (tensor memory accumulators) for 2, 4 and 8 sequences per launch"}
+                   "mac_kernel": "automatic: mma.sync in 4-sequence launches for these plans (nine and three 16-output "
+                                 "blocks); the tcgen05 kernel is chosen for single-block plans at 8 sequences"}
     # the same step with its products, masking and decryption replayed from a
     # CUDA graph (inputs encrypted eagerly every step)
     gstep = w.graph_step()
