@@ -487,14 +487,6 @@ uint64_t blb_kernel_launches(void);
  * traffic of the operation: NTT one read and one write per word; key switch
  * its input, the used key digits and its output; cp_mac every plaintext, every
  * baby-step ciphertext and every partial sum once).  Enabling resets the sums. */
-/* Integer-pipe throughput for the ALU rooflines: register-only kernels on
- * every SM run independent chains of (a) the NTT's lazy butterfly on 64-bit
- * words (a Shoup product by a constant, then X + WY and X - WY + 2q) and (b)
- * the base conversions' 64 x 64 -> 128-bit multiply-accumulate.  Outputs
- * (nullable): operations per second, and per SM cycle (the SM clock measured
- * during the run from %globaltimer and clock64). */
-int blb_int_peaks(blb_ctx* ctx, double* bfly_per_s, double* mad128_per_s, double* bfly_per_sm_cycle,
-                  double* mad128_per_sm_cycle);
 int blb_profile_enable(blb_ctx* ctx, int on);
 int blb_profile_read(blb_ctx* ctx, const char* site, double* ms, uint64_t* count, uint64_t* bytes);
 

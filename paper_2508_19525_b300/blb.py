@@ -116,7 +116,6 @@ SIGNATURES = {
     "blb_ntt_set_split": (ctypes.c_int, [_vp, ctypes.c_int]),
     "blb_ntt_set_radix": (ctypes.c_int, [_vp, ctypes.c_int]),
     "blb_kernel_launches": (_u64, []),
-    "blb_int_peaks": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
     "blb_profile_enable": (ctypes.c_int, [_vp, ctypes.c_int]),
     "blb_profile_read": (ctypes.c_int, [_vp, ctypes.c_char_p, _vp, _vp, _vp]),
 }
@@ -638,14 +637,6 @@ class Context:
         out = (ctypes.c_void_p * count)()
         _check(lib().blb_he2mpc_batch(self.h, keys.h, cs, count, ns.ctypes.data, out, _ptr(share_out)))
         return [Ciphertext(self, c) for c in out], share_out
-
-    def int_peaks(self):
-        """Measured integer-pipe rates: butterflies and 64x64->128 MACs per
-        second and per SM cycle."""
-        a, b, c_, d = _dbl(), _dbl(), _dbl(), _dbl()
-        _check(lib().blb_int_peaks(self.h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c_), ctypes.byref(d)))
-        return {"bfly_per_s": a.value, "mad128_per_s": b.value, "bfly_per_sm_cycle": c_.value,
-                "mad128_per_sm_cycle": d.value}
 
     def profile(self, on=True):
         _check(lib().blb_profile_enable(self.h, int(on)))

@@ -24,7 +24,7 @@ def _stale():
     if not os.path.exists(LIB):
         return True
     deps = sources() + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))]
-    deps += [os.path.join(ROOT, "include", "blb.h"), __file__]
+    deps += [os.path.join(ROOT, "include", "blb.h"), __file__, CSRC]  # the directory: a source removed
     return max(os.path.getmtime(f) for f in deps) > os.path.getmtime(LIB)
 
 
@@ -63,6 +63,25 @@ def build(force=False, verbose=False, extra=(), asan=False):
     return LIB
 
 
+PEAKS_SRC = os.path.join(HERE, "peaks", "peaks.cu")
+PEAKS_LIB = os.path.join(HERE, "libblb_peaks.so")
+
+
+def build_peaks(force=False):
+    """The benchmark's integer-rate microbenchmark (include/blb_peaks.h) as a
+    library of its own, libblb_peaks.so: it is not part of libblb.so."""
+    if not force and os.path.exists(PEAKS_LIB) and os.path.getmtime(PEAKS_LIB) >= max(
+            os.path.getmtime(PEAKS_SRC), os.path.getmtime(os.path.join(ROOT, "include", "blb_peaks.h")), os.path.getmtime(__file__)):
+        return PEAKS_LIB
+    nvcc = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
+    cmd = [nvcc, *ARCH, *FLAGS, "-I", os.path.join(ROOT, "include"), "-shared", "-o", PEAKS_LIB + ".tmp", PEAKS_SRC,
+           "-lcudart"]
+    subprocess.run(cmd, check=True)
+    os.replace(PEAKS_LIB + ".tmp", PEAKS_LIB)
+    return PEAKS_LIB
+
+
 if __name__ == "__main__":
     print(build(force="--force" in sys.argv, verbose="-v" in sys.argv,
                 extra=["-Xptxas", "-v"] if "--ptxas" in sys.argv else [], asan="--asan" in sys.argv))
+    print(build_peaks(force="--force" in sys.argv))

@@ -1,5 +1,7 @@
 // peaks.cu -- integer-pipe throughput of the arithmetic units the NTT and the
-// base conversions are built from, for their ALU rooflines.
+// base conversions are built from, for their ALU rooflines.  A measurement
+// helper of the benchmark, built as its own library (libblb_peaks.so,
+// include/blb_peaks.h); nothing on the hot path uses it.
 //
 // The NTT's unit of work is the lazy Cooley-Tukey butterfly on 64-bit words
 // (one Shoup product by a constant twiddle, then X + WY and X - WY + 2q); the
@@ -10,9 +12,24 @@
 // CTA also reports its SM cycles and nanoseconds, whose ratio is the SM clock
 // during the run, so the rate is also known per SM cycle:
 // peak = rate per SM cycle x SMs x SM clock.
-#include "common.cuh"
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "blb_peaks.h"
 
 namespace {
+
+struct acc128 {
+    uint64_t lo, hi;
+};
+// acc += a b (mod 2^128), the multiply-add pair the base conversions use
+__device__ __forceinline__ void mad128(acc128& acc, uint64_t a, uint64_t b)
+{
+    asm("mad.lo.cc.u64 %0, %2, %3, %0;\n\t"
+        "madc.hi.u64 %1, %2, %3, %1;"
+        : "+l"(acc.lo), "+l"(acc.hi)
+        : "l"(a), "l"(b));
+}
 
 constexpr int PK_T = 256;
 constexpr int PK_CHAINS = 8;
@@ -91,41 +108,44 @@ __global__ void __launch_bounds__(PK_T) k_peak_mad128(uint64_t* __restrict__ out
 
 }  // namespace
 
-extern "C" int blb_int_peaks(blb_ctx* c, double* bfly_per_s, double* mad128_per_s, double* bfly_per_sm_cycle,
-                             double* mad128_per_sm_cycle)
+extern "C" int blb_peaks_int_rates(uint64_t q, void* stream, double* bfly_per_s, double* mad128_per_s,
+                                   double* bfly_per_sm_cycle, double* mad128_per_sm_cycle)
 {
-    if (!c) return blb_fail(BLB_ERR_ARG, "null argument");
-    int dev, sms;
-    BLB_CUDA(cudaGetDevice(&dev));
-    BLB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    if (q < 3 || !(q & 1)) return -1;
+    cudaStream_t st = (cudaStream_t)stream;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return -6;
     const uint32_t blocks = (uint32_t)sms * 8, iters = 4096;
-    Scratch S(c);
-    uint64_t* out = (uint64_t*)S.get((size_t)blocks * PK_T * 8);
-    unsigned long long* cyc = (unsigned long long*)S.get(16);
-    if (!out || !cyc) return blb_fail(BLB_ERR_OOM, "peak buffers");
+    uint64_t* out = nullptr;
+    unsigned long long* cyc = nullptr;
+    if (cudaMalloc(&out, (size_t)blocks * PK_T * 8) != cudaSuccess) return -5;
+    if (cudaMalloc(&cyc, 16) != cudaSuccess) {
+        cudaFree(out);
+        return -5;
+    }
     cudaEvent_t e0, e1;
-    BLB_CUDA(cudaEventCreate(&e0));
-    BLB_CUDA(cudaEventCreate(&e1));
-    const uint64_t q = c->q[0];
-    const uint64_t w = (q >> 3) + 12345, wp = shoup_companion(w, q);
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    // a constant twiddle and its Shoup companion floor(w 2^64 / q)
+    const uint64_t w = (q >> 3) + 12345, wp = (uint64_t)(((unsigned __int128)w << 64) / q);
     double res[2][2] = {{0, 0}, {0, 0}};
-    int rc = BLB_OK;
+    int rc = 0;
     for (int kind = 0; kind < 2 && !rc; kind++) {
         for (int rep = 0; rep < 2 && !rc; rep++) {  // the first run warms up the clocks
-            if (cudaMemsetAsync(cyc, 0, 16, c->stream) != cudaSuccess) rc = blb_fail(BLB_ERR_CUDA, "memset");
-            cudaEventRecord(e0, c->stream);
+            if (cudaMemsetAsync(cyc, 0, 16, st) != cudaSuccess) rc = -6;
+            cudaEventRecord(e0, st);
             if (kind == 0)
-                k_peak_bfly<<<blocks, PK_T, 0, c->stream>>>(out, cyc, w, wp, q, iters);
+                k_peak_bfly<<<blocks, PK_T, 0, st>>>(out, cyc, w, wp, q, iters);
             else
-                k_peak_mad128<<<blocks, PK_T, 0, c->stream>>>(out, cyc, w, wp, iters);
-            if (cudaGetLastError() != cudaSuccess) rc = blb_fail(BLB_ERR_CUDA, "peak kernel launch failed");
-            blb_count_launch();
-            cudaEventRecord(e1, c->stream);
-            if (cudaEventSynchronize(e1) != cudaSuccess) rc = blb_fail(BLB_ERR_CUDA, "peak kernel failed");
+                k_peak_mad128<<<blocks, PK_T, 0, st>>>(out, cyc, w, wp, iters);
+            if (cudaGetLastError() != cudaSuccess) rc = -6;
+            cudaEventRecord(e1, st);
+            if (cudaEventSynchronize(e1) != cudaSuccess) rc = -6;
             float ms = 0;
             cudaEventElapsedTime(&ms, e0, e1);
             unsigned long long cn[2] = {0, 0};
-            if (cudaMemcpy(cn, cyc, 16, cudaMemcpyDeviceToHost) != cudaSuccess) rc = blb_fail(BLB_ERR_CUDA, "copy");
+            if (cudaMemcpy(cn, cyc, 16, cudaMemcpyDeviceToHost) != cudaSuccess) rc = -6;
             const double ops = (double)blocks * PK_T * iters * PK_CHAINS;
             const double ghz = cn[1] ? (double)cn[0] / (double)cn[1] : 1.0;  // SM cycles per ns
             res[kind][0] = ops / (ms / 1e3);
@@ -134,10 +154,12 @@ extern "C" int blb_int_peaks(blb_ctx* c, double* bfly_per_s, double* mad128_per_
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    cudaFree(out);
+    cudaFree(cyc);
     if (rc) return rc;
     if (bfly_per_s) *bfly_per_s = res[0][0];
     if (bfly_per_sm_cycle) *bfly_per_sm_cycle = res[0][1];
     if (mad128_per_s) *mad128_per_s = res[1][0];
     if (mad128_per_sm_cycle) *mad128_per_sm_cycle = res[1][1];
-    return BLB_OK;
+    return 0;
 }

@@ -64,3 +64,15 @@ def test_context_without_device_fails_cleanly():
     rc = blb.lib().blb_ctx_create(ctypes.byref(p), None, ctypes.byref(h))
     assert rc == blb.ERR_CUDA and not h.value
     assert blb.last_error()
+
+
+def test_peaks_library_exports_its_declared_symbol():
+    """The benchmark's integer-rate microbenchmark lives in a library of its own
+    (include/blb_peaks.h, libblb_peaks.so), not in libblb.so."""
+    src = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "blb_peaks.h")).read(), flags=re.S)
+    names = set(re.findall(r"\b(blb_[a-z0-9_]+)\s*\(", src))
+    assert names == {"blb_peaks_int_rates"}
+    L = ctypes.CDLL(build.build_peaks())
+    for n in names:
+        assert hasattr(L, n)
+        assert not hasattr(blb.lib(), n)
