@@ -316,6 +316,7 @@ struct DevProduct {
     uint32_t src;
     uint64_t g;
     const uint64_t* key;
+    uint64_t ginv;  // g^-1 mod 2N: the output position whose digits are read at k' is perm(k', ginv)
 };
 struct DevGroup {
     uint64_t* out0;
@@ -484,6 +485,76 @@ __global__ void __launch_bounds__(256, 6) k_ksb_finish(const DevGroup* __restric
     }
 }
 
+// The finish of a pass whose groups are single rotations of shared sources
+// (hoisted rotations): one thread per (digit position k', prime i, source)
+// reads the source's extended digits at k' once and serves every rotation of
+// that source, whose output position is the k with perm(k, g) = k', i.e.
+// k = perm(k', g^-1); per rotation as k_ksb_finish: the ciphertext-prime inner
+// product with its key, the ModDown finish and the addends.  (k_ksb_finish reads
+// the digits again for every rotation.)
+template <int NB>
+__global__ void __launch_bounds__(256, 6) k_ksb_finish_src(const DevGroup* __restrict__ groups,
+                                 const DevProduct* __restrict__ prods, const uint64_t* __restrict__ ext,
+                                 const KsAdd* __restrict__ adds, const uint64_t* __restrict__ cv,
+                                 const uint32_t* __restrict__ so, const uint32_t* __restrict__ sg, uint32_t n,
+                                 uint32_t E, uint32_t beta, uint32_t np, PInv pinv, const uint64_t* __restrict__ qs,
+                                 const uint64_t* __restrict__ bar, uint32_t logN)
+{
+    constexpr int VN = NB > 0 ? NB : BLB_MAXP;
+    const uint32_t N = 1u << logN;
+    const uint32_t kp = blockIdx.x * blockDim.x + threadIdx.x, i = blockIdx.y, s = blockIdx.z;
+    if (kp >= N) return;
+    const uint64_t q = qs[i], r0 = bar[2 * i], r1 = bar[2 * i + 1];
+    const uint64_t* xs = ext + (size_t)s * beta * E * N + (size_t)i * N + kp;
+    uint64_t v[VN];
+#pragma unroll
+    for (uint32_t j = 0; j < (NB > 0 ? (uint32_t)NB : beta); j++) v[j] = xs[(size_t)j * E * N];
+    for (uint32_t x = so[s]; x < so[s + 1]; x++) {
+        const uint32_t gr = sg[x];
+        const DevGroup G = groups[gr];
+        const DevProduct P = prods[G.prod0];
+        const uint32_t k = perm_index(kp, logN, P.ginv);
+        acc128 a0{0, 0}, a1{0, 0};
+#pragma unroll
+        for (uint32_t j = 0; j < (NB > 0 ? (uint32_t)NB : beta); j++) {
+            mad128(a0, v[j], P.key[(((size_t)j * 2 + 0) * np + i) * N + k]);
+            mad128(a1, v[j], P.key[(((size_t)j * 2 + 1) * np + i) * N + k]);
+        }
+        const uint64_t sm[2] = {barrett128(a0.lo, a0.hi, q, r0, r1), barrett128(a1.lo, a1.hi, q, r0, r1)};
+#pragma unroll
+        for (uint32_t p = 0; p < 2; p++) {
+            const uint64_t c = cv[(((size_t)gr * 2 + p) * n + i) * N + k];
+            uint64_t r = mul_shoup(sub_mod(sm[p], c, q), pinv.w[i], pinv.wp[i], q);
+            for (uint32_t y = G.add0; y < G.add1; y++) {
+                const KsAdd A = adds[y];
+                if (A.poly == p) r = add_mod(r, A.ptr[(size_t)i * N + perm_index(k, logN, A.g)], q);
+            }
+            (p ? G.out1 : G.out0)[(size_t)i * N + k] = r;
+        }
+    }
+}
+
+// g^-1 mod m for odd g and m a power of two (Newton's iteration doubles the
+// correct low bits: 3 -> 6 -> ... -> 96)
+uint64_t inv_mod_pow2(uint64_t g, uint64_t m)
+{
+    uint64_t x = g;
+    for (int it = 0; it < 5; it++) x *= 2 - g * x;
+    return x & (m - 1);
+}
+
+template <typename... Args>
+void launch_finish_src(uint32_t beta, dim3 grid, cudaStream_t st, Args... args)
+{
+    switch (beta) {
+    case 1: k_ksb_finish_src<1><<<grid, kT, 0, st>>>(args...); break;
+    case 2: k_ksb_finish_src<2><<<grid, kT, 0, st>>>(args...); break;
+    case 3: k_ksb_finish_src<3><<<grid, kT, 0, st>>>(args...); break;
+    case 4: k_ksb_finish_src<4><<<grid, kT, 0, st>>>(args...); break;
+    default: k_ksb_finish_src<0><<<grid, kT, 0, st>>>(args...); break;
+    }
+}
+
 // launches with the digit count as a compile-time bound where it is small
 template <typename... Args>
 void launch_inner(uint32_t beta, dim3 grid, cudaStream_t st, Args... args)
@@ -583,11 +654,25 @@ int ks_run(blb_ctx* ctx, uint32_t level, const KsSource* sources, uint32_t n_src
             hg[g].out1 = G.out1;
             hg[g].prod0 = (uint32_t)hp.size();
             for (uint32_t x = G.prod0; x < G.prod1; x++)
-                hp.push_back(DevProduct{(uint32_t)local[prods[x].src], prods[x].g, prods[x].key});
+                hp.push_back(DevProduct{(uint32_t)local[prods[x].src], prods[x].g, prods[x].key,
+                                        inv_mod_pow2(prods[x].g, 2ull * N)});
             hg[g].prod1 = (uint32_t)hp.size();
             hg[g].add0 = (uint32_t)ha.size();
             for (uint32_t x = G.add0; x < G.add1; x++) ha.push_back(adds[x]);
             hg[g].add1 = (uint32_t)ha.size();
+        }
+        // the finish by source when every group is one rotation of a shared
+        // source (hoisted passes): the rotations of each source in one list
+        bool by_src = !accumulate && ns > 0 && ng >= 2 * ns;
+        for (uint32_t g = 0; g < ng && by_src; g++) by_src = hg[g].prod1 == hg[g].prod0 + 1;
+        std::vector<uint32_t> so, sg;
+        if (by_src) {
+            so.assign(ns + 1, 0);
+            for (uint32_t g = 0; g < ng; g++) so[hp[hg[g].prod0].src + 1]++;
+            for (uint32_t s = 0; s < ns; s++) so[s + 1] += so[s];
+            sg.assign(ng, 0);
+            std::vector<uint32_t> fill(so.begin(), so.end() - 1);
+            for (uint32_t g = 0; g < ng; g++) sg[fill[hp[hg[g].prod0].src]++] = g;
         }
         std::vector<uint32_t> ext_rows, p_rows;
         for (uint32_t s = 0; s < ns; s++)
@@ -599,7 +684,7 @@ int ks_run(blb_ctx* ctx, uint32_t level, const KsSource* sources, uint32_t n_src
         auto words = [](size_t bytes) { return (bytes + 7) / 8; };
         const size_t table_words = words(hs.size() * sizeof(DevSource)) + words(hp.size() * sizeof(DevProduct)) +
                                    words(hg.size() * sizeof(DevGroup)) + words(ha.size() * sizeof(KsAdd)) +
-                                   words((ext_rows.size() + p_rows.size()) * 4) + 8;
+                                   words((ext_rows.size() + p_rows.size()) * 4) + words((so.size() + sg.size()) * 4) + 8;
         const bool cap = capturing(ctx);
         if (cap) ctx->captured = true;
         // under capture the tables go to a buffer of their own, so the arena
@@ -637,6 +722,8 @@ int ks_run(blb_ctx* ctx, uint32_t level, const KsSource* sources, uint32_t n_src
         tw += words(ha.size() * sizeof(KsAdd));
         uint32_t* d_ext_rows = (uint32_t*)tw;
         uint32_t* d_p_rows = d_ext_rows + ext_rows.size();
+        uint32_t* d_so = d_p_rows + p_rows.size();
+        uint32_t* d_sg = d_so + so.size();
         if (cap) {
             // fill the host image, copy it once, and point every table into the copy
             memcpy(d_src, hs.data(), hs.size() * sizeof(DevSource));
@@ -645,6 +732,8 @@ int ks_run(blb_ctx* ctx, uint32_t level, const KsSource* sources, uint32_t n_src
             memcpy(d_add, ha.data(), ha.size() * sizeof(KsAdd));
             memcpy(d_ext_rows, ext_rows.data(), ext_rows.size() * 4);
             memcpy(d_p_rows, p_rows.data(), p_rows.size() * 4);
+            memcpy(d_so, so.data(), so.size() * 4);
+            memcpy(d_sg, sg.data(), sg.size() * 4);
             void* dev = nullptr;
             BLB_TRY(persist_upload(ctx, host_tables.data(), table_words * 8, &dev));
             auto rebase = [&](auto* p) { return (decltype(p))((uint8_t*)dev + ((uint8_t*)p - (uint8_t*)tw0)); };
@@ -654,6 +743,8 @@ int ks_run(blb_ctx* ctx, uint32_t level, const KsSource* sources, uint32_t n_src
             d_add = rebase(d_add);
             d_ext_rows = rebase(d_ext_rows);
             d_p_rows = rebase(d_p_rows);
+            d_so = rebase(d_so);
+            d_sg = rebase(d_sg);
         } else {
             auto up = [&](void* dst, const void* src, size_t bytes) {
                 return bytes ? cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, ctx->stream) : cudaSuccess;
@@ -664,6 +755,8 @@ int ks_run(blb_ctx* ctx, uint32_t level, const KsSource* sources, uint32_t n_src
             BLB_CUDA(up(d_add, ha.data(), ha.size() * sizeof(KsAdd)));
             BLB_CUDA(up(d_ext_rows, ext_rows.data(), ext_rows.size() * 4));
             BLB_CUDA(up(d_p_rows, p_rows.data(), p_rows.size() * 4));
+            BLB_CUDA(up(d_so, so.data(), so.size() * 4));
+            BLB_CUDA(up(d_sg, sg.data(), sg.size() * 4));
         }
         // algorithmic bytes: each source read and its digits written once; each
         // product reads its digits and key; each group writes its output
@@ -690,9 +783,15 @@ int ks_run(blb_ctx* ctx, uint32_t level, const KsSource* sources, uint32_t n_src
                             (const uint64_t*)ctx->d_q, (const uint64_t*)ctx->d_bar, N);
         BLB_LAUNCHED();
         BLB_TRY(ntt_forward(ctx, cv, ng * 2 * n, ctx->qmap(n)));
-        launch_finish(beta, dim3(gx, n, ng), ctx->stream, (const DevGroup*)d_grp, (const DevProduct*)d_prod,
-                      (const uint64_t*)ext, (const KsAdd*)d_add, (const uint64_t*)cv, n, E, beta, ctx->np, pinv,
-                      (const uint64_t*)ctx->d_q, (const uint64_t*)ctx->d_bar, ctx->logN, accumulate);
+        if (by_src)
+            launch_finish_src(beta, dim3(gx, n, ns), ctx->stream, (const DevGroup*)d_grp, (const DevProduct*)d_prod,
+                              (const uint64_t*)ext, (const KsAdd*)d_add, (const uint64_t*)cv, (const uint32_t*)d_so,
+                              (const uint32_t*)d_sg, n, E, beta, ctx->np, pinv, (const uint64_t*)ctx->d_q,
+                              (const uint64_t*)ctx->d_bar, ctx->logN);
+        else
+            launch_finish(beta, dim3(gx, n, ng), ctx->stream, (const DevGroup*)d_grp, (const DevProduct*)d_prod,
+                          (const uint64_t*)ext, (const KsAdd*)d_add, (const uint64_t*)cv, n, E, beta, ctx->np, pinv,
+                          (const uint64_t*)ctx->d_q, (const uint64_t*)ctx->d_bar, ctx->logN, accumulate);
         BLB_LAUNCHED();
         for (uint32_t s : used) local[s] = -1;
         g0 = g1;
