@@ -170,6 +170,11 @@ struct blb_ctx {
     uint64_t* d_bar = nullptr;        // [np][2]: floor(2^128/q) lo, hi
     uint64_t* d_tw = nullptr;         // [np][2][N] pairs (w, shoup): psi^brv(k), then psi^-brv(k)
     uint64_t* d_ninv = nullptr;       // [np][2]: N^-1, shoup
+    // [level][np][2]: N^-1 (S/s)^-1 mod s and its Shoup companion, where S is the
+    // product of the conversion sources s belongs to at that level (its ModUp
+    // digit for a ciphertext prime, P for a special prime): the inverse NTT
+    // that feeds a base conversion applies the conversion's first factor
+    uint64_t* d_ninv_conv = nullptr;
     double2* d_zeta = nullptr;        // [N]: (cos, sin)(pi k / N)
     uint64_t* d_cdt = nullptr;        // [19]
     uint32_t* d_kperm = nullptr;      // [N/2]: k_j = (5^j mod 2N - 1)/4
@@ -351,6 +356,11 @@ int ntt_inverse(blb_ctx* ctx, uint64_t* data, uint32_t rows, const LimbMap& map)
 // same on an explicit device row list: entry = row index | prime index << 24
 int ntt_forward_list(blb_ctx* ctx, uint64_t* data, uint32_t rows, const uint32_t* d_rowlist);
 int ntt_inverse_list(blb_ctx* ctx, uint64_t* data, uint32_t rows, const uint32_t* d_rowlist);
+// inverse NTT whose last pass multiplies by ninv[2 pi] (Shoup companion at
+// ninv[2 pi + 1]) instead of N^-1 mod q_pi
+int ntt_inverse_scaled(blb_ctx* ctx, uint64_t* data, uint32_t rows, const LimbMap& map, const uint64_t* ninv);
+int ntt_inverse_list_scaled(blb_ctx* ctx, uint64_t* data, uint32_t rows, const uint32_t* d_rowlist,
+                            const uint64_t* ninv);
 
 // element-wise (row r uses prime map.p[r % map.n]; operand b repeats every
 // b_rows rows)

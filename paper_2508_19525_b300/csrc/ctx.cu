@@ -498,6 +498,20 @@ extern "C" int blb_ctx_create(const blb_params* params, void* stream, blb_ctx** 
         build_conv(c, src, dst, row, c->h_moddown);
         if ((rc = upload(c, &c->d_moddown, &c->h_moddown, 1))) return fail(rc);
     }
+    {
+        std::vector<uint64_t> nc((size_t)c->nQ * np * 2);
+        for (uint32_t l = 0; l < c->nQ; l++)
+            for (uint32_t pi = 0; pi < np; pi++) {
+                const uint64_t q = c->q[pi], ni = host_invmod(N, q);
+                uint64_t f = 1;
+                if (pi >= c->nQ) f = c->h_moddown.hat_inv[pi - c->nQ];
+                else if (pi <= l) f = c->h_modup[(size_t)l * c->dnum + pi / c->alpha].hat_inv[pi % c->alpha];
+                const uint64_t w = host_mulmod(ni, f, q);
+                nc[((size_t)l * np + pi) * 2] = w;
+                nc[((size_t)l * np + pi) * 2 + 1] = shoup_companion(w, q);
+            }
+        if ((rc = upload(c, &c->d_ninv_conv, nc.data(), nc.size()))) return fail(rc);
+    }
 
     // scratch arena: key-switch region + operation temporaries
     {
@@ -546,6 +560,7 @@ static void ctx_destroy(blb_ctx* c)
     dev_free(c, c->d_bar, c->np * 16);
     dev_free(c, c->d_tw, (size_t)c->np * 4 * c->N * 8);
     dev_free(c, c->d_ninv, c->np * 16);
+    dev_free(c, c->d_ninv_conv, (size_t)c->nQ * c->np * 16);
     dev_free(c, c->d_zeta, (size_t)c->N * sizeof(double2));
     dev_free(c, c->d_cdt, 19 * 8);
     dev_free(c, c->d_kperm, (size_t)c->N / 2 * 4);

@@ -53,8 +53,9 @@ __global__ void k_conv(const uint64_t* __restrict__ src, size_t src_ps, const Co
 // y_k < p_k) with the carries counted: the exact rounding unless the fraction
 // is within 2^-65 of 1/2, and no FP64 (a small fraction of B300's integer rate).
 // NS > 0: at most NS source primes, the y_k in registers (NS = 0: any count,
-// the y_k in a local array)
-template <int NS>
+// the y_k in a local array).  PRE: the source rows already hold y_k (the
+// inverse NTT that produced them multiplied by (P/p_k)^-1 with N^-1).
+template <int NS, bool PRE>
 __global__ void k_moddown_conv(const uint64_t* __restrict__ src, size_t src_ps, const ConvTable* __restrict__ tab,
                                uint32_t nt, uint64_t* __restrict__ dst, size_t dst_ps,
                                const uint64_t* __restrict__ qs, const uint64_t* __restrict__ bar, uint32_t N)
@@ -69,8 +70,8 @@ __global__ void k_moddown_conv(const uint64_t* __restrict__ src, size_t src_ps, 
     for (uint32_t k = 0; k < (NS > 0 ? (uint32_t)NS : ns); k++) {
         if (k >= ns) break;
         const uint32_t pk_i = tab->src[k];
-        const uint64_t pk = qs[pk_i];
-        y[k] = mul_shoup(src[poly * src_ps + (size_t)k * N + c], tab->hat_inv[k], tab->hat_inv_sh[k], pk);
+        const uint64_t x = src[poly * src_ps + (size_t)k * N + c];
+        y[k] = PRE ? x : mul_shoup(x, tab->hat_inv[k], tab->hat_inv_sh[k], qs[pk_i]);
         const uint64_t b0 = bar[2 * pk_i], b1 = bar[2 * pk_i + 1];
         const uint64_t lo = y[k] * b0, hi = __umul64hi(y[k], b0) + y[k] * b1;  // y_k floor(2^128/p_k)
         const uint64_t s_lo = f_lo + lo;
@@ -101,15 +102,15 @@ __global__ void k_moddown_conv(const uint64_t* __restrict__ src, size_t src_ps, 
 
 // launches with the register form when the source count allows it (ModDown: nP
 // sources; ModUp below: alpha)
-template <typename... Args>
+template <bool PRE, typename... Args>
 void launch_moddown_conv(uint32_t ns, dim3 grid, cudaStream_t st, Args... args)
 {
     switch (ns) {
-    case 1: k_moddown_conv<1><<<grid, kT, 0, st>>>(args...); break;
-    case 2: k_moddown_conv<2><<<grid, kT, 0, st>>>(args...); break;
-    case 3: k_moddown_conv<3><<<grid, kT, 0, st>>>(args...); break;
-    case 4: k_moddown_conv<4><<<grid, kT, 0, st>>>(args...); break;
-    default: k_moddown_conv<0><<<grid, kT, 0, st>>>(args...); break;
+    case 1: k_moddown_conv<1, PRE><<<grid, kT, 0, st>>>(args...); break;
+    case 2: k_moddown_conv<2, PRE><<<grid, kT, 0, st>>>(args...); break;
+    case 3: k_moddown_conv<3, PRE><<<grid, kT, 0, st>>>(args...); break;
+    case 4: k_moddown_conv<4, PRE><<<grid, kT, 0, st>>>(args...); break;
+    default: k_moddown_conv<0, PRE><<<grid, kT, 0, st>>>(args...); break;
     }
 }
 
@@ -195,7 +196,7 @@ static int keyswitch_impl(blb_ctx* ctx, const uint64_t* d_ntt, uint32_t level, c
     // 4. ModDown: P limbs to coefficient form, convert to Q_l, back to evaluation
     BLB_TRY(ntt_inverse(ctx, acc + (size_t)n * N, nP, ctx->pmap()));
     BLB_TRY(ntt_inverse(ctx, acc + ((size_t)E + n) * N, nP, ctx->pmap()));
-    launch_moddown_conv(nP, dim3((N + kT - 1) / kT, 2), ctx->stream, (const uint64_t*)(acc + (size_t)n * N),
+    launch_moddown_conv<false>(nP, dim3((N + kT - 1) / kT, 2), ctx->stream, (const uint64_t*)(acc + (size_t)n * N),
                         (size_t)E * N, (const ConvTable*)ctx->d_moddown, n, cv, (size_t)n * N,
                         (const uint64_t*)ctx->d_q, (const uint64_t*)ctx->d_bar, N);
     BLB_LAUNCHED();
@@ -250,11 +251,11 @@ int keyswitch_noalloc_prepare(blb_ctx* c)
     const void* kernels[] = {(const void*)k_conv,
                              (const void*)k_ks_inner,
                              (const void*)k_moddown_finish,
-                             (const void*)k_moddown_conv<0>,
-                             (const void*)k_moddown_conv<1>,
-                             (const void*)k_moddown_conv<2>,
-                             (const void*)k_moddown_conv<3>,
-                             (const void*)k_moddown_conv<4>};
+                             (const void*)k_moddown_conv<0, false>,
+                             (const void*)k_moddown_conv<1, false>,
+                             (const void*)k_moddown_conv<2, false>,
+                             (const void*)k_moddown_conv<3, false>,
+                             (const void*)k_moddown_conv<4, false>};
     for (const void* k : kernels) BLB_CUDA(cudaFuncGetAttributes(&fa, k));
     c->noalloc_scratch = (uint64_t*)p;
     return BLB_OK;
@@ -349,7 +350,9 @@ __global__ void k_ksb_gather(uint64_t* __restrict__ coef, uint64_t* __restrict__
     ext[(((size_t)s * beta + i / alpha) * E + i) * N + k] = v;
 }
 
-// ModUp of every digit of every source: grid.y = source * beta + j
+// ModUp of every digit of every source: grid.y = source * beta + j.  The
+// coefficient rows arrive as y_i = [x_i (D_j/q_i)^-1]_{q_i}: the inverse NTT
+// that produced them multiplied by that factor together with N^-1.
 template <int NS>  // as for k_moddown_conv: at most NS primes per digit, 0 = any
 __global__ void k_ksb_modup(const uint64_t* __restrict__ coef, uint64_t* __restrict__ ext,
                             const ConvTable* __restrict__ tabs, uint32_t n, uint32_t E, uint32_t beta,
@@ -368,7 +371,7 @@ __global__ void k_ksb_modup(const uint64_t* __restrict__ coef, uint64_t* __restr
 #pragma unroll
     for (uint32_t i = 0; i < (NS > 0 ? (uint32_t)NS : ns); i++) {
         if (i >= ns) break;
-        y[i] = mul_shoup(in[(size_t)i * N], tab->hat_inv[i], tab->hat_inv_sh[i], qs[tab->src[i]]);
+        y[i] = in[(size_t)i * N];
     }
     for (uint32_t t = 0; t < nt; t++) {
         const uint32_t pt = tab->dst[t];
@@ -395,11 +398,16 @@ void launch_modup(uint32_t alpha, dim3 grid, cudaStream_t st, Args... args)
 }
 
 // acc[group][p][t] = sum over the group's products x of sum_j sigma_x(ext[src_x][j][t]) key_x[j][p][kt]
-// for the special-prime rows t = n + blockIdx.y only: they are the input of
+// for the special-prime rows t = n + blockIdx.z only: they are the input of
 // the ModDown conversion.  The ciphertext-prime rows are summed where they are
 // used, in k_ksb_finish, so they are never written out.
 // NB: the digit count beta as a compile-time loop bound (0 = any), so that
 // every digit's loads are in flight together.
+// Grid order of the inner-product and finish kernels: the group (or source)
+// index is blockIdx.x, so the CTAs of all groups for one coefficient tile and
+// prime are scheduled together and a key tile that several groups use (the
+// giant-step keys of every output, the baby-step keys of every source, the
+// relinearization key) is read from HBM once and then from L2.
 template <int NB>
 __global__ void __launch_bounds__(256, 6) k_ksb_inner(uint64_t* __restrict__ acc, const uint64_t* __restrict__ ext,
                             const DevGroup* __restrict__ groups, const DevProduct* __restrict__ prods, const __grid_constant__ LimbMap emap,
@@ -407,7 +415,7 @@ __global__ void __launch_bounds__(256, 6) k_ksb_inner(uint64_t* __restrict__ acc
                             const uint64_t* __restrict__ qs, const uint64_t* __restrict__ bar, uint32_t logN)
 {
     const uint32_t N = 1u << logN;
-    const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x, t = n + blockIdx.y, gr = blockIdx.z;
+    const uint32_t gr = blockIdx.x, c = blockIdx.y * blockDim.x + threadIdx.x, t = n + blockIdx.z;
     if (c >= N) return;
     const uint32_t pi = emap.p[t];
     const uint32_t kt = nQ + (t - n);
@@ -444,7 +452,7 @@ __global__ void __launch_bounds__(256, 6) k_ksb_finish(const DevGroup* __restric
                              uint32_t logN, int accumulate)
 {
     const uint32_t N = 1u << logN;
-    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x, i = blockIdx.y, gr = blockIdx.z;
+    const uint32_t gr = blockIdx.x, k = blockIdx.y * blockDim.x + threadIdx.x, i = blockIdx.z;
     if (k >= N) return;
     const DevGroup G = groups[gr];
     const uint64_t q = qs[i], r0 = bar[2 * i], r1 = bar[2 * i + 1];
@@ -502,7 +510,7 @@ __global__ void __launch_bounds__(256, 6) k_ksb_finish_src(const DevGroup* __res
 {
     constexpr int VN = NB > 0 ? NB : BLB_MAXP;
     const uint32_t N = 1u << logN;
-    const uint32_t kp = blockIdx.x * blockDim.x + threadIdx.x, i = blockIdx.y, s = blockIdx.z;
+    const uint32_t s = blockIdx.x, kp = blockIdx.y * blockDim.x + threadIdx.x, i = blockIdx.z;
     if (kp >= N) return;
     const uint64_t q = qs[i], r0 = bar[2 * i], r1 = bar[2 * i + 1];
     const uint64_t* xs = ext + (size_t)s * beta * E * N + (size_t)i * N + kp;
@@ -608,6 +616,7 @@ int ks_run(blb_ctx* ctx, uint32_t level, const KsSource* sources, uint32_t n_src
     }
     const LimbMap emap = ctx->extmap(level);
     const uint32_t gx = (N + kT - 1) / kT;
+    const uint64_t* ninv_conv = ctx->d_ninv_conv + (size_t)level * ctx->np * 2;
     std::vector<int32_t> local(n_src, -1);
     for (uint32_t g0 = 0; g0 < n_groups;) {
         // chunk: groups g0..g1 and the sources their products need
@@ -766,30 +775,30 @@ int ks_run(blb_ctx* ctx, uint32_t level, const KsSource* sources, uint32_t n_src
         if (ns) {
             k_ksb_gather<<<dim3(gx, n, ns), kT, 0, ctx->stream>>>(coef, ext, d_src, n, E, beta, alpha, ctx->logN);
             BLB_LAUNCHED();
-            BLB_TRY(ntt_inverse(ctx, coef, ns * n, ctx->qmap(n)));
+            BLB_TRY(ntt_inverse_scaled(ctx, coef, ns * n, ctx->qmap(n), ninv_conv));
             launch_modup(alpha, dim3(gx, ns * beta), ctx->stream, (const uint64_t*)coef, ext,
                          (const ConvTable*)ctx->d_modup[(size_t)level * ctx->dnum], n, E, beta, alpha,
                          (const uint64_t*)ctx->d_q, (const uint64_t*)ctx->d_bar, N);
             BLB_LAUNCHED();
             BLB_TRY(ntt_forward_list(ctx, ext, (uint32_t)ext_rows.size(), d_ext_rows));
         }
-        launch_inner(beta, dim3(gx, nP, ng), ctx->stream, acc, (const uint64_t*)ext, (const DevGroup*)d_grp,
+        launch_inner(beta, dim3(ng, gx, nP), ctx->stream, acc, (const uint64_t*)ext, (const DevGroup*)d_grp,
                      (const DevProduct*)d_prod, emap, n, E, beta, ctx->nQ, ctx->np, (const uint64_t*)ctx->d_q,
                      (const uint64_t*)ctx->d_bar, ctx->logN);
         BLB_LAUNCHED();
-        BLB_TRY(ntt_inverse_list(ctx, acc, (uint32_t)p_rows.size(), d_p_rows));
-        launch_moddown_conv(nP, dim3(gx, 2 * ng), ctx->stream, (const uint64_t*)(acc + (size_t)n * N),
+        BLB_TRY(ntt_inverse_list_scaled(ctx, acc, (uint32_t)p_rows.size(), d_p_rows, ninv_conv));
+        launch_moddown_conv<true>(nP, dim3(gx, 2 * ng), ctx->stream, (const uint64_t*)(acc + (size_t)n * N),
                             (size_t)E * N, (const ConvTable*)ctx->d_moddown, n, cv, (size_t)n * N,
                             (const uint64_t*)ctx->d_q, (const uint64_t*)ctx->d_bar, N);
         BLB_LAUNCHED();
         BLB_TRY(ntt_forward(ctx, cv, ng * 2 * n, ctx->qmap(n)));
         if (by_src)
-            launch_finish_src(beta, dim3(gx, n, ns), ctx->stream, (const DevGroup*)d_grp, (const DevProduct*)d_prod,
+            launch_finish_src(beta, dim3(ns, gx, n), ctx->stream, (const DevGroup*)d_grp, (const DevProduct*)d_prod,
                               (const uint64_t*)ext, (const KsAdd*)d_add, (const uint64_t*)cv, (const uint32_t*)d_so,
                               (const uint32_t*)d_sg, n, E, beta, ctx->np, pinv, (const uint64_t*)ctx->d_q,
                               (const uint64_t*)ctx->d_bar, ctx->logN);
         else
-            launch_finish(beta, dim3(gx, n, ng), ctx->stream, (const DevGroup*)d_grp, (const DevProduct*)d_prod,
+            launch_finish(beta, dim3(ng, gx, n), ctx->stream, (const DevGroup*)d_grp, (const DevProduct*)d_prod,
                           (const uint64_t*)ext, (const KsAdd*)d_add, (const uint64_t*)cv, n, E, beta, ctx->np, pinv,
                           (const uint64_t*)ctx->d_q, (const uint64_t*)ctx->d_bar, ctx->logN, accumulate);
         BLB_LAUNCHED();

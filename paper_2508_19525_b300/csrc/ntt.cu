@@ -275,7 +275,8 @@ __global__ void __launch_bounds__(kThreads, ntt_ctas(RB)) k_ntt(uint64_t* __rest
 // One forward or inverse transform with the column pass over 2^L1-point
 // sub-transforms and the row pass over 2^(LOGN - L1) points (L1 = 0: one pass).
 template <int LOGN, int L1, int RB>
-int run_split(blb_ctx* ctx, uint64_t* data, uint32_t rows, const LimbMap& map, const uint32_t* rowlist, bool inverse)
+int run_split(blb_ctx* ctx, uint64_t* data, uint32_t rows, const LimbMap& map, const uint32_t* rowlist, bool inverse,
+              const uint64_t* ninv)
 {
     constexpr uint32_t N = 1u << LOGN;
     constexpr uint32_t TILE = N < 4096 ? N : 4096;
@@ -287,19 +288,19 @@ int run_split(blb_ctx* ctx, uint64_t* data, uint32_t rows, const LimbMap& map, c
         if (!inverse) {
             if constexpr (L1 > 0) {
                 BLB_CUDA(launch_pdl(k_ntt<false, LOGN, L1, true, RB>, grid, dim3(kThreads), 0, ctx->stream, data, map, rowlist, y0,
-                           (const uint64_t*)ctx->d_q, tw, (const uint64_t*)ctx->d_ninv, (const uint64_t*)ctx->d_bar));
+                           (const uint64_t*)ctx->d_q, tw, ninv, (const uint64_t*)ctx->d_bar));
                 BLB_LAUNCHED();
             }
             BLB_CUDA(launch_pdl(k_ntt<false, LOGN, L2, false, RB>, grid, dim3(kThreads), 0, ctx->stream, data, map, rowlist, y0,
-                       (const uint64_t*)ctx->d_q, tw, (const uint64_t*)ctx->d_ninv, (const uint64_t*)ctx->d_bar));
+                       (const uint64_t*)ctx->d_q, tw, ninv, (const uint64_t*)ctx->d_bar));
             BLB_LAUNCHED();
         } else {
             BLB_CUDA(launch_pdl(k_ntt<true, LOGN, L2, false, RB>, grid, dim3(kThreads), 0, ctx->stream, data, map, rowlist, y0,
-                       (const uint64_t*)ctx->d_q, tw, (const uint64_t*)ctx->d_ninv, (const uint64_t*)ctx->d_bar));
+                       (const uint64_t*)ctx->d_q, tw, ninv, (const uint64_t*)ctx->d_bar));
             BLB_LAUNCHED();
             if constexpr (L1 > 0) {
                 BLB_CUDA(launch_pdl(k_ntt<true, LOGN, L1, true, RB>, grid, dim3(kThreads), 0, ctx->stream, data, map, rowlist, y0,
-                           (const uint64_t*)ctx->d_q, tw, (const uint64_t*)ctx->d_ninv, (const uint64_t*)ctx->d_bar));
+                           (const uint64_t*)ctx->d_q, tw, ninv, (const uint64_t*)ctx->d_bar));
                 BLB_LAUNCHED();
             }
         }
@@ -312,40 +313,46 @@ int run_split(blb_ctx* ctx, uint64_t* data, uint32_t rows, const LimbMap& map, c
 // pass), and two radices of the register rounds (ctx->ntt_radix: 8, four CTAs
 // per SM, or 16, three); blb_ntt_autotune times all of them.
 template <int LOGN, int RB>
-int run_nr(blb_ctx* ctx, uint64_t* data, uint32_t rows, const LimbMap& map, const uint32_t* rowlist, bool inverse)
+int run_nr(blb_ctx* ctx, uint64_t* data, uint32_t rows, const LimbMap& map, const uint32_t* rowlist, bool inverse,
+           const uint64_t* ninv)
 {
     if constexpr (LOGN <= 12) {
-        return run_split<LOGN, 0, RB>(ctx, data, rows, map, rowlist, inverse);
+        return run_split<LOGN, 0, RB>(ctx, data, rows, map, rowlist, inverse, ninv);
     } else {
         constexpr int M = LOGN / 2;
         switch (ctx->ntt_split) {
-        case -1: return run_split<LOGN, M - 1, RB>(ctx, data, rows, map, rowlist, inverse);
+        case -1: return run_split<LOGN, M - 1, RB>(ctx, data, rows, map, rowlist, inverse, ninv);
         case 1:
-            if constexpr (LOGN - (M + 1) >= 1) return run_split<LOGN, M + 1, RB>(ctx, data, rows, map, rowlist, inverse);
-            else return run_split<LOGN, M, RB>(ctx, data, rows, map, rowlist, inverse);
-        default: return run_split<LOGN, M, RB>(ctx, data, rows, map, rowlist, inverse);
+            if constexpr (LOGN - (M + 1) >= 1) return run_split<LOGN, M + 1, RB>(ctx, data, rows, map, rowlist, inverse, ninv);
+            else return run_split<LOGN, M, RB>(ctx, data, rows, map, rowlist, inverse, ninv);
+        default: return run_split<LOGN, M, RB>(ctx, data, rows, map, rowlist, inverse, ninv);
         }
     }
 }
 
 template <int LOGN>
-int run_n(blb_ctx* ctx, uint64_t* data, uint32_t rows, const LimbMap& map, const uint32_t* rowlist, bool inverse)
+int run_n(blb_ctx* ctx, uint64_t* data, uint32_t rows, const LimbMap& map, const uint32_t* rowlist, bool inverse,
+          const uint64_t* ninv)
 {
-    if (ctx->ntt_radix == 16) return run_nr<LOGN, 4>(ctx, data, rows, map, rowlist, inverse);
-    return run_nr<LOGN, 3>(ctx, data, rows, map, rowlist, inverse);
+    if (ctx->ntt_radix == 16) return run_nr<LOGN, 4>(ctx, data, rows, map, rowlist, inverse, ninv);
+    return run_nr<LOGN, 3>(ctx, data, rows, map, rowlist, inverse, ninv);
 }
 
-int run(blb_ctx* ctx, uint64_t* data, uint32_t rows, const LimbMap& map, const uint32_t* rowlist, bool inverse)
+// ninv: [prime][2] the constant the last inverse pass multiplies by and its
+// Shoup companion (N^-1 mod q, or N^-1 times a conversion factor, see
+// ntt_inverse_scaled)
+int run(blb_ctx* ctx, uint64_t* data, uint32_t rows, const LimbMap& map, const uint32_t* rowlist, bool inverse,
+        const uint64_t* ninv)
 {
     switch (ctx->logN) {
-    case 10: return run_n<10>(ctx, data, rows, map, rowlist, inverse);
-    case 11: return run_n<11>(ctx, data, rows, map, rowlist, inverse);
-    case 12: return run_n<12>(ctx, data, rows, map, rowlist, inverse);
-    case 13: return run_n<13>(ctx, data, rows, map, rowlist, inverse);
-    case 14: return run_n<14>(ctx, data, rows, map, rowlist, inverse);
-    case 15: return run_n<15>(ctx, data, rows, map, rowlist, inverse);
-    case 16: return run_n<16>(ctx, data, rows, map, rowlist, inverse);
-    case 17: return run_n<17>(ctx, data, rows, map, rowlist, inverse);
+    case 10: return run_n<10>(ctx, data, rows, map, rowlist, inverse, ninv);
+    case 11: return run_n<11>(ctx, data, rows, map, rowlist, inverse, ninv);
+    case 12: return run_n<12>(ctx, data, rows, map, rowlist, inverse, ninv);
+    case 13: return run_n<13>(ctx, data, rows, map, rowlist, inverse, ninv);
+    case 14: return run_n<14>(ctx, data, rows, map, rowlist, inverse, ninv);
+    case 15: return run_n<15>(ctx, data, rows, map, rowlist, inverse, ninv);
+    case 16: return run_n<16>(ctx, data, rows, map, rowlist, inverse, ninv);
+    case 17: return run_n<17>(ctx, data, rows, map, rowlist, inverse, ninv);
     default: return blb_fail(BLB_ERR_ARG, "no NTT for this ring size");
     }
 }
@@ -378,8 +385,8 @@ extern "C" int blb_ntt_autotune(blb_ctx* ctx, uint32_t rows, int* split_out, int
             float ms = 0;
             for (int rep = 0; rep < 3 && !rc; rep++) {  // the first run is a warm-up
                 cudaEventRecord(e0, ctx->stream);
-                rc = run(ctx, buf, rows, map, nullptr, false);
-                if (!rc) rc = run(ctx, buf, rows, map, nullptr, true);
+                rc = run(ctx, buf, rows, map, nullptr, false, ctx->d_ninv);
+                if (!rc) rc = run(ctx, buf, rows, map, nullptr, true, ctx->d_ninv);
                 cudaEventRecord(e1, ctx->stream);
                 if (!rc && cudaEventSynchronize(e1) != cudaSuccess) rc = blb_fail(BLB_ERR_CUDA, "autotune run failed");
                 float t = 0;
@@ -426,14 +433,14 @@ int ntt_forward(blb_ctx* ctx, uint64_t* data, uint32_t rows, const LimbMap& map)
 {
     if (rows == 0) return BLB_OK;
     ProfScope prof(ctx, "ntt", (uint64_t)rows * ctx->N * 16);  // one read + one write per word
-    return run(ctx, data, rows, map, nullptr, false);
+    return run(ctx, data, rows, map, nullptr, false, ctx->d_ninv);
 }
 
 int ntt_inverse(blb_ctx* ctx, uint64_t* data, uint32_t rows, const LimbMap& map)
 {
     if (rows == 0) return BLB_OK;
     ProfScope prof(ctx, "intt", (uint64_t)rows * ctx->N * 16);
-    return run(ctx, data, rows, map, nullptr, true);
+    return run(ctx, data, rows, map, nullptr, true, ctx->d_ninv);
 }
 
 int ntt_forward_list(blb_ctx* ctx, uint64_t* data, uint32_t rows, const uint32_t* d_rowlist)
@@ -442,7 +449,7 @@ int ntt_forward_list(blb_ctx* ctx, uint64_t* data, uint32_t rows, const uint32_t
     ProfScope prof(ctx, "ntt", (uint64_t)rows * ctx->N * 16);
     LimbMap none{};
     none.n = 1;
-    return run(ctx, data, rows, none, d_rowlist, false);
+    return run(ctx, data, rows, none, d_rowlist, false, ctx->d_ninv);
 }
 
 int ntt_inverse_list(blb_ctx* ctx, uint64_t* data, uint32_t rows, const uint32_t* d_rowlist)
@@ -451,5 +458,21 @@ int ntt_inverse_list(blb_ctx* ctx, uint64_t* data, uint32_t rows, const uint32_t
     ProfScope prof(ctx, "intt", (uint64_t)rows * ctx->N * 16);
     LimbMap none{};
     none.n = 1;
-    return run(ctx, data, rows, none, d_rowlist, true);
+    return run(ctx, data, rows, none, d_rowlist, true, ctx->d_ninv);
+}
+
+int ntt_inverse_scaled(blb_ctx* ctx, uint64_t* data, uint32_t rows, const LimbMap& map, const uint64_t* ninv)
+{
+    if (rows == 0) return BLB_OK;
+    ProfScope prof(ctx, "intt", (uint64_t)rows * ctx->N * 16);
+    return run(ctx, data, rows, map, nullptr, true, ninv);
+}
+
+int ntt_inverse_list_scaled(blb_ctx* ctx, uint64_t* data, uint32_t rows, const uint32_t* d_rowlist, const uint64_t* ninv)
+{
+    if (rows == 0) return BLB_OK;
+    ProfScope prof(ctx, "intt", (uint64_t)rows * ctx->N * 16);
+    LimbMap none{};
+    none.n = 1;
+    return run(ctx, data, rows, none, d_rowlist, true, ninv);
 }
