@@ -62,20 +62,20 @@ __device__ __forceinline__ uint64_t mul_shoup(uint64_t x, uint64_t w, uint64_t w
 }
 
 // Barrett reduction of a 128-bit x = x1 2^64 + x0 with R = floor(2^128 / q)
-// = r1 2^64 + r0: qhat = floor(x R / 2^128) computed exactly, which is at least
-// floor(x / q) - 1, so one conditional subtraction lands in [0, q).
+// = r1 2^64 + r0.  x R / 2^128 = x1 r1 + (x1 r0 + x0 r1) / 2^64 + x0 r0 / 2^128;
+// qhat keeps the whole first term and the integer parts of the second, so it
+// misses at most 2 (three dropped fractions below 1 each) of floor(x R / 2^128),
+// which is itself at least floor(x / q) - 1 and at most x / q.  Hence
+// floor(x / q) - 3 <= qhat <= floor(x / q), r = x - qhat q lies in [0, 4q)
+// (below 2^64 for q < 2^62, so it is exact mod 2^64), and two conditional
+// subtractions land in [0, q).  Any x below 2^128.
 __device__ __forceinline__ uint64_t barrett128(uint64_t x0, uint64_t x1, uint64_t q, uint64_t r0,
                                                uint64_t r1)
 {
-    uint64_t c0 = __umul64hi(x0, r0);
-    uint64_t a_lo = x1 * r0, a_hi = __umul64hi(x1, r0);
-    uint64_t b_lo = x0 * r1, b_hi = __umul64hi(x0, r1);
-    uint64_t s = a_lo + b_lo;
-    uint64_t k1 = s < a_lo;
-    uint64_t s2 = s + c0;
-    uint64_t k2 = s2 < s;
-    uint64_t qhat = x1 * r1 + a_hi + b_hi + k1 + k2;
+    const uint64_t qhat = x1 * r1 + __umul64hi(x1, r0) + __umul64hi(x0, r1);
     uint64_t r = x0 - qhat * q;
+    const uint64_t q2 = q << 1;
+    r = r >= q2 ? r - q2 : r;
     return r >= q ? r - q : r;
 }
 
