@@ -932,8 +932,15 @@ def measure_int_peaks(q, stream):
     rc = f(q, stream, *[ctypes.byref(x) for x in v])
     if rc:
         raise RuntimeError(f"blb_peaks_int_rates failed ({rc})")
-    return {"bfly_per_s": v[0].value, "mad128_per_s": v[1].value, "bfly_per_sm_cycle": v[2].value,
-            "mad128_per_sm_cycle": v[3].value}
+    g = ctypes.CDLL(build.build_peaks()).blb_peaks_reduce_rate
+    g.argtypes = [ctypes.c_uint64, ctypes.c_void_p] + [ctypes.POINTER(ctypes.c_double)] * 2
+    red = [ctypes.c_double() for _ in range(2)]
+    rc = g(q, stream, *[ctypes.byref(x) for x in red])
+    if rc:
+        raise RuntimeError(f"blb_peaks_reduce_rate failed ({rc})")
+    return {"bfly_per_s": v[0].value, "mad128_per_s": v[1].value, "reduce128_per_s": red[0].value,
+            "bfly_per_sm_cycle": v[2].value, "mad128_per_sm_cycle": v[3].value,
+            "reduce128_per_sm_cycle": red[1].value}
 
 
 def run_blb(args):
@@ -954,6 +961,7 @@ def run_blb(args):
     clk = clocks.stop()
     launches = blb.kernel_launches() - launches0
     sites = {s: w.ctx.profile_read(s) for s in ("cp_mac", "keyswitch", "ntt", "intt")}
+    ks_ops = w.ctx.profile_read_ops("keyswitch")
     w.ctx.profile(False)
     int_peaks = measure_int_peaks(w.ctx.primes[0], w.stream.cuda_stream)
     value, dev_max = aggregate(dev_s, TOKENS_PER_STEP * args.steps, world)
@@ -1029,6 +1037,21 @@ def run_blb(args):
             roof[s_]["alu"] = {"bound": "alu", "achieved": round(ach / 1e9, 2), "peak": round(int_peaks["bfly_per_s"] / 1e9, 2),
                                "unit": "Gbutterfly/s", "frac": round(ach / int_peaks["bfly_per_s"], 4),
                                "peak_kind": "measured (register-only lazy butterfly, libblb_peaks.so)"}
+    # ALU roofline of the key-switch site: its counted arithmetic (128-bit
+    # multiply-adds, 128-bit reductions, butterflies of its NTTs and Shoup
+    # products) at the measured register-only rate of each, summed (they share
+    # the integer pipes), is the least time the site could take; frac = that
+    # time / the measured time.  The binding roofline is the larger fraction.
+    if "keyswitch" in roof and ks_ops[0]:
+        ms = sites["keyswitch"][0]
+        t_min = (ks_ops[0] / int_peaks["mad128_per_s"] + ks_ops[1] / int_peaks["reduce128_per_s"]
+                 + ks_ops[2] / int_peaks["bfly_per_s"])
+        alu_frac = t_min / (ms / 1e3)
+        roof["keyswitch"]["alu"] = {
+            "bound": "alu", "frac": round(alu_frac, 4), "min_ms_total": round(t_min * 1e3, 3),
+            "ops_total": {"mad128": ks_ops[0], "reduce128": ks_ops[1], "butterflies": ks_ops[2]},
+            "peak_kind": "measured (register-only rates of each unit, libblb_peaks.so)"}
+        roof["keyswitch"]["binding"] = "alu" if alu_frac > roof["keyswitch"]["frac"] else "hbm"
     # the dominant single-kernel site (the key-switch site is a pipeline of kernels)
     kernel_sites = [s for s in ("cp_mac", "ntt", "intt") if s in roof]
     dominant = max(kernel_sites, key=lambda s: roof[s]["ms_total"]) if kernel_sites else None

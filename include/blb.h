@@ -489,6 +489,14 @@ uint64_t blb_kernel_launches(void);
  * baby-step ciphertext and every partial sum once).  Enabling resets the sums. */
 int blb_profile_enable(blb_ctx* ctx, int on);
 int blb_profile_read(blb_ctx* ctx, const char* site, double* ms, uint64_t* count, uint64_t* bytes);
+/* The arithmetic of the calls bracketed at `site` since profiling was enabled,
+ * for an ALU roofline beside the bytes: 64 x 64 -> 128-bit multiply-adds,
+ * reductions of a 128-bit sum mod a prime, and NTT butterflies (a Shoup product
+ * by a constant counted as one).  Counted by the "keyswitch" site (its ModUp,
+ * inner products, ModDown and the NTTs between them); other sites report 0.
+ * Outputs are nullable host pointers; BLB_ERR_ARG for a null ctx or site. */
+int blb_profile_read_ops(blb_ctx* ctx, const char* site, uint64_t* mad128, uint64_t* reductions,
+                         uint64_t* butterflies);
 
 #ifdef __cplusplus
 }

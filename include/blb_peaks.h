@@ -26,6 +26,13 @@ extern "C" {
 int blb_peaks_int_rates(uint64_t q, void* stream, double* bfly_per_s, double* mad128_per_s,
                         double* bfly_per_sm_cycle, double* mad128_per_sm_cycle);
 
+/* The same measurement for the reduction of a 128-bit value mod q (a Barrett
+ * reduction with floor(2^128 / q): three 64-bit partial products, two
+ * conditional subtractions), in independent register chains whose next input
+ * adds the previous result.  q odd, 3 <= q < 2^62.  Outputs (host, nullable):
+ * reductions per second and per SM cycle.  Returns as blb_peaks_int_rates. */
+int blb_peaks_reduce_rate(uint64_t q, void* stream, double* per_s, double* per_sm_cycle);
+
 #ifdef __cplusplus
 }
 #endif

@@ -118,6 +118,7 @@ SIGNATURES = {
     "blb_kernel_launches": (_u64, []),
     "blb_profile_enable": (ctypes.c_int, [_vp, ctypes.c_int]),
     "blb_profile_read": (ctypes.c_int, [_vp, ctypes.c_char_p, _vp, _vp, _vp]),
+    "blb_profile_read_ops": (ctypes.c_int, [_vp, ctypes.c_char_p, _vp, _vp, _vp]),
 }
 
 _lib = None
@@ -645,6 +646,12 @@ class Context:
         ms, cnt, nb = _dbl(), _u64(), _u64()
         _check(lib().blb_profile_read(self.h, site.encode(), ctypes.byref(ms), ctypes.byref(cnt), ctypes.byref(nb)))
         return ms.value, cnt.value, nb.value
+
+    def profile_read_ops(self, site):
+        """(128-bit multiply-adds, 128-bit reductions, butterflies) counted at a site."""
+        m, r, b = _u64(), _u64(), _u64()
+        _check(lib().blb_profile_read_ops(self.h, site.encode(), ctypes.byref(m), ctypes.byref(r), ctypes.byref(b)))
+        return m.value, r.value, b.value
 
     def ntt_autotune(self, rows=64):
         """Time the NTT's radices (8, 16) and pass splits (-1, 0, +1); keep

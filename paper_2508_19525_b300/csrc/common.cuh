@@ -212,6 +212,10 @@ struct blb_ctx {
         double ms = 0;
         uint64_t count = 0;
         uint64_t bytes = 0;  // algorithmic bytes of the bracketed calls
+        // arithmetic of the bracketed calls, where the site counts it: 64 x 64
+        // -> 128-bit multiply-adds, reductions of a 128-bit sum mod a prime,
+        // NTT butterflies (and Shoup products by a constant)
+        uint64_t mad128 = 0, reductions = 0, butterflies = 0;
     };
     std::vector<ProfSite> prof;
     std::vector<cudaEvent_t> event_pool;
@@ -325,6 +329,7 @@ struct ProfScope {
     cudaEvent_t b = nullptr, e = nullptr;
     ProfScope(blb_ctx* ctx, const char* name, uint64_t algorithmic_bytes);
     ~ProfScope();
+    void ops(uint64_t mad128, uint64_t reductions, uint64_t butterflies);
 };
 
 // ---------------------------------------------------------------------------

@@ -48,13 +48,20 @@ ProfScope::ProfScope(blb_ctx* ctx, const char* name, uint64_t algorithmic_bytes)
     for (size_t i = 0; i < c->prof.size(); i++)
         if (c->prof[i].name == name) site = (int)i;
     if (site < 0) {
-        c->prof.push_back(blb_ctx::ProfSite{name, {}, 0, 0, 0});
+        c->prof.push_back(blb_ctx::ProfSite{name, {}, 0, 0, 0, 0, 0, 0});
         site = (int)c->prof.size() - 1;
     }
     c->prof[site].bytes += algorithmic_bytes;
     b = pool_event(c);
     e = pool_event(c);
     cudaEventRecord(b, c->stream);
+}
+void ProfScope::ops(uint64_t mad128, uint64_t reductions, uint64_t butterflies)
+{
+    if (site < 0) return;
+    c->prof[site].mad128 += mad128;
+    c->prof[site].reductions += reductions;
+    c->prof[site].butterflies += butterflies;
 }
 ProfScope::~ProfScope()
 {
@@ -100,6 +107,22 @@ extern "C" int blb_profile_read(blb_ctx* c, const char* site, double* ms, uint64
             if (ms) *ms = s.ms;
             if (count) *count = s.count;
             if (bytes) *bytes = s.bytes;
+        }
+    return BLB_OK;
+}
+
+extern "C" int blb_profile_read_ops(blb_ctx* c, const char* site, uint64_t* mad128, uint64_t* reductions,
+                                    uint64_t* butterflies)
+{
+    if (!c || !site) return blb_fail(BLB_ERR_ARG, "null argument");
+    if (mad128) *mad128 = 0;
+    if (reductions) *reductions = 0;
+    if (butterflies) *butterflies = 0;
+    for (auto& s : c->prof)
+        if (s.name == site) {
+            if (mad128) *mad128 = s.mad128;
+            if (reductions) *reductions = s.reductions;
+            if (butterflies) *butterflies = s.butterflies;
         }
     return BLB_OK;
 }

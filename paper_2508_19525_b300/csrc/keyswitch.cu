@@ -772,6 +772,25 @@ int ks_run(blb_ctx* ctx, uint32_t level, const KsSource* sources, uint32_t n_src
         ProfScope prof(ctx, "keyswitch",
                        ((uint64_t)ns * (n + (uint64_t)beta * E) + (uint64_t)hp.size() * 3 * beta * E +
                         (uint64_t)ng * 2 * n) * N * 8);
+        {
+            // arithmetic per coefficient, summed over the launches below
+            const uint64_t nprod = hp.size();
+            uint64_t mad = 0, red = 0, bfly = 0;
+            for (uint32_t j = 0; j < beta; j++) {  // ModUp: |D_j| sources to E - |D_j| targets
+                const uint64_t dj = std::min((j + 1) * alpha, n) - j * alpha;
+                mad += ns * dj * (E - dj);
+                red += ns * (E - dj);
+            }
+            mad += nprod * 2 * beta * nP;                      // inner products, special primes
+            red += nprod * 2 * nP;
+            mad += (uint64_t)ng * 2 * (nP + (uint64_t)n * (nP + 1));  // ModDown: rounding sum, n targets
+            red += (uint64_t)ng * 2 * n;
+            mad += nprod * 2 * beta * n;                       // inner products, ciphertext primes
+            for (uint32_t i = 0; i < n; i++) red += 2 * (ctx->q[i] >= (1ull << 50) || by_src ? nprod : ng);
+            bfly += (uint64_t)ng * 2 * n;                      // the P^-1 Shoup products
+            const uint64_t ntt_rows = (uint64_t)ns * n + ext_rows.size() + p_rows.size() + (uint64_t)ng * 2 * n;
+            prof.ops(mad * N, red * N, bfly * N + ntt_rows * (N / 2) * ctx->logN);
+        }
         if (ns) {
             k_ksb_gather<<<dim3(gx, n, ns), kT, 0, ctx->stream>>>(coef, ext, d_src, n, E, beta, alpha, ctx->logN);
             BLB_LAUNCHED();

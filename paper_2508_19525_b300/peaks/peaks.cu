@@ -5,7 +5,8 @@
 //
 // The NTT's unit of work is the lazy Cooley-Tukey butterfly on 64-bit words
 // (one Shoup product by a constant twiddle, then X + WY and X - WY + 2q); the
-// base conversions' unit is a 64 x 64 -> 128-bit multiply-accumulate.  Each
+// base conversions' unit is a 64 x 64 -> 128-bit multiply-accumulate, followed by
+// one reduction of the 128-bit sum per output (blb_peaks_reduce_rate).  Each
 // kernel runs independent chains of one unit entirely in registers (eight per
 // thread, enough CTAs for every SM), so the measured rate is the integer
 // pipes' throughput for that instruction mix with no memory traffic.  Every
@@ -106,7 +107,96 @@ __global__ void __launch_bounds__(PK_T) k_peak_mad128(uint64_t* __restrict__ out
     }
 }
 
+// x mod q for a 128-bit x (the base conversions' and inner products' final
+// reduction; the same three-product Barrett form as the library's)
+__device__ __forceinline__ uint64_t barrett128(uint64_t x0, uint64_t x1, uint64_t q, uint64_t r0, uint64_t r1)
+{
+    const uint64_t qhat = x1 * r1 + __umul64hi(x1, r0) + __umul64hi(x0, r1);
+    uint64_t r = x0 - qhat * q;
+    const uint64_t q2 = q << 1;
+    r = r >= q2 ? r - q2 : r;
+    return r >= q ? r - q : r;
+}
+
+__global__ void __launch_bounds__(PK_T) k_peak_reduce(uint64_t* __restrict__ out,
+                                                      unsigned long long* __restrict__ cycles, uint64_t q,
+                                                      uint64_t r0, uint64_t r1, uint32_t iters)
+{
+    uint64_t x0[PK_CHAINS], x1[PK_CHAINS];
+#pragma unroll
+    for (int k = 0; k < PK_CHAINS; k++) {
+        x0[k] = threadIdx.x * 2654435761ull + k * 40503ull + blockIdx.x;
+        x1[k] = (threadIdx.x * 97ull + k) << 20;
+    }
+    const long long t0 = clock64();
+    const uint64_t n0 = pk_ns();
+    for (uint32_t it = 0; it < iters; it++) {
+#pragma unroll
+        for (int k = 0; k < PK_CHAINS; k++) {
+            const uint64_t r = barrett128(x0[k], x1[k], q, r0, r1);
+            x0[k] += r;  // the next input depends on this result
+        }
+    }
+    const long long t1 = clock64();
+    const uint64_t n1 = pk_ns();
+    uint64_t r = 0;
+#pragma unroll
+    for (int k = 0; k < PK_CHAINS; k++) r ^= x0[k];
+    out[blockIdx.x * PK_T + threadIdx.x] = r;
+    if (threadIdx.x == 0) {
+        atomicAdd(cycles, (unsigned long long)(t1 - t0));
+        atomicAdd(cycles + 1, (unsigned long long)(n1 - n0));
+    }
+}
+
 }  // namespace
+
+extern "C" int blb_peaks_reduce_rate(uint64_t q, void* stream, double* per_s, double* per_sm_cycle)
+{
+    if (q < 3 || !(q & 1) || q >= (1ull << 62)) return -1;
+    cudaStream_t st = (cudaStream_t)stream;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return -6;
+    const uint32_t blocks = (uint32_t)sms * 8, iters = 4096;
+    uint64_t* out = nullptr;
+    unsigned long long* cyc = nullptr;
+    if (cudaMalloc(&out, (size_t)blocks * PK_T * 8) != cudaSuccess) return -5;
+    if (cudaMalloc(&cyc, 16) != cudaSuccess) {
+        cudaFree(out);
+        return -5;
+    }
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const unsigned __int128 R = (~(unsigned __int128)0) / q;  // floor(2^128 / q) for odd q
+    double rate = 0, per_cycle = 0;
+    int rc = 0;
+    for (int rep = 0; rep < 2 && !rc; rep++) {  // the first run warms up the clocks
+        if (cudaMemsetAsync(cyc, 0, 16, st) != cudaSuccess) rc = -6;
+        cudaEventRecord(e0, st);
+        k_peak_reduce<<<blocks, PK_T, 0, st>>>(out, cyc, q, (uint64_t)R, (uint64_t)(R >> 64), iters);
+        if (cudaGetLastError() != cudaSuccess) rc = -6;
+        cudaEventRecord(e1, st);
+        if (cudaEventSynchronize(e1) != cudaSuccess) rc = -6;
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        unsigned long long cn[2] = {0, 0};
+        if (cudaMemcpy(cn, cyc, 16, cudaMemcpyDeviceToHost) != cudaSuccess) rc = -6;
+        const double ops = (double)blocks * PK_T * iters * PK_CHAINS;
+        const double ghz = cn[1] ? (double)cn[0] / (double)cn[1] : 1.0;
+        rate = ops / (ms / 1e3);
+        per_cycle = rate / ((double)sms * ghz * 1e9);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(out);
+    cudaFree(cyc);
+    if (rc) return rc;
+    if (per_s) *per_s = rate;
+    if (per_sm_cycle) *per_sm_cycle = per_cycle;
+    return 0;
+}
 
 extern "C" int blb_peaks_int_rates(uint64_t q, void* stream, double* bfly_per_s, double* mad128_per_s,
                                    double* bfly_per_sm_cycle, double* mad128_per_sm_cycle)

@@ -66,12 +66,12 @@ def test_context_without_device_fails_cleanly():
     assert blb.last_error()
 
 
-def test_peaks_library_exports_its_declared_symbol():
-    """The benchmark's integer-rate microbenchmark lives in a library of its own
-    (include/blb_peaks.h, libblb_peaks.so), not in libblb.so."""
+def test_peaks_library_exports_its_declared_symbols():
+    """The benchmark's integer-rate microbenchmarks live in a library of their
+    own (include/blb_peaks.h, libblb_peaks.so), not in libblb.so."""
     src = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "blb_peaks.h")).read(), flags=re.S)
     names = set(re.findall(r"\b(blb_[a-z0-9_]+)\s*\(", src))
-    assert names == {"blb_peaks_int_rates"}
+    assert names == {"blb_peaks_int_rates", "blb_peaks_reduce_rate"}
     L = ctypes.CDLL(build.build_peaks())
     for n in names:
         assert hasattr(L, n)
