@@ -302,6 +302,68 @@ class BertLayer:
             e0 += n_c
         return Y, outs
 
+    # -- the HE parts of segments 3-6 (ciphertexts in, ciphertexts out) --------
+    def he_attention(self, keys_big, Hg, Pc, Rc, Vc):
+        """Segment 3, one head group (on the big context): the exponentials P
+        times the reciprocal row sums R (smul_cc: product and rescale), P V with
+        matmul_cc (Sec. 5.1), and the merge of complementary diagonals of the
+        padded product (App. C.2).  Returns the merged ciphertexts."""
+        big, pl = self.big, self.cc_pv[Hg]
+        Pn = [big.rescale(big.mul(keys_big, p_, r_)) for p_, r_ in zip(Pc, Rc)]
+        C = big.matmul_cc_plan(keys_big, pl, Pn, Vc)
+        half = self.Dh // pl.info()["Kc"]
+        return [big.add(C[j], C[j + half]) for j in range(half)]
+
+    def he_output_projection(self, keys_big, merged):
+        """Segment 3: Concat(Att_h) W_O on the merged diagonals of every head
+        group (the diagonal-input matmul_cp of App. C.2)."""
+        return self.big.matmul_cp_plan(keys_big, self.p_o, merged)
+
+    def he_residual_ln_head(self, ctx, keys, Y, Xres):
+        """Segments 3 and 5: the residual addition and the LayerNorm head (Alg.
+        LayerNorm lines 1-6) on ctx.  Returns (X_mu ciphertexts, [var])."""
+        R = [ctx.add(a, b) for a, b in zip(Y, Xres)]
+        return ctx.layernorm_head(keys, R, self.L, self.d, len(R))
+
+    def he_ln_tail(self, keys, Xm, Rs, gz, bz):
+        """The LayerNorm tail of segments 4 and 6: the centred columns times
+        1/sigma (smul_cc), times gamma (ewmul_cp, mul_const), plus beta
+        (ewadd_cp)."""
+        ctx = self.ctx
+        out = []
+        for c, x in enumerate(Xm):
+            y = ctx.rescale(ctx.mul(keys, x, Rs))
+            y = ctx.mul_const(y, gz[c])
+            out.append(ctx.add_plain(y, ctx.encode(bz[c], y.level, y.scale)))
+        return out
+
+    def he_ffn_up(self, keys, hs):
+        """Segment 4 after the LN1 tail: W_1 (matmul_cp) and, on each output
+        ciphertext x, the two degree-4 GeLU pieces F0 = e + c x^2 + a x^4 - b x^3
+        + (1/2 - d) x and F1 = e + c x^2 + a x^4 + b x^3 + (1/2 + d) x, every term
+        brought to x's scale by mul_const.  Returns (U, F0, F1)."""
+        ctx = self.ctx
+        U = ctx.matmul_cp_plan(keys, self.p_w1, hs)
+        a, b, cc, dd, e = GELU
+        F0s, F1s = [], []
+        for x in U:
+            x2 = ctx.rescale(ctx.mul(keys, x, x))
+            x1d = ctx.drop_level(x, x2.level)
+            x3 = ctx.rescale(ctx.mul(keys, x2, x1d))
+            x4 = ctx.rescale(ctx.mul(keys, x2, x2))
+            tgt = x.scale
+            t4 = ctx.mul_const(x4, a, tgt)
+            t3 = ctx.mul_const(x3, b, tgt)
+            x2d, x1dd = ctx.drop_level(x2, x3.level), ctx.drop_level(x, x3.level)
+            t2 = ctx.mul_const(x2d, cc, tgt)
+            tm = ctx.mul_const(x1dd, 0.5 - dd, tgt)
+            tp = ctx.mul_const(x1dd, 0.5 + dd, tgt)
+            base = ctx.add(t4, t2)
+            base = ctx.add_plain(base, ctx.encode(np.full(ctx.N // 2, e), base.level, base.scale))
+            F0s.append(ctx.add(ctx.sub(base, t3), tm))
+            F1s.append(ctx.add(ctx.add(base, t3), tp))
+        return U, F0s, F1s
+
     # -- the hybrid evaluation --------------------------------------------------
     def forward(self, X, keys, keys_big, mpc, seed=11):
         """X: (L, d) activation (the previous layer's output, as MPC shares).
@@ -375,21 +437,11 @@ class BertLayer:
             Pc = timed("3 attention", lambda: bb.to_ckks(Pz, self.topb), conv)
             Rc = timed("3 attention", lambda: bb.to_ckks(Rz, self.topb), conv)
             Vc = timed("3 attention", lambda: bb.to_ckks(Vz, self.topb - 1), conv)
-
-            def attn():
-                Pn = [big.rescale(big.mul(keys_big, p_, r_)) for p_, r_ in zip(Pc, Rc)]   # smul_cc
-                C = big.matmul_cc_plan(keys_big, pl, Pn, Vc)
-                half = Dh // Kc
-                return [big.add(C[j], C[j + half]) for j in range(half)]
-            merged += timed("3 attention", attn, he)
+            merged += timed("3 attention", lambda: self.he_attention(keys_big, Hg, Pc, Rc, Vc), he)
             h0 += Hg
-        Eo = timed("3 attention", lambda: big.matmul_cp_plan(keys_big, self.p_o, merged), he)
+        Eo = timed("3 attention", lambda: self.he_output_projection(keys_big, merged), he)
         Xres = timed("3 attention", lambda: bb.to_ckks(pack_columns(X, L, kb), Eo[0].level, Eo[0].scale), conv)
-
-        def ln1():
-            R1 = [big.add(a, b) for a, b in zip(Eo, Xres)]
-            return big.layernorm_head(keys_big, R1, L, d, len(R1))
-        Xmu, var = timed("3 attention", ln1, he)
+        Xmu, var = timed("3 attention", lambda: self.he_residual_ln_head(big, keys_big, Eo, Xres), he)
         xmu = unpack_columns(timed("3 attention", lambda: bb.to_mpc(Xmu), conv), L, kb, d)
         v1 = timed("3 attention", lambda: bb.to_mpc(var), conv)[0][:L]
         # MPC: rsqrt
@@ -402,33 +454,9 @@ class BertLayer:
         hs_out = []
 
         def ffn_up():
-            hs = []
-            for c, x in enumerate(Xm):
-                y = ctx.rescale(ctx.mul(keys, x, Rs))                          # smul_cc(X_mu, 1/sigma)
-                y = ctx.mul_const(y, g1z[c])                                  # ewmul_cp gamma
-                y = ctx.add_plain(y, ctx.encode(b1z[c], y.level, y.scale))      # ewadd_cp beta
-                hs.append(y)
+            hs = self.he_ln_tail(keys, Xm, Rs, g1z, b1z)
             hs_out.extend(hs)
-            U = ctx.matmul_cp_plan(keys, self.p_w1, hs)
-            a, b, cc, dd, e = GELU
-            F0s, F1s = [], []
-            for x in U:
-                x2 = ctx.rescale(ctx.mul(keys, x, x))
-                x1d = ctx.drop_level(x, x2.level)
-                x3 = ctx.rescale(ctx.mul(keys, x2, x1d))
-                x4 = ctx.rescale(ctx.mul(keys, x2, x2))
-                tgt = x.scale
-                t4 = ctx.mul_const(x4, a, tgt)
-                t3 = ctx.mul_const(x3, b, tgt)
-                x2d, x1dd = ctx.drop_level(x2, x3.level), ctx.drop_level(x, x3.level)
-                t2 = ctx.mul_const(x2d, cc, tgt)
-                tm = ctx.mul_const(x1dd, 0.5 - dd, tgt)
-                tp = ctx.mul_const(x1dd, 0.5 + dd, tgt)
-                base = ctx.add(t4, t2)
-                base = ctx.add_plain(base, ctx.encode(np.full(ctx.N // 2, e), base.level, base.scale))
-                F0s.append(ctx.add(ctx.sub(base, t3), tm))
-                F1s.append(ctx.add(ctx.add(base, t3), tp))
-            return U, F0s, F1s
+            return self.he_ffn_up(keys, hs)
         U, F0, F1 = timed("4 FFN up", ffn_up, he)
         u = unpack_columns(timed("4 FFN up", lambda: br.to_mpc(U), conv), L, k, f)
         f0 = unpack_columns(timed("4 FFN up", lambda: br.to_mpc(F0), conv), L, k, f)
@@ -441,10 +469,7 @@ class BertLayer:
         W2o = timed("5 FFN down", lambda: ctx.matmul_cp_plan(keys, self.p_w2, Gc), he)
         Hc = timed("5 FFN down", lambda: br.to_ckks(pack_columns(hmid, L, k), W2o[0].level, W2o[0].scale), conv)
 
-        def ln2():
-            R2 = [ctx.add(a_, b_) for a_, b_ in zip(W2o, Hc)]
-            return ctx.layernorm_head(keys, R2, L, d, len(R2))
-        Xmu2, var2 = timed("5 FFN down", ln2, he)
+        Xmu2, var2 = timed("5 FFN down", lambda: self.he_residual_ln_head(ctx, keys, W2o, Hc), he)
         xmu2 = unpack_columns(timed("5 FFN down", lambda: br.to_mpc(Xmu2), conv), L, k, d)
         v2 = timed("5 FFN down", lambda: br.to_mpc(var2), conv)[0][:L]
         rs2 = 1.0 / np.sqrt(v2)
@@ -453,13 +478,6 @@ class BertLayer:
         Rs2 = timed("6 LN2 tail", lambda: br.to_ckks(np.tile(rs2, k)[None], self.top), conv)[0]
         g2z, b2z = pack_columns(np.tile(self.g2, (L, 1)), L, k), pack_columns(np.tile(self.b2, (L, 1)), L, k)
 
-        def tail():
-            out = []
-            for c, x in enumerate(Xm2):
-                y = ctx.rescale(ctx.mul(keys, x, Rs2))
-                y = ctx.mul_const(y, g2z[c])
-                out.append(ctx.add_plain(y, ctx.encode(b2z[c], y.level, y.scale)))
-            return out
-        Yc = timed("6 LN2 tail", tail, he)
+        Yc = timed("6 LN2 tail", lambda: self.he_ln_tail(keys, Xm2, Rs2, g2z, b2z), he)
         Yv = unpack_columns(timed("6 LN2 tail", lambda: br.to_mpc(Yc), conv), L, k, d)
         return Yv, he, conv
