@@ -48,14 +48,12 @@ __global__ void k_gauss_rows(int64_t* __restrict__ out, uint32_t N, const uint32
 
 // signed row c -> residues of limbs 0..n-1: out[(c n + i) N + k]
 __global__ void k_signed_to_limbs(uint64_t* __restrict__ out, const int64_t* __restrict__ in, uint32_t n,
-                                  const uint64_t* __restrict__ qs, uint32_t N)
+                                  const uint64_t* __restrict__ qs, const uint64_t* __restrict__ bar, uint32_t N)
 {
     const uint32_t row = blockIdx.y, k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= N) return;
     const uint32_t c = row / n, i = row % n;
-    const uint64_t q = qs[i];
-    const int64_t v = in[(size_t)c * N + k];
-    out[(size_t)row * N + k] = v >= 0 ? (uint64_t)v % q : q - 1 - ((uint64_t)(-(v + 1)) % q);
+    out[(size_t)row * N + k] = signed_mod(in[(size_t)c * N + k], qs[i], bar[2 * i + 1]);
 }
 
 // encryption of member c, limb i (row = c n + i):
@@ -194,7 +192,7 @@ extern "C" int blb_encrypt_batch(blb_ctx* c, const blb_keys* K, const blb_pt* co
         k_gauss_rows<<<rows_grid(N, count), kT, 0, c->stream>>>(e, N, d_objs, c->d_cdt, K->seed, PURPOSE_ENC_E);
         if (cudaGetLastError() != cudaSuccess) { rc = blb_fail(BLB_ERR_CUDA, "sampling launch failed"); break; }
         blb_count_launch();
-        k_signed_to_limbs<<<rows_grid(N, rows), kT, 0, c->stream>>>(E, e, n, c->d_q, N);
+        k_signed_to_limbs<<<rows_grid(N, rows), kT, 0, c->stream>>>(E, e, n, c->d_q, c->d_bar, N);
         if (cudaGetLastError() != cudaSuccess) { rc = blb_fail(BLB_ERR_CUDA, "conversion launch failed"); break; }
         blb_count_launch();
         if ((rc = ntt_forward(c, E, rows, qm))) break;

@@ -79,6 +79,21 @@ __device__ __forceinline__ uint64_t barrett128(uint64_t x0, uint64_t x1, uint64_
     return r >= q ? r - q : r;
 }
 
+// x mod q for any 64-bit x, with rb = floor(2^64 / q) (the high word of the
+// Barrett constant floor(2^128 / q)): floor(x rb / 2^64) is at least
+// floor(x / q) - 1 and at most x / q, so one conditional subtraction lands in
+// [0, q).  No division.
+__device__ __forceinline__ uint64_t reduce64(uint64_t x, uint64_t q, uint64_t rb)
+{
+    const uint64_t r = x - __umul64hi(x, rb) * q;
+    return r >= q ? r - q : r;
+}
+// a signed 64-bit v mod q, in [0, q)
+__device__ __forceinline__ uint64_t signed_mod(int64_t v, uint64_t q, uint64_t rb)
+{
+    return v >= 0 ? reduce64((uint64_t)v, q, rb) : q - 1 - reduce64((uint64_t)(-(v + 1)), q, rb);
+}
+
 __device__ __forceinline__ uint64_t mul_mod(uint64_t a, uint64_t b, uint64_t q, uint64_t r0, uint64_t r1)
 {
     return barrett128(a * b, __umul64hi(a, b), q, r0, r1);

@@ -106,7 +106,8 @@ __global__ void __launch_bounds__(kT) k_dit_cols(double2* __restrict__ A, uint32
 // twist by zeta^-t, scale, round half to even, residues: out[pt][i][t], [t+s]
 __global__ void k_twist_round(uint64_t* __restrict__ out, const double2* __restrict__ A, uint32_t logs,
                               const double2* __restrict__ zeta, double f, uint32_t nlimbs,
-                              const uint64_t* __restrict__ qs, int* __restrict__ overflow)
+                              const uint64_t* __restrict__ qs, const uint64_t* __restrict__ bar,
+                              int* __restrict__ overflow)
 {
     const uint32_t s = 1u << logs, N = 2 * s;
     const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x, pt = blockIdx.y;
@@ -118,9 +119,8 @@ __global__ void k_twist_round(uint64_t* __restrict__ out, const double2* __restr
     if (fabs(re) >= 9.2e18 || fabs(im) >= 9.2e18) *overflow = 1;
     long long mr = __double2ll_rn(re), mi = __double2ll_rn(im);
     for (uint32_t i = 0; i < nlimbs; i++) {
-        const uint64_t q = qs[i];
-        uint64_t r0 = mr >= 0 ? (uint64_t)mr % q : q - 1 - ((uint64_t)(-(mr + 1)) % q);
-        uint64_t r1 = mi >= 0 ? (uint64_t)mi % q : q - 1 - ((uint64_t)(-(mi + 1)) % q);
+        const uint64_t q = qs[i], rb = bar[2 * i + 1];
+        const uint64_t r0 = signed_mod(mr, q, rb), r1 = signed_mod(mi, q, rb);
         uint64_t* o = out + ((size_t)pt * nlimbs + i) * N;
         o[t] = r0;
         o[t + s] = r1;
@@ -228,7 +228,7 @@ int encode_slots(blb_ctx* ctx, const double* d_z, uint32_t npts, uint32_t n, uin
         if (cudaMemsetAsync(ctx->d_flag, 0, sizeof(int), ctx->stream) != cudaSuccess) { rc = blb_fail(BLB_ERR_CUDA, "memset failed"); break; }
         const double f = scale / (double)s;
         k_twist_round<<<dim3((s + kT - 1) / kT, npts), kT, 0, ctx->stream>>>(d_out, A, logs, ctx->d_zeta, f, nl,
-                                                                            ctx->d_q, ctx->d_flag);
+                                                                            ctx->d_q, ctx->d_bar, ctx->d_flag);
         if (cudaGetLastError() != cudaSuccess) { rc = blb_fail(BLB_ERR_CUDA, "twist launch failed"); break; }
         if ((rc = ntt_forward(ctx, d_out, npts * nl, ctx->qmap(nl)))) break;
         int flag = 0;

@@ -63,14 +63,12 @@ __global__ void k_automorph_ntt(uint64_t* __restrict__ out, const uint64_t* __re
 }
 
 __global__ void k_signed_to_rows(uint64_t* __restrict__ out, const int64_t* __restrict__ in, const __grid_constant__ LimbMap map,
-                                 const uint64_t* __restrict__ qs, uint32_t N)
+                                 const uint64_t* __restrict__ qs, const uint64_t* __restrict__ bar, uint32_t N)
 {
     const uint32_t row = blockIdx.y, c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= N) return;
-    const uint64_t q = qs[map.p[row % map.n]];
-    int64_t v = in[c];
-    uint64_t r = v >= 0 ? (uint64_t)v % q : q - 1 - ((uint64_t)(-(v + 1)) % q);
-    out[(size_t)row * N + c] = r;
+    const uint32_t pi = map.p[row % map.n];
+    out[(size_t)row * N + c] = signed_mod(in[c], qs[pi], bar[2 * pi + 1]);
 }
 
 // --- Philox draws: counter (coefficient i, sub-index j, object, purpose) ---
@@ -147,19 +145,20 @@ __global__ void k_rescale_finish(uint64_t* __restrict__ out, const uint64_t* __r
 
 // centered lift of the q_l limb (coefficient form) reduced mod q_i, i < level
 __global__ void k_lift_last(uint64_t* __restrict__ T, const uint64_t* __restrict__ last,
-                            const uint64_t* __restrict__ qs, uint32_t N, uint32_t level)
+                            const uint64_t* __restrict__ qs, const uint64_t* __restrict__ bar, uint32_t N,
+                            uint32_t level)
 {
     const uint32_t row = blockIdx.y, c = blockIdx.x * blockDim.x + threadIdx.x;  // row = poly * level + i
     if (c >= N) return;
     const uint32_t poly = row / level, i = row % level;
-    const uint64_t ql = qs[level], q = qs[i];
+    const uint64_t ql = qs[level], q = qs[i], rb = bar[2 * i + 1];
     uint64_t v = last[(size_t)poly * N + c];
     uint64_t r;
     if (v > ql / 2) {  // negative representative v - q_l
-        uint64_t m = (ql - v) % q;
+        uint64_t m = reduce64(ql - v, q, rb);
         r = m ? q - m : 0;
     } else {
-        r = v % q;
+        r = reduce64(v, q, rb);
     }
     T[(size_t)row * N + c] = r;
 }
@@ -263,7 +262,7 @@ int launch_automorph_ntt(blb_ctx* ctx, uint64_t* out, const uint64_t* in, uint32
 int launch_signed_to_rows(blb_ctx* ctx, uint64_t* out, const int64_t* in, uint32_t rows, const LimbMap& map)
 {
     if (!rows) return BLB_OK;
-    k_signed_to_rows<<<grid_rows(ctx->N, rows), kT, 0, ctx->stream>>>(out, in, map, ctx->d_q, ctx->N);
+    k_signed_to_rows<<<grid_rows(ctx->N, rows), kT, 0, ctx->stream>>>(out, in, map, ctx->d_q, ctx->d_bar, ctx->N);
     BLB_LAUNCHED();
     return BLB_OK;
 }
@@ -328,7 +327,7 @@ int launch_rescale_strided(blb_ctx* ctx, uint64_t* out, const uint64_t* in, uint
         blb_count_launch();
         if ((rc = ntt_inverse(ctx, last, npolys, ctx->qmap(1, level)))) break;
         const uint32_t rows = npolys * level;
-        k_lift_last<<<grid_rows(N, rows), kT, 0, ctx->stream>>>(T, last, ctx->d_q, N, level);
+        k_lift_last<<<grid_rows(N, rows), kT, 0, ctx->stream>>>(T, last, ctx->d_q, ctx->d_bar, N, level);
         if (cudaGetLastError() != cudaSuccess) { rc = blb_fail(BLB_ERR_CUDA, "rescale launch failed"); break; }
         blb_count_launch();
         if ((rc = ntt_forward(ctx, T, rows, ctx->qmap(level)))) break;

@@ -148,6 +148,10 @@ __global__ void __launch_bounds__(kS2) k_cc_step2(uint64_t* __restrict__ U, cons
     if (k >= N) return;
     const uint32_t g = t / b1s2, b = t % b1s2;
     const uint64_t q = qs[i], r0 = bar[2 * i], r1 = bar[2 * i + 1];
+    // lazy 128-bit sums: every product is below (2q)^2; for q < 2^50 that is
+    // 2^102, so any count of input ciphertexts below 2^25 sums without a
+    // reduction; larger primes reduce every 8 terms (8 (2q)^2 < 2^128 for q < 2^62)
+    const bool reduce8 = q >= (1ull << 50);
     const size_t nN = (size_t)n * N, off = (size_t)i * N + k, cw = 2 * nN;
     const MaskPair mp = masks[t];
     const bool use_lo = mp.lo != nullptr, use_hi = mp.hi != nullptr;
@@ -162,7 +166,7 @@ __global__ void __launch_bounds__(kS2) k_cc_step2(uint64_t* __restrict__ U, cons
             mad128(z0, a0, v0);
             mad128(z2, a1, v1);
             mad128(zs, a0 + a1, v0 + v1);
-            if ((c & 7) == 7) {
+            if (reduce8 && (c & 7) == 7) {
                 z0 = acc128{barrett128(z0.lo, z0.hi, q, r0, r1), 0};
                 zs = acc128{barrett128(zs.lo, zs.hi, q, r0, r1), 0};
                 z2 = acc128{barrett128(z2.lo, z2.hi, q, r0, r1), 0};
