@@ -25,8 +25,9 @@
 // Reduction: for primes q >= 2^(63 - logN) the butterflies reduce lazily
 // (Harvey): forward values stay in [0, 4q), inverse values in [0, 2q).  For
 // smaller primes no butterfly needs a conditional subtraction: forward values
-// grow by at most 2q per stage, inverse sums at most double per stage, and
-// both stay below 2^64; the last pass reduces once.
+// grow by at most 4q per stage (their products use a cheaper quotient
+// estimate, within [0, 4q)), inverse sums at most double per stage, and both
+// stay below 2^64 ((1 + 4 logN) q < 2^64); the last pass reduces once.
 //
 // Every pass is launched with programmatic stream serialization and starts
 // with pdl_begin, so it can be scheduled while the previous kernel drains.
@@ -73,13 +74,25 @@ __device__ __forceinline__ void bfly_fwd(uint64_t& X, uint64_t& Y, ulonglong2 w,
     Y = x + q2 - t;
 }
 
-// forward, small prime: X + t, X - t + 2q with t = W Y in [0, 2q), no reduction
+// Shoup product with the quotient estimate from the three high 32 x 32-bit
+// partial products of Y wp (the low one and the low halves of the middle two
+// dropped): the estimate is at most 2 below floor(Y wp / 2^64), so the result
+// is in [0, 4q) for any 64-bit Y.
+__device__ __forceinline__ uint64_t mul_shoup_lazy4(uint64_t x, uint64_t w, uint64_t wp, uint64_t q)
+{
+    const uint32_t xl = (uint32_t)x, xh = (uint32_t)(x >> 32), pl = (uint32_t)wp, ph = (uint32_t)(wp >> 32);
+    const uint64_t qt = (uint64_t)xh * ph + __umulhi(xh, pl) + __umulhi(xl, ph);
+    return x * w - qt * q;
+}
+
+// forward, small prime: X + t, X - t + 4q with t = W Y in [0, 4q), no reduction
+// (values grow by at most 4q per stage)
 __device__ __forceinline__ void bfly_fwd_s(uint64_t& X, uint64_t& Y, ulonglong2 w, uint64_t q, uint64_t q2)
 {
-    const uint64_t t = mul_shoup_lazy(Y, w.x, w.y, q);
+    const uint64_t t = mul_shoup_lazy4(Y, w.x, w.y, q);
     const uint64_t x = X;
     X = x + t;
-    Y = x + q2 - t;
+    Y = x + 2 * q2 - t;
 }
 
 // inverse, lazy: X, Y in [0, 2q) -> X + Y, W (X - Y) in [0, 2q)
