@@ -109,6 +109,16 @@ uint64_t blb_ctx_bytes_in_use(const blb_ctx* ctx);
  * usable.  Copies already in flight are always waited for (up to 2 s) before a
  * block exits, whatever the limit.  Applies to calls made after it. */
 int blb_ctx_set_wait_limit(blb_ctx* ctx, uint64_t limit_ns);
+/* Deferred encoding checks.  By default an encoding (blb_encode,
+ * blb_encode_batch, and the plaintext encodings inside other calls) waits for
+ * its kernels and returns BLB_ERR_ARG when a coefficient exceeds 2^63 (value x
+ * scale too large).  With on != 0 encodings do not wait: the overflow
+ * condition of every encoding accumulates on the device, and the next
+ * blb_ctx_sync returns BLB_ERR_ARG (and clears it) if any overflowed; the
+ * outputs of the calls since the previous sync are then invalid.  This keeps
+ * the host from stalling on the device once per encoding.  on = 0 restores
+ * the default for later calls. */
+int blb_ctx_set_deferred_encode_check(blb_ctx* ctx, int on);
 /* Test hook for that error path: with withhold != 0 the pipeline's copy
  * stage issues no copies, so the consumers' waits run out (after the limit
  * above) instead of completing.  Products computed meanwhile are invalid.
@@ -489,6 +499,11 @@ uint64_t blb_kernel_launches(void);
  * baby-step ciphertext and every partial sum once).  Enabling resets the sums. */
 int blb_profile_enable(blb_ctx* ctx, int on);
 int blb_profile_read(blb_ctx* ctx, const char* site, double* ms, uint64_t* count, uint64_t* bytes);
+/* Bracket only the named site while profiling (NULL: every site, the default).
+ * Each bracket is a pair of CUDA events on the stream, which also keeps the
+ * next kernel from being scheduled early (programmatic dependent launch), so
+ * fewer sites perturb the timed work less. */
+int blb_profile_select(blb_ctx* ctx, const char* site);
 /* The arithmetic of the calls bracketed at `site` since profiling was enabled,
  * for an ALU roofline beside the bytes: 64 x 64 -> 128-bit multiply-adds,
  * reductions of a 128-bit sum mod a prime, and NTT butterflies (a Shoup product

@@ -119,6 +119,8 @@ SIGNATURES = {
     "blb_profile_enable": (ctypes.c_int, [_vp, ctypes.c_int]),
     "blb_profile_read": (ctypes.c_int, [_vp, ctypes.c_char_p, _vp, _vp, _vp]),
     "blb_profile_read_ops": (ctypes.c_int, [_vp, ctypes.c_char_p, _vp, _vp, _vp]),
+    "blb_ctx_set_deferred_encode_check": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "blb_profile_select": (ctypes.c_int, [_vp, ctypes.c_char_p]),
 }
 
 _lib = None
@@ -315,6 +317,11 @@ class Context:
     def set_wait_limit(self, limit_ns):
         """Limit of the bounded device waits in nanoseconds (0 = 2 s)."""
         _check(lib().blb_ctx_set_wait_limit(self.h, _u64(limit_ns)))
+
+    def set_deferred_encode_check(self, on=True):
+        """Encodings stop waiting for their overflow check; sync() raises if
+        any encoding since the last sync overflowed."""
+        _check(lib().blb_ctx_set_deferred_encode_check(self.h, int(on)))
 
     def set_batch_mac(self, kind):
         """MAC kernel of batched products: 0 automatic, 1 mma.sync, 2 tcgen05."""
@@ -639,8 +646,10 @@ class Context:
         _check(lib().blb_he2mpc_batch(self.h, keys.h, cs, count, ns.ctypes.data, out, _ptr(share_out)))
         return [Ciphertext(self, c) for c in out], share_out
 
-    def profile(self, on=True):
+    def profile(self, on=True, only=None):
+        """Enable (and reset) the per-site CUDA-event profile; only: one site name."""
         _check(lib().blb_profile_enable(self.h, int(on)))
+        _check(lib().blb_profile_select(self.h, only.encode() if only else None))
 
     def profile_read(self, site):
         ms, cnt, nb = _dbl(), _u64(), _u64()

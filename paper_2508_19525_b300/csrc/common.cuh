@@ -194,6 +194,10 @@ struct blb_ctx {
     uint64_t* d_cdt = nullptr;        // [19]
     uint32_t* d_kperm = nullptr;      // [N/2]: k_j = (5^j mod 2N - 1)/4
     int* d_flag = nullptr;            // device status word (encoding overflow)
+    // deferred encoding checks: the overflow flag of every encoding accumulates
+    // here and blb_ctx_sync reports it (no host wait per encoding)
+    bool encode_deferred = false;
+    int* d_flag_deferred = nullptr;
     uint32_t* d_status = nullptr;     // set by a kernel whose bounded wait expired
     uint64_t wait_ns = 0;             // limit of the bounded device waits (0: the 2 s default)
     uint32_t mac_withhold = 0;        // test hook: the plaintext streamer issues nothing (waits run out)
@@ -233,6 +237,7 @@ struct blb_ctx {
         uint64_t mad128 = 0, reductions = 0, butterflies = 0;
     };
     std::vector<ProfSite> prof;
+    std::string prof_only;  // when not empty, only this site is bracketed
     std::vector<cudaEvent_t> event_pool;
     // grow-only arena for batched key switching (stream-ordered reuse)
     uint64_t* batch = nullptr;

@@ -45,6 +45,7 @@ static cudaEvent_t pool_event(blb_ctx* c)
 ProfScope::ProfScope(blb_ctx* ctx, const char* name, uint64_t algorithmic_bytes) : c(ctx), site(-1)
 {
     if (!c || !c->profiling || capturing(c)) return;  // a captured launch has no time of its own
+    if (!c->prof_only.empty() && c->prof_only != name) return;
     for (size_t i = 0; i < c->prof.size(); i++)
         if (c->prof[i].name == name) site = (int)i;
     if (site < 0) {
@@ -92,6 +93,13 @@ extern "C" int blb_profile_enable(blb_ctx* c, int on)
     prof_collect(c);
     c->prof.clear();
     c->profiling = on != 0;
+    return BLB_OK;
+}
+
+extern "C" int blb_profile_select(blb_ctx* c, const char* site)
+{
+    if (!c) return blb_fail(BLB_ERR_ARG, "null context");
+    c->prof_only = site ? site : "";
     return BLB_OK;
 }
 
@@ -450,6 +458,7 @@ extern "C" int blb_ctx_create(const blb_params* params, void* stream, blb_ctx** 
         if ((rc = upload(c, &c->d_kperm, kp.data(), s))) return fail(rc);
         int zero = 0;
         if ((rc = upload(c, &c->d_flag, &zero, 1))) return fail(rc);
+        if ((rc = upload(c, &c->d_flag_deferred, &zero, 1))) return fail(rc);
         uint32_t uzero = 0;
         if ((rc = upload(c, &c->d_status, &uzero, 1))) return fail(rc);
     }
@@ -588,6 +597,7 @@ static void ctx_destroy(blb_ctx* c)
     dev_free(c, c->d_cdt, 19 * 8);
     dev_free(c, c->d_kperm, (size_t)c->N / 2 * 4);
     dev_free(c, c->d_flag, sizeof(int));
+    dev_free(c, c->d_flag_deferred, sizeof(int));
     dev_free(c, c->d_status, sizeof(uint32_t));
     for (auto& k : c->graph_keep) {
         if (k.second) dev_free(c, k.first, k.second);
@@ -631,6 +641,19 @@ extern "C" int blb_ctx_sync(blb_ctx* c)
         BLB_CUDA(cudaMemset(c->d_status, 0, sizeof(st)));
         return blb_fail(BLB_ERR_TIMEOUT, "a bounded device wait expired (plaintext product pipeline)");
     }
+    int ov = 0;
+    BLB_CUDA(cudaMemcpy(&ov, c->d_flag_deferred, sizeof(ov), cudaMemcpyDeviceToHost));
+    if (ov) {
+        BLB_CUDA(cudaMemset(c->d_flag_deferred, 0, sizeof(ov)));
+        return blb_fail(BLB_ERR_ARG, "an encoding with deferred checks overflowed: value * scale too large");
+    }
+    return BLB_OK;
+}
+
+extern "C" int blb_ctx_set_deferred_encode_check(blb_ctx* c, int on)
+{
+    if (!c) return blb_fail(BLB_ERR_ARG, "null context");
+    c->encode_deferred = on != 0;
     return BLB_OK;
 }
 

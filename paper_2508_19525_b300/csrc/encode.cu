@@ -225,12 +225,15 @@ int encode_slots(blb_ctx* ctx, const double* d_z, uint32_t npts, uint32_t n, uin
         k_scatter_slots<<<dim3((s + kT - 1) / kT, npts), kT, 0, ctx->stream>>>(A, d_z, n, logs, ctx->d_kperm);
         if (cudaGetLastError() != cudaSuccess) { rc = blb_fail(BLB_ERR_CUDA, "scatter launch failed"); break; }
         if ((rc = run_dit(ctx, A, npts, 1, ctx->d_zeta))) break;
-        if (cudaMemsetAsync(ctx->d_flag, 0, sizeof(int), ctx->stream) != cudaSuccess) { rc = blb_fail(BLB_ERR_CUDA, "memset failed"); break; }
+        // deferred checks: the flag accumulates until blb_ctx_sync reads it
+        int* flag_dev = ctx->encode_deferred ? ctx->d_flag_deferred : ctx->d_flag;
+        if (!ctx->encode_deferred && cudaMemsetAsync(ctx->d_flag, 0, sizeof(int), ctx->stream) != cudaSuccess) { rc = blb_fail(BLB_ERR_CUDA, "memset failed"); break; }
         const double f = scale / (double)s;
         k_twist_round<<<dim3((s + kT - 1) / kT, npts), kT, 0, ctx->stream>>>(d_out, A, logs, ctx->d_zeta, f, nl,
-                                                                            ctx->d_q, ctx->d_bar, ctx->d_flag);
+                                                                            ctx->d_q, ctx->d_bar, flag_dev);
         if (cudaGetLastError() != cudaSuccess) { rc = blb_fail(BLB_ERR_CUDA, "twist launch failed"); break; }
         if ((rc = ntt_forward(ctx, d_out, npts * nl, ctx->qmap(nl)))) break;
+        if (ctx->encode_deferred) break;
         int flag = 0;
         if (cudaMemcpyAsync(&flag, ctx->d_flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess ||
             cudaStreamSynchronize(ctx->stream) != cudaSuccess) { rc = blb_fail(BLB_ERR_CUDA, "encode sync failed"); break; }

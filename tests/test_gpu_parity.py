@@ -91,6 +91,31 @@ def test_encode_rejects_overflow():
         ctx.encode(np.full(16, 1e12), 2, 2.0 ** 40)
 
 
+def test_deferred_encode_check_reports_overflow_at_sync():
+    """With deferred checks an overflowing encoding returns at once and the
+    next sync reports it (once); an encoding that fits leaves sync clean and
+    gives the same limbs as the checked encoding."""
+    from paper_2508_19525_b300 import blb
+    prm = wl.TINY
+    o, ctx = make_oracle(prm), make_ctx(prm)
+    z = wl.slot_vector(o.N // 2, seed=5)
+    ref = ctx.pt_export(ctx.encode(z, 2, prm.scale), 2)
+    ctx.set_deferred_encode_check(True)
+    pt = ctx.encode(z, 2, prm.scale)
+    ctx.sync()
+    assert np.array_equal(ctx.pt_export(pt, 2), ref)
+    ctx.encode(np.full(16, 1e12), 2, 2.0 ** 40)
+    ctx.encode(z, 2, prm.scale)  # a later good encoding does not clear the condition
+    with pytest.raises(blb.BlbError) as e:
+        ctx.sync()
+    assert e.value.code == blb.ERR_ARG
+    ctx.sync()  # cleared
+    ctx.set_deferred_encode_check(False)
+    with pytest.raises(blb.BlbError):
+        ctx.encode(np.full(16, 1e12), 2, 2.0 ** 40)
+    ctx.sync()
+
+
 # ------------------------------------------------------------------ encryption
 def test_encrypt_decrypt_parity(pair):
     prm, o, ctx = pair
