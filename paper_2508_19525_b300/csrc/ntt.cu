@@ -128,11 +128,40 @@ struct Geo {
     static constexpr int LOGN2 = LOGN - LP;
 };
 
+// Finishing step of the transform's last pass (applied as the results are
+// stored): the inverse multiplies by N^-1 (or the given factor), both reduce
+// to [0, q)
+struct Fin {
+    uint64_t ni, nis, r1;
+    bool small;
+};
+
+template <bool INV, bool LAST>
+__device__ __forceinline__ uint64_t finish_value(uint64_t v, const Fin& f, uint64_t q, uint64_t q2)
+{
+    if (!LAST) return v;
+    if (INV) v = mul_shoup_lazy(v, f.ni, f.nis, q);
+    else if (f.small) v = v - __umul64hi(v, f.r1) * q;  // any 64-bit v -> [0, 2q)
+    else v = v >= q2 ? v - q2 : v;
+    return v >= q ? v - q : v;
+}
+
+// global position (within the row) of tile element e
+template <int LOGN, int LP, bool COLS>
+__device__ __forceinline__ size_t tile_pos(uint32_t e, uint32_t c0)
+{
+    using G_ = Geo<LOGN, LP, COLS>;
+    if (COLS) return ((size_t)(e >> G_::LOGNSUB) << G_::LOGN2) + c0 + (e & (G_::NSUB - 1));
+    return ((size_t)c0 << LP) + e;
+}
+
 // One round: R stages on groups of 2^R elements whose local indices differ in
-// bits [PLO, PLO + R).
-template <int LOGN, int LP, bool COLS, bool INV, bool SMALL, int PLO, int R>
-__device__ __forceinline__ void round(uint64_t* sm, uint32_t c0, const ulonglong2* __restrict__ W, uint64_t q,
-                                      uint64_t q2)
+// bits [PLO, PLO + R).  The pass's first round reads its groups from the row
+// in global memory (FROM_G) and its last round writes them back, finished
+// (TO_G); the rounds between go through the tile in shared memory.
+template <int LOGN, int LP, bool COLS, bool INV, bool SMALL, int PLO, int R, bool FROM_G, bool TO_G, bool LAST>
+__device__ __forceinline__ void round(uint64_t* sm, uint64_t* __restrict__ a, uint32_t c0,
+                                      const ulonglong2* __restrict__ W, uint64_t q, uint64_t q2, const Fin& fin)
 {
     using G_ = Geo<LOGN, LP, COLS>;
     constexpr uint32_t K = 1u << R;
@@ -160,7 +189,10 @@ __device__ __forceinline__ void round(uint64_t* sm, uint32_t c0, const ulonglong
         }
         uint64_t x[K];
 #pragma unroll
-        for (uint32_t k = 0; k < K; k++) x[k] = sm[padi(e_base + k * e_stride)];
+        for (uint32_t k = 0; k < K; k++) {
+            const uint32_t e = e_base + k * e_stride;
+            x[k] = FROM_G ? a[tile_pos<LOGN, LP, COLS>(e, c0)] : sm[padi(e)];
+        }
         // The butterflied bits of base_r are zero, so for the pair (k, k | 2^u)
         // the lower element's twiddle index splits into a per-stage base plus
         // k >> (u + 1): stage u uses 2^(R-1-u) distinct twiddles.
@@ -198,32 +230,38 @@ __device__ __forceinline__ void round(uint64_t* sm, uint32_t c0, const ulonglong
             }
         }
 #pragma unroll
-        for (uint32_t k = 0; k < K; k++) sm[padi(e_base + k * e_stride)] = x[k];
+        for (uint32_t k = 0; k < K; k++) {
+            const uint32_t e = e_base + k * e_stride;
+            if (TO_G) a[tile_pos<LOGN, LP, COLS>(e, c0)] = finish_value<INV, LAST>(x[k], fin, q, q2);
+            else sm[padi(e)] = x[k];
+        }
     }
 }
 
 // forward rounds: local bits from the top down, up to RB stages per round
-// (radix 2^RB)
-template <int LOGN, int LP, bool COLS, bool SMALL, int PHI, int RB>
-__device__ __forceinline__ void fwd_rounds(uint64_t* sm, uint32_t c0, const ulonglong2* W, uint64_t q, uint64_t q2)
+// (radix 2^RB); the first reads the row, the last writes it
+template <int LOGN, int LP, bool COLS, bool SMALL, int PHI, int RB, bool LAST>
+__device__ __forceinline__ void fwd_rounds(uint64_t* sm, uint64_t* a, uint32_t c0, const ulonglong2* W, uint64_t q,
+                                           uint64_t q2, const Fin& fin)
 {
     if constexpr (PHI > 0) {
         constexpr int R = PHI >= RB ? RB : PHI;
-        round<LOGN, LP, COLS, false, SMALL, PHI - R, R>(sm, c0, W, q, q2);
-        __syncthreads();
-        fwd_rounds<LOGN, LP, COLS, SMALL, PHI - R, RB>(sm, c0, W, q, q2);
+        round<LOGN, LP, COLS, false, SMALL, PHI - R, R, PHI == LP, PHI - R == 0, LAST>(sm, a, c0, W, q, q2, fin);
+        if constexpr (PHI - R > 0) __syncthreads();
+        fwd_rounds<LOGN, LP, COLS, SMALL, PHI - R, RB, LAST>(sm, a, c0, W, q, q2, fin);
     }
 }
 
 // inverse rounds: local bits from the bottom up
-template <int LOGN, int LP, bool COLS, bool SMALL, int PLO, int RB>
-__device__ __forceinline__ void inv_rounds(uint64_t* sm, uint32_t c0, const ulonglong2* W, uint64_t q, uint64_t q2)
+template <int LOGN, int LP, bool COLS, bool SMALL, int PLO, int RB, bool LAST>
+__device__ __forceinline__ void inv_rounds(uint64_t* sm, uint64_t* a, uint32_t c0, const ulonglong2* W, uint64_t q,
+                                           uint64_t q2, const Fin& fin)
 {
     if constexpr (PLO < LP) {
         constexpr int R = LP - PLO >= RB ? RB : LP - PLO;
-        round<LOGN, LP, COLS, true, SMALL, PLO, R>(sm, c0, W, q, q2);
-        __syncthreads();
-        inv_rounds<LOGN, LP, COLS, SMALL, PLO + R, RB>(sm, c0, W, q, q2);
+        round<LOGN, LP, COLS, true, SMALL, PLO, R, PLO == 0, PLO + R == LP, LAST>(sm, a, c0, W, q, q2, fin);
+        if constexpr (PLO + R < LP) __syncthreads();
+        inv_rounds<LOGN, LP, COLS, SMALL, PLO + R, RB, LAST>(sm, a, c0, W, q, q2, fin);
     }
 }
 
@@ -250,38 +288,20 @@ __global__ void __launch_bounds__(kThreads, ntt_ctas(RB)) k_ntt(uint64_t* __rest
     const uint64_t q = qs[pi], q2 = 2 * q;
     const ulonglong2* W = tw + ((size_t)pi * 2 + (INV ? 1 : 0)) * G_::N;
     uint64_t* a = data + (size_t)row * G_::N;
-    // load the tile: element e = r * nsub + sub (columns) or sub * L + r (rows)
-#pragma unroll
-    for (uint32_t e = threadIdx.x; e < G_::TILE; e += kThreads) {
-        if (COLS) sm[padi(e)] = a[((size_t)(e >> G_::LOGNSUB) << G_::LOGN2) + c0 + (e & (G_::NSUB - 1))];
-        else sm[padi(e)] = a[((size_t)c0 << LP) + e];
-    }
-    __syncthreads();
-    const bool small = small_prime(q, LOGN);
-    if (!INV) {
-        if (small) fwd_rounds<LOGN, LP, COLS, true, LP, RB>(sm, c0, W, q, q2);
-        else fwd_rounds<LOGN, LP, COLS, false, LP, RB>(sm, c0, W, q, q2);
-    } else {
-        if (small) inv_rounds<LOGN, LP, COLS, true, 0, RB>(sm, c0, W, q, q2);
-        else inv_rounds<LOGN, LP, COLS, false, 0, RB>(sm, c0, W, q, q2);
-    }
-    uint64_t ni = 0, nis = 0, r1 = 0;
+    Fin fin{0, 0, 0, small_prime(q, LOGN)};
     if (INV && LAST) {
-        ni = ninv[2 * pi];
-        nis = ninv[2 * pi + 1];
+        fin.ni = ninv[2 * pi];
+        fin.nis = ninv[2 * pi + 1];
     }
-    if (!INV && LAST) r1 = bar[2 * pi + 1];  // floor(2^64 / q)
-    auto finish = [&](uint64_t v) -> uint64_t {
-        if (!LAST) return v;
-        if (INV) v = mul_shoup_lazy(v, ni, nis, q);
-        else if (small) v = v - __umul64hi(v, r1) * q;  // any 64-bit v -> [0, 2q)
-        else v = v >= q2 ? v - q2 : v;
-        return v >= q ? v - q : v;
-    };
-#pragma unroll
-    for (uint32_t e = threadIdx.x; e < G_::TILE; e += kThreads) {
-        if (COLS) a[((size_t)(e >> G_::LOGNSUB) << G_::LOGN2) + c0 + (e & (G_::NSUB - 1))] = finish(sm[padi(e)]);
-        else a[((size_t)c0 << LP) + e] = finish(sm[padi(e)]);
+    if (!INV && LAST) fin.r1 = bar[2 * pi + 1];  // floor(2^64 / q)
+    // the first round loads its groups from the row and the last stores them,
+    // so the tile passes through shared memory only between rounds
+    if (!INV) {
+        if (fin.small) fwd_rounds<LOGN, LP, COLS, true, LP, RB, LAST>(sm, a, c0, W, q, q2, fin);
+        else fwd_rounds<LOGN, LP, COLS, false, LP, RB, LAST>(sm, a, c0, W, q, q2, fin);
+    } else {
+        if (fin.small) inv_rounds<LOGN, LP, COLS, true, 0, RB, LAST>(sm, a, c0, W, q, q2, fin);
+        else inv_rounds<LOGN, LP, COLS, false, 0, RB, LAST>(sm, a, c0, W, q, q2, fin);
     }
 }
 
