@@ -12,8 +12,10 @@
 // pair elements N2 or more apart on sub-transforms {c + N2 r}, the "row" pass
 // runs the remaining stages on contiguous blocks of N2.  Every pass reads and
 // writes each word once.  Inside a pass each thread holds a group of up to 8
-// elements in registers and runs up to 3 stages on it (radix 8), so a pass
-// needs 2-3 shared-memory round trips instead of one per stage; radix 8 fits
+// elements in registers and runs up to 3 stages on it (radix 8); the first
+// round loads its groups from global memory and the last stores them, so a
+// pass of two or three rounds makes one or two shared-memory round trips
+// instead of one per stage; radix 8 fits
 // 64 registers, so four CTAs run per SM (measured on the B300 against radix 16
 // at three CTAs and radix 8 at three or five).  Shared memory is padded by one
 // word every 16 to keep strided group accesses conflict-free.
