@@ -108,11 +108,13 @@ __device__ __forceinline__ void bfly_inv(uint64_t& X, uint64_t& Y, ulonglong2 w,
 }
 
 // inverse, small prime, stage inputs below C = 2^(lt+1) q: X + Y, W (X - Y + C)
+// with the cheaper quotient estimate (in [0, 4q), still below 2^(lt+2) q, the
+// next stage's bound, for every stage lt >= 0)
 __device__ __forceinline__ void bfly_inv_s(uint64_t& X, uint64_t& Y, ulonglong2 w, uint64_t q, uint64_t C)
 {
     const uint64_t x = X, y = Y;
     X = x + y;
-    Y = mul_shoup_lazy(x + C - y, w.x, w.y, q);
+    Y = mul_shoup_lazy4(x + C - y, w.x, w.y, q);
 }
 
 __device__ __forceinline__ bool small_prime(uint64_t q, uint32_t logN) { return q < (1ull << (63 - logN)); }
