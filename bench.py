@@ -568,28 +568,28 @@ def cfg4_batching(n_seqs=8, plain_chunks=6, candidates=(16, 32, 64, 128), groups
     return out
 
 
-def cfg4_attention(ctx, stream, lengths, heads=16, dh=64, seed=45, check=2):
-    """The ct-ct attention products of the BERT-large-shaped sequences: per
-    sequence, Q_h K_h^T and P_h V_h for its 16 heads in one group (matmul_cc,
-    Sec. 5.1), the length padded to a power of two L >= 64 (Kc = N/2/(16 L) <= L)
-    with zero rows and columns past the sequence's end, V_h padded to L columns
-    for the square diagonal-packed output.  One plan pair per padded length,
-    the Galois keys of all of them; each product timed with CUDA events after
-    one warm-up product per plan; the first `check` sequences decrypted against
-    FP64.  Then every product of every sequence is captured as one CUDA graph
-    and a replay is timed (its first product's limbs compared with the eager
-    ones)."""
+def cfg4_attention(ctx, stream, lengths, heads=16, dh=64, seed=45, check=2, packed=True):
+    """The ct-ct attention products of the BERT-large-shaped sequences,
+    Q_h K_h^T and P_h V_h (matmul_cc, Sec. 5.1), each length padded to a power
+    of two L >= 64 (Kc = N/2/(16 L) <= L) with zero rows and columns past the
+    sequence's end, V_h padded to L columns for the square diagonal-packed
+    output.  Two forms, each with its own plans and Galois keys:
+      plain:  one product pair per sequence, its 16 heads in one group;
+      packed: the sequences of one padded length S at a time in one product
+              pair, as S x 16 heads of one group (batching.cc_pack_groups), so
+              that step 3's rotations and the relinearizations are shared.
+    Each product is timed with CUDA events after one warm-up product per plan;
+    the first `check` sequences are decrypted against FP64 in both forms.  In
+    the plain form, for up to 8 sequences, every product is also captured as
+    one CUDA graph and a replay is timed (its first product's limbs compared
+    with the eager ones)."""
     import torch
+    from paper_2508_19525_b300 import batching as bt
     from paper_2508_19525_b300 import layer as ly
     from paper_2508_19525_b300 import workloads as wl
     level = ctx.nQ - 1
     pad = [max(64, 1 << int(np.ceil(np.log2(x)))) for x in lengths]
-    plans = {Lp: (ctx.cc_plan(Lp, heads, dh, level), ctx.cc_plan(Lp, heads, Lp, level)) for Lp in sorted(set(pad))}
-    rots = sorted({r for pq, pv in plans.values() for r in pq.rotations() + pv.rotations()})
-    t0 = time.perf_counter()
-    keys = ctx.keygen(46, rots, relin=True)
-    ctx.sync()
-    keygen_s = time.perf_counter() - t0
+    slots = ctx.N // 2
 
     def operands(si, l, Lp):
         Q, K, V, P = wl.attention_operands(Lp, heads, dh, seed=seed + si)
@@ -601,84 +601,113 @@ def cfg4_attention(ctx, stream, lengths, heads=16, dh=64, seed=45, check=2):
         Vp = np.concatenate([V, np.zeros((heads, Lp, Lp - dh))], axis=2)
         return (("qk", Q, np.transpose(K, (0, 2, 1))), ("pv", P, Vp))
 
-    def encrypt(plan, A, B, Lp, nonce):
-        info = plan.info()
-        Az = ly.pack_heads(A, Lp, heads, info["Kc"], info["n_c"], rows=False)
-        Bz = ly.pack_heads(B, Lp, heads, info["Kc"], info["n_c"], rows=True)
-        n = info["n_c"]
-        return (ctx.encrypt_batch(keys, ctx.encode_batch(Az, level), [nonce + c for c in range(n)]),
-                ctx.encrypt_batch(keys, ctx.encode_batch(Bz, level), [nonce + 1000 + c for c in range(n)]))
-
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    work = []                                   # (sequence, kind, plan, A_cts, B_cts, FP64 product)
-    for si, (l, Lp) in enumerate(zip(lengths, pad)):
-        for (kind, A, B), plan in zip(operands(si, l, Lp), plans[Lp]):
-            Ac, Bc = encrypt(plan, A, B, Lp, 10000 * si)
-            work.append((si, kind, plan, Ac, Bc, np.einsum("hik,hkj->hij", A, B) if si < check else None))
-    warm = set()
-    for si, kind, plan, Ac, Bc, _ in work:     # one untimed product per plan (arenas)
-        if id(plan) not in warm:
-            ctx.matmul_cc_plan(keys, plan, Ac, Bc)
-            warm.add(id(plan))
-    ctx.sync()
-    per_len = {}
-    total, err = 0.0, 0.0
-    eager_first = None
-    for si, kind, plan, Ac, Bc, want in work:
-        Lp = pad[si]
-        ev0.record(stream)
-        C = ctx.matmul_cc_plan(keys, plan, Ac, Bc)
-        ev1.record(stream)
-        torch.cuda.synchronize()
-        sec = ev0.elapsed_time(ev1) / 1e3
-        total += sec
-        e = per_len.setdefault(str(Lp), {"sequences": 0, "qk_ms": 0.0, "pv_ms": 0.0})
-        e[kind + "_ms"] += sec * 1e3
-        if kind == "qk":
-            e["sequences"] += 1
-        if want is not None:
-            Z = np.stack([ctx.decrypt(keys, c, coeffs=False)[1] for c in C])
-            err = max(err, float(np.abs(ly.unpack_diagonals(Z, Lp, heads, plan.info()["Kc"]) - want).max()))
-        if eager_first is None:
-            eager_first = [ctx.ct_export(c) for c in C]
-        del C
-    # every product of every sequence captured as one CUDA graph, then replayed
-    # (up to 8 sequences: the graph's pool keeps every product's temporaries)
-    graph_s = graph_same = None
-    if len(lengths) <= 8:
-        torch.cuda.empty_cache()
-        graph, Cg = ctx.capture(lambda: [ctx.matmul_cc_plan(keys, plan, Ac, Bc) for _, _, plan, Ac, Bc, _ in work],
-                                warmup=False)
-        with torch.cuda.stream(stream):
-            graph.replay()
+    def run(groups, graph_ok):
+        plans = {}
+        for Lp, idx in groups:
+            Hg = heads * len(idx)
+            if (Lp, Hg) not in plans:
+                plans[(Lp, Hg)] = (ctx.cc_plan(Lp, Hg, dh, level), ctx.cc_plan(Lp, Hg, Lp, level))
+        rots = sorted({r for pq, pv in plans.values() for r in pq.rotations() + pv.rotations()})
+        t0 = time.perf_counter()
+        keys = ctx.keygen(46, rots, relin=True)
+        ctx.sync()
+        keygen_s = time.perf_counter() - t0
+        work = []                      # (sequences, kind, plan, A_cts, B_cts, padded length, Hg, FP64 products)
+        for gi, (Lp, idx) in enumerate(groups):
+            Hg = heads * len(idx)
+            per = [operands(si, lengths[si], Lp) for si in idx]
+            for k, plan in enumerate(plans[(Lp, Hg)]):
+                A = bt.stack_heads([p[k][1] for p in per])
+                B = bt.stack_heads([p[k][2] for p in per])
+                info = plan.info()
+                Az = ly.pack_heads(A, Lp, Hg, info["Kc"], info["n_c"], rows=False)
+                Bz = ly.pack_heads(B, Lp, Hg, info["Kc"], info["n_c"], rows=True)
+                n, nonce = info["n_c"], 100000 * gi + 50000 * k
+                Ac = ctx.encrypt_batch(keys, ctx.encode_batch(Az, level), [nonce + c for c in range(n)])
+                Bc = ctx.encrypt_batch(keys, ctx.encode_batch(Bz, level), [nonce + 20000 + c for c in range(n)])
+                want = [np.einsum("hik,hkj->hij", p[k][1], p[k][2]) if si < check else None
+                        for si, p in zip(idx, per)]
+                work.append((idx, per[0][k][0], plan, Ac, Bc, Lp, Hg, want))
+        warm = set()
+        for _, _, plan, Ac, Bc, _, _, _ in work:      # one untimed product per plan (arenas)
+            if id(plan) not in warm:
+                ctx.matmul_cc_plan(keys, plan, Ac, Bc)
+                warm.add(id(plan))
+        ctx.sync()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        per_len, total, err, eager_first = {}, 0.0, 0.0, None
+        for idx, kind, plan, Ac, Bc, Lp, Hg, want in work:
             ev0.record(stream)
-            graph.replay()
+            C = ctx.matmul_cc_plan(keys, plan, Ac, Bc)
             ev1.record(stream)
-        torch.cuda.synchronize()
-        graph_s = ev0.elapsed_time(ev1) / 1e3
-        graph_same = all(np.array_equal(ctx.ct_export(a), b) for a, b in zip(Cg[0], eager_first))
-        del graph, Cg
-    del work
-    peak_gb = torch.cuda.max_memory_allocated() / 1e9
-    for e in per_len.values():
-        e["qk_ms"] = round(e["qk_ms"] / e["sequences"], 2)
-        e["pv_ms"] = round(e["pv_ms"] / e["sequences"], 2)
-    info = {str(Lp): {k: v for k, v in pv.info().items() if k in ("Kc", "n_c", "b1s2", "c_chunk", "t_chunk")}
-            for Lp, (_, pv) in plans.items()}
-    for pq, pv in plans.values():
-        pq.free()
-        pv.free()
-    del keys
-    torch.cuda.empty_cache()
-    T = int(sum(lengths))
-    return {"workload": f"{len(lengths)} sequences, Q K^T and P V per sequence, {heads} heads of dim {dh} in one "
-                        f"group, lengths padded to powers of two >= 64, N=2^16, 12 primes",
-            "padded_lengths": pad, "rotation_keys": len(rots), "keygen_s": round(keygen_s, 2),
-            "per_padded_length_ms": per_len, "pv_plans": info, "s_total": round(total, 4),
-            "tokens_per_s": round(T / total, 1), "graph_s": None if graph_s is None else round(graph_s, 4),
-            "graph_tokens_per_s": None if graph_s is None else round(T / graph_s, 1),
-            "graph_equals_eager": None if graph_same is None else bool(graph_same),
-            "max_abs_err_vs_fp64": err, "peak_device_gb": round(peak_gb, 1)}
+            torch.cuda.synchronize()
+            sec = ev0.elapsed_time(ev1) / 1e3
+            total += sec
+            e = per_len.setdefault(str(Lp), {"sequences": 0, "products": 0, "qk_ms": 0.0, "pv_ms": 0.0})
+            e[kind + "_ms"] += sec * 1e3
+            if kind == "qk":
+                e["sequences"] += len(idx)
+                e["products"] += 1
+            if any(x is not None for x in want):
+                Z = np.stack([ctx.decrypt(keys, c, coeffs=False)[1] for c in C])
+                got = bt.split_heads(ly.unpack_diagonals(Z, Lp, Hg, plan.info()["Kc"]), len(idx))
+                for g_, w_ in zip(got, want):
+                    if w_ is not None:
+                        err = max(err, float(np.abs(g_ - w_).max()))
+            if eager_first is None:
+                eager_first = [ctx.ct_export(c) for c in C]
+            del C
+        # every product captured as one CUDA graph, then replayed (up to 8
+        # sequences: the graph's pool keeps every product's temporaries)
+        graph_s = graph_same = None
+        if graph_ok:
+            torch.cuda.empty_cache()
+            graph, Cg = ctx.capture(lambda: [ctx.matmul_cc_plan(keys, w_[2], w_[3], w_[4]) for w_ in work],
+                                    warmup=False)
+            with torch.cuda.stream(stream):
+                graph.replay()
+                ev0.record(stream)
+                graph.replay()
+                ev1.record(stream)
+            torch.cuda.synchronize()
+            graph_s = ev0.elapsed_time(ev1) / 1e3
+            graph_same = all(np.array_equal(ctx.ct_export(a), b) for a, b in zip(Cg[0], eager_first))
+            del graph, Cg
+        del work
+        for e in per_len.values():
+            e["qk_ms_per_sequence"] = round(e.pop("qk_ms") / e["sequences"], 2)
+            e["pv_ms_per_sequence"] = round(e.pop("pv_ms") / e["sequences"], 2)
+        info = {f"L={Lp},Hg={Hg}": {k: v for k, v in pv.info().items() if k in ("Kc", "n_c", "b1s1", "b1s2",
+                                                                                   "c_chunk", "t_chunk")}
+                for (Lp, Hg), (_, pv) in plans.items()}
+        for pq, pv in plans.values():
+            pq.free()
+            pv.free()
+        del keys
+        torch.cuda.empty_cache()
+        T = int(sum(lengths))
+        return {"rotation_keys": len(rots), "keygen_s": round(keygen_s, 2), "per_padded_length": per_len,
+                "pv_plans": info, "s_total": round(total, 4), "tokens_per_s": round(T / total, 1),
+                "graph_s": None if graph_s is None else round(graph_s, 4),
+                "graph_tokens_per_s": None if graph_s is None else round(T / graph_s, 1),
+                "graph_equals_eager": None if graph_same is None else bool(graph_same),
+                "max_abs_err_vs_fp64": err}
+
+    plain = run([(Lp, [i]) for i, Lp in enumerate(pad)], len(lengths) <= 8)
+    out = {"workload": f"{len(lengths)} sequences, Q K^T and P V, {heads} heads of dim {dh}, lengths padded to "
+                       f"powers of two >= 64, N=2^16, 12 primes",
+           "padded_lengths": pad, "plain": plain}
+    if packed:
+        groups = bt.cc_pack_groups(pad, heads, slots)
+        pk = run(groups, False)
+        pk["sequences_per_product"] = [len(i) for _, i in groups]
+        out["packed"] = pk
+        out["packed_speedup_vs_plain"] = round(plain["s_total"] / pk["s_total"], 3)
+    best = out.get("packed", plain)
+    out["s_total"] = best["s_total"]
+    out["tokens_per_s"] = best["tokens_per_s"]
+    out["peak_device_gb"] = round(torch.cuda.max_memory_allocated() / 1e9, 1)
+    return out
 
 
 def layer_bench():

@@ -10,8 +10,18 @@ zero-padded).  Every chunk is packed spatial-first like one m-row activation
 at slots [j m, (j+1) m) of its ciphertext), so one plan serves every chunk,
 whatever the sequence lengths, and the batched product
 (blb_matmul_cp_batch) streams each plaintext diagonal once for a whole group
-of chunks.  Attention (matmul_cc) mixes the rows of one sequence and stays
-per sequence.
+of chunks.
+
+Attention (matmul_cc) mixes the rows of one sequence, so its products cannot
+be chunked; but the heads of one head group are independent products that
+multi-head packing (Sec. 5.1) places side by side in one ciphertext, and the
+heads of several sequences of one client with the same padded length are
+independent in the same way.  `cc_pack_groups` packs S such sequences into one
+product as S x heads heads of one group: the rotations of step 3 and the
+relinearizations (L of each per product) are then shared by the S sequences,
+and steps 1-2 need fewer rotations per sequence (Kc = s/(L S heads) shrinks,
+the input ciphertexts per operand grow by S), while the step-2 tensor products
+per sequence stay the same.
 
 The split of each product's rotations into baby and giant steps (b1, G with
 b1 G = k) and the number of chunks per batched call are chosen by `autotune`:
@@ -132,3 +142,41 @@ def autotune_dnum(make_ctx, candidates, m, reps=3, rotations=8):
         ctx.free()
     best = min(timings, key=timings.get)
     return best, timings
+
+
+def cc_pack_groups(pads, heads, slots, max_pack=None):
+    """Group the sequences (padded lengths `pads`) of one client into matmul_cc
+    products of S sequences each: S a power of two, all of one padded length
+    L, with L x S x heads dividing `slots` (Kc >= 1; `heads` a power of two).
+    Greedy per length: the largest S (at most `max_pack`) that the remaining
+    sequences fill.  Returns [(L, [sequence indices])] covering every sequence
+    once, in order of L."""
+    if heads & (heads - 1):
+        raise ValueError("heads must be a power of two to pack several sequences into one head group")
+    by_len = {}
+    for i, Lp in enumerate(pads):
+        by_len.setdefault(int(Lp), []).append(i)
+    groups = []
+    for Lp in sorted(by_len):
+        idx = by_len[Lp]
+        smax = max(1, slots // (Lp * heads))
+        if max_pack:
+            smax = min(smax, max_pack)
+        while idx:
+            S = 1
+            while 2 * S <= min(smax, len(idx)):
+                S *= 2
+            groups.append((Lp, idx[:S]))
+            idx = idx[S:]
+    return groups
+
+
+def stack_heads(mats):
+    """Per-sequence head stacks (heads, rows, cols) -> one stack of S x heads
+    heads, sequence j's head h at index j heads + h."""
+    return np.concatenate(mats, axis=0)
+
+
+def split_heads(stack, S):
+    """Inverse of stack_heads for S sequences."""
+    return np.split(stack, S, axis=0)
