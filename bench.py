@@ -212,6 +212,7 @@ class Workload:
             self.ctx.ntt_set_radix(ntt_radix)
             self.ntt_radix = ntt_radix
         self.X, Wqkv, Wo = wl.bert_base_cp(seed=0)
+        self.Wqkv, self.Wo = Wqkv, Wo
         self.ref_qkv = self.X @ Wqkv
         self.ref_o = self.ref_qkv[:, :D_O] @ Wo
         t = time.time()
@@ -292,6 +293,67 @@ class Workload:
             self.bp1 = self.torch.zeros_like(self.bp0)
         masked, _ = ctx.he2mpc_batch(keys, outs, self.nonces(len(outs)), share_out=self.bp1)
         ctx.decrypt_batch(keys, masked, coeff_out=self.bp0)
+
+    def packed(self, b1_qkv=16, b1_o=8):
+        """Two sequences per ciphertext: m = 2 x 128 rows, k = N/(2 m) = 64
+        columns (twelve input ciphertexts for the pair instead of six per
+        sequence), so one set of rotations serves 256 tokens: 288 + 168
+        rotations per pair of sequences against 2 x (216 + 132).  Plans, keys
+        (the step's secret, seed 0) and the packed inputs are made on first use;
+        returns the number of ciphertexts per packed input."""
+        if getattr(self, "plan_qkv2", None) is None:
+            m2 = 2 * M
+            k2 = self.N // 2 // m2
+            rots = sorted({r for b1 in (b1_qkv, b1_o)
+                           for r in [b * m2 for b in range(1, b1)] + [g * b1 * m2 for g in range(1, k2 // b1)]})
+            self.keys2 = self.ctx.keygen(0, rots)
+            self.plan_qkv2 = self.ctx.cp_plan(m2, D, self.Wqkv, D_QKV, LEVEL, b1_qkv)
+            self.plan_o2 = self.ctx.cp_plan(m2, D, self.Wo, D_O, LEVEL - 1, b1_o)
+            self.k2 = k2
+            Z2 = pack_columns(np.vstack([self.X, self.X]), m2, k2)
+            self.n_in2 = Z2.shape[0]
+            self.Z2dev = self.torch.tensor(Z2, dtype=self.torch.float64, device=self.p0_dev.device)
+            self.ctx.sync()
+        return self.n_in2
+
+    def step_batched_packed(self, S, keep=False):
+        """S sequences (S even), two per ciphertext, through the packed plans
+        in one batched pass per product, then masking and P0's decryption of
+        every output."""
+        n_in = self.packed()
+        ctx, keys = self.ctx, self.keys2
+        seqs = [ctx.encrypt_batch(keys, ctx.encode_batch(self.Z2dev, LEVEL), self.nonces(n_in))
+                for _ in range(S // 2)]
+        Ys = ctx.matmul_cp_batch(keys, self.plan_qkv2, seqs)
+        Os = ctx.matmul_cp_batch(keys, self.plan_o2, [Y[:n_in] for Y in Ys])
+        outs = [y for Y, O in zip(Ys, Os) for y in Y[n_in:] + O]
+        if getattr(self, "bp0p", None) is None or self.bp0p.shape[0] != len(outs):
+            self.bp0p = self.torch.zeros((len(outs), self.N), dtype=self.torch.uint64, device=self.p0_dev.device)
+            self.bp1p = self.torch.zeros_like(self.bp0p)
+        masked, _ = ctx.he2mpc_batch(keys, outs, self.nonces(len(outs)), share_out=self.bp1p)
+        ctx.decrypt_batch(keys, masked, coeff_out=self.bp0p)
+        return (Ys, Os) if keep else None
+
+    def packed_accuracy(self):
+        """Largest error of the packed form's first pair: both sequences'
+        QKV and W_O outputs decrypted against FP64."""
+        Ys, Os = self.step_batched_packed(2, keep=True)
+        Y, O = Ys[0], Os[0]
+        n_in = self.n_in2
+        dec = lambda cts: np.stack([self.ctx.decrypt(self.keys2, c, coeffs=False)[1] for c in cts])  # noqa: E731
+        got_qkv = unpack_columns(dec(Y), 2 * M, self.k2, D_QKV)
+        got_o = unpack_columns(dec(O), 2 * M, self.k2, D_O)
+        assert len(Y) == -(-D_QKV // self.k2) and len(O) == -(-D_O // self.k2) and n_in == D // self.k2
+        ref_qkv = np.vstack([self.ref_qkv, self.ref_qkv])
+        ref_o = np.vstack([self.ref_o, self.ref_o])
+        return float(max(np.abs(got_qkv - ref_qkv).max(), np.abs(got_o - ref_o).max()))
+
+    def free_packed(self):
+        for name in ("plan_qkv2", "plan_o2", "keys2"):
+            h = getattr(self, name, None)
+            if h is not None:
+                h.free()
+                setattr(self, name, None)
 
     def accuracy(self):
         Y, O, _ = self.step(keep=True)
@@ -453,16 +515,19 @@ def conversion_bench(w, reps):
     return out
 
 
-def cfg4_batching(n_seqs=8, plain_chunks=6, candidates=(16, 32, 64, 128), groups=(1, 2, 4, 8, 16)):
+def cfg4_batching(n_seqs=8, plain_chunks=6, ms=(32, 128, 256), groups=(1, 2, 4, 8)):
     """Batching of uneven-length BERT-large-shaped sequences of one client:
     n_seqs sequences with lengths U[16, 512] (seeded), hidden 1024, FFN 4096;
     the ct-pt products QKV (1024 x 3072), FFN up (1024 x 4096) and FFN down
-    (4096 x 1024) over all their tokens, cut into m = 32-row chunks (one
-    ciphertext holds a chunk's 1024 features), N = 2^16, 12 primes, dnum 4.
-    Batched: a group of chunks per blb_matmul_cp_batch call, every plaintext
-    streamed once per group (at most 8 chunks per MAC launch).  Plain: one
-    chunk per call.  b1 (baby steps, b1 G = 1024) and the group size are
-    autotuned per product by timing every pair on the product."""
+    (4096 x 1024) over all their tokens, laid end to end and cut into m-row
+    chunks, N = 2^16, 12 primes, dnum autotuned.
+    Plain: 32-row chunks (one ciphertext holds a chunk's 1024 features), one
+    chunk per call, the b1 fastest for that form.
+    Batched: m in `ms` rows per ciphertext (more tokens through the same
+    rotations; the plan's plaintexts grow with m), a group of chunks per
+    blb_matmul_cp_batch call (every plaintext streamed once per group); m, b1
+    (two candidates per m from the rotation count) and the group size are
+    autotuned per product by timing every triple on the product itself."""
     import torch
     from paper_2508_19525_b300 import batching as bt
     from paper_2508_19525_b300 import blb
@@ -475,50 +540,85 @@ def cfg4_batching(n_seqs=8, plain_chunks=6, candidates=(16, 32, 64, 128), groups
         lambda dn: blb.Context(prm.logN, prm.q_bits, prm.p_bits, dn, prm.scale, stream=stream), (4, 6, 12), 32)
     ctx = blb.Context(prm.logN, prm.q_bits, prm.p_bits, dnum, prm.scale, stream=stream)
     ntt_split, ntt_radix, ntt_us = ctx.ntt_autotune(256)
-    m, level = 32, ctx.nQ - 1
-    k = ctx.N // 2 // m
+    level, slots = ctx.nQ - 1, ctx.N // 2
     rng = np.random.default_rng(44)
     lengths = rng.integers(16, 513, n_seqs)
     T = int(lengths.sum())
+    products = [("qkv", 1024, 3072, 41), ("ffn_up", 1024, 4096, 42), ("ffn_down", 4096, 1024, 43)]
+    cands = {(name, m): bt.cp_b1_candidates(m, d, d_out, slots) for name, d, d_out, _ in products for m in ms}
     t0 = time.perf_counter()
-    rots = sorted({r for b1 in candidates for r in bt.cp_rotations(m, k, b1)})
+    rots = sorted({r for (name, m), bs in cands.items() for b1 in bs for r in bt.cp_rotations(m, slots // m, b1)})
     keys = ctx.keygen(6, rots)
     ctx.sync()
     keygen_s = time.perf_counter() - t0
-    products = [("qkv", 1024, 3072, 41), ("ffn_up", 1024, 4096, 42), ("ffn_down", 4096, 1024, 43)]
     out = {"workload": f"{n_seqs} BERT-large-shaped sequences, lengths U[16,512] (total {T} tokens), "
-                       f"QKV 1024x3072 + FFN 1024x4096 + 4096x1024 ct-pt products, m={m}-row chunks, "
+                       f"QKV 1024x3072 + FFN 1024x4096 + 4096x1024 ct-pt products over m-row chunks, "
                        f"N=2^16, 12 primes, dnum autotuned", "lengths": [int(x) for x in lengths], "tokens": T,
            "rotation_keys": len(rots),
            "autotuned": {"dnum": dnum, "dnum_s_per_rotation": {str(k): round(v, 5) for k, v in dnum_t.items()},
                          "ntt_split": ntt_split, "ntt_radix": ntt_radix, "ntt_us_per_row_direction": ntt_us_json(ntt_us)},
            "keygen_s": round(keygen_s, 2), "products": {}}
     tot_b = tot_p = tot_g = 0.0
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def encrypt_chunks(X, m):
+        k = slots // m
+        n_cts = -(-X.shape[1] // k)
+        Z = bt.pack_chunks(X, m, k, n_cts)
+        return [ctx.encrypt_batch(keys, ctx.encode_batch(Z[c], level), [1000 * c + i for i in range(n_cts)])
+                for c in range(len(Z))]
+
     for name, d, d_out, seed in products:
         X = wl.uniform((T, d), seed=seed)
         W = wl.uniform((d, d_out), seed=seed + 100)
-        n_cts = d // k
-        Z = bt.pack_chunks(X, m, k, n_cts)
-        chunks = [ctx.encrypt_batch(keys, ctx.encode_batch(Z[c], level), [1000 * c + i for i in range(n_cts)])
-                  for c in range(len(Z))]
-        grp = [x for x in groups if x * n_cts * 128 * ctx.N * 8 * 2 * ctx.nQ < 40e9] or [1]
-        (b1, g), tune = bt.autotune(ctx, keys, m, d, W, d_out, level, chunks, candidates, grp)
+        tune_all, best, pb32 = {}, None, None
+        for m in ms:
+            # a plan's plaintexts grow as m: skip an m whose plan would take
+            # more than half of the device (other products' keys and
+            # ciphertexts, and the attention products later, need the rest)
+            if pb32 is not None and pb32 * m // 32 > 0.5 * torch.cuda.get_device_properties(0).total_memory:
+                continue
+            chunks = encrypt_chunks(X, m)
+            n_cts = len(chunks[0])
+            # baby-step ciphertexts of a call: group x inputs x b1 x 2 polynomials
+            grp = [x for x in groups if x * n_cts * max(cands[(name, m)]) * ctx.N * 8 * 2 * ctx.nQ < 40e9] or [1]
+            try:
+                (b1, g), tune = bt.autotune(ctx, keys, m, d, W, d_out, level, chunks, cands[(name, m)], grp)
+            except ValueError:
+                continue
+            for (b, gg), t in tune.items():
+                tune_all[f"m={m},b1={b},group={gg}"] = round(t, 4)
+            if m == 32:
+                # plain: 32-row chunks, one per call, with the b1 fastest for that form
+                b1p = min((b for b, gg in tune if gg == 1), key=lambda b: tune[(b, 1)])
+                plan_p = ctx.cp_plan(32, d, W, d_out, level, b1p)
+                pb32 = plan_p.info()["plaintext_bytes"]
+                npl = min(plain_chunks, len(chunks))
+                ctx.matmul_cp_plan(keys, plan_p, chunks[0])
+                ev0.record(stream)
+                for c in range(npl):
+                    ctx.matmul_cp_plan(keys, plan_p, chunks[c])
+                ev1.record(stream)
+                torch.cuda.synchronize()
+                plain_per_chunk = ev0.elapsed_time(ev1) / 1e3 / npl
+                n_plain_chunks = len(chunks)
+                plan_p.free()
+            per_tok = tune[(b1, g)] / m
+            if best is None or per_tok < best[0]:
+                best = (per_tok, m, b1, g)
+            del chunks
+            torch.cuda.empty_cache()
+        _, m, b1, g = best
+        k = slots // m
+        chunks = encrypt_chunks(X, m)
         plan = ctx.cp_plan(m, d, W, d_out, level, b1)
         bt.run_batched(ctx, keys, plan, chunks[:g], g)
         ctx.sync()
-        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ev0.record(stream)
         Y = bt.run_batched(ctx, keys, plan, chunks, g)
         ev1.record(stream)
         torch.cuda.synchronize()
         batched_s = ev0.elapsed_time(ev1) / 1e3
-        npl = min(plain_chunks, len(chunks))
-        ev0.record(stream)
-        for c in range(npl):
-            ctx.matmul_cp_plan(keys, plan, chunks[c])
-        ev1.record(stream)
-        torch.cuda.synchronize()
-        plain_per_chunk = ev0.elapsed_time(ev1) / 1e3 / npl
         # the product over every chunk captured once as one CUDA graph (the
         # arenas are already sized by the eager run), replayed and timed
         l0 = blb.kernel_launches()
@@ -539,32 +639,39 @@ def cfg4_batching(n_seqs=8, plain_chunks=6, candidates=(16, 32, 64, 128), groups
             got = bt.unpack_chunk([ctx.decrypt(keys, y, coeffs=False)[1] for y in Y[c]], m, k, d_out)
             rows = min(m, T - c * m)
             err = max(err, float(np.abs(got[:rows] - X[c * m:c * m + rows] @ W).max()))
+        plain_s = plain_per_chunk * n_plain_chunks
         out["products"][name] = {
-            "b1": b1, "G": k // b1,
-            "autotune_s_per_chunk": {f"b1={b},group={gg}": round(t, 4) for (b, gg), t in tune.items()},
+            "m": m, "b1": b1, "G": k // b1,
+            "autotune_s_per_chunk": tune_all,
+            "rotations_per_chunk": bt.cp_rotation_count(m, d, d_out, slots, b1),
             "chunks": len(chunks), "chunks_per_call": g,
             "batched_s": round(batched_s, 3), "batched_tokens_per_s": round(T / batched_s, 1),
-            "plain_s_per_chunk": round(plain_per_chunk, 4),
-            "plain_tokens_per_s": round(m / plain_per_chunk, 1),
-            "speedup": round(plain_per_chunk * len(chunks) / batched_s, 3),
+            "plain": {"m": 32, "b1": b1p, "chunks": n_plain_chunks, "s_per_chunk": round(plain_per_chunk, 4),
+                      "rotations_per_chunk": bt.cp_rotation_count(32, d, d_out, slots, b1p)},
+            "plain_tokens_per_s": round(T / plain_s, 1),
+            "speedup": round(plain_s / batched_s, 3),
             "graph_s": round(graph_s, 3), "graph_tokens_per_s": round(T / graph_s, 1),
             "graph_kernel_nodes": int(graph_kernels), "graph_equals_eager": bool(graph_same),
             "plaintext_bytes": plan.info()["plaintext_bytes"], "max_abs_err_vs_fp64": err}
         tot_b += batched_s
         tot_g += graph_s
-        tot_p += plain_per_chunk * len(chunks)
+        tot_p += plain_s
         del chunks, Y
         plan.free()
+        torch.cuda.empty_cache()
     out["batched_tokens_per_s"] = round(T / tot_b, 1)
     out["graph_tokens_per_s"] = round(T / tot_g, 1)
     out["graph_speedup_vs_plain"] = round(tot_p / tot_g, 3)
     out["plain_tokens_per_s"] = round(T / tot_p, 1)
     out["speedup"] = round(tot_p / tot_b, 3)
+    out["peak_device_gb"] = round(torch.cuda.max_memory_allocated() / 1e9, 1)
     del keys
     torch.cuda.empty_cache()
+    torch.cuda.reset_peak_memory_stats()
     att = cfg4_attention(ctx, stream, [int(x) for x in lengths])
     out["attention"] = att
     out["ct_pt_and_attention_tokens_per_s"] = round(T / (tot_b + att["s_total"]), 1)
+    out["ct_pt_and_attention_plain_tokens_per_s"] = round(T / (tot_p + att["plain"]["s_total"]), 1)
     return out
 
 
@@ -1026,11 +1133,37 @@ def run_blb(args):
         w.ctx.sync()
         bsites = {s_: round(w.ctx.profile_read(s_)[0], 3) for s_ in ("cp_mac", "keyswitch", "ntt", "intt")}
         w.ctx.profile(False)
-        batched = {"sequences_per_step": args.batch, "value": round(bval, 3), "unit": UNIT,
-                   "ms_per_step": round(bsec * 1e3 / bsteps, 3), "speedup_vs_plain": round(bval / value, 3),
-                   "site_ms_one_step": bsites,
-                   "mac_kernel": "automatic: mma.sync in 4-sequence launches for these plans (nine and three 16-output "
-                                 "blocks); the tcgen05 kernel is chosen for single-block plans at 8 sequences"}
+        same = {"value": round(bval, 3), "unit": UNIT,
+                "ms_per_step": round(bsec * 1e3 / bsteps, 3), "speedup_vs_plain": round(bval / value, 3),
+                "site_ms_one_step": bsites,
+                "form": "one sequence per ciphertext (the plain form's plans, m = 128), every plaintext streamed "
+                        "once for all sequences",
+                "mac_kernel": "automatic: mma.sync in 4-sequence launches for these plans (nine and three 16-output "
+                              "blocks); the tcgen05 kernel is chosen for single-block plans at 8 sequences"}
+        batched = {"sequences_per_step": args.batch, "same_packing": same}
+        if args.batch % 2 == 0:
+            # two sequences per ciphertext (m = 256): one set of rotations per pair
+            w.packed()
+            w.step_batched_packed(args.batch)
+            psec = timed_fn(w, lambda: w.step_batched_packed(args.batch), bsteps, world)
+            pval, _ = aggregate(psec, TOKENS_PER_STEP * args.batch * bsteps, world)
+            w.ctx.profile(True)
+            w.step_batched_packed(args.batch)
+            w.ctx.sync()
+            psites = {s_: round(w.ctx.profile_read(s_)[0], 3) for s_ in ("cp_mac", "keyswitch", "ntt", "intt")}
+            w.ctx.profile(False)
+            batched["two_per_ciphertext"] = {
+                "value": round(pval, 3), "unit": UNIT, "ms_per_step": round(psec * 1e3 / bsteps, 3),
+                "speedup_vs_plain": round(pval / value, 3), "site_ms_one_step": psites,
+                "max_abs_err_vs_fp64": w.packed_accuracy(),
+                "form": "two sequences per ciphertext (m = 256 rows, k = 64 columns; b1 = 16 for QKV, 8 for W_O): "
+                        "288 + 168 rotations per pair of sequences against 2 x (216 + 132), plaintexts 2x (streamed "
+                        "once for all pairs)",
+                "plaintext_bytes": w.plan_qkv2.info()["plaintext_bytes"] + w.plan_o2.info()["plaintext_bytes"]}
+            w.free_packed()
+        best = max((v for k_, v in batched.items() if isinstance(v, dict)), key=lambda v: v["value"])
+        batched.update(value=best["value"], unit=UNIT, ms_per_step=best["ms_per_step"],
+                       speedup_vs_plain=best["speedup_vs_plain"])
     # the same step with its products, masking and decryption replayed from a
     # CUDA graph (inputs encrypted eagerly every step)
     gstep = w.graph_step()
@@ -1044,6 +1177,12 @@ def run_blb(args):
                      "(nonces fixed at capture) and P0's decryption"}
     del w.graph, w.graph_out, w.graph_inputs
     conv = conversion_bench(w, 20) if args.conversion else None
+    # the BERT-base step is done: keep its figures, free its plans and keys
+    # (25 GB) before the larger workloads below
+    w_counts, w_cp_bytes = w.counts(), w.cp_bytes()
+    for h in (w.plan_qkv, w.plan_o, w.keys):
+        h.free()
+    torch.cuda.empty_cache()
     cfg4 = cfg4_batching(args.cfg4_seqs) if args.cfg4_seqs and world == 1 else None
     lnorm = layernorm_bench(max(2, min(10, args.steps // 5))) if args.layernorm and world == 1 else None
     layer = layer_bench() if args.layer and world == 1 else None
@@ -1132,8 +1271,8 @@ def run_blb(args):
         "cfg4_batching": cfg4,
         "conversion": dict(conv, sites={k: dict(v, frac_of_hbm=round(v["achieved_gbs"] / hbm, 4), peak_kind=peak_note)
                                         for k, v in conv["sites"].items()}) if conv else None,
-        "counts_per_step": w.counts(),
-        "matmul_cp_bytes_per_step": w.cp_bytes(),
+        "counts_per_step": w_counts,
+        "matmul_cp_bytes_per_step": w_cp_bytes,
         "weights": {"plaintext_bytes": w.plan_bytes, "encode_s": round(w.plan_s, 2), "timed": False},
     }
     if not args.no_cpu_baseline:

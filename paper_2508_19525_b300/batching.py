@@ -23,8 +23,12 @@ and steps 1-2 need fewer rotations per sequence (Kc = s/(L S heads) shrinks,
 the input ciphertexts per operand grow by S), while the step-2 tensor products
 per sequence stay the same.
 
-The split of each product's rotations into baby and giant steps (b1, G with
-b1 G = k) and the number of chunks per batched call are chosen by `autotune`:
+The rows per ciphertext m (a power of two; 32 to 256 at N = 2^16 for the
+1024-feature products) set how many tokens share one ciphertext's rotations:
+the rotations per token fall about as 1/m (`cp_rotation_count`) while the
+plan's plaintexts grow as m.  The split of each product's rotations into baby
+and giant steps (b1, G with b1 G = k) and the number of chunks per batched
+call are chosen by `autotune`:
 every b1 candidate is encoded and every (b1, group) pair timed on the product
 itself, the fastest kept.  The group size matters because the plaintext MAC
 reads each plaintext once per call but its epilogue work grows with the number
@@ -68,6 +72,30 @@ def cp_rotations(m, k, b1):
     """Rotations of one plan: baby steps b m (b < b1), giant steps g b1 m."""
     G = k // b1
     return [b * m for b in range(1, b1)] + [g * b1 * m for g in range(1, G)]
+
+
+def cp_rotation_count(m, d, d_out, slots, b1):
+    """Rotations of one m-row product on ciphertexts of k = slots/m columns:
+    b1 - 1 hoisted baby steps per input ciphertext and G - 1 giant steps per
+    output ciphertext (b1 G = k).  Per token it falls as m grows: a ciphertext
+    of more rows carries more tokens through the same rotations."""
+    k = slots // m
+    nX, nY = -(-d // k), -(-d_out // k)
+    return nX * (b1 - 1) + nY * (k // b1 - 1)
+
+
+def cp_b1_candidates(m, d, d_out, slots, n=2):
+    """Baby-step counts b1 (powers of two below k) to time: the n with the
+    fewest rotations by cp_rotation_count and the next larger power of two
+    (baby steps are hoisted, so they cost less than giant steps and the
+    fastest b1 tends to lie above the count's optimum), ascending."""
+    k = slots // m
+    cands = [1 << i for i in range(1, k.bit_length()) if (1 << i) < k]
+    ranked = sorted(cands, key=lambda b1: (cp_rotation_count(m, d, d_out, slots, b1), b1))
+    pick = set(ranked[:n])
+    if 2 * max(pick) < k:
+        pick.add(2 * max(pick))
+    return sorted(pick)
 
 
 def run_batched(ctx, keys, plan, chunks, group):

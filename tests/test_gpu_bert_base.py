@@ -5,7 +5,9 @@ outputs): every decrypted output against FP64 within 1e-4, and, limb for limb
 against the oracle, what the oracle computes one by one at this size: the
 step's encrypted inputs, the masked outputs and P1's shares of the step (all
 18), P0's decryption of them, and a narrower matmul_cp (128 x 128 @ 128 x 128)
-on the same ring, level, primes, dnum, m and b1."""
+on the same ring, level, primes, dnum, m and b1.  The packed batch form (two
+sequences per ciphertext) against FP64, and a narrow product in its geometry
+against the oracle."""
 import numpy as np
 import pytest
 
@@ -109,3 +111,39 @@ def test_nine_sequence_batch_at_the_step_parameters_equals_single_calls():
         assert len(batched[s]) == len(single)
         for a, b in zip(batched[s], single):
             assert np.array_equal(ctx.ct_export(a), ctx.ct_export(b)), s
+
+
+def test_two_sequences_per_ciphertext_chain_matches_fp64(run):
+    """The benchmark's packed batch form (two 128-token sequences per
+    ciphertext, m = 256, k = 64): QKV then W_O on the QKV output, both
+    sequences of a pair within 1e-4 of FP64."""
+    _, w, _, _, _, _ = run
+    try:
+        assert w.packed_accuracy() <= 1e-4
+    finally:
+        w.free_packed()
+
+
+def test_narrow_two_sequence_matmul_cp_matches_the_oracle():
+    """A narrower product in the packed form's geometry (m = 256 rows, k = 64
+    columns per ciphertext, b1 = 8) at the step's ring, level, primes and dnum:
+    two sequences' rows in one ciphertext, limb for limb against the oracle."""
+    prm = wl.BERT_CP
+    o, ctx = make_oracle(prm), make_ctx(prm)
+    m, d, d_out, b1 = 256, 64, 64, 8
+    k = o.N // 2 // m
+    level = o.nQ - 1
+    X, W = wl.cp_operands(m, d, d_out, seed=79)
+    sk = o.keygen_secret(4)
+    rots = cp_rotations(m, b1, k // b1)
+    keys = ctx.keygen(4, rots)
+    zs = pack_cols(X, m, k, 1)
+    ct = ctx.encrypt(keys, ctx.encode(zs[0], level), nonce=6)
+    ref_in = o.encrypt(sk, o.encode(zs[0], level, prm.scale), 4, 6)
+    plan = ctx.cp_plan(m, d, W, d_out, level, b1)
+    Y = ctx.matmul_cp_plan(keys, plan, [ct])
+    ref = o.matmul_cp(ref_in[None], m, d, W, d_out, b1, oracle_galois(o, sk, 4, rots))
+    assert len(Y) == len(ref) == 1
+    assert np.array_equal(ctx.ct_export(Y[0]), ref[0])
+    got = unpack_cols([ctx.decrypt(keys, Y[0], coeffs=False)[1]], m, k, d_out)
+    assert np.abs(got - X @ W).max() <= 1e-4
