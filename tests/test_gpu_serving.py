@@ -95,16 +95,18 @@ def test_result_alone_equals_result_in_the_mix():
         assert np.abs(got_o - Yq[:, :D] @ Wo).max() <= 1e-4
 
 
-def test_chunked_result_alone_equals_result_in_the_mix():
-    """Requests of 8-60 tokens cut into 16-row chunks (1-4 chunks, one plan pair
-    per model), served in a mix with up to 3 chunks per cross-client product
-    and alone: same masked limbs and shares; every chunk's outputs decrypt to
-    the FP64 products."""
+@pytest.mark.parametrize("m,b1", [(16, 8), (64, 8)])
+def test_chunked_result_alone_equals_result_in_the_mix(m, b1):
+    """Requests of 8-60 tokens cut into m-row chunks (16 rows: 1-4 chunks of one
+    input ciphertext; 64 rows: one chunk of two input ciphertexts, as the
+    serving benchmark's larger chunks have several; one plan pair per model),
+    served in a mix with up to 3 chunks per cross-client product and alone:
+    same masked limbs and shares; every chunk's outputs decrypt to the FP64
+    products."""
     prm = wl.SMALL
     ctx = make_ctx(prm)
-    level, m = ctx.nQ - 1, 16
+    level = ctx.nQ - 1
     k = ctx.N // 2 // m
-    b1 = 8
     weights = {name: (wl.uniform((D, D_QKV), seed=s), wl.uniform((D, D), seed=s + 1))
                for name, s in (("a", 31), ("b", 41))}
     plans = {name: (ctx.cp_plan(m, D, Wq, D_QKV, level, b1), ctx.cp_plan(m, D, Wo, D, level - 1, b1),
@@ -130,13 +132,14 @@ def test_chunked_result_alone_equals_result_in_the_mix():
     done = srv.run(mix)
     assert len(done) == 6 and max(n for _, n in srv.iterations) > 1
     nX, nY = (D + k - 1) // k, (D_QKV + k - 1) // k
+    assert nX == D // k
     for r in mix:
         alone = reqs()[r.rid]
         server().run([alone])
         assert np.array_equal(r.state["p0"], alone.state["p0"]), r.rid
         assert np.array_equal(r.state["shares"], alone.state["shares"]), r.rid
         Wq, Wo = weights[r.model]
-        per = nY - nX + 1
+        per = nY - nX + -(-D // k)          # QKV outputs past the first nX, then W_O's
         n_ch = -(-r.seq // m)
         assert len(r.state["outs"]) == n_ch * per
         Xp = np.zeros((n_ch * m, D))
