@@ -294,36 +294,42 @@ class Workload:
         masked, _ = ctx.he2mpc_batch(keys, outs, self.nonces(len(outs)), share_out=self.bp1)
         ctx.decrypt_batch(keys, masked, coeff_out=self.bp0)
 
-    def packed(self, b1_qkv=16, b1_o=8):
-        """Two sequences per ciphertext: m = 2 x 128 rows, k = N/(2 m) = 64
-        columns (twelve input ciphertexts for the pair instead of six per
-        sequence), so one set of rotations serves 256 tokens: 288 + 168
-        rotations per pair of sequences against 2 x (216 + 132).  Plans, keys
-        (the step's secret, seed 0) and the packed inputs are made on first use;
-        returns the number of ciphertexts per packed input."""
+    # baby-step counts of the packed forms (fewest rotations at each geometry)
+    PACKED_B1 = {2: (16, 8), 4: (8, 8)}
+
+    def packed(self, per=2):
+        """`per` sequences per ciphertext: m = per x 128 rows, k = N/(2 m)
+        columns, so one set of rotations serves per x 128 tokens (two: 288 +
+        168 rotations per pair against 2 x (216 + 132); four: 384 + 240 per
+        four).  Plans, keys (the step's secret, seed 0) and the packed inputs
+        are made on first use (any other packing is freed first); returns the
+        number of ciphertexts per packed input."""
+        if getattr(self, "plan_qkv2", None) is not None and self.per2 != per:
+            self.free_packed()
         if getattr(self, "plan_qkv2", None) is None:
-            m2 = 2 * M
+            b1_qkv, b1_o = self.PACKED_B1[per]
+            m2 = per * M
             k2 = self.N // 2 // m2
             rots = sorted({r for b1 in (b1_qkv, b1_o)
                            for r in [b * m2 for b in range(1, b1)] + [g * b1 * m2 for g in range(1, k2 // b1)]})
             self.keys2 = self.ctx.keygen(0, rots)
             self.plan_qkv2 = self.ctx.cp_plan(m2, D, self.Wqkv, D_QKV, LEVEL, b1_qkv)
             self.plan_o2 = self.ctx.cp_plan(m2, D, self.Wo, D_O, LEVEL - 1, b1_o)
-            self.k2 = k2
-            Z2 = pack_columns(np.vstack([self.X, self.X]), m2, k2)
+            self.k2, self.per2, self.b1_2 = k2, per, (b1_qkv, b1_o)
+            Z2 = pack_columns(np.vstack([self.X] * per), m2, k2)
             self.n_in2 = Z2.shape[0]
             self.Z2dev = self.torch.tensor(Z2, dtype=self.torch.float64, device=self.p0_dev.device)
             self.ctx.sync()
         return self.n_in2
 
     def step_batched_packed(self, S, keep=False):
-        """S sequences (S even), two per ciphertext, through the packed plans
-        in one batched pass per product, then masking and P0's decryption of
-        every output."""
-        n_in = self.packed()
+        """S sequences (a multiple of the packing), `per2` per ciphertext,
+        through the packed plans in one batched pass per product, then masking
+        and P0's decryption of every output."""
+        n_in = self.n_in2
         ctx, keys = self.ctx, self.keys2
         seqs = [ctx.encrypt_batch(keys, ctx.encode_batch(self.Z2dev, LEVEL), self.nonces(n_in))
-                for _ in range(S // 2)]
+                for _ in range(S // self.per2)]
         Ys = ctx.matmul_cp_batch(keys, self.plan_qkv2, seqs)
         Os = ctx.matmul_cp_batch(keys, self.plan_o2, [Y[:n_in] for Y in Ys])
         outs = [y for Y, O in zip(Ys, Os) for y in Y[n_in:] + O]
@@ -335,17 +341,18 @@ class Workload:
         return (Ys, Os) if keep else None
 
     def packed_accuracy(self):
-        """Largest error of the packed form's first pair: both sequences'
-        QKV and W_O outputs decrypted against FP64."""
-        Ys, Os = self.step_batched_packed(2, keep=True)
+        """Largest error of the packed form's first packed input: every
+        sequence's QKV and W_O outputs decrypted against FP64."""
+        per = self.per2
+        Ys, Os = self.step_batched_packed(per, keep=True)
         Y, O = Ys[0], Os[0]
         n_in = self.n_in2
         dec = lambda cts: np.stack([self.ctx.decrypt(self.keys2, c, coeffs=False)[1] for c in cts])  # noqa: E731
-        got_qkv = unpack_columns(dec(Y), 2 * M, self.k2, D_QKV)
-        got_o = unpack_columns(dec(O), 2 * M, self.k2, D_O)
+        got_qkv = unpack_columns(dec(Y), per * M, self.k2, D_QKV)
+        got_o = unpack_columns(dec(O), per * M, self.k2, D_O)
         assert len(Y) == -(-D_QKV // self.k2) and len(O) == -(-D_O // self.k2) and n_in == D // self.k2
-        ref_qkv = np.vstack([self.ref_qkv, self.ref_qkv])
-        ref_o = np.vstack([self.ref_o, self.ref_o])
+        ref_qkv = np.vstack([self.ref_qkv] * per)
+        ref_o = np.vstack([self.ref_o] * per)
         return float(max(np.abs(got_qkv - ref_qkv).max(), np.abs(got_o - ref_o).max()))
 
     def free_packed(self):
@@ -354,6 +361,7 @@ class Workload:
             if h is not None:
                 h.free()
                 setattr(self, name, None)
+        self.torch.cuda.empty_cache()
 
     def accuracy(self):
         Y, O, _ = self.step(keep=True)
@@ -1179,9 +1187,12 @@ def run_blb(args):
                 "mac_kernel": "automatic: mma.sync in 4-sequence launches for these plans (nine and three 16-output "
                               "blocks); the tcgen05 kernel is chosen for single-block plans at 8 sequences"}
         batched = {"sequences_per_step": args.batch, "same_packing": same}
-        if args.batch % 2 == 0:
-            # two sequences per ciphertext (m = 256): one set of rotations per pair
-            w.packed()
+        from paper_2508_19525_b300.batching import cp_rotation_count as bt_rot
+        for per, name in ((2, "two_per_ciphertext"), (4, "four_per_ciphertext")):
+            if args.batch % per:
+                continue
+            # several sequences per ciphertext (m = per x 128): one set of rotations per packed input
+            w.packed(per)
             w.step_batched_packed(args.batch)
             psec = timed_fn(w, lambda: w.step_batched_packed(args.batch), bsteps, world)
             pval, _ = aggregate(psec, TOKENS_PER_STEP * args.batch * bsteps, world)
@@ -1190,13 +1201,15 @@ def run_blb(args):
             w.ctx.sync()
             psites = {s_: round(w.ctx.profile_read(s_)[0], 3) for s_ in ("cp_mac", "keyswitch", "ntt", "intt")}
             w.ctx.profile(False)
-            batched["two_per_ciphertext"] = {
+            k2 = w.k2
+            batched[name] = {
                 "value": round(pval, 3), "unit": UNIT, "ms_per_step": round(psec * 1e3 / bsteps, 3),
                 "speedup_vs_plain": round(pval / value, 3), "site_ms_one_step": psites,
                 "max_abs_err_vs_fp64": w.packed_accuracy(),
-                "form": "two sequences per ciphertext (m = 256 rows, k = 64 columns; b1 = 16 for QKV, 8 for W_O): "
-                        "288 + 168 rotations per pair of sequences against 2 x (216 + 132), plaintexts 2x (streamed "
-                        "once for all pairs)",
+                "form": f"{per} sequences per ciphertext (m = {per * M} rows, k = {k2} columns; b1 = {w.b1_2[0]} for "
+                        f"QKV, {w.b1_2[1]} for W_O), plaintexts {per}x, streamed once for all packed inputs",
+                "rotations_per_packed_input": [bt_rot(per * M, D, D_QKV, w.N // 2, w.b1_2[0]),
+                                               bt_rot(per * M, D, D_O, w.N // 2, w.b1_2[1])],
                 "plaintext_bytes": w.plan_qkv2.info()["plaintext_bytes"] + w.plan_o2.info()["plaintext_bytes"]}
             w.free_packed()
         best = max((v for k_, v in batched.items() if isinstance(v, dict)), key=lambda v: v["value"])

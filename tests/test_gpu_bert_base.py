@@ -113,12 +113,14 @@ def test_nine_sequence_batch_at_the_step_parameters_equals_single_calls():
             assert np.array_equal(ctx.ct_export(a), ctx.ct_export(b)), s
 
 
-def test_two_sequences_per_ciphertext_chain_matches_fp64(run):
-    """The benchmark's packed batch form (two 128-token sequences per
-    ciphertext, m = 256, k = 64): QKV then W_O on the QKV output, both
-    sequences of a pair within 1e-4 of FP64."""
-    _, w, _, _, _, _ = run
+@pytest.mark.parametrize("per", [2, 4])
+def test_several_sequences_per_ciphertext_chain_matches_fp64(run, per):
+    """The benchmark's packed batch forms (two or four 128-token sequences per
+    ciphertext, m = 256 or 512, k = 64 or 32): QKV then W_O on the QKV output,
+    every sequence of a packed input within 1e-4 of FP64."""
+    bench, w, _, _, _, _ = run
     try:
+        assert w.packed(per) == bench.D // (w.N // 2 // (per * bench.M))
         assert w.packed_accuracy() <= 1e-4
     finally:
         w.free_packed()
