@@ -45,7 +45,7 @@ TOKENS_PER_STEP = 128
 
 def config(world):
     return {"workload": WORKLOAD, "global_batch": world, "seq_len": M,
-            "parallelism": "replicas" if world > 1 else "single",
+            "parallelism": f"replicas x{world}" if world > 1 else "single",
             "l2": "working set larger than L2 (25.2 GB of byte-sliced plaintext diagonals read per step)",
             "bsgs_b1": B1,
             "encode_overflow_check": "deferred: read once after the timed steps (blb_ctx_set_deferred_encode_check)"}
