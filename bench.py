@@ -548,7 +548,7 @@ def conversion_bench(w, reps):
     return out
 
 
-def cfg4_batching(n_seqs=8, plain_chunks=6, ms=(32, 128, 256), groups=(1, 2, 4, 8)):
+def bert_large_batching(n_seqs=8, plain_chunks=6, ms=(32, 128, 256), groups=(1, 2, 4, 8)):
     """Batching of uneven-length BERT-large-shaped sequences of one client:
     n_seqs sequences with lengths U[16, 512] (seeded), hidden 1024, FFN 4096;
     the ct-pt products QKV (1024 x 3072), FFN up (1024 x 4096) and FFN down
@@ -701,14 +701,14 @@ def cfg4_batching(n_seqs=8, plain_chunks=6, ms=(32, 128, 256), groups=(1, 2, 4, 
     del keys
     torch.cuda.empty_cache()
     torch.cuda.reset_peak_memory_stats()
-    att = cfg4_attention(ctx, stream, [int(x) for x in lengths])
+    att = bert_large_batch_attention(ctx, stream, [int(x) for x in lengths])
     out["attention"] = att
     out["ct_pt_and_attention_tokens_per_s"] = round(T / (tot_b + att["s_total"]), 1)
     out["ct_pt_and_attention_plain_tokens_per_s"] = round(T / (tot_p + att["plain"]["s_total"]), 1)
     return out
 
 
-def cfg4_attention(ctx, stream, lengths, heads=16, dh=64, seed=45, check=2, packed=True):
+def bert_large_batch_attention(ctx, stream, lengths, heads=16, dh=64, seed=45, check=2, packed=True):
     """The ct-ct attention products of the BERT-large-shaped sequences,
     Q_h K_h^T and P_h V_h (matmul_cc, Sec. 5.1), each length padded to a power
     of two L >= 64 (Kc = N/2/(16 L) <= L) with zero rows and columns past the
@@ -987,7 +987,7 @@ def serving_bench(n_requests=64, rate=20.0, sat_rate=400.0, budget_gb=24, max_ba
     return out
 
 
-def serving_cfg5_bench(n_requests=32, rate=20.0, light_rate=2.0, n_light=12, budget_gb=80, max_batch=4, group=2,
+def serving_n65536_bench(n_requests=32, rate=20.0, light_rate=2.0, n_light=12, budget_gb=80, max_batch=4, group=2,
                        m=32, b1=32, m_batched=128, b1_batched=32):
     """Continuous batching at the serving configuration's own parameters:
     N = 2^16, 12 primes, dnum 4; Poisson arrivals at `rate` req/s, half
@@ -1234,12 +1234,12 @@ def run_blb(args):
     for h in (w.plan_qkv, w.plan_o, w.keys):
         h.free()
     torch.cuda.empty_cache()
-    cfg4 = cfg4_batching(args.cfg4_seqs) if args.cfg4_seqs and world == 1 else None
+    bl_batch = bert_large_batching(args.bert_large_seqs) if args.bert_large_seqs and world == 1 else None
     lnorm = layernorm_bench(max(2, min(10, args.steps // 5))) if args.layernorm and world == 1 else None
     layer = layer_bench() if args.layer and world == 1 else None
     attn = attention_cc(max(1, min(5, args.steps // 4))) if args.attention and world == 1 else None
     serving = serving_bench() if args.serving and world == 1 else None
-    serving5 = serving_cfg5_bench() if args.serving_cfg5 and world == 1 else None
+    serving5 = serving_n65536_bench() if args.serving_n65536 and world == 1 else None
     if rank != 0:
         return
     peaks = {}
@@ -1319,7 +1319,7 @@ def run_blb(args):
         "serving_n65536": serving5,
         "layernorm_head": lnorm,
         "encoder_layer": layer,
-        "cfg4_batching": cfg4,
+        "bert_large_batching": bl_batch,
         "conversion": dict(conv, sites={k: dict(v, frac_of_hbm=round(v["achieved_gbs"] / hbm, 4), peak_kind=peak_note)
                                         for k, v in conv["sites"].items()}) if conv else None,
         "counts_per_step": w_counts,
@@ -1590,7 +1590,7 @@ def main():
     ap.add_argument("--batch", type=int, default=8, help="sequences per batched step (1 = skip)")
     ap.add_argument("--no-attention", dest="attention", action="store_false",
                     help="skip the matmul_cc attention measurement")
-    ap.add_argument("--cfg4-seqs", type=int, default=32,
+    ap.add_argument("--bert-large-seqs", type=int, default=32,
                     help="BERT-large uneven-length sequences of the batching measurement (0 = skip; 32 = the full config)")
     ap.add_argument("--no-layer", dest="layer", action="store_false",
                     help="skip the hybrid encoder-layer measurement")
@@ -1598,7 +1598,7 @@ def main():
                     help="skip the LayerNorm-head (rotate-and-sum) measurement")
     ap.add_argument("--no-conversion", dest="conversion", action="store_false",
                     help="skip the CKKS <-> MPC conversion measurement")
-    ap.add_argument("--no-serving-n65536", dest="serving_cfg5", action="store_false",
+    ap.add_argument("--no-serving-n65536", dest="serving_n65536", action="store_false",
                     help="skip the continuous-batching measurement at N=2^16 (lengths up to 1024, chunked)")
     ap.add_argument("--no-serving", dest="serving", action="store_false",
                     help="skip the continuous-batching serving measurement")
