@@ -1234,12 +1234,24 @@ def run_blb(args):
     for h in (w.plan_qkv, w.plan_o, w.keys):
         h.free()
     torch.cuda.empty_cache()
-    bl_batch = bert_large_batching(args.bert_large_seqs) if args.bert_large_seqs and world == 1 else None
-    lnorm = layernorm_bench(max(2, min(10, args.steps // 5))) if args.layernorm and world == 1 else None
-    layer = layer_bench() if args.layer and world == 1 else None
-    attn = attention_cc(max(1, min(5, args.steps // 4))) if args.attention and world == 1 else None
-    serving = serving_bench() if args.serving and world == 1 else None
-    serving5 = serving_n65536_bench() if args.serving_n65536 and world == 1 else None
+    def section(run, fn):
+        """A further workload's figures; a library error in it (an allocation
+        the device cannot hold, say) is reported in its place instead of
+        ending the run before the line is printed."""
+        if not run or world != 1:
+            return None
+        try:
+            return fn()
+        except blb.BlbError as e:
+            torch.cuda.empty_cache()
+            return {"error": str(e)}
+
+    bl_batch = section(args.bert_large_seqs, lambda: bert_large_batching(args.bert_large_seqs))
+    lnorm = section(args.layernorm, lambda: layernorm_bench(max(2, min(10, args.steps // 5))))
+    layer = section(args.layer, layer_bench)
+    attn = section(args.attention, lambda: attention_cc(max(1, min(5, args.steps // 4))))
+    serving = section(args.serving, serving_bench)
+    serving5 = section(args.serving_n65536, serving_n65536_bench)
     if rank != 0:
         return
     peaks = {}
