@@ -376,6 +376,22 @@ uint64_t galois_element(uint32_t N, int32_t rot);
 // launchers (all on ctx->stream)
 // ---------------------------------------------------------------------------
 // NTT of `rows` rows of N words; row r uses prime map.p[r % map.n]
+// The rescale's forward transform with its elementwise steps fused into it:
+// rows are (polynomial p, prime i < level), row p level + i; the first pass
+// reads the centered lift of the q_level limb of polynomial p (coefficient
+// form, `last`) reduced mod q_i instead of the row, and the last pass writes
+// (in_i - result) q_level^-1 mod q_i to row p level + i of `out` instead of
+// the row (in: polynomial p of a stack of ciphertexts of ppc polynomials,
+// `stride` words apart).  `data` holds the rows between the two passes.
+struct RescaleIO {
+    const uint64_t* last;
+    const uint64_t* in;
+    uint64_t* out;
+    size_t stride;
+    uint32_t level, ppc;
+    uint64_t inv[BLB_MAXP], inv_sh[BLB_MAXP];
+};
+int ntt_forward_rescale(blb_ctx* ctx, uint64_t* data, uint32_t rows, const RescaleIO& rs);
 int ntt_forward(blb_ctx* ctx, uint64_t* data, uint32_t rows, const LimbMap& map);
 int ntt_inverse(blb_ctx* ctx, uint64_t* data, uint32_t rows, const LimbMap& map);
 // same on an explicit device row list: entry = row index | prime index << 24

@@ -118,49 +118,14 @@ __global__ void k_sample_uniform(uint64_t* out, uint32_t N, const __grid_constan
 }
 
 // Rescale (Sec. 2.4), evaluation domain: out_i = (in_i - T_i) * q_l^-1 where T_i
-// is the NTT mod q_i of the centered lift of the last limb.
-struct RescaleConsts {
-    uint64_t inv[BLB_MAXP], inv_sh[BLB_MAXP];
-};
+// is the NTT mod q_i of the centered lift of the last limb (the lift, the
+// transform and the division run as one forward transform, ntt_forward_rescale).
 // input polynomial pp of a stack of ciphertexts with ppc polynomials each,
 // `stride` words apart
 __device__ __forceinline__ const uint64_t* stack_poly(const uint64_t* in, uint32_t pp, uint32_t ppc, size_t stride,
                                                       uint32_t level, uint32_t N)
 {
     return in + (size_t)(pp / ppc) * stride + (size_t)(pp % ppc) * (level + 1) * N;
-}
-
-__global__ void k_rescale_finish(uint64_t* __restrict__ out, const uint64_t* __restrict__ in,
-                                 const uint64_t* __restrict__ T, const uint64_t* __restrict__ qs, uint32_t N,
-                                 uint32_t level, RescaleConsts rc, uint32_t ppc, size_t stride)
-{
-    const uint32_t row = blockIdx.y, c = blockIdx.x * blockDim.x + threadIdx.x;  // row = poly * level + i
-    if (c >= N) return;
-    const uint32_t poly = row / level, i = row % level;
-    const uint64_t q = qs[i];
-    uint64_t x = stack_poly(in, poly, ppc, stride, level, N)[(size_t)i * N + c];
-    uint64_t t = T[(size_t)row * N + c];
-    out[(size_t)row * N + c] = mul_shoup(sub_mod(x, t, q), rc.inv[i], rc.inv_sh[i], q);
-}
-
-// centered lift of the q_l limb (coefficient form) reduced mod q_i, i < level
-__global__ void k_lift_last(uint64_t* __restrict__ T, const uint64_t* __restrict__ last,
-                            const uint64_t* __restrict__ qs, const uint64_t* __restrict__ bar, uint32_t N,
-                            uint32_t level)
-{
-    const uint32_t row = blockIdx.y, c = blockIdx.x * blockDim.x + threadIdx.x;  // row = poly * level + i
-    if (c >= N) return;
-    const uint32_t poly = row / level, i = row % level;
-    const uint64_t ql = qs[level], q = qs[i], rb = bar[2 * i + 1];
-    uint64_t v = last[(size_t)poly * N + c];
-    uint64_t r;
-    if (v > ql / 2) {  // negative representative v - q_l
-        uint64_t m = reduce64(ql - v, q, rb);
-        r = m ? q - m : 0;
-    } else {
-        r = reduce64(v, q, rb);
-    }
-    T[(size_t)row * N + c] = r;
 }
 
 __global__ void k_copy_last(uint64_t* __restrict__ dst, const uint64_t* __restrict__ in, uint32_t N, uint32_t level,
@@ -326,20 +291,20 @@ int launch_rescale_strided(blb_ctx* ctx, uint64_t* out, const uint64_t* in, uint
         if (cudaGetLastError() != cudaSuccess) { rc = blb_fail(BLB_ERR_CUDA, "rescale launch failed"); break; }
         blb_count_launch();
         if ((rc = ntt_inverse(ctx, last, npolys, ctx->qmap(1, level)))) break;
-        const uint32_t rows = npolys * level;
-        k_lift_last<<<grid_rows(N, rows), kT, 0, ctx->stream>>>(T, last, ctx->d_q, ctx->d_bar, N, level);
-        if (cudaGetLastError() != cudaSuccess) { rc = blb_fail(BLB_ERR_CUDA, "rescale launch failed"); break; }
-        blb_count_launch();
-        if ((rc = ntt_forward(ctx, T, rows, ctx->qmap(level)))) break;
-        RescaleConsts rcst{};
+        // the lift of the last limb, its forward transforms and the division
+        // by q_level in one transform (T holds the rows between its passes)
+        RescaleIO rs{};
+        rs.last = last;
+        rs.in = in;
+        rs.out = out;
+        rs.stride = stride;
+        rs.level = level;
+        rs.ppc = ppc;
         for (uint32_t i = 0; i < level; i++) {
-            rcst.inv[i] = ctx->ql_inv[level][i];
-            rcst.inv_sh[i] = shoup_companion(rcst.inv[i], ctx->q[i]);
+            rs.inv[i] = ctx->ql_inv[level][i];
+            rs.inv_sh[i] = shoup_companion(rs.inv[i], ctx->q[i]);
         }
-        k_rescale_finish<<<grid_rows(N, rows), kT, 0, ctx->stream>>>(out, in, T, ctx->d_q, N, level, rcst, ppc,
-                                                                     stride);
-        if (cudaGetLastError() != cudaSuccess) { rc = blb_fail(BLB_ERR_CUDA, "rescale launch failed"); break; }
-        blb_count_launch();
+        if ((rc = ntt_forward_rescale(ctx, T, npolys * level, rs))) break;
     } while (0);
     if (tmp) dev_free(ctx, tmp, need * 8);
     return rc;

@@ -150,6 +150,28 @@ __device__ __forceinline__ uint64_t finish_value(uint64_t v, const Fin& f, uint6
     return v >= q ? v - q : v;
 }
 
+// The row's part of a fused rescale (RescaleIO): where its lift comes from and
+// where its result goes.
+struct RsRow {
+    const uint64_t* last;
+    const uint64_t* in;
+    uint64_t* out;
+    uint64_t ql, rb, inv, inv_sh;
+};
+
+// the centered lift of v (a residue mod ql) reduced mod q, in [0, q)
+__device__ __forceinline__ uint64_t lift_mod(uint64_t v, uint64_t ql, uint64_t q, uint64_t rb)
+{
+    if (v > ql / 2) {
+        const uint64_t m = ql - v;
+        const uint64_t r = m - __umul64hi(m, rb) * q;
+        const uint64_t mr = r >= q ? r - q : r;
+        return mr ? q - mr : 0;
+    }
+    const uint64_t r = v - __umul64hi(v, rb) * q;
+    return r >= q ? r - q : r;
+}
+
 // global position (within the row) of tile element e
 template <int LOGN, int LP, bool COLS>
 __device__ __forceinline__ size_t tile_pos(uint32_t e, uint32_t c0)
@@ -163,9 +185,13 @@ __device__ __forceinline__ size_t tile_pos(uint32_t e, uint32_t c0)
 // bits [PLO, PLO + R).  The pass's first round reads its groups from the row
 // in global memory (FROM_G) and its last round writes them back, finished
 // (TO_G); the rounds between go through the tile in shared memory.
-template <int LOGN, int LP, bool COLS, bool INV, bool SMALL, int PLO, int R, bool FROM_G, bool TO_G, bool LAST>
+// RSL: the first round of a fused rescale's first pass (loads the lift of the
+// last limb); RSS: the last round of its last pass (stores the rescaled limb).
+template <int LOGN, int LP, bool COLS, bool INV, bool SMALL, int PLO, int R, bool FROM_G, bool TO_G, bool LAST,
+          bool RSL = false, bool RSS = false>
 __device__ __forceinline__ void round(uint64_t* sm, uint64_t* __restrict__ a, uint32_t c0,
-                                      const ulonglong2* __restrict__ W, uint64_t q, uint64_t q2, const Fin& fin)
+                                      const ulonglong2* __restrict__ W, uint64_t q, uint64_t q2, const Fin& fin,
+                                      const RsRow& rr)
 {
     using G_ = Geo<LOGN, LP, COLS>;
     constexpr uint32_t K = 1u << R;
@@ -195,7 +221,8 @@ __device__ __forceinline__ void round(uint64_t* sm, uint64_t* __restrict__ a, ui
 #pragma unroll
         for (uint32_t k = 0; k < K; k++) {
             const uint32_t e = e_base + k * e_stride;
-            x[k] = FROM_G ? a[tile_pos<LOGN, LP, COLS>(e, c0)] : sm[padi(e)];
+            if (RSL) x[k] = lift_mod(rr.last[tile_pos<LOGN, LP, COLS>(e, c0)], rr.ql, q, rr.rb);
+            else x[k] = FROM_G ? a[tile_pos<LOGN, LP, COLS>(e, c0)] : sm[padi(e)];
         }
         // The butterflied bits of base_r are zero, so for the pair (k, k | 2^u)
         // the lower element's twiddle index splits into a per-stage base plus
@@ -236,36 +263,44 @@ __device__ __forceinline__ void round(uint64_t* sm, uint64_t* __restrict__ a, ui
 #pragma unroll
         for (uint32_t k = 0; k < K; k++) {
             const uint32_t e = e_base + k * e_stride;
-            if (TO_G) a[tile_pos<LOGN, LP, COLS>(e, c0)] = finish_value<INV, LAST>(x[k], fin, q, q2);
-            else sm[padi(e)] = x[k];
+            if (RSS) {
+                const size_t pos = tile_pos<LOGN, LP, COLS>(e, c0);
+                const uint64_t t = finish_value<INV, LAST>(x[k], fin, q, q2);
+                rr.out[pos] = mul_shoup(sub_mod(rr.in[pos], t, q), rr.inv, rr.inv_sh, q);
+            } else if (TO_G) {
+                a[tile_pos<LOGN, LP, COLS>(e, c0)] = finish_value<INV, LAST>(x[k], fin, q, q2);
+            } else {
+                sm[padi(e)] = x[k];
+            }
         }
     }
 }
 
 // forward rounds: local bits from the top down, up to RB stages per round
 // (radix 2^RB); the first reads the row, the last writes it
-template <int LOGN, int LP, bool COLS, bool SMALL, int PHI, int RB, bool LAST>
+template <int LOGN, int LP, bool COLS, bool SMALL, int PHI, int RB, bool LAST, bool RSL = false, bool RSS = false>
 __device__ __forceinline__ void fwd_rounds(uint64_t* sm, uint64_t* a, uint32_t c0, const ulonglong2* W, uint64_t q,
-                                           uint64_t q2, const Fin& fin)
+                                           uint64_t q2, const Fin& fin, const RsRow& rr)
 {
     if constexpr (PHI > 0) {
         constexpr int R = PHI >= RB ? RB : PHI;
-        round<LOGN, LP, COLS, false, SMALL, PHI - R, R, PHI == LP, PHI - R == 0, LAST>(sm, a, c0, W, q, q2, fin);
+        round<LOGN, LP, COLS, false, SMALL, PHI - R, R, PHI == LP, PHI - R == 0, LAST, RSL && PHI == LP,
+              RSS && PHI - R == 0>(sm, a, c0, W, q, q2, fin, rr);
         if constexpr (PHI - R > 0) __syncthreads();
-        fwd_rounds<LOGN, LP, COLS, SMALL, PHI - R, RB, LAST>(sm, a, c0, W, q, q2, fin);
+        fwd_rounds<LOGN, LP, COLS, SMALL, PHI - R, RB, LAST, RSL, RSS>(sm, a, c0, W, q, q2, fin, rr);
     }
 }
 
 // inverse rounds: local bits from the bottom up
 template <int LOGN, int LP, bool COLS, bool SMALL, int PLO, int RB, bool LAST>
 __device__ __forceinline__ void inv_rounds(uint64_t* sm, uint64_t* a, uint32_t c0, const ulonglong2* W, uint64_t q,
-                                           uint64_t q2, const Fin& fin)
+                                           uint64_t q2, const Fin& fin, const RsRow& rr)
 {
     if constexpr (PLO < LP) {
         constexpr int R = LP - PLO >= RB ? RB : LP - PLO;
-        round<LOGN, LP, COLS, true, SMALL, PLO, R, PLO == 0, PLO + R == LP, LAST>(sm, a, c0, W, q, q2, fin);
+        round<LOGN, LP, COLS, true, SMALL, PLO, R, PLO == 0, PLO + R == LP, LAST>(sm, a, c0, W, q, q2, fin, rr);
         if constexpr (PLO + R < LP) __syncthreads();
-        inv_rounds<LOGN, LP, COLS, SMALL, PLO + R, RB, LAST>(sm, a, c0, W, q, q2, fin);
+        inv_rounds<LOGN, LP, COLS, SMALL, PLO + R, RB, LAST>(sm, a, c0, W, q, q2, fin, rr);
     }
 }
 
@@ -274,16 +309,21 @@ constexpr int ntt_ctas(int RB) { return RB >= 4 ? 3 : 4; }
 
 // One pass over one tile of one row.  The last pass brings results to [0, q)
 // (and, for the inverse, multiplies by N^-1).
-template <bool INV, int LOGN, int LP, bool COLS, int RB>
+// RS: the forward transform of a fused rescale (RescaleIO; rows by the map,
+// no row list).
+template <bool INV, int LOGN, int LP, bool COLS, int RB, bool RS = false>
 __global__ void __launch_bounds__(kThreads, ntt_ctas(RB)) k_ntt(uint64_t* __restrict__ data, const __grid_constant__ LimbMap map,
                                                     const uint32_t* __restrict__ rowlist, uint32_t y0,
                                                     const uint64_t* __restrict__ qs,
                                                     const ulonglong2* __restrict__ tw,
                                                     const uint64_t* __restrict__ ninv,
-                                                    const uint64_t* __restrict__ bar)
+                                                    const uint64_t* __restrict__ bar,
+                                                    const __grid_constant__ RescaleIO rs)
 {
     using G_ = Geo<LOGN, LP, COLS>;
     constexpr bool LAST = (LP == LOGN) || (INV ? COLS : !COLS);
+    constexpr bool FIRST = (LP == LOGN) || (INV ? !COLS : COLS);
+    static_assert(!(RS && INV), "the rescale's transform is a forward one");
     __shared__ uint64_t sm[G_::TILE + G_::TILE / 16];
     pdl_begin();  // launched with programmatic stream serialization
     uint32_t row, pi;
@@ -298,22 +338,34 @@ __global__ void __launch_bounds__(kThreads, ntt_ctas(RB)) k_ntt(uint64_t* __rest
         fin.nis = ninv[2 * pi + 1];
     }
     if (!INV && LAST) fin.r1 = bar[2 * pi + 1];  // floor(2^64 / q)
+    RsRow rr{};
+    if (RS) {  // row = polynomial level + prime
+        const uint32_t poly = row / rs.level, i = row % rs.level;
+        rr.last = rs.last + (size_t)poly * G_::N;
+        rr.in = rs.in + (size_t)(poly / rs.ppc) * rs.stride + ((size_t)(poly % rs.ppc) * (rs.level + 1) + i) * G_::N;
+        rr.out = rs.out + (size_t)row * G_::N;
+        rr.ql = qs[rs.level];
+        rr.rb = bar[2 * pi + 1];
+        rr.inv = rs.inv[i];
+        rr.inv_sh = rs.inv_sh[i];
+    }
     // the first round loads its groups from the row and the last stores them,
     // so the tile passes through shared memory only between rounds
     if (!INV) {
-        if (fin.small) fwd_rounds<LOGN, LP, COLS, true, LP, RB, LAST>(sm, a, c0, W, q, q2, fin);
-        else fwd_rounds<LOGN, LP, COLS, false, LP, RB, LAST>(sm, a, c0, W, q, q2, fin);
+        if (fin.small) fwd_rounds<LOGN, LP, COLS, true, LP, RB, LAST, RS && FIRST, RS && LAST>(sm, a, c0, W, q, q2, fin, rr);
+        else fwd_rounds<LOGN, LP, COLS, false, LP, RB, LAST, RS && FIRST, RS && LAST>(sm, a, c0, W, q, q2, fin, rr);
     } else {
-        if (fin.small) inv_rounds<LOGN, LP, COLS, true, 0, RB, LAST>(sm, a, c0, W, q, q2, fin);
-        else inv_rounds<LOGN, LP, COLS, false, 0, RB, LAST>(sm, a, c0, W, q, q2, fin);
+        if (fin.small) inv_rounds<LOGN, LP, COLS, true, 0, RB, LAST>(sm, a, c0, W, q, q2, fin, rr);
+        else inv_rounds<LOGN, LP, COLS, false, 0, RB, LAST>(sm, a, c0, W, q, q2, fin, rr);
     }
 }
 
 // One forward or inverse transform with the column pass over 2^L1-point
 // sub-transforms and the row pass over 2^(LOGN - L1) points (L1 = 0: one pass).
-template <int LOGN, int L1, int RB>
+// RS: the forward transform of a fused rescale (rs).
+template <int LOGN, int L1, int RB, bool RS>
 int run_split(blb_ctx* ctx, uint64_t* data, uint32_t rows, const LimbMap& map, const uint32_t* rowlist, bool inverse,
-              const uint64_t* ninv)
+              const uint64_t* ninv, const RescaleIO& rs)
 {
     constexpr uint32_t N = 1u << LOGN;
     constexpr uint32_t TILE = N < 4096 ? N : 4096;
@@ -324,20 +376,20 @@ int run_split(blb_ctx* ctx, uint64_t* data, uint32_t rows, const LimbMap& map, c
         const dim3 grid(N / TILE, std::min(kMaxGridY, rows - y0));
         if (!inverse) {
             if constexpr (L1 > 0) {
-                BLB_CUDA(launch_pdl(k_ntt<false, LOGN, L1, true, RB>, grid, dim3(kThreads), 0, ctx->stream, data, map, rowlist, y0,
-                           (const uint64_t*)ctx->d_q, tw, ninv, (const uint64_t*)ctx->d_bar));
+                BLB_CUDA(launch_pdl(k_ntt<false, LOGN, L1, true, RB, RS>, grid, dim3(kThreads), 0, ctx->stream, data, map,
+                                    rowlist, y0, (const uint64_t*)ctx->d_q, tw, ninv, (const uint64_t*)ctx->d_bar, rs));
                 BLB_LAUNCHED();
             }
-            BLB_CUDA(launch_pdl(k_ntt<false, LOGN, L2, false, RB>, grid, dim3(kThreads), 0, ctx->stream, data, map, rowlist, y0,
-                       (const uint64_t*)ctx->d_q, tw, ninv, (const uint64_t*)ctx->d_bar));
+            BLB_CUDA(launch_pdl(k_ntt<false, LOGN, L2, false, RB, RS>, grid, dim3(kThreads), 0, ctx->stream, data, map,
+                                rowlist, y0, (const uint64_t*)ctx->d_q, tw, ninv, (const uint64_t*)ctx->d_bar, rs));
             BLB_LAUNCHED();
-        } else {
+        } else if constexpr (!RS) {
             BLB_CUDA(launch_pdl(k_ntt<true, LOGN, L2, false, RB>, grid, dim3(kThreads), 0, ctx->stream, data, map, rowlist, y0,
-                       (const uint64_t*)ctx->d_q, tw, ninv, (const uint64_t*)ctx->d_bar));
+                       (const uint64_t*)ctx->d_q, tw, ninv, (const uint64_t*)ctx->d_bar, rs));
             BLB_LAUNCHED();
             if constexpr (L1 > 0) {
                 BLB_CUDA(launch_pdl(k_ntt<true, LOGN, L1, true, RB>, grid, dim3(kThreads), 0, ctx->stream, data, map, rowlist, y0,
-                           (const uint64_t*)ctx->d_q, tw, ninv, (const uint64_t*)ctx->d_bar));
+                           (const uint64_t*)ctx->d_q, tw, ninv, (const uint64_t*)ctx->d_bar, rs));
                 BLB_LAUNCHED();
             }
         }
@@ -349,30 +401,48 @@ int run_split(blb_ctx* ctx, uint64_t* data, uint32_t rows, const LimbMap& map, c
 // context (ctx->ntt_split: 0 the middle, -1 / +1 a shorter / longer column
 // pass), and two radices of the register rounds (ctx->ntt_radix: 8, four CTAs
 // per SM, or 16, three); blb_ntt_autotune times all of them.
-template <int LOGN, int RB>
+template <int LOGN, int RB, bool RS>
 int run_nr(blb_ctx* ctx, uint64_t* data, uint32_t rows, const LimbMap& map, const uint32_t* rowlist, bool inverse,
-           const uint64_t* ninv)
+           const uint64_t* ninv, const RescaleIO& rs)
 {
     if constexpr (LOGN <= 12) {
-        return run_split<LOGN, 0, RB>(ctx, data, rows, map, rowlist, inverse, ninv);
+        return run_split<LOGN, 0, RB, RS>(ctx, data, rows, map, rowlist, inverse, ninv, rs);
     } else {
         constexpr int M = LOGN / 2;
         switch (ctx->ntt_split) {
-        case -1: return run_split<LOGN, M - 1, RB>(ctx, data, rows, map, rowlist, inverse, ninv);
+        case -1: return run_split<LOGN, M - 1, RB, RS>(ctx, data, rows, map, rowlist, inverse, ninv, rs);
         case 1:
-            if constexpr (LOGN - (M + 1) >= 1) return run_split<LOGN, M + 1, RB>(ctx, data, rows, map, rowlist, inverse, ninv);
-            else return run_split<LOGN, M, RB>(ctx, data, rows, map, rowlist, inverse, ninv);
-        default: return run_split<LOGN, M, RB>(ctx, data, rows, map, rowlist, inverse, ninv);
+            if constexpr (LOGN - (M + 1) >= 1)
+                return run_split<LOGN, M + 1, RB, RS>(ctx, data, rows, map, rowlist, inverse, ninv, rs);
+            else return run_split<LOGN, M, RB, RS>(ctx, data, rows, map, rowlist, inverse, ninv, rs);
+        default: return run_split<LOGN, M, RB, RS>(ctx, data, rows, map, rowlist, inverse, ninv, rs);
         }
     }
 }
 
-template <int LOGN>
+template <int LOGN, bool RS>
 int run_n(blb_ctx* ctx, uint64_t* data, uint32_t rows, const LimbMap& map, const uint32_t* rowlist, bool inverse,
-          const uint64_t* ninv)
+          const uint64_t* ninv, const RescaleIO& rs)
 {
-    if (ctx->ntt_radix == 16) return run_nr<LOGN, 4>(ctx, data, rows, map, rowlist, inverse, ninv);
-    return run_nr<LOGN, 3>(ctx, data, rows, map, rowlist, inverse, ninv);
+    if (ctx->ntt_radix == 16) return run_nr<LOGN, 4, RS>(ctx, data, rows, map, rowlist, inverse, ninv, rs);
+    return run_nr<LOGN, 3, RS>(ctx, data, rows, map, rowlist, inverse, ninv, rs);
+}
+
+template <bool RS>
+int run_rs(blb_ctx* ctx, uint64_t* data, uint32_t rows, const LimbMap& map, const uint32_t* rowlist, bool inverse,
+           const uint64_t* ninv, const RescaleIO& rs)
+{
+    switch (ctx->logN) {
+    case 10: return run_n<10, RS>(ctx, data, rows, map, rowlist, inverse, ninv, rs);
+    case 11: return run_n<11, RS>(ctx, data, rows, map, rowlist, inverse, ninv, rs);
+    case 12: return run_n<12, RS>(ctx, data, rows, map, rowlist, inverse, ninv, rs);
+    case 13: return run_n<13, RS>(ctx, data, rows, map, rowlist, inverse, ninv, rs);
+    case 14: return run_n<14, RS>(ctx, data, rows, map, rowlist, inverse, ninv, rs);
+    case 15: return run_n<15, RS>(ctx, data, rows, map, rowlist, inverse, ninv, rs);
+    case 16: return run_n<16, RS>(ctx, data, rows, map, rowlist, inverse, ninv, rs);
+    case 17: return run_n<17, RS>(ctx, data, rows, map, rowlist, inverse, ninv, rs);
+    default: return blb_fail(BLB_ERR_ARG, "no NTT for this ring size");
+    }
 }
 
 // ninv: [prime][2] the constant the last inverse pass multiplies by and its
@@ -381,17 +451,8 @@ int run_n(blb_ctx* ctx, uint64_t* data, uint32_t rows, const LimbMap& map, const
 int run(blb_ctx* ctx, uint64_t* data, uint32_t rows, const LimbMap& map, const uint32_t* rowlist, bool inverse,
         const uint64_t* ninv)
 {
-    switch (ctx->logN) {
-    case 10: return run_n<10>(ctx, data, rows, map, rowlist, inverse, ninv);
-    case 11: return run_n<11>(ctx, data, rows, map, rowlist, inverse, ninv);
-    case 12: return run_n<12>(ctx, data, rows, map, rowlist, inverse, ninv);
-    case 13: return run_n<13>(ctx, data, rows, map, rowlist, inverse, ninv);
-    case 14: return run_n<14>(ctx, data, rows, map, rowlist, inverse, ninv);
-    case 15: return run_n<15>(ctx, data, rows, map, rowlist, inverse, ninv);
-    case 16: return run_n<16>(ctx, data, rows, map, rowlist, inverse, ninv);
-    case 17: return run_n<17>(ctx, data, rows, map, rowlist, inverse, ninv);
-    default: return blb_fail(BLB_ERR_ARG, "no NTT for this ring size");
-    }
+    static const RescaleIO none{};
+    return run_rs<false>(ctx, data, rows, map, rowlist, inverse, ninv, none);
 }
 
 }  // namespace
@@ -478,6 +539,13 @@ int ntt_inverse(blb_ctx* ctx, uint64_t* data, uint32_t rows, const LimbMap& map)
     if (rows == 0) return BLB_OK;
     ProfScope prof(ctx, "intt", (uint64_t)rows * ctx->N * 16);
     return run(ctx, data, rows, map, nullptr, true, ctx->d_ninv);
+}
+
+int ntt_forward_rescale(blb_ctx* ctx, uint64_t* data, uint32_t rows, const RescaleIO& rs)
+{
+    if (rows == 0) return BLB_OK;
+    ProfScope prof(ctx, "ntt", (uint64_t)rows * ctx->N * 16);
+    return run_rs<true>(ctx, data, rows, ctx->qmap(rs.level), nullptr, false, ctx->d_ninv, rs);
 }
 
 int ntt_forward_list(blb_ctx* ctx, uint64_t* data, uint32_t rows, const uint32_t* d_rowlist)
