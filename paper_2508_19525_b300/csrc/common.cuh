@@ -392,6 +392,36 @@ struct RescaleIO {
     uint64_t inv[BLB_MAXP], inv_sh[BLB_MAXP];
 };
 int ntt_forward_rescale(blb_ctx* ctx, uint64_t* data, uint32_t rows, const RescaleIO& rs);
+// A key-switch source: its c1 rows (evaluation domain) and the Galois element
+// applied as they are read.
+struct GatherSrc {
+    const uint64_t* c1;
+    uint64_t g;
+};
+// The key switch's gather fused into the inverse transform of its sources:
+// rows are (source s, prime i < n), row s n + i; the first pass reads
+// c1[i][perm(k, g)] of source s instead of the row and also writes that value
+// to row i of the source's extended digit j = i / alpha
+// (ext[((s beta + j) E + i) N + k], the digit's own rows in the evaluation
+// domain).  `data` receives the rows in coefficient form.
+struct GatherIO {
+    const GatherSrc* srcs;  // device array, one per source
+    uint64_t* ext;
+    uint32_t n, E, beta, alpha;
+};
+int ntt_inverse_gather(blb_ctx* ctx, uint64_t* data, uint32_t rows, const GatherIO& ga, const uint64_t* ninv);
+
+// Evaluation-domain position read for output position k under the Galois
+// element g (the forward transform's output order is bit-reversed odd powers
+// of psi: A[k] = a(psi^(2 bitrev(k) + 1))).
+__device__ __forceinline__ uint32_t perm_index(uint32_t k, uint32_t logN, uint64_t g)
+{
+    if (g == 1) return k;
+    const uint32_t N = 1u << logN;
+    const uint64_t e = 2 * (uint64_t)(__brev(k) >> (32 - logN)) + 1;
+    const uint32_t ge = (uint32_t)((g * e) & (2ull * N - 1));
+    return __brev((ge - 1) >> 1) >> (32 - logN);
+}
 int ntt_forward(blb_ctx* ctx, uint64_t* data, uint32_t rows, const LimbMap& map);
 int ntt_inverse(blb_ctx* ctx, uint64_t* data, uint32_t rows, const LimbMap& map);
 // same on an explicit device row list: entry = row index | prime index << 24

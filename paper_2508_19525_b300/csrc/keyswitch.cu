@@ -309,10 +309,7 @@ extern "C" int blb_keyswitch_noalloc(blb_ctx* c, const blb_keys* K, int32_t rot,
 // ===========================================================================
 namespace {
 
-struct DevSource {
-    const uint64_t* c1;
-    uint64_t g;
-};
+using DevSource = GatherSrc;
 struct DevProduct {
     uint32_t src;
     uint64_t g;
@@ -325,30 +322,6 @@ struct DevGroup {
     uint32_t prod0, prod1, add0, add1;
 };
 
-__device__ __forceinline__ uint32_t perm_index(uint32_t k, uint32_t logN, uint64_t g)
-{
-    if (g == 1) return k;
-    const uint32_t N = 1u << logN;
-    const uint64_t e = 2 * (uint64_t)(__brev(k) >> (32 - logN)) + 1;
-    const uint32_t ge = (uint32_t)((g * e) & (2ull * N - 1));
-    return __brev((ge - 1) >> 1) >> (32 - logN);
-}
-
-// v = c1[i][perm(k)] (evaluation domain) goes to coef[src][i][k] (transformed
-// to coefficient form in place next) and to the extended digit of limb i's
-// digit j = i / alpha, whose own rows are the input's evaluation rows
-__global__ void k_ksb_gather(uint64_t* __restrict__ coef, uint64_t* __restrict__ ext,
-                             const DevSource* __restrict__ srcs, uint32_t n, uint32_t E, uint32_t beta,
-                             uint32_t alpha, uint32_t logN)
-{
-    const uint32_t N = 1u << logN;
-    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x, i = blockIdx.y, s = blockIdx.z;
-    if (k >= N) return;
-    const DevSource d = srcs[s];
-    const uint64_t v = d.c1[(size_t)i * N + perm_index(k, logN, d.g)];
-    coef[((size_t)s * n + i) * N + k] = v;
-    ext[(((size_t)s * beta + i / alpha) * E + i) * N + k] = v;
-}
 
 // ModUp of every digit of every source: grid.y = source * beta + j.  The
 // coefficient rows arrive as y_i = [x_i (D_j/q_i)^-1]_{q_i}: the inverse NTT
@@ -792,9 +765,9 @@ int ks_run(blb_ctx* ctx, uint32_t level, const KsSource* sources, uint32_t n_src
             prof.ops(mad * N, red * N, bfly * N + ntt_rows * (N / 2) * ctx->logN);
         }
         if (ns) {
-            k_ksb_gather<<<dim3(gx, n, ns), kT, 0, ctx->stream>>>(coef, ext, d_src, n, E, beta, alpha, ctx->logN);
-            BLB_LAUNCHED();
-            BLB_TRY(ntt_inverse_scaled(ctx, coef, ns * n, ctx->qmap(n), ninv_conv));
+            // the gather of the sources' c1 rows (permuted) runs in the first
+            // pass of their inverse transform
+            BLB_TRY(ntt_inverse_gather(ctx, coef, ns * n, GatherIO{d_src, ext, n, E, beta, alpha}, ninv_conv));
             launch_modup(alpha, dim3(gx, ns * beta), ctx->stream, (const uint64_t*)coef, ext,
                          (const ConvTable*)ctx->d_modup[(size_t)level * ctx->dnum], n, E, beta, alpha,
                          (const uint64_t*)ctx->d_q, (const uint64_t*)ctx->d_bar, N);

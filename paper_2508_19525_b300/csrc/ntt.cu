@@ -157,6 +157,10 @@ struct RsRow {
     const uint64_t* in;
     uint64_t* out;
     uint64_t ql, rb, inv, inv_sh;
+    // gather (GatherIO): the source's c1 row, its Galois element, the digit row
+    const uint64_t* c1;
+    uint64_t g;
+    uint64_t* ext;
 };
 
 // the centered lift of v (a residue mod ql) reduced mod q, in [0, q)
@@ -186,9 +190,11 @@ __device__ __forceinline__ size_t tile_pos(uint32_t e, uint32_t c0)
 // in global memory (FROM_G) and its last round writes them back, finished
 // (TO_G); the rounds between go through the tile in shared memory.
 // RSL: the first round of a fused rescale's first pass (loads the lift of the
-// last limb); RSS: the last round of its last pass (stores the rescaled limb).
+// last limb); RSS: the last round of its last pass (stores the rescaled limb);
+// GL: the first round of a fused gather's first pass (loads the permuted source
+// and writes it to the extended digit too).
 template <int LOGN, int LP, bool COLS, bool INV, bool SMALL, int PLO, int R, bool FROM_G, bool TO_G, bool LAST,
-          bool RSL = false, bool RSS = false>
+          bool RSL = false, bool RSS = false, bool GL = false>
 __device__ __forceinline__ void round(uint64_t* sm, uint64_t* __restrict__ a, uint32_t c0,
                                       const ulonglong2* __restrict__ W, uint64_t q, uint64_t q2, const Fin& fin,
                                       const RsRow& rr)
@@ -221,8 +227,15 @@ __device__ __forceinline__ void round(uint64_t* sm, uint64_t* __restrict__ a, ui
 #pragma unroll
         for (uint32_t k = 0; k < K; k++) {
             const uint32_t e = e_base + k * e_stride;
-            if (RSL) x[k] = lift_mod(rr.last[tile_pos<LOGN, LP, COLS>(e, c0)], rr.ql, q, rr.rb);
-            else x[k] = FROM_G ? a[tile_pos<LOGN, LP, COLS>(e, c0)] : sm[padi(e)];
+            if (RSL) {
+                x[k] = lift_mod(rr.last[tile_pos<LOGN, LP, COLS>(e, c0)], rr.ql, q, rr.rb);
+            } else if (GL) {
+                const uint32_t pos = (uint32_t)tile_pos<LOGN, LP, COLS>(e, c0);
+                x[k] = rr.c1[perm_index(pos, LOGN, rr.g)];
+                rr.ext[pos] = x[k];
+            } else {
+                x[k] = FROM_G ? a[tile_pos<LOGN, LP, COLS>(e, c0)] : sm[padi(e)];
+            }
         }
         // The butterflied bits of base_r are zero, so for the pair (k, k | 2^u)
         // the lower element's twiddle index splits into a per-stage base plus
@@ -292,15 +305,16 @@ __device__ __forceinline__ void fwd_rounds(uint64_t* sm, uint64_t* a, uint32_t c
 }
 
 // inverse rounds: local bits from the bottom up
-template <int LOGN, int LP, bool COLS, bool SMALL, int PLO, int RB, bool LAST>
+template <int LOGN, int LP, bool COLS, bool SMALL, int PLO, int RB, bool LAST, bool GL = false>
 __device__ __forceinline__ void inv_rounds(uint64_t* sm, uint64_t* a, uint32_t c0, const ulonglong2* W, uint64_t q,
                                            uint64_t q2, const Fin& fin, const RsRow& rr)
 {
     if constexpr (PLO < LP) {
         constexpr int R = LP - PLO >= RB ? RB : LP - PLO;
-        round<LOGN, LP, COLS, true, SMALL, PLO, R, PLO == 0, PLO + R == LP, LAST>(sm, a, c0, W, q, q2, fin, rr);
+        round<LOGN, LP, COLS, true, SMALL, PLO, R, PLO == 0, PLO + R == LP, LAST, false, false, GL && PLO == 0>(
+            sm, a, c0, W, q, q2, fin, rr);
         if constexpr (PLO + R < LP) __syncthreads();
-        inv_rounds<LOGN, LP, COLS, SMALL, PLO + R, RB, LAST>(sm, a, c0, W, q, q2, fin, rr);
+        inv_rounds<LOGN, LP, COLS, SMALL, PLO + R, RB, LAST, GL>(sm, a, c0, W, q, q2, fin, rr);
     }
 }
 
@@ -309,21 +323,24 @@ constexpr int ntt_ctas(int RB) { return RB >= 4 ? 3 : 4; }
 
 // One pass over one tile of one row.  The last pass brings results to [0, q)
 // (and, for the inverse, multiplies by N^-1).
-// RS: the forward transform of a fused rescale (RescaleIO; rows by the map,
-// no row list).
-template <bool INV, int LOGN, int LP, bool COLS, int RB, bool RS = false>
+// IO: 0 plain; 1 the forward transform of a fused rescale (RescaleIO); 2 the
+// inverse transform of a fused key-switch gather (GatherIO).  IO > 0: rows by
+// the map, no row list.
+template <bool INV, int LOGN, int LP, bool COLS, int RB, int IO = 0>
 __global__ void __launch_bounds__(kThreads, ntt_ctas(RB)) k_ntt(uint64_t* __restrict__ data, const __grid_constant__ LimbMap map,
                                                     const uint32_t* __restrict__ rowlist, uint32_t y0,
                                                     const uint64_t* __restrict__ qs,
                                                     const ulonglong2* __restrict__ tw,
                                                     const uint64_t* __restrict__ ninv,
                                                     const uint64_t* __restrict__ bar,
-                                                    const __grid_constant__ RescaleIO rs)
+                                                    const __grid_constant__ RescaleIO rs,
+                                                    const __grid_constant__ GatherIO ga)
 {
     using G_ = Geo<LOGN, LP, COLS>;
     constexpr bool LAST = (LP == LOGN) || (INV ? COLS : !COLS);
     constexpr bool FIRST = (LP == LOGN) || (INV ? !COLS : COLS);
-    static_assert(!(RS && INV), "the rescale's transform is a forward one");
+    constexpr bool RS = IO == 1, GA = IO == 2;
+    static_assert(!(RS && INV) && !(GA && !INV), "rescale: forward only; gather: inverse only");
     __shared__ uint64_t sm[G_::TILE + G_::TILE / 16];
     pdl_begin();  // launched with programmatic stream serialization
     uint32_t row, pi;
@@ -349,47 +366,59 @@ __global__ void __launch_bounds__(kThreads, ntt_ctas(RB)) k_ntt(uint64_t* __rest
         rr.inv = rs.inv[i];
         rr.inv_sh = rs.inv_sh[i];
     }
+    if (GA && FIRST) {  // row = source n + prime
+        const uint32_t src = row / ga.n, i = row % ga.n;
+        const GatherSrc d = ga.srcs[src];
+        rr.c1 = d.c1 + (size_t)i * G_::N;
+        rr.g = d.g;
+        rr.ext = ga.ext + (((size_t)src * ga.beta + i / ga.alpha) * ga.E + i) * G_::N;
+    }
     // the first round loads its groups from the row and the last stores them,
     // so the tile passes through shared memory only between rounds
     if (!INV) {
         if (fin.small) fwd_rounds<LOGN, LP, COLS, true, LP, RB, LAST, RS && FIRST, RS && LAST>(sm, a, c0, W, q, q2, fin, rr);
         else fwd_rounds<LOGN, LP, COLS, false, LP, RB, LAST, RS && FIRST, RS && LAST>(sm, a, c0, W, q, q2, fin, rr);
     } else {
-        if (fin.small) inv_rounds<LOGN, LP, COLS, true, 0, RB, LAST>(sm, a, c0, W, q, q2, fin, rr);
-        else inv_rounds<LOGN, LP, COLS, false, 0, RB, LAST>(sm, a, c0, W, q, q2, fin, rr);
+        if (fin.small) inv_rounds<LOGN, LP, COLS, true, 0, RB, LAST, GA && FIRST>(sm, a, c0, W, q, q2, fin, rr);
+        else inv_rounds<LOGN, LP, COLS, false, 0, RB, LAST, GA && FIRST>(sm, a, c0, W, q, q2, fin, rr);
     }
 }
 
 // One forward or inverse transform with the column pass over 2^L1-point
 // sub-transforms and the row pass over 2^(LOGN - L1) points (L1 = 0: one pass).
-// RS: the forward transform of a fused rescale (rs).
-template <int LOGN, int L1, int RB, bool RS>
+// IO as k_ntt: 1 the forward transform of a fused rescale (rs), 2 the inverse
+// transform of a fused gather (ga).
+template <int LOGN, int L1, int RB, int IO>
 int run_split(blb_ctx* ctx, uint64_t* data, uint32_t rows, const LimbMap& map, const uint32_t* rowlist, bool inverse,
-              const uint64_t* ninv, const RescaleIO& rs)
+              const uint64_t* ninv, const RescaleIO& rs, const GatherIO& ga)
 {
     constexpr uint32_t N = 1u << LOGN;
     constexpr uint32_t TILE = N < 4096 ? N : 4096;
     constexpr int L2 = LOGN - L1;
     static_assert(L2 <= 12 && (L1 == 0 || L1 <= 12), "pass longer than a tile");
     const ulonglong2* tw = reinterpret_cast<const ulonglong2*>(ctx->d_tw);
+    const uint64_t* qs = (const uint64_t*)ctx->d_q;
+    const uint64_t* bar = (const uint64_t*)ctx->d_bar;
     for (uint32_t y0 = 0; y0 < rows; y0 += kMaxGridY) {
         const dim3 grid(N / TILE, std::min(kMaxGridY, rows - y0));
         if (!inverse) {
-            if constexpr (L1 > 0) {
-                BLB_CUDA(launch_pdl(k_ntt<false, LOGN, L1, true, RB, RS>, grid, dim3(kThreads), 0, ctx->stream, data, map,
-                                    rowlist, y0, (const uint64_t*)ctx->d_q, tw, ninv, (const uint64_t*)ctx->d_bar, rs));
+            if constexpr (IO != 2) {
+                if constexpr (L1 > 0) {
+                    BLB_CUDA(launch_pdl(k_ntt<false, LOGN, L1, true, RB, IO>, grid, dim3(kThreads), 0, ctx->stream, data,
+                                        map, rowlist, y0, qs, tw, ninv, bar, rs, ga));
+                    BLB_LAUNCHED();
+                }
+                BLB_CUDA(launch_pdl(k_ntt<false, LOGN, L2, false, RB, IO>, grid, dim3(kThreads), 0, ctx->stream, data,
+                                    map, rowlist, y0, qs, tw, ninv, bar, rs, ga));
                 BLB_LAUNCHED();
             }
-            BLB_CUDA(launch_pdl(k_ntt<false, LOGN, L2, false, RB, RS>, grid, dim3(kThreads), 0, ctx->stream, data, map,
-                                rowlist, y0, (const uint64_t*)ctx->d_q, tw, ninv, (const uint64_t*)ctx->d_bar, rs));
-            BLB_LAUNCHED();
-        } else if constexpr (!RS) {
-            BLB_CUDA(launch_pdl(k_ntt<true, LOGN, L2, false, RB>, grid, dim3(kThreads), 0, ctx->stream, data, map, rowlist, y0,
-                       (const uint64_t*)ctx->d_q, tw, ninv, (const uint64_t*)ctx->d_bar, rs));
+        } else if constexpr (IO != 1) {
+            BLB_CUDA(launch_pdl(k_ntt<true, LOGN, L2, false, RB, IO>, grid, dim3(kThreads), 0, ctx->stream, data, map,
+                                rowlist, y0, qs, tw, ninv, bar, rs, ga));
             BLB_LAUNCHED();
             if constexpr (L1 > 0) {
-                BLB_CUDA(launch_pdl(k_ntt<true, LOGN, L1, true, RB>, grid, dim3(kThreads), 0, ctx->stream, data, map, rowlist, y0,
-                           (const uint64_t*)ctx->d_q, tw, ninv, (const uint64_t*)ctx->d_bar, rs));
+                BLB_CUDA(launch_pdl(k_ntt<true, LOGN, L1, true, RB, IO>, grid, dim3(kThreads), 0, ctx->stream, data, map,
+                                    rowlist, y0, qs, tw, ninv, bar, rs, ga));
                 BLB_LAUNCHED();
             }
         }
@@ -401,49 +430,52 @@ int run_split(blb_ctx* ctx, uint64_t* data, uint32_t rows, const LimbMap& map, c
 // context (ctx->ntt_split: 0 the middle, -1 / +1 a shorter / longer column
 // pass), and two radices of the register rounds (ctx->ntt_radix: 8, four CTAs
 // per SM, or 16, three); blb_ntt_autotune times all of them.
-template <int LOGN, int RB, bool RS>
+template <int LOGN, int RB, int IO>
 int run_nr(blb_ctx* ctx, uint64_t* data, uint32_t rows, const LimbMap& map, const uint32_t* rowlist, bool inverse,
-           const uint64_t* ninv, const RescaleIO& rs)
+           const uint64_t* ninv, const RescaleIO& rs, const GatherIO& ga)
 {
     if constexpr (LOGN <= 12) {
-        return run_split<LOGN, 0, RB, RS>(ctx, data, rows, map, rowlist, inverse, ninv, rs);
+        return run_split<LOGN, 0, RB, IO>(ctx, data, rows, map, rowlist, inverse, ninv, rs, ga);
     } else {
         constexpr int M = LOGN / 2;
         switch (ctx->ntt_split) {
-        case -1: return run_split<LOGN, M - 1, RB, RS>(ctx, data, rows, map, rowlist, inverse, ninv, rs);
+        case -1: return run_split<LOGN, M - 1, RB, IO>(ctx, data, rows, map, rowlist, inverse, ninv, rs, ga);
         case 1:
             if constexpr (LOGN - (M + 1) >= 1)
-                return run_split<LOGN, M + 1, RB, RS>(ctx, data, rows, map, rowlist, inverse, ninv, rs);
-            else return run_split<LOGN, M, RB, RS>(ctx, data, rows, map, rowlist, inverse, ninv, rs);
-        default: return run_split<LOGN, M, RB, RS>(ctx, data, rows, map, rowlist, inverse, ninv, rs);
+                return run_split<LOGN, M + 1, RB, IO>(ctx, data, rows, map, rowlist, inverse, ninv, rs, ga);
+            else return run_split<LOGN, M, RB, IO>(ctx, data, rows, map, rowlist, inverse, ninv, rs, ga);
+        default: return run_split<LOGN, M, RB, IO>(ctx, data, rows, map, rowlist, inverse, ninv, rs, ga);
         }
     }
 }
 
-template <int LOGN, bool RS>
+template <int LOGN, int IO>
 int run_n(blb_ctx* ctx, uint64_t* data, uint32_t rows, const LimbMap& map, const uint32_t* rowlist, bool inverse,
-          const uint64_t* ninv, const RescaleIO& rs)
+          const uint64_t* ninv, const RescaleIO& rs, const GatherIO& ga)
 {
-    if (ctx->ntt_radix == 16) return run_nr<LOGN, 4, RS>(ctx, data, rows, map, rowlist, inverse, ninv, rs);
-    return run_nr<LOGN, 3, RS>(ctx, data, rows, map, rowlist, inverse, ninv, rs);
+    if (ctx->ntt_radix == 16) return run_nr<LOGN, 4, IO>(ctx, data, rows, map, rowlist, inverse, ninv, rs, ga);
+    return run_nr<LOGN, 3, IO>(ctx, data, rows, map, rowlist, inverse, ninv, rs, ga);
 }
 
-template <bool RS>
-int run_rs(blb_ctx* ctx, uint64_t* data, uint32_t rows, const LimbMap& map, const uint32_t* rowlist, bool inverse,
-           const uint64_t* ninv, const RescaleIO& rs)
+template <int IO>
+int run_io(blb_ctx* ctx, uint64_t* data, uint32_t rows, const LimbMap& map, const uint32_t* rowlist, bool inverse,
+           const uint64_t* ninv, const RescaleIO& rs, const GatherIO& ga)
 {
     switch (ctx->logN) {
-    case 10: return run_n<10, RS>(ctx, data, rows, map, rowlist, inverse, ninv, rs);
-    case 11: return run_n<11, RS>(ctx, data, rows, map, rowlist, inverse, ninv, rs);
-    case 12: return run_n<12, RS>(ctx, data, rows, map, rowlist, inverse, ninv, rs);
-    case 13: return run_n<13, RS>(ctx, data, rows, map, rowlist, inverse, ninv, rs);
-    case 14: return run_n<14, RS>(ctx, data, rows, map, rowlist, inverse, ninv, rs);
-    case 15: return run_n<15, RS>(ctx, data, rows, map, rowlist, inverse, ninv, rs);
-    case 16: return run_n<16, RS>(ctx, data, rows, map, rowlist, inverse, ninv, rs);
-    case 17: return run_n<17, RS>(ctx, data, rows, map, rowlist, inverse, ninv, rs);
+    case 10: return run_n<10, IO>(ctx, data, rows, map, rowlist, inverse, ninv, rs, ga);
+    case 11: return run_n<11, IO>(ctx, data, rows, map, rowlist, inverse, ninv, rs, ga);
+    case 12: return run_n<12, IO>(ctx, data, rows, map, rowlist, inverse, ninv, rs, ga);
+    case 13: return run_n<13, IO>(ctx, data, rows, map, rowlist, inverse, ninv, rs, ga);
+    case 14: return run_n<14, IO>(ctx, data, rows, map, rowlist, inverse, ninv, rs, ga);
+    case 15: return run_n<15, IO>(ctx, data, rows, map, rowlist, inverse, ninv, rs, ga);
+    case 16: return run_n<16, IO>(ctx, data, rows, map, rowlist, inverse, ninv, rs, ga);
+    case 17: return run_n<17, IO>(ctx, data, rows, map, rowlist, inverse, ninv, rs, ga);
     default: return blb_fail(BLB_ERR_ARG, "no NTT for this ring size");
     }
 }
+
+const RescaleIO kNoRescale{};
+const GatherIO kNoGather{};
 
 // ninv: [prime][2] the constant the last inverse pass multiplies by and its
 // Shoup companion (N^-1 mod q, or N^-1 times a conversion factor, see
@@ -451,8 +483,7 @@ int run_rs(blb_ctx* ctx, uint64_t* data, uint32_t rows, const LimbMap& map, cons
 int run(blb_ctx* ctx, uint64_t* data, uint32_t rows, const LimbMap& map, const uint32_t* rowlist, bool inverse,
         const uint64_t* ninv)
 {
-    static const RescaleIO none{};
-    return run_rs<false>(ctx, data, rows, map, rowlist, inverse, ninv, none);
+    return run_io<0>(ctx, data, rows, map, rowlist, inverse, ninv, kNoRescale, kNoGather);
 }
 
 }  // namespace
@@ -545,7 +576,14 @@ int ntt_forward_rescale(blb_ctx* ctx, uint64_t* data, uint32_t rows, const Resca
 {
     if (rows == 0) return BLB_OK;
     ProfScope prof(ctx, "ntt", (uint64_t)rows * ctx->N * 16);
-    return run_rs<true>(ctx, data, rows, ctx->qmap(rs.level), nullptr, false, ctx->d_ninv, rs);
+    return run_io<1>(ctx, data, rows, ctx->qmap(rs.level), nullptr, false, ctx->d_ninv, rs, kNoGather);
+}
+
+int ntt_inverse_gather(blb_ctx* ctx, uint64_t* data, uint32_t rows, const GatherIO& ga, const uint64_t* ninv)
+{
+    if (rows == 0) return BLB_OK;
+    ProfScope prof(ctx, "intt", (uint64_t)rows * ctx->N * 16);
+    return run_io<2>(ctx, data, rows, ctx->qmap(ga.n), nullptr, true, ninv, kNoRescale, ga);
 }
 
 int ntt_forward_list(blb_ctx* ctx, uint64_t* data, uint32_t rows, const uint32_t* d_rowlist)
