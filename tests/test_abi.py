@@ -14,8 +14,13 @@ from paper_2508_19525_b300 import workloads as wl
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
+def read(*parts):
+    with open(os.path.join(ROOT, *parts)) as f:
+        return f.read()
+
+
 def declared():
-    src = open(os.path.join(ROOT, "include", "blb.h")).read()
+    src = read("include", "blb.h")
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
     names = set(re.findall(r"\b(blb_[a-z0-9_]+)\s*\(", src))
     return names - {"blb_alloc_fn", "blb_free_fn"}
@@ -32,10 +37,10 @@ def test_library_builds_and_exports_every_declared_symbol():
 
 
 def test_binding_has_no_oracle_dependency():
-    src = open(os.path.join(ROOT, "paper_2508_19525_b300", "blb.py")).read()
+    src = read("paper_2508_19525_b300", "blb.py")
     assert "oracle" not in re.sub(r'""".*?"""', "", src, flags=re.S)
     for f in os.listdir(os.path.join(ROOT, "paper_2508_19525_b300", "csrc")):
-        assert "oracle" not in open(os.path.join(ROOT, "paper_2508_19525_b300", "csrc", f)).read()
+        assert "oracle" not in read("paper_2508_19525_b300", "csrc", f)
 
 
 @pytest.mark.parametrize("prm", [wl.TINY, wl.SMALL, wl.BERT_CP, wl.BERT_CC])
@@ -69,7 +74,7 @@ def test_context_without_device_fails_cleanly():
 def test_peaks_library_exports_its_declared_symbols():
     """The benchmark's integer-rate microbenchmarks live in a library of their
     own (include/blb_peaks.h, libblb_peaks.so), not in libblb.so."""
-    src = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "blb_peaks.h")).read(), flags=re.S)
+    src = re.sub(r"/\*.*?\*/", "", read("include", "blb_peaks.h"), flags=re.S)
     names = set(re.findall(r"\b(blb_[a-z0-9_]+)\s*\(", src))
     assert names == {"blb_peaks_int_rates", "blb_peaks_reduce_rate"}
     L = ctypes.CDLL(build.build_peaks())
