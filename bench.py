@@ -1155,7 +1155,7 @@ def run_blb(args):
     # region above brackets only cp_mac)
     w.ctx.profile(True)
     prof_s, _ = timed(w, args.steps, False, world)
-    sites.update({s: w.ctx.profile_read(s) for s in ("keyswitch", "ntt", "intt")})
+    sites.update({s: w.ctx.profile_read(s) for s in ("keyswitch", "ntt", "intt", "intt_gather")})
     ks_ops = w.ctx.profile_read_ops("keyswitch")
     w.ctx.profile(False)
     int_peaks = measure_int_peaks(w.ctx.primes[0], w.stream.cuda_stream)
@@ -1272,13 +1272,14 @@ def run_blb(args):
                                       "a second pass of the same steps with every site bracketed",
                        "algorithmic_bytes_per_call": nbytes // cnt, "peak_kind": peak_note}
     # ALU roofline of the NTT sites: butterflies (rows x N/2 x log2 N; the site
-    # records 16 B per coefficient per row) per second against the measured
-    # register-only butterfly rate of the same instruction mix
+    # records 16 B per coefficient per row, 32 for the gather-fused inverse) per
+    # second against the measured register-only butterfly rate of the same
+    # instruction mix
     logn = int(np.log2(w.N))
-    for s_ in ("ntt", "intt"):
+    for s_, word_bytes in (("ntt", 16), ("intt", 16), ("intt_gather", 32)):
         if s_ in roof:
             ms, cnt, nbytes = sites[s_]
-            bfly = nbytes / 16 * logn / 2
+            bfly = nbytes / word_bytes * logn / 2
             ach = bfly / (ms / 1e3)
             roof[s_]["alu"] = {"bound": "alu", "achieved": round(ach / 1e9, 2), "peak": round(int_peaks["bfly_per_s"] / 1e9, 2),
                                "unit": "Gbutterfly/s", "frac": round(ach / int_peaks["bfly_per_s"], 4),

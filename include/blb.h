@@ -491,10 +491,14 @@ int blb_ntt_set_radix(blb_ctx* ctx, int radix);
  * Total kernel launches issued by this library in this process. */
 uint64_t blb_kernel_launches(void);
 /* When enabled, CUDA events on the context's stream bracket each launch site
- * ("ntt", "intt", "keyswitch", "cp_mac"); blb_profile_read synchronizes the
+ * ("ntt", "intt", "intt_gather", "keyswitch", "cp_mac"; "intt_gather" is the
+ * key switch's inverse transform of its sources with the automorphism's
+ * gather in its first pass, kept apart from "intt" so that the latter counts
+ * plain transforms only); blb_profile_read synchronizes the
  * stream and returns, since profiling was enabled, the summed milliseconds, the
  * number of bracketed calls and their algorithmic bytes (the minimum HBM
- * traffic of the operation: NTT one read and one write per word; key switch
+ * traffic of the operation: NTT one read and one write per word, 32 bytes per
+ * word for "intt_gather" with the gather's read and digit write; key switch
  * its input, the used key digits and its output; cp_mac every plaintext, every
  * baby-step ciphertext and every partial sum once).  Enabling resets the sums. */
 int blb_profile_enable(blb_ctx* ctx, int on);

@@ -190,6 +190,7 @@ struct blb_ctx {
     // digit for a ciphertext prime, P for a special prime): the inverse NTT
     // that feeds a base conversion applies the conversion's first factor
     uint64_t* d_ninv_conv = nullptr;
+    uint64_t* d_ql_inv = nullptr;     // [l][i][2]: q_l^-1 mod q_i and its Shoup companion (i < l < nQ)
     double2* d_zeta = nullptr;        // [N]: (cos, sin)(pi k / N)
     uint64_t* d_cdt = nullptr;        // [19]
     uint32_t* d_kperm = nullptr;      // [N/2]: k_j = (5^j mod 2N - 1)/4
@@ -387,9 +388,9 @@ struct RescaleIO {
     const uint64_t* last;
     const uint64_t* in;
     uint64_t* out;
+    const uint64_t* inv;  // [i][2]: q_level^-1 mod q_i and its Shoup companion (device)
     size_t stride;
     uint32_t level, ppc;
-    uint64_t inv[BLB_MAXP], inv_sh[BLB_MAXP];
 };
 int ntt_forward_rescale(blb_ctx* ctx, uint64_t* data, uint32_t rows, const RescaleIO& rs);
 // A key-switch source: its c1 rows (evaluation domain) and the Galois element

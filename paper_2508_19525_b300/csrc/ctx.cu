@@ -544,6 +544,15 @@ extern "C" int blb_ctx_create(const blb_params* params, void* stream, blb_ctx** 
             }
         if ((rc = upload(c, &c->d_ninv_conv, nc.data(), nc.size()))) return fail(rc);
     }
+    {  // the rescale's q_l^-1 mod q_i with Shoup companions, [l][i][2]
+        std::vector<uint64_t> qi((size_t)c->nQ * c->nQ * 2, 0);
+        for (uint32_t l = 1; l < c->nQ; l++)
+            for (uint32_t i = 0; i < l; i++) {
+                qi[((size_t)l * c->nQ + i) * 2] = c->ql_inv[l][i];
+                qi[((size_t)l * c->nQ + i) * 2 + 1] = shoup_companion(c->ql_inv[l][i], c->q[i]);
+            }
+        if ((rc = upload(c, &c->d_ql_inv, qi.data(), qi.size()))) return fail(rc);
+    }
 
     // scratch arena: key-switch region + operation temporaries
     {
@@ -593,6 +602,7 @@ static void ctx_destroy(blb_ctx* c)
     dev_free(c, c->d_tw, (size_t)c->np * 4 * c->N * 8);
     dev_free(c, c->d_ninv, c->np * 16);
     dev_free(c, c->d_ninv_conv, (size_t)c->nQ * c->np * 16);
+    dev_free(c, c->d_ql_inv, (size_t)c->nQ * c->nQ * 16);
     dev_free(c, c->d_zeta, (size_t)c->N * sizeof(double2));
     dev_free(c, c->d_cdt, 19 * 8);
     dev_free(c, c->d_kperm, (size_t)c->N / 2 * 4);

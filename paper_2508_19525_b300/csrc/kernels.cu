@@ -300,10 +300,7 @@ int launch_rescale_strided(blb_ctx* ctx, uint64_t* out, const uint64_t* in, uint
         rs.stride = stride;
         rs.level = level;
         rs.ppc = ppc;
-        for (uint32_t i = 0; i < level; i++) {
-            rs.inv[i] = ctx->ql_inv[level][i];
-            rs.inv_sh[i] = shoup_companion(rs.inv[i], ctx->q[i]);
-        }
+        rs.inv = ctx->d_ql_inv + (size_t)level * ctx->nQ * 2;
         if ((rc = ntt_forward_rescale(ctx, T, npolys * level, rs))) break;
     } while (0);
     if (tmp) dev_free(ctx, tmp, need * 8);

@@ -363,8 +363,8 @@ __global__ void __launch_bounds__(kThreads, ntt_ctas(RB)) k_ntt(uint64_t* __rest
         rr.out = rs.out + (size_t)row * G_::N;
         rr.ql = qs[rs.level];
         rr.rb = bar[2 * pi + 1];
-        rr.inv = rs.inv[i];
-        rr.inv_sh = rs.inv_sh[i];
+        rr.inv = rs.inv[2 * i];
+        rr.inv_sh = rs.inv[2 * i + 1];
     }
     if (GA && FIRST) {  // row = source n + prime
         const uint32_t src = row / ga.n, i = row % ga.n;
@@ -582,7 +582,9 @@ int ntt_forward_rescale(blb_ctx* ctx, uint64_t* data, uint32_t rows, const Resca
 int ntt_inverse_gather(blb_ctx* ctx, uint64_t* data, uint32_t rows, const GatherIO& ga, const uint64_t* ninv)
 {
     if (rows == 0) return BLB_OK;
-    ProfScope prof(ctx, "intt", (uint64_t)rows * ctx->N * 16);
+    // a site of its own (inside the key-switch site): besides the transform's
+    // 16 bytes per word it reads the permuted source and writes the digit row
+    ProfScope prof(ctx, "intt_gather", (uint64_t)rows * ctx->N * 32);
     return run_io<2>(ctx, data, rows, ctx->qmap(ga.n), nullptr, true, ninv, kNoRescale, ga);
 }
 

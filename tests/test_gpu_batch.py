@@ -66,6 +66,8 @@ def test_batch_rejects_mixed_levels():
         ctx.encrypt_batch(keys, [ctx.encode(v, level), ctx.encode(v, level - 1)], [1, 2])
 
 
+# the two refused captures end empty (the library refuses before it launches)
+@pytest.mark.filterwarnings("ignore:The CUDA Graph is empty")
 def test_masking_and_decryption_replay_from_a_graph():
     """The batched masking and decryption captured into a CUDA graph (their
     host tables go to buffers the context keeps, so a replay never reads
