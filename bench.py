@@ -921,7 +921,7 @@ def layernorm_bench(steps, seqs=(1, 8)):
         torch.cuda.synchronize()
         ms = ev0.elapsed_time(ev1) / steps
         out["per_call"][str(S)] = {"ms": round(ms, 3), "tokens_per_s": round(S * L / (ms / 1e3), 1)}
-    Xm, var = ctx.layernorm_head(keys, cts, L, D, nc)
+    _, var = ctx.layernorm_head(keys, cts, L, D, nc)
     v = ctx.decrypt(keys, var[0], coeffs=False)[1].reshape(k, L)
     out["max_abs_err_var_vs_fp64"] = float(np.abs(v - X.var(axis=1)[None, :]).max())
     return out
@@ -1212,7 +1212,7 @@ def run_blb(args):
                                                bt_rot(per * M, D, D_O, w.N // 2, w.b1_2[1])],
                 "plaintext_bytes": w.plan_qkv2.info()["plaintext_bytes"] + w.plan_o2.info()["plaintext_bytes"]}
             w.free_packed()
-        best = max((v for k_, v in batched.items() if isinstance(v, dict)), key=lambda v: v["value"])
+        best = max((v for v in batched.values() if isinstance(v, dict)), key=lambda v: v["value"])
         batched.update(value=best["value"], unit=UNIT, ms_per_step=best["ms_per_step"],
                        speedup_vs_plain=best["speedup_vs_plain"])
     # the same step with its products, masking and decryption replayed from a
