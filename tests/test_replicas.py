@@ -41,7 +41,7 @@ def _rank(rank, world, port, out):
 
 def test_two_gloo_ranks_aggregate_over_the_slowest_replica():
     world, port = 2, _free_port()
-    with mp.Manager() as mgr:
+    with mp.get_context("spawn").Manager() as mgr:
         out = mgr.dict()
         mp.spawn(_rank, args=(world, port, out), nprocs=world, join=True)
         res = dict(out)
@@ -71,7 +71,7 @@ def _ref_rank(rank, world, out):
 
 def test_reference_arm_runs_on_rank_zero_only():
     world = 2
-    with mp.Manager() as mgr:
+    with mp.get_context("spawn").Manager() as mgr:
         out = mgr.dict()
         mp.spawn(_ref_rank, args=(world, out), nprocs=world, join=True)
         res = dict(out)
