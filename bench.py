@@ -987,7 +987,7 @@ def serving_bench(n_requests=64, rate=20.0, sat_rate=400.0, budget_gb=24, max_ba
     return out
 
 
-def serving_n65536_bench(n_requests=32, rate=20.0, light_rate=2.0, n_light=12, budget_gb=80, max_batch=4, group=2,
+def serving_n65536_bench(n_requests=32, rate=20.0, light_rate=2.0, n_light=12, budget_gb=80, max_batch=4, group=4,
                        m=32, b1=32, m_batched=128, b1_batched=32):
     """Continuous batching at the serving configuration's own parameters:
     N = 2^16, 12 primes, dnum 4; Poisson arrivals at `rate` req/s, half
