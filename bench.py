@@ -1242,9 +1242,9 @@ def run_blb(args):
             return None
         try:
             return fn()
-        except blb.BlbError as e:
+        except (blb.BlbError, torch.OutOfMemoryError) as e:
             torch.cuda.empty_cache()
-            return {"error": str(e)}
+            return {"error": str(e)[:300]}
 
     bl_batch = section(args.bert_large_seqs, lambda: bert_large_batching(args.bert_large_seqs))
     lnorm = section(args.layernorm, lambda: layernorm_bench(max(2, min(10, args.steps // 5))))
