@@ -79,3 +79,29 @@ def test_cc_sequences_packed_as_heads_give_each_sequence_its_product(s, L, heads
     got = bt.split_heads(cs.unpack_diagonals(C, L, Hg, Kc), S)
     for j in range(S):
         assert np.allclose(got[j], np.einsum("hik,hkj->hij", A[j], B[j]), atol=1e-12)
+
+
+def test_rotation_count_per_token_falls_with_rows_per_ciphertext():
+    """The rotation count of one m-row product: baby steps per input
+    ciphertext plus giant steps per output ciphertext, checked against a
+    direct count of the BSGS schedule's rotations (every nonzero baby-step
+    rotation of every input, every nonzero giant-step rotation of every
+    output); per token it falls as m grows for the BERT-large products."""
+    slots = 32768
+    for d, d_out in ((1024, 3072), (1024, 4096), (4096, 1024), (768, 2304)):
+        per_token = []
+        for m in (32, 64, 128, 256):
+            k = slots // m
+            nX, nY = -(-d // k), -(-d_out // k)
+            cands = bt.cp_b1_candidates(m, d, d_out, slots)
+            assert cands == sorted(cands) and all(k % b == 0 and b < k for b in cands)
+            best = min(range(1, k.bit_length()), key=lambda i: bt.cp_rotation_count(m, d, d_out, slots, 1 << i))
+            assert (1 << best) in cands
+            for b1 in cands:
+                G = k // b1
+                direct = sum(1 for _ in range(nX) for b in range(b1) if b) + \
+                    sum(1 for _ in range(nY) for g in range(G) if g)
+                assert bt.cp_rotation_count(m, d, d_out, slots, b1) == direct
+                assert set(bt.cp_rotations(m, k, b1)) == {b * m for b in range(1, b1)} | {g * b1 * m for g in range(1, G)}
+            per_token.append(min(bt.cp_rotation_count(m, d, d_out, slots, b) for b in cands) / m)
+        assert all(a > b for a, b in zip(per_token, per_token[1:])), per_token
